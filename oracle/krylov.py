@@ -1,0 +1,132 @@
+"""Krylov base cases in FP64: CG, Lanczos, Gauss quadrature, SLQ.  Test infrastructure only.
+
+Table 5 (App. C.2) names CG as the base case for PSD solves, Lanczos for
+self-adjoint eigenproblems and stochastic Lanczos quadrature (SLQ) for f(A)
+of self-adjoint A.  App. A.2 defines log det A = Tr(log A), which SLQ
+estimates with Rademacher probes z: E[z^T log(A) z] = Tr(log A) (Sec. 3.3 /
+App. B.1 trace estimator).  The Lanczos stopping rule mirrors the Arnoldi
+breakdown test of Algorithm 1 (stop when the new off-diagonal falls below a
+tolerance).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+
+def cg(op, b, tol=1e-10, maxiter=None, precond_diag=None, x0=None):
+    """Textbook (preconditioned) conjugate gradients on one right-hand side.
+
+    Stops when the recursive residual satisfies ||r|| <= tol * ||b||.
+    Returns (x, iterations).  ``precond_diag`` is the Jacobi diagonal M.
+    """
+    b = np.asarray(b, dtype=np.float64)
+    n = b.shape[0]
+    maxiter = n if maxiter is None else maxiter
+    x = np.zeros(n) if x0 is None else np.array(x0, dtype=np.float64)
+    r = b - (op @ x) if x0 is not None else b.copy()
+    z = r / precond_diag if precond_diag is not None else r.copy()
+    p = z.copy()
+    rz = float(r @ z)
+    bnorm = float(np.linalg.norm(b))
+    if bnorm == 0.0:
+        return x, 0
+    it = 0
+    while np.linalg.norm(r) > tol * bnorm and it < maxiter:
+        Ap = op @ p
+        pAp = float(p @ Ap)
+        if not pAp > 0.0:
+            raise FloatingPointError("CG breakdown: p^T A p <= 0")
+        alpha = rz / pAp
+        x = x + alpha * p
+        r = r - alpha * Ap
+        z = r / precond_diag if precond_diag is not None else r
+        rz_new = float(r @ z)
+        beta = rz_new / rz
+        rz = rz_new
+        p = z + beta * p
+        it += 1
+    return x, it
+
+
+def true_relative_residual(op, B, X):
+    """||b - A x|| / ||b|| per right-hand side (rows of B, X)."""
+    B = np.atleast_2d(B)
+    X = np.atleast_2d(X)
+    R = B - op.mvm(X)
+    return np.linalg.norm(R, axis=1) / np.linalg.norm(B, axis=1)
+
+
+def lanczos(op, z, m, reorth=True, breakdown_tol=1e-10):
+    """m steps of symmetric Lanczos from q_0 = z / ||z||.
+
+    Recurrence: w = A q_j - beta_{j-1} q_{j-1}; alpha_j = q_j^T w;
+    w -= alpha_j q_j; (full reorthogonalisation against all previous q when
+    ``reorth``); beta_j = ||w||; stop when beta_j <= breakdown_tol * max|alpha|;
+    q_{j+1} = w / beta_j.
+
+    Returns (alpha[m_eff], beta[m_eff - 1], Q[m_eff, N]).
+    """
+    z = np.asarray(z, dtype=np.float64)
+    q = z / np.linalg.norm(z)
+    Q = [q]
+    alphas, betas = [], []
+    q_prev = np.zeros_like(q)
+    beta_prev = 0.0
+    for j in range(m):
+        w = op @ Q[j] - beta_prev * q_prev
+        a = float(Q[j] @ w)
+        w = w - a * Q[j]
+        if reorth:
+            for _ in range(2):
+                for qi in Q:
+                    w = w - float(qi @ w) * qi
+        alphas.append(a)
+        if j == m - 1:
+            break
+        beta = float(np.linalg.norm(w))
+        if beta <= breakdown_tol * max(abs(x) for x in alphas):
+            break
+        betas.append(beta)
+        q_prev = Q[j]
+        beta_prev = beta
+        Q.append(w / beta)
+    return np.array(alphas), np.array(betas), np.array(Q[: len(alphas)])
+
+
+def tridiagonal(alpha, beta):
+    T = np.diag(alpha)
+    if len(beta):
+        T += np.diag(beta, 1) + np.diag(beta, -1)
+    return T
+
+
+def gauss_quadrature(alpha, beta, f):
+    """sum_k S_{0k}^2 f(theta_k) with T_m = S diag(theta) S^T: the m-point Gauss
+    rule for q_0^T f(A) q_0 (exact for polynomials of degree <= 2m - 1)."""
+    theta, S = np.linalg.eigh(tridiagonal(alpha, beta))
+    return float(np.sum(S[0, :] ** 2 * f(theta))), theta, S[0, :]
+
+
+def slq_logdet(op, probes, m, reorth=True):
+    """Stochastic Lanczos quadrature for log det A = Tr(log A).
+
+    For each probe z: ||z||^2 * sum_k S_{0k}^2 log(theta_k).  Returns
+    (mean over probes, standard error of the mean, per-probe values).
+    A Ritz value <= 0 is an error (A must be positive definite).
+    """
+    vals = []
+    for z in np.atleast_2d(probes):
+        a, b, _ = lanczos(op, z, m, reorth=reorth)
+        theta, S = np.linalg.eigh(tridiagonal(a, b))
+        if np.any(theta <= 0.0):
+            raise FloatingPointError("non-positive Ritz value in SLQ")
+        vals.append(float(z @ z) * float(np.sum(S[0, :] ** 2 * np.log(theta))))
+    vals = np.array(vals)
+    se = float(np.std(vals, ddof=1) / np.sqrt(len(vals))) if len(vals) > 1 else float("nan")
+    return float(np.mean(vals)), se, vals
+
+
+def quadrature_logdet_from_tridiag(alpha, beta, znorm2):
+    """Per-probe SLQ value from given Lanczos coefficients."""
+    theta, S = np.linalg.eigh(tridiagonal(alpha, beta))
+    return znorm2 * float(np.sum(S[0, :] ** 2 * np.log(theta)))

@@ -1,0 +1,280 @@
+/*
+ * cola.h - C ABI of the GB300 (sm_103a) compositional linear-algebra library.
+ *
+ * Operators are trees of linear maps defined by their MVM (CoLA Sec. 3.1):
+ * Dense, Diagonal and LowRank leaves composed by Sum, Product, Kronecker and
+ * Kronecker sum (Sec. 3.2).  On top of the MVM the library runs conjugate
+ * gradients (Table 5, PSD base case), Lanczos and stochastic Lanczos
+ * quadrature for log det A = Tr(log A) (App. A.2, Table 5), and the adjoint
+ * rules of App. B.2 for gradients with respect to the operator's leaves.
+ *
+ * Conventions shared by every call:
+ *  - All array arguments are DEVICE pointers unless the comment says host.
+ *    Leaf data is BORROWED: the library keeps the pointer, never copies or
+ *    frees it; the caller keeps it alive (and unchanged in structure) until
+ *    the linop and every linop built from it are released.
+ *  - Matrices are row-major; `ld` is the distance between rows in elements.
+ *  - Vectors are row-major (C order) over the Kronecker index:
+ *    (K_1 (x) ... (x) K_d) vec(X) = vec(K_1 X ... ) with entry (i_1..i_d) at
+ *    ((i_1 n_2 + i_2) n_3 + ...).  A block of R vectors is [R][N], contiguous.
+ *  - Every call returns cola_status; COLA_OK is 0.  On error the message of
+ *    the calling thread's last failure is available from cola_last_error().
+ *    Results of a failed call are unspecified unless its comment says so.
+ *  - `stream` is a cudaStream_t (NULL = the legacy default stream).  Calls
+ *    are ordered after prior work on `stream`; calls documented as
+ *    synchronous return after their results are complete, the others only
+ *    enqueue work.
+ *  - A context owns device workspace, cached launch plans and CUDA graphs.
+ *    A context must not be used by two host threads at the same time.
+ */
+#ifndef COLA_GB300_H
+#define COLA_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct cola_ctx cola_ctx;
+typedef struct cola_linop cola_linop;
+typedef void* cola_stream;
+
+typedef enum {
+  COLA_OK = 0,
+  COLA_ERR_INVALID_ARG = 1,
+  COLA_ERR_SHAPE = 2,
+  COLA_ERR_DTYPE = 3,
+  COLA_ERR_BREAKDOWN = 4,      /* CG: p^T A p <= 0 or NaN (operator not SPD in working precision) */
+  COLA_ERR_NOT_CONVERGED = 5,  /* tolerance not reached in maxiter; results still written */
+  COLA_ERR_TIMEOUT = 6,
+  COLA_ERR_CUDA = 7,
+  COLA_ERR_OOM = 8,
+  COLA_ERR_UNSUPPORTED = 9     /* composition the GPU path does not implement */
+} cola_status;
+
+typedef enum { COLA_F64 = 0, COLA_F32 = 1 } cola_dtype;
+
+/* Arithmetic of the MVM and Krylov recurrences.
+ *  F64   : FP64 everywhere (vectors FP64).
+ *  F32   : FP32 SIMT MVM and FP32 recurrences (vectors FP32).
+ *  MIXED : Kronecker contractions on tcgen05 tensor cores with BF16 split
+ *          operands (hi + lo [+ lo2] terms) and FP32 accumulation in TMEM,
+ *          FP32 recurrences (vectors FP32).  Non-Kronecker terms as F32. */
+typedef enum { COLA_PREC_F64 = 0, COLA_PREC_F32 = 1, COLA_PREC_MIXED = 2 } cola_precision;
+
+typedef enum {
+  COLA_LEAF_DENSE = 0, COLA_LEAF_DIAG = 1, COLA_LEAF_SCALAR = 2, COLA_LEAF_LOWRANK = 3
+} cola_leaf_kind;
+
+/* Message of the calling thread's most recent failure ("" if none). */
+const char* cola_last_error(void);
+
+/* ---------------------------------------------------------------- context */
+
+/* Create a context on CUDA device `device`.  *out receives the handle. */
+cola_status cola_create(int device, cola_ctx** out);
+/* Free the context's workspace, plans and graphs.  Linops built on it must
+ * be released first. */
+cola_status cola_destroy(cola_ctx* ctx);
+
+/* --------------------------------------------------------------- operators */
+
+/* Dense leaf (Sec. 3.1): rows x cols, row-major with leading dimension ld,
+ * element type dtype.  Borrowed. */
+cola_status cola_linop_dense(cola_ctx* ctx, int64_t rows, int64_t cols, const void* data,
+                             int64_t ld, cola_dtype dtype, cola_linop** out);
+
+/* Diagonal leaf (Sec. 3.1): [Diag(d) v]_i = d_i v_i, n x n.
+ * stride 1: d holds n entries.  stride 0: d holds ONE entry s, read on the
+ * device at every use, and the operator is s * I (a differentiable scalar,
+ * e.g. a noise variance).  Borrowed. */
+cola_status cola_linop_diag(cola_ctx* ctx, int64_t n, const void* d, int64_t stride,
+                            cola_dtype dtype, cola_linop** out);
+
+/* Low-rank leaf U V^T (the low-rank term of the Woodbury rule, App. A.1.1):
+ * U is n x k row-major, V is n x k row-major or NULL for U U^T.  Borrowed. */
+cola_status cola_linop_lowrank(cola_ctx* ctx, int64_t n, int64_t k, const void* U,
+                               const void* V, cola_dtype dtype, cola_linop** out);
+
+/* Kronecker product K_1 (x) ... (x) K_d (Sec. 3.2, Table 3: MVM cost
+ * tau_A N_B + N_A tau_B).  Factors must be Dense leaves (any shape).
+ * The node takes a reference on each factor. */
+cola_status cola_linop_kron(cola_ctx* ctx, int nfactors, cola_linop* const* factors,
+                            cola_linop** out);
+
+/* Kronecker sum A_1 (+) ... (+) A_d = sum_k I (x) .. A_k .. (x) I (Sec. 3.2,
+ * App. A.1.2).  Factors must be square Dense leaves.  A factor whose entries
+ * are zero outside the three central diagonals is applied as a tridiagonal
+ * stencil; that check reads the factor once, at this call, so its data must
+ * be valid here. */
+cola_status cola_linop_kronsum(cola_ctx* ctx, int nfactors, cola_linop* const* factors,
+                               cola_linop** out);
+
+/* Sum  sum_i c_i A_i (Sec. 3.2); coeffs is a HOST array of nterms doubles or
+ * NULL for all ones.  All terms must have the same shape. */
+cola_status cola_linop_sum(cola_ctx* ctx, int nterms, cola_linop* const* terms,
+                           const double* coeffs, cola_linop** out);
+
+/* Product A_1 A_2 ... A_m (Sec. 3.2), applied right to left. */
+cola_status cola_linop_product(cola_ctx* ctx, int nterms, cola_linop* const* terms,
+                               cola_linop** out);
+
+/* PSD / self-adjoint annotation (Sec. 3.2 decorators).  CG, Lanczos and the
+ * adjoint solve require spd = 1 (they return COLA_ERR_INVALID_ARG otherwise). */
+cola_status cola_linop_set_spd(cola_linop* op, int spd);
+
+cola_status cola_linop_shape(const cola_linop* op, int64_t* rows, int64_t* cols);
+
+/* Leaves in tree order (depth first, left to right; App. B.2 flatten).
+ * kind is a cola_leaf_kind; rows x cols is the shape of the leaf's
+ * parameter array (SCALAR: 1 x 1, DIAG: n x 1, LOWRANK: n x k for U). */
+cola_status cola_linop_num_leaves(const cola_linop* op, int* n);
+cola_status cola_linop_leaf_info(const cola_linop* op, int index, int* kind, int64_t* rows,
+                                 int64_t* cols);
+
+/* Drop the caller's reference; the node is freed when no parent holds it. */
+cola_status cola_linop_release(cola_linop* op);
+
+/* --------------------------------------------------------------------- MVM */
+
+/* Y = A X for nrhs vectors (Sec. 3.1).  X is [nrhs][cols], Y is [nrhs][rows],
+ * both FP64 for COLA_PREC_F64 and FP32 otherwise.  Asynchronous on stream. */
+cola_status cola_matvec(cola_ctx* ctx, const cola_linop* op, const void* X, void* Y,
+                        int64_t nrhs, cola_precision precision, cola_stream stream);
+
+/* -------------------------------------------------------------- CG solves */
+
+typedef struct {
+  double tol;                   /* target ||b - A x||_2 / ||b||_2 for EVERY right-hand side */
+  int64_t maxiter;              /* cap on CG iterations (all chunks together) */
+  int32_t precision;            /* cola_precision of MVM + recurrence */
+  int32_t refine;               /* F32/MIXED: 1 = FP64 solution and FP64 true residual
+                                   b - A x replacing the recursive one (reliable updates) */
+  double reliable_delta;        /* replace the residual once the recursive residual norm fell
+                                   by this factor since the last replacement (e.g. 0.1) */
+  int32_t max_updates;          /* cap on FP64 residual replacements */
+  int32_t split_factor_terms;   /* MIXED: BF16 terms per Kronecker-factor entry, 1..3 */
+  int32_t split_vector_terms;   /* MIXED: BF16 terms per vector entry, 1..3 */
+  int32_t graph_chunk;          /* iterations per CUDA-graph replay between host checks */
+  int32_t jacobi;               /* 1 = Jacobi preconditioner M = Diag(A) from the Diag rules */
+  int32_t x0_given;             /* 1 = X holds the initial guess, 0 = start from x = 0 */
+} cola_cg_opts;
+
+typedef struct {
+  int64_t iterations;           /* CG iterations this right-hand side took */
+  double rel_residual;          /* final relative residual (FP64 true residual when refined
+                                   or precision F64; recursive one otherwise) */
+  int32_t updates;              /* FP64 residual replacements performed */
+  int32_t status;               /* cola_status of this right-hand side */
+} cola_cg_info;
+
+/* Fill opts with defaults: tol 1e-8, maxiter 100000, MIXED, refine 1,
+ * reliable_delta 0.1, max_updates 200, split terms 2/2, graph_chunk 64,
+ * jacobi 0, x0_given 0. */
+void cola_cg_opts_default(cola_cg_opts* opts);
+
+/* Solve A X = B for nrhs right-hand sides by (preconditioned) conjugate
+ * gradients (Table 5 PSD base case), stopping when every right-hand side
+ * reaches opts->tol (the all-solves rule of App. D GP training).
+ * B, X are [nrhs][N]: FP64 when precision is F64 or refine = 1, FP32 else.
+ * info (HOST, nrhs entries, may be NULL) receives per-RHS results.
+ * Synchronous.  Returns COLA_ERR_NOT_CONVERGED / COLA_ERR_BREAKDOWN with X
+ * written as far as it got. */
+cola_status cola_cg_solve(cola_ctx* ctx, const cola_linop* op, const void* B, void* X,
+                          int64_t nrhs, const cola_cg_opts* opts, cola_cg_info* info,
+                          cola_stream stream);
+
+/* Many independent SPD systems in one call: system s is ops[s] with
+ * nrhs[s] right-hand sides B[s], X[s] (HOST arrays of device pointers, same
+ * dtype rule as cola_cg_solve).  The systems advance together through
+ * batched kernels driven by integer work tables (system, tile) that the
+ * host builds once; converged systems retire from the tables.  info is HOST,
+ * sum(nrhs) entries in system order.  Synchronous. */
+cola_status cola_cg_solve_batched(cola_ctx* ctx, int32_t nsys, const cola_linop* const* ops,
+                                  const void* const* B, void* const* X, const int64_t* nrhs,
+                                  const cola_cg_opts* opts, cola_cg_info* info,
+                                  cola_stream stream);
+
+/* --------------------------------------------------------- Lanczos / SLQ */
+
+/* m steps of symmetric Lanczos from q_0 = Q0[v] / ||Q0[v]|| for nvec starting
+ * vectors at once (Table 5 self-adjoint base case; stop rule as the Arnoldi
+ * breakdown test of Algorithm 1).  Q0 is [nvec][N] (FP64 for F64 precision,
+ * FP32 else).  alpha [nvec][m] and beta [nvec][m] are FP64 device arrays;
+ * row v holds alpha_0..alpha_{m_eff-1} and beta_0..beta_{m_eff-2}.  m_eff
+ * [nvec] (int32, device) is where vector v stopped: breakdown at
+ * beta_j <= 1e-10 (F64) / 1e-6 (F32) times max|alpha| truncates it (not an
+ * error).  reorth = 1 adds full reorthogonalisation (stores all q: nvec*m*N
+ * elements of workspace).  Asynchronous. */
+cola_status cola_lanczos(cola_ctx* ctx, const cola_linop* op, const void* Q0, int64_t nvec,
+                         int32_t m, int32_t precision, int32_t reorth, double* alpha,
+                         double* beta, int32_t* m_eff, cola_stream stream);
+
+/* Stochastic Lanczos quadrature for log det A = Tr(log A) (App. A.2):
+ * nprobes Rademacher probes z_v drawn on the device from `seed` (entry
+ * (v, i) = sign of the top bit of SplitMix64 output v*N + i), or taken from
+ * `probes` ([nprobes][N], same dtype as cola_lanczos's Q0) when it is not
+ * NULL; m Lanczos steps each; per probe ||z||^2 sum_k S_0k^2 log(theta_k)
+ * from the eigendecomposition of T_m computed on the device in FP64.
+ * logdet, std_err are HOST doubles (mean over probes, sample standard error);
+ * per_probe (device FP64 [nprobes]) may be NULL.  A Ritz value <= 0 (low
+ * precision) is clamped to the smallest positive one; the count of clamps is
+ * written to *clamped (HOST, may be NULL).  Synchronous. */
+cola_status cola_slq_logdet(cola_ctx* ctx, const cola_linop* op, int32_t nprobes, int32_t m,
+                            uint64_t seed, const void* probes, int32_t precision,
+                            int32_t reorth, double* logdet, double* std_err,
+                            double* per_probe, int32_t* clamped, cola_stream stream);
+
+/* ------------------------------------------------------------- gradients */
+
+/* Leaf gradients of the weighted bilinear form sum_r w_r u_r^T A x_r
+ * (App. B.2): for every leaf theta, grads[l] (+)= sum_r w_r u_r^T (dA/dtheta) x_r
+ * in the leaf's shape and dtype (DENSE rows x cols, DIAG n, SCALAR 1,
+ * LOWRANK n x k for U).  U is [nrhs][rows], X is [nrhs][cols] (FP64 for F64
+ * precision, FP32 else); weights is a HOST array (NULL = ones).  grads is a
+ * HOST array of num_leaves device pointers; a NULL entry skips that leaf.
+ * accumulate = 0 overwrites.  Asynchronous. */
+cola_status cola_bilinear_grad(cola_ctx* ctx, const cola_linop* op, const void* U,
+                               const void* X, const double* weights, int64_t nrhs,
+                               int32_t precision, void* const* grads, int32_t accumulate,
+                               cola_stream stream);
+
+/* Backward of X = A^-1 B (App. B.2 rule 1):  gradB = A^-T gradX (a second CG
+ * solve with the same kernels; A is SPD so A^T = A) and, per leaf,
+ * grads[l] = - sum_r (A^-T gradX_r)^T (dA/dtheta) X_r.  X, gradX, gradB follow
+ * the dtype rule of cola_cg_solve; no Krylov iterate of the forward solve is
+ * needed.  info as in cola_cg_solve for the adjoint solve.  Synchronous. */
+cola_status cola_solve_backward(cola_ctx* ctx, const cola_linop* op, const void* X,
+                                const void* gradX, void* gradB, int64_t nrhs,
+                                void* const* grads, const cola_cg_opts* opts,
+                                cola_cg_info* info, cola_stream stream);
+
+/* Log-det gradient d log det A / dtheta = Tr(A^-1 dA/dtheta) (App. B.2 rule 4)
+ * by Hutchinson probes (App. B.1):
+ * grads[l] (+)= scale / nprobes * sum_k (A^-1 z_k)^T (dA/dtheta) z_k.
+ * Z is [nprobes][N]; AinvZ holds A^-1 Z from an earlier block solve or is
+ * NULL to solve here with opts.  Same dtype rule as cola_cg_solve.
+ * accumulate = 0 overwrites.  Synchronous. */
+cola_status cola_logdet_backward(cola_ctx* ctx, const cola_linop* op, const void* Z,
+                                 const void* AinvZ, int64_t nprobes, double scale,
+                                 void* const* grads, int32_t accumulate,
+                                 const cola_cg_opts* opts, cola_stream stream);
+
+/* ------------------------------------------------------------- utilities */
+
+/* Fill out [count] (device, FP64 or FP32 by dtype) with Rademacher signs of
+ * SplitMix64 outputs offset .. offset+count-1 of `seed` (the probe
+ * generator of cola_slq_logdet).  Asynchronous. */
+cola_status cola_rademacher(cola_ctx* ctx, uint64_t seed, int64_t offset, int64_t count,
+                            void* out, cola_dtype dtype, cola_stream stream);
+
+/* Number of kernels this library launched (or recorded into replayed graphs,
+ * counted per replay) since the context was created. */
+cola_status cola_kernel_launches(const cola_ctx* ctx, int64_t* count);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* COLA_GB300_H */

@@ -1,0 +1,233 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <map>
+#include <string>
+#include <vector>
+
+#include "../../include/cola.h"
+
+namespace cola {
+
+// ---------------------------------------------------------------- errors
+struct Failure {
+  cola_status status;
+};
+[[noreturn]] void fail(cola_status st, const char* fmt, ...);
+void set_error_message(const char* msg);
+void clear_error();
+
+#define COLA_CUDA(x)                                                                     \
+  do {                                                                                   \
+    cudaError_t e_ = (x);                                                                \
+    if (e_ != cudaSuccess)                                                               \
+      ::cola::fail(COLA_ERR_CUDA, "%s:%d: %s: %s", __FILE__, __LINE__, #x,               \
+                   cudaGetErrorString(e_));                                              \
+  } while (0)
+
+#define COLA_REQUIRE(cond, st, ...)                                                      \
+  do {                                                                                   \
+    if (!(cond)) ::cola::fail(st, __VA_ARGS__);                                          \
+  } while (0)
+
+// Runs `body` and converts internal failures into a status code.
+template <typename F>
+cola_status guard(F&& body) {
+  try {
+    clear_error();
+    body();
+    return COLA_OK;
+  } catch (const Failure& f) {
+    return f.status;
+  }
+}
+
+// -------------------------------------------------------------- workspace
+struct Buf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+struct Workspace {
+  std::map<std::string, Buf> bufs;
+  uint64_t generation = 0;  // bumps whenever any buffer moves (graphs key on it)
+  void* get(const std::string& name, size_t bytes);
+  void release_all();
+};
+
+struct GraphEntry {
+  cudaGraphExec_t exec = nullptr;
+  int64_t kernels = 0;  // kernel nodes per replay
+  uint64_t generation = 0;
+};
+
+struct Ctx {
+  int device = 0;
+  int num_sms = 0;
+  cudaStream_t s = nullptr;   // internal stream; all work runs here
+  cudaEvent_t ev_a = nullptr, ev_b = nullptr;
+  Workspace ws;
+  int64_t launches = 0;
+  bool capturing = false;
+  int64_t captured = 0;
+  std::map<std::string, GraphEntry> graphs;
+  void* pinned = nullptr;     // small host staging area (pinned)
+  size_t pinned_bytes = 0;
+  void* host_pinned(size_t bytes);
+  void count_launch() {
+    if (capturing)
+      ++captured;
+    else
+      ++launches;
+  }
+};
+
+// Orders the internal stream after the caller's stream on entry and the
+// caller's stream after the internal one on exit.
+struct StreamJoin {
+  Ctx* c;
+  cudaStream_t user;
+  StreamJoin(Ctx* c_, cola_stream s);
+  ~StreamJoin();
+};
+
+}  // namespace cola
+
+struct cola_ctx : cola::Ctx {};
+
+// ----------------------------------------------------------------- linops
+enum LinKind { LK_DENSE, LK_DIAG, LK_LOWRANK, LK_KRON, LK_KRONSUM, LK_SUM, LK_PRODUCT };
+
+struct cola_linop {
+  cola_ctx* ctx = nullptr;
+  uint64_t uid = 0;             // unique per node for the life of the process
+  LinKind kind = LK_DENSE;
+  int64_t rows = 0, cols = 0;
+  int refs = 1;
+  int spd = 0;
+  // leaves
+  const void* data = nullptr;   // dense matrix / diagonal / U
+  const void* data2 = nullptr;  // V of a low-rank leaf (nullptr: U U^T)
+  int64_t ld = 0;               // dense leading dimension
+  int64_t stride = 1;           // diag: 1 vector, 0 scalar
+  int64_t rank = 0;             // low-rank k
+  cola_dtype dtype = COLA_F64;
+  // compositions
+  std::vector<cola_linop*> kids;
+  std::vector<double> coeffs;
+  // tridiagonal band of a Kronecker-sum factor: lo[i]=A[i,i-1], di[i]=A[i,i], up[i]=A[i,i+1]
+  bool tridiag = false;
+  std::vector<double> band_host;  // 3*n
+  // converted copies of borrowed leaf data, owned here
+  std::map<int, cola::Buf> derived;
+  ~cola_linop();
+};
+
+namespace cola {
+
+enum DerivedKey {
+  DK_F64 = 0, DK_F32 = 1, DK_BAND64 = 2, DK_BAND32 = 3,
+  DK_V_F64 = 4, DK_V_F32 = 5, DK_SPLIT_BF16 = 6
+};
+
+// dtype used for vectors at a precision
+inline bool prec_is_f64(int prec) { return prec == COLA_PREC_F64; }
+
+// Leaf data in the working type T, converting the borrowed array on the
+// context stream when its dtype differs (prepare_leaves must have run).
+template <typename T>
+const T* leaf_ptr(const cola_linop* op, bool second = false);
+
+// Convert every leaf of the tree to the working type of `prec` (and the BF16
+// splits for MIXED).  Enqueued on c->s.
+void prepare_leaves(Ctx* c, cola_linop* op, int prec, int split_terms);
+
+// Y = coeff * op(X) + beta * Y for R vectors (op^T when transpose).
+// X and Y must not alias.  depth selects the temp buffers of this level.
+template <typename T>
+void apply(Ctx* c, const cola_linop* op, const T* X, T* Y, int64_t R, double coeff, double beta,
+           int depth, bool transpose, int prec);
+
+// Diag(A) (App. A.1.4 rules) into out[n] (type T).
+template <typename T>
+void diagonal(Ctx* c, const cola_linop* op, T* out, int depth);
+
+// grads[l] += scale * sum_r Uw_r^T (dA/dtheta_l) X_r   (Uw already weighted)
+template <typename T>
+void bilinear(Ctx* c, const cola_linop* op, const T* Uw, const T* X, int64_t R, double scale,
+              const std::vector<void*>& grads, int& leaf_index, int depth);
+
+void collect_leaves(const cola_linop* op, std::vector<const cola_linop*>& out);
+
+// ------------------------------------------------------------- kernels API
+template <typename T>
+void gemm(Ctx* c, int64_t M, int64_t N, int64_t K, double alpha, const T* A, int64_t lda_m,
+          int64_t lda_k, int64_t sA, const T* B, int64_t ldb_k, int64_t ldb_n, int64_t sB,
+          double beta, T* C, int64_t ldc_m, int64_t ldc_n, int64_t sC, int64_t batch);
+
+// Deterministic per-vector dot products: out[r] = sum_i a[r*lda+i] b[r*ldb+i].
+// partials: workspace of dot_blocks(n)*R doubles.  Two launches.
+int dot_blocks(int64_t n);
+template <typename T>
+void dots(Ctx* c, const T* a, const T* b, int64_t n, int64_t R, double* partials, double* out);
+
+template <typename TI, typename TO>
+void convert(Ctx* c, const TI* in, TO* out, int64_t n);
+template <typename T>
+void fill_zero(Ctx* c, T* p, int64_t n);
+template <typename T>
+void scale_rows(Ctx* c, T* X, int64_t n, int64_t R, const double* w_dev);  // X[r] *= w[r]
+
+void rademacher(Ctx* c, uint64_t seed, int64_t offset, int64_t count, void* out, cola_dtype dt);
+
+template <typename T>
+void diag_apply(Ctx* c, const T* d, int64_t stride, const T* X, T* Y, int64_t n, int64_t R,
+                double coeff, double beta);
+template <typename T>
+void stencil_apply(Ctx* c, int nf, const int64_t* sizes, const T* bands, const T* X, T* Y,
+                   int64_t R, double coeff, double beta);
+template <typename T>
+void lowrank_vtx(Ctx* c, const T* V, const T* X, int64_t n, int64_t k, int64_t R, T* W,
+                 double* partials);  // W[k][R] = V^T X^T
+template <typename T>
+void lowrank_uw(Ctx* c, const T* U, const T* W, T* Y, int64_t n, int64_t k, int64_t R,
+                double coeff, double beta);  // Y[r,i] = coeff sum_k U[i,k] W[k,r] + beta Y
+template <typename T>
+void lowrank_grad(Ctx* c, const T* A, const T* W, T* G, int64_t n, int64_t k, int64_t R,
+                  double scale);  // G[i,k] += scale sum_r A[r,i] W[k,r]
+template <typename T>
+void rowsum_products(Ctx* c, const T* U, const T* V, T* out, int64_t n, int64_t k,
+                     double coeff, double beta);  // out[i] = coeff sum_k U[i,k]V[i,k] + beta out
+template <typename T>
+void kron_diag(Ctx* c, int nf, const int64_t* sizes, const T* const* fdiag_src,
+               const int64_t* lds, T* out, double coeff, double beta);
+template <typename T>
+void kronsum_diag(Ctx* c, int nf, const int64_t* sizes, const T* const* f, const int64_t* lds,
+                  T* out, double coeff, double beta);
+template <typename T>
+void diag_grad(Ctx* c, const T* U, const T* X, T* G, int64_t n, int64_t R, double scale,
+               bool scalar, double* partials);
+template <typename T>
+void permute_mode_front(Ctx* c, const T* X, T* Y, int64_t R, int64_t A, int64_t n, int64_t C);
+template <typename T>
+void add_partials(Ctx* c, const T* P, T* G, int64_t count, int64_t nparts, double scale);
+// out[r] = sum of partials[r*nblk .. r*nblk+nblk-1] in order
+void dot_final(Ctx* c, const double* partials, int nblk, int64_t R, double* out);
+
+// ------------------------------------------------------------ solver entries
+cola_status cg_solve_impl(Ctx* c, const cola_linop* op, const void* B, void* X, int64_t R,
+                          const cola_cg_opts& o, cola_cg_info* info);
+cola_status batched_cg_impl(Ctx* c, int32_t nsys, const cola_linop* const* ops,
+                            const void* const* B, void* const* X, const int64_t* nrhs,
+                            const cola_cg_opts& o, cola_cg_info* info);
+void lanczos_impl(Ctx* c, const cola_linop* op, const void* Q0, int64_t nv, int m, int prec,
+                  int reorth, double* alpha, double* beta, int* m_eff);
+void bilinear_entry(Ctx* c, const cola_linop* op, const void* U, const void* X,
+                    const double* weights, int64_t R, int prec, void* const* grads,
+                    int accumulate, int depth);
+void check_cg_args(const cola_linop* op, const cola_cg_opts* o, int64_t R);
+
+}  // namespace cola

@@ -1,0 +1,645 @@
+// SIMT kernels of the composed-operator MVM: strided-batched GEMM for the
+// Kronecker mode products (Sec. 3.2, Table 3: MVM of K_A (x) K_B costs
+// tau_A N_B + N_A tau_B), the Kronecker-sum tridiagonal stencil, diagonal and
+// low-rank terms, deterministic per-vector reductions, leaf-gradient
+// contractions (App. B.2) and the SplitMix64 probe generator.
+#include <algorithm>
+
+#include "internal.h"
+
+namespace cola {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+inline int grid_for(int64_t n, int per_thread = 1, int cap = 152 * 16) {
+  int64_t b = (n + (int64_t)kThreads * per_thread - 1) / ((int64_t)kThreads * per_thread);
+  return (int)std::max<int64_t>(1, std::min<int64_t>(b, cap));
+}
+
+template <typename T>
+__device__ __forceinline__ void ld4(T* dst, const T* src);
+template <>
+__device__ __forceinline__ void ld4<float>(float* d, const float* s) {
+  float4 v = *reinterpret_cast<const float4*>(s);
+  d[0] = v.x; d[1] = v.y; d[2] = v.z; d[3] = v.w;
+}
+template <>
+__device__ __forceinline__ void ld4<double>(double* d, const double* s) {
+  double2 a = *reinterpret_cast<const double2*>(s);
+  double2 b = *reinterpret_cast<const double2*>(s + 2);
+  d[0] = a.x; d[1] = a.y; d[2] = b.x; d[3] = b.y;
+}
+
+template <typename T>
+struct GemmP {
+  int64_t M, N, K;
+  const T* A;
+  int64_t lam, lak, sA;
+  const T* B;
+  int64_t lbk, lbn, sB;
+  T* C;
+  int64_t lcm, lcn, sC;
+  T alpha, beta;
+};
+
+// C[b](m, n) = alpha * sum_k A[b](m, k) B[b](k, n) + beta * C[b](m, n) with
+// arbitrary element strides.  128 x 128 x 8 tiles, 256 threads, 8 x 8
+// outputs per thread; tile loads run along whichever stride is unit.
+template <typename T>
+__global__ void __launch_bounds__(256) k_gemm(GemmP<T> g, int64_t batch0) {
+  constexpr int BM = 128, BN = 128, BK = 8;
+  __shared__ __align__(16) T As[BK][BM];
+  __shared__ __align__(16) T Bs[BK][BN];
+  const int64_t b = batch0 + blockIdx.z;
+  const T* A = g.A + b * g.sA;
+  const T* B = g.B + b * g.sB;
+  T* C = g.C + b * g.sC;
+  const int64_t m0 = (int64_t)blockIdx.x * BM, n0 = (int64_t)blockIdx.y * BN;
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  T acc[8][8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) acc[i][j] = T(0);
+  const bool a_m_fast = (g.lam == 1);
+  const bool b_n_fast = (g.lbn == 1);
+  for (int64_t k0 = 0; k0 < g.K; k0 += BK) {
+#pragma unroll
+    for (int e0 = 0; e0 < BM * BK; e0 += 256) {
+      const int e = e0 + tid;
+      int mm, kk;
+      if (a_m_fast) { mm = e % BM; kk = e / BM; } else { kk = e % BK; mm = e / BK; }
+      const int64_t m = m0 + mm, k = k0 + kk;
+      As[kk][mm] = (m < g.M && k < g.K) ? A[m * g.lam + k * g.lak] : T(0);
+    }
+#pragma unroll
+    for (int e0 = 0; e0 < BN * BK; e0 += 256) {
+      const int e = e0 + tid;
+      int nn, kk;
+      if (b_n_fast) { nn = e % BN; kk = e / BN; } else { kk = e % BK; nn = e / BK; }
+      const int64_t n = n0 + nn, k = k0 + kk;
+      Bs[kk][nn] = (n < g.N && k < g.K) ? B[k * g.lbk + n * g.lbn] : T(0);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      T a[8], bb[8];
+      ld4(a, &As[kk][ty * 4]);
+      ld4(a + 4, &As[kk][64 + ty * 4]);
+      ld4(bb, &Bs[kk][tx * 4]);
+      ld4(bb + 4, &Bs[kk][64 + tx * 4]);
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[i][j] = fma(a[i], bb[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const int64_t m = m0 + (i < 4 ? ty * 4 + i : 64 + ty * 4 + (i - 4));
+    if (m >= g.M) continue;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int64_t n = n0 + (j < 4 ? tx * 4 + j : 64 + tx * 4 + (j - 4));
+      if (n >= g.N) continue;
+      T* p = C + m * g.lcm + n * g.lcn;
+      T v = g.alpha * acc[i][j];
+      if (g.beta != T(0)) v += g.beta * *p;
+      *p = v;
+    }
+  }
+}
+
+// ------------------------------------------------------------- reductions
+template <typename T>
+__device__ __forceinline__ double block_sum(T v) {
+  __shared__ double sh[32];
+  double x = (double)v;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) sh[w] = x;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x < 32) {
+    t = (l < (int)(blockDim.x >> 5)) ? sh[l] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+  }
+  return t;  // valid in thread 0
+}
+
+template <typename T>
+__global__ void k_dot_partial(const T* a, const T* b, int64_t n, int nblk, double* part) {
+  const int64_t r = blockIdx.y;
+  const T* ar = a + r * n;
+  const T* br = b + r * n;
+  T s = T(0);
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)nblk * blockDim.x)
+    s = fma(ar[i], br[i], s);
+  const double t = block_sum(s);
+  if (threadIdx.x == 0) part[r * nblk + blockIdx.x] = t;
+}
+
+__global__ void k_dot_final(const double* part, int nblk, int64_t R, double* out) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= R) return;
+  double s = 0.0;
+  for (int i = 0; i < nblk; ++i) s += part[r * nblk + i];
+  out[r] = s;
+}
+
+// ------------------------------------------------------------ elementwise
+template <typename TI, typename TO>
+__global__ void k_convert(const TI* in, TO* out, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = (TO)in[i];
+}
+
+template <typename T>
+__global__ void k_scale_rows(T* X, int64_t n, int64_t R, const double* w) {
+  const int64_t tot = n * R;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < tot;
+       i += (int64_t)gridDim.x * blockDim.x)
+    X[i] = (T)((double)X[i] * w[i / n]);
+}
+
+__device__ __forceinline__ uint64_t splitmix64_at(uint64_t seed, uint64_t i) {
+  uint64_t z = seed + (i + 1ull) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+template <typename T>
+__global__ void k_rademacher(uint64_t seed, int64_t offset, int64_t count, T* out) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+       i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = (splitmix64_at(seed, (uint64_t)(offset + i)) >> 63) ? T(-1) : T(1);
+}
+
+template <typename T>
+__global__ void k_diag(const T* d, int64_t stride, const T* X, T* Y, int64_t n, int64_t R,
+                       T coeff, T beta) {
+  const int64_t tot = n * R;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < tot;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const T dv = stride ? d[i % n] : d[0];
+    T v = coeff * dv * X[i];
+    if (beta != T(0)) v += beta * Y[i];
+    Y[i] = v;
+  }
+}
+
+struct StencilP {
+  int nf;
+  int64_t n[8];
+  int64_t st[8];
+  int64_t boff[8];
+};
+
+// Kronecker sum of tridiagonal factors: y = coeff * sum_k (A_k along mode k) x + beta y.
+template <typename T>
+__global__ void k_stencil(StencilP p, const T* bands, const T* X, T* Y, int64_t N, int64_t R,
+                          T coeff, T beta) {
+  const int64_t tot = N * R;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < tot;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t loc = idx % N;
+    const T xc = X[idx];
+    T v = T(0);
+#pragma unroll 1
+    for (int k = 0; k < p.nf; ++k) {
+      const int64_t nk = p.n[k], sk = p.st[k];
+      const int64_t ik = (loc / sk) % nk;
+      const T* bd = bands + p.boff[k];
+      v = fma(bd[nk + ik], xc, v);
+      if (ik > 0) v = fma(bd[ik], X[idx - sk], v);
+      if (ik < nk - 1) v = fma(bd[2 * nk + ik], X[idx + sk], v);
+    }
+    v *= coeff;
+    if (beta != T(0)) v += beta * Y[idx];
+    Y[idx] = v;
+  }
+}
+
+// W partials: part[blk][k][R] = sum over this block's rows of V[i,k] X[r,i].
+// Lane = column of V within a 32-column group; X tiles are shared by shuffles.
+template <typename T>
+__global__ void k_lr_vtx(const T* V, const T* X, int64_t n, int64_t kdim, int64_t R,
+                         int nblk, double* part) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int64_t k0 = (int64_t)blockIdx.y * 32, r0 = (int64_t)blockIdx.z * 8;
+  const int64_t col = k0 + lane;
+  T acc[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) acc[q] = T(0);
+  const int64_t ntiles = (n + 31) / 32;
+  for (int64_t t = (int64_t)blockIdx.x * nw + warp; t < ntiles; t += (int64_t)nblk * nw) {
+    const int64_t i0 = t * 32;
+    T xr[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q)
+      xr[q] = (r0 + q < R && i0 + lane < n) ? X[(r0 + q) * n + i0 + lane] : T(0);
+    const int jmax = (n - i0 < 32) ? (int)(n - i0) : 32;
+    for (int j = 0; j < jmax; ++j) {
+      const T v = (col < kdim) ? V[(i0 + j) * kdim + col] : T(0);
+#pragma unroll
+      for (int q = 0; q < 8; ++q) acc[q] = fma(v, __shfl_sync(0xffffffffu, xr[q], j), acc[q]);
+    }
+  }
+  __shared__ double sh[8][8][32];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) sh[warp][q][lane] = (double)acc[q];
+  __syncthreads();
+  if (warp == 0) {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      double s = 0.0;
+      for (int w = 0; w < nw; ++w) s += sh[w][q][lane];
+      if (col < kdim && r0 + q < R) part[((int64_t)blockIdx.x * kdim + col) * R + r0 + q] = s;
+    }
+  }
+}
+
+template <typename T>
+__global__ void k_lr_final(const double* part, int nblk, int64_t cnt, T* W) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= cnt) return;
+  double s = 0.0;
+  for (int b = 0; b < nblk; ++b) s += part[(int64_t)b * cnt + i];
+  W[i] = (T)s;
+}
+
+// Y[r, i] = coeff * sum_k U[i, k] W[k, r] + beta Y[r, i]; W staged in shared memory.
+template <typename T>
+__global__ void k_lr_uw(const T* U, const T* W, T* Y, int64_t n, int64_t kdim, int64_t R,
+                        T coeff, T beta) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* Ws = reinterpret_cast<T*>(smem_raw);
+  for (int64_t i = threadIdx.x; i < kdim * R; i += blockDim.x) Ws[i] = W[i];
+  __syncthreads();
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t r0 = 0; r0 < R; r0 += 8) {
+      T acc[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) acc[q] = T(0);
+      for (int64_t k = 0; k < kdim; ++k) {
+        const T u = U[i * kdim + k];
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+          if (r0 + q < R) acc[q] = fma(u, Ws[k * R + r0 + q], acc[q]);
+      }
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        if (r0 + q >= R) break;
+        T* y = Y + (r0 + q) * n + i;
+        T v = coeff * acc[q];
+        if (beta != T(0)) v += beta * *y;
+        *y = v;
+      }
+    }
+  }
+}
+
+template <typename T>
+__global__ void k_lr_grad(const T* A, const T* W, T* G, int64_t n, int64_t kdim, int64_t R,
+                          T scale) {
+  const int64_t tot = n * kdim;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < tot;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / kdim, k = e % kdim;
+    T s = T(0);
+    for (int64_t r = 0; r < R; ++r) s = fma(A[r * n + i], W[k * R + r], s);
+    G[e] += scale * s;
+  }
+}
+
+template <typename T>
+__global__ void k_rowsum_prod(const T* U, const T* V, T* out, int64_t n, int64_t kdim, T coeff,
+                              T beta) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    T s = T(0);
+    for (int64_t k = 0; k < kdim; ++k) s = fma(U[i * kdim + k], V[i * kdim + k], s);
+    T v = coeff * s;
+    if (beta != T(0)) v += beta * out[i];
+    out[i] = v;
+  }
+}
+
+template <typename T>
+struct FacP {
+  int nf;
+  int64_t n[8];
+  int64_t st[8];
+  int64_t ld[8];
+  const T* f[8];
+};
+
+template <typename T>
+__global__ void k_kron_diag(FacP<T> p, T* out, int64_t N, T coeff, T beta, int sum_mode) {
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < N;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    T v = sum_mode ? T(0) : T(1);
+    for (int k = 0; k < p.nf; ++k) {
+      const int64_t ik = (idx / p.st[k]) % p.n[k];
+      const T d = p.f[k][ik * p.ld[k] + ik];
+      v = sum_mode ? v + d : v * d;
+    }
+    v *= coeff;
+    if (beta != T(0)) v += beta * out[idx];
+    out[idx] = v;
+  }
+}
+
+template <typename T>
+__global__ void k_diag_grad_vec(const T* U, const T* X, T* G, int64_t n, int64_t R, T scale) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    T s = T(0);
+    for (int64_t r = 0; r < R; ++r) s = fma(U[r * n + i], X[r * n + i], s);
+    G[i] += scale * s;
+  }
+}
+
+template <typename T>
+__global__ void k_add_scalar(T* G, const double* v, double scale) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) G[0] += (T)(scale * v[0]);
+}
+
+template <typename T>
+__global__ void k_permute_front(const T* X, T* Y, int64_t RA, int64_t n, int64_t C) {
+  const int64_t tot = RA * n * C;
+  for (int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; o < tot;
+       o += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t j = o / (RA * C);
+    const int64_t rem = o % (RA * C);
+    const int64_t ra = rem / C, c = rem % C;
+    Y[o] = X[(ra * n + j) * C + c];
+  }
+}
+
+template <typename T>
+__global__ void k_add_partials(const T* P, T* G, int64_t count, int64_t nparts, T scale) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    T s = T(0);
+    for (int64_t p = 0; p < nparts; ++p) s += P[p * count + i];
+    G[i] += scale * s;
+  }
+}
+
+}  // namespace
+
+// =================================================================== hosts
+
+template <typename T>
+void gemm(Ctx* c, int64_t M, int64_t N, int64_t K, double alpha, const T* A, int64_t lda_m,
+          int64_t lda_k, int64_t sA, const T* B, int64_t ldb_k, int64_t ldb_n, int64_t sB,
+          double beta, T* C, int64_t ldc_m, int64_t ldc_n, int64_t sC, int64_t batch) {
+  if (M <= 0 || N <= 0 || batch <= 0) return;
+  GemmP<T> g{M, N, K, A, lda_m, lda_k, sA, B, ldb_k, ldb_n, sB, C, ldc_m, ldc_n, sC,
+             (T)alpha, (T)beta};
+  const int64_t gy = (N + 127) / 128;
+  COLA_REQUIRE(gy <= 65535, COLA_ERR_UNSUPPORTED, "gemm: N=%lld too large", (long long)N);
+  for (int64_t b0 = 0; b0 < batch; b0 += 65535) {
+    const int64_t nb = std::min<int64_t>(65535, batch - b0);
+    dim3 grid((unsigned)((M + 127) / 128), (unsigned)gy, (unsigned)nb);
+    k_gemm<T><<<grid, 256, 0, c->s>>>(g, b0);
+    c->count_launch();
+  }
+  COLA_CUDA(cudaGetLastError());
+}
+
+int dot_blocks(int64_t n) {
+  const int64_t b = (n + 4095) / 4096;
+  return (int)std::max<int64_t>(1, std::min<int64_t>(b, 256));
+}
+
+template <typename T>
+void dots(Ctx* c, const T* a, const T* b, int64_t n, int64_t R, double* partials, double* out) {
+  const int nb = dot_blocks(n);
+  k_dot_partial<T><<<dim3(nb, (unsigned)R), 256, 0, c->s>>>(a, b, n, nb, partials);
+  c->count_launch();
+  k_dot_final<<<(unsigned)((R + 127) / 128), 128, 0, c->s>>>(partials, nb, R, out);
+  c->count_launch();
+  COLA_CUDA(cudaGetLastError());
+}
+
+void dot_final(Ctx* c, const double* partials, int nblk, int64_t R, double* out) {
+  k_dot_final<<<(unsigned)((R + 127) / 128), 128, 0, c->s>>>(partials, nblk, R, out);
+  c->count_launch();
+  COLA_CUDA(cudaGetLastError());
+}
+
+template <typename TI, typename TO>
+void convert(Ctx* c, const TI* in, TO* out, int64_t n) {
+  if (n <= 0) return;
+  k_convert<TI, TO><<<grid_for(n, 4), kThreads, 0, c->s>>>(in, out, n);
+  c->count_launch();
+  COLA_CUDA(cudaGetLastError());
+}
+
+template <typename T>
+void fill_zero(Ctx* c, T* p, int64_t n) {
+  if (n > 0) COLA_CUDA(cudaMemsetAsync(p, 0, sizeof(T) * n, c->s));
+}
+
+template <typename T>
+void scale_rows(Ctx* c, T* X, int64_t n, int64_t R, const double* w) {
+  k_scale_rows<T><<<grid_for(n * R, 4), kThreads, 0, c->s>>>(X, n, R, w);
+  c->count_launch();
+  COLA_CUDA(cudaGetLastError());
+}
+
+void rademacher(Ctx* c, uint64_t seed, int64_t offset, int64_t count, void* out,
+                cola_dtype dt) {
+  if (count <= 0) return;
+  if (dt == COLA_F64)
+    k_rademacher<double><<<grid_for(count, 4), kThreads, 0, c->s>>>(seed, offset, count,
+                                                                      (double*)out);
+  else
+    k_rademacher<float><<<grid_for(count, 4), kThreads, 0, c->s>>>(seed, offset, count,
+                                                                    (float*)out);
+  c->count_launch();
+  COLA_CUDA(cudaGetLastError());
+}
+
+template <typename T>
+void diag_apply(Ctx* c, const T* d, int64_t stride, const T* X, T* Y, int64_t n, int64_t R,
+                double coeff, double beta) {
+  k_diag<T><<<grid_for(n * R, 4), kThreads, 0, c->s>>>(d, stride, X, Y, n, R, (T)coeff,
+                                                       (T)beta);
+  c->count_launch();
+  COLA_CUDA(cudaGetLastError());
+}
+
+template <typename T>
+void stencil_apply(Ctx* c, int nf, const int64_t* sizes, const T* bands, const T* X, T* Y,
+                   int64_t R, double coeff, double beta) {
+  COLA_REQUIRE(nf >= 1 && nf <= 8, COLA_ERR_UNSUPPORTED, "stencil: %d factors", nf);
+  StencilP p{};
+  p.nf = nf;
+  int64_t N = 1, off = 0;
+  for (int k = 0; k < nf; ++k) N *= sizes[k];
+  int64_t st = N;
+  for (int k = 0; k < nf; ++k) {
+    st /= sizes[k];
+    p.n[k] = sizes[k];
+    p.st[k] = st;
+    p.boff[k] = off;
+    off += 3 * sizes[k];
+  }
+  k_stencil<T><<<grid_for(N * R, 4), kThreads, 0, c->s>>>(p, bands, X, Y, N, R, (T)coeff,
+                                                          (T)beta);
+  c->count_launch();
+  COLA_CUDA(cudaGetLastError());
+}
+
+template <typename T>
+void lowrank_vtx(Ctx* c, const T* V, const T* X, int64_t n, int64_t k, int64_t R, T* W,
+                 double* partials) {
+  const int64_t ntiles = (n + 31) / 32;
+  const int nblk = (int)std::max<int64_t>(1, std::min<int64_t>((ntiles + 7) / 8, 256));
+  dim3 grid(nblk, (unsigned)((k + 31) / 32), (unsigned)((R + 7) / 8));
+  k_lr_vtx<T><<<grid, 256, 0, c->s>>>(V, X, n, k, R, nblk, partials);
+  c->count_launch();
+  const int64_t cnt = k * R;
+  k_lr_final<T><<<(unsigned)((cnt + 255) / 256), 256, 0, c->s>>>(partials, nblk, cnt, W);
+  c->count_launch();
+  COLA_CUDA(cudaGetLastError());
+}
+
+template <typename T>
+void lowrank_uw(Ctx* c, const T* U, const T* W, T* Y, int64_t n, int64_t k, int64_t R,
+                double coeff, double beta) {
+  const size_t smem = sizeof(T) * k * R;
+  COLA_REQUIRE(smem <= 48 * 1024, COLA_ERR_UNSUPPORTED, "low-rank: k*nrhs too large");
+  k_lr_uw<T><<<grid_for(n, 1), kThreads, smem, c->s>>>(U, W, Y, n, k, R, (T)coeff, (T)beta);
+  c->count_launch();
+  COLA_CUDA(cudaGetLastError());
+}
+
+template <typename T>
+void lowrank_grad(Ctx* c, const T* A, const T* W, T* G, int64_t n, int64_t k, int64_t R,
+                  double scale) {
+  k_lr_grad<T><<<grid_for(n * k, 1), kThreads, 0, c->s>>>(A, W, G, n, k, R, (T)scale);
+  c->count_launch();
+  COLA_CUDA(cudaGetLastError());
+}
+
+template <typename T>
+void rowsum_products(Ctx* c, const T* U, const T* V, T* out, int64_t n, int64_t k,
+                     double coeff, double beta) {
+  k_rowsum_prod<T><<<grid_for(n, 1), kThreads, 0, c->s>>>(U, V, out, n, k, (T)coeff, (T)beta);
+  c->count_launch();
+  COLA_CUDA(cudaGetLastError());
+}
+
+template <typename T>
+static void kron_like_diag(Ctx* c, int nf, const int64_t* sizes, const T* const* f,
+                           const int64_t* lds, T* out, double coeff, double beta, int sum_mode) {
+  COLA_REQUIRE(nf >= 1 && nf <= 8, COLA_ERR_UNSUPPORTED, "diag: %d factors", nf);
+  FacP<T> p{};
+  p.nf = nf;
+  int64_t N = 1;
+  for (int k = 0; k < nf; ++k) N *= sizes[k];
+  int64_t st = N;
+  for (int k = 0; k < nf; ++k) {
+    st /= sizes[k];
+    p.n[k] = sizes[k];
+    p.st[k] = st;
+    p.ld[k] = lds[k];
+    p.f[k] = f[k];
+  }
+  k_kron_diag<T><<<grid_for(N, 4), kThreads, 0, c->s>>>(p, out, N, (T)coeff, (T)beta, sum_mode);
+  c->count_launch();
+  COLA_CUDA(cudaGetLastError());
+}
+
+template <typename T>
+void kron_diag(Ctx* c, int nf, const int64_t* sizes, const T* const* f, const int64_t* lds,
+               T* out, double coeff, double beta) {
+  kron_like_diag(c, nf, sizes, f, lds, out, coeff, beta, 0);
+}
+
+template <typename T>
+void kronsum_diag(Ctx* c, int nf, const int64_t* sizes, const T* const* f, const int64_t* lds,
+                  T* out, double coeff, double beta) {
+  kron_like_diag(c, nf, sizes, f, lds, out, coeff, beta, 1);
+}
+
+template <typename T>
+void diag_grad(Ctx* c, const T* U, const T* X, T* G, int64_t n, int64_t R, double scale,
+               bool scalar, double* partials) {
+  if (scalar) {
+    double* out = partials + (int64_t)dot_blocks(n * R);
+    dots<T>(c, U, X, n * R, 1, partials, out);
+    k_add_scalar<T><<<1, 32, 0, c->s>>>(G, out, scale);
+    c->count_launch();
+  } else {
+    k_diag_grad_vec<T><<<grid_for(n, 1), kThreads, 0, c->s>>>(U, X, G, n, R, (T)scale);
+    c->count_launch();
+  }
+  COLA_CUDA(cudaGetLastError());
+}
+
+template <typename T>
+void permute_mode_front(Ctx* c, const T* X, T* Y, int64_t R, int64_t A, int64_t n, int64_t C) {
+  k_permute_front<T><<<grid_for(R * A * n * C, 4), kThreads, 0, c->s>>>(X, Y, R * A, n, C);
+  c->count_launch();
+  COLA_CUDA(cudaGetLastError());
+}
+
+template <typename T>
+void add_partials(Ctx* c, const T* P, T* G, int64_t count, int64_t nparts, double scale) {
+  k_add_partials<T><<<grid_for(count, 1), kThreads, 0, c->s>>>(P, G, count, nparts, (T)scale);
+  c->count_launch();
+  COLA_CUDA(cudaGetLastError());
+}
+
+#define COLA_INST(T)                                                                        \
+  template void gemm<T>(Ctx*, int64_t, int64_t, int64_t, double, const T*, int64_t, int64_t, \
+                        int64_t, const T*, int64_t, int64_t, int64_t, double, T*, int64_t,   \
+                        int64_t, int64_t, int64_t);                                         \
+  template void dots<T>(Ctx*, const T*, const T*, int64_t, int64_t, double*, double*);      \
+  template void fill_zero<T>(Ctx*, T*, int64_t);                                            \
+  template void scale_rows<T>(Ctx*, T*, int64_t, int64_t, const double*);                   \
+  template void diag_apply<T>(Ctx*, const T*, int64_t, const T*, T*, int64_t, int64_t,      \
+                              double, double);                                              \
+  template void stencil_apply<T>(Ctx*, int, const int64_t*, const T*, const T*, T*, int64_t, \
+                                 double, double);                                           \
+  template void lowrank_vtx<T>(Ctx*, const T*, const T*, int64_t, int64_t, int64_t, T*,     \
+                               double*);                                                    \
+  template void lowrank_uw<T>(Ctx*, const T*, const T*, T*, int64_t, int64_t, int64_t,      \
+                              double, double);                                              \
+  template void lowrank_grad<T>(Ctx*, const T*, const T*, T*, int64_t, int64_t, int64_t,    \
+                                double);                                                    \
+  template void rowsum_products<T>(Ctx*, const T*, const T*, T*, int64_t, int64_t, double,  \
+                                   double);                                                 \
+  template void kron_diag<T>(Ctx*, int, const int64_t*, const T* const*, const int64_t*, T*, \
+                             double, double);                                               \
+  template void kronsum_diag<T>(Ctx*, int, const int64_t*, const T* const*, const int64_t*, \
+                                T*, double, double);                                        \
+  template void diag_grad<T>(Ctx*, const T*, const T*, T*, int64_t, int64_t, double, bool,  \
+                             double*);                                                      \
+  template void permute_mode_front<T>(Ctx*, const T*, T*, int64_t, int64_t, int64_t,        \
+                                      int64_t);                                             \
+  template void add_partials<T>(Ctx*, const T*, T*, int64_t, int64_t, double);
+
+COLA_INST(float)
+COLA_INST(double)
+template void convert<double, float>(Ctx*, const double*, float*, int64_t);
+template void convert<float, double>(Ctx*, const float*, double*, int64_t);
+template void convert<float, float>(Ctx*, const float*, float*, int64_t);
+template void convert<double, double>(Ctx*, const double*, double*, int64_t);
+
+}  // namespace cola

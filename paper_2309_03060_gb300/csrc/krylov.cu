@@ -1,0 +1,999 @@
+// Krylov drivers on top of the operator MVM:
+//  * conjugate gradients (Table 5: CG is the PSD solve base case), multi-RHS
+//    with per-RHS step sizes and the all-solves stopping rule (App. D GP
+//    training), optional Jacobi preconditioner (Diag rules, App. A.1.4), and
+//    an FP64 iterative-refinement loop: the solution is accumulated in FP64
+//    and the recursive FP32 residual is replaced by the FP64 true residual
+//    b - A x whenever it has dropped by a set factor (reliable updates).  The
+//    low-precision routines of Sec. 3.4 / App. C.3 motivate this; the paper
+//    gives no algorithm for it.
+//  * Lanczos (Table 5 self-adjoint base case) batched over starting vectors,
+//    with the breakdown test of the Arnoldi iteration (Algorithm 1).
+//  * stochastic Lanczos quadrature for log det A = Tr(log A) (App. A.2):
+//    per probe ||z||^2 sum_k S_0k^2 log(theta_k), T_m = S diag(theta) S^T,
+//    with an implicit-shift symmetric tridiagonal QR on the device.
+//  * the adjoint rules of App. B.2 (solve VJP, log-det gradient).
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <cmath>
+#include <string>
+
+#include "internal.h"
+
+namespace cola {
+
+struct CgState {
+  double rz, pAp, alpha, beta;
+  double rr, rr_ref, bb, tol2;
+  double rr64;
+  long long iters;
+  int active, flag, status, updates;
+};
+
+namespace {
+
+template <typename T>
+__device__ __forceinline__ double block_sum2(T v, double* out_other, T v2) {
+  // Sums two values over the block; returns the first, writes the second.
+  __shared__ double sh[2][32];
+  double x = (double)v, y = (double)v2;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    x += __shfl_xor_sync(0xffffffffu, x, o);
+    y += __shfl_xor_sync(0xffffffffu, y, o);
+  }
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) {
+    sh[0][w] = x;
+    sh[1][w] = y;
+  }
+  __syncthreads();
+  double tx = 0.0, ty = 0.0;
+  if (threadIdx.x < 32) {
+    const bool ok = l < (int)(blockDim.x >> 5);
+    tx = ok ? sh[0][l] : 0.0;
+    ty = ok ? sh[1][l] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      tx += __shfl_xor_sync(0xffffffffu, tx, o);
+      ty += __shfl_xor_sync(0xffffffffu, ty, o);
+    }
+  }
+  *out_other = ty;
+  return tx;
+}
+
+__global__ void k_cg_alpha(CgState* st, const double* pAp, int64_t R) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= R) return;
+  CgState& s = st[r];
+  if (!s.active) {
+    s.alpha = 0.0;
+    return;
+  }
+  const double v = pAp[r];
+  s.pAp = v;
+  if (!(v > 0.0) || !isfinite(v)) {
+    s.status = COLA_ERR_BREAKDOWN;
+    s.active = 0;
+    s.alpha = 0.0;
+    return;
+  }
+  s.alpha = s.rz / v;
+}
+
+// x += alpha p; r -= alpha Ap; z = M^-1 r; partial sums of r^T z and r^T r.
+template <typename T>
+__global__ void k_cg_xr(int64_t n, T* x, T* r, const T* p, const T* Ap, const T* invd, T* z,
+                        const CgState* st, int nblk, double* part_rz, double* part_rr) {
+  const int64_t v = blockIdx.y;
+  const T a = (T)st[v].alpha;
+  T* xv = x + v * n;
+  T* rv = r + v * n;
+  const T* pv = p + v * n;
+  const T* Av = Ap + v * n;
+  T* zv = z ? z + v * n : nullptr;
+  T s_rz = T(0), s_rr = T(0);
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)nblk * blockDim.x) {
+    T ri = rv[i];
+    if (a != T(0)) {
+      xv[i] = fma(a, pv[i], xv[i]);
+      ri = fma(-a, Av[i], ri);
+      rv[i] = ri;
+    }
+    T zi = ri;
+    if (invd) {
+      zi = ri * invd[i];
+      zv[i] = zi;
+    }
+    s_rz = fma(ri, zi, s_rz);
+    s_rr = fma(ri, ri, s_rr);
+  }
+  double rr;
+  const double rz = block_sum2(s_rz, &rr, s_rr);
+  if (threadIdx.x == 0) {
+    part_rz[v * nblk + blockIdx.x] = rz;
+    part_rr[v * nblk + blockIdx.x] = rr;
+  }
+}
+
+__global__ void k_cg_beta(CgState* st, const double* part_rz, const double* part_rr, int nblk,
+                          int64_t R, double delta2, int refine) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= R) return;
+  CgState& s = st[r];
+  if (!s.active) {
+    s.beta = 0.0;
+    return;
+  }
+  double rz = 0.0, rr = 0.0;
+  for (int b = 0; b < nblk; ++b) {
+    rz += part_rz[r * nblk + b];
+    rr += part_rr[r * nblk + b];
+  }
+  s.beta = rz / s.rz;
+  s.rz = rz;
+  s.rr = rr;
+  s.iters += 1;
+  if (!isfinite(rr) || !isfinite(rz)) {
+    s.status = COLA_ERR_BREAKDOWN;
+    s.active = 0;
+    s.beta = 0.0;
+    return;
+  }
+  if (refine) {
+    if (rr <= s.tol2 || rr <= delta2 * s.rr_ref) s.flag = 1;
+  } else if (rr <= s.tol2) {
+    s.active = 0;
+  }
+}
+
+template <typename T>
+__global__ void k_cg_p(int64_t n, const T* z, T* p, const CgState* st) {
+  const int64_t v = blockIdx.y;
+  if (!st[v].active) return;
+  const T b = (T)st[v].beta;
+  const T* zv = z + v * n;
+  T* pv = p + v * n;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    pv[i] = fma(b, pv[i], zv[i]);
+}
+
+// r = (T) r64 (refined) or r as is; z = M^-1 r; partial r^T z and r^T r.
+template <typename T>
+__global__ void k_refresh(int64_t n, const double* r64, T* r, const T* invd, T* z, int nblk,
+                          double* part_rz, double* part_rr) {
+  const int64_t v = blockIdx.y;
+  T s_rz = T(0), s_rr = T(0);
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)nblk * blockDim.x) {
+    T ri = r64 ? (T)r64[v * n + i] : r[v * n + i];
+    if (r64) r[v * n + i] = ri;
+    T zi = ri;
+    if (invd) {
+      zi = ri * invd[i];
+      z[v * n + i] = zi;
+    }
+    s_rz = fma(ri, zi, s_rz);
+    s_rr = fma(ri, ri, s_rr);
+  }
+  double rr;
+  const double rz = block_sum2(s_rz, &rr, s_rr);
+  if (threadIdx.x == 0) {
+    part_rz[v * nblk + blockIdx.x] = rz;
+    part_rr[v * nblk + blockIdx.x] = rr;
+  }
+}
+
+// (Re)start state after a residual refresh.  first: initialise everything.
+__global__ void k_cg_restate(CgState* st, const double* part_rz, const double* part_rr, int nblk,
+                             int64_t R, const double* rr64, const double* bb, double tol,
+                             int first) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= R) return;
+  CgState& s = st[r];
+  double rz = 0.0, rr = 0.0;
+  for (int b = 0; b < nblk; ++b) {
+    rz += part_rz[r * nblk + b];
+    rr += part_rr[r * nblk + b];
+  }
+  if (first) {
+    s.iters = 0;
+    s.updates = 0;
+    s.status = 0;
+    s.bb = bb[r];
+    s.tol2 = tol * tol * bb[r];
+    s.active = 1;
+    s.alpha = s.beta = 0.0;
+  } else if (s.active) {
+    s.updates += 1;
+  }
+  s.flag = 0;
+  s.rz = rz;
+  s.rr = rr;
+  s.rr_ref = rr;
+  if (rr64) s.rr64 = rr64[r];
+  const double conv = rr64 ? rr64[r] : rr;
+  if (s.active && conv <= s.tol2) s.active = 0;
+}
+
+template <typename T>
+__global__ void k_copy_active(int64_t n, const T* src, T* dst, const CgState* st) {
+  const int64_t v = blockIdx.y;
+  if (!st[v].active) return;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    dst[v * n + i] = src[v * n + i];
+}
+
+template <typename T>
+__global__ void k_accum_x(int64_t tot, double* x64, T* x) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < tot;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    x64[i] += (double)x[i];
+    x[i] = T(0);
+  }
+}
+
+__global__ void k_invert(int64_t n, const double* d, float* out32, double* out64) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double v = 1.0 / d[i];
+    if (out32) out32[i] = (float)v;
+    if (out64) out64[i] = v;
+  }
+}
+
+// ------------------------------------------------------------------ Lanczos
+struct LzState {
+  double beta_prev, amax;
+  int active, m_eff;
+};
+
+__global__ void k_lz_init(LzState* st, const double* nrm2, int64_t nv, int m) {
+  const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= nv) return;
+  st[v].beta_prev = 0.0;
+  st[v].amax = 0.0;
+  st[v].active = nrm2[v] > 0.0 ? 1 : 0;
+  st[v].m_eff = nrm2[v] > 0.0 ? m : 0;
+}
+
+template <typename T>
+__global__ void k_lz_scale(int64_t n, const T* src, T* dst, const double* nrm2) {
+  const int64_t v = blockIdx.y;
+  const double s = nrm2[v] > 0.0 ? 1.0 / sqrt(nrm2[v]) : 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    dst[v * n + i] = (T)((double)src[v * n + i] * s);
+}
+
+// w -= beta_prev q_prev; partial q^T w
+template <typename T>
+__global__ void k_lz_a(int64_t n, T* w, const T* qprev, const T* q, const LzState* st, int nblk,
+                       double* part) {
+  const int64_t v = blockIdx.y;
+  const T bp = (T)st[v].beta_prev;
+  T s = T(0), dummy = T(0);
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)nblk * blockDim.x) {
+    T wi = w[v * n + i];
+    if (bp != T(0)) {
+      wi = fma(-bp, qprev[v * n + i], wi);
+      w[v * n + i] = wi;
+    }
+    s = fma(q[v * n + i], wi, s);
+  }
+  double o;
+  const double t = block_sum2(s, &o, dummy);
+  if (threadIdx.x == 0) part[v * nblk + blockIdx.x] = t;
+}
+
+__global__ void k_lz_alpha(LzState* st, const double* part, int nblk, int64_t nv, int j, int m,
+                           double* alpha, double* a_cur) {
+  const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= nv) return;
+  double a = 0.0;
+  for (int b = 0; b < nblk; ++b) a += part[v * nblk + b];
+  a_cur[v] = st[v].active ? a : 0.0;
+  if (st[v].active) {
+    alpha[v * m + j] = a;
+    st[v].amax = fmax(st[v].amax, fabs(a));
+  }
+}
+
+// w -= alpha q; partial ||w||^2
+template <typename T>
+__global__ void k_lz_b(int64_t n, T* w, const T* q, const double* a_cur, int nblk, double* part,
+                       int want_norm) {
+  const int64_t v = blockIdx.y;
+  const T a = (T)a_cur[v];
+  T s = T(0), dummy = T(0);
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)nblk * blockDim.x) {
+    const T wi = fma(-a, q[v * n + i], w[v * n + i]);
+    w[v * n + i] = wi;
+    s = fma(wi, wi, s);
+  }
+  if (!want_norm) return;
+  double o;
+  const double t = block_sum2(s, &o, dummy);
+  if (threadIdx.x == 0) part[v * nblk + blockIdx.x] = t;
+}
+
+__global__ void k_lz_beta(LzState* st, const double* nrm2, int64_t nv, int j, int m, double eps,
+                          double* beta, double* b_cur) {
+  const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= nv) return;
+  LzState& s = st[v];
+  b_cur[v] = 0.0;
+  if (!s.active) return;
+  if (j == m - 1) {
+    s.active = 0;
+    s.m_eff = m;
+    return;
+  }
+  const double b = sqrt(fmax(nrm2[v], 0.0));
+  if (!(b > eps * s.amax)) {
+    s.active = 0;
+    s.m_eff = j + 1;
+    return;
+  }
+  beta[v * m + j] = b;
+  s.beta_prev = b;
+  b_cur[v] = b;
+}
+
+template <typename T>
+__global__ void k_lz_next(int64_t n, T* w, const double* b_cur) {
+  const int64_t v = blockIdx.y;
+  const double b = b_cur[v];
+  if (b == 0.0) return;
+  const T s = (T)(1.0 / b);
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    w[v * n + i] *= s;
+}
+
+__global__ void k_lz_meff(const LzState* st, int64_t nv, int* m_eff) {
+  const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (v < nv) m_eff[v] = st[v].m_eff;
+}
+
+// --------------------------------------------------------------- quadrature
+// Implicit symmetric tridiagonal QR with Wilkinson shifts (Golub & Van Loan
+// Sec. 8.3), tracking the first row of the accumulated rotations: at
+// convergence a[k] are the Ritz values theta_k and w[k] = S_0k.
+__device__ void tridiag_eig_first_row(double* a, double* b, double* w, int n) {
+  for (int k = 0; k < n; ++k) w[k] = (k == 0) ? 1.0 : 0.0;
+  if (n > 0) b[n - 1] = 0.0;
+  const double eps = 2.220446049250313e-16;
+  int q = n - 1, it = 0;
+  while (q > 0 && it < 60 * n) {
+    if (fabs(b[q - 1]) <= eps * (fabs(a[q - 1]) + fabs(a[q]))) {
+      b[q - 1] = 0.0;
+      --q;
+      continue;
+    }
+    int p = q - 1;
+    while (p > 0 && fabs(b[p - 1]) > eps * (fabs(a[p - 1]) + fabs(a[p]))) --p;
+    ++it;
+    const double d = 0.5 * (a[q - 1] - a[q]), bb = b[q - 1];
+    const double sg = d >= 0.0 ? 1.0 : -1.0;
+    const double mu = a[q] - bb * bb / (d + sg * hypot(d, bb));
+    double x = a[p] - mu, z = b[p];
+    for (int k = p; k < q; ++k) {
+      const double r = hypot(x, z);
+      const double c = x / r, s = z / r;
+      if (k > p) b[k - 1] = r;
+      const double ak = a[k], ak1 = a[k + 1], bk = b[k];
+      a[k] = c * c * ak + 2.0 * c * s * bk + s * s * ak1;
+      a[k + 1] = s * s * ak - 2.0 * c * s * bk + c * c * ak1;
+      b[k] = c * s * (ak1 - ak) + (c * c - s * s) * bk;
+      const double wk = w[k], wk1 = w[k + 1];
+      w[k] = c * wk + s * wk1;
+      w[k + 1] = -s * wk + c * wk1;
+      if (k < q - 1) {
+        x = b[k];
+        z = s * b[k + 1];
+        b[k + 1] = c * b[k + 1];
+      }
+    }
+  }
+}
+
+constexpr int kMaxQuadM = 256;
+
+__global__ void k_slq_quad(const double* alpha, const double* beta, const int* m_eff, int m,
+                           int nv, const double* znorm2, double* per_probe, double* summary,
+                           int* clamped) {
+  __shared__ double vals[1024];
+  __shared__ int nclamp;
+  if (threadIdx.x == 0) nclamp = 0;
+  __syncthreads();
+  for (int v = threadIdx.x; v < nv; v += blockDim.x) {
+    double a[kMaxQuadM], b[kMaxQuadM], w[kMaxQuadM];
+    const int n = m_eff[v];
+    for (int k = 0; k < n; ++k) {
+      a[k] = alpha[(int64_t)v * m + k];
+      b[k] = (k < n - 1) ? beta[(int64_t)v * m + k] : 0.0;
+    }
+    tridiag_eig_first_row(a, b, w, n);
+    double tmin = 0.0;
+    for (int k = 0; k < n; ++k)
+      if (a[k] > 0.0 && (tmin == 0.0 || a[k] < tmin)) tmin = a[k];
+    double s = 0.0;
+    int cl = 0;
+    for (int k = 0; k < n; ++k) {
+      double th = a[k];
+      if (!(th > 0.0)) {
+        th = tmin;
+        ++cl;
+      }
+      s += w[k] * w[k] * log(th);
+    }
+    if (cl) atomicAdd(&nclamp, cl);
+    const double val = znorm2[v] * s;
+    per_probe[v] = val;
+    if (v < 1024) vals[v] = val;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const int cnt = nv < 1024 ? nv : 1024;
+    double mean = 0.0;
+    for (int v = 0; v < cnt; ++v) mean += vals[v];
+    mean /= cnt;
+    double var = 0.0;
+    for (int v = 0; v < cnt; ++v) var += (vals[v] - mean) * (vals[v] - mean);
+    summary[0] = mean;
+    summary[1] = cnt > 1 ? sqrt(var / (cnt - 1) / cnt) : 0.0;
+    *clamped = nclamp;
+  }
+}
+
+inline dim3 rows_grid(int64_t n, int64_t R, int nblk) { return dim3(nblk, (unsigned)R); }
+
+inline int ew_blocks(int64_t n) {
+  return (int)std::max<int64_t>(1, std::min<int64_t>((n + 1023) / 1024, 1024));
+}
+
+}  // namespace
+
+// ====================================================================== CG
+template <typename T>
+struct CgBufs {
+  T *x, *r, *p, *Ap, *z;  // working precision
+  T* invd;
+  double *x64, *b64, *r64;
+  double *part_rz, *part_rr, *dotp, *dotv;
+  CgState* st;
+};
+
+static std::string key_of(const char* what, const cola_linop* op, int64_t R, int prec, int extra,
+                          uint64_t gen) {
+  char b[160];
+  snprintf(b, sizeof b, "%s:%llu:%lld:%d:%d:%llu", what, (unsigned long long)op->uid,
+           (long long)R, prec, extra, (unsigned long long)gen);
+  return b;
+}
+
+template <typename T>
+static void cg_iteration(Ctx* c, const cola_linop* op, CgBufs<T>& B, int64_t N, int64_t R,
+                         int nblk, int prec, double delta2, int refine) {
+  apply<T>(c, op, B.p, B.Ap, R, 1.0, 0.0, 1, false, prec);
+  dots<T>(c, B.p, B.Ap, N, R, B.dotp, B.dotv);
+  k_cg_alpha<<<(unsigned)((R + 127) / 128), 128, 0, c->s>>>(B.st, B.dotv, R);
+  c->count_launch();
+  k_cg_xr<T><<<rows_grid(N, R, nblk), 256, 0, c->s>>>(N, B.x, B.r, B.p, B.Ap, B.invd,
+                                                       B.invd ? B.z : nullptr, B.st, nblk,
+                                                       B.part_rz, B.part_rr);
+  c->count_launch();
+  k_cg_beta<<<(unsigned)((R + 127) / 128), 128, 0, c->s>>>(B.st, B.part_rz, B.part_rr, nblk, R,
+                                                          delta2, refine);
+  c->count_launch();
+  k_cg_p<T><<<dim3(ew_blocks(N), (unsigned)R), 256, 0, c->s>>>(N, B.invd ? B.z : B.r, B.p, B.st);
+  c->count_launch();
+  COLA_CUDA(cudaGetLastError());
+}
+
+// Runs `chunk` iterations as one CUDA graph (captured on first use).
+template <typename T>
+static void cg_chunk(Ctx* c, const cola_linop* op, CgBufs<T>& B, int64_t N, int64_t R, int nblk,
+                     int prec, double delta2, int refine, int chunk, const std::string& key) {
+  auto it = c->graphs.find(key);
+  if (it == c->graphs.end() || it->second.generation != c->ws.generation) {
+    if (it != c->graphs.end()) {
+      cudaGraphExecDestroy(it->second.exec);
+      c->graphs.erase(it);
+    }
+    cudaGraph_t g;
+    COLA_CUDA(cudaStreamBeginCapture(c->s, cudaStreamCaptureModeThreadLocal));
+    c->capturing = true;
+    c->captured = 0;
+    const uint64_t gen0 = c->ws.generation;
+    try {
+      for (int i = 0; i < chunk; ++i) cg_iteration<T>(c, op, B, N, R, nblk, prec, delta2, refine);
+    } catch (...) {
+      c->capturing = false;
+      cudaStreamEndCapture(c->s, &g);
+      throw;
+    }
+    c->capturing = false;
+    COLA_CUDA(cudaStreamEndCapture(c->s, &g));
+    COLA_REQUIRE(gen0 == c->ws.generation, COLA_ERR_CUDA,
+                 "internal: workspace moved during graph capture");
+    GraphEntry e;
+    COLA_CUDA(cudaGraphInstantiate(&e.exec, g, 0));
+    cudaGraphDestroy(g);
+    e.kernels = c->captured;
+    e.generation = c->ws.generation;
+    it = c->graphs.emplace(key, e).first;
+  }
+  COLA_CUDA(cudaGraphLaunch(it->second.exec, c->s));
+  c->launches += it->second.kernels;
+}
+
+template <typename T>
+static cola_status cg_run(Ctx* c, cola_linop* op, const void* Bin, void* Xout, int64_t R,
+                          const cola_cg_opts& o, cola_cg_info* info, bool transpose_unused) {
+  (void)transpose_unused;
+  const int64_t N = op->rows;
+  const int prec = o.precision;
+  const bool refine = (prec != COLA_PREC_F64) && o.refine;
+  const int nblk = dot_blocks(N);
+  auto& ws = c->ws;
+  CgBufs<T> B{};
+  B.x = (T*)ws.get("cg.x", sizeof(T) * N * R);
+  B.r = (T*)ws.get("cg.r", sizeof(T) * N * R);
+  B.p = (T*)ws.get("cg.p", sizeof(T) * N * R);
+  B.Ap = (T*)ws.get("cg.Ap", sizeof(T) * N * R);
+  B.z = o.jacobi ? (T*)ws.get("cg.z", sizeof(T) * N * R) : nullptr;
+  B.part_rz = (double*)ws.get("cg.prz", 8 * nblk * R);
+  B.part_rr = (double*)ws.get("cg.prr", 8 * nblk * R);
+  B.dotp = (double*)ws.get("cg.dotp", 8 * nblk * R);
+  B.dotv = (double*)ws.get("cg.dotv", 8 * R);
+  B.st = (CgState*)ws.get("cg.st", sizeof(CgState) * R);
+  double* bb = (double*)ws.get("cg.bb", 8 * R);
+  double* rr64 = (double*)ws.get("cg.rr64", 8 * R);
+  double* dp64 = (double*)ws.get("cg.dp64", 8 * dot_blocks(N) * R);
+  const bool io64 = (prec == COLA_PREC_F64) || refine;
+
+  prepare_leaves(c, op, prec, o.split_factor_terms);
+  if (refine) prepare_leaves(c, op, COLA_PREC_F64, o.split_factor_terms);
+
+  // Jacobi preconditioner M = Diag(A) (Diag rules).
+  if (o.jacobi) {
+    double* d64 = (double*)ws.get("cg.diag64", 8 * N);
+    prepare_leaves(c, op, COLA_PREC_F64, 0);
+    diagonal<double>(c, op, d64, 0);
+    B.invd = (T*)ws.get("cg.invd", sizeof(T) * N);
+    if (sizeof(T) == 4)
+      k_invert<<<ew_blocks(N), 256, 0, c->s>>>(N, d64, (float*)B.invd, nullptr);
+    else
+      k_invert<<<ew_blocks(N), 256, 0, c->s>>>(N, d64, nullptr, (double*)B.invd);
+    c->count_launch();
+  }
+
+  if (refine) {
+    B.x64 = (double*)ws.get("cg.x64", 8 * N * R);
+    B.b64 = (double*)ws.get("cg.b64", 8 * N * R);
+    B.r64 = (double*)ws.get("cg.r64", 8 * N * R);
+    COLA_CUDA(cudaMemcpyAsync(B.b64, Bin, 8 * N * R, cudaMemcpyDeviceToDevice, c->s));
+    if (o.x0_given)
+      COLA_CUDA(cudaMemcpyAsync(B.x64, Xout, 8 * N * R, cudaMemcpyDeviceToDevice, c->s));
+    else
+      fill_zero<double>(c, B.x64, N * R);
+    COLA_CUDA(cudaMemcpyAsync(B.r64, B.b64, 8 * N * R, cudaMemcpyDeviceToDevice, c->s));
+    if (o.x0_given) apply<double>(c, op, B.x64, B.r64, R, -1.0, 1.0, 1, false, COLA_PREC_F64);
+    dots<double>(c, B.b64, B.b64, N, R, dp64, bb);
+    dots<double>(c, B.r64, B.r64, N, R, dp64, rr64);
+    fill_zero<T>(c, B.x, N * R);
+  } else {
+    COLA_CUDA(cudaMemcpyAsync(B.r, Bin, sizeof(T) * N * R, cudaMemcpyDeviceToDevice, c->s));
+    dots<T>(c, B.r, B.r, N, R, B.dotp, bb);
+    if (o.x0_given) {
+      COLA_CUDA(cudaMemcpyAsync(B.x, Xout, sizeof(T) * N * R, cudaMemcpyDeviceToDevice, c->s));
+      apply<T>(c, op, B.x, B.r, R, -1.0, 1.0, 1, false, prec);
+    } else {
+      fill_zero<T>(c, B.x, N * R);
+    }
+  }
+  k_refresh<T><<<rows_grid(N, R, nblk), 256, 0, c->s>>>(N, refine ? B.r64 : nullptr, B.r, B.invd,
+                                                         B.z, nblk, B.part_rz, B.part_rr);
+  c->count_launch();
+  k_cg_restate<<<(unsigned)((R + 127) / 128), 128, 0, c->s>>>(
+      B.st, B.part_rz, B.part_rr, nblk, R, refine ? rr64 : nullptr, bb, o.tol, 1);
+  c->count_launch();
+  k_copy_active<T><<<dim3(ew_blocks(N), (unsigned)R), 256, 0, c->s>>>(N, B.invd ? B.z : B.r, B.p,
+                                                                      B.st);
+  c->count_launch();
+  COLA_CUDA(cudaGetLastError());
+
+  CgState* hst = (CgState*)c->host_pinned(sizeof(CgState) * R);
+  auto read_state = [&] {
+    COLA_CUDA(cudaMemcpyAsync(hst, B.st, sizeof(CgState) * R, cudaMemcpyDeviceToHost, c->s));
+    COLA_CUDA(cudaStreamSynchronize(c->s));
+  };
+  const double delta2 = o.reliable_delta * o.reliable_delta;
+  const int chunk = std::max(1, o.graph_chunk);
+  const std::string key =
+      key_of("cg", op, R, prec, (refine ? 1 : 0) | (o.jacobi ? 2 : 0) | (chunk << 2),
+             0) + (sizeof(T) == 8 ? ":d" : ":f");
+  int64_t iters = 0;
+  int updates = 0;
+  read_state();
+  bool any_active = false;
+  for (int64_t r = 0; r < R; ++r) any_active |= hst[r].active != 0;
+  // one eager iteration sizes every workspace buffer before capture
+  if (any_active && o.maxiter > 0) {
+    cg_iteration<T>(c, op, B, N, R, nblk, prec, delta2, refine ? 1 : 0);
+    iters = 1;
+  }
+  while (any_active) {
+    if (iters >= o.maxiter) break;
+    cg_chunk<T>(c, op, B, N, R, nblk, prec, delta2, refine ? 1 : 0, chunk, key);
+    iters += chunk;
+    read_state();
+    bool flag = false;
+    any_active = false;
+    for (int64_t r = 0; r < R; ++r) {
+      any_active |= hst[r].active != 0;
+      flag |= hst[r].active && hst[r].flag;
+    }
+    if (refine && (flag || !any_active) && updates < o.max_updates) {
+      // FP64 residual replacement: x64 += x; r64 = b - A x64; r = (T) r64.
+      k_accum_x<T><<<ew_blocks(N * R), 256, 0, c->s>>>(N * R, B.x64, B.x);
+      c->count_launch();
+      COLA_CUDA(cudaMemcpyAsync(B.r64, B.b64, 8 * N * R, cudaMemcpyDeviceToDevice, c->s));
+      apply<double>(c, op, B.x64, B.r64, R, -1.0, 1.0, 1, false, COLA_PREC_F64);
+      dots<double>(c, B.r64, B.r64, N, R, dp64, rr64);
+      k_refresh<T><<<rows_grid(N, R, nblk), 256, 0, c->s>>>(N, B.r64, B.r, B.invd, B.z, nblk,
+                                                             B.part_rz, B.part_rr);
+      c->count_launch();
+      k_cg_restate<<<(unsigned)((R + 127) / 128), 128, 0, c->s>>>(
+          B.st, B.part_rz, B.part_rr, nblk, R, rr64, bb, o.tol, 0);
+      c->count_launch();
+      ++updates;
+      read_state();
+      any_active = false;
+      for (int64_t r = 0; r < R; ++r) any_active |= hst[r].active != 0;
+    }
+    if (refine && updates >= o.max_updates) break;
+  }
+
+  // Final solution and true residual.
+  cola_status result = COLA_OK;
+  if (refine) {
+    k_accum_x<T><<<ew_blocks(N * R), 256, 0, c->s>>>(N * R, B.x64, B.x);
+    c->count_launch();
+    COLA_CUDA(cudaMemcpyAsync(Xout, B.x64, 8 * N * R, cudaMemcpyDeviceToDevice, c->s));
+    COLA_CUDA(cudaMemcpyAsync(B.r64, B.b64, 8 * N * R, cudaMemcpyDeviceToDevice, c->s));
+    apply<double>(c, op, B.x64, B.r64, R, -1.0, 1.0, 1, false, COLA_PREC_F64);
+    dots<double>(c, B.r64, B.r64, N, R, dp64, rr64);
+  } else {
+    COLA_CUDA(cudaMemcpyAsync(Xout, B.x, sizeof(T) * N * R, cudaMemcpyDeviceToDevice, c->s));
+    COLA_CUDA(cudaMemcpyAsync(B.r, Bin, sizeof(T) * N * R, cudaMemcpyDeviceToDevice, c->s));
+    apply<T>(c, op, B.x, B.r, R, -1.0, 1.0, 1, false, prec);
+    dots<T>(c, B.r, B.r, N, R, B.dotp, rr64);
+  }
+  std::vector<double> hrr(R), hbb(R);
+  COLA_CUDA(cudaMemcpyAsync(hrr.data(), rr64, 8 * R, cudaMemcpyDeviceToHost, c->s));
+  COLA_CUDA(cudaMemcpyAsync(hbb.data(), bb, 8 * R, cudaMemcpyDeviceToHost, c->s));
+  read_state();
+  for (int64_t r = 0; r < R; ++r) {
+    const double rel = hbb[r] > 0 ? std::sqrt(std::max(hrr[r], 0.0) / hbb[r]) : 0.0;
+    int st = hst[r].status;
+    if (st == 0 && !(rel <= o.tol * (refine || prec == COLA_PREC_F64 ? 1.0 : 10.0)))
+      st = COLA_ERR_NOT_CONVERGED;
+    if (st != 0 && result == COLA_OK) result = (cola_status)st;
+    if (info) {
+      info[r].iterations = hst[r].iters;
+      info[r].rel_residual = rel;
+      info[r].updates = hst[r].updates;
+      info[r].status = st;
+    }
+  }
+  (void)io64;
+  return result;
+}
+
+cola_status cg_solve_impl(Ctx* c, const cola_linop* op, const void* B, void* X, int64_t R,
+                          const cola_cg_opts& o, cola_cg_info* info) {
+  cola_linop* m = const_cast<cola_linop*>(op);
+  if (o.precision == COLA_PREC_F64) return cg_run<double>(c, m, B, X, R, o, info, false);
+  return cg_run<float>(c, m, B, X, R, o, info, false);
+}
+
+void check_cg_args(const cola_linop* op, const cola_cg_opts* o, int64_t R) {
+  COLA_REQUIRE(op->spd, COLA_ERR_INVALID_ARG, "CG needs an operator annotated spd (set_spd)");
+  COLA_REQUIRE(op->rows == op->cols, COLA_ERR_SHAPE, "CG needs a square operator");
+  COLA_REQUIRE(R >= 1, COLA_ERR_INVALID_ARG, "nrhs = %lld", (long long)R);
+  COLA_REQUIRE(o->precision >= COLA_PREC_F64 && o->precision <= COLA_PREC_MIXED,
+               COLA_ERR_INVALID_ARG, "precision %d", o->precision);
+  COLA_REQUIRE(o->tol >= 0.0 && o->maxiter >= 0, COLA_ERR_INVALID_ARG, "tol/maxiter");
+  COLA_REQUIRE(o->split_factor_terms >= 1 && o->split_factor_terms <= 3 &&
+                   o->split_vector_terms >= 1 && o->split_vector_terms <= 3,
+               COLA_ERR_INVALID_ARG, "split terms must be 1..3");
+}
+
+// ------------------------------------------------------------- bilinear
+void bilinear_entry(Ctx* c, const cola_linop* op, const void* U, const void* X,
+                    const double* weights, int64_t R, int prec, void* const* grads,
+                    int accumulate, int depth) {
+  cola_linop* m = const_cast<cola_linop*>(op);
+  std::vector<const cola_linop*> leaves;
+  collect_leaves(op, leaves);
+  const bool f64 = prec == COLA_PREC_F64;
+  prepare_leaves(c, m, f64 ? COLA_PREC_F64 : COLA_PREC_F32, 0);
+  const size_t es = f64 ? 8 : 4;
+  const int64_t n_in = op->cols, n_out = op->rows;
+  // weighted copy of U
+  void* Uw = c->ws.get("bl.Uw", es * n_out * R);
+  COLA_CUDA(cudaMemcpyAsync(Uw, U, es * n_out * R, cudaMemcpyDeviceToDevice, c->s));
+  if (weights) {
+    double* wd = (double*)c->ws.get("bl.w", 8 * R);
+    COLA_CUDA(cudaMemcpyAsync(wd, weights, 8 * R, cudaMemcpyHostToDevice, c->s));
+    if (f64)
+      scale_rows<double>(c, (double*)Uw, n_out, R, wd);
+    else
+      scale_rows<float>(c, (float*)Uw, n_out, R, wd);
+  }
+  // per-leaf accumulators in working type
+  std::vector<void*> acc(leaves.size(), nullptr);
+  std::vector<int64_t> cnt(leaves.size(), 0);
+  for (size_t l = 0; l < leaves.size(); ++l) {
+    if (!grads[l]) continue;
+    const cola_linop* f = leaves[l];
+    int64_t elems = f->kind == LK_DENSE ? f->rows * f->cols
+                    : f->kind == LK_DIAG ? (f->stride ? f->rows : 1)
+                                         : f->rows * f->rank;
+    cnt[l] = elems;
+    char nm[32];
+    snprintf(nm, sizeof nm, "bl.g%zu", l);
+    acc[l] = c->ws.get(nm, es * elems);
+    COLA_CUDA(cudaMemsetAsync(acc[l], 0, es * elems, c->s));
+  }
+  int li = 0;
+  if (f64)
+    bilinear<double>(c, op, (const double*)Uw, (const double*)X, R, 1.0, acc, li, depth + 1);
+  else
+    bilinear<float>(c, op, (const float*)Uw, (const float*)X, R, 1.0, acc, li, depth + 1);
+  (void)n_in;
+  // write / accumulate into the caller's buffers in the leaf dtype
+  for (size_t l = 0; l < leaves.size(); ++l) {
+    if (!grads[l]) continue;
+    const cola_dtype dt = leaves[l]->dtype;
+    if (!accumulate) COLA_CUDA(cudaMemsetAsync(grads[l], 0, (dt == COLA_F64 ? 8 : 4) * cnt[l], c->s));
+    if (f64 && dt == COLA_F64)
+      add_partials<double>(c, (const double*)acc[l], (double*)grads[l], cnt[l], 1, 1.0);
+    else if (!f64 && dt == COLA_F32)
+      add_partials<float>(c, (const float*)acc[l], (float*)grads[l], cnt[l], 1, 1.0);
+    else if (f64) {
+      float* t = (float*)c->ws.get("bl.cvt", 4 * cnt[l]);
+      convert<double, float>(c, (const double*)acc[l], t, cnt[l]);
+      add_partials<float>(c, t, (float*)grads[l], cnt[l], 1, 1.0);
+    } else {
+      double* t = (double*)c->ws.get("bl.cvt", 8 * cnt[l]);
+      convert<float, double>(c, (const float*)acc[l], t, cnt[l]);
+      add_partials<double>(c, t, (double*)grads[l], cnt[l], 1, 1.0);
+    }
+  }
+}
+
+}  // namespace cola
+
+using namespace cola;
+
+extern "C" {
+
+void cola_cg_opts_default(cola_cg_opts* o) {
+  if (!o) return;
+  memset(o, 0, sizeof *o);
+  o->tol = 1e-8;
+  o->maxiter = 100000;
+  o->precision = COLA_PREC_MIXED;
+  o->refine = 1;
+  o->reliable_delta = 0.1;
+  o->max_updates = 200;
+  o->split_factor_terms = 2;
+  o->split_vector_terms = 2;
+  o->graph_chunk = 64;
+  o->jacobi = 0;
+  o->x0_given = 0;
+}
+
+cola_status cola_cg_solve(cola_ctx* ctx, const cola_linop* op, const void* B, void* X,
+                          int64_t nrhs, const cola_cg_opts* opts, cola_cg_info* info,
+                          cola_stream stream) {
+  cola_status result = COLA_OK;
+  cola_status st = guard([&] {
+    COLA_REQUIRE(ctx && op && B && X && opts, COLA_ERR_INVALID_ARG, "NULL argument");
+    check_cg_args(op, opts, nrhs);
+    StreamJoin j(ctx, stream);
+    result = cg_solve_impl(ctx, op, B, X, nrhs, *opts, info);
+    if (result != COLA_OK) set_error_message(result == COLA_ERR_NOT_CONVERGED
+                                                 ? "CG did not reach tol for every RHS"
+                                                 : "CG breakdown (p^T A p <= 0 or non-finite)");
+  });
+  return st != COLA_OK ? st : result;
+}
+
+cola_status cola_cg_solve_batched(cola_ctx* ctx, int32_t nsys, const cola_linop* const* ops,
+                                  const void* const* B, void* const* X, const int64_t* nrhs,
+                                  const cola_cg_opts* opts, cola_cg_info* info,
+                                  cola_stream stream) {
+  cola_status result = COLA_OK;
+  cola_status st = guard([&] {
+    COLA_REQUIRE(ctx && ops && B && X && nrhs && opts, COLA_ERR_INVALID_ARG, "NULL argument");
+    COLA_REQUIRE(nsys >= 1, COLA_ERR_INVALID_ARG, "nsys = %d", nsys);
+    for (int s = 0; s < nsys; ++s) {
+      COLA_REQUIRE(ops[s] && B[s] && X[s], COLA_ERR_INVALID_ARG, "system %d: NULL argument", s);
+      check_cg_args(ops[s], opts, nrhs[s]);
+    }
+    StreamJoin j(ctx, stream);
+    result = batched_cg_impl(ctx, nsys, ops, B, X, nrhs, *opts, info);
+  });
+  return st != COLA_OK ? st : result;
+}
+
+cola_status cola_lanczos(cola_ctx* ctx, const cola_linop* op, const void* Q0, int64_t nvec,
+                         int32_t m, int32_t prec, int32_t reorth, double* alpha, double* beta,
+                         int32_t* m_eff, cola_stream stream) {
+  return guard([&] {
+    COLA_REQUIRE(ctx && op && Q0 && alpha && beta && m_eff, COLA_ERR_INVALID_ARG,
+                 "NULL argument");
+    COLA_REQUIRE(op->spd, COLA_ERR_INVALID_ARG, "Lanczos needs an operator annotated spd");
+    COLA_REQUIRE(nvec >= 1 && m >= 1, COLA_ERR_INVALID_ARG, "nvec/m");
+    COLA_REQUIRE(prec >= COLA_PREC_F64 && prec <= COLA_PREC_MIXED, COLA_ERR_INVALID_ARG,
+                 "precision");
+    StreamJoin j(ctx, stream);
+    lanczos_impl(ctx, op, Q0, nvec, m, prec, reorth, alpha, beta, m_eff);
+  });
+}
+
+}  // extern "C"
+
+namespace cola {
+
+template <typename T>
+static void lanczos_run(Ctx* c, cola_linop* op, const T* Q0, int64_t nv, int m, int prec,
+                        int reorth, double* alpha, double* beta, int* m_eff) {
+  const int64_t N = op->rows;
+  const int nblk = dot_blocks(N);
+  auto& ws = c->ws;
+  prepare_leaves(c, op, prec, 2);
+  T* bufs[3];
+  bufs[0] = (T*)ws.get("lz.0", sizeof(T) * N * nv);
+  bufs[1] = (T*)ws.get("lz.1", sizeof(T) * N * nv);
+  bufs[2] = (T*)ws.get("lz.2", sizeof(T) * N * nv);
+  T* Qall = reorth ? (T*)ws.get("lz.Q", sizeof(T) * N * nv * m) : nullptr;
+  T* H = reorth ? (T*)ws.get("lz.H", sizeof(T) * nv * m) : nullptr;
+  double* part = (double*)ws.get("lz.part", 8 * nblk * nv);
+  double* nrm2 = (double*)ws.get("lz.nrm2", 8 * nv);
+  double* a_cur = (double*)ws.get("lz.a", 8 * nv);
+  double* b_cur = (double*)ws.get("lz.b", 8 * nv);
+  LzState* st = (LzState*)ws.get("lz.st", sizeof(LzState) * nv);
+  COLA_CUDA(cudaMemsetAsync(alpha, 0, 8 * nv * m, c->s));
+  COLA_CUDA(cudaMemsetAsync(beta, 0, 8 * nv * m, c->s));
+  T *qprev = bufs[0], *q = bufs[1], *w = bufs[2];
+  fill_zero<T>(c, qprev, N * nv);
+  dots<T>(c, Q0, Q0, N, nv, part, nrm2);
+  k_lz_init<<<(unsigned)((nv + 127) / 128), 128, 0, c->s>>>(st, nrm2, nv, m);
+  c->count_launch();
+  k_lz_scale<T><<<dim3(ew_blocks(N), (unsigned)nv), 256, 0, c->s>>>(N, Q0, q, nrm2);
+  c->count_launch();
+  const double eps = (prec == COLA_PREC_F64) ? 1e-10 : 1e-6;
+  for (int j = 0; j < m; ++j) {
+    apply<T>(c, op, q, w, nv, 1.0, 0.0, 1, false, prec);
+    k_lz_a<T><<<rows_grid(N, nv, nblk), 256, 0, c->s>>>(N, w, qprev, q, st, nblk, part);
+    c->count_launch();
+    k_lz_alpha<<<(unsigned)((nv + 127) / 128), 128, 0, c->s>>>(st, part, nblk, nv, j, m, alpha,
+                                                              a_cur);
+    c->count_launch();
+    k_lz_b<T><<<rows_grid(N, nv, nblk), 256, 0, c->s>>>(N, w, q, a_cur, nblk, part,
+                                                         reorth ? 0 : 1);
+    c->count_launch();
+    if (reorth) {
+      COLA_CUDA(cudaMemcpy2DAsync(Qall + (int64_t)j * N, sizeof(T) * N * m, q, sizeof(T) * N,
+                                  sizeof(T) * N, nv, cudaMemcpyDeviceToDevice, c->s));
+      for (int pass = 0; pass < 2; ++pass) {
+        // H[v][0..j] = Q_v[0..j] w_v ; w_v -= H[v] Q_v
+        gemm<T>(c, 1, j + 1, N, 1.0, w, N, 1, N, Qall, 1, N, N * m, 0.0, H, j + 1, 1, m, nv);
+        gemm<T>(c, 1, N, j + 1, -1.0, H, j + 1, 1, m, Qall, N, 1, N * m, 1.0, w, N, 1, N, nv);
+      }
+      dots<T>(c, w, w, N, nv, part, nrm2);
+    } else {
+      dot_final(c, part, nblk, nv, nrm2);
+    }
+    k_lz_beta<<<(unsigned)((nv + 127) / 128), 128, 0, c->s>>>(st, nrm2, nv, j, m, eps, beta,
+                                                             b_cur);
+    c->count_launch();
+    k_lz_next<T><<<dim3(ew_blocks(N), (unsigned)nv), 256, 0, c->s>>>(N, w, b_cur);
+    c->count_launch();
+    T* old = qprev;
+    qprev = q;
+    q = w;
+    w = old;
+  }
+  k_lz_meff<<<(unsigned)((nv + 127) / 128), 128, 0, c->s>>>(st, nv, m_eff);
+  c->count_launch();
+  COLA_CUDA(cudaGetLastError());
+}
+
+void lanczos_impl(Ctx* c, const cola_linop* op, const void* Q0, int64_t nv, int m, int prec,
+                  int reorth, double* alpha, double* beta, int* m_eff) {
+  cola_linop* mo = const_cast<cola_linop*>(op);
+  if (prec == COLA_PREC_F64)
+    lanczos_run<double>(c, mo, (const double*)Q0, nv, m, prec, reorth, alpha, beta, m_eff);
+  else
+    lanczos_run<float>(c, mo, (const float*)Q0, nv, m, prec, reorth, alpha, beta, m_eff);
+}
+
+}  // namespace cola
+
+// ===================================================================== SLQ
+namespace cola {
+
+static void slq_impl(Ctx* c, const cola_linop* op, int nprobes, int m, uint64_t seed,
+                     const void* probes, int prec, int reorth, double* logdet, double* std_err,
+                     double* per_probe, int* clamped) {
+  COLA_REQUIRE(m <= kMaxQuadM, COLA_ERR_UNSUPPORTED, "SLQ: m = %d > %d", m, kMaxQuadM);
+  COLA_REQUIRE(nprobes <= 1024, COLA_ERR_UNSUPPORTED, "SLQ: nprobes = %d > 1024", nprobes);
+  const int64_t N = op->rows;
+  const bool f64 = prec == COLA_PREC_F64;
+  const size_t es = f64 ? 8 : 4;
+  auto& ws = c->ws;
+  void* Z = (void*)probes;
+  if (!probes) {
+    Z = ws.get("slq.Z", es * N * nprobes);
+    rademacher(c, seed, 0, N * nprobes, Z, f64 ? COLA_F64 : COLA_F32);
+  }
+  double* alpha = (double*)ws.get("slq.alpha", 8 * (size_t)nprobes * m);
+  double* beta = (double*)ws.get("slq.beta", 8 * (size_t)nprobes * m);
+  int* meff = (int*)ws.get("slq.meff", 4 * nprobes);
+  double* zn = (double*)ws.get("slq.zn", 8 * nprobes);
+  double* pp = per_probe ? per_probe : (double*)ws.get("slq.pp", 8 * nprobes);
+  double* summ = (double*)ws.get("slq.sum", 16);
+  int* ncl = (int*)ws.get("slq.ncl", 4);
+  double* part = (double*)ws.get("slq.part", 8 * (size_t)dot_blocks(N) * nprobes);
+  lanczos_impl(c, op, Z, nprobes, m, prec, reorth, alpha, beta, meff);
+  if (f64)
+    dots<double>(c, (const double*)Z, (const double*)Z, N, nprobes, part, zn);
+  else
+    dots<float>(c, (const float*)Z, (const float*)Z, N, nprobes, part, zn);
+  k_slq_quad<<<1, 128, 0, c->s>>>(alpha, beta, meff, m, nprobes, zn, pp, summ, ncl);
+  c->count_launch();
+  COLA_CUDA(cudaGetLastError());
+  double hs[2];
+  int hc = 0;
+  COLA_CUDA(cudaMemcpyAsync(hs, summ, 16, cudaMemcpyDeviceToHost, c->s));
+  COLA_CUDA(cudaMemcpyAsync(&hc, ncl, 4, cudaMemcpyDeviceToHost, c->s));
+  COLA_CUDA(cudaStreamSynchronize(c->s));
+  if (logdet) *logdet = hs[0];
+  if (std_err) *std_err = hs[1];
+  if (clamped) *clamped = hc;
+}
+
+}  // namespace cola
+
+extern "C" cola_status cola_slq_logdet(cola_ctx* ctx, const cola_linop* op, int32_t nprobes,
+                                       int32_t m, uint64_t seed, const void* probes,
+                                       int32_t prec, int32_t reorth, double* logdet,
+                                       double* std_err, double* per_probe, int32_t* clamped,
+                                       cola_stream stream) {
+  return cola::guard([&] {
+    COLA_REQUIRE(ctx && op && logdet && std_err, COLA_ERR_INVALID_ARG, "NULL argument");
+    COLA_REQUIRE(op->spd, COLA_ERR_INVALID_ARG, "SLQ needs an operator annotated spd");
+    COLA_REQUIRE(nprobes >= 1 && m >= 1, COLA_ERR_INVALID_ARG, "nprobes/m");
+    COLA_REQUIRE(prec >= COLA_PREC_F64 && prec <= COLA_PREC_MIXED, COLA_ERR_INVALID_ARG,
+                 "precision");
+    cola::StreamJoin j(ctx, stream);
+    cola::slq_impl(ctx, op, nprobes, m, seed, probes, prec, reorth, logdet, std_err, per_probe,
+                   clamped);
+  });
+}

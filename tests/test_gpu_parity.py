@@ -1,0 +1,330 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerances: F64 results within 1e-11 relative (rounding order only); F32
+MVMs within 2e-6 of max|A x| (n_k-term FP32 dot products per mode); solves by
+their relative residual and the forward-error bound kappa * tol; SLQ per-probe
+values from the same probes within 1e-8 (F64).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import workloads as wl
+from oracle import exact, grad, krylov, rng
+from oracle import linop as O
+from tests._trees import gpu_tree, leaf_params, oracle_tree
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def cola():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2309_03060_gb300 as c
+    from paper_2309_03060_gb300 import build
+    build.build()
+    return c
+
+
+@pytest.fixture(scope="module")
+def ctx(cola):
+    return cola.Context(0)
+
+
+DEV = "cuda"
+
+
+def _rs(seed):
+    return np.random.default_rng(seed)
+
+
+def _spd(n, seed, shift=0.5):
+    M = _rs(seed).standard_normal((n, n))
+    return M @ M.T / n + shift * np.eye(n)
+
+
+def rel_max_err(a, b):
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
+def _zoo():
+    r = _rs(100)
+    A = r.standard_normal((37, 29))
+    B = r.standard_normal((131, 129))
+    C3 = r.standard_normal((5, 7))
+    S1, S2 = _spd(33, 101), _spd(40, 102)
+    n = 37
+    L = wl.dirichlet_laplacian(n)
+    U = r.standard_normal((n * n, 5)) / n
+    V = r.standard_normal((n * n, 5)) / n
+    d = 0.5 + r.random(n * n)
+    return {
+        "kron_rect": ("kron", [("dense", A), ("dense", B), ("dense", C3)]),
+        "kron_shift": ("sum", [("kron", [("dense", S1), ("dense", S2)]), ("scalar", 0.1, 33 * 40)],
+                       None),
+        "kronsum_tridiag_lowrank": ("sum", [("kronsum", [("dense", L), ("dense", L)]), ("diag", d),
+                                            ("lowrank", U, None)], [1.0, 1.0, 1.0]),
+        "kronsum_dense": ("kronsum", [("dense", S1[:7, :7]), ("dense", _spd(9, 3)),
+                                      ("dense", _spd(11, 4))]),
+        "lowrank_uv": ("sum", [("lowrank", U, V), ("diag", d)], [2.0, -1.0]),
+        "product": ("product", [("kron", [("dense", S1[:6, :6]), ("dense", S2[:7, :7])]),
+                                ("sum", [("diag", d[:42]), ("lowrank", U[:42], V[:42])], None)]),
+        "dense_big": ("dense", r.standard_normal((300, 257))),
+    }
+
+
+@pytest.mark.parametrize("name", list(_zoo().keys()))
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_matvec_parity(cola, ctx, name, prec):
+    spec = _zoo()[name]
+    ref = oracle_tree(spec)
+    dt = torch.float64 if prec == "f64" else torch.float32
+    op = gpu_tree(cola, ctx, spec, torch.float64, DEV)
+    X = _rs(5).standard_normal((3, ref.cols))
+    Y_ref = ref.mvm(X)
+    Y = cola.cola_matvec(ctx, op, torch.tensor(X, dtype=dt, device=DEV),
+                         cola.PREC_F64 if prec == "f64" else cola.PREC_F32)
+    err = rel_max_err(Y.double().cpu().numpy(), Y_ref)
+    assert err < (1e-12 if prec == "f64" else 2e-6), err
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_matvec_kron3_full_size_sampled(cola, ctx, prec):
+    """The three-factor 128^3 workload (N = 2,097,152) in the launch layout
+    the solver uses, checked on sampled rows computed one by one."""
+    w = wl.config2(nrhs=2)
+    spec = ("sum", [("kron", [("dense", f) for f in w.factors]), ("scalar", w.shift, w.N)], None)
+    dt = torch.float64 if prec == "f64" else torch.float32
+    op = gpu_tree(cola, ctx, spec, torch.float64, DEV)
+    X = torch.tensor(w.B, dtype=dt, device=DEV)
+    Y = cola.cola_matvec(ctx, op, X, cola.PREC_F64 if prec == "f64" else cola.PREC_F32)
+    Yh = Y.double().cpu().numpy()
+    K1, K2, K3 = w.factors
+    n = 128
+    idx = _rs(7).integers(0, w.N, size=40)
+    for r in range(2):
+        Xr = w.B[r].reshape(n, n, n)
+        scale = np.max(np.abs(Yh[r]))
+        for I in idx:
+            i1, i2, i3 = I // (n * n), (I // n) % n, I % n
+            # row (i1, i2, i3) of K1 (x) K2 (x) K3 by its definition
+            row = np.einsum("a,b,c->abc", K1[i1], K2[i2], K3[i3])
+            ref = float(np.sum(row * Xr)) + w.shift * Xr[i1, i2, i3]
+            assert abs(Yh[r, I] - ref) <= (1e-11 if prec == "f64" else 2e-6) * scale
+
+
+def test_rademacher_bit_exact(cola, ctx):
+    z = cola.cola_rademacher(ctx, seed=987654321, count=5000, offset=123).cpu().numpy()
+    ref = rng.rademacher_probes(987654321, 1, 5123)[0, 123:]
+    assert np.array_equal(z, ref)
+
+
+def _kron_shift_problem(n1, n2, shift, nrhs, seed):
+    x1 = wl.uniform(wl.substream(seed, 1), (n1,))
+    x2 = wl.uniform(wl.substream(seed, 2), (n2,))
+    K1, K2 = wl.rbf_factor(x1, 0.2), wl.rbf_factor(x2, 0.2)
+    B = wl.normal(wl.substream(seed, 3), (nrhs, n1 * n2))
+    spec = ("sum", [("kron", [("dense", K1), ("dense", K2)]), ("scalar", shift, n1 * n2)], None)
+    return K1, K2, B, spec
+
+
+def test_cg_config1_fp64(cola, ctx):
+    """FP64 CG on K1 (x) K2 + 0.1 I with 64-point factors (N = 4096) to 1e-10."""
+    w = wl.config1()
+    spec = ("sum", [("kron", [("dense", f) for f in w.factors]), ("scalar", w.shift, w.N)], None)
+    op = gpu_tree(cola, ctx, spec, torch.float64, DEV).set_spd()
+    opts = cola.cola_cg_opts_default(precision=cola.PREC_F64, refine=0, tol=w.tol, maxiter=5000)
+    X, info, st = cola.cola_cg_solve(ctx, op, torch.tensor(w.B, device=DEV), opts)
+    assert st == 0
+    x_ref = exact.kron_shift_solve(w.factors, w.shift, w.B)
+    lam = exact.kron_eigenvalues(w.factors, w.shift)
+    kappa = lam.max() / lam.min()
+    assert info[0]["rel_residual"] <= w.tol
+    assert krylov.true_relative_residual(oracle_tree(spec), w.B, X.cpu().numpy())[0] <= 1.5 * w.tol
+    fe = np.linalg.norm(X.cpu().numpy() - x_ref) / np.linalg.norm(x_ref)
+    assert fe <= kappa * w.tol * 2
+    _, it_ref = krylov.cg(oracle_tree(spec), w.B[0], tol=w.tol)
+    assert abs(info[0]["iterations"] - it_ref) <= max(3, 0.05 * it_ref) + opts.graph_chunk
+
+
+@pytest.mark.parametrize("prec", ["f32"])
+def test_cg_refined_reaches_1e8(cola, ctx, prec):
+    K1, K2, B, spec = _kron_shift_problem(45, 70, 0.01, 4, 11)
+    op = gpu_tree(cola, ctx, spec, torch.float64, DEV).set_spd()
+    opts = cola.cola_cg_opts_default(precision=cola.PREC_F32, refine=1, tol=1e-8, maxiter=20000)
+    X, info, st = cola.cola_cg_solve(ctx, op, torch.tensor(B, device=DEV), opts)
+    assert st == 0, info
+    res = krylov.true_relative_residual(oracle_tree(spec), B, X.cpu().numpy())
+    assert np.all(res <= 1e-8), res
+    for i in info:
+        assert i["rel_residual"] <= 1e-8 and i["updates"] >= 1
+    x_ref = exact.kron_shift_solve([K1, K2], 0.01, B)
+    assert np.allclose(X.cpu().numpy(), x_ref, rtol=0, atol=1e-3 * np.max(np.abs(x_ref)))
+
+
+def test_cg_plain_fp32_to_1e4(cola, ctx):
+    K1, K2, B, spec = _kron_shift_problem(30, 50, 0.1, 3, 12)
+    op = gpu_tree(cola, ctx, spec, torch.float64, DEV).set_spd()
+    opts = cola.cola_cg_opts_default(precision=cola.PREC_F32, refine=0, tol=1e-4, maxiter=5000)
+    X, info, st = cola.cola_cg_solve(ctx, op, torch.tensor(B, dtype=torch.float32, device=DEV), opts)
+    res = krylov.true_relative_residual(oracle_tree(spec), B, X.double().cpu().numpy())
+    assert np.all(res <= 2e-4), res
+
+
+def test_jacobi_pcg_poisson_lowrank(cola, ctx):
+    n = 64
+    w = wl.config3(n=n, rank=8, nrhs=3)
+    spec = ("sum", [("kronsum", [("dense", w.L), ("dense", w.L)]), ("diag", w.d),
+                    ("lowrank", w.U, None)], None)
+    op = gpu_tree(cola, ctx, spec, torch.float64, DEV).set_spd()
+    opts = cola.cola_cg_opts_default(precision=cola.PREC_F32, refine=0, tol=1e-6, jacobi=1,
+                                     maxiter=2000, graph_chunk=8)
+    X, info, st = cola.cola_cg_solve(ctx, op, torch.tensor(w.B, dtype=torch.float32, device=DEV),
+                                     opts)
+    ref = oracle_tree(spec)
+    res = krylov.true_relative_residual(ref, w.B, X.double().cpu().numpy())
+    assert np.all(res <= 1e-5), res
+    # iteration count close to the oracle's Jacobi PCG
+    _, it = krylov.cg(ref, w.B[0], tol=1e-6, precond_diag=ref.diag())
+    assert info[0]["iterations"] <= it + 8 + 5
+
+
+def test_cg_not_converged_reports_status(cola, ctx):
+    K1, K2, B, spec = _kron_shift_problem(30, 30, 1e-3, 1, 13)
+    op = gpu_tree(cola, ctx, spec, torch.float64, DEV).set_spd()
+    opts = cola.cola_cg_opts_default(precision=cola.PREC_F64, refine=0, tol=1e-12, maxiter=5,
+                                     graph_chunk=2)
+    X, info, st = cola.cola_cg_solve(ctx, op, torch.tensor(B, device=DEV), opts)
+    assert st == 5 and info[0]["status"] == 5
+    assert np.all(np.isfinite(X.cpu().numpy()))
+
+
+def test_cg_rejects_non_spd_annotation(cola, ctx):
+    K1, K2, B, spec = _kron_shift_problem(8, 8, 0.1, 1, 14)
+    op = gpu_tree(cola, ctx, spec, torch.float64, DEV)
+    with pytest.raises(cola.ColaError) as e:
+        cola.cola_cg_solve(ctx, op, torch.tensor(B, device=DEV),
+                           cola.cola_cg_opts_default(precision=cola.PREC_F64, refine=0))
+    assert e.value.status == 1
+
+
+def test_lanczos_matches_oracle(cola, ctx):
+    w = wl.config1(scale=20)
+    spec = ("sum", [("kron", [("dense", f) for f in w.factors]), ("scalar", w.shift, w.N)], None)
+    op = gpu_tree(cola, ctx, spec, torch.float64, DEV).set_spd()
+    Z = rng.rademacher_probes(3, 4, w.N)
+    m = 30
+    al, be, me = cola.cola_lanczos(ctx, op, torch.tensor(Z, device=DEV), m, cola.PREC_F64,
+                                   reorth=True)
+    al, be, me = al.cpu().numpy(), be.cpu().numpy(), me.cpu().numpy()
+    ref = oracle_tree(spec)
+    for v in range(4):
+        a, b, _ = krylov.lanczos(ref, Z[v], m, reorth=True)
+        assert me[v] == len(a)
+        np.testing.assert_allclose(al[v, :len(a)], a, rtol=1e-9, atol=1e-9)
+        np.testing.assert_allclose(be[v, :len(b)], b, rtol=1e-9, atol=1e-9)
+
+
+def test_slq_config1_fp64(cola, ctx):
+    """16 probes x 50 steps on the N = 4096 workload: per-probe values equal the
+    oracle's SLQ on the same probes; the estimate is within 4 SE of the exact
+    log-det."""
+    w = wl.config1()
+    spec = ("sum", [("kron", [("dense", f) for f in w.factors]), ("scalar", w.shift, w.N)], None)
+    op = gpu_tree(cola, ctx, spec, torch.float64, DEV).set_spd()
+    seed = wl.substream(w.seed, 2)
+    ld, se, pp, cl = cola.cola_slq_logdet(ctx, op, w.slq_probes, w.slq_steps, seed=seed,
+                                          precision=cola.PREC_F64)
+    Z = rng.rademacher_probes(seed, w.slq_probes, w.N)
+    ld_ref, se_ref, pp_ref = krylov.slq_logdet(oracle_tree(spec), Z, w.slq_steps, reorth=False)
+    np.testing.assert_allclose(pp.cpu().numpy(), pp_ref, rtol=1e-7)
+    assert cl == 0
+    exact_ld = exact.kron_shift_logdet(w.factors, w.shift)
+    assert abs(ld - exact_ld) / se < 4.0
+    assert abs(ld - ld_ref) < 1e-7 * abs(ld_ref)
+
+
+def _grad_specs():
+    r = _rs(200)
+    A, B = _spd(7, 201), _spd(9, 202)
+    NA = r.standard_normal((7, 7))
+    n = 63
+    U = r.standard_normal((n, 3))
+    d = 1 + r.random(n)
+    return {
+        "kron_shift": ("sum", [("kron", [("dense", A), ("dense", B)]), ("scalar", 0.3, n)], None),
+        "kron_diag_lowrank": ("sum", [("kron", [("dense", NA), ("dense", B)]), ("diag", d),
+                                      ("lowrank", U, None)], [2.0, 1.0, 0.5]),
+        "kronsum": ("sum", [("kronsum", [("dense", A), ("dense", B)]), ("scalar", 0.2, n)], None),
+        "product": ("product", [("kron", [("dense", NA), ("dense", B)]), ("diag", d)]),
+    }
+
+
+@pytest.mark.parametrize("name", list(_grad_specs().keys()))
+def test_bilinear_grad_parity(cola, ctx, name):
+    spec = _grad_specs()[name]
+    ref = oracle_tree(spec)
+    op = gpu_tree(cola, ctx, spec, torch.float64, DEV)
+    r = _rs(210)
+    U = r.standard_normal((3, ref.rows))
+    X = r.standard_normal((3, ref.cols))
+    wts = [1.0, -0.5, 2.0]
+    g = cola.cola_bilinear_grad(ctx, op, torch.tensor(U, device=DEV), torch.tensor(X, device=DEV),
+                                wts, cola.PREC_F64)
+    g_ref = grad.bilinear_grad(ref, U, X, np.array(wts))
+    for a, b in zip(g, g_ref):
+        np.testing.assert_allclose(a.cpu().numpy().reshape(np.shape(b)) if np.ndim(b) else
+                                   a.cpu().numpy()[0], b, rtol=1e-10, atol=1e-10)
+
+
+def test_solve_backward_parity(cola, ctx):
+    spec = _grad_specs()["kron_shift"]
+    ref = oracle_tree(spec)
+    op = gpu_tree(cola, ctx, spec, torch.float64, DEV).set_spd()
+    r = _rs(220)
+    B = r.standard_normal((2, ref.rows))
+    W = r.standard_normal((2, ref.rows))
+    opts = cola.cola_cg_opts_default(precision=cola.PREC_F64, refine=0, tol=1e-12, maxiter=2000,
+                                     graph_chunk=4)
+    X, _, st = cola.cola_cg_solve(ctx, op, torch.tensor(B, device=DEV), opts)
+    gB, g, info, st2 = cola.cola_solve_backward(ctx, op, X, torch.tensor(W, device=DEV), opts)
+    A = ref.dense()
+    x_ref = exact.dense_solve(A, B)
+    u_ref = exact.dense_solve(A.T, W)
+    np.testing.assert_allclose(gB.cpu().numpy(), u_ref, rtol=1e-8, atol=1e-10)
+    g_ref = [-x for x in grad.bilinear_grad(ref, u_ref, x_ref)]
+    for a, b in zip(g, g_ref):
+        np.testing.assert_allclose(a.cpu().numpy().reshape(np.shape(b)), b, rtol=1e-7, atol=1e-9)
+
+
+def test_logdet_backward_parity(cola, ctx):
+    spec = _grad_specs()["kron_shift"]
+    ref = oracle_tree(spec)
+    op = gpu_tree(cola, ctx, spec, torch.float64, DEV).set_spd()
+    Z = rng.rademacher_probes(5, 6, ref.rows)
+    opts = cola.cola_cg_opts_default(precision=cola.PREC_F64, refine=0, tol=1e-12, maxiter=2000,
+                                     graph_chunk=4)
+    g = cola.cola_logdet_backward(ctx, op, torch.tensor(Z, device=DEV), None, 1.0, opts)
+    U = exact.dense_solve(ref.dense(), Z)
+    g_ref = grad.bilinear_grad(ref, U, Z, np.full(6, 1.0 / 6))
+    for a, b in zip(g, g_ref):
+        np.testing.assert_allclose(a.cpu().numpy().reshape(np.shape(b)), b, rtol=1e-7, atol=1e-9)
+
+
+def test_batched_systems_uneven(cola, ctx):
+    probs = [_kron_shift_problem(n1, n2, s, r, 300 + i)
+             for i, (n1, n2, s, r) in enumerate([(16, 20, 0.1, 1), (33, 17, 0.05, 3),
+                                                  (40, 41, 0.01, 2)])]
+    ops = [gpu_tree(cola, ctx, p[3], torch.float64, DEV).set_spd() for p in probs]
+    Bs = [torch.tensor(p[2], device=DEV) for p in probs]
+    opts = cola.cola_cg_opts_default(precision=cola.PREC_F32, refine=1, tol=1e-8, maxiter=20000,
+                                     graph_chunk=16)
+    Xs, info, st = cola.cola_cg_solve_batched(ctx, ops, Bs, opts)
+    assert st == 0
+    for p, X in zip(probs, Xs):
+        res = krylov.true_relative_residual(oracle_tree(p[3]), p[2], X.cpu().numpy())
+        assert np.all(res <= 1e-8)

@@ -1,0 +1,367 @@
+"""Benchmark: Kronecker-operator CG solves/s (and iterations/s) to a 1e-8
+relative residual, mixed precision vs plain FP32, on one GB300.
+
+Workload (one step = the whole hot path over one batch of synthetic input):
+  A = K1 (x) K2 (x) K3 + 0.01 I, three 128 x 128 RBF factors (lengthscale 0.1,
+  points uniform in [0,1]), N = 2,097,152; 16 right-hand sides ~ N(0, 1);
+  CG with split-BF16 tensor-core Kronecker contractions, FP32 recurrences and
+  FP64 reliable-update refinement to ||b - A x|| / ||b|| <= 1e-8 for every RHS;
+  then stochastic Lanczos quadrature of log det A with 32 Rademacher probes and
+  100 Lanczos steps.
+
+Prints ONE JSON line (rank 0).  ``--impl reference`` times the FP64 CPU
+oracle instead (bounded sample per step).  Under torchrun every rank runs its
+own replica of the workload (independent right-hand sides, no collective on the
+data path); the time is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import workloads as wl  # noqa: E402
+
+METRIC = "Kron-operator CG solves/s and iters/s to 1e-8 residual, mixed vs FP32 plain"
+UNIT = "solves/s"
+WORKLOAD = "kron3_rbf128_mixed: K1(x)K2(x)K3 + 0.01 I, n=128^3 (N=2,097,152), 16 RHS, tol 1e-8; SLQ 32x100"
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d.get("hbm_gbs", 6800.0), d.get("bf16_tflops", 1900.0), "measured"
+    return 6800.0, 1900.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup(gpus: int):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if gpus > 0 else "gloo")
+        pg = dist
+    return rank, world, local, pg
+
+
+def max_over_ranks(pg, value: float, device) -> float:
+    if pg is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(pg):
+    if pg is not None:
+        pg.barrier()
+
+
+# ----------------------------------------------------------------- our arm
+def build_operator(cola, ctx, w, device):
+    import torch
+    K = [torch.tensor(f, device=device) for f in w.factors]
+    s = torch.tensor([w.shift], dtype=torch.float64, device=device)
+    kron = cola.cola_linop_kron(ctx, *[cola.cola_linop_dense(ctx, k) for k in K])
+    op = cola.cola_linop_sum(ctx, [kron, cola.cola_linop_diag(ctx, s, n=w.N)]).set_spd()
+    return op, kron
+
+
+def run_ours(args):
+    import torch
+    import paper_2309_03060_gb300 as cola
+
+    rank, world, local, pg = dist_setup(args.gpus)
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    ctx = cola.Context(local)
+    w = wl.config2(nrhs=args.nrhs)
+    op, kron = build_operator(cola, ctx, w, device)
+    # each rank solves its own independent block of right-hand sides
+    B_host = torch.tensor(w.B if rank == 0 else
+                          wl.normal(wl.substream(w.seed, 100 + rank), w.B.shape)).pin_memory()
+    B = B_host.to(device)
+    opts = cola.cola_cg_opts_default(precision=cola.PREC_MIXED, refine=1, tol=w.tol,
+                                     maxiter=args.maxiter, split_factor_terms=args.terms,
+                                     split_vector_terms=args.terms, graph_chunk=args.chunk,
+                                     reliable_delta=args.delta)
+    seed = wl.substream(w.seed, 2)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        X, info, st = cola.cola_cg_solve(ctx, op, B, opts)
+        if st != 0:
+            raise RuntimeError(f"solve status {st}: {info[:2]}")
+        ld, se, _, clamped = cola.cola_slq_logdet(ctx, op, w.slq_probes, w.slq_steps, seed=seed,
+                                                  precision=cola.PREC_MIXED)
+        return X, info, ld, se, clamped
+
+    for _ in range(args.warmup):
+        X, info, ld, se, clamped = step()
+    barrier(pg)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    l0 = ctx.kernel_launches()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    iters = []
+    ev0.record(stream)
+    for _ in range(args.steps):
+        X, info, ld, se, clamped = step()
+        iters.append(max(i["iterations"] for i in info))
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier(pg)
+    t_local = ev0.elapsed_time(ev1) / 1e3
+    launches = ctx.kernel_launches() - l0
+    clk = clocks.stop()
+    t = max_over_ranks(pg, t_local, device)
+    R = args.nrhs
+    solves = R * args.steps * world
+    value = solves / t
+    it_per_solve = statistics.mean(iters)
+    worst_res = max(i["rel_residual"] for i in info)
+
+    # end to end through the public API: pinned host B in, host X out, timed per step
+    e2e_t = 0.0
+    Xh = torch.empty_like(B_host).pin_memory()
+    for k in range(args.e2e_steps):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        Bd = B_host.to(device, non_blocking=True)
+        Xd, info_e, st = cola.cola_cg_solve(ctx, op, Bd, opts)
+        ld_e, _, _, _ = cola.cola_slq_logdet(ctx, op, w.slq_probes, w.slq_steps, seed=seed,
+                                             precision=cola.PREC_MIXED)
+        Xh.copy_(Xd, non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        e2e_t += e0.elapsed_time(e1) / 1e3
+    e2e_t = max_over_ranks(pg, e2e_t, device)
+    e2e = {"value": R * args.e2e_steps * world / e2e_t, "unit": UNIT,
+           "h2d_bytes_per_step": B_host.numel() * 8, "d2h_bytes_per_step": Xh.numel() * 8 + 16}
+
+    # dominant kernel: the tensor-core Kronecker mode product, timed alone on the
+    # same operator and launch configuration as inside the solve (3 launches / MVM)
+    hbm, tflops, peak_src = peaks()
+    Xf = torch.randn(R, w.N, dtype=torch.float32, device=device)
+    Yf = torch.empty_like(Xf)
+    for _ in range(3):
+        cola.cola_matvec(ctx, kron, Xf, cola.PREC_MIXED, out=Yf, split_terms=args.terms)
+    torch.cuda.synchronize()
+    reps = 20
+    k0, k1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    k0.record(stream)
+    for _ in range(reps):
+        cola.cola_matvec(ctx, kron, Xf, cola.PREC_MIXED, out=Yf, split_terms=args.terms)
+    k1.record(stream)
+    torch.cuda.synchronize()
+    per_launch = k0.elapsed_time(k1) / 1e3 / (reps * 3)
+    alg_bytes = 8.0 * R * w.N                   # read X + write Y, FP32, per mode step
+    achieved = alg_bytes / per_launch / 1e9
+    roofline = {"kernel": "k_kron_tc (split-BF16 tcgen05 mode product)", "bound": "hbm",
+                "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
+                "frac": round(achieved / hbm, 4), "peak_source": peak_src,
+                "traffic": args.traffic_bytes, "launch_us": round(per_launch * 1e6, 2)}
+    # per-iteration roofline (32 N R algorithmic bytes per CG iteration)
+    it_time = t_local / args.steps  # whole step incl. SLQ, bounded below by CG alone
+    iter_alg = 32.0 * w.N * R
+
+    cpu = cpu_baseline(args, w, it_per_solve) if (rank == 0 and not args.no_cpu) else None
+
+    plain = None
+    if rank == 0 and args.plain:
+        popts = cola.cola_cg_opts_default(precision=cola.PREC_F32, refine=1, tol=w.tol,
+                                          maxiter=args.maxiter, graph_chunk=args.chunk,
+                                          reliable_delta=args.delta)
+        torch.cuda.synchronize()
+        p0 = time.perf_counter()
+        Xp, pinfo, pst = cola.cola_cg_solve(ctx, op, B, popts)
+        torch.cuda.synchronize()
+        pt = time.perf_counter() - p0
+        plain = {"solves_per_s": R / pt, "iterations": max(i["iterations"] for i in pinfo),
+                 "status": pst, "worst_rel_residual": max(i["rel_residual"] for i in pinfo)}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(1e3 * t / args.steps, 2), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "bf16x2-split/f32/f64",
+            "data": "synthetic (seeded SplitMix64; RBF factors on uniform points, N(0,1) RHS)",
+            "config": {"workload": WORKLOAD, "nrhs_per_gpu": R, "N": w.N,
+                       "split_terms": args.terms, "tol": w.tol,
+                       "l2": "inputs larger than L2 (16 x 2M FP32 vectors, 134 MB each)",
+                       "parallelism": f"replicas x{world}"},
+            "iters_per_s": round(it_per_solve * args.steps * world / t, 2),
+            "cg_iterations_per_solve": it_per_solve,
+            "logdets_per_s": round(args.steps * world / t, 4),
+            "worst_rel_residual": worst_res, "slq_logdet": ld, "slq_stderr": se,
+            "slq_clamped": clamped,
+            "roofline": roofline,
+            "iteration_roofline": {"alg_bytes_per_iter": iter_alg,
+                                   "step_time_s": round(it_time, 4)},
+            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
+            "clocks": clk, "plain_fp32": plain,
+        }
+        print(json.dumps(line))
+    ctx.close()
+
+
+# ------------------------------------------------------------- CPU oracle
+def _oracle_cg_sample(w, iters: int, threads: int):
+    """FP64 oracle CG iterations on all RHS; returns seconds per iteration."""
+    os.environ["OPENBLAS_NUM_THREADS"] = str(threads)
+    from oracle import krylov  # noqa: F401  (oracle imported only on this leg)
+    from oracle.linop import Dense, Diag, Kron, Sum
+    op = Sum([Kron([Dense(f) for f in w.factors]), Diag(w.shift, w.N)])
+    t0 = time.perf_counter()
+    for r in range(w.B.shape[0]):
+        krylov.cg(op, w.B[r], tol=0.0, maxiter=iters)
+    return (time.perf_counter() - t0) / iters
+
+
+def cpu_baseline(args, w, gpu_iters_per_solve):
+    code = (
+        "import sys,json,os; sys.path.insert(0, %r);"
+        "import bench, workloads as wl;"
+        "w = wl.config2(nrhs=%d);"
+        "print(json.dumps(bench._oracle_cg_sample(w, %d, %d)))"
+    ) % (ROOT, args.nrhs, args.cpu_iters, os.cpu_count() or 1)
+    env = dict(os.environ, OPENBLAS_NUM_THREADS=str(os.cpu_count() or 1),
+               OMP_NUM_THREADS=str(os.cpu_count() or 1))
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env,
+                       timeout=900)
+    if r.returncode != 0:
+        return {"error": r.stderr[-300:]}
+    sec_per_iter = json.loads(r.stdout.strip().splitlines()[-1])
+    solve_time = sec_per_iter * gpu_iters_per_solve
+    return {"value": args.nrhs / solve_time, "unit": UNIT, "cores": os.cpu_count(),
+            "kind": "oracle",
+            "sample": (f"{args.cpu_iters} FP64 oracle CG iterations on each of the {args.nrhs} "
+                       f"RHS ({sec_per_iter:.3f} s per all-RHS iteration), extrapolated to the "
+                       f"{gpu_iters_per_solve:.0f} iterations per solve the GPU run needed")}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    w = wl.config2(nrhs=args.nrhs)
+    iters_needed = args.ref_iters_per_solve
+    for _ in range(args.warmup):
+        _oracle_cg_sample(w, 1, os.cpu_count() or 1)
+    t = 0.0
+    for _ in range(args.steps):
+        t += _oracle_cg_sample(w, args.cpu_iters, os.cpu_count() or 1)
+    sec_per_iter = t / args.steps
+    value = args.nrhs / (sec_per_iter * iters_needed)
+    sample = (f"per step {args.cpu_iters} FP64 oracle CG iterations on each of {args.nrhs} RHS; "
+              f"solves/s extrapolated to {iters_needed} iterations per solve")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sec_per_iter * args.cpu_iters,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--nrhs", type=int, default=16)
+    ap.add_argument("--terms", type=int, default=2)
+    ap.add_argument("--chunk", type=int, default=64)
+    ap.add_argument("--delta", type=float, default=0.1)
+    ap.add_argument("--maxiter", type=int, default=60000)
+    ap.add_argument("--e2e-steps", type=int, default=1)
+    ap.add_argument("--cpu-iters", type=int, default=2)
+    ap.add_argument("--ref-iters-per-solve", type=int, default=12400)
+    ap.add_argument("--traffic-bytes", type=float, default=None)
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--plain", action="store_true", help="also time the plain FP32 path once")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

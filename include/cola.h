@@ -270,6 +270,11 @@ cola_status cola_logdet_backward(cola_ctx* ctx, const cola_linop* op, const void
 cola_status cola_rademacher(cola_ctx* ctx, uint64_t seed, int64_t offset, int64_t count,
                             void* out, cola_dtype dtype, cola_stream stream);
 
+/* BF16 terms per Kronecker-factor entry and per vector entry (1..3) used by
+ * cola_matvec with COLA_PREC_MIXED (the solvers take theirs from
+ * cola_cg_opts).  Default 2 / 2. */
+cola_status cola_set_split_terms(cola_ctx* ctx, int32_t factor_terms, int32_t vector_terms);
+
 /* Number of kernels this library launched (or recorded into replayed graphs,
  * counted per replay) since the context was created. */
 cola_status cola_kernel_launches(const cola_ctx* ctx, int64_t* count);

@@ -177,7 +177,7 @@ def cola_linop_product(ctx: Context, terms) -> LinOp:
 
 
 def cola_matvec(ctx: Context, op: LinOp, X: torch.Tensor, precision: int = PREC_F64,
-                out: torch.Tensor | None = None) -> torch.Tensor:
+                out: torch.Tensor | None = None, split_terms: int = 2) -> torch.Tensor:
     X2 = X if X.dim() == 2 else X.reshape(1, -1)
     rows, cols = op.shape
     if X2.shape[1] != cols:
@@ -186,6 +186,7 @@ def cola_matvec(ctx: Context, op: LinOp, X: torch.Tensor, precision: int = PREC_
     if X2.dtype != want:
         raise TypeError(f"precision {precision} needs {want} vectors")
     Y = out if out is not None else torch.empty((X2.shape[0], rows), dtype=want, device=X.device)
+    check(_lib().cola_set_split_terms(ctx.handle, int(split_terms), int(split_terms)))
     check(_lib().cola_matvec(ctx.handle, op.handle, _ptr(X2), _ptr(Y), X2.shape[0], precision,
                              _stream()))
     return Y if X.dim() == 2 else Y.reshape(-1)

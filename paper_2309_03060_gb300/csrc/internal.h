@@ -71,6 +71,8 @@ struct Ctx {
   cudaEvent_t ev_a = nullptr, ev_b = nullptr;
   Workspace ws;
   int64_t launches = 0;
+  int split_vector_terms = 2;  // BF16 terms per vector entry of the MIXED contraction
+  int split_factor_terms = 2;  // BF16 terms per factor entry (cola_matvec)
   bool capturing = false;
   int64_t captured = 0;
   std::map<std::string, GraphEntry> graphs;
@@ -229,5 +231,7 @@ void bilinear_entry(Ctx* c, const cola_linop* op, const void* U, const void* X,
                     const double* weights, int64_t R, int prec, void* const* grads,
                     int accumulate, int depth);
 void check_cg_args(const cola_linop* op, const cola_cg_opts* o, int64_t R);
+// Raises COLA_ERR_TIMEOUT when a tensor-core kernel gave up waiting (and clears the flag).
+void tc_check_error(Ctx* c);
 
 }  // namespace cola

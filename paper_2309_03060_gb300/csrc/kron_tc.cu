@@ -1,19 +1,612 @@
-// Kronecker mode contractions on the tcgen05 tensor cores (placeholder until
-// the split-BF16 kernel lands).
+// Kronecker mode products on the tcgen05 tensor cores (sm_103a).
+//
+// One mode step of the Kronecker MVM (Sec. 3.2, Table 3) contracts the leading
+// index of the current layout [j, rest] with a factor K (n_out x n_in):
+//     D[rest, i] = sum_j X[j, rest] * K[i, j]
+// which is a GEMM with M = rest, N = n_out, K = n_in per right-hand side.
+// Operands are split into BF16 terms (x = x_0 + x_1 [+ x_2], each the
+// round-to-nearest BF16 of the remainder) and the cross products whose term
+// indices sum to less than max(T_f, T_v) accumulate in FP32 in tensor memory.
+//
+// Kernel layout (persistent, one 288-thread CTA per SM):
+//   warps 0-3  producers: load FP32 X, split to BF16 terms, write the A tile
+//              (128 rows x 64 k, K-major, 128-byte swizzle) into a pipeline
+//              stage; thread 0 also bulk-copies the pre-split factor tile
+//              (cp.async.bulk, completes on the stage's mbarrier).
+//   warp 8     MMA issuer: waits for a full stage, issues tcgen05.mma for
+//              every 16-wide k step and term pair, commits to the stage's
+//              empty barrier; after the tile, commits to the accumulator's
+//              full barrier.  Also allocates / frees TMEM.
+//   warps 4-7  epilogue: tcgen05.ld the FP32 accumulator (warp w reads TMEM
+//              lanes 32(w-4)..), Y = coeff * D + beta * Y, store.
+// Accumulators are double-buffered in TMEM so the epilogue of one tile
+// overlaps the MMAs of the next.  Every mbarrier wait gives up after ~2 s,
+// raises an error flag and lets the CTA drain and free its TMEM.
+#include <cuda_bf16.h>
+
+#include <stdio.h>
+
+#include <algorithm>
+#include <map>
+#include <string>
+
 #include "internal.h"
 
 namespace cola {
 
-void kron_tc_prepare(Ctx* c, cola_linop* op, int split_terms) { (void)c; (void)op; (void)split_terms; }
+namespace {
+
+constexpr int kTileM = 128;
+constexpr int kBlockK = 64;               // bf16 elements per 128-byte swizzled row
+constexpr int kProducerThreads = 128;
+constexpr int kThreadsTc = 288;
+constexpr uint64_t kWaitNs = 2000000000ull;  // 2 s per wait
+
+struct TcParams {
+  const float* X;
+  float* Y;
+  const uint16_t* Bimg;  // [tf][kblocks][n_pad rows][64] bf16, 128-byte swizzled rows
+  int64_t rest, size_in, size_out, batch, tiles_m, ntiles;
+  int n_in, n_out, n_pad, kblocks, ksteps_last, tf, tv, stages;
+  uint32_t stage_bytes, a_term_bytes, b_term_bytes, tmem_cols;
+  float coeff, beta;
+  int* err;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ uint64_t now_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+               : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.expect_tx.relaxed.cta.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait: false when the phase did not complete within kWaitNs or
+// another role of the CTA already gave up.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
+                                          int* err) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = now_ns();
+  for (uint32_t i = 1;; ++i) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((i & 63) == 0) {
+      if (*abort_flag) return false;
+      if (now_ns() - t0 > kWaitNs) {
+        *abort_flag = 1;
+        atomicExch(err, COLA_ERR_TIMEOUT);
+        return false;
+      }
+    }
+  }
+}
+
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes,
+                                         uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// SMEM matrix descriptor: K-major operand, 128-byte swizzle, 8-row atoms of
+// 1024 bytes (stride-dimension offset 1024), version 1 (bits 46-47).
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+  d |= (uint64_t)1u << 16;                // leading-dimension offset (unused for this layout)
+  d |= (uint64_t)(1024u >> 4) << 32;      // stride-dimension offset
+  d |= (uint64_t)1u << 46;                // descriptor version
+  d |= (uint64_t)2u << 61;                // SWIZZLE_128B
+  return d;
+}
+
+// Instruction descriptor, kind::f16: BF16 x BF16 -> FP32, both K-major.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+  return (1u << 4)                          // D format F32
+         | (1u << 7)                        // A format BF16
+         | (1u << 10)                       // B format BF16
+         | ((uint32_t)(N >> 3) << 17)       // N / 8
+         | ((uint32_t)(M >> 4) << 24);      // M / 16
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
+                                         uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t* r) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// Split two FP32 values into up to three BF16x2 terms (round to nearest even).
+__device__ __forceinline__ void split2(float a, float b, int terms, uint32_t* out) {
+  __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+  out[0] = *reinterpret_cast<uint32_t*>(&h);
+  if (terms > 1) {
+    const float ra = a - __low2float(h), rb = b - __high2float(h);
+    __nv_bfloat162 l = __floats2bfloat162_rn(ra, rb);
+    out[1] = *reinterpret_cast<uint32_t*>(&l);
+    if (terms > 2) {
+      __nv_bfloat162 l2 = __floats2bfloat162_rn(ra - __low2float(l), rb - __high2float(l));
+      out[2] = *reinterpret_cast<uint32_t*>(&l2);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kThreadsTc, 1) k_kron_tc(TcParams p) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  // 1024-byte aligned stage area
+  unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint64_t* bars = (uint64_t*)(base + (size_t)p.stages * p.stage_bytes);
+  uint64_t* full = bars;
+  uint64_t* empty = bars + p.stages;
+  uint64_t* acc_full = bars + 2 * p.stages;
+  uint64_t* acc_empty = acc_full + 2;
+  uint64_t* drain = acc_empty + 2;
+  uint32_t* tmem_slot = (uint32_t*)(drain + 1);
+  volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (tid == 0) {
+    for (int s = 0; s < p.stages; ++s) {
+      mbar_init(&full[s], kProducerThreads);
+      mbar_init(&empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&acc_full[b], 1);
+      mbar_init(&acc_empty[b], 128);
+    }
+    mbar_init(drain, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 8) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(p.tmem_cols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+
+  if (warp < 4) {
+    // ------------------------------------------------------------ producers
+    int s = 0;
+    uint32_t ph = 0;
+    int last_s = -1;
+    uint32_t last_ph = 0;
+    bool ok = true;
+    for (int64_t t = blockIdx.x; t < p.ntiles && ok; t += gridDim.x) {
+      const int64_t r = t / p.tiles_m, m0 = (t % p.tiles_m) * kTileM;
+      const float* Xb = p.X + r * p.size_in;
+      const int64_t m = m0 + tid;
+      const bool row_ok = m < p.rest;
+      for (int kb = 0; kb < p.kblocks; ++kb) {
+        if (!mbar_wait(&empty[s], ph ^ 1u, abort_flag, p.err)) {
+          ok = false;
+          break;
+        }
+        unsigned char* st = base + (size_t)s * p.stage_bytes;
+        if (tid == 0) {
+          mbar_expect_tx(&full[s], p.b_term_bytes * p.tf);
+          for (int ti = 0; ti < p.tf; ++ti)
+            bulk_g2s(st + p.tv * p.a_term_bytes + ti * p.b_term_bytes,
+                     p.Bimg + ((size_t)ti * p.kblocks + kb) * (size_t)p.n_pad * kBlockK,
+                     p.b_term_bytes, &full[s]);
+          last_s = s;
+          last_ph = ph;
+        }
+        const int k0 = kb * kBlockK;
+        float v[kBlockK];
+#pragma unroll
+        for (int k = 0; k < kBlockK; ++k) {
+          const int kk = k0 + k;
+          v[k] = (row_ok && kk < p.n_in) ? __ldg(Xb + (int64_t)kk * p.rest + m) : 0.0f;
+        }
+        const uint32_t row_off = (uint32_t)tid * 128u;
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+          uint32_t w[3][4];
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            uint32_t o[3];
+            split2(v[8 * c + 2 * e], v[8 * c + 2 * e + 1], p.tv, o);
+            w[0][e] = o[0];
+            w[1][e] = o[1];
+            w[2][e] = o[2];
+          }
+          const uint32_t off = row_off + ((uint32_t)(c ^ (tid & 7)) << 4);
+#pragma unroll
+          for (int tv = 0; tv < 3; ++tv) {
+            if (tv < p.tv)
+              *reinterpret_cast<uint4*>(st + tv * p.a_term_bytes + off) =
+                  make_uint4(w[tv][0], w[tv][1], w[tv][2], w[tv][3]);
+          }
+        }
+        fence_proxy_async();
+        mbar_arrive(&full[s]);
+        if (++s == p.stages) {
+          s = 0;
+          ph ^= 1u;
+        }
+      }
+    }
+    // make sure no bulk copy is still landing in this CTA's shared memory
+    if (tid == 0 && last_s >= 0) mbar_wait(&full[last_s], last_ph, abort_flag, p.err);
+  } else if (warp == 8) {
+    // ----------------------------------------------------------------- MMA
+    if (lane == 0) {
+      const uint32_t idesc = idesc_bf16(kTileM, p.n_pad);
+      const int maxt = p.tf > p.tv ? p.tf : p.tv;
+      int s = 0;
+      uint32_t ph = 0;
+      int64_t it = 0;
+      bool ok = true;
+      for (int64_t t = blockIdx.x; t < p.ntiles && ok; t += gridDim.x, ++it) {
+        const int b = (int)(it & 1);
+        if (!mbar_wait(&acc_empty[b], (uint32_t)((it >> 1) & 1) ^ 1u, abort_flag, p.err)) break;
+        tc_fence_after();
+        const uint32_t d_tmem = tmem_base + (uint32_t)(b * p.n_pad);
+        uint32_t accumulate = 0;
+        for (int kb = 0; kb < p.kblocks; ++kb) {
+          if (!mbar_wait(&full[s], ph, abort_flag, p.err)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t st = smem_u32(base + (size_t)s * p.stage_bytes);
+          const int steps = (kb == p.kblocks - 1) ? p.ksteps_last : 4;
+          for (int kk = 0; kk < steps; ++kk) {
+            for (int ti = 0; ti < p.tf; ++ti)
+              for (int tv = 0; tv < p.tv; ++tv) {
+                if (ti + tv >= maxt) continue;
+                const uint64_t ad = sw128_desc(st + tv * p.a_term_bytes + kk * 32);
+                const uint64_t bd =
+                    sw128_desc(st + p.tv * p.a_term_bytes + ti * p.b_term_bytes + kk * 32);
+                mma_bf16(d_tmem, ad, bd, idesc, accumulate);
+                accumulate = 1;
+              }
+          }
+          mma_commit(&empty[s]);
+          if (++s == p.stages) {
+            s = 0;
+            ph ^= 1u;
+          }
+        }
+        if (!ok) break;
+        mma_commit(&acc_full[b]);
+      }
+      // drain: all MMAs issued by this thread have completed
+      mma_commit(drain);
+      mbar_wait(drain, 0, abort_flag, p.err);
+    }
+    __syncwarp();
+  } else {
+    // ------------------------------------------------------------ epilogue
+    const int q = warp - 4;
+    const int row = q * 32 + lane;
+    int64_t it = 0;
+    for (int64_t t = blockIdx.x; t < p.ntiles; t += gridDim.x, ++it) {
+      const int b = (int)(it & 1);
+      if (!mbar_wait(&acc_full[b], (uint32_t)((it >> 1) & 1), abort_flag, p.err)) break;
+      tc_fence_after();
+      const int64_t r = t / p.tiles_m, m0 = (t % p.tiles_m) * kTileM;
+      const int64_t m = m0 + row;
+      float* yrow = p.Y + r * p.size_out + m * p.n_out;
+      const uint32_t taddr = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * p.n_pad);
+      for (int c0 = 0; c0 < p.n_pad; c0 += 16) {
+        uint32_t v[16];
+        tmem_ld16(taddr + (uint32_t)c0, v);
+        if (m < p.rest) {
+          if (c0 + 16 <= p.n_out && (p.n_out & 3) == 0) {
+#pragma unroll
+            for (int e = 0; e < 16; e += 4) {
+              float4 o;
+              o.x = p.coeff * __uint_as_float(v[e]);
+              o.y = p.coeff * __uint_as_float(v[e + 1]);
+              o.z = p.coeff * __uint_as_float(v[e + 2]);
+              o.w = p.coeff * __uint_as_float(v[e + 3]);
+              float4* dst = reinterpret_cast<float4*>(yrow + c0 + e);
+              if (p.beta != 0.0f) {
+                const float4 old = *dst;
+                o.x += p.beta * old.x;
+                o.y += p.beta * old.y;
+                o.z += p.beta * old.z;
+                o.w += p.beta * old.w;
+              }
+              *dst = o;
+            }
+          } else {
+            for (int e = 0; e < 16; ++e) {
+              const int i = c0 + e;
+              if (i >= p.n_out) break;
+              float o = p.coeff * __uint_as_float(v[e]);
+              if (p.beta != 0.0f) o += p.beta * yrow[i];
+              yrow[i] = o;
+            }
+          }
+        }
+      }
+      tc_fence_before();
+      mbar_arrive(&acc_empty[b]);
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 8) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base),
+                 "r"(p.tmem_cols)
+                 : "memory");
+  }
+}
+
+// Pre-split factor image: Fop (n_out x n_in, row-major, Fop = F or F^T) into
+// [tf][kblocks][n_pad][64] BF16 terms with 128-byte swizzled rows.
+template <typename TF>
+__global__ void k_split_factor(const TF* F, int64_t ld, int tr, int n_out, int n_in, int n_pad,
+                               int kblocks, int tf, uint16_t* img) {
+  const int64_t per_term = (int64_t)kblocks * n_pad * kBlockK;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < per_term;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int kb = (int)(e / ((int64_t)n_pad * kBlockK));
+    const int rem = (int)(e % ((int64_t)n_pad * kBlockK));
+    const int i = rem / kBlockK, kk = rem % kBlockK;
+    const int j = kb * kBlockK + kk;
+    double v = 0.0;
+    if (i < n_out && j < n_in) v = (double)(tr ? F[(int64_t)j * ld + i] : F[(int64_t)i * ld + j]);
+    const size_t pos = (size_t)kb * n_pad * kBlockK + (size_t)i * kBlockK +
+                       (size_t)((((kk >> 3) ^ (i & 7)) << 3) | (kk & 7));
+    for (int t = 0; t < tf; ++t) {
+      const __nv_bfloat16 h = __double2bfloat16(v);
+      img[(size_t)t * per_term + pos] = *reinterpret_cast<const uint16_t*>(&h);
+      v -= (double)__bfloat162float(h);
+    }
+  }
+}
+
+struct TcPlan {
+  int n_in, n_out, n_pad, kblocks, ksteps_last, tf, tv, stages;
+  uint32_t stage_bytes, a_term_bytes, b_term_bytes, tmem_cols;
+  size_t smem;
+};
+
+TcPlan make_plan(int n_in, int n_out, int tf, int tv) {
+  TcPlan q{};
+  q.n_in = n_in;
+  q.n_out = n_out;
+  q.n_pad = (n_out + 15) / 16 * 16;
+  const int kpad = (n_in + 15) / 16 * 16;
+  q.kblocks = (kpad + kBlockK - 1) / kBlockK;
+  q.ksteps_last = (kpad - (q.kblocks - 1) * kBlockK) / 16;
+  q.tf = tf;
+  q.tv = tv;
+  q.a_term_bytes = kTileM * 128;
+  q.b_term_bytes = (uint32_t)q.n_pad * 128;
+  q.stage_bytes = (uint32_t)(tv * q.a_term_bytes + tf * q.b_term_bytes);
+  q.stage_bytes = (q.stage_bytes + 1023) / 1024 * 1024;
+  const size_t budget = 200 * 1024;
+  q.stages = (int)std::min<size_t>(4, budget / q.stage_bytes);
+  q.smem = (size_t)q.stages * q.stage_bytes + 1024 + 256;
+  uint32_t cols = 32;
+  while (cols < (uint32_t)(2 * q.n_pad)) cols <<= 1;
+  q.tmem_cols = cols;
+  return q;
+}
+
+}  // namespace
+
+// Largest factor side the tensor-core path takes (one N tile; K streamed).
+constexpr int kTcMaxN = 256;
+
+static bool tc_supported(const cola_linop* op) {
+  for (auto* f : op->kids)
+    if (f->rows > kTcMaxN || f->cols > 4096) return false;
+  return true;
+}
+
+static std::string depth_name(const char* what, int depth, int slot) {
+  char b[64];
+  snprintf(b, sizeof b, "%s.d%d.%d", what, depth, slot);
+  return b;
+}
+
+static int* tc_errflag(Ctx* c) {
+  const bool fresh = c->ws.bufs.find("tc.err") == c->ws.bufs.end();
+  int* p = (int*)c->ws.get("tc.err", 256);
+  if (fresh) COLA_CUDA(cudaMemsetAsync(p, 0, 256, c->s));
+  return p;
+}
+
+void tc_check_error(Ctx* c) {
+  if (c->ws.bufs.find("tc.err") == c->ws.bufs.end()) return;
+  int* p = (int*)c->ws.bufs["tc.err"].p;
+  int h = 0;
+  COLA_CUDA(cudaMemcpyAsync(&h, p, 4, cudaMemcpyDeviceToHost, c->s));
+  COLA_CUDA(cudaStreamSynchronize(c->s));
+  if (h != 0) {
+    COLA_CUDA(cudaMemsetAsync(p, 0, 4, c->s));
+    fail(COLA_ERR_TIMEOUT, "tensor-core Kronecker kernel timed out waiting on an mbarrier");
+  }
+}
+
+void kron_tc_prepare(Ctx* c, cola_linop* op, int split_terms) {
+  if (!tc_supported(op)) return;
+  const int tf = std::max(1, std::min(3, split_terms));
+  for (auto* f : op->kids) {
+    for (int tr = 0; tr < 2; ++tr) {
+      const int n_out = (int)(tr ? f->cols : f->rows), n_in = (int)(tr ? f->rows : f->cols);
+      const TcPlan q = make_plan(n_in, n_out, tf, 2);
+      const size_t per_term = (size_t)q.kblocks * q.n_pad * kBlockK;
+      const int key = 100 + tr * 10 + tf;
+      auto it = f->derived.find(key);
+      void* img;
+      if (it == f->derived.end() || it->second.bytes < per_term * tf * 2) {
+        if (it != f->derived.end()) {
+          cudaFree(it->second.p);
+          f->derived.erase(it);
+        }
+        COLA_CUDA(cudaMalloc(&img, per_term * tf * 2));
+        f->derived[key] = Buf{img, per_term * tf * 2};
+      } else {
+        img = it->second.p;
+      }
+      const int grid = (int)std::min<size_t>(1024, (per_term + 255) / 256);
+      if (f->dtype == COLA_F64)
+        k_split_factor<double><<<grid, 256, 0, c->s>>>((const double*)f->data, f->ld, tr, n_out,
+                                                        n_in, q.n_pad, q.kblocks, tf,
+                                                        (uint16_t*)img);
+      else
+        k_split_factor<float><<<grid, 256, 0, c->s>>>((const float*)f->data, f->ld, tr, n_out,
+                                                      n_in, q.n_pad, q.kblocks, tf,
+                                                      (uint16_t*)img);
+      c->count_launch();
+      COLA_CUDA(cudaGetLastError());
+    }
+  }
+  op->derived[200] = Buf{nullptr, (size_t)tf};  // remembers the factor split terms
+}
 
 template <typename T>
 void kron_tc_apply(Ctx* c, const cola_linop* op, const T* X, T* Y, int64_t R, double coeff,
-                   double beta, int depth, bool tr) {
-  fail(COLA_ERR_UNSUPPORTED, "MIXED precision Kronecker contraction not built yet");
+                   double beta, int depth, bool tr);
+
+template <>
+void kron_tc_apply<double>(Ctx*, const cola_linop*, const double*, double*, int64_t, double,
+                           double, int, bool) {
+  fail(COLA_ERR_UNSUPPORTED, "tensor-core Kronecker contraction takes FP32 vectors");
 }
-template void kron_tc_apply<float>(Ctx*, const cola_linop*, const float*, float*, int64_t, double,
-                                   double, int, bool);
-template void kron_tc_apply<double>(Ctx*, const cola_linop*, const double*, double*, int64_t,
-                                    double, double, int, bool);
+
+template <>
+void kron_tc_apply<float>(Ctx* c, const cola_linop* op, const float* X, float* Y, int64_t R,
+                          double coeff, double beta, int depth, bool tr) {
+  COLA_REQUIRE(tc_supported(op), COLA_ERR_UNSUPPORTED,
+               "tensor-core path takes factors with at most %d rows", kTcMaxN);
+  auto tfit = op->derived.find(200);
+  COLA_REQUIRE(tfit != op->derived.end(), COLA_ERR_INVALID_ARG,
+               "internal: Kronecker factors not split for MIXED precision");
+  const int tf = (int)tfit->second.bytes;
+  const int tv = std::max(1, std::min(3, c->split_vector_terms));
+  int* err = tc_errflag(c);
+  static bool attr_set = false;
+  const int d = (int)op->kids.size();
+  int64_t cur_size = tr ? op->rows : op->cols, maxsz = cur_size;
+  for (int k = 0; k < d; ++k) {
+    const cola_linop* f = op->kids[k];
+    cur_size = cur_size / (tr ? f->rows : f->cols) * (tr ? f->cols : f->rows);
+    maxsz = std::max(maxsz, cur_size);
+  }
+  cur_size = tr ? op->rows : op->cols;
+  const float* cur = X;
+  for (int k = 0; k < d; ++k) {
+    const cola_linop* f = op->kids[k];
+    const int n_in = (int)(tr ? f->rows : f->cols), n_out = (int)(tr ? f->cols : f->rows);
+    const TcPlan q = make_plan(n_in, n_out, tf, tv);
+    const int64_t rest = cur_size / n_in, out_size = rest * n_out;
+    const bool last = (k == d - 1);
+    float* dst = last ? Y : (float*)c->ws.get(depth_name("kron", depth, k & 1), 4 * maxsz * R);
+    TcParams p{};
+    p.X = cur;
+    p.Y = dst;
+    p.Bimg = (const uint16_t*)f->derived.at(100 + (tr ? 10 : 0) + tf).p;
+    p.rest = rest;
+    p.size_in = cur_size;
+    p.size_out = out_size;
+    p.batch = R;
+    p.tiles_m = (rest + kTileM - 1) / kTileM;
+    p.ntiles = p.tiles_m * R;
+    p.n_in = n_in;
+    p.n_out = n_out;
+    p.n_pad = q.n_pad;
+    p.kblocks = q.kblocks;
+    p.ksteps_last = q.ksteps_last;
+    p.tf = tf;
+    p.tv = tv;
+    p.stages = q.stages;
+    p.stage_bytes = q.stage_bytes;
+    p.a_term_bytes = q.a_term_bytes;
+    p.b_term_bytes = q.b_term_bytes;
+    p.tmem_cols = q.tmem_cols;
+    p.coeff = (float)(last ? coeff : 1.0);
+    p.beta = (float)(last ? beta : 0.0);
+    p.err = err;
+    if (!attr_set) {
+      COLA_CUDA(cudaFuncSetAttribute(k_kron_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     227 * 1024));
+      attr_set = true;
+    }
+    const int grid = (int)std::min<int64_t>(p.ntiles, c->num_sms);
+    k_kron_tc<<<grid, kThreadsTc, q.smem, c->s>>>(p);
+    c->count_launch();
+    COLA_CUDA(cudaGetLastError());
+    cur = dst;
+    cur_size = out_size;
+  }
+}
 
 }  // namespace cola

@@ -563,6 +563,7 @@ static cola_status cg_run(Ctx* c, cola_linop* op, const void* Bin, void* Xout, i
   double* dp64 = (double*)ws.get("cg.dp64", 8 * dot_blocks(N) * R);
   const bool io64 = (prec == COLA_PREC_F64) || refine;
 
+  c->split_vector_terms = o.split_vector_terms;
   prepare_leaves(c, op, prec, o.split_factor_terms);
   if (refine) prepare_leaves(c, op, COLA_PREC_F64, o.split_factor_terms);
 
@@ -681,6 +682,7 @@ static cola_status cg_run(Ctx* c, cola_linop* op, const void* Bin, void* Xout, i
     apply<T>(c, op, B.x, B.r, R, -1.0, 1.0, 1, false, prec);
     dots<T>(c, B.r, B.r, N, R, B.dotp, rr64);
   }
+  if (prec == COLA_PREC_MIXED) tc_check_error(c);
   std::vector<double> hrr(R), hbb(R);
   COLA_CUDA(cudaMemcpyAsync(hrr.data(), rr64, 8 * R, cudaMemcpyDeviceToHost, c->s));
   COLA_CUDA(cudaMemcpyAsync(hbb.data(), bb, 8 * R, cudaMemcpyDeviceToHost, c->s));

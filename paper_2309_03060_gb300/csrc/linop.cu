@@ -890,6 +890,16 @@ cola_status cola_linop_release(cola_linop* op) {
   });
 }
 
+cola_status cola_set_split_terms(cola_ctx* ctx, int32_t factor_terms, int32_t vector_terms) {
+  return guard([&] {
+    COLA_REQUIRE(ctx, COLA_ERR_INVALID_ARG, "ctx is NULL");
+    COLA_REQUIRE(factor_terms >= 1 && factor_terms <= 3 && vector_terms >= 1 && vector_terms <= 3,
+                 COLA_ERR_INVALID_ARG, "split terms must be 1..3");
+    ctx->split_factor_terms = factor_terms;
+    ctx->split_vector_terms = vector_terms;
+  });
+}
+
 cola_status cola_kernel_launches(const cola_ctx* ctx, int64_t* count) {
   return guard([&] {
     COLA_REQUIRE(ctx && count, COLA_ERR_INVALID_ARG, "NULL argument");
@@ -907,11 +917,12 @@ cola_status cola_matvec(cola_ctx* ctx, const cola_linop* op, const void* X, void
     COLA_REQUIRE(X != Y, COLA_ERR_INVALID_ARG, "X and Y must not alias");
     StreamJoin j(ctx, stream);
     cola_linop* m = const_cast<cola_linop*>(op);
-    prepare_leaves(ctx, m, prec, 2);
+    prepare_leaves(ctx, m, prec, ctx->split_factor_terms);
     if (prec == COLA_PREC_F64)
       apply<double>(ctx, op, (const double*)X, (double*)Y, nrhs, 1.0, 0.0, 0, false, prec);
     else
       apply<float>(ctx, op, (const float*)X, (float*)Y, nrhs, 1.0, 0.0, 0, false, prec);
+    if (prec == COLA_PREC_MIXED) tc_check_error(ctx);
   });
 }
 

@@ -230,22 +230,28 @@ def test_lanczos_matches_oracle(cola, ctx):
 
 
 def test_slq_config1_fp64(cola, ctx):
-    """16 probes x 50 steps on the N = 4096 workload: per-probe values equal the
-    oracle's SLQ on the same probes; the estimate is within 4 SE of the exact
-    log-det."""
+    """16 probes x 50 steps on the N = 4096 workload.  With full
+    reorthogonalisation on both sides the per-probe quadrature values match
+    the oracle's on the same probes to 1e-9; without it (the default), loss of
+    orthogonality amplifies reduction-order differences, so they agree to
+    1e-5.  The estimate lies within 4 SE of the exact log-det."""
     w = wl.config1()
     spec = ("sum", [("kron", [("dense", f) for f in w.factors]), ("scalar", w.shift, w.N)], None)
     op = gpu_tree(cola, ctx, spec, torch.float64, DEV).set_spd()
     seed = wl.substream(w.seed, 2)
+    Z = rng.rademacher_probes(seed, w.slq_probes, w.N)
+    ld_r, se_r, pp_r, cl = cola.cola_slq_logdet(ctx, op, w.slq_probes, w.slq_steps, seed=seed,
+                                                precision=cola.PREC_F64, reorth=True)
+    _, _, pp_ref_r = krylov.slq_logdet(oracle_tree(spec), Z, w.slq_steps, reorth=True)
+    np.testing.assert_allclose(pp_r.cpu().numpy(), pp_ref_r, rtol=1e-9)
     ld, se, pp, cl = cola.cola_slq_logdet(ctx, op, w.slq_probes, w.slq_steps, seed=seed,
                                           precision=cola.PREC_F64)
-    Z = rng.rademacher_probes(seed, w.slq_probes, w.N)
     ld_ref, se_ref, pp_ref = krylov.slq_logdet(oracle_tree(spec), Z, w.slq_steps, reorth=False)
-    np.testing.assert_allclose(pp.cpu().numpy(), pp_ref, rtol=1e-7)
+    np.testing.assert_allclose(pp.cpu().numpy(), pp_ref, rtol=1e-5)
     assert cl == 0
     exact_ld = exact.kron_shift_logdet(w.factors, w.shift)
     assert abs(ld - exact_ld) / se < 4.0
-    assert abs(ld - ld_ref) < 1e-7 * abs(ld_ref)
+    assert abs(ld_r - exact_ld) / se_r < 4.0
 
 
 def _grad_specs():
@@ -328,3 +334,70 @@ def test_batched_systems_uneven(cola, ctx):
     for p, X in zip(probs, Xs):
         res = krylov.true_relative_residual(oracle_tree(p[3]), p[2], X.cpu().numpy())
         assert np.all(res <= 1e-8)
+
+
+# ----------------------------------------------------------------- tensor cores
+# Split-BF16 contraction error: with T terms per operand the unrepresented
+# remainder is below 2^-(8T+1) of each entry and dropped cross terms are of
+# the same order, so per mode the error is < ~3 * 2^-(8T) of sum|K||x|.
+MIXED_TOL = {1: 2e-2, 2: 2e-4, 3: 3e-6}
+
+
+@pytest.mark.parametrize("name", ["kron_rect", "kron_shift"])
+@pytest.mark.parametrize("terms", [1, 2, 3])
+def test_matvec_mixed_parity(cola, ctx, name, terms):
+    spec = _zoo()[name]
+    ref = oracle_tree(spec)
+    op = gpu_tree(cola, ctx, spec, torch.float64, DEV)
+    X = _rs(6).standard_normal((3, ref.cols))
+    absop = oracle_tree(_abs_spec(spec))
+    scale = np.max(absop.mvm(np.abs(X)))
+    Y = cola.cola_matvec(ctx, op, torch.tensor(X, dtype=torch.float32, device=DEV),
+                         cola.PREC_MIXED, split_terms=terms)
+    err = float(np.max(np.abs(Y.double().cpu().numpy() - ref.mvm(X))))
+    assert err < MIXED_TOL[terms] * scale, (err / scale)
+
+
+def _abs_spec(spec):
+    k = spec[0]
+    if k in ("dense", "diag"):
+        return (k, np.abs(spec[1]))
+    if k == "scalar":
+        return (k, abs(spec[1]), spec[2])
+    if k == "lowrank":
+        return spec
+    if k in ("kron", "kronsum", "product"):
+        return (k, [_abs_spec(s) for s in spec[1]])
+    return (k, [_abs_spec(s) for s in spec[1]], spec[2])
+
+
+def test_matvec_mixed_kron3_full_size_sampled(cola, ctx):
+    w = wl.config2(nrhs=2)
+    spec = ("sum", [("kron", [("dense", f) for f in w.factors]), ("scalar", w.shift, w.N)], None)
+    op = gpu_tree(cola, ctx, spec, torch.float64, DEV)
+    X = torch.tensor(w.B, dtype=torch.float32, device=DEV)
+    Yh = cola.cola_matvec(ctx, op, X, cola.PREC_MIXED, split_terms=3).double().cpu().numpy()
+    K1, K2, K3 = w.factors
+    n = 128
+    idx = _rs(8).integers(0, w.N, size=40)
+    for r in range(2):
+        Xr = w.B[r].reshape(n, n, n)
+        for I in idx:
+            i1, i2, i3 = I // (n * n), (I // n) % n, I % n
+            row = np.einsum("a,b,c->abc", K1[i1], K2[i2], K3[i3])
+            ref = float(np.sum(row * Xr)) + w.shift * Xr[i1, i2, i3]
+            bound = float(np.sum(row * np.abs(Xr))) + w.shift * abs(Xr[i1, i2, i3])
+            assert abs(Yh[r, I] - ref) <= MIXED_TOL[3] * 3 * bound
+
+
+@pytest.mark.parametrize("terms", [2, 3])
+def test_cg_mixed_reaches_1e8(cola, ctx, terms):
+    K1, K2, B, spec = _kron_shift_problem(64, 96, 0.01, 4, 15)
+    op = gpu_tree(cola, ctx, spec, torch.float64, DEV).set_spd()
+    opts = cola.cola_cg_opts_default(precision=cola.PREC_MIXED, refine=1, tol=1e-8,
+                                     maxiter=20000, split_factor_terms=terms,
+                                     split_vector_terms=terms)
+    X, info, st = cola.cola_cg_solve(ctx, op, torch.tensor(B, device=DEV), opts)
+    assert st == 0, info
+    res = krylov.true_relative_residual(oracle_tree(spec), B, X.cpu().numpy())
+    assert np.all(res <= 1e-8), res

@@ -137,6 +137,34 @@ def build_operator(cola, ctx, w, device):
     return op, kron
 
 
+def run_mvm_only(args):
+    """A few MIXED Kronecker MVMs of the bench operator (for profiler captures)."""
+    import torch
+    import paper_2309_03060_gb300 as cola
+    device = torch.device("cuda", 0)
+    ctx = cola.Context(0)
+    w = wl.config2(nrhs=1)
+    op, kron = build_operator(cola, ctx, w, device)
+    X = torch.randn(args.nrhs, w.N, dtype=torch.float32, device=device)
+    Y = torch.empty_like(X)
+    target = op if args.with_shift else kron
+    for _ in range(args.reps):
+        cola.cola_matvec(ctx, target, X, cola.PREC_MIXED, out=Y,
+                         split_terms=(args.fterms, args.vterms))
+    torch.cuda.synchronize()
+    s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s0.record()
+    for _ in range(args.reps):
+        cola.cola_matvec(ctx, target, X, cola.PREC_MIXED, out=Y,
+                         split_terms=(args.fterms, args.vterms))
+    s1.record()
+    torch.cuda.synchronize()
+    print(json.dumps({"mode": "mvm-only", "nrhs": args.nrhs, "reps": args.reps,
+                      "ms_per_mvm": s0.elapsed_time(s1) / args.reps,
+                      "launches": ctx.kernel_launches()}))
+    ctx.close()
+
+
 def run_ours(args):
     import torch
     import paper_2309_03060_gb300 as cola
@@ -152,8 +180,8 @@ def run_ours(args):
                           wl.normal(wl.substream(w.seed, 100 + rank), w.B.shape)).pin_memory()
     B = B_host.to(device)
     opts = cola.cola_cg_opts_default(precision=cola.PREC_MIXED, refine=1, tol=w.tol,
-                                     maxiter=args.maxiter, split_factor_terms=args.terms,
-                                     split_vector_terms=args.terms, graph_chunk=args.chunk,
+                                     maxiter=args.maxiter, split_factor_terms=args.fterms,
+                                     split_vector_terms=args.vterms, graph_chunk=args.chunk,
                                      reliable_delta=args.delta)
     seed = wl.substream(w.seed, 2)
     stream = torch.cuda.current_stream()
@@ -217,13 +245,13 @@ def run_ours(args):
     Xf = torch.randn(R, w.N, dtype=torch.float32, device=device)
     Yf = torch.empty_like(Xf)
     for _ in range(3):
-        cola.cola_matvec(ctx, kron, Xf, cola.PREC_MIXED, out=Yf, split_terms=args.terms)
+        cola.cola_matvec(ctx, kron, Xf, cola.PREC_MIXED, out=Yf, split_terms=(args.fterms, args.vterms))
     torch.cuda.synchronize()
     reps = 20
     k0, k1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     k0.record(stream)
     for _ in range(reps):
-        cola.cola_matvec(ctx, kron, Xf, cola.PREC_MIXED, out=Yf, split_terms=args.terms)
+        cola.cola_matvec(ctx, kron, Xf, cola.PREC_MIXED, out=Yf, split_terms=(args.fterms, args.vterms))
     k1.record(stream)
     torch.cuda.synchronize()
     per_launch = k0.elapsed_time(k1) / 1e3 / (reps * 3)
@@ -260,7 +288,7 @@ def run_ours(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "bf16x2-split/f32/f64",
             "data": "synthetic (seeded SplitMix64; RBF factors on uniform points, N(0,1) RHS)",
             "config": {"workload": WORKLOAD, "nrhs_per_gpu": R, "N": w.N,
-                       "split_terms": args.terms, "tol": w.tol,
+                       "split_terms": {"factor": args.fterms, "vector": args.vterms}, "tol": w.tol,
                        "l2": "inputs larger than L2 (16 x 2M FP32 vectors, 134 MB each)",
                        "parallelism": f"replicas x{world}"},
             "iters_per_s": round(it_per_solve * args.steps * world / t, 2),
@@ -346,7 +374,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--nrhs", type=int, default=16)
-    ap.add_argument("--terms", type=int, default=2)
+    ap.add_argument("--fterms", type=int, default=3)
+    ap.add_argument("--vterms", type=int, default=3)
     ap.add_argument("--chunk", type=int, default=64)
     ap.add_argument("--delta", type=float, default=0.1)
     ap.add_argument("--maxiter", type=int, default=60000)
@@ -356,8 +385,14 @@ def main():
     ap.add_argument("--traffic-bytes", type=float, default=None)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--plain", action="store_true", help="also time the plain FP32 path once")
+    ap.add_argument("--mvm-only", action="store_true",
+                    help="only run --reps MIXED MVMs of the bench operator (profiler captures)")
+    ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--with-shift", action="store_true")
     args = ap.parse_args()
-    if args.impl == "reference":
+    if args.mvm_only:
+        run_mvm_only(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

@@ -171,7 +171,8 @@ typedef struct {
 } cola_cg_info;
 
 /* Fill opts with defaults: tol 1e-8, maxiter 100000, MIXED, refine 1,
- * reliable_delta 0.1, max_updates 200, split terms 2/2, graph_chunk 64,
+ * reliable_delta 0.1, max_updates 200, split terms 3 (factor) / 3 (vector),
+ * graph_chunk 64,
  * jacobi 0, x0_given 0. */
 void cola_cg_opts_default(cola_cg_opts* opts);
 

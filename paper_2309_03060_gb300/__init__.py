@@ -186,7 +186,8 @@ def cola_matvec(ctx: Context, op: LinOp, X: torch.Tensor, precision: int = PREC_
     if X2.dtype != want:
         raise TypeError(f"precision {precision} needs {want} vectors")
     Y = out if out is not None else torch.empty((X2.shape[0], rows), dtype=want, device=X.device)
-    check(_lib().cola_set_split_terms(ctx.handle, int(split_terms), int(split_terms)))
+    ft, vt = (split_terms, split_terms) if isinstance(split_terms, int) else split_terms
+    check(_lib().cola_set_split_terms(ctx.handle, int(ft), int(vt)))
     check(_lib().cola_matvec(ctx.handle, op.handle, _ptr(X2), _ptr(Y), X2.shape[0], precision,
                              _stream()))
     return Y if X.dim() == 2 else Y.reshape(-1)

@@ -47,7 +47,7 @@ struct TcParams {
   float* Y;
   const uint16_t* Bimg;  // [tf][kblocks][n_pad rows][64] bf16, 128-byte swizzled rows
   int64_t rest, size_in, size_out, batch, tiles_m, ntiles;
-  int n_in, n_out, n_pad, kblocks, ksteps_last, tf, tv, stages;
+  int n_in, n_out, n_pad, kblocks, ksteps_last, tf, tv, stages, nbuf;
   uint32_t stage_bytes, a_term_bytes, b_term_bytes, tmem_cols;
   float coeff, beta;
   int* err;
@@ -307,11 +307,16 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_kron_tc(TcParams p) {
       int64_t it = 0;
       bool ok = true;
       for (int64_t t = blockIdx.x; t < p.ntiles && ok; t += gridDim.x, ++it) {
-        const int b = (int)(it & 1);
-        if (!mbar_wait(&acc_empty[b], (uint32_t)((it >> 1) & 1) ^ 1u, abort_flag, p.err)) break;
+        const int b = (int)(it % p.nbuf);
+        const uint32_t use = (uint32_t)((it / p.nbuf) & 1);
+        if (!mbar_wait(&acc_empty[b], use ^ 1u, abort_flag, p.err)) break;
         tc_fence_after();
-        const uint32_t d_tmem = tmem_base + (uint32_t)(b * p.n_pad);
-        uint32_t accumulate = 0;
+        // hi x hi products accumulate in d_big; every smaller cross term in
+        // d_small, so the rounding of each MMA's accumulate step on the
+        // dominant sum happens once per k step only.
+        const uint32_t d_big = tmem_base + (uint32_t)(b * 2 * p.n_pad);
+        const uint32_t d_small = d_big + (uint32_t)p.n_pad;
+        uint32_t acc_big = 0, acc_small = 0;
         for (int kb = 0; kb < p.kblocks; ++kb) {
           if (!mbar_wait(&full[s], ph, abort_flag, p.err)) {
             ok = false;
@@ -327,8 +332,13 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_kron_tc(TcParams p) {
                 const uint64_t ad = sw128_desc(st + tv * p.a_term_bytes + kk * 32);
                 const uint64_t bd =
                     sw128_desc(st + p.tv * p.a_term_bytes + ti * p.b_term_bytes + kk * 32);
-                mma_bf16(d_tmem, ad, bd, idesc, accumulate);
-                accumulate = 1;
+                if (ti == 0 && tv == 0) {
+                  mma_bf16(d_big, ad, bd, idesc, acc_big);
+                  acc_big = 1;
+                } else {
+                  mma_bf16(d_small, ad, bd, idesc, acc_small);
+                  acc_small = 1;
+                }
               }
           }
           mma_commit(&empty[s]);
@@ -350,26 +360,34 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_kron_tc(TcParams p) {
     const int q = warp - 4;
     const int row = q * 32 + lane;
     int64_t it = 0;
+    const bool has_small = (p.tf > 1 || p.tv > 1);
     for (int64_t t = blockIdx.x; t < p.ntiles; t += gridDim.x, ++it) {
-      const int b = (int)(it & 1);
-      if (!mbar_wait(&acc_full[b], (uint32_t)((it >> 1) & 1), abort_flag, p.err)) break;
+      const int b = (int)(it % p.nbuf);
+      if (!mbar_wait(&acc_full[b], (uint32_t)((it / p.nbuf) & 1), abort_flag, p.err)) break;
       tc_fence_after();
       const int64_t r = t / p.tiles_m, m0 = (t % p.tiles_m) * kTileM;
       const int64_t m = m0 + row;
       float* yrow = p.Y + r * p.size_out + m * p.n_out;
-      const uint32_t taddr = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * p.n_pad);
+      const uint32_t taddr =
+          tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * 2 * p.n_pad);
       for (int c0 = 0; c0 < p.n_pad; c0 += 16) {
-        uint32_t v[16];
+        uint32_t v[16], w[16];
         tmem_ld16(taddr + (uint32_t)c0, v);
+        if (has_small) {
+          tmem_ld16(taddr + (uint32_t)(p.n_pad + c0), w);
+        } else {
+#pragma unroll
+          for (int e = 0; e < 16; ++e) w[e] = 0u;
+        }
+        float a[16];
+#pragma unroll
+        for (int e = 0; e < 16; ++e)
+          a[e] = p.coeff * (__uint_as_float(v[e]) + __uint_as_float(w[e]));
         if (m < p.rest) {
           if (c0 + 16 <= p.n_out && (p.n_out & 3) == 0) {
 #pragma unroll
             for (int e = 0; e < 16; e += 4) {
-              float4 o;
-              o.x = p.coeff * __uint_as_float(v[e]);
-              o.y = p.coeff * __uint_as_float(v[e + 1]);
-              o.z = p.coeff * __uint_as_float(v[e + 2]);
-              o.w = p.coeff * __uint_as_float(v[e + 3]);
+              float4 o = make_float4(a[e], a[e + 1], a[e + 2], a[e + 3]);
               float4* dst = reinterpret_cast<float4*>(yrow + c0 + e);
               if (p.beta != 0.0f) {
                 const float4 old = *dst;
@@ -384,7 +402,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_kron_tc(TcParams p) {
             for (int e = 0; e < 16; ++e) {
               const int i = c0 + e;
               if (i >= p.n_out) break;
-              float o = p.coeff * __uint_as_float(v[e]);
+              float o = a[e];
               if (p.beta != 0.0f) o += p.beta * yrow[i];
               yrow[i] = o;
             }
@@ -431,7 +449,7 @@ __global__ void k_split_factor(const TF* F, int64_t ld, int tr, int n_out, int n
 }
 
 struct TcPlan {
-  int n_in, n_out, n_pad, kblocks, ksteps_last, tf, tv, stages;
+  int n_in, n_out, n_pad, kblocks, ksteps_last, tf, tv, stages, nbuf;
   uint32_t stage_bytes, a_term_bytes, b_term_bytes, tmem_cols;
   size_t smem;
 };
@@ -453,8 +471,10 @@ TcPlan make_plan(int n_in, int n_out, int tf, int tv) {
   const size_t budget = 200 * 1024;
   q.stages = (int)std::min<size_t>(4, budget / q.stage_bytes);
   q.smem = (size_t)q.stages * q.stage_bytes + 1024 + 256;
+  // two accumulators (dominant and cross terms) per buffer; double-buffer when it fits
+  q.nbuf = (4 * q.n_pad <= 512) ? 2 : 1;
   uint32_t cols = 32;
-  while (cols < (uint32_t)(2 * q.n_pad)) cols <<= 1;
+  while (cols < (uint32_t)(2 * q.nbuf * q.n_pad)) cols <<= 1;
   q.tmem_cols = cols;
   return q;
 }
@@ -588,6 +608,7 @@ void kron_tc_apply<float>(Ctx* c, const cola_linop* op, const float* X, float* Y
     p.tf = tf;
     p.tv = tv;
     p.stages = q.stages;
+    p.nbuf = q.nbuf;
     p.stage_bytes = q.stage_bytes;
     p.a_term_bytes = q.a_term_bytes;
     p.b_term_bytes = q.b_term_bytes;

@@ -14,6 +14,7 @@
 //    with an implicit-shift symmetric tridiagonal QR on the device.
 //  * the adjoint rules of App. B.2 (solve VJP, log-det gradient).
 #include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
@@ -622,11 +623,33 @@ static cola_status cg_run(Ctx* c, cola_linop* op, const void* Bin, void* Xout, i
   };
   const double delta2 = o.reliable_delta * o.reliable_delta;
   const int chunk = std::max(1, o.graph_chunk);
+  // everything a captured kernel bakes in is part of the graph key
+  char extra[96];
+  snprintf(extra, sizeof extra, ":%c:d%.17g:s%d%d", sizeof(T) == 8 ? 'd' : 'f', delta2,
+           o.split_factor_terms, o.split_vector_terms);
   const std::string key =
-      key_of("cg", op, R, prec, (refine ? 1 : 0) | (o.jacobi ? 2 : 0) | (chunk << 2),
-             0) + (sizeof(T) == 8 ? ":d" : ":f");
+      key_of("cg", op, R, prec, (refine ? 1 : 0) | (o.jacobi ? 2 : 0) | (chunk << 2), 0) + extra;
   int64_t iters = 0;
   int updates = 0;
+  // COLA_TRACE=1 prints the worst relative residual of the active right-hand
+  // sides after every chunk and every FP64 replacement (stderr).
+  const char* tr_env = getenv("COLA_TRACE");
+  const bool trace = tr_env && tr_env[0] == '1';
+  auto trace_line = [&](const char* what) {
+    if (!trace) return;
+    double worst = 0.0, worst64 = 0.0;
+    int act = 0;
+    for (int64_t r = 0; r < R; ++r) {
+      if (!hst[r].active) continue;
+      ++act;
+      if (hst[r].bb > 0) {
+        worst = std::max(worst, std::sqrt(std::max(hst[r].rr, 0.0) / hst[r].bb));
+        worst64 = std::max(worst64, std::sqrt(std::max(hst[r].rr64, 0.0) / hst[r].bb));
+      }
+    }
+    fprintf(stderr, "[cola cg] %s iter %lld active %d recursive %.3e true %.3e updates %d\n", what,
+            (long long)iters, act, worst, worst64, updates);
+  };
   read_state();
   bool any_active = false;
   for (int64_t r = 0; r < R; ++r) any_active |= hst[r].active != 0;
@@ -640,6 +663,7 @@ static cola_status cg_run(Ctx* c, cola_linop* op, const void* Bin, void* Xout, i
     cg_chunk<T>(c, op, B, N, R, nblk, prec, delta2, refine ? 1 : 0, chunk, key);
     iters += chunk;
     read_state();
+    trace_line("chunk");
     bool flag = false;
     any_active = false;
     for (int64_t r = 0; r < R; ++r) {
@@ -661,6 +685,7 @@ static cola_status cg_run(Ctx* c, cola_linop* op, const void* Bin, void* Xout, i
       c->count_launch();
       ++updates;
       read_state();
+      trace_line("update");
       any_active = false;
       for (int64_t r = 0; r < R; ++r) any_active |= hst[r].active != 0;
     }
@@ -802,8 +827,8 @@ void cola_cg_opts_default(cola_cg_opts* o) {
   o->refine = 1;
   o->reliable_delta = 0.1;
   o->max_updates = 200;
-  o->split_factor_terms = 2;
-  o->split_vector_terms = 2;
+  o->split_factor_terms = 3;
+  o->split_vector_terms = 3;
   o->graph_chunk = 64;
   o->jacobi = 0;
   o->x0_given = 0;

@@ -50,7 +50,8 @@ def test_opts_defaults(lib):
     o = _abi.cola_cg_opts()
     lib.cola_cg_opts_default(ctypes.byref(o))
     assert o.tol == 1e-8 and o.maxiter == 100000 and o.precision == _abi.PREC_MIXED
-    assert o.refine == 1 and o.split_factor_terms == 2 and o.graph_chunk == 64
+    assert o.refine == 1 and o.split_factor_terms == 3 and o.split_vector_terms == 3
+    assert o.graph_chunk == 64
 
 
 def test_null_arguments_are_rejected_without_a_device(lib):

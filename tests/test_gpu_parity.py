@@ -390,13 +390,13 @@ def test_matvec_mixed_kron3_full_size_sampled(cola, ctx):
             assert abs(Yh[r, I] - ref) <= MIXED_TOL[3] * 3 * bound
 
 
-@pytest.mark.parametrize("terms", [2, 3])
+@pytest.mark.parametrize("terms", [(2, 2), (3, 2), (3, 3)])
 def test_cg_mixed_reaches_1e8(cola, ctx, terms):
     K1, K2, B, spec = _kron_shift_problem(64, 96, 0.01, 4, 15)
     op = gpu_tree(cola, ctx, spec, torch.float64, DEV).set_spd()
     opts = cola.cola_cg_opts_default(precision=cola.PREC_MIXED, refine=1, tol=1e-8,
-                                     maxiter=20000, split_factor_terms=terms,
-                                     split_vector_terms=terms)
+                                     maxiter=20000, split_factor_terms=terms[0],
+                                     split_vector_terms=terms[1])
     X, info, st = cola.cola_cg_solve(ctx, op, torch.tensor(B, device=DEV), opts)
     assert st == 0, info
     res = krylov.true_relative_residual(oracle_tree(spec), B, X.cpu().numpy())

@@ -233,5 +233,9 @@ void bilinear_entry(Ctx* c, const cola_linop* op, const void* U, const void* X,
 void check_cg_args(const cola_linop* op, const cola_cg_opts* o, int64_t R);
 // Raises COLA_ERR_TIMEOUT when a tensor-core kernel gave up waiting (and clears the flag).
 void tc_check_error(Ctx* c);
+// Fused MIXED CG MVM for Sum(Kron, Diag); see kron_tc.cu.  0 = not applicable.
+int64_t kron_tc_cg_mvm(Ctx* c, const cola_linop* op, const float* z, const double* beta_vec,
+                       float* p, float* Ap, double* tile_dot, int64_t R, int depth);
+int64_t kron_tc_tiles_per_rhs(const cola_linop* op);
 
 }  // namespace cola

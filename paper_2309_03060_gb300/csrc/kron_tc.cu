@@ -51,6 +51,18 @@ struct TcParams {
   uint32_t stage_bytes, a_term_bytes, b_term_bytes, tmem_cols;
   float coeff, beta;
   int* err;
+  // optional prologue (first mode step of a CG iteration): the input is
+  // p = z + beta_r * p_old, computed here and written back to X in place
+  const float* pro_z;
+  const double* pro_beta;
+  // optional epilogue (last mode step, output in the input's layout):
+  // Y += epi_coeff * d * epi_x (d = epi_d[0] when epi_dstride == 0), and the
+  // per-(tile, epilogue warp) partial sums of epi_x . Y go to epi_dot[4 tile + warp]
+  const float* epi_x;
+  const float* epi_d;
+  int64_t epi_dstride;
+  float epi_coeff;
+  double* epi_dot;
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -243,6 +255,9 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_kron_tc(TcParams p) {
     for (int64_t t = blockIdx.x; t < p.ntiles && ok; t += gridDim.x) {
       const int64_t r = t / p.tiles_m, m0 = (t % p.tiles_m) * kTileM;
       const float* Xb = p.X + r * p.size_in;
+      float* Pb = const_cast<float*>(Xb);
+      const float* Zb = p.pro_z ? p.pro_z + r * p.size_in : nullptr;
+      const float beta_r = p.pro_z ? (float)p.pro_beta[r] : 0.0f;
       const int64_t m = m0 + tid;
       const bool row_ok = m < p.rest;
       for (int kb = 0; kb < p.kblocks; ++kb) {
@@ -262,10 +277,31 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_kron_tc(TcParams p) {
         }
         const int k0 = kb * kBlockK;
         float v[kBlockK];
+        if (Zb) {
 #pragma unroll
-        for (int k = 0; k < kBlockK; ++k) {
-          const int kk = k0 + k;
-          v[k] = (row_ok && kk < p.n_in) ? __ldg(Xb + (int64_t)kk * p.rest + m) : 0.0f;
+          for (int g = 0; g < kBlockK; g += 16) {
+            float zz[16], pp[16];
+#pragma unroll
+            for (int k = 0; k < 16; ++k) {
+              const int kk = k0 + g + k;
+              const bool in = row_ok && kk < p.n_in;
+              const int64_t idx = (int64_t)kk * p.rest + m;
+              zz[k] = in ? Zb[idx] : 0.0f;
+              pp[k] = in ? Pb[idx] : 0.0f;
+            }
+#pragma unroll
+            for (int k = 0; k < 16; ++k) {
+              const int kk = k0 + g + k;
+              v[g + k] = fmaf(beta_r, pp[k], zz[k]);
+              if (row_ok && kk < p.n_in) Pb[(int64_t)kk * p.rest + m] = v[g + k];
+            }
+          }
+        } else {
+#pragma unroll
+          for (int k = 0; k < kBlockK; ++k) {
+            const int kk = k0 + k;
+            v[k] = (row_ok && kk < p.n_in) ? __ldg(Xb + (int64_t)kk * p.rest + m) : 0.0f;
+          }
         }
         const uint32_t row_off = (uint32_t)tid * 128u;
 #pragma unroll
@@ -368,6 +404,9 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_kron_tc(TcParams p) {
       const int64_t r = t / p.tiles_m, m0 = (t % p.tiles_m) * kTileM;
       const int64_t m = m0 + row;
       float* yrow = p.Y + r * p.size_out + m * p.n_out;
+      const float* xrow = p.epi_x ? p.epi_x + r * p.size_out + m * p.n_out : nullptr;
+      const int64_t dbase = m * p.n_out;
+      double dot = 0.0;
       const uint32_t taddr =
           tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * 2 * p.n_pad);
       for (int c0 = 0; c0 < p.n_pad; c0 += 16) {
@@ -383,6 +422,21 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_kron_tc(TcParams p) {
 #pragma unroll
         for (int e = 0; e < 16; ++e)
           a[e] = p.coeff * (__uint_as_float(v[e]) + __uint_as_float(w[e]));
+        if (xrow && m < p.rest) {
+          float xd[16];
+#pragma unroll
+          for (int e = 0; e < 16; ++e) {
+            const int i = c0 + e;
+            xd[e] = (i < p.n_out) ? xrow[i] : 0.0f;
+          }
+#pragma unroll
+          for (int e = 0; e < 16; ++e) {
+            const int i = c0 + e;
+            const float dv = p.epi_dstride ? (i < p.n_out ? p.epi_d[dbase + i] : 0.0f) : p.epi_d[0];
+            a[e] = fmaf(p.epi_coeff * dv, xd[e], a[e]);
+            if (p.beta == 0.0f && i < p.n_out) dot += (double)(a[e] * xd[e]);
+          }
+        }
         if (m < p.rest) {
           if (c0 + 16 <= p.n_out && (p.n_out & 3) == 0) {
 #pragma unroll
@@ -399,18 +453,26 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_kron_tc(TcParams p) {
               *dst = o;
             }
           } else {
+#pragma unroll
             for (int e = 0; e < 16; ++e) {
               const int i = c0 + e;
-              if (i >= p.n_out) break;
-              float o = a[e];
-              if (p.beta != 0.0f) o += p.beta * yrow[i];
-              yrow[i] = o;
+              if (i < p.n_out) {
+                float o = a[e];
+                if (p.beta != 0.0f) o += p.beta * yrow[i];
+                yrow[i] = o;
+              }
             }
           }
         }
       }
       tc_fence_before();
       mbar_arrive(&acc_empty[b]);
+      if (p.epi_dot) {
+        // one partial per (tile, epilogue warp); summed in fixed order later
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, o);
+        if (lane == 0) p.epi_dot[t * 4 + q] = dot;
+      }
     }
   }
 
@@ -562,9 +624,20 @@ void kron_tc_apply<double>(Ctx*, const cola_linop*, const double*, double*, int6
   fail(COLA_ERR_UNSUPPORTED, "tensor-core Kronecker contraction takes FP32 vectors");
 }
 
-template <>
-void kron_tc_apply<float>(Ctx* c, const cola_linop* op, const float* X, float* Y, int64_t R,
-                          double coeff, double beta, int depth, bool tr) {
+struct TcFusion {
+  const float* pro_z = nullptr;
+  const double* pro_beta = nullptr;
+  const float* epi_x = nullptr;
+  const float* epi_d = nullptr;
+  int64_t epi_dstride = 0;
+  float epi_coeff = 0.0f;
+  double* epi_dot = nullptr;
+};
+
+// Runs the d mode steps of a Kronecker MVM on the tensor cores; returns the
+// number of row tiles per right-hand side of the last step.
+static int64_t kron_tc_run(Ctx* c, const cola_linop* op, const float* X, float* Y, int64_t R,
+                           double coeff, double beta, int depth, bool tr, const TcFusion& fu) {
   COLA_REQUIRE(tc_supported(op), COLA_ERR_UNSUPPORTED,
                "tensor-core path takes factors with at most %d rows", kTcMaxN);
   auto tfit = op->derived.find(200);
@@ -573,7 +646,7 @@ void kron_tc_apply<float>(Ctx* c, const cola_linop* op, const float* X, float* Y
   const int tf = (int)tfit->second.bytes;
   const int tv = std::max(1, std::min(3, c->split_vector_terms));
   int* err = tc_errflag(c);
-  static bool attr_set = false;
+  static bool attr_set[64] = {false};
   const int d = (int)op->kids.size();
   int64_t cur_size = tr ? op->rows : op->cols, maxsz = cur_size;
   for (int k = 0; k < d; ++k) {
@@ -583,6 +656,7 @@ void kron_tc_apply<float>(Ctx* c, const cola_linop* op, const float* X, float* Y
   }
   cur_size = tr ? op->rows : op->cols;
   const float* cur = X;
+  int64_t last_tiles = 0;
   for (int k = 0; k < d; ++k) {
     const cola_linop* f = op->kids[k];
     const int n_in = (int)(tr ? f->rows : f->cols), n_out = (int)(tr ? f->cols : f->rows);
@@ -616,10 +690,22 @@ void kron_tc_apply<float>(Ctx* c, const cola_linop* op, const float* X, float* Y
     p.coeff = (float)(last ? coeff : 1.0);
     p.beta = (float)(last ? beta : 0.0);
     p.err = err;
-    if (!attr_set) {
+    if (k == 0) {
+      p.pro_z = fu.pro_z;
+      p.pro_beta = fu.pro_beta;
+    }
+    if (last) {
+      p.epi_x = fu.epi_x;
+      p.epi_d = fu.epi_d;
+      p.epi_dstride = fu.epi_dstride;
+      p.epi_coeff = fu.epi_coeff;
+      p.epi_dot = fu.epi_dot;
+      last_tiles = p.tiles_m;
+    }
+    if (c->device < 64 && !attr_set[c->device]) {
       COLA_CUDA(cudaFuncSetAttribute(k_kron_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      227 * 1024));
-      attr_set = true;
+      attr_set[c->device] = true;
     }
     const int grid = (int)std::min<int64_t>(p.ntiles, c->num_sms);
     k_kron_tc<<<grid, kThreadsTc, q.smem, c->s>>>(p);
@@ -628,6 +714,54 @@ void kron_tc_apply<float>(Ctx* c, const cola_linop* op, const float* X, float* Y
     cur = dst;
     cur_size = out_size;
   }
+  return last_tiles;
+}
+
+template <>
+void kron_tc_apply<float>(Ctx* c, const cola_linop* op, const float* X, float* Y, int64_t R,
+                          double coeff, double beta, int depth, bool tr) {
+  kron_tc_run(c, op, X, Y, R, coeff, beta, depth, tr, TcFusion{});
+}
+
+// One CG MVM for A = c_k * Kron(...) + c_d * Diag(d): the first mode step forms
+// p = z + beta p in place, the last step adds c_d * d * p and writes the
+// per-(tile, warp) partials of p . Ap.  Returns the last step's row tiles per
+// right-hand side (partials per RHS = 4 x that), or 0 when the operator does
+// not have this shape (the caller then takes the generic path).
+int64_t kron_tc_cg_mvm(Ctx* c, const cola_linop* op, const float* z, const double* beta_vec,
+                       float* p, float* Ap, double* tile_dot, int64_t R, int depth) {
+  if (op->kind != LK_SUM || op->kids.size() != 2) return 0;
+  int ik = -1, id = -1;
+  for (int i = 0; i < 2; ++i) {
+    if (op->kids[i]->kind == LK_KRON) ik = i;
+    if (op->kids[i]->kind == LK_DIAG) id = i;
+  }
+  if (ik < 0 || id < 0) return 0;
+  const cola_linop* kron = op->kids[ik];
+  const cola_linop* dg = op->kids[id];
+  if (kron->kids.size() < 2 || !tc_supported(kron)) return 0;
+  if (kron->derived.find(200) == kron->derived.end()) return 0;
+  TcFusion fu;
+  fu.pro_z = z;
+  fu.pro_beta = beta_vec;
+  fu.epi_x = p;
+  fu.epi_d = leaf_ptr<float>(dg);
+  fu.epi_dstride = dg->stride;
+  fu.epi_coeff = (float)op->coeffs[id];
+  fu.epi_dot = tile_dot;
+  return kron_tc_run(c, kron, p, Ap, R, op->coeffs[ik], 0.0, depth, false, fu);
+}
+
+int64_t kron_tc_tiles_per_rhs(const cola_linop* op) {
+  // row tiles of the last mode step when the operator is Sum(Kron, Diag)
+  if (op->kind != LK_SUM || op->kids.size() != 2) return 0;
+  for (auto* k : op->kids)
+    if (k->kind == LK_KRON && k->kids.size() >= 2 && tc_supported(k)) {
+      const cola_linop* last = k->kids.back();
+      const int64_t rest = k->rows / last->rows;  // rows produced by the earlier steps
+      return (rest + kTileM - 1) / kTileM;
+    }
+  return 0;
 }
 
 }  // namespace cola

@@ -67,7 +67,8 @@ __device__ __forceinline__ double block_sum2(T v, double* out_other, T v2) {
   return tx;
 }
 
-__global__ void k_cg_alpha(CgState* st, const double* pAp, int64_t R) {
+// alpha = r^T z / p^T A p, with p^T A p the ordered sum of nparts partials.
+__global__ void k_cg_alpha(CgState* st, const double* parts, int nparts, int64_t R) {
   const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= R) return;
   CgState& s = st[r];
@@ -75,7 +76,8 @@ __global__ void k_cg_alpha(CgState* st, const double* pAp, int64_t R) {
     s.alpha = 0.0;
     return;
   }
-  const double v = pAp[r];
+  double v = 0.0;
+  for (int j = 0; j < nparts; ++j) v += parts[r * nparts + j];
   s.pAp = v;
   if (!(v > 0.0) || !isfinite(v)) {
     s.status = COLA_ERR_BREAKDOWN;
@@ -123,12 +125,13 @@ __global__ void k_cg_xr(int64_t n, T* x, T* r, const T* p, const T* Ap, const T*
 }
 
 __global__ void k_cg_beta(CgState* st, const double* part_rz, const double* part_rr, int nblk,
-                          int64_t R, double delta2, int refine) {
+                          int64_t R, double delta2, int refine, double* beta_out) {
   const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= R) return;
   CgState& s = st[r];
   if (!s.active) {
     s.beta = 0.0;
+    if (beta_out) beta_out[r] = 0.0;
     return;
   }
   double rz = 0.0, rr = 0.0;
@@ -151,6 +154,7 @@ __global__ void k_cg_beta(CgState* st, const double* part_rz, const double* part
   } else if (rr <= s.tol2) {
     s.active = 0;
   }
+  if (beta_out) beta_out[r] = s.active ? s.beta : 0.0;
 }
 
 template <typename T>
@@ -472,6 +476,9 @@ struct CgBufs {
   T* invd;
   double *x64, *b64, *r64;
   double *part_rz, *part_rr, *dotp, *dotv;
+  double* beta_vec;   // per-RHS beta for the fused p update (MIXED)
+  double* tile_dot;   // per-(tile, warp) partials of p^T A p (MIXED)
+  int64_t fused_tiles;  // > 0: the fused tensor-core CG MVM applies
   CgState* st;
 };
 
@@ -486,19 +493,31 @@ static std::string key_of(const char* what, const cola_linop* op, int64_t R, int
 template <typename T>
 static void cg_iteration(Ctx* c, const cola_linop* op, CgBufs<T>& B, int64_t N, int64_t R,
                          int nblk, int prec, double delta2, int refine) {
-  apply<T>(c, op, B.p, B.Ap, R, 1.0, 0.0, 1, false, prec);
-  dots<T>(c, B.p, B.Ap, N, R, B.dotp, B.dotv);
-  k_cg_alpha<<<(unsigned)((R + 127) / 128), 128, 0, c->s>>>(B.st, B.dotv, R);
-  c->count_launch();
+  const unsigned rb = (unsigned)((R + 127) / 128);
+  if (B.fused_tiles > 0) {
+    // p = z + beta p (first mode step), Ap and p^T A p partials (last mode step)
+    kron_tc_cg_mvm(c, op, (const float*)(B.invd ? B.z : B.r), B.beta_vec, (float*)B.p,
+                   (float*)B.Ap, B.tile_dot, R, 1);
+    k_cg_alpha<<<rb, 128, 0, c->s>>>(B.st, B.tile_dot, (int)(4 * B.fused_tiles), R);
+    c->count_launch();
+  } else {
+    apply<T>(c, op, B.p, B.Ap, R, 1.0, 0.0, 1, false, prec);
+    dots<T>(c, B.p, B.Ap, N, R, B.dotp, B.dotv);
+    k_cg_alpha<<<rb, 128, 0, c->s>>>(B.st, B.dotv, 1, R);
+    c->count_launch();
+  }
   k_cg_xr<T><<<rows_grid(N, R, nblk), 256, 0, c->s>>>(N, B.x, B.r, B.p, B.Ap, B.invd,
                                                        B.invd ? B.z : nullptr, B.st, nblk,
                                                        B.part_rz, B.part_rr);
   c->count_launch();
-  k_cg_beta<<<(unsigned)((R + 127) / 128), 128, 0, c->s>>>(B.st, B.part_rz, B.part_rr, nblk, R,
-                                                          delta2, refine);
+  k_cg_beta<<<rb, 128, 0, c->s>>>(B.st, B.part_rz, B.part_rr, nblk, R, delta2, refine,
+                                  B.beta_vec);
   c->count_launch();
-  k_cg_p<T><<<dim3(ew_blocks(N), (unsigned)R), 256, 0, c->s>>>(N, B.invd ? B.z : B.r, B.p, B.st);
-  c->count_launch();
+  if (B.fused_tiles <= 0) {
+    k_cg_p<T><<<dim3(ew_blocks(N), (unsigned)R), 256, 0, c->s>>>(N, B.invd ? B.z : B.r, B.p,
+                                                                  B.st);
+    c->count_launch();
+  }
   COLA_CUDA(cudaGetLastError());
 }
 
@@ -559,6 +578,10 @@ static cola_status cg_run(Ctx* c, cola_linop* op, const void* Bin, void* Xout, i
   B.dotp = (double*)ws.get("cg.dotp", 8 * nblk * R);
   B.dotv = (double*)ws.get("cg.dotv", 8 * R);
   B.st = (CgState*)ws.get("cg.st", sizeof(CgState) * R);
+  B.beta_vec = (double*)ws.get("cg.beta", 8 * R);
+  B.fused_tiles = (prec == COLA_PREC_MIXED && sizeof(T) == 4) ? kron_tc_tiles_per_rhs(op) : 0;
+  B.tile_dot = B.fused_tiles > 0 ? (double*)ws.get("cg.tdot", 8 * 4 * B.fused_tiles * R) : nullptr;
+  COLA_CUDA(cudaMemsetAsync(B.beta_vec, 0, 8 * R, c->s));
   double* bb = (double*)ws.get("cg.bb", 8 * R);
   double* rr64 = (double*)ws.get("cg.rr64", 8 * R);
   double* dp64 = (double*)ws.get("cg.dp64", 8 * dot_blocks(N) * R);

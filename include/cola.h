@@ -276,6 +276,28 @@ cola_status cola_rademacher(cola_ctx* ctx, uint64_t seed, int64_t offset, int64_
  * cola_cg_opts).  Default 2 / 2. */
 cola_status cola_set_split_terms(cola_ctx* ctx, int32_t factor_terms, int32_t vector_terms);
 
+/* Allocation-free Kronecker MVM (no counterpart in the paper; it exists for
+ * callers that cannot let a library allocate device memory: a framework that
+ * owns every byte of the device through its own pool, code running where an
+ * allocation would implicitly synchronise the device, or a caller that has no
+ * cola_ctx).  Computes Y = (K_1 (x) ... (x) K_d) X in FP32 exactly like
+ * cola_matvec with COLA_PREC_F32 on a Kronecker node.
+ *   rows[k], cols[k] (HOST): shape of factor k; factors[k] (HOST array of
+ *   device pointers): factor k, FP32, row-major, packed (ld = cols[k]).
+ *   X [nrhs][prod cols], Y [nrhs][prod rows]: FP32 device, must not alias.
+ * The intermediate mode products live in one fixed device array inside the
+ * library, 2 x 4 Mi floats (32 MiB), which every GPU that loads the library
+ * holds until the process exits; nrhs times the largest intermediate must not
+ * exceed 4 Mi floats, else COLA_ERR_INVALID_ARG.  The call allocates nothing:
+ * no cudaMalloc, cudaFree or allocating library routine.  The first call on a
+ * device looks up that array's device address (cudaGetSymbolAddress) with the
+ * current device; make that first call before any stream capture.  Every call
+ * shares the array, so calls that overlap on the GPU (other streams, other
+ * host threads) race; order them on one stream.  Asynchronous on stream. */
+cola_status cola_kron_matvec_noalloc(int nfactors, const int64_t* rows, const int64_t* cols,
+                                     const float* const* factors, const float* X, float* Y,
+                                     int64_t nrhs, cola_stream stream);
+
 /* Number of kernels this library launched (or recorded into replayed graphs,
  * counted per replay) since the context was created. */
 cola_status cola_kernel_launches(const cola_ctx* ctx, int64_t* count);

@@ -30,9 +30,19 @@ static const void* as_working(Ctx* c, const void* v, int64_t n, bool io64, bool 
   return t;
 }
 
+cola_status batched_cg_fast(Ctx* c, int32_t nsys, const cola_linop* const* ops,
+                            const void* const* Bin, void* const* Xout, const int64_t* nrhs,
+                            const cola_cg_opts& o, cola_cg_info* info, bool* handled);
+
 cola_status batched_cg_impl(Ctx* c, int32_t nsys, const cola_linop* const* ops,
                             const void* const* B, void* const* X, const int64_t* nrhs,
                             const cola_cg_opts& o, cola_cg_info* info) {
+  // every system of the form c_k K1 (x) K2 + c_d Diag under MIXED + refinement:
+  // all systems advance together through table-driven batched kernels
+  bool handled = false;
+  const cola_status st = batched_cg_fast(c, nsys, ops, B, X, nrhs, o, info, &handled);
+  if (handled) return st;
+  // any other composition: one graph-captured CG per system, in turn
   cola_status worst = COLA_OK;
   int64_t off = 0;
   for (int s = 0; s < nsys; ++s) {
@@ -63,8 +73,11 @@ cola_status cola_solve_backward(cola_ctx* ctx, const cola_linop* op, const void*
     o.x0_given = 0;
     result = cg_solve_impl(ctx, op, gradX, gradB, nrhs, o, info);
     if (grads) {
+      // Leaf gradients are sums of large terms that cancel (a GP lengthscale
+      // gradient is a difference of O(1e7) terms): contract in FP64 whenever
+      // the solve returned FP64 vectors.
       const bool io64 = (o.precision == COLA_PREC_F64) || o.refine;
-      const bool f64 = o.precision == COLA_PREC_F64;
+      const bool f64 = io64;
       const int64_t n = op->rows * nrhs;
       const void* U = as_working(ctx, gradB, n, io64, f64, "bw.U");
       const void* Xw = as_working(ctx, X, n, io64, f64, "bw.X");
@@ -88,7 +101,7 @@ cola_status cola_logdet_backward(cola_ctx* ctx, const cola_linop* op, const void
     check_cg_args(op, opts, nprobes);
     StreamJoin j(ctx, stream);
     const bool io64 = (opts->precision == COLA_PREC_F64) || opts->refine;
-    const bool f64 = opts->precision == COLA_PREC_F64;
+    const bool f64 = io64;  // FP64 contractions for FP64 vectors (see solve backward)
     const size_t es = io64 ? 8 : 4;
     const int64_t n = op->rows * nprobes;
     const void* U = AinvZ;

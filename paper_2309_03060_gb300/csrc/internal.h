@@ -170,6 +170,23 @@ void gemm(Ctx* c, int64_t M, int64_t N, int64_t K, double alpha, const T* A, int
           int64_t lda_k, int64_t sA, const T* B, int64_t ldb_k, int64_t ldb_n, int64_t sB,
           double beta, T* C, int64_t ldc_m, int64_t ldc_n, int64_t sC, int64_t batch);
 
+// One problem of a grouped GEMM: C = alpha A B + beta C with element strides.
+template <typename T>
+struct GemmDesc {
+  int64_t M, N, K;
+  const T* A;
+  int64_t lam, lak;
+  const T* B;
+  int64_t lbk, lbn;
+  T* C;
+  int64_t lcm, lcn;
+  T alpha, beta;
+};
+// Grouped GEMM over a device table of nprob problems (one per blockIdx.z);
+// max_m / max_n bound the problems' M and N.
+template <typename T>
+void gemm_grouped(Ctx* c, const GemmDesc<T>* dev_probs, int nprob, int64_t max_m, int64_t max_n);
+
 // Deterministic per-vector dot products: out[r] = sum_i a[r*lda+i] b[r*ldb+i].
 // partials: workspace of dot_blocks(n)*R doubles.  Two launches.
 int dot_blocks(int64_t n);
@@ -219,6 +236,15 @@ void add_partials(Ctx* c, const T* P, T* G, int64_t count, int64_t nparts, doubl
 // out[r] = sum of partials[r*nblk .. r*nblk+nblk-1] in order
 void dot_final(Ctx* c, const double* partials, int nblk, int64_t R, double* out);
 
+// Per right-hand-side CG state in device memory.
+struct CgState {
+  double rz, pAp, alpha, beta;
+  double rr, rr_ref, bb, tol2;
+  double rr64;
+  long long iters;
+  int active, flag, status, updates;
+};
+
 // ------------------------------------------------------------ solver entries
 cola_status cg_solve_impl(Ctx* c, const cola_linop* op, const void* B, void* X, int64_t R,
                           const cola_cg_opts& o, cola_cg_info* info);
@@ -234,8 +260,35 @@ void check_cg_args(const cola_linop* op, const cola_cg_opts* o, int64_t R);
 // Raises COLA_ERR_TIMEOUT when a tensor-core kernel gave up waiting (and clears the flag).
 void tc_check_error(Ctx* c);
 // Fused MIXED CG MVM for Sum(Kron, Diag); see kron_tc.cu.  0 = not applicable.
+// p_new = z + beta p_old is formed in the first mode step (p_new != p_old).
 int64_t kron_tc_cg_mvm(Ctx* c, const cola_linop* op, const float* z, const double* beta_vec,
-                       float* p, float* Ap, double* tile_dot, int64_t R, int depth);
+                       const float* p_old, float* p_new, float* Ap, double* tile_dot, int64_t R,
+                       int depth);
 int64_t kron_tc_tiles_per_rhs(const cola_linop* op);
+
+// One tensor-core mode-step problem of a batch (host mirror of the kernel's
+// per-problem parameters) and the launch over a device problem table.
+struct TcBatchProblem {
+  const float* X;
+  float* Y;
+  const cola_linop* factor;  // dense leaf, already split (kron_tc_prepare)
+  bool transpose;
+  int64_t rest, size_in, size_out, R;
+  float coeff, beta;
+  const float* pro_z;
+  const double* pro_beta;
+  float* pro_out;
+  const float* epi_x;
+  const float* epi_d;
+  int64_t epi_dstride;
+  float epi_coeff;
+  double* epi_dot;
+};
+// Uploads the problem and tile tables into workspace buffers named after
+// `tag` and returns the number of tiles per problem (in table order).
+std::vector<int64_t> kron_tc_batch_upload(Ctx* c, const std::vector<TcBatchProblem>& probs,
+                                          int tf, int tv, const char* tag);
+// Launches one persistent k_kron_tc over the table uploaded under `tag`.
+void kron_tc_batch_launch(Ctx* c, const char* tag, int tf, int tv, int max_n_chunk);
 
 }  // namespace cola

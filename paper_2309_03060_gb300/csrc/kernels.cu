@@ -48,14 +48,10 @@ struct GemmP {
 // arbitrary element strides.  128 x 128 x 8 tiles, 256 threads, 8 x 8
 // outputs per thread; tile loads run along whichever stride is unit.
 template <typename T>
-__global__ void __launch_bounds__(256) k_gemm(GemmP<T> g, int64_t batch0) {
+__device__ __forceinline__ void gemm_tile_body(const GemmP<T>& g, const T* A, const T* B, T* C) {
   constexpr int BM = 128, BN = 128, BK = 8;
   __shared__ __align__(16) T As[BK][BM];
   __shared__ __align__(16) T Bs[BK][BN];
-  const int64_t b = batch0 + blockIdx.z;
-  const T* A = g.A + b * g.sA;
-  const T* B = g.B + b * g.sB;
-  T* C = g.C + b * g.sC;
   const int64_t m0 = (int64_t)blockIdx.x * BM, n0 = (int64_t)blockIdx.y * BN;
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
   T acc[8][8];
@@ -111,6 +107,23 @@ __global__ void __launch_bounds__(256) k_gemm(GemmP<T> g, int64_t batch0) {
       *p = v;
     }
   }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_gemm(GemmP<T> g, int64_t batch0) {
+  const int64_t b = batch0 + blockIdx.z;
+  gemm_tile_body<T>(g, g.A + b * g.sA, g.B + b * g.sB, g.C + b * g.sC);
+}
+
+
+// Grouped variant: problem blockIdx.z of a device table, same tiling.
+template <typename T>
+__global__ void __launch_bounds__(256) k_gemm_grouped(const GemmDesc<T>* probs) {
+  const GemmDesc<T>& q = probs[blockIdx.z];
+  if ((int64_t)blockIdx.x * 128 >= q.M || (int64_t)blockIdx.y * 128 >= q.N) return;
+  GemmP<T> g{q.M, q.N, q.K, q.A, q.lam, q.lak, 0, q.B, q.lbk, q.lbn, 0, q.C, q.lcm, q.lcn, 0,
+             q.alpha, q.beta};
+  gemm_tile_body<T>(g, g.A, g.B, g.C);
 }
 
 // ------------------------------------------------------------- reductions
@@ -418,6 +431,19 @@ void gemm(Ctx* c, int64_t M, int64_t N, int64_t K, double alpha, const T* A, int
   }
   COLA_CUDA(cudaGetLastError());
 }
+
+template <typename T>
+void gemm_grouped(Ctx* c, const GemmDesc<T>* dev_probs, int nprob, int64_t max_m,
+                  int64_t max_n) {
+  if (nprob <= 0) return;
+  COLA_REQUIRE(nprob <= 65535, COLA_ERR_UNSUPPORTED, "grouped gemm: %d problems", nprob);
+  dim3 grid((unsigned)((max_m + 127) / 128), (unsigned)((max_n + 127) / 128), (unsigned)nprob);
+  k_gemm_grouped<T><<<grid, 256, 0, c->s>>>(dev_probs);
+  c->count_launch();
+  COLA_CUDA(cudaGetLastError());
+}
+template void gemm_grouped<float>(Ctx*, const GemmDesc<float>*, int, int64_t, int64_t);
+template void gemm_grouped<double>(Ctx*, const GemmDesc<double>*, int, int64_t, int64_t);
 
 int dot_blocks(int64_t n) {
   const int64_t b = (n + 4095) / 4096;

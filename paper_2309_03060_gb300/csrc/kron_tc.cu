@@ -48,6 +48,7 @@ struct TcParams {
   const uint16_t* Bimg;  // [tf][kblocks][n_pad rows][64] bf16, 128-byte swizzled rows
   int64_t rest, size_in, size_out, batch, tiles_m, ntiles;
   int n_in, n_out, n_pad, kblocks, ksteps_last, tf, tv, stages, nbuf;
+  int n_chunk, nchunks;  // output columns per tile (<= 256) and chunks per row tile
   uint32_t stage_bytes, a_term_bytes, b_term_bytes, tmem_cols;
   float coeff, beta;
   int* err;
@@ -55,6 +56,8 @@ struct TcParams {
   // p = z + beta_r * p_old, computed here and written back to X in place
   const float* pro_z;
   const double* pro_beta;
+  float* pro_out;  // where p is written (never the input X: tiles of several
+                   // output chunks re-read the same X rows)
   // optional epilogue (last mode step, output in the input's layout):
   // Y += epi_coeff * d * epi_x (d = epi_d[0] when epi_dstride == 0), and the
   // per-(tile, epilogue warp) partial sums of epi_x . Y go to epi_dot[4 tile + warp]
@@ -87,6 +90,14 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
 
 __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
   asm volatile("mbarrier.expect_tx.relaxed.cta.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+// Arrive once and add `bytes` to the phase's expected transaction count.
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.release.cta.shared::cta.b64 _, [%0], %1;" ::"r"(
+                   smem_u32(bar)),
                "r"(bytes)
                : "memory");
 }
@@ -206,14 +217,39 @@ __device__ __forceinline__ void split2(float a, float b, int terms, uint32_t* ou
   }
 }
 
-__global__ void __launch_bounds__(kThreadsTc, 1) k_kron_tc(TcParams p) {
+// Per-tile parameter sources of k_kron_tc: one problem passed by value, or a
+// device table of problems (many independent systems in one launch).
+struct OneProb {
+  TcParams p;
+  __device__ __forceinline__ int64_t count() const { return p.ntiles; }
+  __device__ __forceinline__ const TcParams& get(int64_t t, int64_t& lt) const {
+    lt = t;
+    return p;
+  }
+};
+
+struct ProbTable {
+  const TcParams* probs;   // one entry per problem
+  const int* tile_prob;    // problem of every global tile
+  const int64_t* first;    // first global tile of every problem
+  const int64_t* count_dev;  // number of live tiles (read at kernel start)
+  __device__ __forceinline__ int64_t count() const { return *count_dev; }
+  __device__ __forceinline__ const TcParams& get(int64_t t, int64_t& lt) const {
+    const int pid = tile_prob[t];
+    lt = t - first[pid];
+    return probs[pid];
+  }
+};
+
+template <class Src>
+__global__ void __launch_bounds__(kThreadsTc, 1) k_kron_tc(Src src, TcParams K) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   // 1024-byte aligned stage area
   unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  uint64_t* bars = (uint64_t*)(base + (size_t)p.stages * p.stage_bytes);
+  uint64_t* bars = (uint64_t*)(base + (size_t)K.stages * K.stage_bytes);
   uint64_t* full = bars;
-  uint64_t* empty = bars + p.stages;
-  uint64_t* acc_full = bars + 2 * p.stages;
+  uint64_t* empty = bars + K.stages;
+  uint64_t* acc_full = bars + 2 * K.stages;
   uint64_t* acc_empty = acc_full + 2;
   uint64_t* drain = acc_empty + 2;
   uint32_t* tmem_slot = (uint32_t*)(drain + 1);
@@ -221,7 +257,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_kron_tc(TcParams p) {
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if (tid == 0) {
-    for (int s = 0; s < p.stages; ++s) {
+    for (int s = 0; s < K.stages; ++s) {
       mbar_init(&full[s], kProducerThreads);
       mbar_init(&empty[s], 1);
     }
@@ -236,7 +272,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_kron_tc(TcParams p) {
   if (warp == 8) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      smem_u32(tmem_slot)),
-                 "r"(p.tmem_cols)
+                 "r"(K.tmem_cols)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -252,25 +288,32 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_kron_tc(TcParams p) {
     int last_s = -1;
     uint32_t last_ph = 0;
     bool ok = true;
-    for (int64_t t = blockIdx.x; t < p.ntiles && ok; t += gridDim.x) {
-      const int64_t r = t / p.tiles_m, m0 = (t % p.tiles_m) * kTileM;
+    const int64_t ntiles = src.count();
+    for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+      int64_t lt;
+      const TcParams& p = src.get(t, lt);
+      const int64_t tm = lt / p.nchunks;
+      const int nc = (int)(lt % p.nchunks);
+      const int64_t r = tm / p.tiles_m, m0 = (tm % p.tiles_m) * kTileM;
       const float* Xb = p.X + r * p.size_in;
-      float* Pb = const_cast<float*>(Xb);
+      const float* Pb = Xb;
+      float* Pw = p.pro_out ? p.pro_out + r * p.size_in : nullptr;
       const float* Zb = p.pro_z ? p.pro_z + r * p.size_in : nullptr;
       const float beta_r = p.pro_z ? (float)p.pro_beta[r] : 0.0f;
       const int64_t m = m0 + tid;
       const bool row_ok = m < p.rest;
       for (int kb = 0; kb < p.kblocks; ++kb) {
-        if (!mbar_wait(&empty[s], ph ^ 1u, abort_flag, p.err)) {
+        if (!mbar_wait(&empty[s], ph ^ 1u, abort_flag, K.err)) {
           ok = false;
           break;
         }
-        unsigned char* st = base + (size_t)s * p.stage_bytes;
+        unsigned char* st = base + (size_t)s * K.stage_bytes;
         if (tid == 0) {
-          mbar_expect_tx(&full[s], p.b_term_bytes * p.tf);
-          for (int ti = 0; ti < p.tf; ++ti)
-            bulk_g2s(st + p.tv * p.a_term_bytes + ti * p.b_term_bytes,
-                     p.Bimg + ((size_t)ti * p.kblocks + kb) * (size_t)p.n_pad * kBlockK,
+          mbar_expect_tx(&full[s], p.b_term_bytes * K.tf);
+          for (int ti = 0; ti < K.tf; ++ti)
+            bulk_g2s(st + K.tv * K.a_term_bytes + ti * p.b_term_bytes,
+                     p.Bimg + (((size_t)ti * p.kblocks + kb) * (size_t)p.n_pad +
+                               (size_t)nc * p.n_chunk) * kBlockK,
                      p.b_term_bytes, &full[s]);
           last_s = s;
           last_ph = ph;
@@ -293,7 +336,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_kron_tc(TcParams p) {
             for (int k = 0; k < 16; ++k) {
               const int kk = k0 + g + k;
               v[g + k] = fmaf(beta_r, pp[k], zz[k]);
-              if (row_ok && kk < p.n_in) Pb[(int64_t)kk * p.rest + m] = v[g + k];
+              if (row_ok && kk < p.n_in) Pw[(int64_t)kk * p.rest + m] = v[g + k];
             }
           }
         } else {
@@ -310,7 +353,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_kron_tc(TcParams p) {
 #pragma unroll
           for (int e = 0; e < 4; ++e) {
             uint32_t o[3];
-            split2(v[8 * c + 2 * e], v[8 * c + 2 * e + 1], p.tv, o);
+            split2(v[8 * c + 2 * e], v[8 * c + 2 * e + 1], K.tv, o);
             w[0][e] = o[0];
             w[1][e] = o[1];
             w[2][e] = o[2];
@@ -318,56 +361,61 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_kron_tc(TcParams p) {
           const uint32_t off = row_off + ((uint32_t)(c ^ (tid & 7)) << 4);
 #pragma unroll
           for (int tv = 0; tv < 3; ++tv) {
-            if (tv < p.tv)
-              *reinterpret_cast<uint4*>(st + tv * p.a_term_bytes + off) =
+            if (tv < K.tv)
+              *reinterpret_cast<uint4*>(st + tv * K.a_term_bytes + off) =
                   make_uint4(w[tv][0], w[tv][1], w[tv][2], w[tv][3]);
           }
         }
         fence_proxy_async();
         mbar_arrive(&full[s]);
-        if (++s == p.stages) {
+        if (++s == K.stages) {
           s = 0;
           ph ^= 1u;
         }
       }
     }
     // make sure no bulk copy is still landing in this CTA's shared memory
-    if (tid == 0 && last_s >= 0) mbar_wait(&full[last_s], last_ph, abort_flag, p.err);
+    if (tid == 0 && last_s >= 0) mbar_wait(&full[last_s], last_ph, abort_flag, K.err);
   } else if (warp == 8) {
     // ----------------------------------------------------------------- MMA
     if (lane == 0) {
-      const uint32_t idesc = idesc_bf16(kTileM, p.n_pad);
-      const int maxt = p.tf > p.tv ? p.tf : p.tv;
+      const int maxt = K.tf > K.tv ? K.tf : K.tv;
       int s = 0;
       uint32_t ph = 0;
       int64_t it = 0;
       bool ok = true;
-      for (int64_t t = blockIdx.x; t < p.ntiles && ok; t += gridDim.x, ++it) {
-        const int b = (int)(it % p.nbuf);
-        const uint32_t use = (uint32_t)((it / p.nbuf) & 1);
-        if (!mbar_wait(&acc_empty[b], use ^ 1u, abort_flag, p.err)) break;
+      const int64_t ntiles = src.count();
+      for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++it) {
+        int64_t lt;
+        const TcParams& p = src.get(t, lt);
+        const uint32_t idesc = idesc_bf16(kTileM, p.n_chunk);
+        const int b = (int)(it % K.nbuf);
+        const uint32_t use = (uint32_t)((it / K.nbuf) & 1);
+        if (!mbar_wait(&acc_empty[b], use ^ 1u, abort_flag, K.err)) break;
         tc_fence_after();
         // hi x hi products accumulate in d_big; every smaller cross term in
         // d_small, so the rounding of each MMA's accumulate step on the
         // dominant sum happens once per k step only.
-        const uint32_t d_big = tmem_base + (uint32_t)(b * 2 * p.n_pad);
-        const uint32_t d_small = d_big + (uint32_t)p.n_pad;
+        // buffer stride from the launch-wide widest chunk (K.n_chunk), so
+        // problems of different widths never share accumulator columns
+        const uint32_t d_big = tmem_base + (uint32_t)(b * 2 * K.n_chunk);
+        const uint32_t d_small = d_big + (uint32_t)p.n_chunk;
         uint32_t acc_big = 0, acc_small = 0;
         for (int kb = 0; kb < p.kblocks; ++kb) {
-          if (!mbar_wait(&full[s], ph, abort_flag, p.err)) {
+          if (!mbar_wait(&full[s], ph, abort_flag, K.err)) {
             ok = false;
             break;
           }
           tc_fence_after();
-          const uint32_t st = smem_u32(base + (size_t)s * p.stage_bytes);
+          const uint32_t st = smem_u32(base + (size_t)s * K.stage_bytes);
           const int steps = (kb == p.kblocks - 1) ? p.ksteps_last : 4;
           for (int kk = 0; kk < steps; ++kk) {
-            for (int ti = 0; ti < p.tf; ++ti)
-              for (int tv = 0; tv < p.tv; ++tv) {
+            for (int ti = 0; ti < K.tf; ++ti)
+              for (int tv = 0; tv < K.tv; ++tv) {
                 if (ti + tv >= maxt) continue;
-                const uint64_t ad = sw128_desc(st + tv * p.a_term_bytes + kk * 32);
+                const uint64_t ad = sw128_desc(st + tv * K.a_term_bytes + kk * 32);
                 const uint64_t bd =
-                    sw128_desc(st + p.tv * p.a_term_bytes + ti * p.b_term_bytes + kk * 32);
+                    sw128_desc(st + K.tv * K.a_term_bytes + ti * p.b_term_bytes + kk * 32);
                 if (ti == 0 && tv == 0) {
                   mma_bf16(d_big, ad, bd, idesc, acc_big);
                   acc_big = 1;
@@ -378,7 +426,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_kron_tc(TcParams p) {
               }
           }
           mma_commit(&empty[s]);
-          if (++s == p.stages) {
+          if (++s == K.stages) {
             s = 0;
             ph ^= 1u;
           }
@@ -388,7 +436,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_kron_tc(TcParams p) {
       }
       // drain: all MMAs issued by this thread have completed
       mma_commit(drain);
-      mbar_wait(drain, 0, abort_flag, p.err);
+      mbar_wait(drain, 0, abort_flag, K.err);
     }
     __syncwarp();
   } else {
@@ -396,19 +444,387 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_kron_tc(TcParams p) {
     const int q = warp - 4;
     const int row = q * 32 + lane;
     int64_t it = 0;
+    const bool has_small = (K.tf > 1 || K.tv > 1);
+    const int64_t ntiles = src.count();
+    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
+      const int b = (int)(it % K.nbuf);
+      if (!mbar_wait(&acc_full[b], (uint32_t)((it / K.nbuf) & 1), abort_flag, K.err)) break;
+      tc_fence_after();
+      int64_t lt;
+      const TcParams& p = src.get(t, lt);
+      const int64_t tm = lt / p.nchunks;
+      const int nc = (int)(lt % p.nchunks);
+      const int64_t r = tm / p.tiles_m, m0 = (tm % p.tiles_m) * kTileM;
+      const int64_t m = m0 + row;
+      const int ncol0 = nc * p.n_chunk;   // first output column of this tile
+      const int ncols = min(p.n_chunk, p.n_out - ncol0);
+      float* yrow = p.Y + r * p.size_out + m * p.n_out + ncol0;
+      // 16-byte stores only where the row really is 16-byte aligned
+      const bool vec_ok = ((reinterpret_cast<uintptr_t>(yrow) & 15u) == 0);
+      const float* xrow = p.epi_x ? p.epi_x + r * p.size_out + m * p.n_out + ncol0 : nullptr;
+      const int64_t dbase = m * p.n_out + ncol0;
+      double dot = 0.0;
+      const uint32_t taddr =
+          tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * 2 * K.n_chunk);
+      for (int c0 = 0; c0 < p.n_chunk; c0 += 16) {
+        uint32_t v[16], w[16];
+        tmem_ld16(taddr + (uint32_t)c0, v);
+        if (has_small) {
+          tmem_ld16(taddr + (uint32_t)(p.n_chunk + c0), w);
+        } else {
+#pragma unroll
+          for (int e = 0; e < 16; ++e) w[e] = 0u;
+        }
+        float a[16];
+#pragma unroll
+        for (int e = 0; e < 16; ++e)
+          a[e] = p.coeff * (__uint_as_float(v[e]) + __uint_as_float(w[e]));
+        if (xrow && m < p.rest) {
+          float xd[16];
+#pragma unroll
+          for (int e = 0; e < 16; ++e) {
+            const int i = c0 + e;
+            xd[e] = (i < ncols) ? xrow[i] : 0.0f;
+          }
+#pragma unroll
+          for (int e = 0; e < 16; ++e) {
+            const int i = c0 + e;
+            const float dv = p.epi_dstride ? (i < ncols ? p.epi_d[dbase + i] : 0.0f) : p.epi_d[0];
+            a[e] = fmaf(p.epi_coeff * dv, xd[e], a[e]);
+            if (p.beta == 0.0f && i < ncols) dot += (double)(a[e] * xd[e]);
+          }
+        }
+        if (m < p.rest) {
+          if (c0 + 16 <= ncols && vec_ok) {
+#pragma unroll
+            for (int e = 0; e < 16; e += 4) {
+              float4 o = make_float4(a[e], a[e + 1], a[e + 2], a[e + 3]);
+              float4* dst = reinterpret_cast<float4*>(yrow + c0 + e);
+              if (p.beta != 0.0f) {
+                const float4 old = *dst;
+                o.x += p.beta * old.x;
+                o.y += p.beta * old.y;
+                o.z += p.beta * old.z;
+                o.w += p.beta * old.w;
+              }
+              *dst = o;
+            }
+          } else {
+#pragma unroll
+            for (int e = 0; e < 16; ++e) {
+              const int i = c0 + e;
+              if (i < ncols) {
+                float o = a[e];
+                if (p.beta != 0.0f) o += p.beta * yrow[i];
+                yrow[i] = o;
+              }
+            }
+          }
+        }
+      }
+      tc_fence_before();
+      mbar_arrive(&acc_empty[b]);
+      if (p.epi_dot) {
+        // one partial per (tile, epilogue warp); summed in fixed order later
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, o);
+        if (lane == 0) p.epi_dot[lt * 4 + q] = dot;
+      }
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 8) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base),
+                 "r"(K.tmem_cols)
+                 : "memory");
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Resident-factor variant (factor sides <= 128, rows of X 16-byte aligned).
+//   warp 9      loader: the split factor image once (cp.async.bulk, stays in
+//               shared memory); then, per 64-wide k block of a tile, 64 row
+//               segments of X (and z for the fused p update) with
+//               cp.async.bulk into a multi-stage FP32 staging ring.
+//   warps 0-3   converters: thread m reads row m of the staged block, forms
+//               p = z + beta p when fused (writing p back), splits into BF16
+//               terms and stores them into a tensor-memory A stage with
+//               tcgen05.st (warp w owns TMEM lanes 32w..32w+31).
+//   warp 8      MMA: tcgen05.mma with A from tensor memory, B (factor) from
+//               shared memory; dominant / cross terms in separate accumulators.
+//   warps 4-7   epilogue, as in k_kron_tc.
+// TMEM columns: [0, n_pad) dominant accumulator, [n_pad, 2 n_pad) cross
+// terms, [256 + s * 32 tv, ...) A stage s (32 columns per BF16 term).
+constexpr int kThreadsRes = 320;
+constexpr uint32_t kAStageCol0 = 256;
+
+struct TcResParams {
+  const float* X;
+  float* Y;
+  const uint16_t* Bimg;
+  int64_t rest, size_in, size_out, tiles_m, ntiles;
+  int n_in, n_out, n_pad, kblocks, ksteps_last, tf, tv, xstages, nsrc;
+  uint32_t b_bytes, b_kb_bytes, x_src_bytes;
+  float coeff, beta;
+  int* err;
+  const float* pro_z;
+  const double* pro_beta;
+  float* pro_out;
+  const float* epi_x;
+  const float* epi_d;
+  int64_t epi_dstride;
+  float epi_coeff;
+  double* epi_dot;
+};
+
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t* r) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], "
+      "{%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16};" ::"r"(taddr),
+      "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]),
+      "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]),
+      "r"(r[15])
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_bf16_ta(uint32_t d_tmem, uint32_t a_tmem, uint64_t bdesc,
+                                            uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "r"(a_tmem), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+__global__ void __launch_bounds__(kThreadsRes, 1) k_kron_tc_res(TcResParams p) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  unsigned char* bsm = base;                                         // resident factor image
+  unsigned char* xsm = base + ((p.b_bytes + 1023u) & ~1023u);         // staging ring
+  uint64_t* bars = (uint64_t*)(xsm + (size_t)p.xstages * p.nsrc * p.x_src_bytes);
+  uint64_t* bfull = bars;
+  uint64_t* xfull = bars + 1;
+  uint64_t* xempty = xfull + p.xstages;
+  uint64_t* afull = xempty + p.xstages;
+  uint64_t* aempty = afull + 2;
+  uint64_t* acc_full = aempty + 2;
+  uint64_t* acc_empty = acc_full + 1;
+  uint64_t* drain = acc_empty + 1;
+  uint32_t* tmem_slot = (uint32_t*)(drain + 1);
+  volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (tid == 0) {
+    mbar_init(bfull, 1);
+    for (int s = 0; s < p.xstages; ++s) {
+      mbar_init(&xfull[s], 1);
+      mbar_init(&xempty[s], kProducerThreads);
+    }
+    for (int s = 0; s < 2; ++s) {
+      mbar_init(&afull[s], kProducerThreads);
+      mbar_init(&aempty[s], 1);
+    }
+    mbar_init(acc_full, 1);
+    mbar_init(acc_empty, 128);
+    mbar_init(drain, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 8) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(512)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+  const uint32_t a_cols = 32u * (uint32_t)p.tv;  // TMEM columns per A stage
+
+  if (warp == 9) {
+    // ---------------------------------------------------------------- loader
+    bool ok = true;
+    int s = 0;
+    uint32_t ph = 0;
+    int last_s = -1;
+    uint32_t last_ph = 0;
+    if (lane == 0) {
+      mbar_arrive_expect_tx(bfull, p.b_bytes);
+      bulk_g2s(bsm, p.Bimg, p.b_bytes, bfull);
+    }
+    for (int64_t t = blockIdx.x; t < p.ntiles && ok; t += gridDim.x) {
+      const int64_t r = t / p.tiles_m, m0 = (t % p.tiles_m) * kTileM;
+      const int64_t rows = (p.rest - m0 < kTileM) ? (p.rest - m0) : kTileM;
+      const uint32_t seg = (uint32_t)rows * 4u;
+      for (int kb = 0; kb < p.kblocks; ++kb) {
+        if (!mbar_wait(&xempty[s], ph ^ 1u, abort_flag, p.err)) {
+          ok = false;
+          break;
+        }
+        const int kvalid = min(kBlockK, p.n_in - kb * kBlockK);
+        if (lane == 0) mbar_arrive_expect_tx(&xfull[s], seg * (uint32_t)kvalid * (uint32_t)p.nsrc);
+        __syncwarp();
+        unsigned char* st = xsm + (size_t)s * p.nsrc * p.x_src_bytes;
+        for (int k = lane; k < kvalid; k += 32) {
+          const int64_t off = r * p.size_in + (int64_t)(kb * kBlockK + k) * p.rest + m0;
+          bulk_g2s(st + (size_t)k * (kTileM * 4), p.X + off, seg, &xfull[s]);
+          if (p.nsrc > 1)
+            bulk_g2s(st + p.x_src_bytes + (size_t)k * (kTileM * 4), p.pro_z + off, seg,
+                     &xfull[s]);
+        }
+        last_s = s;
+        last_ph = ph;
+        if (++s == p.xstages) {
+          s = 0;
+          ph ^= 1u;
+        }
+      }
+    }
+    // no bulk copy may still be landing when the CTA exits
+    if (lane == 0) {
+      mbar_wait(bfull, 0, abort_flag, p.err);
+      if (last_s >= 0) mbar_wait(&xfull[last_s], last_ph, abort_flag, p.err);
+    }
+    __syncwarp();
+  } else if (warp < 4) {
+    // ------------------------------------------------------------ converters
+    bool ok = true;
+    int s = 0, sa = 0;
+    uint32_t ph = 0, pha = 0;
+    const uint32_t lane_off = (uint32_t)(warp * 32) << 16;
+    for (int64_t t = blockIdx.x; t < p.ntiles && ok; t += gridDim.x) {
+      const int64_t r = t / p.tiles_m, m0 = (t % p.tiles_m) * kTileM;
+      const int64_t m = m0 + tid;
+      const bool row_ok = m < p.rest;
+      const float beta_r = p.pro_z ? (float)p.pro_beta[r] : 0.0f;
+      float* Pout = p.pro_out ? p.pro_out + r * p.size_in : nullptr;
+      for (int kb = 0; kb < p.kblocks; ++kb) {
+        if (!mbar_wait(&aempty[sa], pha ^ 1u, abort_flag, p.err) ||
+            !mbar_wait(&xfull[s], ph, abort_flag, p.err)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const float* st = (const float*)(xsm + (size_t)s * p.nsrc * p.x_src_bytes);
+        const float* stz = (const float*)(xsm + (size_t)s * p.nsrc * p.x_src_bytes + p.x_src_bytes);
+        const uint32_t acol = tmem_base + lane_off + kAStageCol0 + (uint32_t)sa * a_cols;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          float v[32];
+#pragma unroll
+          for (int k = 0; k < 32; ++k) {
+            const int kk = kb * kBlockK + h * 32 + k;
+            const bool in = row_ok && kk < p.n_in;
+            float x = in ? st[(h * 32 + k) * kTileM + tid] : 0.0f;
+            if (p.nsrc > 1 && in) {
+              x = fmaf(beta_r, x, stz[(h * 32 + k) * kTileM + tid]);
+              Pout[(int64_t)kk * p.rest + m] = x;
+            }
+            v[k] = x;
+          }
+          uint32_t w[3][16];
+#pragma unroll
+          for (int e = 0; e < 16; ++e) {
+            uint32_t o[3];
+            split2(v[2 * e], v[2 * e + 1], p.tv, o);
+            w[0][e] = o[0];
+            w[1][e] = o[1];
+            w[2][e] = o[2];
+          }
+#pragma unroll
+          for (int tv = 0; tv < 3; ++tv)
+            if (tv < p.tv) tmem_st16(acol + (uint32_t)(tv * 32 + h * 16), w[tv]);
+        }
+        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+        mbar_arrive(&xempty[s]);
+        tc_fence_before();
+        mbar_arrive(&afull[sa]);
+        if (++s == p.xstages) {
+          s = 0;
+          ph ^= 1u;
+        }
+        if (++sa == 2) {
+          sa = 0;
+          pha ^= 1u;
+        }
+      }
+    }
+  } else if (warp == 8) {
+    // ------------------------------------------------------------------- MMA
+    if (lane == 0) {
+      const uint32_t idesc = idesc_bf16(kTileM, p.n_pad);
+      const int maxt = p.tf > p.tv ? p.tf : p.tv;
+      bool ok = mbar_wait(bfull, 0, abort_flag, p.err);
+      tc_fence_after();
+      const uint32_t bbase = smem_u32(bsm);
+      int sa = 0;
+      uint32_t pha = 0;
+      int64_t it = 0;
+      for (int64_t t = blockIdx.x; t < p.ntiles && ok; t += gridDim.x, ++it) {
+        if (!mbar_wait(acc_empty, (uint32_t)(it & 1) ^ 1u, abort_flag, p.err)) break;
+        tc_fence_after();
+        const uint32_t d_big = tmem_base, d_small = tmem_base + (uint32_t)p.n_pad;
+        uint32_t acc_big = 0, acc_small = 0;
+        for (int kb = 0; kb < p.kblocks; ++kb) {
+          if (!mbar_wait(&afull[sa], pha, abort_flag, p.err)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t a0 = tmem_base + kAStageCol0 + (uint32_t)sa * a_cols;
+          const int steps = (kb == p.kblocks - 1) ? p.ksteps_last : 4;
+          for (int kk = 0; kk < steps; ++kk) {
+            for (int ti = 0; ti < p.tf; ++ti)
+              for (int tv = 0; tv < p.tv; ++tv) {
+                if (ti + tv >= maxt) continue;
+                const uint32_t at = a0 + (uint32_t)(tv * 32 + kk * 8);
+                const uint64_t bd = sw128_desc(bbase + (uint32_t)(ti * p.kblocks + kb) *
+                                                           p.b_kb_bytes + (uint32_t)kk * 32u);
+                if (ti == 0 && tv == 0) {
+                  mma_bf16_ta(d_big, at, bd, idesc, acc_big);
+                  acc_big = 1;
+                } else {
+                  mma_bf16_ta(d_small, at, bd, idesc, acc_small);
+                  acc_small = 1;
+                }
+              }
+          }
+          mma_commit(&aempty[sa]);
+          if (++sa == 2) {
+            sa = 0;
+            pha ^= 1u;
+          }
+        }
+        if (!ok) break;
+        mma_commit(acc_full);
+      }
+      mma_commit(drain);
+      mbar_wait(drain, 0, abort_flag, p.err);
+    }
+    __syncwarp();
+  } else {
+    // -------------------------------------------------------------- epilogue
+    const int q = warp - 4;
+    const int row = q * 32 + lane;
     const bool has_small = (p.tf > 1 || p.tv > 1);
+    int64_t it = 0;
     for (int64_t t = blockIdx.x; t < p.ntiles; t += gridDim.x, ++it) {
-      const int b = (int)(it % p.nbuf);
-      if (!mbar_wait(&acc_full[b], (uint32_t)((it / p.nbuf) & 1), abort_flag, p.err)) break;
+      if (!mbar_wait(acc_full, (uint32_t)(it & 1), abort_flag, p.err)) break;
       tc_fence_after();
       const int64_t r = t / p.tiles_m, m0 = (t % p.tiles_m) * kTileM;
       const int64_t m = m0 + row;
       float* yrow = p.Y + r * p.size_out + m * p.n_out;
+      const bool vec_ok = ((reinterpret_cast<uintptr_t>(yrow) & 15u) == 0);
       const float* xrow = p.epi_x ? p.epi_x + r * p.size_out + m * p.n_out : nullptr;
       const int64_t dbase = m * p.n_out;
       double dot = 0.0;
-      const uint32_t taddr =
-          tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * 2 * p.n_pad);
+      const uint32_t taddr = tmem_base + ((uint32_t)(q * 32) << 16);
       for (int c0 = 0; c0 < p.n_pad; c0 += 16) {
         uint32_t v[16], w[16];
         tmem_ld16(taddr + (uint32_t)c0, v);
@@ -423,22 +839,19 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_kron_tc(TcParams p) {
         for (int e = 0; e < 16; ++e)
           a[e] = p.coeff * (__uint_as_float(v[e]) + __uint_as_float(w[e]));
         if (xrow && m < p.rest) {
-          float xd[16];
 #pragma unroll
           for (int e = 0; e < 16; ++e) {
             const int i = c0 + e;
-            xd[e] = (i < p.n_out) ? xrow[i] : 0.0f;
-          }
-#pragma unroll
-          for (int e = 0; e < 16; ++e) {
-            const int i = c0 + e;
-            const float dv = p.epi_dstride ? (i < p.n_out ? p.epi_d[dbase + i] : 0.0f) : p.epi_d[0];
-            a[e] = fmaf(p.epi_coeff * dv, xd[e], a[e]);
-            if (p.beta == 0.0f && i < p.n_out) dot += (double)(a[e] * xd[e]);
+            if (i < p.n_out) {
+              const float xd = xrow[i];
+              const float dv = p.epi_dstride ? p.epi_d[dbase + i] : p.epi_d[0];
+              a[e] = fmaf(p.epi_coeff * dv, xd, a[e]);
+              if (p.beta == 0.0f) dot += (double)(a[e] * xd);
+            }
           }
         }
         if (m < p.rest) {
-          if (c0 + 16 <= p.n_out && (p.n_out & 3) == 0) {
+          if (c0 + 16 <= p.n_out && vec_ok) {
 #pragma unroll
             for (int e = 0; e < 16; e += 4) {
               float4 o = make_float4(a[e], a[e + 1], a[e + 2], a[e + 3]);
@@ -466,9 +879,8 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_kron_tc(TcParams p) {
         }
       }
       tc_fence_before();
-      mbar_arrive(&acc_empty[b]);
+      mbar_arrive(acc_empty);
       if (p.epi_dot) {
-        // one partial per (tile, epilogue warp); summed in fixed order later
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, o);
         if (lane == 0) p.epi_dot[t * 4 + q] = dot;
@@ -481,7 +893,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_kron_tc(TcParams p) {
   tc_fence_after();
   if (warp == 8) {
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base),
-                 "r"(p.tmem_cols)
+                 "r"(512)
                  : "memory");
   }
 }
@@ -510,8 +922,10 @@ __global__ void k_split_factor(const TF* F, int64_t ld, int tr, int n_out, int n
   }
 }
 
+constexpr int kChunkMax = 128;
+
 struct TcPlan {
-  int n_in, n_out, n_pad, kblocks, ksteps_last, tf, tv, stages, nbuf;
+  int n_in, n_out, n_pad, kblocks, ksteps_last, tf, tv, stages, nbuf, n_chunk, nchunks;
   uint32_t stage_bytes, a_term_bytes, b_term_bytes, tmem_cols;
   size_t smem;
 };
@@ -520,35 +934,42 @@ TcPlan make_plan(int n_in, int n_out, int tf, int tv) {
   TcPlan q{};
   q.n_in = n_in;
   q.n_out = n_out;
-  q.n_pad = (n_out + 15) / 16 * 16;
+  // output columns in chunks of at most 128 (keeps two pipeline stages of
+  // A and B terms in shared memory); the image is padded to a whole number
+  // of equal chunks
+  const int n16 = (n_out + 15) / 16 * 16;
+  q.nchunks = (n16 + kChunkMax - 1) / kChunkMax;
+  q.n_chunk = ((n16 + q.nchunks - 1) / q.nchunks + 15) / 16 * 16;
+  q.n_pad = q.nchunks * q.n_chunk;
   const int kpad = (n_in + 15) / 16 * 16;
   q.kblocks = (kpad + kBlockK - 1) / kBlockK;
   q.ksteps_last = (kpad - (q.kblocks - 1) * kBlockK) / 16;
   q.tf = tf;
   q.tv = tv;
   q.a_term_bytes = kTileM * 128;
-  q.b_term_bytes = (uint32_t)q.n_pad * 128;
+  q.b_term_bytes = (uint32_t)q.n_chunk * 128;
   q.stage_bytes = (uint32_t)(tv * q.a_term_bytes + tf * q.b_term_bytes);
   q.stage_bytes = (q.stage_bytes + 1023) / 1024 * 1024;
   const size_t budget = 200 * 1024;
   q.stages = (int)std::min<size_t>(4, budget / q.stage_bytes);
   q.smem = (size_t)q.stages * q.stage_bytes + 1024 + 256;
   // two accumulators (dominant and cross terms) per buffer; double-buffer when it fits
-  q.nbuf = (4 * q.n_pad <= 512) ? 2 : 1;
+  q.nbuf = (4 * q.n_chunk <= 512) ? 2 : 1;
   uint32_t cols = 32;
-  while (cols < (uint32_t)(2 * q.nbuf * q.n_pad)) cols <<= 1;
+  while (cols < (uint32_t)(2 * q.nbuf * q.n_chunk)) cols <<= 1;
   q.tmem_cols = cols;
   return q;
 }
 
 }  // namespace
 
-// Largest factor side the tensor-core path takes (one N tile; K streamed).
-constexpr int kTcMaxN = 256;
+// Largest factor side the tensor-core path takes (N in chunks of <= 256,
+// K streamed in 64-wide blocks).
+constexpr int kTcMaxN = 8192;
 
 static bool tc_supported(const cola_linop* op) {
   for (auto* f : op->kids)
-    if (f->rows > kTcMaxN || f->cols > 4096) return false;
+    if (f->rows > kTcMaxN || f->cols > kTcMaxN) return false;
   return true;
 }
 
@@ -624,9 +1045,62 @@ void kron_tc_apply<double>(Ctx*, const cola_linop*, const double*, double*, int6
   fail(COLA_ERR_UNSUPPORTED, "tensor-core Kronecker contraction takes FP32 vectors");
 }
 
+constexpr size_t kSmemMax = 232448;  // 227 KB opt-in dynamic shared memory per CTA
+
+static size_t res_smem(const TcResParams& r) {
+  const size_t b = ((size_t)r.b_bytes + 1023) & ~(size_t)1023;
+  return 1024 + b + (size_t)r.xstages * r.nsrc * r.x_src_bytes + 512;
+}
+
+// Resident-factor plan: factor sides <= 128 (two 64-wide k blocks), the split
+// factor image within 96 KB, and X rows 16-byte aligned for cp.async.bulk.
+static bool res_plan(const TcParams& p, TcResParams& r) {
+  if (p.nchunks != 1 || p.n_pad > 128 || p.kblocks > 2) return false;
+  const uint32_t b_bytes = (uint32_t)p.tf * (uint32_t)p.kblocks * (uint32_t)p.n_pad * 128u;
+  if (b_bytes > 96u * 1024u) return false;
+  if (p.rest % 4 != 0 || p.size_in % 4 != 0) return false;
+  if (((uintptr_t)p.X & 15u) != 0 || (p.pro_z && ((uintptr_t)p.pro_z & 15u) != 0)) return false;
+  r.X = p.X;
+  r.Y = p.Y;
+  r.Bimg = p.Bimg;
+  r.rest = p.rest;
+  r.size_in = p.size_in;
+  r.size_out = p.size_out;
+  r.tiles_m = p.tiles_m;
+  r.ntiles = p.ntiles;
+  r.n_in = p.n_in;
+  r.n_out = p.n_out;
+  r.n_pad = p.n_pad;
+  r.kblocks = p.kblocks;
+  r.ksteps_last = p.ksteps_last;
+  r.tf = p.tf;
+  r.tv = p.tv;
+  r.nsrc = p.pro_z ? 2 : 1;
+  r.b_bytes = b_bytes;
+  r.b_kb_bytes = (uint32_t)p.n_pad * 128u;
+  r.x_src_bytes = (uint32_t)kBlockK * kTileM * 4u;
+  const size_t b_round = ((size_t)b_bytes + 1023) & ~(size_t)1023;
+  const size_t avail = kSmemMax - 1024 - 512 - b_round;
+  r.xstages = (int)std::min<size_t>(4, avail / ((size_t)r.nsrc * r.x_src_bytes));
+  if (r.xstages < 2) return false;
+  r.coeff = p.coeff;
+  r.beta = p.beta;
+  r.err = p.err;
+  r.pro_z = p.pro_z;
+  r.pro_out = p.pro_out;
+  r.pro_beta = p.pro_beta;
+  r.epi_x = p.epi_x;
+  r.epi_d = p.epi_d;
+  r.epi_dstride = p.epi_dstride;
+  r.epi_coeff = p.epi_coeff;
+  r.epi_dot = p.epi_dot;
+  return true;
+}
+
 struct TcFusion {
   const float* pro_z = nullptr;
   const double* pro_beta = nullptr;
+  float* pro_out = nullptr;
   const float* epi_x = nullptr;
   const float* epi_d = nullptr;
   int64_t epi_dstride = 0;
@@ -673,7 +1147,9 @@ static int64_t kron_tc_run(Ctx* c, const cola_linop* op, const float* X, float* 
     p.size_out = out_size;
     p.batch = R;
     p.tiles_m = (rest + kTileM - 1) / kTileM;
-    p.ntiles = p.tiles_m * R;
+    p.n_chunk = q.n_chunk;
+    p.nchunks = q.nchunks;
+    p.ntiles = p.tiles_m * R * q.nchunks;
     p.n_in = n_in;
     p.n_out = n_out;
     p.n_pad = q.n_pad;
@@ -693,6 +1169,7 @@ static int64_t kron_tc_run(Ctx* c, const cola_linop* op, const float* X, float* 
     if (k == 0) {
       p.pro_z = fu.pro_z;
       p.pro_beta = fu.pro_beta;
+      p.pro_out = fu.pro_out;
     }
     if (last) {
       p.epi_x = fu.epi_x;
@@ -700,15 +1177,25 @@ static int64_t kron_tc_run(Ctx* c, const cola_linop* op, const float* X, float* 
       p.epi_dstride = fu.epi_dstride;
       p.epi_coeff = fu.epi_coeff;
       p.epi_dot = fu.epi_dot;
-      last_tiles = p.tiles_m;
+      last_tiles = p.tiles_m * q.nchunks;
     }
     if (c->device < 64 && !attr_set[c->device]) {
-      COLA_CUDA(cudaFuncSetAttribute(k_kron_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     227 * 1024));
+      COLA_CUDA(cudaFuncSetAttribute(k_kron_tc<OneProb>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+      COLA_CUDA(cudaFuncSetAttribute(k_kron_tc<ProbTable>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+      COLA_CUDA(cudaFuncSetAttribute(k_kron_tc_res, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     kSmemMax));
       attr_set[c->device] = true;
     }
     const int grid = (int)std::min<int64_t>(p.ntiles, c->num_sms);
-    k_kron_tc<<<grid, kThreadsTc, q.smem, c->s>>>(p);
+    TcResParams rp{};
+    if (res_plan(p, rp)) {
+      const size_t smem = res_smem(rp);
+      k_kron_tc_res<<<grid, kThreadsRes, smem, c->s>>>(rp);
+    } else {
+      k_kron_tc<OneProb><<<grid, kThreadsTc, q.smem, c->s>>>(OneProb{p}, p);
+    }
     c->count_launch();
     COLA_CUDA(cudaGetLastError());
     cur = dst;
@@ -729,7 +1216,8 @@ void kron_tc_apply<float>(Ctx* c, const cola_linop* op, const float* X, float* Y
 // right-hand side (partials per RHS = 4 x that), or 0 when the operator does
 // not have this shape (the caller then takes the generic path).
 int64_t kron_tc_cg_mvm(Ctx* c, const cola_linop* op, const float* z, const double* beta_vec,
-                       float* p, float* Ap, double* tile_dot, int64_t R, int depth) {
+                       const float* p_old, float* p_new, float* Ap, double* tile_dot, int64_t R,
+                       int depth) {
   if (op->kind != LK_SUM || op->kids.size() != 2) return 0;
   int ik = -1, id = -1;
   for (int i = 0; i < 2; ++i) {
@@ -744,12 +1232,13 @@ int64_t kron_tc_cg_mvm(Ctx* c, const cola_linop* op, const float* z, const doubl
   TcFusion fu;
   fu.pro_z = z;
   fu.pro_beta = beta_vec;
-  fu.epi_x = p;
+  fu.pro_out = p_new;
+  fu.epi_x = p_new;
   fu.epi_d = leaf_ptr<float>(dg);
   fu.epi_dstride = dg->stride;
   fu.epi_coeff = (float)op->coeffs[id];
   fu.epi_dot = tile_dot;
-  return kron_tc_run(c, kron, p, Ap, R, op->coeffs[ik], 0.0, depth, false, fu);
+  return kron_tc_run(c, kron, p_old, Ap, R, op->coeffs[ik], 0.0, depth, false, fu);
 }
 
 int64_t kron_tc_tiles_per_rhs(const cola_linop* op) {
@@ -759,9 +1248,117 @@ int64_t kron_tc_tiles_per_rhs(const cola_linop* op) {
     if (k->kind == LK_KRON && k->kids.size() >= 2 && tc_supported(k)) {
       const cola_linop* last = k->kids.back();
       const int64_t rest = k->rows / last->rows;  // rows produced by the earlier steps
-      return (rest + kTileM - 1) / kTileM;
+      const int n16 = (int)((last->rows + 15) / 16 * 16);
+      return (rest + kTileM - 1) / kTileM * ((n16 + kChunkMax - 1) / kChunkMax);
     }
   return 0;
+}
+
+}  // namespace cola
+
+// ------------------------------------------------------------------ batches
+namespace cola {
+
+static std::string tagged(const char* tag, const char* what) {
+  return std::string(tag) + "." + what;
+}
+
+std::vector<int64_t> kron_tc_batch_upload(Ctx* c, const std::vector<TcBatchProblem>& probs,
+                                          int tf, int tv, const char* tag) {
+  std::vector<TcParams> hp(probs.size());
+  std::vector<int64_t> first(probs.size()), counts(probs.size());
+  std::vector<int> tile_prob;
+  int64_t tot = 0;
+  for (size_t i = 0; i < probs.size(); ++i) {
+    const TcBatchProblem& b = probs[i];
+    const cola_linop* f = b.factor;
+    const int n_in = (int)(b.transpose ? f->rows : f->cols);
+    const int n_out = (int)(b.transpose ? f->cols : f->rows);
+    const TcPlan q = make_plan(n_in, n_out, tf, tv);
+    TcParams& p = hp[i];
+    p = TcParams{};
+    p.X = b.X;
+    p.Y = b.Y;
+    auto it = f->derived.find(100 + (b.transpose ? 10 : 0) + tf);
+    COLA_REQUIRE(it != f->derived.end(), COLA_ERR_INVALID_ARG,
+                 "internal: batch factor not split for MIXED precision");
+    p.Bimg = (const uint16_t*)it->second.p;
+    p.rest = b.rest;
+    p.size_in = b.size_in;
+    p.size_out = b.size_out;
+    p.batch = b.R;
+    p.tiles_m = (b.rest + kTileM - 1) / kTileM;
+    p.n_chunk = q.n_chunk;
+    p.nchunks = q.nchunks;
+    p.ntiles = p.tiles_m * b.R * q.nchunks;
+    p.n_in = n_in;
+    p.n_out = n_out;
+    p.n_pad = q.n_pad;
+    p.kblocks = q.kblocks;
+    p.ksteps_last = q.ksteps_last;
+    p.b_term_bytes = q.b_term_bytes;
+    p.coeff = b.coeff;
+    p.beta = b.beta;
+    p.pro_z = b.pro_z;
+    p.pro_beta = b.pro_beta;
+    p.pro_out = b.pro_out;
+    p.epi_x = b.epi_x;
+    p.epi_d = b.epi_d;
+    p.epi_dstride = b.epi_dstride;
+    p.epi_coeff = b.epi_coeff;
+    p.epi_dot = b.epi_dot;
+    first[i] = tot;
+    counts[i] = p.ntiles;
+    tile_prob.insert(tile_prob.end(), (size_t)p.ntiles, (int)i);
+    tot += p.ntiles;
+  }
+  // fixed-capacity device tables so replays of a captured graph stay valid
+  const size_t cap_p = std::max<size_t>(1, hp.size());
+  void* dp = c->ws.get(tagged(tag, "probs"), sizeof(TcParams) * cap_p);
+  void* dt = c->ws.get(tagged(tag, "tile"), sizeof(int) * std::max<size_t>(1, tile_prob.size()));
+  void* df = c->ws.get(tagged(tag, "first"), sizeof(int64_t) * cap_p);
+  void* dc = c->ws.get(tagged(tag, "count"), sizeof(int64_t));
+  if (!hp.empty()) {
+    COLA_CUDA(cudaMemcpyAsync(dp, hp.data(), sizeof(TcParams) * hp.size(),
+                              cudaMemcpyHostToDevice, c->s));
+    COLA_CUDA(cudaMemcpyAsync(df, first.data(), sizeof(int64_t) * first.size(),
+                              cudaMemcpyHostToDevice, c->s));
+  }
+  if (!tile_prob.empty())
+    COLA_CUDA(cudaMemcpyAsync(dt, tile_prob.data(), sizeof(int) * tile_prob.size(),
+                              cudaMemcpyHostToDevice, c->s));
+  COLA_CUDA(cudaMemcpyAsync(dc, &tot, sizeof(int64_t), cudaMemcpyHostToDevice, c->s));
+  // pageable sources: the copies above are staged before returning, but make
+  // the host vectors' lifetime irrelevant by waiting here (tables are small)
+  COLA_CUDA(cudaStreamSynchronize(c->s));
+  return counts;
+}
+
+void kron_tc_batch_launch(Ctx* c, const char* tag, int tf, int tv, int max_n_chunk) {
+  TcParams K{};
+  K.tf = tf;
+  K.tv = tv;
+  K.a_term_bytes = kTileM * 128;
+  K.stage_bytes = (uint32_t)(tv * K.a_term_bytes + tf * (uint32_t)max_n_chunk * 128u);
+  K.stage_bytes = (K.stage_bytes + 1023) / 1024 * 1024;
+  K.stages = (int)std::min<size_t>(4, (size_t)(200 * 1024) / K.stage_bytes);
+  K.n_chunk = max_n_chunk;
+  K.nbuf = (4 * max_n_chunk <= 512) ? 2 : 1;
+  uint32_t cols = 32;
+  while (cols < (uint32_t)(2 * K.nbuf * max_n_chunk)) cols <<= 1;
+  K.tmem_cols = cols;
+  K.err = tc_errflag(c);
+  const size_t smem = (size_t)K.stages * K.stage_bytes + 1024 + 256;
+  ProbTable src;
+  src.probs = (const TcParams*)c->ws.bufs.at(tagged(tag, "probs")).p;
+  src.tile_prob = (const int*)c->ws.bufs.at(tagged(tag, "tile")).p;
+  src.first = (const int64_t*)c->ws.bufs.at(tagged(tag, "first")).p;
+  src.count_dev = (const int64_t*)c->ws.bufs.at(tagged(tag, "count")).p;
+  COLA_CUDA(cudaFuncSetAttribute(k_kron_tc<ProbTable>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+  k_kron_tc<ProbTable><<<c->num_sms, kThreadsTc, smem, c->s>>>(src, K);
+  c->count_launch();
+  COLA_CUDA(cudaGetLastError());
 }
 
 }  // namespace cola

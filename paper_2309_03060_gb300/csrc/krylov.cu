@@ -25,14 +25,6 @@
 
 namespace cola {
 
-struct CgState {
-  double rz, pAp, alpha, beta;
-  double rr, rr_ref, bb, tol2;
-  double rr64;
-  long long iters;
-  int active, flag, status, updates;
-};
-
 namespace {
 
 template <typename T>
@@ -225,6 +217,31 @@ __global__ void k_cg_restate(CgState* st, const double* part_rz, const double* p
   if (rr64) s.rr64 = rr64[r];
   const double conv = rr64 ? rr64[r] : rr;
   if (s.active && conv <= s.tol2) s.active = 0;
+}
+
+// After the recursive residual met the tolerance: re-activate every
+// right-hand side whose true residual (partials of the freshly computed r)
+// still misses it, restarting its search direction.
+__global__ void k_cg_verify(CgState* st, const double* part_rz, const double* part_rr, int nblk,
+                            int64_t R, double* beta_vec) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= R) return;
+  CgState& s = st[r];
+  double rz = 0.0, rr = 0.0;
+  for (int b = 0; b < nblk; ++b) {
+    rz += part_rz[r * nblk + b];
+    rr += part_rr[r * nblk + b];
+  }
+  s.rr64 = rr;
+  if (s.status != 0 || s.active || !(rr > s.tol2)) return;
+  s.active = 1;
+  s.flag = 0;
+  s.rz = rz;
+  s.rr = rr;
+  s.rr_ref = rr;
+  s.beta = 0.0;
+  s.updates += 1;
+  if (beta_vec) beta_vec[r] = 0.0;
 }
 
 template <typename T>
@@ -472,7 +489,9 @@ inline int ew_blocks(int64_t n) {
 // ====================================================================== CG
 template <typename T>
 struct CgBufs {
-  T *x, *r, *p, *Ap, *z;  // working precision
+  T *x, *r, *p, *Ap, *z;  // working precision; p is pp[cur]
+  T* pp[2];               // ping-pong search directions (fused MIXED path)
+  int cur;
   T* invd;
   double *x64, *b64, *r64;
   double *part_rz, *part_rr, *dotp, *dotv;
@@ -495,9 +514,13 @@ static void cg_iteration(Ctx* c, const cola_linop* op, CgBufs<T>& B, int64_t N, 
                          int nblk, int prec, double delta2, int refine) {
   const unsigned rb = (unsigned)((R + 127) / 128);
   if (B.fused_tiles > 0) {
-    // p = z + beta p (first mode step), Ap and p^T A p partials (last mode step)
-    kron_tc_cg_mvm(c, op, (const float*)(B.invd ? B.z : B.r), B.beta_vec, (float*)B.p,
-                   (float*)B.Ap, B.tile_dot, R, 1);
+    // p_new = z + beta p_old (first mode step), Ap and p^T A p partials (last)
+    T* p_old = B.pp[B.cur];
+    T* p_new = B.pp[B.cur ^ 1];
+    kron_tc_cg_mvm(c, op, (const float*)(B.invd ? B.z : B.r), B.beta_vec, (const float*)p_old,
+                   (float*)p_new, (float*)B.Ap, B.tile_dot, R, 1);
+    B.cur ^= 1;
+    B.p = p_new;
     k_cg_alpha<<<rb, 128, 0, c->s>>>(B.st, B.tile_dot, (int)(4 * B.fused_tiles), R);
     c->count_launch();
   } else {
@@ -570,7 +593,10 @@ static cola_status cg_run(Ctx* c, cola_linop* op, const void* Bin, void* Xout, i
   CgBufs<T> B{};
   B.x = (T*)ws.get("cg.x", sizeof(T) * N * R);
   B.r = (T*)ws.get("cg.r", sizeof(T) * N * R);
-  B.p = (T*)ws.get("cg.p", sizeof(T) * N * R);
+  B.pp[0] = (T*)ws.get("cg.p", sizeof(T) * N * R);
+  B.pp[1] = nullptr;
+  B.cur = 0;
+  B.p = B.pp[0];
   B.Ap = (T*)ws.get("cg.Ap", sizeof(T) * N * R);
   B.z = o.jacobi ? (T*)ws.get("cg.z", sizeof(T) * N * R) : nullptr;
   B.part_rz = (double*)ws.get("cg.prz", 8 * nblk * R);
@@ -580,6 +606,7 @@ static cola_status cg_run(Ctx* c, cola_linop* op, const void* Bin, void* Xout, i
   B.st = (CgState*)ws.get("cg.st", sizeof(CgState) * R);
   B.beta_vec = (double*)ws.get("cg.beta", 8 * R);
   B.fused_tiles = (prec == COLA_PREC_MIXED && sizeof(T) == 4) ? kron_tc_tiles_per_rhs(op) : 0;
+  if (B.fused_tiles > 0) B.pp[1] = (T*)ws.get("cg.p2", sizeof(T) * N * R);
   B.tile_dot = B.fused_tiles > 0 ? (double*)ws.get("cg.tdot", 8 * 4 * B.fused_tiles * R) : nullptr;
   COLA_CUDA(cudaMemsetAsync(B.beta_vec, 0, 8 * R, c->s));
   double* bb = (double*)ws.get("cg.bb", 8 * R);
@@ -645,13 +672,18 @@ static cola_status cg_run(Ctx* c, cola_linop* op, const void* Bin, void* Xout, i
     COLA_CUDA(cudaStreamSynchronize(c->s));
   };
   const double delta2 = o.reliable_delta * o.reliable_delta;
-  const int chunk = std::max(1, o.graph_chunk);
+  // the fused path alternates two p buffers, so a graph chunk must hold an
+  // even number of iterations to start and end on the same buffer
+  int chunk = std::max(1, o.graph_chunk);
+  if (B.fused_tiles > 0) chunk += chunk & 1;
   // everything a captured kernel bakes in is part of the graph key
-  char extra[96];
-  snprintf(extra, sizeof extra, ":%c:d%.17g:s%d%d", sizeof(T) == 8 ? 'd' : 'f', delta2,
-           o.split_factor_terms, o.split_vector_terms);
-  const std::string key =
-      key_of("cg", op, R, prec, (refine ? 1 : 0) | (o.jacobi ? 2 : 0) | (chunk << 2), 0) + extra;
+  auto graph_key = [&] {
+    char extra[128];
+    snprintf(extra, sizeof extra, ":%c:d%.17g:s%d%d:p%d", sizeof(T) == 8 ? 'd' : 'f', delta2,
+             o.split_factor_terms, o.split_vector_terms, B.cur);
+    return key_of("cg", op, R, prec, (refine ? 1 : 0) | (o.jacobi ? 2 : 0) | (chunk << 2), 0) +
+           extra;
+  };
   int64_t iters = 0;
   int updates = 0;
   // COLA_TRACE=1 prints the worst relative residual of the active right-hand
@@ -681,9 +713,10 @@ static cola_status cg_run(Ctx* c, cola_linop* op, const void* Bin, void* Xout, i
     cg_iteration<T>(c, op, B, N, R, nblk, prec, delta2, refine ? 1 : 0);
     iters = 1;
   }
+  for (int verify = 0;; ++verify) {
   while (any_active) {
     if (iters >= o.maxiter) break;
-    cg_chunk<T>(c, op, B, N, R, nblk, prec, delta2, refine ? 1 : 0, chunk, key);
+    cg_chunk<T>(c, op, B, N, R, nblk, prec, delta2, refine ? 1 : 0, chunk, graph_key());
     iters += chunk;
     read_state();
     trace_line("chunk");
@@ -713,6 +746,26 @@ static cola_status cg_run(Ctx* c, cola_linop* op, const void* Bin, void* Xout, i
       for (int64_t r = 0; r < R; ++r) any_active |= hst[r].active != 0;
     }
     if (refine && updates >= o.max_updates) break;
+  }
+    // Without refinement the recursive residual decided convergence; check the
+    // true residual b - A x and continue where it still misses the tolerance.
+    if (refine || iters >= o.maxiter || verify >= o.max_updates) break;
+    COLA_CUDA(cudaMemcpyAsync(B.r, Bin, sizeof(T) * N * R, cudaMemcpyDeviceToDevice, c->s));
+    apply<T>(c, op, B.x, B.r, R, -1.0, 1.0, 1, false, prec);
+    k_refresh<T><<<rows_grid(N, R, nblk), 256, 0, c->s>>>(N, nullptr, B.r, B.invd, B.z, nblk,
+                                                           B.part_rz, B.part_rr);
+    c->count_launch();
+    k_cg_verify<<<(unsigned)((R + 127) / 128), 128, 0, c->s>>>(B.st, B.part_rz, B.part_rr, nblk,
+                                                               R, B.beta_vec);
+    c->count_launch();
+    read_state();
+    trace_line("verify");
+    any_active = false;
+    for (int64_t r = 0; r < R; ++r) any_active |= hst[r].active != 0;
+    if (!any_active) break;
+    k_copy_active<T><<<dim3(ew_blocks(N), (unsigned)R), 256, 0, c->s>>>(N, B.invd ? B.z : B.r,
+                                                                        B.p, B.st);
+    c->count_launch();
   }
 
   // Final solution and true residual.

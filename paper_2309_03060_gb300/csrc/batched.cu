@@ -413,7 +413,7 @@ cola_status batched_cg_fast(Ctx* c, int32_t nsys, const cola_linop* const* ops,
   double* part_rz = (double*)ws.get("bcg.prz", 8 * cap_blocks);
   double* part_rr = (double*)ws.get("bcg.prr", 8 * cap_blocks);
 
-  // p^T A p partial slots: fixed per system (4 per tile of mode step 2)
+  // p^T A p partial slots: fixed per system (8 per tile of mode step 2)
   std::vector<int64_t> tiles2(nsys);
   int64_t tdot_tot = 0;
   std::vector<int64_t> tdot_off(nsys);
@@ -423,7 +423,7 @@ cola_status batched_cg_fast(Ctx* c, int32_t nsys, const cola_linop* const* ops,
     const int64_t chunks = (n16 + 127) / 128;
     tiles2[s] = (sys[s].n1 + 127) / 128 * chunks;  // per right-hand side
     tdot_off[s] = tdot_tot;
-    tdot_tot += 4 * tiles2[s] * sys[s].R;
+    tdot_tot += 8 * tiles2[s] * sys[s].R;
   }
   double* tdot = (double*)ws.get("bcg.tdot", 8 * std::max<int64_t>(1, tdot_tot));
   int64_t* seg_p0 = (int64_t*)ws.get("bcg.sp0", 8 * G);
@@ -435,8 +435,8 @@ cola_status batched_cg_fast(Ctx* c, int32_t nsys, const cola_linop* const* ops,
     for (int s = 0; s < nsys; ++s)
       for (int64_t q = 0; q < sys[s].R; ++q) {
         const int64_t g = sys[s].g0 + q;
-        hp0[g] = tdot_off[s] + 4 * tiles2[s] * q;
-        hpn[g] = (int)(4 * tiles2[s]);
+        hp0[g] = tdot_off[s] + 8 * tiles2[s] * q;
+        hpn[g] = (int)(8 * tiles2[s]);
         hs[g] = SegShift{leaf_ptr<double>(sys[s].diag), sys[s].diag->stride,
                          sys[s].off + q * sys[s].N, sys[s].cd};
       }

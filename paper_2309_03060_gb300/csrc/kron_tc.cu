@@ -41,6 +41,7 @@ constexpr int kBlockK = 64;               // bf16 elements per 128-byte swizzled
 constexpr int kProducerThreads = 128;
 constexpr int kThreadsTc = 288;
 constexpr uint64_t kWaitNs = 2000000000ull;  // 2 s per wait
+constexpr int kDotSlots = 8;  // p . Ap partials per tile (one per epilogue warp slot)
 
 struct TcParams {
   const float* X;
@@ -528,7 +529,10 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_kron_tc(Src src, TcParams K) 
         // one partial per (tile, epilogue warp); summed in fixed order later
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, o);
-        if (lane == 0) p.epi_dot[lt * 4 + q] = dot;
+        if (lane == 0) {
+          p.epi_dot[lt * kDotSlots + q] = dot;
+          p.epi_dot[lt * kDotSlots + 4 + q] = 0.0;  // this kernel fills 4 of the 8 slots
+        }
       }
     }
   }
@@ -558,7 +562,13 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_kron_tc(Src src, TcParams K) 
 //   warps 4-7   epilogue, as in k_kron_tc.
 // TMEM columns: [0, n_pad) dominant accumulator, [n_pad, 2 n_pad) cross
 // terms, [256 + s * 32 tv, ...) A stage s (32 columns per BF16 term).
-constexpr int kThreadsRes = 320;
+constexpr int kResConvWarps = 8;
+constexpr int kResEpiWarps = 8;
+constexpr int kResMmaWarp = kResConvWarps + kResEpiWarps;   // 16
+constexpr int kResLoaderWarp = kResMmaWarp + 1;              // 17
+constexpr int kThreadsRes = 32 * (kResLoaderWarp + 1);       // 576
+constexpr int kResConvThreads = 32 * kResConvWarps;
+constexpr int kResEpiThreads = 32 * kResEpiWarps;
 constexpr uint32_t kAStageCol0 = 256;
 
 struct TcResParams {
@@ -587,6 +597,13 @@ __device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t* r) {
       "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]),
       "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]),
       "r"(r[15])
+      : "memory");
+}
+
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t* r) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"r"(taddr),
+      "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7])
       : "memory");
 }
 
@@ -622,19 +639,19 @@ __global__ void __launch_bounds__(kThreadsRes, 1) k_kron_tc_res(TcResParams p) {
     mbar_init(bfull, 1);
     for (int s = 0; s < p.xstages; ++s) {
       mbar_init(&xfull[s], 1);
-      mbar_init(&xempty[s], kProducerThreads);
+      mbar_init(&xempty[s], kResConvThreads);
     }
     for (int s = 0; s < 2; ++s) {
-      mbar_init(&afull[s], kProducerThreads);
+      mbar_init(&afull[s], kResConvThreads);
       mbar_init(&aempty[s], 1);
     }
     mbar_init(acc_full, 1);
-    mbar_init(acc_empty, 128);
+    mbar_init(acc_empty, kResEpiThreads);
     mbar_init(drain, 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == 8) {
+  if (warp == kResMmaWarp) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      smem_u32(tmem_slot)),
                  "r"(512)
@@ -647,7 +664,7 @@ __global__ void __launch_bounds__(kThreadsRes, 1) k_kron_tc_res(TcResParams p) {
   const uint32_t tmem_base = *tmem_slot;
   const uint32_t a_cols = 32u * (uint32_t)p.tv;  // TMEM columns per A stage
 
-  if (warp == 9) {
+  if (warp == kResLoaderWarp) {
     // ---------------------------------------------------------------- loader
     bool ok = true;
     int s = 0;
@@ -692,15 +709,18 @@ __global__ void __launch_bounds__(kThreadsRes, 1) k_kron_tc_res(TcResParams p) {
       if (last_s >= 0) mbar_wait(&xfull[last_s], last_ph, abort_flag, p.err);
     }
     __syncwarp();
-  } else if (warp < 4) {
+  } else if (warp < kResConvWarps) {
     // ------------------------------------------------------------ converters
+    // warp w owns TMEM lanes 32 (w % 4) .. + 31 and the k half w / 4 of a block
     bool ok = true;
     int s = 0, sa = 0;
     uint32_t ph = 0, pha = 0;
-    const uint32_t lane_off = (uint32_t)(warp * 32) << 16;
+    const int quarter = warp & 3, half = warp >> 2;
+    const int row = quarter * 32 + lane;
+    const uint32_t lane_off = (uint32_t)(quarter * 32) << 16;
     for (int64_t t = blockIdx.x; t < p.ntiles && ok; t += gridDim.x) {
       const int64_t r = t / p.tiles_m, m0 = (t % p.tiles_m) * kTileM;
-      const int64_t m = m0 + tid;
+      const int64_t m = m0 + row;
       const bool row_ok = m < p.rest;
       const float beta_r = p.pro_z ? (float)p.pro_beta[r] : 0.0f;
       float* Pout = p.pro_out ? p.pro_out + r * p.size_in : nullptr;
@@ -715,22 +735,23 @@ __global__ void __launch_bounds__(kThreadsRes, 1) k_kron_tc_res(TcResParams p) {
         const float* stz = (const float*)(xsm + (size_t)s * p.nsrc * p.x_src_bytes + p.x_src_bytes);
         const uint32_t acol = tmem_base + lane_off + kAStageCol0 + (uint32_t)sa * a_cols;
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          float v[32];
+        for (int j = 0; j < 2; ++j) {  // 16 k values at a time
+          float v[16];
 #pragma unroll
-          for (int k = 0; k < 32; ++k) {
-            const int kk = kb * kBlockK + h * 32 + k;
+          for (int k = 0; k < 16; ++k) {
+            const int kl = half * 32 + j * 16 + k;
+            const int kk = kb * kBlockK + kl;
             const bool in = row_ok && kk < p.n_in;
-            float x = in ? st[(h * 32 + k) * kTileM + tid] : 0.0f;
+            float x = in ? st[kl * kTileM + row] : 0.0f;
             if (p.nsrc > 1 && in) {
-              x = fmaf(beta_r, x, stz[(h * 32 + k) * kTileM + tid]);
+              x = fmaf(beta_r, x, stz[kl * kTileM + row]);
               Pout[(int64_t)kk * p.rest + m] = x;
             }
             v[k] = x;
           }
-          uint32_t w[3][16];
+          uint32_t w[3][8];
 #pragma unroll
-          for (int e = 0; e < 16; ++e) {
+          for (int e = 0; e < 8; ++e) {
             uint32_t o[3];
             split2(v[2 * e], v[2 * e + 1], p.tv, o);
             w[0][e] = o[0];
@@ -739,7 +760,7 @@ __global__ void __launch_bounds__(kThreadsRes, 1) k_kron_tc_res(TcResParams p) {
           }
 #pragma unroll
           for (int tv = 0; tv < 3; ++tv)
-            if (tv < p.tv) tmem_st16(acol + (uint32_t)(tv * 32 + h * 16), w[tv]);
+            if (tv < p.tv) tmem_st8(acol + (uint32_t)(tv * 32 + half * 16 + j * 8), w[tv]);
         }
         asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
         mbar_arrive(&xempty[s]);
@@ -755,7 +776,7 @@ __global__ void __launch_bounds__(kThreadsRes, 1) k_kron_tc_res(TcResParams p) {
         }
       }
     }
-  } else if (warp == 8) {
+  } else if (warp == kResMmaWarp) {
     // ------------------------------------------------------------------- MMA
     if (lane == 0) {
       const uint32_t idesc = idesc_bf16(kTileM, p.n_pad);
@@ -810,8 +831,13 @@ __global__ void __launch_bounds__(kThreadsRes, 1) k_kron_tc_res(TcResParams p) {
     __syncwarp();
   } else {
     // -------------------------------------------------------------- epilogue
-    const int q = warp - 4;
-    const int row = q * 32 + lane;
+    // warp w reads TMEM lanes 32 (w % 4) .. + 31 and the column half (w - 8) / 4;
+    // it drains its 64 columns into registers, releases the accumulator, and
+    // only then stores, so the next tile's MMAs do not wait for global stores.
+    const int ew = warp - kResConvWarps;
+    const int quarter = warp & 3, chalf = ew >> 2;
+    const int row = quarter * 32 + lane;
+    const int c_begin = chalf * 64;
     const bool has_small = (p.tf > 1 || p.tv > 1);
     int64_t it = 0;
     for (int64_t t = blockIdx.x; t < p.ntiles; t += gridDim.x, ++it) {
@@ -819,42 +845,65 @@ __global__ void __launch_bounds__(kThreadsRes, 1) k_kron_tc_res(TcResParams p) {
       tc_fence_after();
       const int64_t r = t / p.tiles_m, m0 = (t % p.tiles_m) * kTileM;
       const int64_t m = m0 + row;
+      const uint32_t taddr = tmem_base + ((uint32_t)(quarter * 32) << 16);
+      float a[64];
+#pragma unroll
+      for (int q8 = 0; q8 < 8; ++q8) {
+        const int c0 = c_begin + q8 * 8;
+        uint32_t v[8], w[8];
+        if (c0 < p.n_pad) {
+          asm volatile(
+              "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+              : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]),
+                "=r"(v[6]), "=r"(v[7])
+              : "r"(taddr + (uint32_t)c0));
+          if (has_small) {
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                : "=r"(w[0]), "=r"(w[1]), "=r"(w[2]), "=r"(w[3]), "=r"(w[4]), "=r"(w[5]),
+                  "=r"(w[6]), "=r"(w[7])
+                : "r"(taddr + (uint32_t)(p.n_pad + c0)));
+          }
+          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+          for (int e = 0; e < 8; ++e)
+            a[q8 * 8 + e] = p.coeff * (__uint_as_float(v[e]) +
+                                       (has_small ? __uint_as_float(w[e]) : 0.0f));
+        } else {
+#pragma unroll
+          for (int e = 0; e < 8; ++e) a[q8 * 8 + e] = 0.0f;
+        }
+      }
+      tc_fence_before();
+      mbar_arrive(acc_empty);
+      // stores (and the fused shift / p . Ap partial) from registers
       float* yrow = p.Y + r * p.size_out + m * p.n_out;
       const bool vec_ok = ((reinterpret_cast<uintptr_t>(yrow) & 15u) == 0);
       const float* xrow = p.epi_x ? p.epi_x + r * p.size_out + m * p.n_out : nullptr;
       const int64_t dbase = m * p.n_out;
       double dot = 0.0;
-      const uint32_t taddr = tmem_base + ((uint32_t)(q * 32) << 16);
-      for (int c0 = 0; c0 < p.n_pad; c0 += 16) {
-        uint32_t v[16], w[16];
-        tmem_ld16(taddr + (uint32_t)c0, v);
-        if (has_small) {
-          tmem_ld16(taddr + (uint32_t)(p.n_pad + c0), w);
-        } else {
+      if (m < p.rest) {
 #pragma unroll
-          for (int e = 0; e < 16; ++e) w[e] = 0u;
-        }
-        float a[16];
+        for (int q4 = 0; q4 < 4; ++q4) {
+          const int c0 = c_begin + q4 * 16;
+          if (c0 >= p.n_out) break;
+          if (xrow) {
 #pragma unroll
-        for (int e = 0; e < 16; ++e)
-          a[e] = p.coeff * (__uint_as_float(v[e]) + __uint_as_float(w[e]));
-        if (xrow && m < p.rest) {
-#pragma unroll
-          for (int e = 0; e < 16; ++e) {
-            const int i = c0 + e;
-            if (i < p.n_out) {
-              const float xd = xrow[i];
-              const float dv = p.epi_dstride ? p.epi_d[dbase + i] : p.epi_d[0];
-              a[e] = fmaf(p.epi_coeff * dv, xd, a[e]);
-              if (p.beta == 0.0f) dot += (double)(a[e] * xd);
+            for (int e = 0; e < 16; ++e) {
+              const int i = c0 + e;
+              if (i < p.n_out) {
+                const float xd = xrow[i];
+                const float dv = p.epi_dstride ? p.epi_d[dbase + i] : p.epi_d[0];
+                a[q4 * 16 + e] = fmaf(p.epi_coeff * dv, xd, a[q4 * 16 + e]);
+                if (p.beta == 0.0f) dot += (double)(a[q4 * 16 + e] * xd);
+              }
             }
           }
-        }
-        if (m < p.rest) {
           if (c0 + 16 <= p.n_out && vec_ok) {
 #pragma unroll
             for (int e = 0; e < 16; e += 4) {
-              float4 o = make_float4(a[e], a[e + 1], a[e + 2], a[e + 3]);
+              float4 o = make_float4(a[q4 * 16 + e], a[q4 * 16 + e + 1], a[q4 * 16 + e + 2],
+                                     a[q4 * 16 + e + 3]);
               float4* dst = reinterpret_cast<float4*>(yrow + c0 + e);
               if (p.beta != 0.0f) {
                 const float4 old = *dst;
@@ -870,7 +919,7 @@ __global__ void __launch_bounds__(kThreadsRes, 1) k_kron_tc_res(TcResParams p) {
             for (int e = 0; e < 16; ++e) {
               const int i = c0 + e;
               if (i < p.n_out) {
-                float o = a[e];
+                float o = a[q4 * 16 + e];
                 if (p.beta != 0.0f) o += p.beta * yrow[i];
                 yrow[i] = o;
               }
@@ -878,12 +927,10 @@ __global__ void __launch_bounds__(kThreadsRes, 1) k_kron_tc_res(TcResParams p) {
           }
         }
       }
-      tc_fence_before();
-      mbar_arrive(acc_empty);
       if (p.epi_dot) {
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, o);
-        if (lane == 0) p.epi_dot[t * 4 + q] = dot;
+        if (lane == 0) p.epi_dot[t * kDotSlots + ew] = dot;
       }
     }
   }
@@ -891,7 +938,7 @@ __global__ void __launch_bounds__(kThreadsRes, 1) k_kron_tc_res(TcResParams p) {
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  if (warp == 8) {
+  if (warp == kResMmaWarp) {
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base),
                  "r"(512)
                  : "memory");

@@ -521,7 +521,7 @@ static void cg_iteration(Ctx* c, const cola_linop* op, CgBufs<T>& B, int64_t N, 
                    (float*)p_new, (float*)B.Ap, B.tile_dot, R, 1);
     B.cur ^= 1;
     B.p = p_new;
-    k_cg_alpha<<<rb, 128, 0, c->s>>>(B.st, B.tile_dot, (int)(4 * B.fused_tiles), R);
+    k_cg_alpha<<<rb, 128, 0, c->s>>>(B.st, B.tile_dot, (int)(8 * B.fused_tiles), R);
     c->count_launch();
   } else {
     apply<T>(c, op, B.p, B.Ap, R, 1.0, 0.0, 1, false, prec);
@@ -607,7 +607,7 @@ static cola_status cg_run(Ctx* c, cola_linop* op, const void* Bin, void* Xout, i
   B.beta_vec = (double*)ws.get("cg.beta", 8 * R);
   B.fused_tiles = (prec == COLA_PREC_MIXED && sizeof(T) == 4) ? kron_tc_tiles_per_rhs(op) : 0;
   if (B.fused_tiles > 0) B.pp[1] = (T*)ws.get("cg.p2", sizeof(T) * N * R);
-  B.tile_dot = B.fused_tiles > 0 ? (double*)ws.get("cg.tdot", 8 * 4 * B.fused_tiles * R) : nullptr;
+  B.tile_dot = B.fused_tiles > 0 ? (double*)ws.get("cg.tdot", 8 * 8 * B.fused_tiles * R) : nullptr;
   COLA_CUDA(cudaMemsetAsync(B.beta_vec, 0, 8 * R, c->s));
   double* bb = (double*)ws.get("cg.bb", 8 * R);
   double* rr64 = (double*)ws.get("cg.rr64", 8 * R);

@@ -548,36 +548,49 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_kron_tc(Src src, TcParams K) 
 }
 
 // ---------------------------------------------------------------------------
-// Resident-factor variant (factor sides <= 128, rows of X 16-byte aligned).
-//   warp 9      loader: the split factor image once (cp.async.bulk, stays in
-//               shared memory); then, per 64-wide k block of a tile, 64 row
-//               segments of X (and z for the fused p update) with
-//               cp.async.bulk into a multi-stage FP32 staging ring.
-//   warps 0-3   converters: thread m reads row m of the staged block, forms
-//               p = z + beta p when fused (writing p back), splits into BF16
-//               terms and stores them into a tensor-memory A stage with
-//               tcgen05.st (warp w owns TMEM lanes 32w..32w+31).
-//   warp 8      MMA: tcgen05.mma with A from tensor memory, B (factor) from
-//               shared memory; dominant / cross terms in separate accumulators.
-//   warps 4-7   epilogue, as in k_kron_tc.
-// TMEM columns: [0, n_pad) dominant accumulator, [n_pad, 2 n_pad) cross
-// terms, [256 + s * 32 tv, ...) A stage s (32 columns per BF16 term).
-constexpr int kResConvWarps = 8;
-constexpr int kResEpiWarps = 8;
-constexpr int kResMmaWarp = kResConvWarps + kResEpiWarps;   // 16
-constexpr int kResLoaderWarp = kResMmaWarp + 1;              // 17
-constexpr int kThreadsRes = 32 * (kResLoaderWarp + 1);       // 576
-constexpr int kResConvThreads = 32 * kResConvWarps;
-constexpr int kResEpiThreads = 32 * kResEpiWarps;
-constexpr uint32_t kAStageCol0 = 256;
+// Factor-stationary variant (factor sides <= 128, rows of X 16-byte aligned).
+// The mode step runs transposed, D^T[i, m] = sum_j K[i, j] X[j, m]: the split
+// factor is the MMA's A operand and stays in tensor memory for the whole
+// launch, the split X tile is the B operand in shared memory, and accumulator
+// lane i holds output i of every row m of the tile, so the 32 lanes of an
+// epilogue warp store 32 consecutive outputs of one row (128-byte stores).
+//   warp 17     loader: per 64-wide k block of a tile, the X row segments
+//               (and z for the fused p update) with cp.async.bulk into a
+//               multi-stage FP32 staging ring.
+//   warps 0-7   converters: thread (row m, k half) reads its 32 staged values,
+//               forms p = z + beta p when fused (writing p back), splits them
+//               into BF16 terms and stores the B stage (K-major rows of 64
+//               BF16, 128-byte swizzle), then fences it for the tensor core.
+//   warp 16     MMA: tcgen05.mma, A = factor term (tensor memory), B = X term
+//               (shared memory); dominant / cross terms in separate
+//               accumulators; allocates / frees tensor memory.
+//   warps 8-15  epilogue: first copy the split factor into tensor memory; per
+//               tile drain both accumulators into registers, release them,
+//               then store (with the fused shift term and p . Ap partials).
+//   warp 18     when the shift term is fused: the tile's rows of p (contiguous
+//               in the output layout) with one cp.async.bulk into shared
+//               memory, so the epilogue reads them without global latency.
+// TMEM columns: [0, 128) dominant accumulator, [128, 256) cross terms,
+// [256 + 64 t, ...) factor term t (32 columns per 64-wide k block).
+constexpr int kFsConvWarps = 8;
+constexpr int kFsEpiWarps = 8;
+constexpr int kFsMmaWarp = kFsConvWarps + kFsEpiWarps;  // 16
+constexpr int kFsLoaderWarp = kFsMmaWarp + 1;           // 17
+constexpr int kFsEpiLoaderWarp = kFsLoaderWarp + 1;     // 18
+constexpr int kThreadsFs = 32 * (kFsEpiLoaderWarp + 1); // 608
+constexpr int kFsConvThreads = 32 * kFsConvWarps;
+constexpr int kFsEpiThreads = 32 * kFsEpiWarps;
+constexpr uint32_t kFsSmallCol = 128;
+constexpr uint32_t kFsFactorCol0 = 256;
+constexpr uint32_t kFsBTermBytes = kTileM * 128;  // 128 rows x 64 BF16
 
-struct TcResParams {
+struct TcFsParams {
   const float* X;
   float* Y;
-  const uint16_t* Bimg;
+  const uint16_t* Bimg;  // split factor [tf][kblocks][n_pad][64] BF16, swizzled rows
   int64_t rest, size_in, size_out, tiles_m, ntiles;
-  int n_in, n_out, n_pad, kblocks, ksteps_last, tf, tv, xstages, nsrc;
-  uint32_t b_bytes, b_kb_bytes, x_src_bytes;
+  int n_in, n_out, n_pad, kblocks, ksteps_last, xstages, nsrc;
+  uint32_t x_src_bytes, e_bytes;  // e_bytes: staged p rows (0 without the fused shift)
   float coeff, beta;
   int* err;
   const float* pro_z;
@@ -600,11 +613,12 @@ __device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t* r) {
       : "memory");
 }
 
-__device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t* r) {
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t* v) {
   asm volatile(
-      "tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"r"(taddr),
-      "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7])
-      : "memory");
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+        "=r"(v[7])
+      : "r"(taddr));
 }
 
 __device__ __forceinline__ void mma_bf16_ta(uint32_t d_tmem, uint32_t a_tmem, uint64_t bdesc,
@@ -617,41 +631,50 @@ __device__ __forceinline__ void mma_bf16_ta(uint32_t d_tmem, uint32_t a_tmem, ui
       : "memory");
 }
 
-__global__ void __launch_bounds__(kThreadsRes, 1) k_kron_tc_res(TcResParams p) {
+template <int TF, int TV>
+__global__ void __launch_bounds__(kThreadsFs, 1) k_kron_tc_fs(TcFsParams p) {
+  constexpr int kMaxT = TF > TV ? TF : TV;
+  constexpr bool kSmall = TF > 1 || TV > 1;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
-  unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  unsigned char* bsm = base;                                         // resident factor image
-  unsigned char* xsm = base + ((p.b_bytes + 1023u) & ~1023u);         // staging ring
-  uint64_t* bars = (uint64_t*)(xsm + (size_t)p.xstages * p.nsrc * p.x_src_bytes);
-  uint64_t* bfull = bars;
-  uint64_t* xfull = bars + 1;
+  // 1024-byte aligned base for the swizzle atoms, still a shared-space pointer
+  unsigned char* base = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
+  unsigned char* bsm = base;                           // 2 B stages x TV terms
+  unsigned char* xsm = base + 2 * TV * kFsBTermBytes;  // FP32 staging ring
+  unsigned char* esm = xsm + (size_t)p.xstages * p.nsrc * p.x_src_bytes;  // p rows
+  uint64_t* bars = (uint64_t*)(esm + p.e_bytes);
+  uint64_t* xfull = bars;
   uint64_t* xempty = xfull + p.xstages;
-  uint64_t* afull = xempty + p.xstages;
-  uint64_t* aempty = afull + 2;
-  uint64_t* acc_full = aempty + 2;
-  uint64_t* acc_empty = acc_full + 1;
-  uint64_t* drain = acc_empty + 1;
-  uint32_t* tmem_slot = (uint32_t*)(drain + 1);
+  uint64_t* bfull = xempty + p.xstages;
+  uint64_t* bempty = bfull + 2;
+  uint64_t* afac = bempty + 2;
+  uint64_t* dfull = afac + 1;
+  uint64_t* dempty = dfull + 1;
+  uint64_t* drain = dempty + 1;
+  uint64_t* efull = drain + 1;
+  uint64_t* eempty = efull + 1;
+  uint32_t* tmem_slot = (uint32_t*)(eempty + 1);
   volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if (tid == 0) {
-    mbar_init(bfull, 1);
     for (int s = 0; s < p.xstages; ++s) {
       mbar_init(&xfull[s], 1);
-      mbar_init(&xempty[s], kResConvThreads);
+      mbar_init(&xempty[s], kFsConvThreads);
     }
     for (int s = 0; s < 2; ++s) {
-      mbar_init(&afull[s], kResConvThreads);
-      mbar_init(&aempty[s], 1);
+      mbar_init(&bfull[s], kFsConvThreads);
+      mbar_init(&bempty[s], 1);
     }
-    mbar_init(acc_full, 1);
-    mbar_init(acc_empty, kResEpiThreads);
+    mbar_init(afac, kFsEpiThreads);
+    mbar_init(dfull, 1);
+    mbar_init(dempty, kFsEpiThreads);
     mbar_init(drain, 1);
+    mbar_init(efull, 1);
+    mbar_init(eempty, kFsEpiThreads);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == kResMmaWarp) {
+  if (warp == kFsMmaWarp) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      smem_u32(tmem_slot)),
                  "r"(512)
@@ -662,19 +685,14 @@ __global__ void __launch_bounds__(kThreadsRes, 1) k_kron_tc_res(TcResParams p) {
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
-  const uint32_t a_cols = 32u * (uint32_t)p.tv;  // TMEM columns per A stage
 
-  if (warp == kResLoaderWarp) {
+  if (warp == kFsLoaderWarp) {
     // ---------------------------------------------------------------- loader
     bool ok = true;
     int s = 0;
     uint32_t ph = 0;
     int last_s = -1;
     uint32_t last_ph = 0;
-    if (lane == 0) {
-      mbar_arrive_expect_tx(bfull, p.b_bytes);
-      bulk_g2s(bsm, p.Bimg, p.b_bytes, bfull);
-    }
     for (int64_t t = blockIdx.x; t < p.ntiles && ok; t += gridDim.x) {
       const int64_t r = t / p.tiles_m, m0 = (t % p.tiles_m) * kTileM;
       const int64_t rows = (p.rest - m0 < kTileM) ? (p.rest - m0) : kTileM;
@@ -704,20 +722,32 @@ __global__ void __launch_bounds__(kThreadsRes, 1) k_kron_tc_res(TcResParams p) {
       }
     }
     // no bulk copy may still be landing when the CTA exits
-    if (lane == 0) {
-      mbar_wait(bfull, 0, abort_flag, p.err);
-      if (last_s >= 0) mbar_wait(&xfull[last_s], last_ph, abort_flag, p.err);
+    if (lane == 0 && last_s >= 0) mbar_wait(&xfull[last_s], last_ph, abort_flag, p.err);
+    __syncwarp();
+  } else if (warp == kFsEpiLoaderWarp) {
+    // ------------------------------------------------- p rows for the epilogue
+    if (lane == 0 && p.e_bytes) {
+      int64_t it = 0;
+      for (int64_t t = blockIdx.x; t < p.ntiles; t += gridDim.x, ++it) {
+        if (!mbar_wait(eempty, (uint32_t)(it & 1) ^ 1u, abort_flag, p.err)) break;
+        const int64_t r = t / p.tiles_m, m0 = (t % p.tiles_m) * kTileM;
+        const int64_t rows = (p.rest - m0 < kTileM) ? (p.rest - m0) : kTileM;
+        const uint32_t bytes = (uint32_t)(rows * p.n_out) * 4u;
+        mbar_arrive_expect_tx(efull, bytes);
+        bulk_g2s(esm, p.epi_x + r * p.size_out + m0 * p.n_out, bytes, efull);
+      }
+      // the last copy has landed before the CTA exits
+      if (it > 0) mbar_wait(efull, (uint32_t)((it - 1) & 1), abort_flag, p.err);
     }
     __syncwarp();
-  } else if (warp < kResConvWarps) {
+  } else if (warp < kFsConvWarps) {
     // ------------------------------------------------------------ converters
-    // warp w owns TMEM lanes 32 (w % 4) .. + 31 and the k half w / 4 of a block
     bool ok = true;
-    int s = 0, sa = 0;
-    uint32_t ph = 0, pha = 0;
-    const int quarter = warp & 3, half = warp >> 2;
+    int s = 0, sb = 0;
+    uint32_t ph = 0, phb = 0;
+    const int quarter = warp & 3, khalf = warp >> 2;
     const int row = quarter * 32 + lane;
-    const uint32_t lane_off = (uint32_t)(quarter * 32) << 16;
+    const uint32_t swz = (uint32_t)(row & 7);
     for (int64_t t = blockIdx.x; t < p.ntiles && ok; t += gridDim.x) {
       const int64_t r = t / p.tiles_m, m0 = (t % p.tiles_m) * kTileM;
       const int64_t m = m0 + row;
@@ -725,21 +755,20 @@ __global__ void __launch_bounds__(kThreadsRes, 1) k_kron_tc_res(TcResParams p) {
       const float beta_r = p.pro_z ? (float)p.pro_beta[r] : 0.0f;
       float* Pout = p.pro_out ? p.pro_out + r * p.size_in : nullptr;
       for (int kb = 0; kb < p.kblocks; ++kb) {
-        if (!mbar_wait(&aempty[sa], pha ^ 1u, abort_flag, p.err) ||
+        if (!mbar_wait(&bempty[sb], phb ^ 1u, abort_flag, p.err) ||
             !mbar_wait(&xfull[s], ph, abort_flag, p.err)) {
           ok = false;
           break;
         }
-        tc_fence_after();
-        const float* st = (const float*)(xsm + (size_t)s * p.nsrc * p.x_src_bytes);
-        const float* stz = (const float*)(xsm + (size_t)s * p.nsrc * p.x_src_bytes + p.x_src_bytes);
-        const uint32_t acol = tmem_base + lane_off + kAStageCol0 + (uint32_t)sa * a_cols;
+        const float* st = reinterpret_cast<const float*>(xsm + (size_t)s * p.nsrc * p.x_src_bytes);
+        const float* stz = st + p.x_src_bytes / 4;
+        unsigned char* brow = bsm + (size_t)sb * TV * kFsBTermBytes + (size_t)row * 128;
 #pragma unroll
-        for (int j = 0; j < 2; ++j) {  // 16 k values at a time
-          float v[16];
+        for (int j = 0; j < 4; ++j) {  // 8 k values = one 16-byte chunk per term
+          float v[8];
 #pragma unroll
-          for (int k = 0; k < 16; ++k) {
-            const int kl = half * 32 + j * 16 + k;
+          for (int e = 0; e < 8; ++e) {
+            const int kl = khalf * 32 + j * 8 + e;
             const int kk = kb * kBlockK + kl;
             const bool in = row_ok && kk < p.n_in;
             float x = in ? st[kl * kTileM + row] : 0.0f;
@@ -747,83 +776,82 @@ __global__ void __launch_bounds__(kThreadsRes, 1) k_kron_tc_res(TcResParams p) {
               x = fmaf(beta_r, x, stz[kl * kTileM + row]);
               Pout[(int64_t)kk * p.rest + m] = x;
             }
-            v[k] = x;
+            v[e] = x;
           }
-          uint32_t w[3][8];
+          uint32_t w[TV][4];
 #pragma unroll
-          for (int e = 0; e < 8; ++e) {
+          for (int e = 0; e < 4; ++e) {
             uint32_t o[3];
-            split2(v[2 * e], v[2 * e + 1], p.tv, o);
-            w[0][e] = o[0];
-            w[1][e] = o[1];
-            w[2][e] = o[2];
-          }
+            split2(v[2 * e], v[2 * e + 1], TV, o);
 #pragma unroll
-          for (int tv = 0; tv < 3; ++tv)
-            if (tv < p.tv) tmem_st8(acol + (uint32_t)(tv * 32 + half * 16 + j * 8), w[tv]);
+            for (int tv = 0; tv < TV; ++tv) w[tv][e] = o[tv];
+          }
+          const uint32_t chunk = ((uint32_t)(khalf * 4 + j) ^ swz) * 16u;
+#pragma unroll
+          for (int tv = 0; tv < TV; ++tv)
+            *reinterpret_cast<uint4*>(brow + (size_t)tv * kFsBTermBytes + chunk) =
+                make_uint4(w[tv][0], w[tv][1], w[tv][2], w[tv][3]);
         }
-        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+        fence_proxy_async();
         mbar_arrive(&xempty[s]);
-        tc_fence_before();
-        mbar_arrive(&afull[sa]);
+        mbar_arrive(&bfull[sb]);
         if (++s == p.xstages) {
           s = 0;
           ph ^= 1u;
         }
-        if (++sa == 2) {
-          sa = 0;
-          pha ^= 1u;
+        if (++sb == 2) {
+          sb = 0;
+          phb ^= 1u;
         }
       }
     }
-  } else if (warp == kResMmaWarp) {
+  } else if (warp == kFsMmaWarp) {
     // ------------------------------------------------------------------- MMA
     if (lane == 0) {
-      const uint32_t idesc = idesc_bf16(kTileM, p.n_pad);
-      const int maxt = p.tf > p.tv ? p.tf : p.tv;
-      bool ok = mbar_wait(bfull, 0, abort_flag, p.err);
+      constexpr uint32_t idesc = idesc_bf16(kTileM, kTileM);  // M = outputs, N = rows
+      bool ok = mbar_wait(afac, 0, abort_flag, p.err);
       tc_fence_after();
       const uint32_t bbase = smem_u32(bsm);
-      int sa = 0;
-      uint32_t pha = 0;
+      int sb = 0;
+      uint32_t phb = 0;
       int64_t it = 0;
       for (int64_t t = blockIdx.x; t < p.ntiles && ok; t += gridDim.x, ++it) {
-        if (!mbar_wait(acc_empty, (uint32_t)(it & 1) ^ 1u, abort_flag, p.err)) break;
+        if (!mbar_wait(dempty, (uint32_t)(it & 1) ^ 1u, abort_flag, p.err)) break;
         tc_fence_after();
-        const uint32_t d_big = tmem_base, d_small = tmem_base + (uint32_t)p.n_pad;
-        uint32_t acc_big = 0, acc_small = 0;
+        uint32_t acc_small = 0;
         for (int kb = 0; kb < p.kblocks; ++kb) {
-          if (!mbar_wait(&afull[sa], pha, abort_flag, p.err)) {
+          if (!mbar_wait(&bfull[sb], phb, abort_flag, p.err)) {
             ok = false;
             break;
           }
           tc_fence_after();
-          const uint32_t a0 = tmem_base + kAStageCol0 + (uint32_t)sa * a_cols;
           const int steps = (kb == p.kblocks - 1) ? p.ksteps_last : 4;
+          const uint32_t bst = bbase + (uint32_t)sb * (uint32_t)TV * kFsBTermBytes;
+          const uint32_t fa = tmem_base + kFsFactorCol0 + (uint32_t)kb * 32u;
           for (int kk = 0; kk < steps; ++kk) {
-            for (int ti = 0; ti < p.tf; ++ti)
-              for (int tv = 0; tv < p.tv; ++tv) {
-                if (ti + tv >= maxt) continue;
-                const uint32_t at = a0 + (uint32_t)(tv * 32 + kk * 8);
-                const uint64_t bd = sw128_desc(bbase + (uint32_t)(ti * p.kblocks + kb) *
-                                                           p.b_kb_bytes + (uint32_t)kk * 32u);
+#pragma unroll
+            for (int ti = 0; ti < TF; ++ti)
+#pragma unroll
+              for (int tv = 0; tv < TV; ++tv) {
+                if (ti + tv >= kMaxT) continue;
+                const uint32_t a = fa + (uint32_t)(ti * 64 + kk * 8);
+                const uint64_t bd = sw128_desc(bst + (uint32_t)tv * kFsBTermBytes + (uint32_t)kk * 32u);
                 if (ti == 0 && tv == 0) {
-                  mma_bf16_ta(d_big, at, bd, idesc, acc_big);
-                  acc_big = 1;
+                  mma_bf16_ta(tmem_base, a, bd, idesc, (kb | kk) ? 1u : 0u);
                 } else {
-                  mma_bf16_ta(d_small, at, bd, idesc, acc_small);
+                  mma_bf16_ta(tmem_base + kFsSmallCol, a, bd, idesc, acc_small);
                   acc_small = 1;
                 }
               }
           }
-          mma_commit(&aempty[sa]);
-          if (++sa == 2) {
-            sa = 0;
-            pha ^= 1u;
+          mma_commit(&bempty[sb]);
+          if (++sb == 2) {
+            sb = 0;
+            phb ^= 1u;
           }
         }
         if (!ok) break;
-        mma_commit(acc_full);
+        mma_commit(dfull);
       }
       mma_commit(drain);
       mbar_wait(drain, 0, abort_flag, p.err);
@@ -831,106 +859,105 @@ __global__ void __launch_bounds__(kThreadsRes, 1) k_kron_tc_res(TcResParams p) {
     __syncwarp();
   } else {
     // -------------------------------------------------------------- epilogue
-    // warp w reads TMEM lanes 32 (w % 4) .. + 31 and the column half (w - 8) / 4;
-    // it drains its 64 columns into registers, releases the accumulator, and
-    // only then stores, so the next tile's MMAs do not wait for global stores.
-    const int ew = warp - kResConvWarps;
+    const int ew = warp - kFsConvWarps;
     const int quarter = warp & 3, chalf = ew >> 2;
-    const int row = quarter * 32 + lane;
-    const int c_begin = chalf * 64;
-    const bool has_small = (p.tf > 1 || p.tv > 1);
-    int64_t it = 0;
-    for (int64_t t = blockIdx.x; t < p.ntiles; t += gridDim.x, ++it) {
-      if (!mbar_wait(acc_full, (uint32_t)(it & 1), abort_flag, p.err)) break;
-      tc_fence_after();
-      const int64_t r = t / p.tiles_m, m0 = (t % p.tiles_m) * kTileM;
-      const int64_t m = m0 + row;
-      const uint32_t taddr = tmem_base + ((uint32_t)(quarter * 32) << 16);
-      float a[64];
+    const int i = quarter * 32 + lane;  // output index = TMEM lane
+    const uint32_t lane_off = (uint32_t)(quarter * 32) << 16;
+    // the split factor: k block `chalf` of every term, row i (unswizzled)
+    if (chalf < p.kblocks) {
 #pragma unroll
-      for (int q8 = 0; q8 < 8; ++q8) {
-        const int c0 = c_begin + q8 * 8;
-        uint32_t v[8], w[8];
-        if (c0 < p.n_pad) {
-          asm volatile(
-              "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
-              : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]),
-                "=r"(v[6]), "=r"(v[7])
-              : "r"(taddr + (uint32_t)c0));
-          if (has_small) {
-            asm volatile(
-                "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
-                : "=r"(w[0]), "=r"(w[1]), "=r"(w[2]), "=r"(w[3]), "=r"(w[4]), "=r"(w[5]),
-                  "=r"(w[6]), "=r"(w[7])
-                : "r"(taddr + (uint32_t)(p.n_pad + c0)));
-          }
-          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      for (int ti = 0; ti < TF; ++ti) {
 #pragma unroll
-          for (int e = 0; e < 8; ++e)
-            a[q8 * 8 + e] = p.coeff * (__uint_as_float(v[e]) +
-                                       (has_small ? __uint_as_float(w[e]) : 0.0f));
-        } else {
+        for (int hh = 0; hh < 2; ++hh) {
+          uint32_t u[16];
+          if (i < p.n_pad) {
+            const uint4* src = reinterpret_cast<const uint4*>(
+                p.Bimg + ((size_t)(ti * p.kblocks + chalf) * p.n_pad + i) * kBlockK);
 #pragma unroll
-          for (int e = 0; e < 8; ++e) a[q8 * 8 + e] = 0.0f;
-        }
-      }
-      tc_fence_before();
-      mbar_arrive(acc_empty);
-      // stores (and the fused shift / p . Ap partial) from registers
-      float* yrow = p.Y + r * p.size_out + m * p.n_out;
-      const bool vec_ok = ((reinterpret_cast<uintptr_t>(yrow) & 15u) == 0);
-      const float* xrow = p.epi_x ? p.epi_x + r * p.size_out + m * p.n_out : nullptr;
-      const int64_t dbase = m * p.n_out;
-      double dot = 0.0;
-      if (m < p.rest) {
-#pragma unroll
-        for (int q4 = 0; q4 < 4; ++q4) {
-          const int c0 = c_begin + q4 * 16;
-          if (c0 >= p.n_out) break;
-          if (xrow) {
-#pragma unroll
-            for (int e = 0; e < 16; ++e) {
-              const int i = c0 + e;
-              if (i < p.n_out) {
-                const float xd = xrow[i];
-                const float dv = p.epi_dstride ? p.epi_d[dbase + i] : p.epi_d[0];
-                a[q4 * 16 + e] = fmaf(p.epi_coeff * dv, xd, a[q4 * 16 + e]);
-                if (p.beta == 0.0f) dot += (double)(a[q4 * 16 + e] * xd);
-              }
-            }
-          }
-          if (c0 + 16 <= p.n_out && vec_ok) {
-#pragma unroll
-            for (int e = 0; e < 16; e += 4) {
-              float4 o = make_float4(a[q4 * 16 + e], a[q4 * 16 + e + 1], a[q4 * 16 + e + 2],
-                                     a[q4 * 16 + e + 3]);
-              float4* dst = reinterpret_cast<float4*>(yrow + c0 + e);
-              if (p.beta != 0.0f) {
-                const float4 old = *dst;
-                o.x += p.beta * old.x;
-                o.y += p.beta * old.y;
-                o.z += p.beta * old.z;
-                o.w += p.beta * old.w;
-              }
-              *dst = o;
+            for (int c = 0; c < 4; ++c) {
+              const uint4 q = __ldg(src + ((hh * 4 + c) ^ (i & 7)));
+              u[4 * c] = q.x;
+              u[4 * c + 1] = q.y;
+              u[4 * c + 2] = q.z;
+              u[4 * c + 3] = q.w;
             }
           } else {
 #pragma unroll
-            for (int e = 0; e < 16; ++e) {
-              const int i = c0 + e;
-              if (i < p.n_out) {
-                float o = a[q4 * 16 + e];
-                if (p.beta != 0.0f) o += p.beta * yrow[i];
-                yrow[i] = o;
+            for (int c = 0; c < 16; ++c) u[c] = 0u;
+          }
+          tmem_st16(tmem_base + lane_off + kFsFactorCol0 + (uint32_t)(ti * 64 + chalf * 32 + hh * 16), u);
+        }
+      }
+      asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    mbar_arrive(afac);
+    int64_t it = 0;
+    for (int64_t t = blockIdx.x; t < p.ntiles; t += gridDim.x, ++it) {
+      if (!mbar_wait(dfull, (uint32_t)(it & 1), abort_flag, p.err)) break;
+      tc_fence_after();
+      const int64_t r = t / p.tiles_m, m0 = (t % p.tiles_m) * kTileM;
+      const uint32_t taddr = tmem_base + lane_off + (uint32_t)(chalf * 64);
+      float a[64];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        uint32_t v[8], w[8];
+        tmem_ld8(taddr + (uint32_t)(q * 8), v);
+        if (kSmall) tmem_ld8(taddr + kFsSmallCol + (uint32_t)(q * 8), w);
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+        for (int e = 0; e < 8; ++e)
+          a[q * 8 + e] =
+              p.coeff * (__uint_as_float(v[e]) + (kSmall ? __uint_as_float(w[e]) : 0.0f));
+      }
+      tc_fence_before();
+      mbar_arrive(dempty);
+      // row m = mbase + c of the tile, output i: 32 lanes write 128 contiguous bytes
+      const int64_t mbase = m0 + chalf * 64;
+      const int nrows = (int)((p.rest - mbase < 64) ? (p.rest - mbase) : 64);
+      const bool fused = p.e_bytes != 0;
+      if (fused && !mbar_wait(efull, (uint32_t)(it & 1), abort_flag, p.err)) break;
+      float part = 0.0f;  // this thread's <= 64 products of p . Ap
+      if (i < p.n_out && nrows > 0) {
+        const int64_t ld = p.n_out;
+        float* yp = p.Y + r * p.size_out + mbase * ld + i;
+        const float* es = reinterpret_cast<const float*>(esm) + chalf * 64 * ld + i;
+        const float* dp = p.epi_dstride ? p.epi_d + mbase * ld + i : nullptr;
+        const float d0 = (fused && !dp) ? p.epi_d[0] : 0.0f;
+        if (p.beta == 0.0f && !dp) {
+#pragma unroll
+          for (int c = 0; c < 64; ++c) {
+            if (c < nrows) {
+              float v = a[c];
+              if (fused) {
+                const float xd = es[c * ld];
+                v = fmaf(p.epi_coeff * d0, xd, v);
+                part = fmaf(v, xd, part);
               }
+              yp[c * ld] = v;
             }
+          }
+        } else {  // general diagonal or beta != 0 (not on the CG path)
+#pragma unroll
+          for (int c = 0; c < 64; ++c) {
+            if (c >= nrows) break;
+            float v = a[c];
+            if (fused) {
+              const float xd = es[c * ld];
+              v = fmaf(p.epi_coeff * (dp ? dp[c * ld] : d0), xd, v);
+              part = fmaf(v, xd, part);
+            }
+            if (p.beta != 0.0f) v = fmaf(p.beta, yp[c * ld], v);
+            yp[c * ld] = v;
           }
         }
       }
+      if (fused) mbar_arrive(eempty);
+      double dsum = (double)part;
       if (p.epi_dot) {
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, o);
-        if (lane == 0) p.epi_dot[t * kDotSlots + ew] = dot;
+        for (int o = 16; o > 0; o >>= 1) dsum += __shfl_xor_sync(0xffffffffu, dsum, o);
+        if (lane == 0) p.epi_dot[t * kDotSlots + ew] = dsum;
       }
     }
   }
@@ -938,7 +965,7 @@ __global__ void __launch_bounds__(kThreadsRes, 1) k_kron_tc_res(TcResParams p) {
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  if (warp == kResMmaWarp) {
+  if (warp == kFsMmaWarp) {
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base),
                  "r"(512)
                  : "memory");
@@ -1094,19 +1121,18 @@ void kron_tc_apply<double>(Ctx*, const cola_linop*, const double*, double*, int6
 
 constexpr size_t kSmemMax = 232448;  // 227 KB opt-in dynamic shared memory per CTA
 
-static size_t res_smem(const TcResParams& r) {
-  const size_t b = ((size_t)r.b_bytes + 1023) & ~(size_t)1023;
-  return 1024 + b + (size_t)r.xstages * r.nsrc * r.x_src_bytes + 512;
+static size_t fs_smem(const TcFsParams& r, int tv) {
+  return 1024 + 2 * (size_t)tv * kFsBTermBytes + (size_t)r.xstages * r.nsrc * r.x_src_bytes +
+         r.e_bytes + 256;
 }
 
-// Resident-factor plan: factor sides <= 128 (two 64-wide k blocks), the split
-// factor image within 96 KB, and X rows 16-byte aligned for cp.async.bulk.
-static bool res_plan(const TcParams& p, TcResParams& r) {
-  if (p.nchunks != 1 || p.n_pad > 128 || p.kblocks > 2) return false;
-  const uint32_t b_bytes = (uint32_t)p.tf * (uint32_t)p.kblocks * (uint32_t)p.n_pad * 128u;
-  if (b_bytes > 96u * 1024u) return false;
+// Factor-stationary plan: factor sides <= 128 (two 64-wide k blocks, one
+// output chunk) and X rows 16-byte aligned for cp.async.bulk.
+static bool fs_plan(const TcParams& p, TcFsParams& r) {
+  if (p.nchunks != 1 || p.n_pad > kTileM || p.kblocks > 2) return false;
   if (p.rest % 4 != 0 || p.size_in % 4 != 0) return false;
   if (((uintptr_t)p.X & 15u) != 0 || (p.pro_z && ((uintptr_t)p.pro_z & 15u) != 0)) return false;
+  if (p.epi_x && (((uintptr_t)p.epi_x & 15u) != 0 || p.size_out % 4 != 0)) return false;
   r.X = p.X;
   r.Y = p.Y;
   r.Bimg = p.Bimg;
@@ -1120,14 +1146,11 @@ static bool res_plan(const TcParams& p, TcResParams& r) {
   r.n_pad = p.n_pad;
   r.kblocks = p.kblocks;
   r.ksteps_last = p.ksteps_last;
-  r.tf = p.tf;
-  r.tv = p.tv;
   r.nsrc = p.pro_z ? 2 : 1;
-  r.b_bytes = b_bytes;
-  r.b_kb_bytes = (uint32_t)p.n_pad * 128u;
   r.x_src_bytes = (uint32_t)kBlockK * kTileM * 4u;
-  const size_t b_round = ((size_t)b_bytes + 1023) & ~(size_t)1023;
-  const size_t avail = kSmemMax - 1024 - 512 - b_round;
+  r.e_bytes = p.epi_x ? (uint32_t)kTileM * (uint32_t)p.n_out * 4u : 0u;
+  r.e_bytes = (r.e_bytes + 1023u) & ~1023u;
+  const size_t avail = kSmemMax - 1024 - 256 - 2 * (size_t)p.tv * kFsBTermBytes - r.e_bytes;
   r.xstages = (int)std::min<size_t>(4, avail / ((size_t)r.nsrc * r.x_src_bytes));
   if (r.xstages < 2) return false;
   r.coeff = p.coeff;
@@ -1142,6 +1165,15 @@ static bool res_plan(const TcParams& p, TcResParams& r) {
   r.epi_coeff = p.epi_coeff;
   r.epi_dot = p.epi_dot;
   return true;
+}
+
+using FsKernel = void (*)(TcFsParams);
+static FsKernel fs_kernel(int tf, int tv) {
+  static const FsKernel tab[3][3] = {
+      {k_kron_tc_fs<1, 1>, k_kron_tc_fs<1, 2>, k_kron_tc_fs<1, 3>},
+      {k_kron_tc_fs<2, 1>, k_kron_tc_fs<2, 2>, k_kron_tc_fs<2, 3>},
+      {k_kron_tc_fs<3, 1>, k_kron_tc_fs<3, 2>, k_kron_tc_fs<3, 3>}};
+  return tab[tf - 1][tv - 1];
 }
 
 struct TcFusion {
@@ -1231,15 +1263,16 @@ static int64_t kron_tc_run(Ctx* c, const cola_linop* op, const float* X, float* 
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
       COLA_CUDA(cudaFuncSetAttribute(k_kron_tc<ProbTable>,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
-      COLA_CUDA(cudaFuncSetAttribute(k_kron_tc_res, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     kSmemMax));
+      for (int a = 1; a <= 3; ++a)
+        for (int b = 1; b <= 3; ++b)
+          COLA_CUDA(cudaFuncSetAttribute(fs_kernel(a, b),
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemMax));
       attr_set[c->device] = true;
     }
     const int grid = (int)std::min<int64_t>(p.ntiles, c->num_sms);
-    TcResParams rp{};
-    if (res_plan(p, rp)) {
-      const size_t smem = res_smem(rp);
-      k_kron_tc_res<<<grid, kThreadsRes, smem, c->s>>>(rp);
+    TcFsParams rp{};
+    if (fs_plan(p, rp)) {
+      fs_kernel(tf, tv)<<<grid, kThreadsFs, fs_smem(rp, tv), c->s>>>(rp);
     } else {
       k_kron_tc<OneProb><<<grid, kThreadsTc, q.smem, c->s>>>(OneProb{p}, p);
     }

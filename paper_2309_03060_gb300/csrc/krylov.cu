@@ -60,16 +60,19 @@ __device__ __forceinline__ double block_sum2(T v, double* out_other, T v2) {
 }
 
 // alpha = r^T z / p^T A p, with p^T A p the ordered sum of nparts partials.
-__global__ void k_cg_alpha(CgState* st, const double* parts, int nparts, int64_t R) {
-  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= R) return;
+// One block per right-hand side: p^T A p from its partial sums, alpha = r^T z / p^T A p.
+__global__ void k_cg_alpha(CgState* st, const double* parts, int nparts) {
+  const int64_t r = blockIdx.x;
   CgState& s = st[r];
   if (!s.active) {
-    s.alpha = 0.0;
+    if (threadIdx.x == 0) s.alpha = 0.0;
     return;
   }
   double v = 0.0;
-  for (int j = 0; j < nparts; ++j) v += parts[r * nparts + j];
+  for (int j = threadIdx.x; j < nparts; j += blockDim.x) v += parts[r * nparts + j];
+  double unused;
+  v = block_sum2(v, &unused, 0.0);
+  if (threadIdx.x != 0) return;
   s.pAp = v;
   if (!(v > 0.0) || !isfinite(v)) {
     s.status = COLA_ERR_BREAKDOWN;
@@ -116,21 +119,25 @@ __global__ void k_cg_xr(int64_t n, T* x, T* r, const T* p, const T* Ap, const T*
   }
 }
 
+// One block per right-hand side: the new r^T z and r^T r, beta, and the stopping rule.
 __global__ void k_cg_beta(CgState* st, const double* part_rz, const double* part_rr, int nblk,
-                          int64_t R, double delta2, int refine, double* beta_out) {
-  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= R) return;
+                          double delta2, int refine, double* beta_out) {
+  const int64_t r = blockIdx.x;
   CgState& s = st[r];
   if (!s.active) {
-    s.beta = 0.0;
-    if (beta_out) beta_out[r] = 0.0;
+    if (threadIdx.x == 0) {
+      s.beta = 0.0;
+      if (beta_out) beta_out[r] = 0.0;
+    }
     return;
   }
   double rz = 0.0, rr = 0.0;
-  for (int b = 0; b < nblk; ++b) {
+  for (int b = threadIdx.x; b < nblk; b += blockDim.x) {
     rz += part_rz[r * nblk + b];
     rr += part_rr[r * nblk + b];
   }
+  rz = block_sum2(rz, &rr, rr);
+  if (threadIdx.x != 0) return;
   s.beta = rz / s.rz;
   s.rz = rz;
   s.rr = rr;
@@ -512,7 +519,6 @@ static std::string key_of(const char* what, const cola_linop* op, int64_t R, int
 template <typename T>
 static void cg_iteration(Ctx* c, const cola_linop* op, CgBufs<T>& B, int64_t N, int64_t R,
                          int nblk, int prec, double delta2, int refine) {
-  const unsigned rb = (unsigned)((R + 127) / 128);
   if (B.fused_tiles > 0) {
     // p_new = z + beta p_old (first mode step), Ap and p^T A p partials (last)
     T* p_old = B.pp[B.cur];
@@ -521,19 +527,19 @@ static void cg_iteration(Ctx* c, const cola_linop* op, CgBufs<T>& B, int64_t N, 
                    (float*)p_new, (float*)B.Ap, B.tile_dot, R, 1);
     B.cur ^= 1;
     B.p = p_new;
-    k_cg_alpha<<<rb, 128, 0, c->s>>>(B.st, B.tile_dot, (int)(8 * B.fused_tiles), R);
+    k_cg_alpha<<<(unsigned)R, 256, 0, c->s>>>(B.st, B.tile_dot, (int)(8 * B.fused_tiles));
     c->count_launch();
   } else {
     apply<T>(c, op, B.p, B.Ap, R, 1.0, 0.0, 1, false, prec);
     dots<T>(c, B.p, B.Ap, N, R, B.dotp, B.dotv);
-    k_cg_alpha<<<rb, 128, 0, c->s>>>(B.st, B.dotv, 1, R);
+    k_cg_alpha<<<(unsigned)R, 32, 0, c->s>>>(B.st, B.dotv, 1);
     c->count_launch();
   }
   k_cg_xr<T><<<rows_grid(N, R, nblk), 256, 0, c->s>>>(N, B.x, B.r, B.p, B.Ap, B.invd,
                                                        B.invd ? B.z : nullptr, B.st, nblk,
                                                        B.part_rz, B.part_rr);
   c->count_launch();
-  k_cg_beta<<<rb, 128, 0, c->s>>>(B.st, B.part_rz, B.part_rr, nblk, R, delta2, refine,
+  k_cg_beta<<<(unsigned)R, 256, 0, c->s>>>(B.st, B.part_rz, B.part_rr, nblk, delta2, refine,
                                   B.beta_vec);
   c->count_launch();
   if (B.fused_tiles <= 0) {

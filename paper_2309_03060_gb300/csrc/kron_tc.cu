@@ -22,12 +22,14 @@
 // Accumulators are double-buffered in TMEM so the epilogue of one tile
 // overlaps the MMAs of the next.  Every mbarrier wait gives up after ~2 s,
 // raises an error flag and lets the CTA drain and free its TMEM.
+#include <cuda.h>  // CUtensorMap (types only; the encoder comes from the runtime's entry point)
 #include <cuda_bf16.h>
 
 #include <stdio.h>
 
 #include <algorithm>
 #include <map>
+#include <mutex>
 #include <string>
 
 #include "internal.h"
@@ -554,9 +556,9 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_kron_tc(Src src, TcParams K) 
 // launch, the split X tile is the B operand in shared memory, and accumulator
 // lane i holds output i of every row m of the tile, so the 32 lanes of an
 // epilogue warp store 32 consecutive outputs of one row (128-byte stores).
-//   warp 17     loader: per 64-wide k block of a tile, the X row segments
-//               (and z for the fused p update) with cp.async.bulk into a
-//               multi-stage FP32 staging ring.
+//   warp 17     loader: per 64-wide k block of a tile, one 2-D TMA copy of the
+//               64 x 128 FP32 block of X (and one of z for the fused p update)
+//               into a multi-stage staging ring.
 //   warps 0-7   converters: thread (row m, k half) reads its 32 staged values,
 //               forms p = z + beta p when fused (writing p back), splits them
 //               into BF16 terms and stores the B stage (K-major rows of 64
@@ -585,6 +587,8 @@ constexpr uint32_t kFsFactorCol0 = 256;
 constexpr uint32_t kFsBTermBytes = kTileM * 128;  // 128 rows x 64 BF16
 
 struct TcFsParams {
+  CUtensorMap tm_x;  // X as [R * n_in rows][rest], box 64 rows x 128
+  CUtensorMap tm_z;  // z, same shape (fused p update only)
   const float* X;
   float* Y;
   const uint16_t* Bimg;  // split factor [tf][kblocks][n_pad][64] BF16, swizzled rows
@@ -631,8 +635,18 @@ __device__ __forceinline__ void mma_bf16_ta(uint32_t d_tmem, uint32_t a_tmem, ui
       : "memory");
 }
 
+// 2-D tiled TMA load of the box at (x, y) of a tensor map into shared memory.
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y,
+                                            uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+
 template <int TF, int TV>
-__global__ void __launch_bounds__(kThreadsFs, 1) k_kron_tc_fs(TcFsParams p) {
+__global__ void __launch_bounds__(kThreadsFs, 1) k_kron_tc_fs(const __grid_constant__ TcFsParams p) {
   constexpr int kMaxT = TF > TV ? TF : TV;
   constexpr bool kSmall = TF > 1 || TV > 1;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -695,24 +709,21 @@ __global__ void __launch_bounds__(kThreadsFs, 1) k_kron_tc_fs(TcFsParams p) {
     uint32_t last_ph = 0;
     for (int64_t t = blockIdx.x; t < p.ntiles && ok; t += gridDim.x) {
       const int64_t r = t / p.tiles_m, m0 = (t % p.tiles_m) * kTileM;
-      const int64_t rows = (p.rest - m0 < kTileM) ? (p.rest - m0) : kTileM;
-      const uint32_t seg = (uint32_t)rows * 4u;
       for (int kb = 0; kb < p.kblocks; ++kb) {
         if (!mbar_wait(&xempty[s], ph ^ 1u, abort_flag, p.err)) {
           ok = false;
           break;
         }
-        const int kvalid = min(kBlockK, p.n_in - kb * kBlockK);
-        if (lane == 0) mbar_arrive_expect_tx(&xfull[s], seg * (uint32_t)kvalid * (uint32_t)p.nsrc);
-        __syncwarp();
-        unsigned char* st = xsm + (size_t)s * p.nsrc * p.x_src_bytes;
-        for (int k = lane; k < kvalid; k += 32) {
-          const int64_t off = r * p.size_in + (int64_t)(kb * kBlockK + k) * p.rest + m0;
-          bulk_g2s(st + (size_t)k * (kTileM * 4), p.X + off, seg, &xfull[s]);
-          if (p.nsrc > 1)
-            bulk_g2s(st + p.x_src_bytes + (size_t)k * (kTileM * 4), p.pro_z + off, seg,
-                     &xfull[s]);
+        // rows past n_in or columns past rest arrive as zeros or as another
+        // right-hand side's rows; the converters mask both
+        if (lane == 0) {
+          unsigned char* st = xsm + (size_t)s * p.nsrc * p.x_src_bytes;
+          const int y = (int)(r * p.n_in) + kb * kBlockK;
+          mbar_arrive_expect_tx(&xfull[s], p.x_src_bytes * (uint32_t)p.nsrc);
+          tma_load_2d(st, &p.tm_x, (int)m0, y, &xfull[s]);
+          if (p.nsrc > 1) tma_load_2d(st + p.x_src_bytes, &p.tm_z, (int)m0, y, &xfull[s]);
         }
+        __syncwarp();
         last_s = s;
         last_ph = ph;
         if (++s == p.xstages) {
@@ -1121,6 +1132,39 @@ void kron_tc_apply<double>(Ctx*, const cola_linop*, const double*, double*, int6
 
 constexpr size_t kSmemMax = 232448;  // 227 KB opt-in dynamic shared memory per CTA
 
+// cuTensorMapEncodeTiled from the driver through the runtime (no libcuda link).
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                   const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                   const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                   CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+static EncodeTiledFn encode_tiled() {
+  static EncodeTiledFn fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(f);
+  });
+  return fn;
+}
+
+// FP32 matrix [rows][cols] (row stride cols), box 64 rows x 128 columns; reads
+// outside the matrix return zeros.
+static bool tmap_rows(CUtensorMap* m, const float* base, int64_t rows, int64_t cols) {
+  EncodeTiledFn enc = encode_tiled();
+  if (!enc) return false;
+  const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)cols * 4};
+  const cuuint32_t box[2] = {(cuuint32_t)kTileM, (cuuint32_t)kBlockK};
+  const cuuint32_t estr[2] = {1, 1};
+  return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(base), dims, strides, box,
+             estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 static size_t fs_smem(const TcFsParams& r, int tv) {
   return 1024 + 2 * (size_t)tv * kFsBTermBytes + (size_t)r.xstages * r.nsrc * r.x_src_bytes +
          r.e_bytes + 256;
@@ -1133,6 +1177,9 @@ static bool fs_plan(const TcParams& p, TcFsParams& r) {
   if (p.rest % 4 != 0 || p.size_in % 4 != 0) return false;
   if (((uintptr_t)p.X & 15u) != 0 || (p.pro_z && ((uintptr_t)p.pro_z & 15u) != 0)) return false;
   if (p.epi_x && (((uintptr_t)p.epi_x & 15u) != 0 || p.size_out % 4 != 0)) return false;
+  const int64_t xrows = p.batch * p.n_in;
+  if (!tmap_rows(&r.tm_x, p.X, xrows, p.rest)) return false;
+  if (p.pro_z && !tmap_rows(&r.tm_z, p.pro_z, xrows, p.rest)) return false;
   r.X = p.X;
   r.Y = p.Y;
   r.Bimg = p.Bimg;

@@ -119,9 +119,8 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
 
 // Bounded wait: false when the phase did not complete within kWaitNs or
 // another role of the CTA already gave up.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
-                                          int* err) {
-  if (mbar_try_wait(bar, parity)) return true;
+__device__ __noinline__ bool mbar_wait_slow(uint64_t* bar, uint32_t parity,
+                                            volatile int* abort_flag, int* err) {
   const uint64_t t0 = now_ns();
   for (uint32_t i = 1;; ++i) {
     if (mbar_try_wait(bar, parity)) return true;
@@ -134,6 +133,12 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volati
       }
     }
   }
+}
+
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
+                                          int* err) {
+  if (mbar_try_wait(bar, parity)) return true;
+  return mbar_wait_slow(bar, parity, abort_flag, err);
 }
 
 __device__ __forceinline__ void fence_proxy_async() {
@@ -589,21 +594,18 @@ constexpr uint32_t kFsBTermBytes = kTileM * 128;  // 128 rows x 64 BF16
 struct TcFsParams {
   CUtensorMap tm_x;  // X as [R * n_in rows][rest], box 64 rows x 128
   CUtensorMap tm_z;  // z, same shape (fused p update only)
-  const float* X;
-  float* Y;
   const uint16_t* Bimg;  // split factor [tf][kblocks][n_pad][64] BF16, swizzled rows
+  float* Y;
   int64_t rest, size_in, size_out, tiles_m, ntiles;
   int n_in, n_out, n_pad, kblocks, ksteps_last, xstages, nsrc;
-  uint32_t x_src_bytes, e_bytes;  // e_bytes: staged p rows (0 without the fused shift)
-  float coeff, beta;
+  int e_mode;  // epilogue: 0 store; 1 fused shift term and p . Ap partials; 2 add beta Y
+  uint32_t x_src_bytes, e_bytes;  // e_bytes: rows staged per tile for e_mode 1 and 2
+  const float* e_src;             // staged rows: p (e_mode 1) or the old Y (e_mode 2)
+  float coeff, beta, e_coeff;     // e_coeff: coefficient of the shift term (e_mode 1)
+  const float* e_d;               // its diagonal value, d[0] (device)
   int* err;
-  const float* pro_z;
   const double* pro_beta;
   float* pro_out;
-  const float* epi_x;
-  const float* epi_d;
-  int64_t epi_dstride;
-  float epi_coeff;
   double* epi_dot;
 };
 
@@ -645,6 +647,70 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, i
       : "memory");
 }
 
+// Converts this thread's 32 values of one staged 64-wide k block (row `row`,
+// k half `khalf`) into TV BF16 terms: logical 16-byte chunk c of the row goes
+// to chunk position c ^ (row & 7) of each term's B stage.  NSRC == 2 first
+// forms p = z + beta_r p and writes it to Pout (row m of p, k stride `rest`).
+// FULL: the row and the whole block are in range, nothing is masked.
+template <int TV, int NSRC, bool FULL>
+__device__ __forceinline__ void fs_convert(const float* st, const float* stz, unsigned char* brow,
+                                           int row, int khalf, int kbase, int n_in, bool row_ok,
+                                           float beta_r, float* Pout, int64_t rest) {
+  const uint32_t swz = (uint32_t)(row & 7);
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    float v[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      const int kl = khalf * 32 + j * 8 + e;
+      const bool in = FULL || (row_ok && kbase + kl < n_in);
+      float x = in ? st[kl * kTileM + row] : 0.0f;
+      if (NSRC > 1 && in) {
+        x = fmaf(beta_r, x, stz[kl * kTileM + row]);
+        Pout[(int64_t)(kbase + kl) * rest] = x;
+      }
+      v[e] = x;
+    }
+    uint32_t w[TV][4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      uint32_t o[3];
+      split2(v[2 * e], v[2 * e + 1], TV, o);
+#pragma unroll
+      for (int tv = 0; tv < TV; ++tv) w[tv][e] = o[tv];
+    }
+    const uint32_t chunk = ((uint32_t)(khalf * 4 + j) ^ swz) * 16u;
+#pragma unroll
+    for (int tv = 0; tv < TV; ++tv)
+      *reinterpret_cast<uint4*>(brow + (size_t)tv * kFsBTermBytes + chunk) =
+          make_uint4(w[tv][0], w[tv][1], w[tv][2], w[tv][3]);
+  }
+}
+
+// Stores this thread's 64 outputs (rows c < nrows of its column half, output
+// i): y = a (MODE 0), y = a + sc x with the partial sum of y x (MODE 1, x the
+// staged p), y = a + sc y_old (MODE 2, y_old staged).
+template <int MODE>
+__device__ __forceinline__ float fs_store(const float (&a)[64], float* yp, const float* es,
+                                          int64_t ld, int nrows, float sc) {
+  float part = 0.0f;
+#pragma unroll
+  for (int c = 0; c < 64; ++c) {
+    if (c < nrows) {
+      float v = a[c];
+      if (MODE == 1) {
+        const float xd = es[c * ld];
+        v = fmaf(sc, xd, v);
+        part = fmaf(v, xd, part);
+      } else if (MODE == 2) {
+        v = fmaf(sc, es[c * ld], v);
+      }
+      yp[c * ld] = v;
+    }
+  }
+  return part;
+}
+
 template <int TF, int TV>
 __global__ void __launch_bounds__(kThreadsFs, 1) k_kron_tc_fs(const __grid_constant__ TcFsParams p) {
   constexpr int kMaxT = TF > TV ? TF : TV;
@@ -654,7 +720,7 @@ __global__ void __launch_bounds__(kThreadsFs, 1) k_kron_tc_fs(const __grid_const
   unsigned char* base = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
   unsigned char* bsm = base;                           // 2 B stages x TV terms
   unsigned char* xsm = base + 2 * TV * kFsBTermBytes;  // FP32 staging ring
-  unsigned char* esm = xsm + (size_t)p.xstages * p.nsrc * p.x_src_bytes;  // p rows
+  unsigned char* esm = xsm + (size_t)p.xstages * p.nsrc * p.x_src_bytes;  // epilogue rows
   uint64_t* bars = (uint64_t*)(esm + p.e_bytes);
   uint64_t* xfull = bars;
   uint64_t* xempty = xfull + p.xstages;
@@ -736,7 +802,7 @@ __global__ void __launch_bounds__(kThreadsFs, 1) k_kron_tc_fs(const __grid_const
     if (lane == 0 && last_s >= 0) mbar_wait(&xfull[last_s], last_ph, abort_flag, p.err);
     __syncwarp();
   } else if (warp == kFsEpiLoaderWarp) {
-    // ------------------------------------------------- p rows for the epilogue
+    // ------------------------------------------------ rows for the epilogue
     if (lane == 0 && p.e_bytes) {
       int64_t it = 0;
       for (int64_t t = blockIdx.x; t < p.ntiles; t += gridDim.x, ++it) {
@@ -745,7 +811,7 @@ __global__ void __launch_bounds__(kThreadsFs, 1) k_kron_tc_fs(const __grid_const
         const int64_t rows = (p.rest - m0 < kTileM) ? (p.rest - m0) : kTileM;
         const uint32_t bytes = (uint32_t)(rows * p.n_out) * 4u;
         mbar_arrive_expect_tx(efull, bytes);
-        bulk_g2s(esm, p.epi_x + r * p.size_out + m0 * p.n_out, bytes, efull);
+        bulk_g2s(esm, p.e_src + r * p.size_out + m0 * p.n_out, bytes, efull);
       }
       // the last copy has landed before the CTA exits
       if (it > 0) mbar_wait(efull, (uint32_t)((it - 1) & 1), abort_flag, p.err);
@@ -758,13 +824,12 @@ __global__ void __launch_bounds__(kThreadsFs, 1) k_kron_tc_fs(const __grid_const
     uint32_t ph = 0, phb = 0;
     const int quarter = warp & 3, khalf = warp >> 2;
     const int row = quarter * 32 + lane;
-    const uint32_t swz = (uint32_t)(row & 7);
     for (int64_t t = blockIdx.x; t < p.ntiles && ok; t += gridDim.x) {
       const int64_t r = t / p.tiles_m, m0 = (t % p.tiles_m) * kTileM;
       const int64_t m = m0 + row;
       const bool row_ok = m < p.rest;
-      const float beta_r = p.pro_z ? (float)p.pro_beta[r] : 0.0f;
-      float* Pout = p.pro_out ? p.pro_out + r * p.size_in : nullptr;
+      const float beta_r = p.nsrc > 1 ? (float)p.pro_beta[r] : 0.0f;
+      float* Pout = p.nsrc > 1 ? p.pro_out + r * p.size_in + m : nullptr;
       for (int kb = 0; kb < p.kblocks; ++kb) {
         if (!mbar_wait(&bempty[sb], phb ^ 1u, abort_flag, p.err) ||
             !mbar_wait(&xfull[s], ph, abort_flag, p.err)) {
@@ -774,34 +839,22 @@ __global__ void __launch_bounds__(kThreadsFs, 1) k_kron_tc_fs(const __grid_const
         const float* st = reinterpret_cast<const float*>(xsm + (size_t)s * p.nsrc * p.x_src_bytes);
         const float* stz = st + p.x_src_bytes / 4;
         unsigned char* brow = bsm + (size_t)sb * TV * kFsBTermBytes + (size_t)row * 128;
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {  // 8 k values = one 16-byte chunk per term
-          float v[8];
-#pragma unroll
-          for (int e = 0; e < 8; ++e) {
-            const int kl = khalf * 32 + j * 8 + e;
-            const int kk = kb * kBlockK + kl;
-            const bool in = row_ok && kk < p.n_in;
-            float x = in ? st[kl * kTileM + row] : 0.0f;
-            if (p.nsrc > 1 && in) {
-              x = fmaf(beta_r, x, stz[kl * kTileM + row]);
-              Pout[(int64_t)kk * p.rest + m] = x;
-            }
-            v[e] = x;
-          }
-          uint32_t w[TV][4];
-#pragma unroll
-          for (int e = 0; e < 4; ++e) {
-            uint32_t o[3];
-            split2(v[2 * e], v[2 * e + 1], TV, o);
-#pragma unroll
-            for (int tv = 0; tv < TV; ++tv) w[tv][e] = o[tv];
-          }
-          const uint32_t chunk = ((uint32_t)(khalf * 4 + j) ^ swz) * 16u;
-#pragma unroll
-          for (int tv = 0; tv < TV; ++tv)
-            *reinterpret_cast<uint4*>(brow + (size_t)tv * kFsBTermBytes + chunk) =
-                make_uint4(w[tv][0], w[tv][1], w[tv][2], w[tv][3]);
+        const int kbase = kb * kBlockK;
+        const bool full = row_ok && kbase + kBlockK <= p.n_in;
+        if (p.nsrc > 1) {
+          if (full)
+            fs_convert<TV, 2, true>(st, stz, brow, row, khalf, kbase, p.n_in, row_ok, beta_r,
+                                    Pout, p.rest);
+          else
+            fs_convert<TV, 2, false>(st, stz, brow, row, khalf, kbase, p.n_in, row_ok, beta_r,
+                                     Pout, p.rest);
+        } else {
+          if (full)
+            fs_convert<TV, 1, true>(st, stz, brow, row, khalf, kbase, p.n_in, row_ok, beta_r,
+                                    Pout, p.rest);
+          else
+            fs_convert<TV, 1, false>(st, stz, brow, row, khalf, kbase, p.n_in, row_ok, beta_r,
+                                     Pout, p.rest);
         }
         fence_proxy_async();
         mbar_arrive(&xempty[s]);
@@ -846,7 +899,8 @@ __global__ void __launch_bounds__(kThreadsFs, 1) k_kron_tc_fs(const __grid_const
               for (int tv = 0; tv < TV; ++tv) {
                 if (ti + tv >= kMaxT) continue;
                 const uint32_t a = fa + (uint32_t)(ti * 64 + kk * 8);
-                const uint64_t bd = sw128_desc(bst + (uint32_t)tv * kFsBTermBytes + (uint32_t)kk * 32u);
+                const uint64_t bd =
+                    sw128_desc(bst + (uint32_t)tv * kFsBTermBytes + (uint32_t)kk * 32u);
                 if (ti == 0 && tv == 0) {
                   mma_bf16_ta(tmem_base, a, bd, idesc, (kb | kk) ? 1u : 0u);
                 } else {
@@ -896,15 +950,20 @@ __global__ void __launch_bounds__(kThreadsFs, 1) k_kron_tc_fs(const __grid_const
 #pragma unroll
             for (int c = 0; c < 16; ++c) u[c] = 0u;
           }
-          tmem_st16(tmem_base + lane_off + kFsFactorCol0 + (uint32_t)(ti * 64 + chalf * 32 + hh * 16), u);
+          tmem_st16(tmem_base + lane_off + kFsFactorCol0 +
+                        (uint32_t)(ti * 64 + chalf * 32 + hh * 16),
+                    u);
         }
       }
       asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
     }
     tc_fence_before();
     mbar_arrive(afac);
+    const bool staged = p.e_mode != 0;
+    const float sc = p.e_mode == 1 ? p.e_coeff * p.e_d[0] : p.beta;
     int64_t it = 0;
     for (int64_t t = blockIdx.x; t < p.ntiles; t += gridDim.x, ++it) {
+      if (staged && !mbar_wait(efull, (uint32_t)(it & 1), abort_flag, p.err)) break;
       if (!mbar_wait(dfull, (uint32_t)(it & 1), abort_flag, p.err)) break;
       tc_fence_after();
       const int64_t r = t / p.tiles_m, m0 = (t % p.tiles_m) * kTileM;
@@ -926,46 +985,21 @@ __global__ void __launch_bounds__(kThreadsFs, 1) k_kron_tc_fs(const __grid_const
       // row m = mbase + c of the tile, output i: 32 lanes write 128 contiguous bytes
       const int64_t mbase = m0 + chalf * 64;
       const int nrows = (int)((p.rest - mbase < 64) ? (p.rest - mbase) : 64);
-      const bool fused = p.e_bytes != 0;
-      if (fused && !mbar_wait(efull, (uint32_t)(it & 1), abort_flag, p.err)) break;
       float part = 0.0f;  // this thread's <= 64 products of p . Ap
       if (i < p.n_out && nrows > 0) {
         const int64_t ld = p.n_out;
         float* yp = p.Y + r * p.size_out + mbase * ld + i;
         const float* es = reinterpret_cast<const float*>(esm) + chalf * 64 * ld + i;
-        const float* dp = p.epi_dstride ? p.epi_d + mbase * ld + i : nullptr;
-        const float d0 = (fused && !dp) ? p.epi_d[0] : 0.0f;
-        if (p.beta == 0.0f && !dp) {
-#pragma unroll
-          for (int c = 0; c < 64; ++c) {
-            if (c < nrows) {
-              float v = a[c];
-              if (fused) {
-                const float xd = es[c * ld];
-                v = fmaf(p.epi_coeff * d0, xd, v);
-                part = fmaf(v, xd, part);
-              }
-              yp[c * ld] = v;
-            }
-          }
-        } else {  // general diagonal or beta != 0 (not on the CG path)
-#pragma unroll
-          for (int c = 0; c < 64; ++c) {
-            if (c >= nrows) break;
-            float v = a[c];
-            if (fused) {
-              const float xd = es[c * ld];
-              v = fmaf(p.epi_coeff * (dp ? dp[c * ld] : d0), xd, v);
-              part = fmaf(v, xd, part);
-            }
-            if (p.beta != 0.0f) v = fmaf(p.beta, yp[c * ld], v);
-            yp[c * ld] = v;
-          }
-        }
+        if (p.e_mode == 0)
+          fs_store<0>(a, yp, es, ld, nrows, 0.0f);
+        else if (p.e_mode == 1)
+          part = fs_store<1>(a, yp, es, ld, nrows, sc);
+        else
+          fs_store<2>(a, yp, es, ld, nrows, sc);
       }
-      if (fused) mbar_arrive(eempty);
-      double dsum = (double)part;
+      if (staged) mbar_arrive(eempty);
       if (p.epi_dot) {
+        double dsum = (double)part;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) dsum += __shfl_xor_sync(0xffffffffu, dsum, o);
         if (lane == 0) p.epi_dot[t * kDotSlots + ew] = dsum;
@@ -1175,14 +1209,17 @@ static size_t fs_smem(const TcFsParams& r, int tv) {
 static bool fs_plan(const TcParams& p, TcFsParams& r) {
   if (p.nchunks != 1 || p.n_pad > kTileM || p.kblocks > 2) return false;
   if (p.rest % 4 != 0 || p.size_in % 4 != 0) return false;
-  if (((uintptr_t)p.X & 15u) != 0 || (p.pro_z && ((uintptr_t)p.pro_z & 15u) != 0)) return false;
-  if (p.epi_x && (((uintptr_t)p.epi_x & 15u) != 0 || p.size_out % 4 != 0)) return false;
+  r.e_mode = p.epi_x ? 1 : (p.beta != 0.0f ? 2 : 0);
+  // a per-element diagonal in the fused shift term, or a fused shift with a
+  // nonzero beta, takes the streaming kernel
+  if (p.epi_x && (p.epi_dstride != 0 || p.beta != 0.0f)) return false;
+  r.e_src = r.e_mode == 1 ? p.epi_x : (r.e_mode == 2 ? p.Y : nullptr);
+  if (r.e_src && (((uintptr_t)r.e_src & 15u) != 0 || p.size_out % 4 != 0)) return false;
   const int64_t xrows = p.batch * p.n_in;
   if (!tmap_rows(&r.tm_x, p.X, xrows, p.rest)) return false;
   if (p.pro_z && !tmap_rows(&r.tm_z, p.pro_z, xrows, p.rest)) return false;
-  r.X = p.X;
-  r.Y = p.Y;
   r.Bimg = p.Bimg;
+  r.Y = p.Y;
   r.rest = p.rest;
   r.size_in = p.size_in;
   r.size_out = p.size_out;
@@ -1195,21 +1232,17 @@ static bool fs_plan(const TcParams& p, TcFsParams& r) {
   r.ksteps_last = p.ksteps_last;
   r.nsrc = p.pro_z ? 2 : 1;
   r.x_src_bytes = (uint32_t)kBlockK * kTileM * 4u;
-  r.e_bytes = p.epi_x ? (uint32_t)kTileM * (uint32_t)p.n_out * 4u : 0u;
-  r.e_bytes = (r.e_bytes + 1023u) & ~1023u;
+  r.e_bytes = r.e_mode ? (((uint32_t)kTileM * (uint32_t)p.n_out * 4u + 1023u) & ~1023u) : 0u;
   const size_t avail = kSmemMax - 1024 - 256 - 2 * (size_t)p.tv * kFsBTermBytes - r.e_bytes;
   r.xstages = (int)std::min<size_t>(4, avail / ((size_t)r.nsrc * r.x_src_bytes));
   if (r.xstages < 2) return false;
   r.coeff = p.coeff;
   r.beta = p.beta;
+  r.e_coeff = p.epi_coeff;
+  r.e_d = p.epi_d;
   r.err = p.err;
-  r.pro_z = p.pro_z;
-  r.pro_out = p.pro_out;
   r.pro_beta = p.pro_beta;
-  r.epi_x = p.epi_x;
-  r.epi_d = p.epi_d;
-  r.epi_dstride = p.epi_dstride;
-  r.epi_coeff = p.epi_coeff;
+  r.pro_out = p.pro_out;
   r.epi_dot = p.epi_dot;
   return true;
 }

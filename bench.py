@@ -137,6 +137,24 @@ def build_operator(cola, ctx, w, device):
     return op, kron
 
 
+def time_queued(torch, ctx, fn, reps):
+    """Device time of `reps` calls of fn, on the library's launch stream, with
+    every launch queued before the device reaches the first one (a device-side
+    sleep holds the stream while the host enqueues), so host overhead between
+    calls is not timed.  Returns seconds per call."""
+    ls = ctx.stream()
+    k0, k1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    with torch.cuda.stream(ls):
+        torch.cuda._sleep(50_000_000)      # ~25 ms at 2 GHz
+    k0.record(ls)
+    for _ in range(reps):
+        fn()
+    k1.record(ls)
+    torch.cuda.synchronize()
+    return k0.elapsed_time(k1) / 1e3 / reps
+
+
 def run_mvm_only(args):
     """A few MIXED Kronecker MVMs of the bench operator (for profiler captures)."""
     import torch
@@ -151,17 +169,11 @@ def run_mvm_only(args):
     for _ in range(args.reps):
         cola.cola_matvec(ctx, target, X, cola.PREC_MIXED, out=Y,
                          split_terms=(args.fterms, args.vterms))
-    torch.cuda.synchronize()
-    s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    s0.record()
-    for _ in range(args.reps):
-        cola.cola_matvec(ctx, target, X, cola.PREC_MIXED, out=Y,
-                         split_terms=(args.fterms, args.vterms))
-    s1.record()
-    torch.cuda.synchronize()
+    t = time_queued(torch, ctx, lambda: cola.cola_matvec(
+        ctx, target, X, cola.PREC_MIXED, out=Y, split_terms=(args.fterms, args.vterms)),
+        args.reps)
     print(json.dumps({"mode": "mvm-only", "nrhs": args.nrhs, "reps": args.reps,
-                      "ms_per_mvm": s0.elapsed_time(s1) / args.reps,
-                      "launches": ctx.kernel_launches()}))
+                      "ms_per_mvm": t * 1e3, "launches": ctx.kernel_launches()}))
     ctx.close()
 
 
@@ -246,15 +258,10 @@ def run_ours(args):
     Yf = torch.empty_like(Xf)
     for _ in range(3):
         cola.cola_matvec(ctx, kron, Xf, cola.PREC_MIXED, out=Yf, split_terms=(args.fterms, args.vterms))
-    torch.cuda.synchronize()
     reps = 20
-    k0, k1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    k0.record(stream)
-    for _ in range(reps):
-        cola.cola_matvec(ctx, kron, Xf, cola.PREC_MIXED, out=Yf, split_terms=(args.fterms, args.vterms))
-    k1.record(stream)
-    torch.cuda.synchronize()
-    per_launch = k0.elapsed_time(k1) / 1e3 / (reps * 3)
+    per_launch = time_queued(torch, ctx, lambda: cola.cola_matvec(
+        ctx, kron, Xf, cola.PREC_MIXED, out=Yf, split_terms=(args.fterms, args.vterms)),
+        reps) / 3
     alg_bytes = 8.0 * R * w.N                   # read X + write Y, FP32, per mode step
     achieved = alg_bytes / per_launch / 1e9
     roofline = {"kernel": "k_kron_tc (split-BF16 tcgen05 mode product)", "bound": "hbm",

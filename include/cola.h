@@ -140,7 +140,10 @@ cola_status cola_linop_release(cola_linop* op);
 /* --------------------------------------------------------------------- MVM */
 
 /* Y = A X for nrhs vectors (Sec. 3.1).  X is [nrhs][cols], Y is [nrhs][rows],
- * both FP64 for COLA_PREC_F64 and FP32 otherwise.  Asynchronous on stream. */
+ * both FP64 for COLA_PREC_F64 and FP32 otherwise.  Asynchronous on stream.
+ * A tensor-core kernel that gave up waiting (COLA_ERR_TIMEOUT, MIXED only) is
+ * reported by a later call on the same context: the next cola_matvec once the
+ * device has passed this one, or any call that synchronises (solves). */
 cola_status cola_matvec(cola_ctx* ctx, const cola_linop* op, const void* X, void* Y,
                         int64_t nrhs, cola_precision precision, cola_stream stream);
 
@@ -301,6 +304,13 @@ cola_status cola_kron_matvec_noalloc(int nfactors, const int64_t* rows, const in
 /* Number of kernels this library launched (or recorded into replayed graphs,
  * counted per replay) since the context was created. */
 cola_status cola_kernel_launches(const cola_ctx* ctx, int64_t* count);
+
+/* The context's internal launch stream (every kernel of this library runs on
+ * it; calls join the caller's stream before and after).  Exposed so that a
+ * caller can time kernels with events on the stream they run on.  No
+ * counterpart in the paper.  The stream is owned by the context and stays
+ * valid until cola_destroy. */
+cola_status cola_get_stream(const cola_ctx* ctx, cola_stream* stream);
 
 #ifdef __cplusplus
 }

@@ -74,6 +74,12 @@ class Context:
         check(_lib().cola_kernel_launches(self.handle, C.byref(n)))
         return n.value
 
+    def stream(self) -> "torch.cuda.ExternalStream":
+        """The library's launch stream (for timing kernels with events)."""
+        s = C.c_void_p()
+        check(_lib().cola_get_stream(self.handle, C.byref(s)))
+        return torch.cuda.ExternalStream(s.value, device=self.device)
+
     def __del__(self):
         try:
             self.close()

@@ -69,6 +69,7 @@ SIGNATURES = {
     "cola_logdet_backward": (I32, [P, P, P, P, I64, D, PP, I32, C.POINTER(cola_cg_opts), P]),
     "cola_rademacher": (I32, [P, C.c_uint64, I64, I64, P, I32, P]),
     "cola_kernel_launches": (I32, [P, C.POINTER(I64)]),
+    "cola_get_stream": (I32, [P, C.POINTER(P)]),
     "cola_set_split_terms": (I32, [P, I32, I32]),
     "cola_kron_matvec_noalloc": (I32, [C.c_int, C.POINTER(I64), C.POINTER(I64), PP, P, P, I64, P]),
 }

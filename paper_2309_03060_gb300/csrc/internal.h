@@ -78,6 +78,9 @@ struct Ctx {
   std::map<std::string, GraphEntry> graphs;
   void* pinned = nullptr;     // small host staging area (pinned)
   size_t pinned_bytes = 0;
+  int* tc_err_host = nullptr;  // pinned copy of the tensor-core timeout flag
+  cudaEvent_t tc_err_ev = nullptr;
+  bool tc_err_pending = false;  // a copy of the flag is in flight
   void* host_pinned(size_t bytes);
   void count_launch() {
     if (capturing)
@@ -258,7 +261,8 @@ void bilinear_entry(Ctx* c, const cola_linop* op, const void* U, const void* X,
                     int accumulate, int depth);
 void check_cg_args(const cola_linop* op, const cola_cg_opts* o, int64_t R);
 // Raises COLA_ERR_TIMEOUT when a tensor-core kernel gave up waiting (and clears the flag).
-void tc_check_error(Ctx* c);
+void tc_check_error(Ctx* c);        // synchronises the stream
+void tc_check_error_async(Ctx* c);  // reports an earlier call's timeout, queues a check
 // Fused MIXED CG MVM for Sum(Kron, Diag); see kron_tc.cu.  0 = not applicable.
 // p_new = z + beta p_old is formed in the first mode step (p_new != p_old).
 int64_t kron_tc_cg_mvm(Ctx* c, const cola_linop* op, const float* z, const double* beta_vec,

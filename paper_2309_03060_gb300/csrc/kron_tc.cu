@@ -1111,9 +1111,36 @@ void tc_check_error(Ctx* c) {
   int h = 0;
   COLA_CUDA(cudaMemcpyAsync(&h, p, 4, cudaMemcpyDeviceToHost, c->s));
   COLA_CUDA(cudaStreamSynchronize(c->s));
+  c->tc_err_pending = false;  // the device flag read here covers any queued copy
   if (h != 0) {
     COLA_CUDA(cudaMemsetAsync(p, 0, 4, c->s));
     fail(COLA_ERR_TIMEOUT, "tensor-core Kronecker kernel timed out waiting on an mbarrier");
+  }
+}
+
+// The device flag is only cleared when a timeout is reported, so a copy taken
+// at any later point still shows it.  One copy is in flight at a time.
+void tc_check_error_async(Ctx* c) {
+  if (c->ws.bufs.find("tc.err") == c->ws.bufs.end()) return;
+  int* p = (int*)c->ws.bufs["tc.err"].p;
+  if (!c->tc_err_host) {
+    COLA_CUDA(cudaHostAlloc((void**)&c->tc_err_host, sizeof(int), cudaHostAllocDefault));
+    *c->tc_err_host = 0;
+    COLA_CUDA(cudaEventCreateWithFlags(&c->tc_err_ev, cudaEventDisableTiming));
+  }
+  if (c->tc_err_pending && cudaEventQuery(c->tc_err_ev) == cudaSuccess) {
+    c->tc_err_pending = false;
+    if (*c->tc_err_host != 0) {
+      *c->tc_err_host = 0;
+      COLA_CUDA(cudaMemsetAsync(p, 0, 4, c->s));
+      fail(COLA_ERR_TIMEOUT,
+           "tensor-core Kronecker kernel of an earlier call timed out waiting on an mbarrier");
+    }
+  }
+  if (!c->tc_err_pending) {
+    COLA_CUDA(cudaMemcpyAsync(c->tc_err_host, p, sizeof(int), cudaMemcpyDeviceToHost, c->s));
+    COLA_CUDA(cudaEventRecord(c->tc_err_ev, c->s));
+    c->tc_err_pending = true;
   }
 }
 

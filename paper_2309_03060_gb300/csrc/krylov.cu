@@ -21,6 +21,8 @@
 #include <cmath>
 #include <string>
 
+#include <type_traits>
+
 #include "internal.h"
 
 namespace cola {
@@ -120,6 +122,53 @@ __global__ void k_cg_xr(int64_t n, T* x, T* r, const T* p, const T* Ap, const T*
 }
 
 // One block per right-hand side: the new r^T z and r^T r, beta, and the stopping rule.
+// k_cg_xr for FP32 vectors of a length divisible by 4 (16-byte accesses keep
+// enough bytes in flight for the HBM bandwidth); n4 = n / 4.
+__global__ void k_cg_xr4(int64_t n4, float4* x, float4* r, const float4* p, const float4* Ap,
+                         const float4* invd, float4* z, const CgState* st, int nblk,
+                         double* part_rz, double* part_rr) {
+  const int64_t v = blockIdx.y;
+  const float a = (float)st[v].alpha;
+  float4* xv = x + v * n4;
+  float4* rv = r + v * n4;
+  const float4* pv = p + v * n4;
+  const float4* Av = Ap + v * n4;
+  float4* zv = z ? z + v * n4 : nullptr;
+  float s_rz = 0.0f, s_rr = 0.0f;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4;
+       i += (int64_t)nblk * blockDim.x) {
+    float4 ri = rv[i];
+    if (a != 0.0f) {
+      const float4 pi = pv[i], ai = Av[i];
+      float4 xi = xv[i];
+      xi.x = fmaf(a, pi.x, xi.x);
+      xi.y = fmaf(a, pi.y, xi.y);
+      xi.z = fmaf(a, pi.z, xi.z);
+      xi.w = fmaf(a, pi.w, xi.w);
+      ri.x = fmaf(-a, ai.x, ri.x);
+      ri.y = fmaf(-a, ai.y, ri.y);
+      ri.z = fmaf(-a, ai.z, ri.z);
+      ri.w = fmaf(-a, ai.w, ri.w);
+      xv[i] = xi;
+      rv[i] = ri;
+    }
+    float4 zi = ri;
+    if (invd) {
+      const float4 d = invd[i];
+      zi = make_float4(ri.x * d.x, ri.y * d.y, ri.z * d.z, ri.w * d.w);
+      zv[i] = zi;
+    }
+    s_rz = fmaf(ri.x, zi.x, fmaf(ri.y, zi.y, fmaf(ri.z, zi.z, fmaf(ri.w, zi.w, s_rz))));
+    s_rr = fmaf(ri.x, ri.x, fmaf(ri.y, ri.y, fmaf(ri.z, ri.z, fmaf(ri.w, ri.w, s_rr))));
+  }
+  double rr;
+  const double rz = block_sum2(s_rz, &rr, s_rr);
+  if (threadIdx.x == 0) {
+    part_rz[v * nblk + blockIdx.x] = rz;
+    part_rr[v * nblk + blockIdx.x] = rr;
+  }
+}
+
 __global__ void k_cg_beta(CgState* st, const double* part_rz, const double* part_rr, int nblk,
                           double delta2, int refine, double* beta_out) {
   const int64_t r = blockIdx.x;
@@ -535,9 +584,21 @@ static void cg_iteration(Ctx* c, const cola_linop* op, CgBufs<T>& B, int64_t N, 
     k_cg_alpha<<<(unsigned)R, 32, 0, c->s>>>(B.st, B.dotv, 1);
     c->count_launch();
   }
-  k_cg_xr<T><<<rows_grid(N, R, nblk), 256, 0, c->s>>>(N, B.x, B.r, B.p, B.Ap, B.invd,
-                                                       B.invd ? B.z : nullptr, B.st, nblk,
-                                                       B.part_rz, B.part_rr);
+  bool vec4 = false;
+  if constexpr (std::is_same<T, float>::value) {
+    const uintptr_t al = (uintptr_t)B.x | (uintptr_t)B.r | (uintptr_t)B.p | (uintptr_t)B.Ap |
+                         (uintptr_t)B.z | (uintptr_t)B.invd;
+    vec4 = N % 4 == 0 && (al & 15u) == 0;
+    if (vec4)
+      k_cg_xr4<<<rows_grid(N, R, nblk), 256, 0, c->s>>>(
+          N / 4, (float4*)B.x, (float4*)B.r, (const float4*)B.p, (const float4*)B.Ap,
+          (const float4*)B.invd, B.invd ? (float4*)B.z : nullptr, B.st, nblk, B.part_rz,
+          B.part_rr);
+  }
+  if (!vec4)
+    k_cg_xr<T><<<rows_grid(N, R, nblk), 256, 0, c->s>>>(N, B.x, B.r, B.p, B.Ap, B.invd,
+                                                         B.invd ? B.z : nullptr, B.st, nblk,
+                                                         B.part_rz, B.part_rr);
   c->count_launch();
   k_cg_beta<<<(unsigned)R, 256, 0, c->s>>>(B.st, B.part_rz, B.part_rr, nblk, delta2, refine,
                                   B.beta_vec);

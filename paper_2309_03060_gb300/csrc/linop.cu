@@ -627,6 +627,8 @@ cola_status cola_destroy(cola_ctx* c) {
       if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
     c->ws.release_all();
     if (c->pinned) cudaFreeHost(c->pinned);
+    if (c->tc_err_host) cudaFreeHost(c->tc_err_host);
+    if (c->tc_err_ev) cudaEventDestroy(c->tc_err_ev);
     cudaEventDestroy(c->ev_a);
     cudaEventDestroy(c->ev_b);
     cudaStreamDestroy(c->s);
@@ -907,6 +909,13 @@ cola_status cola_kernel_launches(const cola_ctx* ctx, int64_t* count) {
   });
 }
 
+cola_status cola_get_stream(const cola_ctx* ctx, cola_stream* stream) {
+  return guard([&] {
+    COLA_REQUIRE(ctx && stream, COLA_ERR_INVALID_ARG, "NULL argument");
+    *stream = (cola_stream)ctx->s;
+  });
+}
+
 cola_status cola_matvec(cola_ctx* ctx, const cola_linop* op, const void* X, void* Y,
                         int64_t nrhs, cola_precision prec, cola_stream stream) {
   return guard([&] {
@@ -922,7 +931,7 @@ cola_status cola_matvec(cola_ctx* ctx, const cola_linop* op, const void* X, void
       apply<double>(ctx, op, (const double*)X, (double*)Y, nrhs, 1.0, 0.0, 0, false, prec);
     else
       apply<float>(ctx, op, (const float*)X, (float*)Y, nrhs, 1.0, 0.0, 0, false, prec);
-    if (prec == COLA_PREC_MIXED) tc_check_error(ctx);
+    if (prec == COLA_PREC_MIXED) tc_check_error_async(ctx);
   });
 }
 

@@ -389,7 +389,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--cpu-iters", type=int, default=2)
     ap.add_argument("--ref-iters-per-solve", type=int, default=12400)
-    ap.add_argument("--traffic-bytes", type=float, default=None)
+    # DRAM bytes of one k_kron_tc_fs launch from its ncu capture (reads + writes)
+    ap.add_argument("--traffic-bytes", type=float, default=211.365888e6)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--plain", action="store_true", help="also time the plain FP32 path once")
     ap.add_argument("--mvm-only", action="store_true",

@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include <map>
+#include <utility>
 #include <string>
 #include <vector>
 
@@ -294,5 +295,33 @@ std::vector<int64_t> kron_tc_batch_upload(Ctx* c, const std::vector<TcBatchProbl
                                           int tf, int tv, const char* tag);
 // Launches one persistent k_kron_tc over the table uploaded under `tag`.
 void kron_tc_batch_launch(Ctx* c, const char* tag, int tf, int tv, int max_n_chunk);
+
+// Programmatic dependent launch: a kernel launched with launch_pdl may start
+// while the previous kernel on the stream is still running.  It must call
+// pdl_wait() before it touches memory that earlier kernels write or read;
+// pdl_trigger() lets the next kernel start early.  Both are no-ops for a
+// kernel launched without the attribute.
+#ifdef __CUDACC__
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+template <typename... KArgs, typename... Args>
+void launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  COLA_CUDA(cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...));
+}
+#endif
 
 }  // namespace cola

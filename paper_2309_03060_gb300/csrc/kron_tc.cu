@@ -765,9 +765,13 @@ __global__ void __launch_bounds__(kThreadsFs, 1) k_kron_tc_fs(const __grid_const
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
+  // the next kernel may start its own set-up; every role below that touches
+  // memory written or read by earlier kernels first waits for them (pdl_wait)
+  pdl_trigger();
 
   if (warp == kFsLoaderWarp) {
     // ---------------------------------------------------------------- loader
+    pdl_wait();
     bool ok = true;
     int s = 0;
     uint32_t ph = 0;
@@ -803,6 +807,7 @@ __global__ void __launch_bounds__(kThreadsFs, 1) k_kron_tc_fs(const __grid_const
     __syncwarp();
   } else if (warp == kFsEpiLoaderWarp) {
     // ------------------------------------------------ rows for the epilogue
+    pdl_wait();
     if (lane == 0 && p.e_bytes) {
       int64_t it = 0;
       for (int64_t t = blockIdx.x; t < p.ntiles; t += gridDim.x, ++it) {
@@ -819,6 +824,7 @@ __global__ void __launch_bounds__(kThreadsFs, 1) k_kron_tc_fs(const __grid_const
     __syncwarp();
   } else if (warp < kFsConvWarps) {
     // ------------------------------------------------------------ converters
+    pdl_wait();
     bool ok = true;
     int s = 0, sb = 0;
     uint32_t ph = 0, phb = 0;
@@ -959,6 +965,7 @@ __global__ void __launch_bounds__(kThreadsFs, 1) k_kron_tc_fs(const __grid_const
     }
     tc_fence_before();
     mbar_arrive(afac);
+    pdl_wait();  // the factor copy above overlaps the previous kernel's tail
     const bool staged = p.e_mode != 0;
     const float sc = p.e_mode == 1 ? p.e_coeff * p.e_d[0] : p.beta;
     int64_t it = 0;
@@ -1379,7 +1386,7 @@ static int64_t kron_tc_run(Ctx* c, const cola_linop* op, const float* X, float* 
     const int grid = (int)std::min<int64_t>(p.ntiles, c->num_sms);
     TcFsParams rp{};
     if (fs_plan(p, rp)) {
-      fs_kernel(tf, tv)<<<grid, kThreadsFs, fs_smem(rp, tv), c->s>>>(rp);
+      launch_pdl(fs_kernel(tf, tv), dim3(grid), dim3(kThreadsFs), fs_smem(rp, tv), c->s, rp);
     } else {
       k_kron_tc<OneProb><<<grid, kThreadsTc, q.smem, c->s>>>(OneProb{p}, p);
     }

@@ -64,6 +64,8 @@ __device__ __forceinline__ double block_sum2(T v, double* out_other, T v2) {
 // alpha = r^T z / p^T A p, with p^T A p the ordered sum of nparts partials.
 // One block per right-hand side: p^T A p from its partial sums, alpha = r^T z / p^T A p.
 __global__ void k_cg_alpha(CgState* st, const double* parts, int nparts) {
+  pdl_trigger();
+  pdl_wait();
   const int64_t r = blockIdx.x;
   CgState& s = st[r];
   if (!s.active) {
@@ -127,6 +129,8 @@ __global__ void k_cg_xr(int64_t n, T* x, T* r, const T* p, const T* Ap, const T*
 __global__ void k_cg_xr4(int64_t n4, float4* x, float4* r, const float4* p, const float4* Ap,
                          const float4* invd, float4* z, const CgState* st, int nblk,
                          double* part_rz, double* part_rr) {
+  pdl_trigger();
+  pdl_wait();
   const int64_t v = blockIdx.y;
   const float a = (float)st[v].alpha;
   float4* xv = x + v * n4;
@@ -171,6 +175,8 @@ __global__ void k_cg_xr4(int64_t n4, float4* x, float4* r, const float4* p, cons
 
 __global__ void k_cg_beta(CgState* st, const double* part_rz, const double* part_rr, int nblk,
                           double delta2, int refine, double* beta_out) {
+  pdl_trigger();
+  pdl_wait();
   const int64_t r = blockIdx.x;
   CgState& s = st[r];
   if (!s.active) {
@@ -576,6 +582,8 @@ static void cg_iteration(Ctx* c, const cola_linop* op, CgBufs<T>& B, int64_t N, 
                    (float*)p_new, (float*)B.Ap, B.tile_dot, R, 1);
     B.cur ^= 1;
     B.p = p_new;
+    // the small CG kernels launch normally (an early launch measured slower);
+    // their pdl_trigger lets the next tensor-core step start its set-up early
     k_cg_alpha<<<(unsigned)R, 256, 0, c->s>>>(B.st, B.tile_dot, (int)(8 * B.fused_tiles));
     c->count_launch();
   } else {
@@ -601,7 +609,7 @@ static void cg_iteration(Ctx* c, const cola_linop* op, CgBufs<T>& B, int64_t N, 
                                                          B.part_rz, B.part_rr);
   c->count_launch();
   k_cg_beta<<<(unsigned)R, 256, 0, c->s>>>(B.st, B.part_rz, B.part_rr, nblk, delta2, refine,
-                                  B.beta_vec);
+                                            B.beta_vec);
   c->count_launch();
   if (B.fused_tiles <= 0) {
     k_cg_p<T><<<dim3(ew_blocks(N), (unsigned)R), 256, 0, c->s>>>(N, B.invd ? B.z : B.r, B.p,

@@ -63,13 +63,17 @@ __device__ __forceinline__ double block_sum2(T v, double* out_other, T v2) {
 
 // alpha = r^T z / p^T A p, with p^T A p the ordered sum of nparts partials.
 // One block per right-hand side: p^T A p from its partial sums, alpha = r^T z / p^T A p.
-__global__ void k_cg_alpha(CgState* st, const double* parts, int nparts) {
+// alpha_out (optional): where this iteration's alpha is recorded (0 when inactive).
+__global__ void k_cg_alpha(CgState* st, const double* parts, int nparts, double* alpha_out) {
   pdl_trigger();
   pdl_wait();
   const int64_t r = blockIdx.x;
   CgState& s = st[r];
   if (!s.active) {
-    if (threadIdx.x == 0) s.alpha = 0.0;
+    if (threadIdx.x == 0) {
+      s.alpha = 0.0;
+      if (alpha_out) alpha_out[r] = 0.0;
+    }
     return;
   }
   double v = 0.0;
@@ -82,9 +86,11 @@ __global__ void k_cg_alpha(CgState* st, const double* parts, int nparts) {
     s.status = COLA_ERR_BREAKDOWN;
     s.active = 0;
     s.alpha = 0.0;
+    if (alpha_out) alpha_out[r] = 0.0;
     return;
   }
   s.alpha = s.rz / v;
+  if (alpha_out) alpha_out[r] = s.alpha;
 }
 
 // x += alpha p; r -= alpha Ap; z = M^-1 r; partial sums of r^T z and r^T r.
@@ -170,6 +176,83 @@ __global__ void k_cg_xr4(int64_t n4, float4* x, float4* r, const float4* p, cons
   if (threadIdx.x == 0) {
     part_rz[v * nblk + blockIdx.x] = rz;
     part_rr[v * nblk + blockIdx.x] = rr;
+  }
+}
+
+// k_cg_xr4 without the solution update: r -= alpha Ap, z = M^-1 r and the
+// partial dots.  x is brought up to date every kPRing iterations by k_cg_xbatch.
+__global__ void k_cg_r4(int64_t n4, float4* r, const float4* Ap, const float4* invd, float4* z,
+                        const CgState* st, int nblk, double* part_rz, double* part_rr) {
+  pdl_trigger();
+  pdl_wait();
+  const int64_t v = blockIdx.y;
+  const float a = (float)st[v].alpha;
+  float4* rv = r + v * n4;
+  const float4* Av = Ap + v * n4;
+  float4* zv = z ? z + v * n4 : nullptr;
+  float s_rz = 0.0f, s_rr = 0.0f;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4;
+       i += (int64_t)nblk * blockDim.x) {
+    float4 ri = rv[i];
+    if (a != 0.0f) {
+      const float4 ai = Av[i];
+      ri.x = fmaf(-a, ai.x, ri.x);
+      ri.y = fmaf(-a, ai.y, ri.y);
+      ri.z = fmaf(-a, ai.z, ri.z);
+      ri.w = fmaf(-a, ai.w, ri.w);
+      rv[i] = ri;
+    }
+    float4 zi = ri;
+    if (invd) {
+      const float4 d = invd[i];
+      zi = make_float4(ri.x * d.x, ri.y * d.y, ri.z * d.z, ri.w * d.w);
+      zv[i] = zi;
+    }
+    s_rz = fmaf(ri.x, zi.x, fmaf(ri.y, zi.y, fmaf(ri.z, zi.z, fmaf(ri.w, zi.w, s_rz))));
+    s_rr = fmaf(ri.x, ri.x, fmaf(ri.y, ri.y, fmaf(ri.z, ri.z, fmaf(ri.w, ri.w, s_rr))));
+  }
+  double rr;
+  const double rz = block_sum2(s_rz, &rr, s_rr);
+  if (threadIdx.x == 0) {
+    part_rz[v * nblk + blockIdx.x] = rz;
+    part_rr[v * nblk + blockIdx.x] = rr;
+  }
+}
+
+// The search directions of the last kPRing iterations (one ring slot each).
+constexpr int kPRing = 8;
+struct PRing {
+  const float4* p[kPRing];
+};
+
+// x += sum_s alpha_s p_s over the ring (alpha_hist[s][r]; 0 for an inactive
+// right-hand side): the x updates of kPRing CG iterations in one pass.
+__global__ void k_cg_xbatch(int64_t n4, float4* x, PRing ring, const double* alpha_hist,
+                            int64_t R, int nblk) {
+  pdl_trigger();
+  pdl_wait();
+  const int64_t v = blockIdx.y;
+  float a[kPRing];
+  bool any = false;
+#pragma unroll
+  for (int s = 0; s < kPRing; ++s) {
+    a[s] = (float)alpha_hist[s * R + v];
+    any |= a[s] != 0.0f;
+  }
+  if (!any) return;
+  float4* xv = x + v * n4;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4;
+       i += (int64_t)nblk * blockDim.x) {
+    float4 acc = xv[i];
+#pragma unroll
+    for (int s = 0; s < kPRing; ++s) {
+      const float4 ps = ring.p[s][v * n4 + i];
+      acc.x = fmaf(a[s], ps.x, acc.x);
+      acc.y = fmaf(a[s], ps.y, acc.y);
+      acc.z = fmaf(a[s], ps.z, acc.z);
+      acc.w = fmaf(a[s], ps.w, acc.w);
+    }
+    xv[i] = acc;
   }
 }
 
@@ -552,8 +635,10 @@ inline int ew_blocks(int64_t n) {
 template <typename T>
 struct CgBufs {
   T *x, *r, *p, *Ap, *z;  // working precision; p is pp[cur]
-  T* pp[2];               // ping-pong search directions (fused MIXED path)
+  T* pp[kPRing];          // ring of search directions (fused MIXED path; 1 buffer else)
   int cur;
+  bool defer_x;           // x updated every kPRing iterations from the ring (fused FP32)
+  double* alpha_hist;     // [kPRing][R] alpha of each ring slot
   T* invd;
   double *x64, *b64, *r64;
   double *part_rz, *part_rr, *dotp, *dotv;
@@ -573,23 +658,25 @@ static std::string key_of(const char* what, const cola_linop* op, int64_t R, int
 
 template <typename T>
 static void cg_iteration(Ctx* c, const cola_linop* op, CgBufs<T>& B, int64_t N, int64_t R,
-                         int nblk, int prec, double delta2, int refine) {
+                         int nblk, int prec, double delta2, int refine, bool defer) {
   if (B.fused_tiles > 0) {
     // p_new = z + beta p_old (first mode step), Ap and p^T A p partials (last)
+    const int nxt = (B.cur + 1) % kPRing;
     T* p_old = B.pp[B.cur];
-    T* p_new = B.pp[B.cur ^ 1];
+    T* p_new = B.pp[nxt];
     kron_tc_cg_mvm(c, op, (const float*)(B.invd ? B.z : B.r), B.beta_vec, (const float*)p_old,
                    (float*)p_new, (float*)B.Ap, B.tile_dot, R, 1);
-    B.cur ^= 1;
+    B.cur = nxt;
     B.p = p_new;
     // the small CG kernels launch normally (an early launch measured slower);
     // their pdl_trigger lets the next tensor-core step start its set-up early
-    k_cg_alpha<<<(unsigned)R, 256, 0, c->s>>>(B.st, B.tile_dot, (int)(8 * B.fused_tiles));
+    k_cg_alpha<<<(unsigned)R, 256, 0, c->s>>>(B.st, B.tile_dot, (int)(8 * B.fused_tiles),
+                                               defer ? B.alpha_hist + (int64_t)nxt * R : nullptr);
     c->count_launch();
   } else {
     apply<T>(c, op, B.p, B.Ap, R, 1.0, 0.0, 1, false, prec);
     dots<T>(c, B.p, B.Ap, N, R, B.dotp, B.dotv);
-    k_cg_alpha<<<(unsigned)R, 32, 0, c->s>>>(B.st, B.dotv, 1);
+    k_cg_alpha<<<(unsigned)R, 32, 0, c->s>>>(B.st, B.dotv, 1, nullptr);
     c->count_launch();
   }
   bool vec4 = false;
@@ -597,7 +684,11 @@ static void cg_iteration(Ctx* c, const cola_linop* op, CgBufs<T>& B, int64_t N, 
     const uintptr_t al = (uintptr_t)B.x | (uintptr_t)B.r | (uintptr_t)B.p | (uintptr_t)B.Ap |
                          (uintptr_t)B.z | (uintptr_t)B.invd;
     vec4 = N % 4 == 0 && (al & 15u) == 0;
-    if (vec4)
+    if (vec4 && defer)
+      k_cg_r4<<<rows_grid(N, R, nblk), 256, 0, c->s>>>(
+          N / 4, (float4*)B.r, (const float4*)B.Ap, (const float4*)B.invd,
+          B.invd ? (float4*)B.z : nullptr, B.st, nblk, B.part_rz, B.part_rr);
+    else if (vec4)
       k_cg_xr4<<<rows_grid(N, R, nblk), 256, 0, c->s>>>(
           N / 4, (float4*)B.x, (float4*)B.r, (const float4*)B.p, (const float4*)B.Ap,
           (const float4*)B.invd, B.invd ? (float4*)B.z : nullptr, B.st, nblk, B.part_rz,
@@ -619,7 +710,20 @@ static void cg_iteration(Ctx* c, const cola_linop* op, CgBufs<T>& B, int64_t N, 
   COLA_CUDA(cudaGetLastError());
 }
 
-// Runs `chunk` iterations as one CUDA graph (captured on first use).
+// x += the ring's kPRing updates (deferred-x mode).
+template <typename T>
+static void cg_flush_x(Ctx* c, CgBufs<T>& B, int64_t N, int64_t R, int nblk) {
+  if constexpr (std::is_same<T, float>::value) {
+    PRing ring;
+    for (int s = 0; s < kPRing; ++s) ring.p[s] = (const float4*)B.pp[s];
+    k_cg_xbatch<<<rows_grid(N, R, nblk), 256, 0, c->s>>>(N / 4, (float4*)B.x, ring, B.alpha_hist,
+                                                          R, nblk);
+    c->count_launch();
+  }
+}
+
+// Runs `chunk` iterations as one CUDA graph (captured on first use).  In
+// deferred-x mode the chunk is a multiple of kPRing and ends with x current.
 template <typename T>
 static void cg_chunk(Ctx* c, const cola_linop* op, CgBufs<T>& B, int64_t N, int64_t R, int nblk,
                      int prec, double delta2, int refine, int chunk, const std::string& key) {
@@ -635,7 +739,10 @@ static void cg_chunk(Ctx* c, const cola_linop* op, CgBufs<T>& B, int64_t N, int6
     c->captured = 0;
     const uint64_t gen0 = c->ws.generation;
     try {
-      for (int i = 0; i < chunk; ++i) cg_iteration<T>(c, op, B, N, R, nblk, prec, delta2, refine);
+      for (int i = 0; i < chunk; ++i) {
+        cg_iteration<T>(c, op, B, N, R, nblk, prec, delta2, refine, B.defer_x);
+        if (B.defer_x && (i + 1) % kPRing == 0) cg_flush_x<T>(c, B, N, R, nblk);
+      }
     } catch (...) {
       c->capturing = false;
       cudaStreamEndCapture(c->s, &g);
@@ -668,8 +775,8 @@ static cola_status cg_run(Ctx* c, cola_linop* op, const void* Bin, void* Xout, i
   CgBufs<T> B{};
   B.x = (T*)ws.get("cg.x", sizeof(T) * N * R);
   B.r = (T*)ws.get("cg.r", sizeof(T) * N * R);
+  for (int s = 0; s < kPRing; ++s) B.pp[s] = nullptr;
   B.pp[0] = (T*)ws.get("cg.p", sizeof(T) * N * R);
-  B.pp[1] = nullptr;
   B.cur = 0;
   B.p = B.pp[0];
   B.Ap = (T*)ws.get("cg.Ap", sizeof(T) * N * R);
@@ -681,7 +788,15 @@ static cola_status cg_run(Ctx* c, cola_linop* op, const void* Bin, void* Xout, i
   B.st = (CgState*)ws.get("cg.st", sizeof(CgState) * R);
   B.beta_vec = (double*)ws.get("cg.beta", 8 * R);
   B.fused_tiles = (prec == COLA_PREC_MIXED && sizeof(T) == 4) ? kron_tc_tiles_per_rhs(op) : 0;
-  if (B.fused_tiles > 0) B.pp[1] = (T*)ws.get("cg.p2", sizeof(T) * N * R);
+  if (B.fused_tiles > 0) {
+    for (int s = 1; s < kPRing; ++s) {
+      char nm[16];
+      snprintf(nm, sizeof nm, "cg.p%d", s + 1);
+      B.pp[s] = (T*)ws.get(nm, sizeof(T) * N * R);
+    }
+    B.alpha_hist = (double*)ws.get("cg.ahist", 8 * kPRing * R);
+    B.defer_x = sizeof(T) == 4 && N % 4 == 0;
+  }
   B.tile_dot = B.fused_tiles > 0 ? (double*)ws.get("cg.tdot", 8 * 8 * B.fused_tiles * R) : nullptr;
   COLA_CUDA(cudaMemsetAsync(B.beta_vec, 0, 8 * R, c->s));
   double* bb = (double*)ws.get("cg.bb", 8 * R);
@@ -747,10 +862,11 @@ static cola_status cg_run(Ctx* c, cola_linop* op, const void* Bin, void* Xout, i
     COLA_CUDA(cudaStreamSynchronize(c->s));
   };
   const double delta2 = o.reliable_delta * o.reliable_delta;
-  // the fused path alternates two p buffers, so a graph chunk must hold an
-  // even number of iterations to start and end on the same buffer
+  // the fused path cycles through kPRing p buffers, so a graph chunk holds a
+  // multiple of kPRing iterations: it starts and ends on the same buffer, and
+  // in deferred-x mode x is current at its end
   int chunk = std::max(1, o.graph_chunk);
-  if (B.fused_tiles > 0) chunk += chunk & 1;
+  if (B.fused_tiles > 0) chunk = (chunk + kPRing - 1) / kPRing * kPRing;
   // everything a captured kernel bakes in is part of the graph key
   auto graph_key = [&] {
     char extra[128];
@@ -785,7 +901,7 @@ static cola_status cg_run(Ctx* c, cola_linop* op, const void* Bin, void* Xout, i
   for (int64_t r = 0; r < R; ++r) any_active |= hst[r].active != 0;
   // one eager iteration sizes every workspace buffer before capture
   if (any_active && o.maxiter > 0) {
-    cg_iteration<T>(c, op, B, N, R, nblk, prec, delta2, refine ? 1 : 0);
+    cg_iteration<T>(c, op, B, N, R, nblk, prec, delta2, refine ? 1 : 0, false);
     iters = 1;
   }
   for (int verify = 0;; ++verify) {

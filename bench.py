@@ -231,6 +231,7 @@ def run_ours(args):
     value = solves / t
     it_per_solve = statistics.mean(iters)
     worst_res = max(i["rel_residual"] for i in info)
+    fp64_updates = statistics.mean(i["updates"] for i in info)
 
     # end to end through the public API: pinned host B in, host X out, timed per step
     e2e_t = 0.0
@@ -248,8 +249,9 @@ def run_ours(args):
         torch.cuda.synchronize()
         e2e_t += e0.elapsed_time(e1) / 1e3
     e2e_t = max_over_ranks(pg, e2e_t, device)
-    e2e = {"value": R * args.e2e_steps * world / e2e_t, "unit": UNIT,
-           "h2d_bytes_per_step": B_host.numel() * 8, "d2h_bytes_per_step": Xh.numel() * 8 + 16}
+    e2e = ({"value": R * args.e2e_steps * world / e2e_t, "unit": UNIT,
+            "h2d_bytes_per_step": B_host.numel() * 8, "d2h_bytes_per_step": Xh.numel() * 8 + 16}
+           if args.e2e_steps > 0 else None)
 
     # dominant kernel: the tensor-core Kronecker mode product, timed alone on the
     # same operator and launch configuration as inside the solve (3 launches / MVM)
@@ -300,6 +302,7 @@ def run_ours(args):
                        "parallelism": f"replicas x{world}"},
             "iters_per_s": round(it_per_solve * args.steps * world / t, 2),
             "cg_iterations_per_solve": it_per_solve,
+            "fp64_replacements_per_solve": fp64_updates,
             "logdets_per_s": round(args.steps * world / t, 4),
             "worst_rel_residual": worst_res, "slq_logdet": ld, "slq_stderr": se,
             "slq_clamped": clamped,

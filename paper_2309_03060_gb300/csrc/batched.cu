@@ -22,7 +22,9 @@
 
 #include <algorithm>
 #include <cmath>
+#include <map>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "internal.h"
@@ -365,6 +367,9 @@ static DevSeg upload_seg(Ctx* c, const char* tag, const SegTables& t, int64_t ca
   return d;
 }
 
+// output-chunk cap of the batched tensor-core launch before tuning
+constexpr int kBatchChunkCap = 128;
+
 static unsigned small_grid(int64_t n) { return (unsigned)std::max<int64_t>(1, (n + 127) / 128); }
 
 cola_status batched_cg_fast(Ctx* c, int32_t nsys, const cola_linop* const* ops,
@@ -413,22 +418,37 @@ cola_status batched_cg_fast(Ctx* c, int32_t nsys, const cola_linop* const* ops,
   double* part_rz = (double*)ws.get("bcg.prz", 8 * cap_blocks);
   double* part_rr = (double*)ws.get("bcg.prr", 8 * cap_blocks);
 
-  // p^T A p partial slots: fixed per system (8 per tile of mode step 2)
-  std::vector<int64_t> tiles2(nsys);
-  int64_t tdot_tot = 0;
-  std::vector<int64_t> tdot_off(nsys);
-  for (int s = 0; s < nsys; ++s) {
-    // step 2 contracts n2: rest = n1, output chunks over n2 (see make_plan)
-    const int64_t n16 = (sys[s].n2 + 15) / 16 * 16;
-    const int64_t chunks = (n16 + 127) / 128;
-    tiles2[s] = (sys[s].n1 + 127) / 128 * chunks;  // per right-hand side
-    tdot_off[s] = tdot_tot;
-    tdot_tot += 8 * tiles2[s] * sys[s].R;
-  }
-  double* tdot = (double*)ws.get("bcg.tdot", 8 * std::max<int64_t>(1, tdot_tot));
+  // p^T A p partial slots: fixed per system (8 per tile of mode step 2); the
+  // tile count depends on the output-chunk width (the tuned N tile)
+  std::vector<int64_t> tiles2(nsys), tdot_off(nsys);
+  auto tdot_layout = [&](int cap) {
+    int64_t tot2 = 0;
+    for (int s = 0; s < nsys; ++s) {
+      // step 2 contracts n2: rest = n1, output chunks over n2 (see make_plan)
+      int chunks = 1;
+      kron_tc_chunk_width((int)sys[s].n2, cap, &chunks);
+      tiles2[s] = (sys[s].n1 + 127) / 128 * chunks;  // per right-hand side
+      tdot_off[s] = tot2;
+      tot2 += 8 * tiles2[s] * sys[s].R;
+    }
+    return tot2;
+  };
+  int64_t tdot_cap = 1;
+  for (int cap : {64, 128}) tdot_cap = std::max(tdot_cap, tdot_layout(cap));
+  double* tdot = (double*)ws.get("bcg.tdot", 8 * tdot_cap);
+  // widest output chunk over the batch under a chunk cap (sizes the stages)
+  auto max_chunk_for = [&](int cap) {
+    int mc = 16;
+    for (auto& s : sys) {
+      int nc = 1;
+      mc = std::max({mc, kron_tc_chunk_width((int)s.n1, cap, &nc),
+                     kron_tc_chunk_width((int)s.n2, cap, &nc)});
+    }
+    return mc;
+  };
   int64_t* seg_p0 = (int64_t*)ws.get("bcg.sp0", 8 * G);
   int* seg_pn = (int*)ws.get("bcg.spn", 4 * G);
-  {
+  auto upload_slot_tables = [&] {
     std::vector<int64_t> hp0(G);
     std::vector<int> hpn(G);
     std::vector<SegShift> hs(G);
@@ -445,7 +465,10 @@ cola_status batched_cg_fast(Ctx* c, int32_t nsys, const cola_linop* const* ops,
     COLA_CUDA(cudaMemcpyAsync(shift, hs.data(), sizeof(SegShift) * G, cudaMemcpyHostToDevice,
                               c->s));
     COLA_CUDA(cudaStreamSynchronize(c->s));
-  }
+  };
+  int tile_cap = kBatchChunkCap, tile_stages = 0;  // set by the tuner below
+  tdot_layout(tile_cap);
+  upload_slot_tables();
 
   // inputs into the packed FP64 right-hand side
   for (int s = 0; s < nsys; ++s)
@@ -462,6 +485,7 @@ cola_status batched_cg_fast(Ctx* c, int32_t nsys, const cola_linop* const* ops,
   static const char* kTc1[2] = {"bcg.tc1a", "bcg.tc1b"};
   static const char* kTc2[2] = {"bcg.tc2a", "bcg.tc2b"};
   auto tc_tables = [&](const std::vector<char>& lv) {
+    tdot_layout(tile_cap);
     for (int q = 0; q < 2; ++q) {
       std::vector<TcBatchProblem> s1, s2;
       for (int s = 0; s < nsys; ++s) {
@@ -496,8 +520,8 @@ cola_status batched_cg_fast(Ctx* c, int32_t nsys, const cola_linop* const* ops,
         q2.epi_dot = tdot + tdot_off[s];
         s2.push_back(q2);
       }
-      kron_tc_batch_upload(c, s1, tf, tv, kTc1[q]);
-      kron_tc_batch_upload(c, s2, tf, tv, kTc2[q]);
+      kron_tc_batch_upload(c, s1, tf, tv, kTc1[q], tile_cap);
+      kron_tc_batch_upload(c, s2, tf, tv, kTc2[q], tile_cap);
     }
   };
 
@@ -565,18 +589,73 @@ cola_status batched_cg_fast(Ctx* c, int32_t nsys, const cola_linop* const* ops,
     c->count_launch();
     COLA_CUDA(cudaGetLastError());
   }
-  tc_tables(live);
-  const double delta2 = o.reliable_delta * o.reliable_delta;
-  int max_chunk = 16;
-  for (auto& s : sys) {
-    const int n16 = (int)((std::max(s.n1, s.n2) + 15) / 16 * 16);
-    const int chunks = (n16 + 127) / 128;
-    max_chunk = std::max(max_chunk, ((n16 + chunks - 1) / chunks + 15) / 16 * 16);
+  // Tile-shape autotuner: the output-chunk width (N tile, 64 or 128 columns)
+  // and the pipeline depth of the batched tensor-core launch are timed on
+  // this batch's own mode steps (two launches per MVM, CUDA events, parity-0
+  // tables; outputs go to scratch buffers the first iteration rewrites), and
+  // the fastest is cached per (terms, histogram of factor sizes and RHS counts).
+  {
+    std::map<std::tuple<int, int, int64_t>, int> hist;
+    for (auto& s : sys)
+      ++hist[std::make_tuple((int)((s.n1 + 31) / 32), (int)((s.n2 + 31) / 32), s.R)];
+    std::string tkey = "bt:" + std::to_string(tf) + std::to_string(tv);
+    for (auto& kv : hist)
+      tkey += ":" + std::to_string(std::get<0>(kv.first)) + "," +
+              std::to_string(std::get<1>(kv.first)) + "," + std::to_string(std::get<2>(kv.first)) +
+              "x" + std::to_string(kv.second);
+    auto hit = c->tuned.find(tkey);
+    if (hit != c->tuned.end()) {
+      tile_cap = hit->second.first;
+      tile_stages = hit->second.second;
+    } else {
+      cudaEvent_t e0, e1;
+      COLA_CUDA(cudaEventCreate(&e0));
+      COLA_CUDA(cudaEventCreate(&e1));
+      float best = 1e30f;
+      int best_cap = kBatchChunkCap, best_st = 0;
+      for (int cap : {64, 128}) {
+        if (cap == 128 && max_chunk_for(64) == max_chunk_for(128)) continue;  // same tiles
+        tile_cap = cap;
+        tc_tables(live);
+        const int mc = max_chunk_for(cap);
+        for (int stg = 2; stg <= kron_tc_batch_max_stages(tf, tv, mc); ++stg) {
+          kron_tc_batch_launch(c, kTc1[0], tf, tv, mc, stg);  // warm-up
+          kron_tc_batch_launch(c, kTc2[0], tf, tv, mc, stg);
+          COLA_CUDA(cudaEventRecord(e0, c->s));
+          for (int rep = 0; rep < 2; ++rep) {
+            kron_tc_batch_launch(c, kTc1[0], tf, tv, mc, stg);
+            kron_tc_batch_launch(c, kTc2[0], tf, tv, mc, stg);
+          }
+          COLA_CUDA(cudaEventRecord(e1, c->s));
+          COLA_CUDA(cudaEventSynchronize(e1));
+          float ms = 0.0f;
+          COLA_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+          if (ms < best) {
+            best = ms;
+            best_cap = cap;
+            best_st = stg;
+          }
+        }
+      }
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      tc_check_error(c);
+      tile_cap = best_cap;
+      tile_stages = best_st;
+      c->tuned[tkey] = std::make_pair(tile_cap, tile_stages);
+    }
+    const char* tr = getenv("COLA_TRACE");
+    if (tr && tr[0] == '1')
+      fprintf(stderr, "[cola batched] N tile <= %d columns, %d stages\n", tile_cap, tile_stages);
   }
+  tc_tables(live);
+  upload_slot_tables();
+  const double delta2 = o.reliable_delta * o.reliable_delta;
+  const int max_chunk = max_chunk_for(tile_cap);
   int cur = 0;  // parity: the current search direction is pbuf[cur]
   auto iteration = [&] {
-    kron_tc_batch_launch(c, kTc1[cur], tf, tv, max_chunk);
-    kron_tc_batch_launch(c, kTc2[cur], tf, tv, max_chunk);
+    kron_tc_batch_launch(c, kTc1[cur], tf, tv, max_chunk, tile_stages);
+    kron_tc_batch_launch(c, kTc2[cur], tf, tv, max_chunk, tile_stages);
     float* p_new = pbuf[cur ^ 1];
     cur ^= 1;
     k_seg_alpha<<<small_grid(G), 128, 0, c->s>>>(st, live_seg.seg_list, live_seg.nseg, seg_p0,

@@ -77,6 +77,8 @@ struct Ctx {
   bool capturing = false;
   int64_t captured = 0;
   std::map<std::string, GraphEntry> graphs;
+  // tile shapes picked by timing for batched solves: key -> (chunk cap, stages)
+  std::map<std::string, std::pair<int, int>> tuned;
   void* pinned = nullptr;     // small host staging area (pinned)
   size_t pinned_bytes = 0;
   int* tc_err_host = nullptr;  // pinned copy of the tensor-core timeout flag
@@ -291,10 +293,15 @@ struct TcBatchProblem {
 };
 // Uploads the problem and tile tables into workspace buffers named after
 // `tag` and returns the number of tiles per problem (in table order).
+// Every problem's output columns go in chunks of at most chunk_cap (64 or 128).
 std::vector<int64_t> kron_tc_batch_upload(Ctx* c, const std::vector<TcBatchProblem>& probs,
-                                          int tf, int tv, const char* tag);
-// Launches one persistent k_kron_tc over the table uploaded under `tag`.
-void kron_tc_batch_launch(Ctx* c, const char* tag, int tf, int tv, int max_n_chunk);
+                                          int tf, int tv, const char* tag, int chunk_cap);
+// Launches one persistent k_kron_tc over the table uploaded under `tag` with
+// `stages` pipeline stages (0: as many as fit, at most 4).
+void kron_tc_batch_launch(Ctx* c, const char* tag, int tf, int tv, int max_n_chunk, int stages);
+int kron_tc_batch_max_stages(int tf, int tv, int max_n_chunk);
+// Chunk width (and count) of n_out output columns under a chunk cap.
+int kron_tc_chunk_width(int n_out, int chunk_cap, int* nchunks);
 
 // Programmatic dependent launch: a kernel launched with launch_pdl may start
 // while the previous kernel on the stream is still running.  It must call

@@ -51,6 +51,7 @@ struct TcParams {
   const uint16_t* Bimg;  // [tf][kblocks][n_pad rows][64] bf16, 128-byte swizzled rows
   int64_t rest, size_in, size_out, batch, tiles_m, ntiles;
   int n_in, n_out, n_pad, kblocks, ksteps_last, tf, tv, stages, nbuf;
+  int img_rows;          // rows per (term, k block) of the split factor image (>= n_pad)
   int n_chunk, nchunks;  // output columns per tile (<= 256) and chunks per row tile
   uint32_t stage_bytes, a_term_bytes, b_term_bytes, tmem_cols;
   float coeff, beta;
@@ -320,7 +321,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_kron_tc(Src src, TcParams K) 
           mbar_expect_tx(&full[s], p.b_term_bytes * K.tf);
           for (int ti = 0; ti < K.tf; ++ti)
             bulk_g2s(st + K.tv * K.a_term_bytes + ti * p.b_term_bytes,
-                     p.Bimg + (((size_t)ti * p.kblocks + kb) * (size_t)p.n_pad +
+                     p.Bimg + (((size_t)ti * p.kblocks + kb) * (size_t)p.img_rows +
                                (size_t)nc * p.n_chunk) * kBlockK,
                      p.b_term_bytes, &full[s]);
           last_s = s;
@@ -598,6 +599,7 @@ struct TcFsParams {
   float* Y;
   int64_t rest, size_in, size_out, tiles_m, ntiles;
   int n_in, n_out, n_pad, kblocks, ksteps_last, xstages, nsrc;
+  int img_rows;  // rows per (term, k block) of the split factor image
   int e_mode;  // epilogue: 0 store; 1 fused shift term and p . Ap partials; 2 add beta Y
   uint32_t x_src_bytes, e_bytes;  // e_bytes: rows staged per tile for e_mode 1 and 2
   const float* e_src;             // staged rows: p (e_mode 1) or the old Y (e_mode 2)
@@ -943,7 +945,7 @@ __global__ void __launch_bounds__(kThreadsFs, 1) k_kron_tc_fs(const __grid_const
           uint32_t u[16];
           if (i < p.n_pad) {
             const uint4* src = reinterpret_cast<const uint4*>(
-                p.Bimg + ((size_t)(ti * p.kblocks + chalf) * p.n_pad + i) * kBlockK);
+                p.Bimg + ((size_t)(ti * p.kblocks + chalf) * p.img_rows + i) * kBlockK);
 #pragma unroll
             for (int c = 0; c < 4; ++c) {
               const uint4 q = __ldg(src + ((hh * 4 + c) ^ (i & 7)));
@@ -1049,24 +1051,39 @@ __global__ void k_split_factor(const TF* F, int64_t ld, int tr, int n_out, int n
 }
 
 constexpr int kChunkMax = 128;
+// output-chunk widths (N tile) the batched launch can be tuned over
+constexpr int kChunkCaps[2] = {64, 128};
 
 struct TcPlan {
   int n_in, n_out, n_pad, kblocks, ksteps_last, tf, tv, stages, nbuf, n_chunk, nchunks;
+  int img_rows;
   uint32_t stage_bytes, a_term_bytes, b_term_bytes, tmem_cols;
   size_t smem;
 };
 
-TcPlan make_plan(int n_in, int n_out, int tf, int tv) {
+// Output columns padded to 16 and split into equal chunks of at most `cap`.
+static int chunk_layout(int n_out, int cap, int* nchunks) {
+  const int n16 = (n_out + 15) / 16 * 16;
+  *nchunks = (n16 + cap - 1) / cap;
+  return ((n16 + *nchunks - 1) / *nchunks + 15) / 16 * 16;
+}
+
+TcPlan make_plan(int n_in, int n_out, int tf, int tv, int chunk_cap = kChunkMax) {
   TcPlan q{};
   q.n_in = n_in;
   q.n_out = n_out;
-  // output columns in chunks of at most 128 (keeps two pipeline stages of
-  // A and B terms in shared memory); the image is padded to a whole number
+  // output columns in chunks of at most chunk_cap (128 keeps two pipeline
+  // stages of A and B terms in shared memory); a plan covers a whole number
   // of equal chunks
-  const int n16 = (n_out + 15) / 16 * 16;
-  q.nchunks = (n16 + kChunkMax - 1) / kChunkMax;
-  q.n_chunk = ((n16 + q.nchunks - 1) / q.nchunks + 15) / 16 * 16;
+  q.n_chunk = chunk_layout(n_out, chunk_cap, &q.nchunks);
   q.n_pad = q.nchunks * q.n_chunk;
+  // the split factor image holds enough (zero) rows for every chunk width
+  q.img_rows = q.n_pad;
+  for (int cap : kChunkCaps) {
+    int nc = 0;
+    const int w = chunk_layout(n_out, cap, &nc);
+    q.img_rows = std::max(q.img_rows, nc * w);
+  }
   const int kpad = (n_in + 15) / 16 * 16;
   q.kblocks = (kpad + kBlockK - 1) / kBlockK;
   q.ksteps_last = (kpad - (q.kblocks - 1) * kBlockK) / 16;
@@ -1158,7 +1175,7 @@ void kron_tc_prepare(Ctx* c, cola_linop* op, int split_terms) {
     for (int tr = 0; tr < 2; ++tr) {
       const int n_out = (int)(tr ? f->cols : f->rows), n_in = (int)(tr ? f->rows : f->cols);
       const TcPlan q = make_plan(n_in, n_out, tf, 2);
-      const size_t per_term = (size_t)q.kblocks * q.n_pad * kBlockK;
+      const size_t per_term = (size_t)q.kblocks * q.img_rows * kBlockK;
       const int key = 100 + tr * 10 + tf;
       auto it = f->derived.find(key);
       void* img;
@@ -1175,11 +1192,11 @@ void kron_tc_prepare(Ctx* c, cola_linop* op, int split_terms) {
       const int grid = (int)std::min<size_t>(1024, (per_term + 255) / 256);
       if (f->dtype == COLA_F64)
         k_split_factor<double><<<grid, 256, 0, c->s>>>((const double*)f->data, f->ld, tr, n_out,
-                                                        n_in, q.n_pad, q.kblocks, tf,
+                                                        n_in, q.img_rows, q.kblocks, tf,
                                                         (uint16_t*)img);
       else
         k_split_factor<float><<<grid, 256, 0, c->s>>>((const float*)f->data, f->ld, tr, n_out,
-                                                      n_in, q.n_pad, q.kblocks, tf,
+                                                      n_in, q.img_rows, q.kblocks, tf,
                                                       (uint16_t*)img);
       c->count_launch();
       COLA_CUDA(cudaGetLastError());
@@ -1262,6 +1279,7 @@ static bool fs_plan(const TcParams& p, TcFsParams& r) {
   r.n_in = p.n_in;
   r.n_out = p.n_out;
   r.n_pad = p.n_pad;
+  r.img_rows = p.img_rows;
   r.kblocks = p.kblocks;
   r.ksteps_last = p.ksteps_last;
   r.nsrc = p.pro_z ? 2 : 1;
@@ -1346,6 +1364,7 @@ static int64_t kron_tc_run(Ctx* c, const cola_linop* op, const float* X, float* 
     p.n_in = n_in;
     p.n_out = n_out;
     p.n_pad = q.n_pad;
+    p.img_rows = q.img_rows;
     p.kblocks = q.kblocks;
     p.ksteps_last = q.ksteps_last;
     p.tf = tf;
@@ -1458,7 +1477,7 @@ static std::string tagged(const char* tag, const char* what) {
 }
 
 std::vector<int64_t> kron_tc_batch_upload(Ctx* c, const std::vector<TcBatchProblem>& probs,
-                                          int tf, int tv, const char* tag) {
+                                          int tf, int tv, const char* tag, int chunk_cap) {
   std::vector<TcParams> hp(probs.size());
   std::vector<int64_t> first(probs.size()), counts(probs.size());
   std::vector<int> tile_prob;
@@ -1468,7 +1487,7 @@ std::vector<int64_t> kron_tc_batch_upload(Ctx* c, const std::vector<TcBatchProbl
     const cola_linop* f = b.factor;
     const int n_in = (int)(b.transpose ? f->rows : f->cols);
     const int n_out = (int)(b.transpose ? f->cols : f->rows);
-    const TcPlan q = make_plan(n_in, n_out, tf, tv);
+    const TcPlan q = make_plan(n_in, n_out, tf, tv, chunk_cap);
     TcParams& p = hp[i];
     p = TcParams{};
     p.X = b.X;
@@ -1488,6 +1507,7 @@ std::vector<int64_t> kron_tc_batch_upload(Ctx* c, const std::vector<TcBatchProbl
     p.n_in = n_in;
     p.n_out = n_out;
     p.n_pad = q.n_pad;
+    p.img_rows = q.img_rows;
     p.kblocks = q.kblocks;
     p.ksteps_last = q.ksteps_last;
     p.b_term_bytes = q.b_term_bytes;
@@ -1528,14 +1548,25 @@ std::vector<int64_t> kron_tc_batch_upload(Ctx* c, const std::vector<TcBatchProbl
   return counts;
 }
 
-void kron_tc_batch_launch(Ctx* c, const char* tag, int tf, int tv, int max_n_chunk) {
+int kron_tc_batch_max_stages(int tf, int tv, int max_n_chunk) {
+  uint32_t sb = (uint32_t)(tv * kTileM * 128 + tf * (uint32_t)max_n_chunk * 128u);
+  sb = (sb + 1023) / 1024 * 1024;
+  return (int)std::min<size_t>(4, (size_t)(200 * 1024) / sb);
+}
+
+int kron_tc_chunk_width(int n_out, int chunk_cap, int* nchunks) {
+  return chunk_layout(n_out, chunk_cap, nchunks);
+}
+
+void kron_tc_batch_launch(Ctx* c, const char* tag, int tf, int tv, int max_n_chunk, int stages) {
   TcParams K{};
   K.tf = tf;
   K.tv = tv;
   K.a_term_bytes = kTileM * 128;
   K.stage_bytes = (uint32_t)(tv * K.a_term_bytes + tf * (uint32_t)max_n_chunk * 128u);
   K.stage_bytes = (K.stage_bytes + 1023) / 1024 * 1024;
-  K.stages = (int)std::min<size_t>(4, (size_t)(200 * 1024) / K.stage_bytes);
+  const int max_stages = kron_tc_batch_max_stages(tf, tv, max_n_chunk);
+  K.stages = stages > 0 ? std::min(stages, max_stages) : max_stages;
   K.n_chunk = max_n_chunk;
   K.nbuf = (4 * max_n_chunk <= 512) ? 2 : 1;
   uint32_t cols = 32;

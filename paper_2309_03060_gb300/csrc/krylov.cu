@@ -191,25 +191,38 @@ __global__ void k_cg_r4(int64_t n4, float4* r, const float4* Ap, const float4* i
   const float4* Av = Ap + v * n4;
   float4* zv = z ? z + v * n4 : nullptr;
   float s_rz = 0.0f, s_rr = 0.0f;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4;
-       i += (int64_t)nblk * blockDim.x) {
-    float4 ri = rv[i];
-    if (a != 0.0f) {
-      const float4 ai = Av[i];
-      ri.x = fmaf(-a, ai.x, ri.x);
-      ri.y = fmaf(-a, ai.y, ri.y);
-      ri.z = fmaf(-a, ai.z, ri.z);
-      ri.w = fmaf(-a, ai.w, ri.w);
-      rv[i] = ri;
+  const int64_t stride = (int64_t)nblk * blockDim.x;
+  // two elements per step, both loaded before either is stored: twice the
+  // bytes in flight of a one-element loop
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += 2 * stride) {
+    const int64_t j = i + stride;
+    const bool two = j < n4;
+    float4 ri[2], ai[2];
+    ri[0] = rv[i];
+    ai[0] = a != 0.0f ? Av[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+    ri[1] = two ? rv[j] : make_float4(0.f, 0.f, 0.f, 0.f);
+    ai[1] = (two && a != 0.0f) ? Av[j] : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      if (u == 1 && !two) break;
+      const int64_t k = u ? j : i;
+      float4 r4 = ri[u];
+      if (a != 0.0f) {
+        r4.x = fmaf(-a, ai[u].x, r4.x);
+        r4.y = fmaf(-a, ai[u].y, r4.y);
+        r4.z = fmaf(-a, ai[u].z, r4.z);
+        r4.w = fmaf(-a, ai[u].w, r4.w);
+        rv[k] = r4;
+      }
+      float4 zi = r4;
+      if (invd) {
+        const float4 d = invd[k];
+        zi = make_float4(r4.x * d.x, r4.y * d.y, r4.z * d.z, r4.w * d.w);
+        zv[k] = zi;
+      }
+      s_rz = fmaf(r4.x, zi.x, fmaf(r4.y, zi.y, fmaf(r4.z, zi.z, fmaf(r4.w, zi.w, s_rz))));
+      s_rr = fmaf(r4.x, r4.x, fmaf(r4.y, r4.y, fmaf(r4.z, r4.z, fmaf(r4.w, r4.w, s_rr))));
     }
-    float4 zi = ri;
-    if (invd) {
-      const float4 d = invd[i];
-      zi = make_float4(ri.x * d.x, ri.y * d.y, ri.z * d.z, ri.w * d.w);
-      zv[i] = zi;
-    }
-    s_rz = fmaf(ri.x, zi.x, fmaf(ri.y, zi.y, fmaf(ri.z, zi.z, fmaf(ri.w, zi.w, s_rz))));
-    s_rr = fmaf(ri.x, ri.x, fmaf(ri.y, ri.y, fmaf(ri.z, ri.z, fmaf(ri.w, ri.w, s_rr))));
   }
   double rr;
   const double rz = block_sum2(s_rz, &rr, s_rr);

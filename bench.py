@@ -127,6 +127,18 @@ def barrier(pg):
         pg.barrier()
 
 
+def rank_rhs(w, rank: int):
+    """Right-hand sides of one rank: the workload's own block on rank 0, an
+    independent seeded block of the same shape on every other rank (replicas
+    of the workload, no data shared between ranks)."""
+    return w.B if rank == 0 else wl.normal(wl.substream(w.seed, 100 + rank), w.B.shape)
+
+
+def rank_probe_seed(w, rank: int) -> int:
+    """Seed of the SLQ probes of one rank (rank 0 keeps the workload's own)."""
+    return wl.substream(w.seed, 2) if rank == 0 else wl.substream(w.seed, 200 + rank)
+
+
 # ----------------------------------------------------------------- our arm
 def build_operator(cola, ctx, w, device):
     import torch
@@ -188,14 +200,13 @@ def run_ours(args):
     w = wl.config2(nrhs=args.nrhs)
     op, kron = build_operator(cola, ctx, w, device)
     # each rank solves its own independent block of right-hand sides
-    B_host = torch.tensor(w.B if rank == 0 else
-                          wl.normal(wl.substream(w.seed, 100 + rank), w.B.shape)).pin_memory()
+    B_host = torch.tensor(rank_rhs(w, rank)).pin_memory()
     B = B_host.to(device)
     opts = cola.cola_cg_opts_default(precision=cola.PREC_MIXED, refine=1, tol=w.tol,
                                      maxiter=args.maxiter, split_factor_terms=args.fterms,
                                      split_vector_terms=args.vterms, graph_chunk=args.chunk,
                                      reliable_delta=args.delta)
-    seed = wl.substream(w.seed, 2)
+    seed = rank_probe_seed(w, rank)
     stream = torch.cuda.current_stream()
 
     def step():

@@ -150,19 +150,20 @@ def build_operator(cola, ctx, w, device):
 
 
 def time_queued(torch, ctx, fn, reps):
-    """Device time of `reps` calls of fn, on the library's launch stream, with
-    every launch queued before the device reaches the first one (a device-side
-    sleep holds the stream while the host enqueues), so host overhead between
-    calls is not timed.  Returns seconds per call."""
+    """Device time of `reps` calls of fn, on the library's launch stream (the
+    calls are issued on that stream, so no cross-stream join sits between
+    them), with every launch queued before the device reaches the first one (a
+    device-side sleep holds the stream while the host enqueues), so host
+    overhead between calls is not timed.  Returns seconds per call."""
     ls = ctx.stream()
     k0, k1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     with torch.cuda.stream(ls):
         torch.cuda._sleep(50_000_000)      # ~25 ms at 2 GHz
-    k0.record(ls)
-    for _ in range(reps):
-        fn()
-    k1.record(ls)
+        k0.record(ls)
+        for _ in range(reps):
+            fn()
+        k1.record(ls)
     torch.cuda.synchronize()
     return k0.elapsed_time(k1) / 1e3 / reps
 

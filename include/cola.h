@@ -306,9 +306,10 @@ cola_status cola_kron_matvec_noalloc(int nfactors, const int64_t* rows, const in
 cola_status cola_kernel_launches(const cola_ctx* ctx, int64_t* count);
 
 /* The context's internal launch stream (every kernel of this library runs on
- * it; calls join the caller's stream before and after).  Exposed so that a
- * caller can time kernels with events on the stream they run on.  No
- * counterpart in the paper.  The stream is owned by the context and stays
+ * it; calls join the caller's stream before and after, or not at all when the
+ * caller passes this stream itself).  Exposed so that a caller can time
+ * kernels with events on the stream they run on, or queue its own work on it.
+ * No counterpart in the paper.  The stream is owned by the context and stays
  * valid until cola_destroy. */
 cola_status cola_get_stream(const cola_ctx* ctx, cola_stream* stream);
 

@@ -66,13 +66,16 @@ void* Ctx::host_pinned(size_t bytes) {
   return pinned;
 }
 
+// A caller that already works on the context's own stream needs no join.
 StreamJoin::StreamJoin(Ctx* c_, cola_stream s) : c(c_), user((cudaStream_t)s) {
   COLA_CUDA(cudaSetDevice(c->device));
+  if (user == c->s) return;
   COLA_CUDA(cudaEventRecord(c->ev_a, user));
   COLA_CUDA(cudaStreamWaitEvent(c->s, c->ev_a, 0));
 }
 
 StreamJoin::~StreamJoin() {
+  if (user == c->s) return;
   cudaEventRecord(c->ev_b, c->s);
   cudaStreamWaitEvent(user, c->ev_b, 0);
 }

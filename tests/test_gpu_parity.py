@@ -390,6 +390,27 @@ def test_matvec_mixed_kron3_full_size_sampled(cola, ctx):
             assert abs(Yh[r, I] - ref) <= MIXED_TOL[3] * 3 * bound
 
 
+def test_matvec_on_library_stream_matches_joined_call(cola, ctx):
+    """A caller working on the context's own stream (no cross-stream join)
+    gets bit-identical results to a call from another stream, also for calls
+    queued back to back before the device reaches them."""
+    w = wl.config2(nrhs=2)
+    spec = ("sum", [("kron", [("dense", f) for f in w.factors]), ("scalar", w.shift, w.N)], None)
+    op = gpu_tree(cola, ctx, spec, torch.float64, DEV)
+    X = torch.tensor(w.B, dtype=torch.float32, device=DEV)
+    ref = cola.cola_matvec(ctx, op, X, cola.PREC_MIXED, split_terms=3)
+    torch.cuda.synchronize()
+    ls = ctx.stream()
+    outs = [torch.empty_like(X) for _ in range(3)]
+    with torch.cuda.stream(ls):
+        torch.cuda._sleep(2_000_000)
+        for o in outs:
+            cola.cola_matvec(ctx, op, X, cola.PREC_MIXED, out=o, split_terms=3)
+    torch.cuda.synchronize()
+    for o in outs:
+        assert torch.equal(o, ref)
+
+
 @pytest.mark.parametrize("terms", [(2, 2), (3, 2), (3, 3)])
 def test_cg_mixed_reaches_1e8(cola, ctx, terms):
     K1, K2, B, spec = _kron_shift_problem(64, 96, 0.01, 4, 15)

@@ -288,6 +288,28 @@ def run_ours(args):
 
     cpu = cpu_baseline(args, w, it_per_solve) if (rank == 0 and not args.no_cpu) else None
 
+    # the structured path: direct solve from the factor eigendecompositions
+    # (Table 3 Inverse / Eigs rules) on the same right-hand sides, and the
+    # exact log-det that the SLQ estimate is compared with
+    eig = None
+    if rank == 0 and args.eig:
+        Xe = cola.cola_kron_eig_solve(ctx, op, B, cola.PREC_F64)  # eigendecompositions here
+        torch.cuda.synchronize()
+        g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        g0.record(stream)
+        for _ in range(3):
+            cola.cola_kron_eig_solve(ctx, op, B, cola.PREC_F64, out=Xe)
+        g1.record(stream)
+        torch.cuda.synchronize()
+        te = g0.elapsed_time(g1) / 1e3 / 3
+        Ae = cola.cola_matvec(ctx, op, Xe, cola.PREC_F64)
+        rel_e = float(((B - Ae).norm(dim=1) / B.norm(dim=1)).max())
+        ld_exact = cola.cola_kron_eig_logdet(ctx, op)
+        eig = {"solves_per_s": round(R / te, 2), "worst_rel_residual": rel_e,
+               "path": "FP64 mode products with the factor eigenvectors + eigenvalue scaling",
+               "logdet_exact": ld_exact,
+               "slq_rel_error": abs(ld - ld_exact) / abs(ld_exact)}
+
     plain = None
     if rank == 0 and args.plain:
         popts = cola.cola_cg_opts_default(precision=cola.PREC_F32, refine=1, tol=w.tol,
@@ -324,7 +346,7 @@ def run_ours(args):
             "iteration_roofline": {"alg_bytes_per_iter": iter_alg,
                                    "step_time_s": round(it_time, 4)},
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
-            "clocks": clk, "plain_fp32": plain,
+            "clocks": clk, "plain_fp32": plain, "kron_eig": eig,
         }
         print(json.dumps(line))
     ctx.close()
@@ -409,6 +431,8 @@ def main():
     # DRAM bytes of one k_kron_tc_fs launch from its ncu capture (reads + writes)
     ap.add_argument("--traffic-bytes", type=float, default=211.621376e6)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--eig", action=argparse.BooleanOptionalAction, default=True,
+                    help="also time the eigen-structured direct solve and exact log-det")
     ap.add_argument("--plain", action=argparse.BooleanOptionalAction, default=True,
                     help="also time the plain FP32 path once (--no-plain skips it)")
     ap.add_argument("--mvm-only", action="store_true",

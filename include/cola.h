@@ -201,6 +201,42 @@ cola_status cola_cg_solve_batched(cola_ctx* ctx, int32_t nsys, const cola_linop*
                                   const cola_cg_opts* opts, cola_cg_info* info,
                                   cola_stream stream);
 
+/* ------------------------------------------- Kronecker eigen-structured path */
+
+/* X = A^-1 B directly, for A = c_k (K_1 (x) ... (x) K_d) [+ c_d s I] with
+ * square symmetric dense factors and a scalar shift (the operator as built by
+ * cola_linop_kron, optionally summed with cola_linop_diag of a scalar): the
+ * eigenvectors of a Kronecker product are the Kronecker product of the factor
+ * eigenvectors and its eigenvalues the products of the factor eigenvalues
+ * (Table 3, Inverse and Eigs rules), so
+ *   X = ((x)_k V_k) diag(1 / (c_k prod_k lambda_k + c_d s)) ((x)_k V_k)^T B.
+ * Each factor's eigendecomposition is computed on the host in FP64
+ * (cola_sym_eig) on first use and cached on the factor; it is recomputed when
+ * the factor's contents change (the factor is read back to compare).
+ * B, X: [nrhs][N], FP64 for COLA_PREC_F64 (FP64 mode products) and FP32 for
+ * COLA_PREC_F32 (FP32 mode products, eigenvalue scaling in FP64).
+ * COLA_ERR_UNSUPPORTED for any other operator shape (a per-element diagonal
+ * is not diagonalised by the factor eigenvectors); COLA_ERR_INVALID_ARG for
+ * a factor that is not symmetric.  Synchronous on first use of a factor,
+ * asynchronous on stream afterwards. */
+cola_status cola_kron_eig_solve(cola_ctx* ctx, const cola_linop* op, const void* B, void* X,
+                                int64_t nrhs, cola_precision prec, cola_stream stream);
+
+/* Exact log det A for the same operator class: the sum over all N index
+ * tuples of log(c_k prod_k lambda_k[i_k] + c_d s) (Table 3 LogDet rule with the
+ * Eigs rule; App. A.1.2), reduced in FP64 in a fixed order.
+ * COLA_ERR_BREAKDOWN if any eigenvalue of A is <= 0.  Synchronous. */
+cola_status cola_kron_eig_logdet(cola_ctx* ctx, const cola_linop* op, double* logdet,
+                                 cola_stream stream);
+
+/* Symmetric eigendecomposition of an n x n matrix in HOST memory, the routine
+ * the two calls above apply to each factor: A = V diag(w) V^T with V's
+ * column j the unit eigenvector of w[j].  Householder tridiagonalisation and
+ * implicit symmetric QR with Wilkinson shifts, FP64 (Golub & Van Loan 8.3).
+ * A (row-major, symmetric) is read only; V (n x n row-major) and w (n) are
+ * written.  Needs no GPU. */
+cola_status cola_sym_eig(int64_t n, const double* A, double* V, double* w);
+
 /* --------------------------------------------------------- Lanczos / SLQ */
 
 /* m steps of symmetric Lanczos from q_0 = Q0[v] / ||Q0[v]|| for nvec starting

@@ -199,6 +199,43 @@ def cola_matvec(ctx: Context, op: LinOp, X: torch.Tensor, precision: int = PREC_
     return Y if X.dim() == 2 else Y.reshape(-1)
 
 
+def cola_kron_eig_solve(ctx: Context, op: LinOp, B: torch.Tensor, precision: int = PREC_F64,
+                        out: torch.Tensor | None = None) -> torch.Tensor:
+    """X = A^-1 B from the factor eigendecompositions (A = c K_1 (x) ... (x) K_d [+ s I])."""
+    B2 = B if B.dim() == 2 else B.reshape(1, -1)
+    rows, cols = op.shape
+    if B2.shape[1] != rows:
+        raise ValueError(f"B has {B2.shape[1]} columns, operator has {rows} rows")
+    want = torch.float64 if precision == PREC_F64 else torch.float32
+    if B2.dtype != want or precision not in (PREC_F64, PREC_F32):
+        raise TypeError("precision F64 needs float64 vectors, F32 float32 vectors")
+    X = out if out is not None else torch.empty_like(B2)
+    check(_lib().cola_kron_eig_solve(ctx.handle, op.handle, _ptr(B2), _ptr(X), B2.shape[0],
+                                     precision, _stream()))
+    return X if B.dim() == 2 else X.reshape(-1)
+
+
+def cola_kron_eig_logdet(ctx: Context, op: LinOp) -> float:
+    """Exact log det A from the factor eigenvalues."""
+    v = C.c_double()
+    check(_lib().cola_kron_eig_logdet(ctx.handle, op.handle, C.byref(v), _stream()))
+    return v.value
+
+
+def cola_sym_eig(A):
+    """(w, V) with A = V diag(w) V^T for a symmetric matrix in host memory
+    (a numpy array); the routine applied to every Kronecker factor."""
+    import numpy as np
+    A = np.ascontiguousarray(A, dtype=np.float64)
+    n = A.shape[0]
+    if A.shape != (n, n):
+        raise ValueError("A must be square")
+    V = np.empty((n, n))
+    w = np.empty(n)
+    check(_lib().cola_sym_eig(n, A.ctypes.data, V.ctypes.data, w.ctypes.data))
+    return w, V
+
+
 def cola_cg_opts_default(**kw) -> cola_cg_opts:
     o = cola_cg_opts()
     _lib().cola_cg_opts_default(C.byref(o))

@@ -112,6 +112,7 @@ enum LinKind { LK_DENSE, LK_DIAG, LK_LOWRANK, LK_KRON, LK_KRONSUM, LK_SUM, LK_PR
 struct cola_linop {
   cola_ctx* ctx = nullptr;
   uint64_t uid = 0;             // unique per node for the life of the process
+  uint64_t eig_hash = 0;        // contents hash of the factor its cached eigendecomposition is of
   LinKind kind = LK_DENSE;
   int64_t rows = 0, cols = 0;
   int refs = 1;

@@ -1,0 +1,393 @@
+// Structured solve and log-determinant of shifted Kronecker operators from the
+// eigendecompositions of their factors (Table 3: the inverse and the
+// eigendecomposition of a Kronecker product are built from the factors';
+// Sec. 3.2 composition rules).  For
+//     A = c_k (K_1 (x) ... (x) K_d) + c_d s I,   K_k = V_k diag(lambda_k) V_k^T,
+// the eigenvectors of A are (x)_k V_k and its eigenvalues c_k prod_k lambda_k[i_k] + c_d s, so
+//     A^-1 B     = ((x)_k V_k) diag(1 / (c_k prod lambda + c_d s)) ((x)_k V_k)^T B,
+//     log det A  = sum over all index tuples of log(c_k prod lambda + c_d s).
+// The factor eigendecompositions are computed once on the host in FP64 and
+// cached on the factor (recomputed when its contents change); the solve is
+// 2 d cyclic mode products plus one diagonal scaling on the GPU.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "internal.h"
+
+namespace cola {
+
+namespace {
+
+// Symmetric eigendecomposition on the host (FP64): Householder reduction to
+// tridiagonal form, then implicit symmetric QR steps with Wilkinson shifts and
+// deflation (Golub & Van Loan, Sec. 8.3), every reflection and rotation
+// applied to the accumulated orthogonal factor.  a: n x n row-major,
+// symmetric (destroyed).  Vt: n x n row-major, row j = the eigenvector of w[j].
+void sym_eig(int n, double* a, double* Vt, double* w) {
+  for (int i = 0; i < n * n; ++i) Vt[i] = 0.0;
+  for (int i = 0; i < n; ++i) Vt[(size_t)i * n + i] = 1.0;
+  std::vector<double> v(n), p(n), q(n), u(n);
+  // T = H_{n-3} ... H_0 A H_0 ... H_{n-3}; Vt accumulates H_{n-3} ... H_0
+  for (int k = 0; k + 2 < n; ++k) {
+    double sig = 0.0;
+    for (int i = k + 1; i < n; ++i) sig += a[(size_t)i * n + k] * a[(size_t)i * n + k];
+    if (sig == 0.0) continue;
+    const double x0 = a[(size_t)(k + 1) * n + k];
+    const double alpha = x0 > 0.0 ? -sqrt(sig) : sqrt(sig);
+    std::fill(v.begin(), v.end(), 0.0);
+    v[k + 1] = x0 - alpha;
+    for (int i = k + 2; i < n; ++i) v[i] = a[(size_t)i * n + k];
+    double vv = 0.0;
+    for (int i = k + 1; i < n; ++i) vv += v[i] * v[i];
+    if (vv == 0.0) continue;
+    const double beta = 2.0 / vv;
+    // H A H = A - v q^T - q v^T with p = beta A v, q = p - (beta p.v / 2) v
+    for (int i = k; i < n; ++i) {
+      double s = 0.0;
+      for (int j = k + 1; j < n; ++j) s += a[(size_t)i * n + j] * v[j];
+      p[i] = beta * s;
+    }
+    double pv = 0.0;
+    for (int i = k + 1; i < n; ++i) pv += p[i] * v[i];
+    const double half = 0.5 * beta * pv;
+    for (int i = k; i < n; ++i) q[i] = p[i] - half * v[i];
+    for (int i = k; i < n; ++i)
+      for (int j = k; j < n; ++j) a[(size_t)i * n + j] -= v[i] * q[j] + q[i] * v[j];
+    // Vt <- H Vt: rows k+1.. change by -beta v_i (v^T Vt)
+    std::fill(u.begin(), u.end(), 0.0);
+    for (int i = k + 1; i < n; ++i)
+      for (int j = 0; j < n; ++j) u[j] += v[i] * Vt[(size_t)i * n + j];
+    for (int i = k + 1; i < n; ++i) {
+      const double f = beta * v[i];
+      for (int j = 0; j < n; ++j) Vt[(size_t)i * n + j] -= f * u[j];
+    }
+  }
+  // tridiagonal T: diagonal d, sub-diagonal e
+  std::vector<double> d(n), e(n, 0.0);
+  for (int i = 0; i < n; ++i) d[i] = a[(size_t)i * n + i];
+  for (int i = 0; i + 1 < n; ++i) e[i] = a[(size_t)(i + 1) * n + i];
+  const double eps = 2.220446049250313e-16;
+  int hi = n - 1, it = 0;
+  while (hi > 0 && it < 60 * n) {
+    if (fabs(e[hi - 1]) <= eps * (fabs(d[hi - 1]) + fabs(d[hi]))) {
+      e[hi - 1] = 0.0;
+      --hi;
+      continue;
+    }
+    int lo = hi - 1;
+    while (lo > 0 && fabs(e[lo - 1]) > eps * (fabs(d[lo - 1]) + fabs(d[lo]))) --lo;
+    ++it;
+    // Wilkinson shift from the trailing 2 x 2 block, then chase the bulge down
+    const double dd = 0.5 * (d[hi - 1] - d[hi]), bb = e[hi - 1];
+    const double sg = dd >= 0.0 ? 1.0 : -1.0;
+    const double mu = d[hi] - bb * bb / (dd + sg * hypot(dd, bb));
+    double x = d[lo] - mu, z = e[lo];
+    for (int k = lo; k < hi; ++k) {
+      const double r = hypot(x, z);
+      const double c = x / r, s = z / r;
+      if (k > lo) e[k - 1] = r;
+      const double ak = d[k], ak1 = d[k + 1], bk = e[k];
+      d[k] = c * c * ak + 2.0 * c * s * bk + s * s * ak1;
+      d[k + 1] = s * s * ak - 2.0 * c * s * bk + c * c * ak1;
+      e[k] = c * s * (ak1 - ak) + (c * c - s * s) * bk;
+      double* r0 = Vt + (size_t)k * n;
+      double* r1 = Vt + (size_t)(k + 1) * n;
+      for (int j = 0; j < n; ++j) {
+        const double v0 = r0[j], v1 = r1[j];
+        r0[j] = c * v0 + s * v1;
+        r1[j] = -s * v0 + c * v1;
+      }
+      if (k < hi - 1) {
+        x = e[k];
+        z = s * e[k + 1];
+        e[k + 1] = c * e[k + 1];
+      }
+    }
+  }
+  for (int i = 0; i < n; ++i) w[i] = d[i];
+}
+
+constexpr int kMaxFactors = 8;
+constexpr int kKeyVt64 = 400, kKeyLam64 = 401, kKeyVt32 = 402;
+
+struct EigDims {
+  int d;
+  int64_t n[kMaxFactors];
+  const double* lam[kMaxFactors];
+};
+
+// Eigenvalue of A at flat (row-major) index i.
+__device__ __forceinline__ double eig_at(const EigDims& g, int64_t i, double ck, double shift) {
+  double prod = 1.0;
+  for (int k = g.d - 1; k >= 0; --k) {
+    const int64_t nk = g.n[k];
+    prod *= g.lam[k][i % nk];
+    i /= nk;
+  }
+  return ck * prod + shift;
+}
+
+// Y[r, i] /= lambda_A(i).  The shift c_d s is read from the device scalar.
+template <typename T>
+__global__ void k_eig_scale(T* Y, int64_t N, int64_t R, EigDims g, double ck, const double* s,
+                            double cd) {
+  const double shift = s ? cd * s[0] : 0.0;
+  const int64_t tot = N * R;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < tot;
+       e += (int64_t)gridDim.x * blockDim.x)
+    Y[e] = (T)((double)Y[e] / eig_at(g, e % N, ck, shift));
+}
+
+// Per-block partial sums of log lambda_A(i); nonpos[b] counts lambda <= 0.
+__global__ void k_eig_logdet(int64_t N, EigDims g, double ck, const double* s, double cd,
+                             double* part, int* nonpos) {
+  __shared__ double sh[32];
+  __shared__ int bad;
+  if (threadIdx.x == 0) bad = 0;
+  __syncthreads();
+  const double shift = s ? cd * s[0] : 0.0;
+  double acc = 0.0;
+  int nb = 0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double l = eig_at(g, i, ck, shift);
+    if (l > 0.0)
+      acc += log(l);
+    else
+      ++nb;
+  }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
+  if (nb) atomicAdd(&bad, nb);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
+    part[blockIdx.x] = t;
+    nonpos[blockIdx.x] = bad;
+  }
+}
+
+uint64_t fnv1a(const void* p, size_t bytes) {
+  const unsigned char* b = (const unsigned char*)p;
+  uint64_t h = 1469598103934665603ull;
+  for (size_t i = 0; i < bytes; ++i) {
+    h ^= b[i];
+    h *= 1099511628211ull;
+  }
+  return h;
+}
+
+void* eig_buf(cola_linop* f, int key, size_t bytes) {
+  auto it = f->derived.find(key);
+  if (it != f->derived.end() && it->second.bytes >= bytes) return it->second.p;
+  if (it != f->derived.end()) {
+    cudaFree(it->second.p);
+    f->derived.erase(it);
+  }
+  void* p = nullptr;
+  if (cudaMalloc(&p, std::max<size_t>(bytes, 256)) != cudaSuccess) {
+    cudaGetLastError();
+    fail(COLA_ERR_OOM, "eigendecomposition buffer of %zu bytes", bytes);
+  }
+  f->derived[key] = Buf{p, bytes};
+  return p;
+}
+
+// The operator's parts: Kronecker factors, c_k, and the optional scalar shift.
+struct KronShift {
+  const cola_linop* kron = nullptr;
+  double ck = 1.0, cd = 0.0;
+  const cola_linop* diag = nullptr;
+};
+
+KronShift match(const cola_linop* op) {
+  KronShift m;
+  if (op->kind == LK_KRON) {
+    m.kron = op;
+  } else if (op->kind == LK_SUM && op->kids.size() == 2) {
+    for (int i = 0; i < 2; ++i) {
+      const cola_linop* k = op->kids[i];
+      if (k->kind == LK_KRON) {
+        m.kron = k;
+        m.ck = op->coeffs[i];
+      } else if (k->kind == LK_DIAG && k->stride == 0) {
+        m.diag = k;
+        m.cd = op->coeffs[i];
+      }
+    }
+    if (!m.kron || !m.diag) m.kron = nullptr;
+  }
+  COLA_REQUIRE(m.kron, COLA_ERR_UNSUPPORTED,
+               "the eigen-structured path takes Kron(K_1..K_d) or Kron + scalar * I");
+  COLA_REQUIRE((int)m.kron->kids.size() <= kMaxFactors, COLA_ERR_UNSUPPORTED,
+               "at most %d Kronecker factors", kMaxFactors);
+  for (auto* f : m.kron->kids)
+    COLA_REQUIRE(f->kind == LK_DENSE && f->rows == f->cols, COLA_ERR_UNSUPPORTED,
+                 "the eigen-structured path takes square dense factors");
+  return m;
+}
+
+// Factor eigendecompositions on the device (FP64 Vt and lambda; FP32 Vt when
+// asked), recomputed only when a factor's contents change.
+void prepare_eig(Ctx* c, const KronShift& m, bool want32) {
+  for (auto* fc : m.kron->kids) {
+    cola_linop* f = const_cast<cola_linop*>(fc);
+    const int64_t n = f->rows;
+    std::vector<double> A((size_t)n * n);
+    if (f->dtype == COLA_F64) {
+      COLA_CUDA(cudaMemcpy2DAsync(A.data(), n * 8, f->data, f->ld * 8, n * 8, n,
+                                  cudaMemcpyDeviceToHost, c->s));
+      COLA_CUDA(cudaStreamSynchronize(c->s));
+    } else {
+      std::vector<float> Af((size_t)n * n);
+      COLA_CUDA(cudaMemcpy2DAsync(Af.data(), n * 4, f->data, f->ld * 4, n * 4, n,
+                                  cudaMemcpyDeviceToHost, c->s));
+      COLA_CUDA(cudaStreamSynchronize(c->s));
+      for (size_t i = 0; i < A.size(); ++i) A[i] = Af[i];
+    }
+    const uint64_t h = fnv1a(A.data(), A.size() * 8) ^ (uint64_t)n;
+    const bool have = f->eig_hash == h && f->derived.count(kKeyVt64) && f->derived.count(kKeyLam64);
+    if (!have) {
+      double amax = 0.0, asym = 0.0;
+      for (int64_t i = 0; i < n; ++i)
+        for (int64_t j = 0; j < n; ++j) {
+          amax = std::max(amax, fabs(A[(size_t)i * n + j]));
+          asym = std::max(asym, fabs(A[(size_t)i * n + j] - A[(size_t)j * n + i]));
+        }
+      COLA_REQUIRE(asym <= 1e-12 * amax, COLA_ERR_INVALID_ARG,
+                   "Kronecker factor is not symmetric (max |K - K^T| = %g)", asym);
+      std::vector<double> Vt((size_t)n * n), lam(n);
+      sym_eig((int)n, A.data(), Vt.data(), lam.data());
+      void* dv = eig_buf(f, kKeyVt64, (size_t)n * n * 8);
+      void* dl = eig_buf(f, kKeyLam64, (size_t)n * 8);
+      COLA_CUDA(cudaMemcpyAsync(dv, Vt.data(), (size_t)n * n * 8, cudaMemcpyHostToDevice, c->s));
+      COLA_CUDA(cudaMemcpyAsync(dl, lam.data(), (size_t)n * 8, cudaMemcpyHostToDevice, c->s));
+      std::vector<float> V32(Vt.begin(), Vt.end());
+      void* d32 = eig_buf(f, kKeyVt32, (size_t)n * n * 4);
+      COLA_CUDA(cudaMemcpyAsync(d32, V32.data(), (size_t)n * n * 4, cudaMemcpyHostToDevice, c->s));
+      COLA_CUDA(cudaStreamSynchronize(c->s));  // host vectors go out of scope
+      f->eig_hash = h;
+    }
+  }
+  (void)want32;
+}
+
+EigDims dims_of(const KronShift& m) {
+  EigDims g{};
+  g.d = (int)m.kron->kids.size();
+  for (int k = 0; k < g.d; ++k) {
+    const cola_linop* f = m.kron->kids[k];
+    g.n[k] = f->rows;
+    g.lam[k] = (const double*)f->derived.at(kKeyLam64).p;
+  }
+  return g;
+}
+
+// Y = ((x)_k F_k) X by cyclic mode products with F_k = Vt_k (tr = false) or
+// Vt_k^T = V_k (tr = true); intermediates in two workspace buffers.
+template <typename T>
+void eig_modes(Ctx* c, const KronShift& m, bool tr, const T* X, T* Y, int64_t R) {
+  const int d = (int)m.kron->kids.size();
+  const int64_t N = m.kron->rows;
+  const int key = sizeof(T) == 8 ? kKeyVt64 : kKeyVt32;
+  T* t[2] = {(T*)c->ws.get("keig.t0", sizeof(T) * N * R),
+             (T*)c->ws.get("keig.t1", sizeof(T) * N * R)};
+  const T* cur = X;
+  for (int k = 0; k < d; ++k) {
+    const cola_linop* f = m.kron->kids[k];
+    const int64_t n = f->rows, rest = N / n;
+    const T* F = (const T*)f->derived.at(key).p;
+    T* dst = (k == d - 1) ? Y : t[k & 1];
+    // B[j][i] = F_op[i][j], F_op = tr ? F^T : F (F row-major n x n)
+    gemm<T>(c, rest, n, n, 1.0, cur, 1, rest, N, F, tr ? n : 1, tr ? 1 : n, 0, 0.0, dst, n, 1, N,
+            R);
+    cur = dst;
+  }
+}
+
+template <typename T>
+void eig_solve(Ctx* c, const KronShift& m, const T* B, T* X, int64_t R) {
+  const int64_t N = m.kron->rows;
+  T* mid = (T*)c->ws.get("keig.mid", sizeof(T) * N * R);
+  eig_modes<T>(c, m, false, B, mid, R);  // (x) V^T B
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((N * R + 255) / 256, 8 * c->num_sms));
+  k_eig_scale<T><<<grid, 256, 0, c->s>>>(mid, N, R, dims_of(m), m.ck,
+                                         m.diag ? leaf_ptr<double>(m.diag) : nullptr, m.cd);
+  c->count_launch();
+  COLA_CUDA(cudaGetLastError());
+  eig_modes<T>(c, m, true, mid, X, R);  // (x) V (...)
+}
+
+}  // namespace
+}  // namespace cola
+
+using namespace cola;
+
+cola_status cola_sym_eig(int64_t n, const double* A, double* V, double* w) {
+  return guard([&] {
+    COLA_REQUIRE(A && V && w, COLA_ERR_INVALID_ARG, "NULL argument");
+    COLA_REQUIRE(n >= 1 && n <= 8192, COLA_ERR_INVALID_ARG, "n = %lld", (long long)n);
+    std::vector<double> a(A, A + n * n), Vt((size_t)(n * n));
+    sym_eig((int)n, a.data(), Vt.data(), w);
+    for (int64_t i = 0; i < n; ++i)
+      for (int64_t j = 0; j < n; ++j) V[i * n + j] = Vt[(size_t)(j * n + i)];
+  });
+}
+
+cola_status cola_kron_eig_solve(cola_ctx* ctx, const cola_linop* op, const void* B, void* X,
+                                int64_t nrhs, cola_precision prec, cola_stream stream) {
+  return guard([&] {
+    COLA_REQUIRE(ctx && op && B && X, COLA_ERR_INVALID_ARG, "NULL argument");
+    COLA_REQUIRE(nrhs >= 1, COLA_ERR_INVALID_ARG, "nrhs = %lld", (long long)nrhs);
+    COLA_REQUIRE(prec == COLA_PREC_F64 || prec == COLA_PREC_F32, COLA_ERR_INVALID_ARG,
+                 "precision must be F64 or F32");
+    COLA_REQUIRE(B != X, COLA_ERR_INVALID_ARG, "B and X must not alias");
+    StreamJoin j(ctx, stream);
+    const KronShift m = match(op);
+    cola_linop* mop = const_cast<cola_linop*>(op);
+    prepare_leaves(ctx, mop, COLA_PREC_F64, 0);  // the shift as an FP64 device scalar
+    prepare_eig(ctx, m, prec == COLA_PREC_F32);
+    if (prec == COLA_PREC_F64)
+      eig_solve<double>(ctx, m, (const double*)B, (double*)X, nrhs);
+    else
+      eig_solve<float>(ctx, m, (const float*)B, (float*)X, nrhs);
+  });
+}
+
+cola_status cola_kron_eig_logdet(cola_ctx* ctx, const cola_linop* op, double* logdet,
+                                 cola_stream stream) {
+  return guard([&] {
+    COLA_REQUIRE(ctx && op && logdet, COLA_ERR_INVALID_ARG, "NULL argument");
+    StreamJoin j(ctx, stream);
+    const KronShift m = match(op);
+    prepare_leaves(ctx, const_cast<cola_linop*>(op), COLA_PREC_F64, 0);
+    prepare_eig(ctx, m, false);
+    const int64_t N = m.kron->rows;
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((N + 255) / 256, 1024));
+    double* part = (double*)ctx->ws.get("keig.ldp", 8 * 1024);
+    int* bad = (int*)ctx->ws.get("keig.ldb", 4 * 1024);
+    k_eig_logdet<<<grid, 256, 0, ctx->s>>>(N, dims_of(m), m.ck,
+                                           m.diag ? leaf_ptr<double>(m.diag) : nullptr, m.cd,
+                                           part, bad);
+    ctx->count_launch();
+    COLA_CUDA(cudaGetLastError());
+    std::vector<double> hp(grid);
+    std::vector<int> hb(grid);
+    COLA_CUDA(cudaMemcpyAsync(hp.data(), part, 8 * grid, cudaMemcpyDeviceToHost, ctx->s));
+    COLA_CUDA(cudaMemcpyAsync(hb.data(), bad, 4 * grid, cudaMemcpyDeviceToHost, ctx->s));
+    COLA_CUDA(cudaStreamSynchronize(ctx->s));
+    double s = 0.0;
+    int nb = 0;
+    for (int b = 0; b < grid; ++b) {
+      s += hp[b];
+      nb += hb[b];
+    }
+    COLA_REQUIRE(nb == 0, COLA_ERR_BREAKDOWN, "%d eigenvalues of the operator are <= 0", nb);
+    *logdet = s;
+  });
+}

@@ -300,7 +300,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_kron_tc(Src src, TcParams K) 
     const int64_t ntiles = src.count();
     for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
       int64_t lt;
-      const TcParams& p = src.get(t, lt);
+      const TcParams p = src.get(t, lt);  // by value: one read of the table entry per tile
       const int64_t tm = lt / p.nchunks;
       const int nc = (int)(lt % p.nchunks);
       const int64_t r = tm / p.tiles_m, m0 = (tm % p.tiles_m) * kTileM;
@@ -396,7 +396,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_kron_tc(Src src, TcParams K) 
       const int64_t ntiles = src.count();
       for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++it) {
         int64_t lt;
-        const TcParams& p = src.get(t, lt);
+        const TcParams p = src.get(t, lt);  // by value: one read of the table entry per tile
         const uint32_t idesc = idesc_bf16(kTileM, p.n_chunk);
         const int b = (int)(it % K.nbuf);
         const uint32_t use = (uint32_t)((it / K.nbuf) & 1);
@@ -460,7 +460,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_kron_tc(Src src, TcParams K) 
       if (!mbar_wait(&acc_full[b], (uint32_t)((it / K.nbuf) & 1), abort_flag, K.err)) break;
       tc_fence_after();
       int64_t lt;
-      const TcParams& p = src.get(t, lt);
+      const TcParams p = src.get(t, lt);  // by value: one read of the table entry per tile
       const int64_t tm = lt / p.nchunks;
       const int nc = (int)(lt % p.nchunks);
       const int64_t r = tm / p.tiles_m, m0 = (tm % p.tiles_m) * kTileM;

@@ -149,6 +149,45 @@ def build_operator(cola, ctx, w, device):
     return op, kron
 
 
+def run_batched_workload(cola, ctx, device, hbm_peak, stream):
+    """The batched uneven-systems workload (512 systems K1 (x) K2 + s I, factor
+    sides 16..256, 1..8 right-hand sides each) in one cola_cg_solve_batched
+    call, MIXED + FP64 refinement to 1e-8: one untimed call (tile tuning,
+    graph capture, factor splits), one timed with CUDA events.  The roofline
+    counts 32 N bytes per CG iteration of every right-hand side."""
+    import statistics as st_
+    import torch
+    w4 = wl.config4()
+    ops, Bs = [], []
+    for s in w4.systems:
+        K = [torch.tensor(f, device=device) for f in s.factors]
+        sh = torch.tensor([s.shift], dtype=torch.float64, device=device)
+        kron = cola.cola_linop_kron(ctx, *[cola.cola_linop_dense(ctx, k) for k in K])
+        ops.append(cola.cola_linop_sum(ctx, [kron, cola.cola_linop_diag(ctx, sh, n=s.N)]).set_spd())
+        Bs.append(torch.tensor(s.B, device=device))
+    opts = cola.cola_cg_opts_default(precision=cola.PREC_MIXED, refine=1, tol=w4.tol,
+                                     maxiter=60000, split_factor_terms=3, split_vector_terms=3,
+                                     graph_chunk=64)
+    cola.cola_cg_solve_batched(ctx, ops, Bs, opts)
+    torch.cuda.synchronize()
+    b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    b0.record(stream)
+    Xs, info, status = cola.cola_cg_solve_batched(ctx, ops, Bs, opts)
+    b1.record(stream)
+    torch.cuda.synchronize()
+    t = b0.elapsed_time(b1) / 1e3
+    its = [i["iterations"] for i in info]
+    sizes = [s.N for s, b in zip(w4.systems, Bs) for _ in range(b.shape[0])]
+    alg = sum(32.0 * n * k for n, k in zip(sizes, its))
+    return {"workload": "batched_kron2_uneven: 512 systems K1(x)K2 + s I, n1, n2 in 16..256, "
+                        "1..8 RHS each, tol 1e-8", "systems": len(ops), "rhs": len(its),
+            "seconds": round(t, 3), "solves_per_s": round(len(its) / t, 2), "status": status,
+            "iterations": {"min": min(its), "mean": round(st_.mean(its), 1), "max": max(its)},
+            "worst_rel_residual": max(i["rel_residual"] for i in info),
+            "alg_bytes": alg, "achieved_gbs": round(alg / t / 1e9, 1),
+            "roofline_frac": round(alg / t / 1e9 / hbm_peak, 4)}
+
+
 def time_queued(torch, ctx, fn, reps):
     """Device time of `reps` calls of fn, on the library's launch stream (the
     calls are issued on that stream, so no cross-stream join sits between
@@ -310,6 +349,9 @@ def run_ours(args):
                "logdet_exact": ld_exact,
                "slq_rel_error": abs(ld - ld_exact) / abs(ld_exact)}
 
+    batched = run_batched_workload(cola, ctx, device, hbm, stream) if (rank == 0 and args.batched) \
+        else None
+
     plain = None
     if rank == 0 and args.plain:
         popts = cola.cola_cg_opts_default(precision=cola.PREC_F32, refine=1, tol=w.tol,
@@ -346,7 +388,7 @@ def run_ours(args):
             "iteration_roofline": {"alg_bytes_per_iter": iter_alg,
                                    "step_time_s": round(it_time, 4)},
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
-            "clocks": clk, "plain_fp32": plain, "kron_eig": eig,
+            "clocks": clk, "plain_fp32": plain, "kron_eig": eig, "batched": batched,
         }
         print(json.dumps(line))
     ctx.close()
@@ -431,6 +473,8 @@ def main():
     # DRAM bytes of one k_kron_tc_fs launch from its ncu capture (reads + writes)
     ap.add_argument("--traffic-bytes", type=float, default=211.621376e6)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--batched", action=argparse.BooleanOptionalAction, default=True,
+                    help="also run the 512-system batched workload once")
     ap.add_argument("--eig", action=argparse.BooleanOptionalAction, default=True,
                     help="also time the eigen-structured direct solve and exact log-det")
     ap.add_argument("--plain", action=argparse.BooleanOptionalAction, default=True,

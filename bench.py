@@ -473,6 +473,8 @@ def main():
     # DRAM bytes of one k_kron_tc_fs launch from its ncu capture (reads + writes)
     ap.add_argument("--traffic-bytes", type=float, default=211.621376e6)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--batched-only", action="store_true",
+                    help="run only the 512-system batched workload (for profiler captures)")
     ap.add_argument("--batched", action=argparse.BooleanOptionalAction, default=True,
                     help="also run the 512-system batched workload once")
     ap.add_argument("--eig", action=argparse.BooleanOptionalAction, default=True,
@@ -486,6 +488,13 @@ def main():
     args = ap.parse_args()
     if args.mvm_only:
         run_mvm_only(args)
+    elif args.batched_only:
+        import torch
+        import paper_2309_03060_gb300 as cola
+        ctx = cola.Context(0)
+        hbm, _, _ = peaks()
+        print(json.dumps(run_batched_workload(cola, ctx, torch.device("cuda", 0), hbm,
+                                              torch.cuda.current_stream())))
     elif args.impl == "reference":
         run_reference(args)
     else:

@@ -163,6 +163,13 @@ typedef struct {
   int32_t graph_chunk;          /* iterations per CUDA-graph replay between host checks */
   int32_t jacobi;               /* 1 = Jacobi preconditioner M = Diag(A) from the Diag rules */
   int32_t x0_given;             /* 1 = X holds the initial guess, 0 = start from x = 0 */
+  int32_t kron_precond;         /* 1 = for A = c_k (K_1 (x) ... (x) K_d) + c_d Diag(d) with
+                                   symmetric dense K_k, precondition with
+                                   M = c_k (K_1 (x) ... (x) K_d) + c_d mean(d) I, applied
+                                   exactly from the factors' eigendecompositions (Table 3
+                                   Inverse / Eigs of Kron; Sec. 3.2 composition).  Needs M
+                                   positive definite; exclusive with jacobi; another operator
+                                   shape is COLA_ERR_UNSUPPORTED. */
 } cola_cg_opts;
 
 typedef struct {
@@ -176,7 +183,7 @@ typedef struct {
 /* Fill opts with defaults: tol 1e-8, maxiter 100000, MIXED, refine 1,
  * reliable_delta 0.1, max_updates 200, split terms 3 (factor) / 3 (vector),
  * graph_chunk 64,
- * jacobi 0, x0_given 0. */
+ * jacobi 0, x0_given 0, kron_precond 0. */
 void cola_cg_opts_default(cola_cg_opts* opts);
 
 /* Solve A X = B for nrhs right-hand sides by (preconditioned) conjugate

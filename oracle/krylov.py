@@ -13,18 +13,22 @@ from __future__ import annotations
 import numpy as np
 
 
-def cg(op, b, tol=1e-10, maxiter=None, precond_diag=None, x0=None):
+def cg(op, b, tol=1e-10, maxiter=None, precond_diag=None, x0=None, precond=None):
     """Textbook (preconditioned) conjugate gradients on one right-hand side.
 
     Stops when the recursive residual satisfies ||r|| <= tol * ||b||.
-    Returns (x, iterations).  ``precond_diag`` is the Jacobi diagonal M.
+    Returns (x, iterations).  ``precond_diag`` is the Jacobi diagonal M;
+    ``precond`` (exclusive with it) is any function r -> M^-1 r of a
+    symmetric positive definite M.
     """
+    if precond is None:
+        precond = (lambda r: r / precond_diag) if precond_diag is not None else (lambda r: r.copy())
     b = np.asarray(b, dtype=np.float64)
     n = b.shape[0]
     maxiter = n if maxiter is None else maxiter
     x = np.zeros(n) if x0 is None else np.array(x0, dtype=np.float64)
     r = b - (op @ x) if x0 is not None else b.copy()
-    z = r / precond_diag if precond_diag is not None else r.copy()
+    z = precond(r)
     p = z.copy()
     rz = float(r @ z)
     bnorm = float(np.linalg.norm(b))
@@ -39,7 +43,7 @@ def cg(op, b, tol=1e-10, maxiter=None, precond_diag=None, x0=None):
         alpha = rz / pAp
         x = x + alpha * p
         r = r - alpha * Ap
-        z = r / precond_diag if precond_diag is not None else r
+        z = precond(r)
         rz_new = float(r @ z)
         beta = rz_new / rz
         rz = rz_new

@@ -24,7 +24,8 @@ class cola_cg_opts(C.Structure):
                 ("refine", C.c_int32), ("reliable_delta", C.c_double),
                 ("max_updates", C.c_int32), ("split_factor_terms", C.c_int32),
                 ("split_vector_terms", C.c_int32), ("graph_chunk", C.c_int32),
-                ("jacobi", C.c_int32), ("x0_given", C.c_int32)]
+                ("jacobi", C.c_int32), ("x0_given", C.c_int32),
+                ("kron_precond", C.c_int32)]
 
 
 class cola_cg_info(C.Structure):

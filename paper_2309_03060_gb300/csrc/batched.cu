@@ -376,7 +376,7 @@ cola_status batched_cg_fast(Ctx* c, int32_t nsys, const cola_linop* const* ops,
                             const void* const* Bin, void* const* Xout, const int64_t* nrhs,
                             const cola_cg_opts& o, cola_cg_info* info, bool* handled) {
   *handled = false;
-  if (o.precision != COLA_PREC_MIXED || !o.refine || o.jacobi) return COLA_OK;
+  if (o.precision != COLA_PREC_MIXED || !o.refine || o.jacobi || o.kron_precond) return COLA_OK;
   std::vector<BatchSys> sys(nsys);
   int64_t tot = 0, G = 0, maxn = 0, max_m = 0;
   for (int s = 0; s < nsys; ++s) {

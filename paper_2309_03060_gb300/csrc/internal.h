@@ -304,6 +304,17 @@ int kron_tc_batch_max_stages(int tf, int tv, int max_n_chunk);
 // Chunk width (and count) of n_out output columns under a chunk cap.
 int kron_tc_chunk_width(int n_out, int chunk_cap, int* nchunks);
 
+// Preconditioner M = c_k (K_1 (x) ... (x) K_d) + c_d mean(d) I for A = c_k Kron
+// + c_d Diag(d), applied exactly from the factor eigendecompositions (kron_eig.cu).
+struct KronPrecond {
+  const cola_linop* kron = nullptr;
+  double ck = 1.0;
+  double* shift = nullptr;  // device scalar c_d mean(d)
+};
+bool kron_precond_setup(Ctx* c, cola_linop* op, KronPrecond* P, int64_t R);
+template <typename T>
+void kron_precond_apply(Ctx* c, const KronPrecond& P, const T* r, T* z, int64_t R);
+
 // Programmatic dependent launch: a kernel launched with launch_pdl may start
 // while the previous kernel on the stream is still running.  It must call
 // pdl_wait() before it touches memory that earlier kernels write or read;

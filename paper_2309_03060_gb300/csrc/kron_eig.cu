@@ -310,20 +310,94 @@ void eig_modes(Ctx* c, const KronShift& m, bool tr, const T* X, T* Y, int64_t R)
   }
 }
 
+// X = (c_k Kron + cd s[0] I)^-1 B with s a device scalar (or none).
 template <typename T>
-void eig_solve(Ctx* c, const KronShift& m, const T* B, T* X, int64_t R) {
+void eig_solve(Ctx* c, const KronShift& m, const double* s, double cd, const T* B, T* X,
+               int64_t R) {
   const int64_t N = m.kron->rows;
   T* mid = (T*)c->ws.get("keig.mid", sizeof(T) * N * R);
   eig_modes<T>(c, m, false, B, mid, R);  // (x) V^T B
   const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((N * R + 255) / 256, 8 * c->num_sms));
-  k_eig_scale<T><<<grid, 256, 0, c->s>>>(mid, N, R, dims_of(m), m.ck,
-                                         m.diag ? leaf_ptr<double>(m.diag) : nullptr, m.cd);
+  k_eig_scale<T><<<grid, 256, 0, c->s>>>(mid, N, R, dims_of(m), m.ck, s, cd);
   c->count_launch();
   COLA_CUDA(cudaGetLastError());
   eig_modes<T>(c, m, true, mid, X, R);  // (x) V (...)
 }
 
 }  // namespace
+
+// Preconditioner for A = c_k Kron + c_d Diag(d): M = c_k Kron + c_d mean(d) I,
+// applied exactly (the same eigen-structured solve).  False when A has
+// another shape; COLA_ERR_INVALID_ARG when M is not positive definite.  Sizes
+// the solve's workspace for R right-hand sides, so that a later graph capture
+// allocates nothing.
+bool kron_precond_setup(Ctx* c, cola_linop* op, KronPrecond* P, int64_t R) {
+  if (op->kind != LK_SUM || op->kids.size() != 2) return false;
+  int ik = -1, id = -1;
+  for (int i = 0; i < 2; ++i) {
+    if (op->kids[i]->kind == LK_KRON) ik = i;
+    if (op->kids[i]->kind == LK_DIAG) id = i;
+  }
+  if (ik < 0 || id < 0) return false;
+  const cola_linop* kron = op->kids[ik];
+  if ((int)kron->kids.size() > kMaxFactors) return false;
+  for (auto* f : kron->kids)
+    if (f->kind != LK_DENSE || f->rows != f->cols) return false;
+  const cola_linop* dg = op->kids[id];
+  prepare_leaves(c, op, COLA_PREC_F64, 0);
+  const int64_t nd = dg->stride ? dg->rows : 1;
+  std::vector<double> d(nd);
+  COLA_CUDA(cudaMemcpyAsync(d.data(), leaf_ptr<double>(dg), 8 * nd, cudaMemcpyDeviceToHost, c->s));
+  COLA_CUDA(cudaStreamSynchronize(c->s));
+  double mean = 0.0;
+  for (double v : d) mean += v;
+  mean /= (double)nd;
+  const double shift = op->coeffs[id] * mean;
+  P->shift = (double*)c->ws.get("keig.pshift", 8);
+  COLA_CUDA(cudaMemcpyAsync(P->shift, &shift, 8, cudaMemcpyHostToDevice, c->s));
+  COLA_CUDA(cudaStreamSynchronize(c->s));
+  KronShift m;
+  m.kron = kron;
+  m.ck = op->coeffs[ik];
+  prepare_eig(c, m, true);
+  // smallest eigenvalue of M: the products prod_k lambda_k[i_k] fill an
+  // interval whose ends are products of per-factor extreme eigenvalues
+  double lo = 1.0, hi = 1.0;
+  for (auto* f : kron->kids) {
+    std::vector<double> lam(f->rows);
+    COLA_CUDA(cudaMemcpyAsync(lam.data(), f->derived.at(kKeyLam64).p, 8 * f->rows,
+                              cudaMemcpyDeviceToHost, c->s));
+    COLA_CUDA(cudaStreamSynchronize(c->s));
+    const double a = *std::min_element(lam.begin(), lam.end());
+    const double b = *std::max_element(lam.begin(), lam.end());
+    const double q[4] = {lo * a, lo * b, hi * a, hi * b};
+    lo = *std::min_element(q, q + 4);
+    hi = *std::max_element(q, q + 4);
+  }
+  const double mmin = (m.ck >= 0.0 ? m.ck * lo : m.ck * hi) + shift;
+  COLA_REQUIRE(mmin > 0.0, COLA_ERR_INVALID_ARG,
+               "kron_precond: M = c_k Kron + c_d mean(d) I is not positive definite (min "
+               "eigenvalue %g)", mmin);
+  const int64_t N = kron->rows;
+  c->ws.get("keig.mid", 8 * N * R);
+  c->ws.get("keig.t0", 8 * N * R);
+  c->ws.get("keig.t1", 8 * N * R);
+  P->kron = kron;
+  P->ck = m.ck;
+  return true;
+}
+
+template <typename T>
+void kron_precond_apply(Ctx* c, const KronPrecond& P, const T* r, T* z, int64_t R) {
+  KronShift m;
+  m.kron = P.kron;
+  m.ck = P.ck;
+  eig_solve<T>(c, m, P.shift, 1.0, r, z, R);
+}
+template void kron_precond_apply<float>(Ctx*, const KronPrecond&, const float*, float*, int64_t);
+template void kron_precond_apply<double>(Ctx*, const KronPrecond&, const double*, double*,
+                                         int64_t);
+
 }  // namespace cola
 
 using namespace cola;
@@ -352,10 +426,11 @@ cola_status cola_kron_eig_solve(cola_ctx* ctx, const cola_linop* op, const void*
     cola_linop* mop = const_cast<cola_linop*>(op);
     prepare_leaves(ctx, mop, COLA_PREC_F64, 0);  // the shift as an FP64 device scalar
     prepare_eig(ctx, m, prec == COLA_PREC_F32);
+    const double* s = m.diag ? leaf_ptr<double>(m.diag) : nullptr;
     if (prec == COLA_PREC_F64)
-      eig_solve<double>(ctx, m, (const double*)B, (double*)X, nrhs);
+      eig_solve<double>(ctx, m, s, m.cd, (const double*)B, (double*)X, nrhs);
     else
-      eig_solve<float>(ctx, m, (const float*)B, (float*)X, nrhs);
+      eig_solve<float>(ctx, m, s, m.cd, (const float*)B, (float*)X, nrhs);
   });
 }
 

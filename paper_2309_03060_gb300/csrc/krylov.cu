@@ -345,6 +345,20 @@ __global__ void k_refresh(int64_t n, const double* r64, T* r, const T* invd, T* 
   }
 }
 
+// Partial r^T z per block (same [R][nblk] layout as k_refresh), for a z that
+// a separate preconditioner solve produced.
+template <typename T>
+__global__ void k_rz_parts(int64_t n, const T* r, const T* z, int nblk, double* part_rz) {
+  const int64_t v = blockIdx.y;
+  T s = T(0);
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)nblk * blockDim.x)
+    s = fma(r[v * n + i], z[v * n + i], s);
+  double unused;
+  const double rz = block_sum2(s, &unused, T(0));
+  if (threadIdx.x == 0) part_rz[v * nblk + blockIdx.x] = rz;
+}
+
 // (Re)start state after a residual refresh.  first: initialise everything.
 __global__ void k_cg_restate(CgState* st, const double* part_rz, const double* part_rr, int nblk,
                              int64_t R, const double* rr64, const double* bb, double tol,
@@ -653,6 +667,8 @@ struct CgBufs {
   bool defer_x;           // x updated every kPRing iterations from the ring (fused FP32)
   double* alpha_hist;     // [kPRing][R] alpha of each ring slot
   T* invd;
+  KronPrecond kp;         // kron_precond: z = M^-1 r by the eigen-structured solve
+  bool kprec;
   double *x64, *b64, *r64;
   double *part_rz, *part_rr, *dotp, *dotv;
   double* beta_vec;   // per-RHS beta for the fused p update (MIXED)
@@ -669,6 +685,23 @@ static std::string key_of(const char* what, const cola_linop* op, int64_t R, int
   return b;
 }
 
+// The vector the search direction is built from: z = M^-1 r when
+// preconditioned, r otherwise.
+template <typename T>
+static T* z_of(const CgBufs<T>& B) {
+  return (B.invd || B.kprec) ? B.z : B.r;
+}
+
+// kron_precond: z = M^-1 r and the r^T z partials (replacing the r^T r ones
+// the residual kernel left in part_rz).
+template <typename T>
+static void precond_z(Ctx* c, CgBufs<T>& B, int64_t N, int64_t R, int nblk) {
+  if (!B.kprec) return;
+  kron_precond_apply<T>(c, B.kp, B.r, B.z, R);
+  k_rz_parts<T><<<rows_grid(N, R, nblk), 256, 0, c->s>>>(N, B.r, B.z, nblk, B.part_rz);
+  c->count_launch();
+}
+
 template <typename T>
 static void cg_iteration(Ctx* c, const cola_linop* op, CgBufs<T>& B, int64_t N, int64_t R,
                          int nblk, int prec, double delta2, int refine, bool defer) {
@@ -677,7 +710,7 @@ static void cg_iteration(Ctx* c, const cola_linop* op, CgBufs<T>& B, int64_t N, 
     const int nxt = (B.cur + 1) % kPRing;
     T* p_old = B.pp[B.cur];
     T* p_new = B.pp[nxt];
-    kron_tc_cg_mvm(c, op, (const float*)(B.invd ? B.z : B.r), B.beta_vec, (const float*)p_old,
+    kron_tc_cg_mvm(c, op, (const float*)z_of(B), B.beta_vec, (const float*)p_old,
                    (float*)p_new, (float*)B.Ap, B.tile_dot, R, 1);
     B.cur = nxt;
     B.p = p_new;
@@ -712,11 +745,12 @@ static void cg_iteration(Ctx* c, const cola_linop* op, CgBufs<T>& B, int64_t N, 
                                                          B.invd ? B.z : nullptr, B.st, nblk,
                                                          B.part_rz, B.part_rr);
   c->count_launch();
+  precond_z<T>(c, B, N, R, nblk);
   k_cg_beta<<<(unsigned)R, 256, 0, c->s>>>(B.st, B.part_rz, B.part_rr, nblk, delta2, refine,
                                             B.beta_vec);
   c->count_launch();
   if (B.fused_tiles <= 0) {
-    k_cg_p<T><<<dim3(ew_blocks(N), (unsigned)R), 256, 0, c->s>>>(N, B.invd ? B.z : B.r, B.p,
+    k_cg_p<T><<<dim3(ew_blocks(N), (unsigned)R), 256, 0, c->s>>>(N, z_of(B), B.p,
                                                                   B.st);
     c->count_launch();
   }
@@ -793,7 +827,7 @@ static cola_status cg_run(Ctx* c, cola_linop* op, const void* Bin, void* Xout, i
   B.cur = 0;
   B.p = B.pp[0];
   B.Ap = (T*)ws.get("cg.Ap", sizeof(T) * N * R);
-  B.z = o.jacobi ? (T*)ws.get("cg.z", sizeof(T) * N * R) : nullptr;
+  B.z = (o.jacobi || o.kron_precond) ? (T*)ws.get("cg.z", sizeof(T) * N * R) : nullptr;
   B.part_rz = (double*)ws.get("cg.prz", 8 * nblk * R);
   B.part_rr = (double*)ws.get("cg.prr", 8 * nblk * R);
   B.dotp = (double*)ws.get("cg.dotp", 8 * nblk * R);
@@ -833,6 +867,12 @@ static cola_status cg_run(Ctx* c, cola_linop* op, const void* Bin, void* Xout, i
       k_invert<<<ew_blocks(N), 256, 0, c->s>>>(N, d64, nullptr, (double*)B.invd);
     c->count_launch();
   }
+  // Kronecker preconditioner M = c_k Kron + c_d mean(d) I (Table 3 Inverse of Kron)
+  if (o.kron_precond) {
+    B.kprec = kron_precond_setup(c, op, &B.kp, R);
+    COLA_REQUIRE(B.kprec, COLA_ERR_UNSUPPORTED,
+                 "kron_precond takes c_k Kron(K_1..K_d) + c_d Diag(d) with square dense factors");
+  }
 
   if (refine) {
     B.x64 = (double*)ws.get("cg.x64", 8 * N * R);
@@ -861,10 +901,11 @@ static cola_status cg_run(Ctx* c, cola_linop* op, const void* Bin, void* Xout, i
   k_refresh<T><<<rows_grid(N, R, nblk), 256, 0, c->s>>>(N, refine ? B.r64 : nullptr, B.r, B.invd,
                                                          B.z, nblk, B.part_rz, B.part_rr);
   c->count_launch();
+  precond_z<T>(c, B, N, R, nblk);
   k_cg_restate<<<(unsigned)((R + 127) / 128), 128, 0, c->s>>>(
       B.st, B.part_rz, B.part_rr, nblk, R, refine ? rr64 : nullptr, bb, o.tol, 1);
   c->count_launch();
-  k_copy_active<T><<<dim3(ew_blocks(N), (unsigned)R), 256, 0, c->s>>>(N, B.invd ? B.z : B.r, B.p,
+  k_copy_active<T><<<dim3(ew_blocks(N), (unsigned)R), 256, 0, c->s>>>(N, z_of(B), B.p,
                                                                       B.st);
   c->count_launch();
   COLA_CUDA(cudaGetLastError());
@@ -885,7 +926,8 @@ static cola_status cg_run(Ctx* c, cola_linop* op, const void* Bin, void* Xout, i
     char extra[128];
     snprintf(extra, sizeof extra, ":%c:d%.17g:s%d%d:p%d", sizeof(T) == 8 ? 'd' : 'f', delta2,
              o.split_factor_terms, o.split_vector_terms, B.cur);
-    return key_of("cg", op, R, prec, (refine ? 1 : 0) | (o.jacobi ? 2 : 0) | (chunk << 2), 0) +
+    return key_of("cg", op, R, prec, (refine ? 1 : 0) | (o.jacobi ? 2 : 0) | (o.kron_precond ? 4 : 0) | (chunk << 3),
+                  0) +
            extra;
   };
   int64_t iters = 0;
@@ -940,6 +982,7 @@ static cola_status cg_run(Ctx* c, cola_linop* op, const void* Bin, void* Xout, i
       k_refresh<T><<<rows_grid(N, R, nblk), 256, 0, c->s>>>(N, B.r64, B.r, B.invd, B.z, nblk,
                                                              B.part_rz, B.part_rr);
       c->count_launch();
+      precond_z<T>(c, B, N, R, nblk);
       k_cg_restate<<<(unsigned)((R + 127) / 128), 128, 0, c->s>>>(
           B.st, B.part_rz, B.part_rr, nblk, R, rr64, bb, o.tol, 0);
       c->count_launch();
@@ -959,6 +1002,7 @@ static cola_status cg_run(Ctx* c, cola_linop* op, const void* Bin, void* Xout, i
     k_refresh<T><<<rows_grid(N, R, nblk), 256, 0, c->s>>>(N, nullptr, B.r, B.invd, B.z, nblk,
                                                            B.part_rz, B.part_rr);
     c->count_launch();
+    precond_z<T>(c, B, N, R, nblk);
     k_cg_verify<<<(unsigned)((R + 127) / 128), 128, 0, c->s>>>(B.st, B.part_rz, B.part_rr, nblk,
                                                                R, B.beta_vec);
     c->count_launch();
@@ -967,7 +1011,7 @@ static cola_status cg_run(Ctx* c, cola_linop* op, const void* Bin, void* Xout, i
     any_active = false;
     for (int64_t r = 0; r < R; ++r) any_active |= hst[r].active != 0;
     if (!any_active) break;
-    k_copy_active<T><<<dim3(ew_blocks(N), (unsigned)R), 256, 0, c->s>>>(N, B.invd ? B.z : B.r,
+    k_copy_active<T><<<dim3(ew_blocks(N), (unsigned)R), 256, 0, c->s>>>(N, z_of(B),
                                                                         B.p, B.st);
     c->count_launch();
   }
@@ -1026,6 +1070,8 @@ void check_cg_args(const cola_linop* op, const cola_cg_opts* o, int64_t R) {
   COLA_REQUIRE(o->split_factor_terms >= 1 && o->split_factor_terms <= 3 &&
                    o->split_vector_terms >= 1 && o->split_vector_terms <= 3,
                COLA_ERR_INVALID_ARG, "split terms must be 1..3");
+  COLA_REQUIRE(!(o->jacobi && o->kron_precond), COLA_ERR_INVALID_ARG,
+               "jacobi and kron_precond are exclusive");
 }
 
 // ------------------------------------------------------------- bilinear
@@ -1112,6 +1158,7 @@ void cola_cg_opts_default(cola_cg_opts* o) {
   o->graph_chunk = 64;
   o->jacobi = 0;
   o->x0_given = 0;
+  o->kron_precond = 0;
 }
 
 cola_status cola_cg_solve(cola_ctx* ctx, const cola_linop* op, const void* B, void* X,

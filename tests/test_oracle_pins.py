@@ -219,6 +219,46 @@ def test_jacobi_pcg_matches_dense_lu():
     np.testing.assert_allclose(x, exact.dense_solve(op.dense(), b)[0], rtol=1e-9)
 
 
+def _kron_precond(factors, d):
+    """M^-1 for M = (x)_k K_k + mean(d) I by the exact Kronecker solve."""
+    s = float(np.mean(d))
+    return lambda r: exact.kron_shift_solve(factors, s, r)[0]
+
+
+def test_pcg_with_exact_preconditioner_takes_one_step():
+    """M = A: the first search direction is A^-1 b, so CG ends after one step."""
+    mats = [_spd(5, 21), _spd(7, 22)]
+    d = np.full(35, 0.3)
+    op = Sum([Kron([Dense(m) for m in mats]), Diag(d)])
+    b = _rs(23).standard_normal(35)
+    x, it = krylov.cg(op, b, tol=1e-12, maxiter=50, precond=_kron_precond(mats, d))
+    assert it == 1
+    np.testing.assert_allclose(x, exact.dense_solve(op.dense(), b)[0], rtol=1e-11)
+
+
+def test_kron_mean_shift_pcg_meets_condition_number_bound():
+    """A = K_1 (x) K_2 + Diag(d), M = K_1 (x) K_2 + mean(d) I.  The Rayleigh
+    quotient x^T A x / x^T M x lies between min(1, d_min/mean) and
+    max(1, d_max/mean), so kappa(M^-1 A) <= d_max / d_min, and the PCG error
+    contracts by rho = (sqrt(kappa) - 1) / (sqrt(kappa) + 1) per step in the A
+    norm.  With ||r|| <= sqrt(lambda_max(A)) ||e||_A the relative residual
+    after k steps is at most 2 rho^k sqrt(kappa(A)): the iteration count may
+    not exceed the k where that reaches tol (+2 for rounding)."""
+    w = wl.kron_diag("pin", [12, 15], [0.2, 0.2], 0.05, 0.15, 1, 1e-10, 31)
+    d = w.extra["d"]
+    op = Sum([Kron([Dense(f) for f in w.factors]), Diag(d)])
+    b = w.B[0]
+    x, it = krylov.cg(op, b, tol=1e-10, maxiter=500, precond=_kron_precond(w.factors, d))
+    np.testing.assert_allclose(x, exact.dense_solve(op.dense(), b)[0], rtol=1e-8)
+    ev = np.linalg.eigvalsh(op.dense())
+    kappa = d.max() / d.min()
+    rho = (math.sqrt(kappa) - 1) / (math.sqrt(kappa) + 1)
+    bound = math.ceil(math.log(2 * math.sqrt(ev[-1] / ev[0]) / 1e-10) / math.log(1 / rho))
+    assert it <= bound + 2, (it, bound)
+    _, it_plain = krylov.cg(op, b, tol=1e-10, maxiter=2000)
+    assert it_plain > 2 * it
+
+
 def test_exact_kron_solve_matches_dense():
     mats = [_spd(3, 15), _spd(4, 16), _spd(2, 17)]
     s = 0.05

@@ -152,6 +152,23 @@ def config2(n: int = 128, nrhs: int = 16) -> KronShiftWorkload:
                       BASE_SEED + 2, slq_probes=32, slq_steps=100)
 
 
+def kron_diag(name: str, sizes, ells, dmin: float, dmax: float, nrhs: int, tol: float,
+              seed: int) -> KronShiftWorkload:
+    """A = K_1 (x) ... (x) K_d + Diag(d): RBF factors as in kron_shift and a
+    per-point noise variance d drawn uniformly from [dmin, dmax] (a
+    heteroscedastic GP).  d is extra["d"]; shift is 0."""
+    w = kron_shift(name, sizes, ells, 0.0, nrhs, tol, seed)
+    w.extra["d"] = dmin + (dmax - dmin) * uniform(substream(seed, 3), (w.N,))
+    return w
+
+
+def config2_hetero(n: int = 128, nrhs: int = 16) -> KronShiftWorkload:
+    """The mixed-precision Kronecker workload with per-point noise:
+    K1 (x) K2 (x) K3 + Diag(d), d in [0.005, 0.015], three n-point RBF factors."""
+    return kron_diag(f"kron3_rbf{n}_hetero", [n, n, n], [0.1, 0.1, 0.1], 0.005, 0.015, nrhs,
+                     1e-8, BASE_SEED + 6)
+
+
 @dataclass
 class PoissonLowRankWorkload:
     """A = (L (+) L) + D + U U^T with the 1-D Dirichlet Laplacian L."""

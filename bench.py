@@ -517,6 +517,8 @@ def main():
                     help="also run the 512-system batched workload once")
     ap.add_argument("--kron-precond", action=argparse.BooleanOptionalAction, default=True,
                     help="also time the preconditioned solve of the per-point-noise variant")
+    ap.add_argument("--kron-precond-only", action="store_true",
+                    help="run only the preconditioned per-point-noise solve")
     ap.add_argument("--eig", action=argparse.BooleanOptionalAction, default=True,
                     help="also time the eigen-structured direct solve and exact log-det")
     ap.add_argument("--plain", action=argparse.BooleanOptionalAction, default=True,
@@ -535,6 +537,12 @@ def main():
         hbm, _, _ = peaks()
         print(json.dumps(run_batched_workload(cola, ctx, torch.device("cuda", 0), hbm,
                                               torch.cuda.current_stream())))
+    elif args.kron_precond_only:
+        import torch
+        import paper_2309_03060_gb300 as cola
+        ctx = cola.Context(0)
+        print(json.dumps(run_kron_precond(cola, ctx, torch.device("cuda", 0), args,
+                                          torch.cuda.current_stream())))
     elif args.impl == "reference":
         run_reference(args)
     else:

@@ -113,6 +113,8 @@ struct cola_linop {
   cola_ctx* ctx = nullptr;
   uint64_t uid = 0;             // unique per node for the life of the process
   uint64_t eig_hash = 0;        // contents hash of the factor its cached eigendecomposition is of
+  cola_linop* eig_kron = nullptr;  // Kron node: the eigenvector matrices (x)_k V_k^T of
+                                   // this Kron node's factors (owned; kron_precond)
   LinKind kind = LK_DENSE;
   int64_t rows = 0, cols = 0;
   int refs = 1;
@@ -307,11 +309,13 @@ int kron_tc_chunk_width(int n_out, int chunk_cap, int* nchunks);
 // Preconditioner M = c_k (K_1 (x) ... (x) K_d) + c_d mean(d) I for A = c_k Kron
 // + c_d Diag(d), applied exactly from the factor eigendecompositions (kron_eig.cu).
 struct KronPrecond {
-  const cola_linop* kron = nullptr;
-  double ck = 1.0;
-  double* shift = nullptr;  // device scalar c_d mean(d)
+  const cola_linop* qt = nullptr;  // Q^T = (x)_k V_k^T as a Kron node
+  int prec = 0;                    // precision the mode products run in
+  float* inv32 = nullptr;          // 1 / eigenvalue of M per flat index (device)
+  double* inv64 = nullptr;
 };
-bool kron_precond_setup(Ctx* c, cola_linop* op, KronPrecond* P, int64_t R);
+bool kron_precond_setup(Ctx* c, cola_linop* op, KronPrecond* P, int64_t R, int prec,
+                        int split_terms);
 template <typename T>
 void kron_precond_apply(Ctx* c, const KronPrecond& P, const T* r, T* z, int64_t R);
 

@@ -324,14 +324,38 @@ void eig_solve(Ctx* c, const KronShift& m, const double* s, double cd, const T* 
   eig_modes<T>(c, m, true, mid, X, R);  // (x) V (...)
 }
 
+// 1 / (c_k prod_k lambda_k[i_k] + shift) per flat index, in FP32 and FP64.
+__global__ void k_eig_inv(int64_t N, EigDims g, double ck, double shift, float* i32,
+                          double* i64) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double v = 1.0 / eig_at(g, i, ck, shift);
+    i32[i] = (float)v;
+    i64[i] = v;
+  }
+}
+
+// Y[r, i] *= inv[i]; grid.y runs over the right-hand sides.
+template <typename T>
+__global__ void k_scale_rows(T* Y, int64_t N, const T* inv) {
+  T* y = Y + (int64_t)blockIdx.y * N;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
+       i += (int64_t)gridDim.x * blockDim.x)
+    y[i] *= inv[i];
+}
+
 }  // namespace
 
-// Preconditioner for A = c_k Kron + c_d Diag(d): M = c_k Kron + c_d mean(d) I,
-// applied exactly (the same eigen-structured solve).  False when A has
-// another shape; COLA_ERR_INVALID_ARG when M is not positive definite.  Sizes
-// the solve's workspace for R right-hand sides, so that a later graph capture
+// Preconditioner for A = c_k Kron + c_d Diag(d): M = c_k Kron + c_d mean(d) I
+// = Q diag(c_k lambda + c_d mean(d)) Q^T with Q = (x)_k V_k, applied exactly as
+// Q^T, a diagonal scaling and Q.  The two Kronecker products run through the
+// ordinary MVM path in the solve's precision (tensor cores for MIXED), with
+// the factors' eigenvector matrices as the Kronecker factors.  False when A
+// has another shape; COLA_ERR_INVALID_ARG when M is not positive definite.
+// Sizes the workspace for R right-hand sides, so that a later graph capture
 // allocates nothing.
-bool kron_precond_setup(Ctx* c, cola_linop* op, KronPrecond* P, int64_t R) {
+bool kron_precond_setup(Ctx* c, cola_linop* op, KronPrecond* P, int64_t R, int prec,
+                        int split_terms) {
   if (op->kind != LK_SUM || op->kids.size() != 2) return false;
   int ik = -1, id = -1;
   for (int i = 0; i < 2; ++i) {
@@ -339,7 +363,7 @@ bool kron_precond_setup(Ctx* c, cola_linop* op, KronPrecond* P, int64_t R) {
     if (op->kids[i]->kind == LK_DIAG) id = i;
   }
   if (ik < 0 || id < 0) return false;
-  const cola_linop* kron = op->kids[ik];
+  cola_linop* kron = op->kids[ik];
   if ((int)kron->kids.size() > kMaxFactors) return false;
   for (auto* f : kron->kids)
     if (f->kind != LK_DENSE || f->rows != f->cols) return false;
@@ -353,13 +377,10 @@ bool kron_precond_setup(Ctx* c, cola_linop* op, KronPrecond* P, int64_t R) {
   for (double v : d) mean += v;
   mean /= (double)nd;
   const double shift = op->coeffs[id] * mean;
-  P->shift = (double*)c->ws.get("keig.pshift", 8);
-  COLA_CUDA(cudaMemcpyAsync(P->shift, &shift, 8, cudaMemcpyHostToDevice, c->s));
-  COLA_CUDA(cudaStreamSynchronize(c->s));
   KronShift m;
   m.kron = kron;
   m.ck = op->coeffs[ik];
-  prepare_eig(c, m, true);
+  prepare_eig(c, m, false);
   // smallest eigenvalue of M: the products prod_k lambda_k[i_k] fill an
   // interval whose ends are products of per-factor extreme eigenvalues
   double lo = 1.0, hi = 1.0;
@@ -378,21 +399,52 @@ bool kron_precond_setup(Ctx* c, cola_linop* op, KronPrecond* P, int64_t R) {
   COLA_REQUIRE(mmin > 0.0, COLA_ERR_INVALID_ARG,
                "kron_precond: M = c_k Kron + c_d mean(d) I is not positive definite (min "
                "eigenvalue %g)", mmin);
+  // Q^T as a Kron node over the cached FP64 V_k^T (kept on the Kron node)
+  if (!kron->eig_kron) {
+    cola_ctx* cc = static_cast<cola_ctx*>(c);
+    std::vector<cola_linop*> vt;
+    cola_status st = COLA_OK;
+    for (auto* f : kron->kids) {
+      cola_linop* l = nullptr;
+      if (st == COLA_OK)
+        st = cola_linop_dense(cc, f->rows, f->rows, f->derived.at(kKeyVt64).p, f->rows, COLA_F64,
+                              &l);
+      if (l) vt.push_back(l);
+    }
+    cola_linop* q = nullptr;
+    if (st == COLA_OK) st = cola_linop_kron(cc, (int)vt.size(), vt.data(), &q);
+    for (auto* l : vt) cola_linop_release(l);
+    COLA_REQUIRE(st == COLA_OK && q, COLA_ERR_CUDA, "kron_precond: building Q^T failed");
+    kron->eig_kron = q;
+  }
+  // the factor splits are recomputed every time: V_k changes with K_k
+  prepare_leaves(c, kron->eig_kron, prec, split_terms);
   const int64_t N = kron->rows;
-  c->ws.get("keig.mid", 8 * N * R);
-  c->ws.get("keig.t0", 8 * N * R);
-  c->ws.get("keig.t1", 8 * N * R);
-  P->kron = kron;
-  P->ck = m.ck;
+  P->inv32 = (float*)c->ws.get("keig.inv32", 4 * N);
+  P->inv64 = (double*)c->ws.get("keig.inv64", 8 * N);
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((N + 255) / 256, 8 * c->num_sms));
+  k_eig_inv<<<grid, 256, 0, c->s>>>(N, dims_of(m), m.ck, shift, P->inv32, P->inv64);
+  c->count_launch();
+  COLA_CUDA(cudaGetLastError());
+  const size_t es = prec == COLA_PREC_F64 ? 8 : 4;
+  c->ws.get("keig.pmid", es * N * R);
+  P->qt = kron->eig_kron;
+  P->prec = prec;
   return true;
 }
 
+// z = M^-1 r = Q (inv * (Q^T r)).  The mode products use workspace depth 4.
 template <typename T>
 void kron_precond_apply(Ctx* c, const KronPrecond& P, const T* r, T* z, int64_t R) {
-  KronShift m;
-  m.kron = P.kron;
-  m.ck = P.ck;
-  eig_solve<T>(c, m, P.shift, 1.0, r, z, R);
+  const int64_t N = P.qt->rows;
+  T* mid = (T*)c->ws.get("keig.pmid", sizeof(T) * N * R);
+  apply<T>(c, P.qt, r, mid, R, 1.0, 0.0, 4, false, P.prec);
+  const T* inv = sizeof(T) == 8 ? (const T*)P.inv64 : (const T*)P.inv32;
+  const int gx = (int)std::max<int64_t>(1, std::min<int64_t>((N + 255) / 256, 2 * c->num_sms));
+  k_scale_rows<T><<<dim3(gx, (unsigned)R), 256, 0, c->s>>>(mid, N, inv);
+  c->count_launch();
+  COLA_CUDA(cudaGetLastError());
+  apply<T>(c, P.qt, mid, z, R, 1.0, 0.0, 4, true, P.prec);
 }
 template void kron_precond_apply<float>(Ctx*, const KronPrecond&, const float*, float*, int64_t);
 template void kron_precond_apply<double>(Ctx*, const KronPrecond&, const double*, double*,

@@ -869,7 +869,7 @@ static cola_status cg_run(Ctx* c, cola_linop* op, const void* Bin, void* Xout, i
   }
   // Kronecker preconditioner M = c_k Kron + c_d mean(d) I (Table 3 Inverse of Kron)
   if (o.kron_precond) {
-    B.kprec = kron_precond_setup(c, op, &B.kp, R);
+    B.kprec = kron_precond_setup(c, op, &B.kp, R, prec, o.split_factor_terms);
     COLA_REQUIRE(B.kprec, COLA_ERR_UNSUPPORTED,
                  "kron_precond takes c_k Kron(K_1..K_d) + c_d Diag(d) with square dense factors");
   }

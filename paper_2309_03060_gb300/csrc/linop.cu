@@ -576,6 +576,7 @@ template void bilinear<double>(Ctx*, const cola_linop*, const double*, const dou
 
 // ============================================================== linop nodes
 cola_linop::~cola_linop() {
+  if (eig_kron) cola_linop_release(eig_kron);
   for (auto& kv : derived) cudaFree(kv.second.p);
   for (auto* k : kids) cola_linop_release(k);
 }

@@ -74,20 +74,29 @@ def test_kron_precond_f64_small_vs_dense(cola, ctx):
 
 
 def test_kron_precond_coefficients_f32(cola, ctx):
-    """Sum coefficients 2 (Kron) and 0.5 (Diag), FP32 vectors without
-    refinement (the unfused FP32 recurrence), against dense LU."""
-    w = wl.kron_diag("kd_coeff", [16, 20, 8], [0.3, 0.3, 0.3], 0.1, 0.3, 3, 1e-5, 42)
+    """Sum coefficients 2 (Kron) and 0.5 (Diag) on the FP32 SIMT path (the
+    unfused FP32 recurrence).  With FP64 refinement the true residual reaches
+    1e-8; without it the solver's own FP32 check of b - A x holds it to 10 tol
+    (kappa(A) ~ 1e4 puts the FP32 residual floor near 1e-5)."""
+    w = wl.kron_diag("kd_coeff", [16, 20, 8], [0.3, 0.3, 0.3], 0.1, 0.3, 3, 1e-8, 42)
     spec = _spec(w, [2.0, 0.5])
+    ref = oracle_tree(spec)
     op = gpu_tree(cola, ctx, spec, torch.float64, DEV).set_spd()
-    opts = cola.cola_cg_opts_default(precision=cola.PREC_F32, refine=0, tol=1e-5, maxiter=300,
+    opts = cola.cola_cg_opts_default(precision=cola.PREC_F32, refine=1, tol=1e-8, maxiter=600,
                                      graph_chunk=4, kron_precond=1)
-    X, info, st = cola.cola_cg_solve(ctx, op, torch.tensor(w.B, dtype=torch.float32, device=DEV),
-                                     opts)
+    X, info, st = cola.cola_cg_solve(ctx, op, torch.tensor(w.B, device=DEV), opts)
     assert st == 0, info
-    res = krylov.true_relative_residual(oracle_tree(spec), w.B, X.double().cpu().numpy())
-    assert np.all(res <= 1e-5), res
-    it_o = max(_oracle_pcg_iters(spec, w, w.B[r], 1e-5, 2.0, 0.5) for r in range(3))
-    assert max(i["iterations"] for i in info) <= it_o + 4 + 4
+    res = krylov.true_relative_residual(ref, w.B, X.cpu().numpy())
+    assert np.all(res <= 1e-8), res
+    it_o = max(_oracle_pcg_iters(spec, w, w.B[r], 1e-8, 2.0, 0.5) for r in range(3))
+    assert max(i["iterations"] for i in info) <= 1.5 * it_o + 8, (info, it_o)
+    opts32 = cola.cola_cg_opts_default(precision=cola.PREC_F32, refine=0, tol=1e-5, maxiter=300,
+                                       graph_chunk=4, kron_precond=1)
+    X32, info32, st32 = cola.cola_cg_solve(
+        ctx, op, torch.tensor(w.B, dtype=torch.float32, device=DEV), opts32)
+    assert st32 == 0, info32
+    res32 = krylov.true_relative_residual(ref, w.B, X32.double().cpu().numpy())
+    assert np.all(res32 <= 1e-4), res32
 
 
 def test_kron_precond_mixed_full_size(cola, ctx):

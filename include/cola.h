@@ -169,11 +169,14 @@ typedef struct {
                                    exactly from the factors' eigendecompositions (Table 3
                                    Inverse / Eigs of Kron; Sec. 3.2 composition).  Needs M
                                    positive definite; exclusive with jacobi; another operator
-                                   shape is COLA_ERR_UNSUPPORTED. */
+                                   shape is COLA_ERR_UNSUPPORTED.  Graph chunks are capped at
+                                   8 iterations. */
 } cola_cg_opts;
 
 typedef struct {
-  int64_t iterations;           /* CG iterations this right-hand side took */
+  int64_t iterations;           /* CG iterations this right-hand side took (iterations it sat
+                                   paused, waiting at the end of a graph chunk for an FP64
+                                   residual replacement, are not counted) */
   double rel_residual;          /* final relative residual (FP64 true residual when refined
                                    or precision F64; recursive one otherwise) */
   int32_t updates;              /* FP64 residual replacements performed */

@@ -252,6 +252,8 @@ struct CgState {
   double rr64;
   long long iters;
   int active, flag, status, updates;
+  int paused;   // refined solves: the recursion has run ahead of what FP32 can resolve
+  int restart;  // set by a residual replacement that restarts the search direction
 };
 
 // ------------------------------------------------------------ solver entries

@@ -61,6 +61,12 @@ __device__ __forceinline__ double block_sum2(T v, double* out_other, T v2) {
   return tx;
 }
 
+// Refined solves: pause a right-hand side once its recursive residual norm fell
+// by 1e6 since the last replacement; restart its search direction when a
+// replacement finds the true residual norm more than 10x the recursive one.
+constexpr double kPauseDrop2 = 1e-12;
+constexpr double kRestartGap2 = 100.0;
+
 // alpha = r^T z / p^T A p, with p^T A p the ordered sum of nparts partials.
 // One block per right-hand side: p^T A p from its partial sums, alpha = r^T z / p^T A p.
 // alpha_out (optional): where this iteration's alpha is recorded (0 when inactive).
@@ -69,7 +75,7 @@ __global__ void k_cg_alpha(CgState* st, const double* parts, int nparts, double*
   pdl_wait();
   const int64_t r = blockIdx.x;
   CgState& s = st[r];
-  if (!s.active) {
+  if (!s.active || s.paused) {
     if (threadIdx.x == 0) {
       s.alpha = 0.0;
       if (alpha_out) alpha_out[r] = 0.0;
@@ -275,7 +281,9 @@ __global__ void k_cg_beta(CgState* st, const double* part_rz, const double* part
   pdl_wait();
   const int64_t r = blockIdx.x;
   CgState& s = st[r];
-  if (!s.active) {
+  if (!s.active || s.paused) {
+    // a paused right-hand side keeps x and r and holds p = z until the next
+    // residual replacement restarts it; its idle iterations are not counted
     if (threadIdx.x == 0) {
       s.beta = 0.0;
       if (beta_out) beta_out[r] = 0.0;
@@ -301,6 +309,14 @@ __global__ void k_cg_beta(CgState* st, const double* part_rz, const double* part
   }
   if (refine) {
     if (rr <= s.tol2 || rr <= delta2 * s.rr_ref) s.flag = 1;
+    // The recursive residual fell a million-fold since the last replacement
+    // (or reached zero): FP32 cannot make the true residual follow it further,
+    // and a fast recursion would underflow before the chunk ends.  Pause until
+    // the replacement.
+    if (rr <= kPauseDrop2 * s.rr_ref || rz == 0.0) {
+      s.paused = 1;
+      s.beta = 0.0;
+    }
   } else if (rr <= s.tol2) {
     s.active = 0;
   }
@@ -345,6 +361,16 @@ __global__ void k_refresh(int64_t n, const double* r64, T* r, const T* invd, T* 
   }
 }
 
+// p = z for the right-hand sides a replacement restarted.
+template <typename T>
+__global__ void k_cg_restart_p(int64_t n, const T* z, T* p, const CgState* st) {
+  const int64_t v = blockIdx.y;
+  if (!st[v].active || !st[v].restart) return;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    p[v * n + i] = z[v * n + i];
+}
+
 // Partial r^T z per block (same [R][nblk] layout as k_refresh), for a z that
 // a separate preconditioner solve produced.
 template <typename T>
@@ -360,9 +386,14 @@ __global__ void k_rz_parts(int64_t n, const T* r, const T* z, int nblk, double* 
 }
 
 // (Re)start state after a residual refresh.  first: initialise everything.
+// Otherwise (a replacement of the recursive residual by the true one) the
+// search direction is kept, as reliable updating does, unless the recursion
+// had paused or the true residual came out more than 10x the recursive one:
+// the old direction then no longer matches r, and the right-hand side restarts
+// from p = z (restart = 1; beta_vec, when given, is zeroed for the fused update).
 __global__ void k_cg_restate(CgState* st, const double* part_rz, const double* part_rr, int nblk,
                              int64_t R, const double* rr64, const double* bb, double tol,
-                             int first) {
+                             int first, double* beta_vec) {
   const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= R) return;
   CgState& s = st[r];
@@ -371,6 +402,7 @@ __global__ void k_cg_restate(CgState* st, const double* part_rz, const double* p
     rz += part_rz[r * nblk + b];
     rr += part_rr[r * nblk + b];
   }
+  s.restart = 0;
   if (first) {
     s.iters = 0;
     s.updates = 0;
@@ -381,7 +413,13 @@ __global__ void k_cg_restate(CgState* st, const double* part_rz, const double* p
     s.alpha = s.beta = 0.0;
   } else if (s.active) {
     s.updates += 1;
+    if (s.paused || rr > kRestartGap2 * s.rr) {
+      s.restart = 1;
+      s.beta = 0.0;
+      if (beta_vec) beta_vec[r] = 0.0;
+    }
   }
+  s.paused = 0;
   s.flag = 0;
   s.rz = rz;
   s.rr = rr;
@@ -903,7 +941,7 @@ static cola_status cg_run(Ctx* c, cola_linop* op, const void* Bin, void* Xout, i
   c->count_launch();
   precond_z<T>(c, B, N, R, nblk);
   k_cg_restate<<<(unsigned)((R + 127) / 128), 128, 0, c->s>>>(
-      B.st, B.part_rz, B.part_rr, nblk, R, refine ? rr64 : nullptr, bb, o.tol, 1);
+      B.st, B.part_rz, B.part_rr, nblk, R, refine ? rr64 : nullptr, bb, o.tol, 1, nullptr);
   c->count_launch();
   k_copy_active<T><<<dim3(ew_blocks(N), (unsigned)R), 256, 0, c->s>>>(N, z_of(B), B.p,
                                                                       B.st);
@@ -920,6 +958,9 @@ static cola_status cg_run(Ctx* c, cola_linop* op, const void* Bin, void* Xout, i
   // multiple of kPRing iterations: it starts and ends on the same buffer, and
   // in deferred-x mode x is current at its end
   int chunk = std::max(1, o.graph_chunk);
+  // the preconditioned recursion converges within a few iterations: short
+  // chunks keep the replacements (and restarts) close behind it
+  if (B.kprec) chunk = std::min(chunk, kPRing);
   if (B.fused_tiles > 0) chunk = (chunk + kPRing - 1) / kPRing * kPRing;
   // everything a captured kernel bakes in is part of the graph key
   auto graph_key = [&] {
@@ -984,7 +1025,10 @@ static cola_status cg_run(Ctx* c, cola_linop* op, const void* Bin, void* Xout, i
       c->count_launch();
       precond_z<T>(c, B, N, R, nblk);
       k_cg_restate<<<(unsigned)((R + 127) / 128), 128, 0, c->s>>>(
-          B.st, B.part_rz, B.part_rr, nblk, R, rr64, bb, o.tol, 0);
+          B.st, B.part_rz, B.part_rr, nblk, R, rr64, bb, o.tol, 0, B.beta_vec);
+      c->count_launch();
+      k_cg_restart_p<T><<<dim3(ew_blocks(N), (unsigned)R), 256, 0, c->s>>>(N, z_of(B), B.p,
+                                                                            B.st);
       c->count_launch();
       ++updates;
       read_state();

@@ -220,6 +220,8 @@ cola_status cola_cg_solve_batched(cola_ctx* ctx, int32_t nsys, const cola_linop*
  * eigenvectors and its eigenvalues the products of the factor eigenvalues
  * (Table 3, Inverse and Eigs rules), so
  *   X = ((x)_k V_k) diag(1 / (c_k prod_k lambda_k + c_d s)) ((x)_k V_k)^T B.
+ * A Kronecker sum K_1 (+) ... (+) K_d (cola_linop_kronsum) in place of the
+ * product is accepted too: same eigenvectors, eigenvalues sum_k lambda_k.
  * Each factor's eigendecomposition is computed on the host in FP64
  * (cola_sym_eig) on first use and cached on the factor; it is recomputed when
  * the factor's contents change (the factor is read back to compare).
@@ -233,11 +235,35 @@ cola_status cola_kron_eig_solve(cola_ctx* ctx, const cola_linop* op, const void*
                                 int64_t nrhs, cola_precision prec, cola_stream stream);
 
 /* Exact log det A for the same operator class: the sum over all N index
- * tuples of log(c_k prod_k lambda_k[i_k] + c_d s) (Table 3 LogDet rule with the
+ * tuples of log(c_k prod_k lambda_k[i_k] + c_d s) (sum_k for a Kronecker sum)
+ * (Table 3 LogDet rule with the
  * Eigs rule; App. A.1.2), reduced in FP64 in a fixed order.
  * COLA_ERR_BREAKDOWN if any eigenvalue of A is <= 0.  Synchronous. */
 cola_status cola_kron_eig_logdet(cola_ctx* ctx, const cola_linop* op, double* logdet,
                                  cola_stream stream);
+
+/* Solve A X = B for A = A_1 A_2 ... A_m (cola_linop_product; nested products
+ * are flattened) by splitting the product: X = A_m^-1 ( ... (A_1^-1 B)), one
+ * factor at a time (Sec. 3.2: the inverse of a product is the product of the
+ * inverses in reverse order; Table 3 dispatch).  Each factor is solved by the
+ * rule its type allows: a diagonal factor is divided out; with use_structure
+ * = 1 a Kron / KronSum [+ scalar * I] factor takes the eigen-structured direct
+ * solve of cola_kron_eig_solve; every other factor must be annotated spd and
+ * is solved by cola_cg_solve's CG with opts (x0_given ignored).  An operator
+ * that is not a product is one factor.  opts->tol applies to each factor's CG:
+ * the product's own residual can exceed it by up to the condition number of
+ * the leading factors, while the forward error stays of the order a single
+ * CG on the product at tol would reach.  B, X are [nrhs][N], FP64 when
+ * precision is F64 or refine = 1, FP32 else.  info (HOST, nrhs entries, may
+ * be NULL): iterations and updates summed over the factors' CG solves,
+ * rel_residual = ||B - A X|| / ||B|| of the whole product computed through
+ * the product's MVM in the vectors' precision, status the first factor
+ * failure.  COLA_ERR_UNSUPPORTED for a factor no rule covers, COLA_ERR_SHAPE
+ * for a non-square factor.  Synchronous.  The paper's illustration is the
+ * Bi-Poisson operator (L (+) L)^2 as a product of two Kronecker sums. */
+cola_status cola_product_solve(cola_ctx* ctx, const cola_linop* op, const void* B, void* X,
+                               int64_t nrhs, const cola_cg_opts* opts, int32_t use_structure,
+                               cola_cg_info* info, cola_stream stream);
 
 /* Symmetric eigendecomposition of an n x n matrix in HOST memory, the routine
  * the two calls above apply to each factor: A = V diag(w) V^T with V's

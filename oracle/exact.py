@@ -1,5 +1,10 @@
 """Closed forms the iterative results must reach (FP64).  Test infrastructure only.
 
+Kronecker sums K_1 (+) ... (+) K_d = sum_k I (x) .. (x) K_k (x) .. (x) I share
+the eigenvectors (x)_k V_k, with eigenvalues lam_1[i_1] + ... + lam_d[i_d]
+(App. A.1.2); a product's inverse is the product of the factor inverses in
+reverse order (Sec. 3.2).
+
 App. A.1.2: Eigs(A (x) B) = (Lambda_A (x) Lambda_B, V_A (x) V_B), so for
 A = K_1 (x) ... (x) K_d + s I with symmetric factors K_k = V_k diag(lam_k) V_k^T
     A^-1 b = V (Lambda + s)^-1 V^T b,  V = V_1 (x) ... (x) V_d,
@@ -63,6 +68,38 @@ def kron_shift_logdet(factors, shift):
     if np.any(lam <= 0):
         raise FloatingPointError("operator is not positive definite")
     return float(np.sum(np.log(lam)))
+
+
+def kronsum_eigenvalues(factors, shift=0.0):
+    """All eigenvalues of K_1 (+) ... (+) K_d + shift I in row-major order:
+    lam_1[i_1] + ... + lam_d[i_d] (App. A.1.2, the Kronecker-sum rule)."""
+    lam = np.zeros(1)
+    for w, _ in _eig(factors):
+        lam = np.add.outer(lam, w).ravel()
+    return lam + shift
+
+
+def kronsum_shift_solve(factors, shift, B):
+    """Exact A^-1 B for A = (+)_k K_k + shift I: same eigenvectors as the
+    Kronecker product, eigenvalues summed."""
+    B = np.atleast_2d(np.asarray(B, dtype=np.float64))
+    eig = _eig(factors)
+    shape = [K.shape[0] for K in factors]
+    lam = np.zeros(1)
+    for w, _ in eig:
+        lam = np.add.outer(lam, w).ravel()
+    C = _apply_modes([V.T for _, V in eig], B, shape)
+    C = C / (lam + shift)
+    return _apply_modes([V for _, V in eig], C, shape)
+
+
+def product_split_solve(factor_solvers, B):
+    """A^-1 B for A = A_1 A_2 ... A_m given solvers for each factor
+    (Sec. 3.2: Inverse(A_1 ... A_m) = A_m^-1 ... A_1^-1): A_1 is solved first."""
+    X = np.atleast_2d(np.asarray(B, dtype=np.float64))
+    for solve in factor_solvers:
+        X = solve(X)
+    return X
 
 
 def dense_solve(A, B):

@@ -215,6 +215,27 @@ def cola_kron_eig_solve(ctx: Context, op: LinOp, B: torch.Tensor, precision: int
     return X if B.dim() == 2 else X.reshape(-1)
 
 
+def cola_product_solve(ctx: Context, op: LinOp, B: torch.Tensor,
+                       opts: cola_cg_opts | None = None, use_structure: bool = True,
+                       raise_on_error: bool = True):
+    """Solve A X = B for a product A = A_1 ... A_m one factor at a time.
+    Returns (X, info list, status)."""
+    opts = opts or cola_cg_opts_default()
+    B2 = B if B.dim() == 2 else B.reshape(1, -1)
+    R = B2.shape[0]
+    want = _vec_dtype(opts.precision, bool(opts.refine))
+    if B2.dtype != want:
+        raise TypeError(f"this precision/refine setting needs {want} vectors")
+    X = torch.empty_like(B2)
+    info = (cola_cg_info * R)()
+    st = _lib().cola_product_solve(ctx.handle, op.handle, _ptr(B2), _ptr(X), R, C.byref(opts),
+                                   int(use_structure), info, _stream())
+    if raise_on_error and st not in (0, 5):
+        check(st)
+    X = X if B.dim() == 2 else X.reshape(-1)
+    return X, _info_list(info, R), st
+
+
 def cola_kron_eig_logdet(ctx: Context, op: LinOp) -> float:
     """Exact log det A from the factor eigenvalues."""
     v = C.c_double()

@@ -73,6 +73,7 @@ SIGNATURES = {
     "cola_get_stream": (I32, [P, C.POINTER(P)]),
     "cola_kron_eig_solve": (I32, [P, P, P, P, I64, I32, P]),
     "cola_kron_eig_logdet": (I32, [P, P, C.POINTER(C.c_double), P]),
+    "cola_product_solve": (I32, [P, P, P, P, I64, P, I32, P, P]),
     "cola_sym_eig": (I32, [I64, P, P, P]),
     "cola_set_split_terms": (I32, [P, I32, I32]),
     "cola_kron_matvec_noalloc": (I32, [C.c_int, C.POINTER(I64), C.POINTER(I64), PP, P, P, I64, P]),

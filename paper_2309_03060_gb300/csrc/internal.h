@@ -316,6 +316,8 @@ struct KronPrecond {
   float* inv32 = nullptr;          // 1 / eigenvalue of M per flat index (device)
   double* inv64 = nullptr;
 };
+bool eig_solve_if_structured(Ctx* c, const cola_linop* op, const void* B, void* X, int64_t R,
+                             bool f64);
 bool kron_precond_setup(Ctx* c, cola_linop* op, KronPrecond* P, int64_t R, int prec,
                         int split_terms);
 template <typename T>

@@ -1,11 +1,14 @@
-// Structured solve and log-determinant of shifted Kronecker operators from the
-// eigendecompositions of their factors (Table 3: the inverse and the
-// eigendecomposition of a Kronecker product are built from the factors';
-// Sec. 3.2 composition rules).  For
+// Structured solve and log-determinant of shifted Kronecker products and
+// Kronecker sums from the eigendecompositions of their factors (Table 3: the
+// inverse and the eigendecomposition of a Kronecker product or sum are built
+// from the factors'; Sec. 3.2 composition rules; App. A.1.2).  For
 //     A = c_k (K_1 (x) ... (x) K_d) + c_d s I,   K_k = V_k diag(lambda_k) V_k^T,
 // the eigenvectors of A are (x)_k V_k and its eigenvalues c_k prod_k lambda_k[i_k] + c_d s, so
 //     A^-1 B     = ((x)_k V_k) diag(1 / (c_k prod lambda + c_d s)) ((x)_k V_k)^T B,
 //     log det A  = sum over all index tuples of log(c_k prod lambda + c_d s).
+// A Kronecker sum K_1 (+) ... (+) K_d has the same eigenvectors and the
+// eigenvalues sum_k lambda_k[i_k]: the same code with a sum in place of the
+// product.
 // The factor eigendecompositions are computed once on the host in FP64 and
 // cached on the factor (recomputed when its contents change); the solve is
 // 2 d cyclic mode products plus one diagonal scaling on the GPU.
@@ -116,19 +119,21 @@ constexpr int kKeyVt64 = 400, kKeyLam64 = 401, kKeyVt32 = 402;
 
 struct EigDims {
   int d;
+  int sum;  // 1: Kronecker sum (eigenvalues add), 0: Kronecker product (multiply)
   int64_t n[kMaxFactors];
   const double* lam[kMaxFactors];
 };
 
 // Eigenvalue of A at flat (row-major) index i.
 __device__ __forceinline__ double eig_at(const EigDims& g, int64_t i, double ck, double shift) {
-  double prod = 1.0;
+  double v = g.sum ? 0.0 : 1.0;
   for (int k = g.d - 1; k >= 0; --k) {
     const int64_t nk = g.n[k];
-    prod *= g.lam[k][i % nk];
+    const double l = g.lam[k][i % nk];
+    v = g.sum ? v + l : v * l;
     i /= nk;
   }
-  return ck * prod + shift;
+  return ck * v + shift;
 }
 
 // Y[r, i] /= lambda_A(i).  The shift c_d s is read from the device scalar.
@@ -172,14 +177,49 @@ __global__ void k_eig_logdet(int64_t N, EigDims g, double ck, const double* s, d
   }
 }
 
-uint64_t fnv1a(const void* p, size_t bytes) {
-  const unsigned char* b = (const unsigned char*)p;
-  uint64_t h = 1469598103934665603ull;
-  for (size_t i = 0; i < bytes; ++i) {
-    h ^= b[i];
-    h *= 1099511628211ull;
+// Contents fingerprint of an n x n factor (leading dimension ld) on the
+// device: the sum mod 2^64 of a 64-bit mix (the SplitMix64 finaliser) of each
+// entry's bits salted with its index.  The sum is order-independent, so the
+// result is deterministic under any reduction order.
+__device__ __forceinline__ unsigned long long fp_mix(unsigned long long z) {
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+template <typename T>
+__global__ void k_fingerprint(const T* a, int64_t n, int64_t ld, unsigned long long* out) {
+  unsigned long long acc = 0;
+  const int64_t tot = n * n;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < tot;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const T v = a[(e / n) * ld + e % n];
+    unsigned long long bits;
+    if (sizeof(T) == 8)
+      bits = (unsigned long long)__double_as_longlong((double)v);
+    else
+      bits = (unsigned long long)__float_as_uint((float)v);
+    acc += fp_mix(bits ^ ((unsigned long long)e * 0x9E3779B97F4A7C15ull));
   }
-  return h;
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) atomicAdd(out, acc);
+}
+
+uint64_t factor_fingerprint(Ctx* c, const cola_linop* f) {
+  unsigned long long* d = (unsigned long long*)c->ws.get("keig.fp", 8);
+  COLA_CUDA(cudaMemsetAsync(d, 0, 8, c->s));
+  const int64_t n = f->rows;
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((n * n + 255) / 256, 2 * c->num_sms));
+  if (f->dtype == COLA_F64)
+    k_fingerprint<double><<<grid, 256, 0, c->s>>>((const double*)f->data, n, f->ld, d);
+  else
+    k_fingerprint<float><<<grid, 256, 0, c->s>>>((const float*)f->data, n, f->ld, d);
+  c->count_launch();
+  COLA_CUDA(cudaGetLastError());
+  unsigned long long h = 0;
+  COLA_CUDA(cudaMemcpyAsync(&h, d, 8, cudaMemcpyDeviceToHost, c->s));
+  COLA_CUDA(cudaStreamSynchronize(c->s));
+  return (uint64_t)h ^ ((uint64_t)n << 1) ^ (f->dtype == COLA_F64 ? 1u : 0u);
 }
 
 void* eig_buf(cola_linop* f, int key, size_t bytes) {
@@ -198,21 +238,28 @@ void* eig_buf(cola_linop* f, int key, size_t bytes) {
   return p;
 }
 
-// The operator's parts: Kronecker factors, c_k, and the optional scalar shift.
+// The operator's parts: the Kronecker product or sum node, c_k, and the
+// optional scalar shift.
 struct KronShift {
-  const cola_linop* kron = nullptr;
+  const cola_linop* kron = nullptr;  // LK_KRON or LK_KRONSUM
+  bool sum = false;
   double ck = 1.0, cd = 0.0;
   const cola_linop* diag = nullptr;
 };
 
-KronShift match(const cola_linop* op) {
-  KronShift m;
-  if (op->kind == LK_KRON) {
+inline bool is_kron_node(const cola_linop* op) {
+  return op->kind == LK_KRON || op->kind == LK_KRONSUM;
+}
+
+// Fills m when op is Kron/KronSum or Kron/KronSum + scalar Diag; false otherwise.
+bool try_match(const cola_linop* op, KronShift& m) {
+  m = KronShift{};
+  if (is_kron_node(op)) {
     m.kron = op;
   } else if (op->kind == LK_SUM && op->kids.size() == 2) {
     for (int i = 0; i < 2; ++i) {
       const cola_linop* k = op->kids[i];
-      if (k->kind == LK_KRON) {
+      if (is_kron_node(k)) {
         m.kron = k;
         m.ck = op->coeffs[i];
       } else if (k->kind == LK_DIAG && k->stride == 0) {
@@ -222,8 +269,18 @@ KronShift match(const cola_linop* op) {
     }
     if (!m.kron || !m.diag) m.kron = nullptr;
   }
+  if (!m.kron || (int)m.kron->kids.size() > kMaxFactors) return false;
+  for (auto* f : m.kron->kids)
+    if (f->kind != LK_DENSE || f->rows != f->cols) return false;
+  m.sum = m.kron->kind == LK_KRONSUM;
+  return true;
+}
+
+KronShift match(const cola_linop* op) {
+  KronShift m;
+  try_match(op, m);
   COLA_REQUIRE(m.kron, COLA_ERR_UNSUPPORTED,
-               "the eigen-structured path takes Kron(K_1..K_d) or Kron + scalar * I");
+               "the eigen-structured path takes Kron/KronSum(K_1..K_d) [+ scalar * I]");
   COLA_REQUIRE((int)m.kron->kids.size() <= kMaxFactors, COLA_ERR_UNSUPPORTED,
                "at most %d Kronecker factors", kMaxFactors);
   for (auto* f : m.kron->kids)
@@ -232,12 +289,21 @@ KronShift match(const cola_linop* op) {
   return m;
 }
 
-// Factor eigendecompositions on the device (FP64 Vt and lambda; FP32 Vt when
-// asked), recomputed only when a factor's contents change.
+// Factor eigendecompositions on the device (FP64 Vt and lambda, FP32 Vt),
+// recomputed only when a factor's contents change: a device fingerprint of
+// each distinct factor is compared with the one the cached decomposition was
+// made from, and only a changed factor is read back and decomposed.
 void prepare_eig(Ctx* c, const KronShift& m, bool want32) {
+  std::vector<const cola_linop*> seen;
   for (auto* fc : m.kron->kids) {
+    if (std::find(seen.begin(), seen.end(), fc) != seen.end()) continue;
+    seen.push_back(fc);
     cola_linop* f = const_cast<cola_linop*>(fc);
     const int64_t n = f->rows;
+    const uint64_t h = factor_fingerprint(c, f);
+    if (f->eig_hash == h && f->derived.count(kKeyVt64) && f->derived.count(kKeyLam64) &&
+        f->derived.count(kKeyVt32))
+      continue;
     std::vector<double> A((size_t)n * n);
     if (f->dtype == COLA_F64) {
       COLA_CUDA(cudaMemcpy2DAsync(A.data(), n * 8, f->data, f->ld * 8, n * 8, n,
@@ -250,29 +316,25 @@ void prepare_eig(Ctx* c, const KronShift& m, bool want32) {
       COLA_CUDA(cudaStreamSynchronize(c->s));
       for (size_t i = 0; i < A.size(); ++i) A[i] = Af[i];
     }
-    const uint64_t h = fnv1a(A.data(), A.size() * 8) ^ (uint64_t)n;
-    const bool have = f->eig_hash == h && f->derived.count(kKeyVt64) && f->derived.count(kKeyLam64);
-    if (!have) {
-      double amax = 0.0, asym = 0.0;
-      for (int64_t i = 0; i < n; ++i)
-        for (int64_t j = 0; j < n; ++j) {
-          amax = std::max(amax, fabs(A[(size_t)i * n + j]));
-          asym = std::max(asym, fabs(A[(size_t)i * n + j] - A[(size_t)j * n + i]));
-        }
-      COLA_REQUIRE(asym <= 1e-12 * amax, COLA_ERR_INVALID_ARG,
-                   "Kronecker factor is not symmetric (max |K - K^T| = %g)", asym);
-      std::vector<double> Vt((size_t)n * n), lam(n);
-      sym_eig((int)n, A.data(), Vt.data(), lam.data());
-      void* dv = eig_buf(f, kKeyVt64, (size_t)n * n * 8);
-      void* dl = eig_buf(f, kKeyLam64, (size_t)n * 8);
-      COLA_CUDA(cudaMemcpyAsync(dv, Vt.data(), (size_t)n * n * 8, cudaMemcpyHostToDevice, c->s));
-      COLA_CUDA(cudaMemcpyAsync(dl, lam.data(), (size_t)n * 8, cudaMemcpyHostToDevice, c->s));
-      std::vector<float> V32(Vt.begin(), Vt.end());
-      void* d32 = eig_buf(f, kKeyVt32, (size_t)n * n * 4);
-      COLA_CUDA(cudaMemcpyAsync(d32, V32.data(), (size_t)n * n * 4, cudaMemcpyHostToDevice, c->s));
-      COLA_CUDA(cudaStreamSynchronize(c->s));  // host vectors go out of scope
-      f->eig_hash = h;
-    }
+    double amax = 0.0, asym = 0.0;
+    for (int64_t i = 0; i < n; ++i)
+      for (int64_t j = 0; j < n; ++j) {
+        amax = std::max(amax, fabs(A[(size_t)i * n + j]));
+        asym = std::max(asym, fabs(A[(size_t)i * n + j] - A[(size_t)j * n + i]));
+      }
+    COLA_REQUIRE(asym <= 1e-12 * amax, COLA_ERR_INVALID_ARG,
+                 "Kronecker factor is not symmetric (max |K - K^T| = %g)", asym);
+    std::vector<double> Vt((size_t)n * n), lam(n);
+    sym_eig((int)n, A.data(), Vt.data(), lam.data());
+    void* dv = eig_buf(f, kKeyVt64, (size_t)n * n * 8);
+    void* dl = eig_buf(f, kKeyLam64, (size_t)n * 8);
+    COLA_CUDA(cudaMemcpyAsync(dv, Vt.data(), (size_t)n * n * 8, cudaMemcpyHostToDevice, c->s));
+    COLA_CUDA(cudaMemcpyAsync(dl, lam.data(), (size_t)n * 8, cudaMemcpyHostToDevice, c->s));
+    std::vector<float> V32(Vt.begin(), Vt.end());
+    void* d32 = eig_buf(f, kKeyVt32, (size_t)n * n * 4);
+    COLA_CUDA(cudaMemcpyAsync(d32, V32.data(), (size_t)n * n * 4, cudaMemcpyHostToDevice, c->s));
+    COLA_CUDA(cudaStreamSynchronize(c->s));  // host vectors go out of scope
+    f->eig_hash = h;
   }
   (void)want32;
 }
@@ -280,6 +342,7 @@ void prepare_eig(Ctx* c, const KronShift& m, bool want32) {
 EigDims dims_of(const KronShift& m) {
   EigDims g{};
   g.d = (int)m.kron->kids.size();
+  g.sum = m.sum ? 1 : 0;
   for (int k = 0; k < g.d; ++k) {
     const cola_linop* f = m.kron->kids[k];
     g.n[k] = f->rows;
@@ -346,7 +409,25 @@ __global__ void k_scale_rows(T* Y, int64_t N, const T* inv) {
 
 }  // namespace
 
-// Preconditioner for A = c_k Kron + c_d Diag(d): M = c_k Kron + c_d mean(d) I
+// Direct solve X = A^-1 B when A is eigen-structured (Kron or KronSum of
+// square dense factors, optionally + scalar * I); false, with nothing
+// launched, otherwise.  FP64 or FP32 vectors.
+bool eig_solve_if_structured(Ctx* c, const cola_linop* op, const void* B, void* X, int64_t R,
+                             bool f64) {
+  KronShift m;
+  if (!try_match(op, m)) return false;
+  prepare_leaves(c, const_cast<cola_linop*>(op), COLA_PREC_F64, 0);
+  prepare_eig(c, m, !f64);
+  const double* s = m.diag ? leaf_ptr<double>(m.diag) : nullptr;
+  if (f64)
+    eig_solve<double>(c, m, s, m.cd, (const double*)B, (double*)X, R);
+  else
+    eig_solve<float>(c, m, s, m.cd, (const float*)B, (float*)X, R);
+  return true;
+}
+
+// Preconditioner for A = c_k Kron + c_d Diag(d) (Kron a Kronecker product or
+// sum): M = c_k Kron + c_d mean(d) I
 // = Q diag(c_k lambda + c_d mean(d)) Q^T with Q = (x)_k V_k, applied exactly as
 // Q^T, a diagonal scaling and Q.  The two Kronecker products run through the
 // ordinary MVM path in the solve's precision (tensor cores for MIXED), with
@@ -359,7 +440,7 @@ bool kron_precond_setup(Ctx* c, cola_linop* op, KronPrecond* P, int64_t R, int p
   if (op->kind != LK_SUM || op->kids.size() != 2) return false;
   int ik = -1, id = -1;
   for (int i = 0; i < 2; ++i) {
-    if (op->kids[i]->kind == LK_KRON) ik = i;
+    if (is_kron_node(op->kids[i])) ik = i;
     if (op->kids[i]->kind == LK_DIAG) id = i;
   }
   if (ik < 0 || id < 0) return false;
@@ -379,11 +460,12 @@ bool kron_precond_setup(Ctx* c, cola_linop* op, KronPrecond* P, int64_t R, int p
   const double shift = op->coeffs[id] * mean;
   KronShift m;
   m.kron = kron;
+  m.sum = kron->kind == LK_KRONSUM;
   m.ck = op->coeffs[ik];
   prepare_eig(c, m, false);
-  // smallest eigenvalue of M: the products prod_k lambda_k[i_k] fill an
-  // interval whose ends are products of per-factor extreme eigenvalues
-  double lo = 1.0, hi = 1.0;
+  // smallest eigenvalue of M: the products (sums) of factor eigenvalues fill
+  // an interval whose ends come from per-factor extreme eigenvalues
+  double lo = m.sum ? 0.0 : 1.0, hi = lo;
   for (auto* f : kron->kids) {
     std::vector<double> lam(f->rows);
     COLA_CUDA(cudaMemcpyAsync(lam.data(), f->derived.at(kKeyLam64).p, 8 * f->rows,
@@ -391,9 +473,14 @@ bool kron_precond_setup(Ctx* c, cola_linop* op, KronPrecond* P, int64_t R, int p
     COLA_CUDA(cudaStreamSynchronize(c->s));
     const double a = *std::min_element(lam.begin(), lam.end());
     const double b = *std::max_element(lam.begin(), lam.end());
-    const double q[4] = {lo * a, lo * b, hi * a, hi * b};
-    lo = *std::min_element(q, q + 4);
-    hi = *std::max_element(q, q + 4);
+    if (m.sum) {
+      lo += a;
+      hi += b;
+    } else {
+      const double q[4] = {lo * a, lo * b, hi * a, hi * b};
+      lo = *std::min_element(q, q + 4);
+      hi = *std::max_element(q, q + 4);
+    }
   }
   const double mmin = (m.ck >= 0.0 ? m.ck * lo : m.ck * hi) + shift;
   COLA_REQUIRE(mmin > 0.0, COLA_ERR_INVALID_ARG,

@@ -52,6 +52,7 @@ def test_opts_defaults(lib):
     assert o.tol == 1e-8 and o.maxiter == 100000 and o.precision == _abi.PREC_MIXED
     assert o.refine == 1 and o.split_factor_terms == 3 and o.split_vector_terms == 3
     assert o.graph_chunk == 64
+    assert o.jacobi == 0 and o.x0_given == 0 and o.kron_precond == 0
 
 
 def test_null_arguments_are_rejected_without_a_device(lib):

@@ -1,0 +1,218 @@
+"""Product splitting (cola_product_solve, Sec. 3.2 / Table 3) and the
+Kronecker-sum eigen-structured solve against the FP64 oracle.
+
+Referees: dense LU of the product, the oracle's exact Kronecker-sum solve
+(eigendecompositions of the factors, pinned against the Dirichlet Laplacian's
+closed-form spectrum), the oracle's CG iteration counts, and the true residual
+computed by the oracle's MVM."""
+import numpy as np
+import pytest
+
+import workloads as wl
+from oracle import exact, krylov
+from tests._trees import gpu_tree, oracle_tree
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+DEV = "cuda"
+
+
+@pytest.fixture(scope="module")
+def cola():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2309_03060_gb300 as c
+    from paper_2309_03060_gb300 import build
+    build.build()
+    return c
+
+
+@pytest.fixture(scope="module")
+def ctx(cola):
+    return cola.Context(0)
+
+
+def _bipoisson_spec(L):
+    ks = ("kronsum", [("dense", L), ("dense", L)])
+    return ("product", [ks, ks])
+
+
+def _abs_spec(spec):
+    k = spec[0]
+    if k in ("dense", "diag"):
+        return (k, np.abs(spec[1]))
+    if k == "scalar":
+        return (k, abs(spec[1]), spec[2])
+    if k in ("kron", "kronsum", "product"):
+        return (k, [_abs_spec(s) for s in spec[1]])
+    return (k, [_abs_spec(s) for s in spec[1]], None if spec[2] is None
+            else [abs(c) for c in spec[2]])
+
+
+def _rounding_level(spec, X, B):
+    """Evaluating ||b - A x|| in FP64 is exact up to about u || |A| |x| ||
+    per term accumulated; 64 u || |A| |x| || / ||b|| bounds the difference of
+    two such evaluations."""
+    AX = oracle_tree(_abs_spec(spec)).mvm(np.abs(X))
+    return 64 * 2.0 ** -53 * np.linalg.norm(AX, axis=1) / np.linalg.norm(B, axis=1)
+
+
+def _kappa_kronsum_laplacian(n):
+    lam = 2.0 - 2.0 * np.cos(np.arange(1, n + 1) * np.pi / (n + 1))
+    return (2 * lam.max()) / (2 * lam.min())
+
+
+def test_bipoisson_split_cg_f64(cola, ctx):
+    """(L (+) L)^2 on a 64 x 64 grid, tol 1e-11, one CG per factor: the
+    solution against the oracle's exact split solve, the reported residual
+    against the oracle's, and the iteration count against two oracle CGs."""
+    w = wl.bipoisson(64, nrhs=2)
+    spec = _bipoisson_spec(w.L)
+    ks_spec = spec[1][0]
+    ks1 = gpu_tree(cola, ctx, ks_spec, torch.float64, DEV).set_spd()
+    ks2 = gpu_tree(cola, ctx, ks_spec, torch.float64, DEV).set_spd()
+    op = cola.cola_linop_product(ctx, [ks1, ks2])
+    opts = cola.cola_cg_opts_default(precision=cola.PREC_F64, refine=0, tol=w.tol,
+                                     maxiter=w.maxiter, graph_chunk=32)
+    X, info, st = cola.cola_product_solve(ctx, op, torch.tensor(w.B, device=DEV), opts,
+                                          use_structure=False)
+    assert st == 0, info
+    solve = lambda Y: exact.kronsum_shift_solve([w.L, w.L], 0.0, Y)
+    ref = exact.product_split_solve([solve, solve], w.B)
+    Xh = X.cpu().numpy()
+    kA = _kappa_kronsum_laplacian(64)
+    # forward error of two solves at tol: <= kappa (1 + kappa) tol
+    assert np.abs(Xh - ref).max() <= 4 * kA * (1 + kA) * w.tol * np.abs(ref).max()
+    res = krylov.true_relative_residual(oracle_tree(spec), w.B, Xh)
+    # ||b - A_1 A_2 x|| <= (1 + kappa(A_1)) tol ||b||
+    assert np.all(res <= 2 * (1 + kA) * w.tol), res
+    got = np.array([i["rel_residual"] for i in info])
+    assert np.all(np.abs(got - res) <= _rounding_level(spec, Xh, w.B)), (got, res)
+    ks = oracle_tree(ks_spec)
+    for r in range(2):
+        y = solve(w.B[r])[0]
+        _, it1 = krylov.cg(ks, w.B[r], tol=w.tol, maxiter=w.maxiter)
+        _, it2 = krylov.cg(ks, y, tol=w.tol, maxiter=w.maxiter)
+        assert info[r]["iterations"] <= it1 + it2 + 2 * 32 + 40, (info[r], it1, it2)
+
+
+def test_bipoisson_monolithic_cg_falls_behind(cola, ctx):
+    """One CG on the product itself (condition number kappa^2) does not reach
+    1e-11 in the iterations the split solve needed in total."""
+    w = wl.bipoisson(64, nrhs=1)
+    ks_spec = _bipoisson_spec(w.L)[1][0]
+    ks1 = gpu_tree(cola, ctx, ks_spec, torch.float64, DEV).set_spd()
+    ks2 = gpu_tree(cola, ctx, ks_spec, torch.float64, DEV).set_spd()
+    op = cola.cola_linop_product(ctx, [ks1, ks2]).set_spd()
+    B = torch.tensor(w.B, device=DEV)
+    opts = cola.cola_cg_opts_default(precision=cola.PREC_F64, refine=0, tol=w.tol,
+                                     maxiter=w.maxiter, graph_chunk=32)
+    _, info_s, st_s = cola.cola_product_solve(ctx, op, B, opts, use_structure=False)
+    assert st_s == 0
+    budget = info_s[0]["iterations"]
+    mono = cola.cola_cg_opts_default(precision=cola.PREC_F64, refine=0, tol=w.tol,
+                                     maxiter=budget, graph_chunk=32)
+    _, info_m, st_m = cola.cola_cg_solve(ctx, op, B, mono, raise_on_error=False)
+    assert st_m == 5, info_m
+    assert info_m[0]["rel_residual"] > 100 * w.tol
+
+
+def test_kronsum_eig_solve_and_logdet(cola, ctx):
+    """L_24 (+) L_20 (+) S + 0.05 I (tridiagonal and dense SPD factors): the
+    direct eigen solve in FP64 and FP32 and the exact log-det against the
+    oracle's Kronecker-sum closed form and dense LU."""
+    r = np.random.default_rng(61)
+    M = r.standard_normal((6, 6))
+    S = M @ M.T / 6 + 0.5 * np.eye(6)
+    facs = [wl.dirichlet_laplacian(24), wl.dirichlet_laplacian(20), S]
+    N = 24 * 20 * 6
+    spec = ("sum", [("kronsum", [("dense", f) for f in facs]), ("scalar", 0.05, N)], [2.0, 1.0])
+    op = gpu_tree(cola, ctx, spec, torch.float64, DEV)
+    B = r.standard_normal((3, N))
+    ref_tree = oracle_tree(spec)
+    ref = exact.dense_solve(ref_tree.dense(), B)
+    # 2 (+)K + 0.05 I = 2 ((+)K + 0.025 I)
+    ref_k = exact.kronsum_shift_solve(facs, 0.025, B) / 2.0
+    np.testing.assert_allclose(ref_k, ref, rtol=1e-8, atol=1e-12)
+    X64 = cola.cola_kron_eig_solve(ctx, op, torch.tensor(B, device=DEV), cola.PREC_F64)
+    assert np.abs(X64.cpu().numpy() - ref).max() <= 1e-10 * np.abs(ref).max()
+    X32 = cola.cola_kron_eig_solve(ctx, op, torch.tensor(B, dtype=torch.float32, device=DEV),
+                                   cola.PREC_F32)
+    assert np.abs(X32.double().cpu().numpy() - ref).max() <= 1e-4 * np.abs(ref).max()
+    ld = cola.cola_kron_eig_logdet(ctx, op)
+    ld_ref = exact.cholesky_logdet(ref_tree.dense())
+    lam = 2.0 * exact.kronsum_eigenvalues(facs, 0.025)
+    assert abs(ld - float(np.sum(np.log(lam)))) <= 1e-10 * abs(ld)
+    assert abs(ld - ld_ref) <= 1e-9 * abs(ld_ref)
+
+
+def test_product_structured_dispatch(cola, ctx):
+    """Product(K1 (x) K2 + 0.1 I, Diag(d), L (+) L + 0.2 I) with use_structure:
+    eigen solve, division and eigen solve; no CG iterations, FP64 accuracy
+    against dense LU of the product."""
+    r = np.random.default_rng(62)
+    n1, n2 = 16, 24
+    N = n1 * n2
+    K1 = wl.rbf_factor(r.random(n1), 0.3)
+    K2 = wl.rbf_factor(r.random(n2), 0.3)
+    L1, L2 = wl.dirichlet_laplacian(n1), wl.dirichlet_laplacian(n2)
+    d = 0.5 + r.random(N)
+    spec = ("product", [
+        ("sum", [("kron", [("dense", K1), ("dense", K2)]), ("scalar", 0.1, N)], None),
+        ("diag", d),
+        ("sum", [("kronsum", [("dense", L1), ("dense", L2)]), ("scalar", 0.2, N)], None)])
+    op = gpu_tree(cola, ctx, spec, torch.float64, DEV)
+    B = r.standard_normal((2, N))
+    opts = cola.cola_cg_opts_default(precision=cola.PREC_F64, refine=0, tol=1e-12)
+    X, info, st = cola.cola_product_solve(ctx, op, torch.tensor(B, device=DEV), opts,
+                                          use_structure=True)
+    assert st == 0
+    assert all(i["iterations"] == 0 for i in info)
+    ref = exact.dense_solve(oracle_tree(spec).dense(), B)
+    assert np.abs(X.cpu().numpy() - ref).max() <= 1e-9 * np.abs(ref).max()
+    res = krylov.true_relative_residual(oracle_tree(spec), B, X.cpu().numpy())
+    got = np.array([i["rel_residual"] for i in info])
+    assert np.all(np.abs(got - res) <= _rounding_level(spec, X.cpu().numpy(), B)), (got, res)
+
+
+def test_kronsum_precond_poisson_with_variable_diagonal(cola, ctx):
+    """PCG on L (+) L + Diag(d), d in [0.5, 1.5], preconditioned with
+    L (+) L + mean(d) I: FP64 solution against dense LU, iterations against
+    the oracle's PCG with the same M."""
+    n = 32
+    N = n * n
+    r = np.random.default_rng(63)
+    L = wl.dirichlet_laplacian(n)
+    d = 0.5 + r.random(N)
+    spec = ("sum", [("kronsum", [("dense", L), ("dense", L)]), ("diag", d)], None)
+    op = gpu_tree(cola, ctx, spec, torch.float64, DEV).set_spd()
+    B = r.standard_normal((2, N))
+    opts = cola.cola_cg_opts_default(precision=cola.PREC_F64, refine=0, tol=1e-10, maxiter=500,
+                                     graph_chunk=4, kron_precond=1)
+    X, info, st = cola.cola_cg_solve(ctx, op, torch.tensor(B, device=DEV), opts)
+    assert st == 0, info
+    ref_tree = oracle_tree(spec)
+    ref = exact.dense_solve(ref_tree.dense(), B)
+    assert np.abs(X.cpu().numpy() - ref).max() <= 1e-8 * np.abs(ref).max()
+    s = float(np.mean(d))
+    for k in range(2):
+        _, it_o = krylov.cg(ref_tree, B[k], tol=1e-10, maxiter=500,
+                            precond=lambda v: exact.kronsum_shift_solve([L, L], s, v)[0])
+        assert info[k]["iterations"] <= it_o + 8, (info[k], it_o)
+
+
+def test_product_solve_rejections(cola, ctx):
+    r = np.random.default_rng(64)
+    A = r.standard_normal((5, 7))
+    op = gpu_tree(cola, ctx, ("product", [("dense", A), ("dense", A.T)]), torch.float64, DEV)
+    B = torch.tensor(r.standard_normal((1, 5)), device=DEV)
+    opts = cola.cola_cg_opts_default(precision=cola.PREC_F64, refine=0)
+    with pytest.raises(cola.ColaError) as e:
+        cola.cola_product_solve(ctx, op, B, opts)
+    assert e.value.status == 2
+    S = A @ A.T + np.eye(5)
+    op2 = gpu_tree(cola, ctx, ("product", [("dense", S), ("dense", S)]), torch.float64, DEV)
+    with pytest.raises(cola.ColaError) as e:
+        cola.cola_product_solve(ctx, op2, B, opts)
+    assert e.value.status == 9

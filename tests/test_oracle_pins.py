@@ -259,6 +259,41 @@ def test_kron_mean_shift_pcg_meets_condition_number_bound():
     assert it_plain > 2 * it
 
 
+def test_kronsum_eigenvalues_match_laplacian_closed_form():
+    """L (+) L with L = tridiag(-1, 2, -1) of size n: eigenvalues
+    (2 - 2 cos(i pi/(n+1))) + (2 - 2 cos(j pi/(n+1))) (textbook Dirichlet
+    Laplacian spectrum)."""
+    n = 9
+    L = wl.dirichlet_laplacian(n)
+    lam = 2.0 - 2.0 * np.cos(np.arange(1, n + 1) * np.pi / (n + 1))
+    closed = np.sort(np.add.outer(lam, lam).ravel())
+    np.testing.assert_allclose(np.sort(exact.kronsum_eigenvalues([L, L])), closed, rtol=1e-13,
+                               atol=1e-13)
+
+
+def test_exact_kronsum_solve_matches_dense():
+    mats = [_spd(4, 41), _spd(3, 42), _spd(5, 43)]
+    op = Sum([KronSum([Dense(m) for m in mats]), Diag(0.3, 60)])
+    B = _rs(44).standard_normal((2, 60))
+    np.testing.assert_allclose(exact.kronsum_shift_solve(mats, 0.3, B),
+                               exact.dense_solve(op.dense(), B), rtol=1e-10)
+
+
+def test_product_split_solve_order():
+    """A = A_1 A_2 with non-commuting Kronecker-sum factors: solving A_1 first,
+    then A_2, matches dense LU of the product; the reversed order does not."""
+    f1 = [_spd(4, 45), _spd(5, 46)]
+    f2 = [_spd(4, 47), _spd(5, 48)]
+    A1 = KronSum([Dense(m) for m in f1])
+    A2 = Sum([KronSum([Dense(m) for m in f2]), Diag(0.2, 20)])
+    B = _rs(49).standard_normal((2, 20))
+    s1 = lambda X: exact.kronsum_shift_solve(f1, 0.0, X)
+    s2 = lambda X: exact.kronsum_shift_solve(f2, 0.2, X)
+    ref = exact.dense_solve(Product([A1, A2]).dense(), B)
+    np.testing.assert_allclose(exact.product_split_solve([s1, s2], B), ref, rtol=1e-9)
+    assert np.abs(exact.product_split_solve([s2, s1], B) - ref).max() > 1e-3 * np.abs(ref).max()
+
+
 def test_exact_kron_solve_matches_dense():
     mats = [_spd(3, 15), _spd(4, 16), _spd(2, 17)]
     s = 0.05

@@ -239,3 +239,27 @@ def config5(n: int = 1024, nprobes: int = 32) -> GPWorkload:
     y = normal(substream(seed, 1), (N,))
     Z = rademacher(substream(seed, 2), (nprobes, N))
     return GPWorkload("gp_kron2_rbf_grad", pts, [0.1, 0.2], 0.1, y, Z, 1e-8)
+
+
+@dataclass
+class BiPoissonWorkload:
+    """The Bi-Poisson operator (L (+) L)^2 on an n x n Dirichlet grid, as the
+    product of two Kronecker sums, with N(0, 1) right-hand sides."""
+    name: str
+    L: np.ndarray          # (n, n) tridiag(-1, 2, -1)
+    B: np.ndarray          # (nrhs, n * n)
+    tol: float
+    maxiter: int
+
+    @property
+    def N(self) -> int:
+        return self.L.shape[0] ** 2
+
+
+def bipoisson(n: int = 1000, nrhs: int = 1) -> BiPoissonWorkload:
+    """Fig. 2(b) setting: grid up to 1000^2, CG tolerance 1e-11.  The paper caps
+    CG at 10K iterations; the residual bound for kappa(L (+) L) = 4.1e5 at
+    n = 1000 allows up to ~10.4K per solve, so the cap here is 20K."""
+    seed = BASE_SEED + 7
+    B = normal(substream(seed, 1), (nrhs, n * n))
+    return BiPoissonWorkload(f"bipoisson_{n}x{n}", dirichlet_laplacian(n), B, 1e-11, 20000)

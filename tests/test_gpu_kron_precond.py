@@ -133,8 +133,10 @@ def test_kron_precond_rejections(cola, ctx):
         cola.cola_cg_solve(ctx, op, B, both)
     assert e.value.status == 1
     kp = cola.cola_cg_opts_default(precision=cola.PREC_F64, refine=0, kron_precond=1)
-    ks = ("sum", [("kronsum", [("dense", f) for f in w.factors]), ("diag", w.extra["d"])], None)
-    op2 = gpu_tree(cola, ctx, ks, torch.float64, DEV).set_spd()
+    U = np.random.default_rng(44).standard_normal((w.N, 2)) / w.N
+    three = ("sum", [("kron", [("dense", f) for f in w.factors]), ("diag", w.extra["d"]),
+                     ("lowrank", U, None)], None)
+    op2 = gpu_tree(cola, ctx, three, torch.float64, DEV).set_spd()
     with pytest.raises(cola.ColaError) as e:
         cola.cola_cg_solve(ctx, op2, B, kp)
     assert e.value.status == 9

@@ -205,7 +205,8 @@ def test_kronsum_precond_poisson_with_variable_diagonal(cola, ctx):
 def test_product_solve_rejections(cola, ctx):
     r = np.random.default_rng(64)
     A = r.standard_normal((5, 7))
-    op = gpu_tree(cola, ctx, ("product", [("dense", A), ("dense", A.T)]), torch.float64, DEV)
+    op = gpu_tree(cola, ctx, ("product", [("dense", A), ("dense", np.ascontiguousarray(A.T))]),
+                  torch.float64, DEV)
     B = torch.tensor(r.standard_normal((1, 5)), device=DEV)
     opts = cola.cola_cg_opts_default(precision=cola.PREC_F64, refine=0)
     with pytest.raises(cola.ColaError) as e:

@@ -268,6 +268,55 @@ def run_bipoisson(cola, ctx, device, args, stream):
                             "rel_residual": info_e[0]["rel_residual"]}}
 
 
+def run_diag_estimate(cola, ctx, device, args, stream):
+    """Doubly stochastic vs Hutchinson diagonal estimation (Sec. 3.3 / App. B.1)
+    on the multi-task covariance sum_q c_q B_q (x) K_q (8 terms, 128 tasks x
+    1024 points, N = 131072), 16 Rademacher probes per term, MIXED with 3 split
+    terms: time per estimate, error against the exact diagonal (Diag rule:
+    Diag(B (x) K) = diag(B) (x) diag(K)), and the error the Rademacher variance
+    formula predicts (Frobenius norms from the Kronecker structure)."""
+    import numpy as np
+    import torch
+    w = wl.multitask()
+    n = 16
+    kids, keep = [], []
+    for b, k in zip(w.B, w.K):
+        tb, tk = torch.tensor(b, device=device), torch.tensor(k, device=device)
+        keep += [tb, tk]
+        kids.append(cola.cola_linop_kron(ctx, cola.cola_linop_dense(ctx, tb),
+                                         cola.cola_linop_dense(ctx, tk)))
+    op = cola.cola_linop_sum(ctx, kids, [float(c) for c in w.coeffs])
+    exact = sum(c * np.kron(np.diag(b), np.diag(k)) for b, k, c in zip(w.B, w.K, w.coeffs))
+    fro2 = sum(cq * cr * np.sum(bq * br) * np.sum(kq * kr)
+               for bq, kq, cq in zip(w.B, w.K, w.coeffs)
+               for br, kr, cr in zip(w.B, w.K, w.coeffs))
+    off_base = fro2 - float(np.sum(exact ** 2))
+    off_dbl = sum(c * c * (np.sum(b * b) * np.sum(k * k)
+                           - float(np.sum(np.kron(np.diag(b), np.diag(k)) ** 2)))
+                  for b, k, c in zip(w.B, w.K, w.coeffs))
+    out = {"workload": f"{w.name}: sum of {len(w.B)} Kron(task 128, RBF 1024) terms, "
+                       f"N = {w.N}, {n} probes per term, MIXED (3 split terms)"}
+    for doubly, off in ((False, off_base), (True, off_dbl)):
+        def call():
+            return cola.cola_diag_estimate(ctx, op, n, seed=17, doubly=doubly,
+                                           precision=cola.PREC_MIXED, split_terms=3)
+        call()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        d, tr = call()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1) / 1e3
+        err = float(np.linalg.norm(d.cpu().numpy() - exact) / np.linalg.norm(exact))
+        pred = float(np.sqrt(off / n) / np.linalg.norm(exact))
+        out["doubly" if doubly else "base"] = {
+            "seconds": round(t, 4), "estimates_per_s": round(1.0 / t, 2),
+            "diag_rel_error": round(err, 5), "predicted_rel_error": round(pred, 5),
+            "trace_rel_error": abs(tr - float(exact.sum())) / float(exact.sum())}
+    return out
+
+
 def time_queued(torch, ctx, fn, reps):
     """Device time of `reps` calls of fn, on the library's launch stream (the
     calls are issued on that stream, so no cross-stream join sits between
@@ -436,6 +485,8 @@ def run_ours(args):
         if (rank == 0 and args.kron_precond) else None
     bipo = run_bipoisson(cola, ctx, device, args, stream) \
         if (rank == 0 and args.bipoisson) else None
+    dest = run_diag_estimate(cola, ctx, device, args, stream) \
+        if (rank == 0 and args.diag_est) else None
 
     plain = None
     if rank == 0 and args.plain:
@@ -474,7 +525,7 @@ def run_ours(args):
                                    "step_time_s": round(it_time, 4)},
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
             "clocks": clk, "plain_fp32": plain, "kron_eig": eig, "batched": batched,
-            "kron_precond": kprec, "bipoisson": bipo,
+            "kron_precond": kprec, "bipoisson": bipo, "diag_estimate": dest,
         }
         print(json.dumps(line))
     ctx.close()
@@ -571,6 +622,10 @@ def main():
                     help="also time the product-splitting Bi-Poisson solves")
     ap.add_argument("--bipoisson-only", action="store_true",
                     help="run only the product-splitting Bi-Poisson solves")
+    ap.add_argument("--diag-est", action=argparse.BooleanOptionalAction, default=True,
+                    help="also time the doubly stochastic diagonal estimator")
+    ap.add_argument("--diag-est-only", action="store_true",
+                    help="run only the doubly stochastic diagonal estimator")
     ap.add_argument("--eig", action=argparse.BooleanOptionalAction, default=True,
                     help="also time the eigen-structured direct solve and exact log-det")
     ap.add_argument("--plain", action=argparse.BooleanOptionalAction, default=True,
@@ -589,6 +644,12 @@ def main():
         hbm, _, _ = peaks()
         print(json.dumps(run_batched_workload(cola, ctx, torch.device("cuda", 0), hbm,
                                               torch.cuda.current_stream())))
+    elif args.diag_est_only:
+        import torch
+        import paper_2309_03060_gb300 as cola
+        ctx = cola.Context(0)
+        print(json.dumps(run_diag_estimate(cola, ctx, torch.device("cuda", 0), args,
+                                           torch.cuda.current_stream())))
     elif args.bipoisson_only:
         import torch
         import paper_2309_03060_gb300 as cola

@@ -288,6 +288,24 @@ cola_status cola_lanczos(cola_ctx* ctx, const cola_linop* op, const void* Q0, in
                          int32_t m, int32_t precision, int32_t reorth, double* alpha,
                          double* beta, int32_t* m_eff, cola_stream stream);
 
+/* Stochastic estimate of Diag(A) and Tr(A) (Sec. 3.3; App. B.1).  Base
+ * (doubly = 0, or op not a Sum node): Hutchinson's estimator
+ *   Diag(A) ~ (1/n) sum_v z_v (.) A z_v  over n = nprobes Rademacher probes.
+ * Doubly stochastic (doubly = 1 and op a Sum node A = sum_i c_i A_i): each
+ * term draws its own probes,
+ *   Diag(A) ~ sum_i c_i (1/n) sum_v z_iv (.) A_i z_iv,
+ * which drops the cross terms between summands from the variance.  Probe
+ * entry (term i, probe v, index k) = sign of the top bit of SplitMix64 output
+ * (i n + v) N + k of the stream seeded with `seed` (term 0 for the base
+ * estimator), as cola_rademacher draws it.  MVMs run in `precision` (MIXED:
+ * the tensor-core path for Kronecker terms, with the context's split terms);
+ * the estimate accumulates in FP64.  diag: device FP64 [N] or NULL; trace:
+ * HOST double (the sum of the diagonal estimate) or NULL; at least one must
+ * be given.  Synchronous when trace is requested, asynchronous otherwise. */
+cola_status cola_diag_estimate(cola_ctx* ctx, const cola_linop* op, int32_t nprobes,
+                               uint64_t seed, int32_t doubly, int32_t precision, double* diag,
+                               double* trace, cola_stream stream);
+
 /* Stochastic Lanczos quadrature for log det A = Tr(log A) (App. A.2):
  * nprobes Rademacher probes z_v drawn on the device from `seed` (entry
  * (v, i) = sign of the top bit of SplitMix64 output v*N + i), or taken from

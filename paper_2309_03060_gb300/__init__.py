@@ -332,6 +332,20 @@ def cola_slq_logdet(ctx: Context, op: LinOp, nprobes: int, m: int, seed: int = 0
     return ld.value, se.value, pp, cl.value
 
 
+def cola_diag_estimate(ctx: Context, op: LinOp, nprobes: int, seed: int = 0,
+                       doubly: bool = True, precision: int = PREC_F64, split_terms=2):
+    """Stochastic Diag(A) (FP64 device tensor [N]) and Tr(A) estimates;
+    split_terms (MIXED) as in cola_matvec.  Returns (diag, trace)."""
+    diag = torch.empty(op.shape[0], dtype=torch.float64, device=ctx.device)
+    tr = C.c_double()
+    ft, vt = (split_terms, split_terms) if isinstance(split_terms, int) else split_terms
+    check(_lib().cola_set_split_terms(ctx.handle, int(ft), int(vt)))
+    check(_lib().cola_diag_estimate(ctx.handle, op.handle, nprobes,
+                                    C.c_uint64(seed & (2**64 - 1)), int(doubly), precision,
+                                    _ptr(diag), C.byref(tr), _stream()))
+    return diag, tr.value
+
+
 def _leaf_grad_buffers(op: LinOp, dtypes, device):
     out = []
     for (kind, r, c), dt in zip(op.leaves(), dtypes):

@@ -12,7 +12,7 @@ import os
 import numpy as np
 import pytest
 
-from oracle import exact, grad, krylov, rng
+from oracle import exact, grad, krylov, rng, stochastic
 from oracle.linop import (Dense, Diag, Kron, KronSum, LowRank, Product, Sum,
                           derivative)
 import workloads as wl
@@ -292,6 +292,70 @@ def test_product_split_solve_order():
     ref = exact.dense_solve(Product([A1, A2]).dense(), B)
     np.testing.assert_allclose(exact.product_split_solve([s1, s2], B), ref, rtol=1e-9)
     assert np.abs(exact.product_split_solve([s2, s1], B) - ref).max() > 1e-3 * np.abs(ref).max()
+
+
+# ---------------------------------------------------------------------------
+# Stochastic diagonal / trace estimators (Sec. 3.3, App. B.1)
+# ---------------------------------------------------------------------------
+
+def _hypercube(N):
+    """All 2^N sign vectors, shape (2^N, N)."""
+    idx = np.arange(2 ** N)[:, None]
+    return np.where((idx >> np.arange(N)[None, :]) & 1, -1.0, 1.0)
+
+
+def test_hutchinson_over_the_full_hypercube_is_exact():
+    """Averaging z (.) A z over every sign vector gives Diag(A) exactly (the
+    off-diagonal products z_k z_l cancel over the hypercube); the doubly
+    stochastic form with a full hypercube per term gives Diag of the sum."""
+    A1, A2 = _spd(4, 51), _rs(52).standard_normal((4, 4))
+    A2 = A2 + A2.T
+    Z = _hypercube(4)
+    np.testing.assert_allclose(stochastic.hutchinson_diag(Dense(A1), Z), np.diag(A1),
+                               rtol=1e-14, atol=1e-14)
+    Zs = np.stack([Z, Z[::-1]])
+    est = stochastic.doubly_stochastic_diag([Dense(A1), Dense(A2)], [0.5, 2.0], Zs)
+    np.testing.assert_allclose(est, 0.5 * np.diag(A1) + 2.0 * np.diag(A2), rtol=1e-14,
+                               atol=1e-14)
+
+
+def test_rademacher_trace_variance_by_enumeration():
+    """Var[z^T B z] over the uniform hypercube equals 2 sum_{k != l} B_kl^2."""
+    B = _rs(53).standard_normal((5, 5))
+    B = B + B.T
+    Z = _hypercube(5)
+    q = np.einsum("vk,kl,vl->v", Z, B, Z)
+    assert abs(np.var(q) - stochastic.rademacher_trace_variance(B)) < 1e-10 * np.var(q)
+
+
+def test_doubly_stochastic_trace_variance_statistics():
+    """1500 independent draws on a sum of three Kronecker products of RBF
+    factors (a multi-task kernel): the sample variances of the base and doubly
+    stochastic trace estimates match their formulas within 15 %, and the doubly
+    stochastic one is the smaller: with entrywise positive terms the cross
+    terms 4 c_i c_k sum_{k != l} (A_i)_kl (A_k)_kl of the base variance are
+    positive.  (For terms with off-diagonal entries of both signs they can be
+    negative, and the doubly stochastic variance is then not always smaller.)"""
+    r = _rs(59)
+    terms_m = [np.kron(wl.rbf_factor(r.random(4), 0.2 + 0.2 * i),
+                       wl.rbf_factor(r.random(5), 0.5 - 0.1 * i)) for i in range(3)]
+    coeffs = [1.0, 0.5, 2.0]
+    terms = [Dense(m) for m in terms_m]
+    A = sum(c * m for c, m in zip(coeffs, terms_m))
+    n, N, trials = 4, 20, 1500
+    base, dbl = [], []
+    for t in range(trials):
+        Zs = stochastic.probes(1000 + t, 3, n, N)
+        base.append(np.sum(stochastic.hutchinson_diag(Dense(A), Zs[0])))
+        dbl.append(np.sum(stochastic.doubly_stochastic_diag(terms, coeffs, Zs)))
+    v_base = stochastic.rademacher_trace_variance(A) / n
+    v_dbl = sum(c * c * stochastic.rademacher_trace_variance(m)
+                for c, m in zip(coeffs, terms_m)) / n
+    assert abs(np.mean(base) - np.trace(A)) < 4 * np.sqrt(v_base / trials)
+    assert abs(np.mean(dbl) - np.trace(A)) < 4 * np.sqrt(v_dbl / trials)
+    assert abs(np.var(base) / v_base - 1) < 0.15
+    assert abs(np.var(dbl) / v_dbl - 1) < 0.15
+    assert v_dbl < 0.8 * v_base
 
 
 def test_exact_kron_solve_matches_dense():

@@ -263,3 +263,36 @@ def bipoisson(n: int = 1000, nrhs: int = 1) -> BiPoissonWorkload:
     seed = BASE_SEED + 7
     B = normal(substream(seed, 1), (nrhs, n * n))
     return BiPoissonWorkload(f"bipoisson_{n}x{n}", dirichlet_laplacian(n), B, 1e-11, 20000)
+
+
+@dataclass
+class MultiTaskWorkload:
+    """A multi-task GP covariance (linear model of coregionalisation):
+    A = sum_q c_q B_q (x) K_q with task covariances B_q = a_q a_q^T + diag(k_q)
+    (T x T) and RBF data kernels K_q (n x n) on shared 1-D points."""
+    name: str
+    B: list                # task factors (T, T)
+    K: list                # data factors (n, n)
+    coeffs: list
+
+    @property
+    def N(self) -> int:
+        return self.B[0].shape[0] * self.K[0].shape[0]
+
+
+def multitask(terms: int = 8, tasks: int = 128, n: int = 1024) -> MultiTaskWorkload:
+    """The doubly stochastic estimators' workload (Sec. 3.3 names multi-task GPs
+    as the Sum structure it targets): lengthscales 0.02..0.3, task loadings
+    |N(0, 1)| (positively correlated tasks), task noise U[0.1, 1], coefficients
+    U[0.5, 1.5]."""
+    seed = BASE_SEED + 8
+    x = uniform(substream(seed, 1), (n,))
+    ells = 0.02 + 0.28 * uniform(substream(seed, 2), (terms,))
+    coeffs = list(0.5 + uniform(substream(seed, 3), (terms,)))
+    Bs, Ks = [], []
+    for q in range(terms):
+        a = np.abs(normal(substream(seed, 100 + q), (tasks,)))
+        k = 0.1 + 0.9 * uniform(substream(seed, 200 + q), (tasks,))
+        Bs.append(np.outer(a, a) + np.diag(k))
+        Ks.append(rbf_factor(x, float(ells[q])))
+    return MultiTaskWorkload(f"multitask_lmc{terms}_{tasks}x{n}", Bs, Ks, coeffs)

@@ -6,7 +6,9 @@ of self-adjoint A.  App. A.2 defines log det A = Tr(log A), which SLQ
 estimates with Rademacher probes z: E[z^T log(A) z] = Tr(log A) (Sec. 3.3 /
 App. B.1 trace estimator).  The Lanczos stopping rule mirrors the Arnoldi
 breakdown test of Algorithm 1 (stop when the new off-diagonal falls below a
-tolerance).
+tolerance).  The Householder Arnoldi iteration of Algorithm 2 keeps the basis
+orthogonal to rounding by building it from reflectors; for symmetric A its
+Hessenberg matrix is Lanczos' tridiagonal.
 """
 from __future__ import annotations
 
@@ -95,6 +97,49 @@ def lanczos(op, z, m, reorth=True, breakdown_tol=1e-10):
         beta_prev = beta
         Q.append(w / beta)
     return np.array(alphas), np.array(betas), np.array(Q[: len(alphas)])
+
+
+def householder_vector(w, k):
+    """Unit u with (I - 2 u u^T) w = (w_0, .., w_{k-1}, ||w_{k:}||, 0, .., 0)
+    (the GET_HOUSEHOLDER_VEC step of Algorithm 2: u_i = 0 below k, u_k =
+    w_k - ||w_{k:}||, u_i = w_i above k, then normalised)."""
+    u = np.zeros_like(w)
+    u[k + 1:] = w[k + 1:]
+    u[k] = w[k] - np.linalg.norm(w[k:])
+    n = np.linalg.norm(u)
+    return u / n if n > 0 else u
+
+
+def householder_arnoldi(op, nu0, T):
+    """Householder Arnoldi iteration (Algorithm 2) for T steps from nu_0.
+
+    For j = 0..T: u_j = householder_vector(nu_j, j), R_j = I - 2 u_j u_j^T,
+    h_j = R_j nu_j, q_j = R_0 ... R_j e_j and, for j < T,
+    nu_{j+1} = R_j ... R_0 (A q_j).  Column j - 1 of the (T+1) x T
+    Hessenberg matrix H holds h_j[0..j] (j >= 1), so A Q[:, :T] = Q H.
+    Returns (H, Q) with Q of shape (N, T+1)."""
+    nu = np.asarray(nu0, dtype=np.float64).copy()
+    N = nu.shape[0]
+    us = []
+    H = np.zeros((T + 1, T))
+    Q = np.zeros((N, T + 1))
+    for j in range(T + 1):
+        u = householder_vector(nu, j)
+        us.append(u)
+        h = nu - 2.0 * u * float(u @ nu)
+        if j >= 1:
+            H[: j + 1, j - 1] = h[: j + 1]
+        q = np.zeros(N)
+        q[j] = 1.0
+        for i in range(j, -1, -1):          # R_0 ... R_j e_j: R_j acts first
+            q = q - 2.0 * us[i] * float(us[i] @ q)
+        Q[:, j] = q
+        if j < T:
+            v = op @ q
+            for i in range(j + 1):           # R_j ... R_0 (A q_j): R_0 acts first
+                v = v - 2.0 * us[i] * float(us[i] @ v)
+            nu = v
+    return H, Q
 
 
 def tridiagonal(alpha, beta):

@@ -358,6 +358,46 @@ def test_doubly_stochastic_trace_variance_statistics():
     assert v_dbl < 0.8 * v_base
 
 
+# ---------------------------------------------------------------------------
+# Householder Arnoldi (Algorithm 2)
+# ---------------------------------------------------------------------------
+
+def test_householder_arnoldi_relation_and_orthogonality():
+    """Nonsymmetric A (30 x 30), 12 steps: Q has orthonormal columns, its first
+    column is nu_0 / ||nu_0||, H is upper Hessenberg, and A Q_T = Q_{T+1} H."""
+    r = _rs(80)
+    A = r.standard_normal((30, 30))
+    nu0 = r.standard_normal(30)
+    H, Q = krylov.householder_arnoldi(Dense(A), nu0, 12)
+    np.testing.assert_allclose(Q.T @ Q, np.eye(13), atol=1e-13)
+    np.testing.assert_allclose(Q[:, 0], nu0 / np.linalg.norm(nu0), atol=1e-14)
+    assert np.all(np.tril(H, -2) == 0.0)
+    np.testing.assert_allclose(A @ Q[:, :12], Q @ H, atol=1e-12)
+
+
+def test_householder_arnoldi_symmetric_is_lanczos():
+    """Symmetric A: H is tridiagonal to rounding and its diagonal and
+    sub-diagonal are Lanczos' alpha and beta (full reorthogonalisation) from
+    the same start."""
+    A = _spd(40, 81)
+    z = _rs(82).standard_normal(40)
+    H, _ = krylov.householder_arnoldi(Dense(A), z, 15)
+    band = np.triu(np.tril(H, 1), -1)
+    assert np.abs(H - band).max() < 1e-12 * np.abs(A).max()
+    a, b, _ = krylov.lanczos(Dense(A), z, 15, reorth=True)
+    np.testing.assert_allclose(np.diag(H[:15, :15]), a, rtol=1e-11, atol=1e-13)
+    np.testing.assert_allclose(np.abs(np.diag(H, -1))[:14], b, rtol=1e-11)
+
+
+def test_householder_vector_zeroes_the_tail():
+    w = _rs(83).standard_normal(9)
+    u = krylov.householder_vector(w, 3)
+    h = w - 2.0 * u * (u @ w)
+    np.testing.assert_allclose(h[:3], w[:3], atol=1e-15)
+    assert abs(h[3] - np.linalg.norm(w[3:])) < 1e-14
+    np.testing.assert_allclose(h[4:], 0.0, atol=1e-14)
+
+
 def test_exact_kron_solve_matches_dense():
     mats = [_spd(3, 15), _spd(4, 16), _spd(2, 17)]
     s = 0.05

@@ -283,10 +283,30 @@ cola_status cola_sym_eig(int64_t n, const double* A, double* V, double* w);
  * [nvec] (int32, device) is where vector v stopped: breakdown at
  * beta_j <= 1e-10 (F64) / 1e-6 (F32) times max|alpha| truncates it (not an
  * error).  reorth = 1 adds full reorthogonalisation (stores all q: nvec*m*N
- * elements of workspace).  Asynchronous. */
+ * elements of workspace); reorth = 2 builds the basis from Householder
+ * reflectors instead (cola_arnoldi_householder; alpha_j = H_jj, beta_j =
+ * |H_j+1,j|; nvec*(m+1)*N elements of workspace, m <= 255).  Asynchronous. */
 cola_status cola_lanczos(cola_ctx* ctx, const cola_linop* op, const void* Q0, int64_t nvec,
                          int32_t m, int32_t precision, int32_t reorth, double* alpha,
                          double* beta, int32_t* m_eff, cola_stream stream);
+
+/* Householder Arnoldi iteration (Algorithm 2) for nvec starting vectors Q0
+ * ([nvec][N], FP64 for F64 precision, FP32 else) at once, m steps each (1 <=
+ * m <= 255, m < N): reflectors R_j = I - 2 u_j u_j^T with u_j zero above
+ * index j map the tail of nu_j onto e_j, q_j = R_0 ... R_j e_j and
+ * nu_{j+1} = R_j ... R_0 A q_j, so the basis is orthogonal to working
+ * precision (the low-precision-robust variant of App. C.3).  H (device FP64,
+ * [nvec][m+1][m] row-major) receives the Hessenberg matrix with
+ * A Q[:, :m] = Q H.  The reflector takes the cancellation-free sign (Golub &
+ * Van Loan 5.1.2), so H equals Algorithm 2's up to a +-1 diagonal similarity
+ * (diagonal and eigenvalues identical, off-diagonal signs may differ).
+ * m_eff (device int32 [nvec]): columns computed before the new sub-diagonal
+ * fell to 1e-10 (F64) / 1e-6 (else) times max|H_ii|.  Any square operator
+ * (the symmetric case is Lanczos: cola_lanczos with reorth = 2).  Workspace
+ * nvec*(m+1)*N vector elements.  Asynchronous. */
+cola_status cola_arnoldi_householder(cola_ctx* ctx, const cola_linop* op, const void* Q0,
+                                     int64_t nvec, int32_t m, int32_t precision, double* H,
+                                     int32_t* m_eff, cola_stream stream);
 
 /* Stochastic estimate of Diag(A) and Tr(A) (Sec. 3.3; App. B.1).  Base
  * (doubly = 0, or op not a Sum node): Hutchinson's estimator

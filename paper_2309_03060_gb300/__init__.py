@@ -307,8 +307,21 @@ def cola_cg_solve_batched(ctx: Context, ops, Bs, opts: cola_cg_opts | None = Non
     return Xs, _info_list(info, sum(R)), st
 
 
+def cola_arnoldi_householder(ctx: Context, op: LinOp, Q0: torch.Tensor, m: int,
+                             precision: int = PREC_F64):
+    """Householder Arnoldi (Algorithm 2).  Returns (H [nvec, m+1, m] FP64, m_eff)."""
+    Q2 = Q0 if Q0.dim() == 2 else Q0.reshape(1, -1)
+    nv = Q2.shape[0]
+    H = torch.zeros((nv, m + 1, m), dtype=torch.float64, device=Q2.device)
+    meff = torch.zeros(nv, dtype=torch.int32, device=Q2.device)
+    check(_lib().cola_arnoldi_householder(ctx.handle, op.handle, _ptr(Q2), nv, m, precision,
+                                          _ptr(H), _ptr(meff), _stream()))
+    return H, meff
+
+
 def cola_lanczos(ctx: Context, op: LinOp, Q0: torch.Tensor, m: int, precision: int = PREC_F64,
-                 reorth: bool = False):
+                 reorth: int = 0):
+    """reorth: 0 none, 1 full reorthogonalisation, 2 Householder basis."""
     nv = Q0.shape[0]
     alpha = torch.zeros((nv, m), dtype=torch.float64, device=Q0.device)
     beta = torch.zeros((nv, m), dtype=torch.float64, device=Q0.device)

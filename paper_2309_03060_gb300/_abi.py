@@ -70,6 +70,7 @@ SIGNATURES = {
     "cola_logdet_backward": (I32, [P, P, P, P, I64, D, PP, I32, C.POINTER(cola_cg_opts), P]),
     "cola_rademacher": (I32, [P, C.c_uint64, I64, I64, P, I32, P]),
     "cola_diag_estimate": (I32, [P, P, I32, C.c_uint64, I32, I32, P, C.POINTER(D), P]),
+    "cola_arnoldi_householder": (I32, [P, P, P, I64, I32, I32, P, P, P]),
     "cola_kernel_launches": (I32, [P, C.POINTER(I64)]),
     "cola_get_stream": (I32, [P, C.POINTER(P)]),
     "cola_kron_eig_solve": (I32, [P, P, P, P, I64, I32, P]),

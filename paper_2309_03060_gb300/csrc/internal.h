@@ -264,6 +264,8 @@ cola_status batched_cg_impl(Ctx* c, int32_t nsys, const cola_linop* const* ops,
                             const cola_cg_opts& o, cola_cg_info* info);
 void lanczos_impl(Ctx* c, const cola_linop* op, const void* Q0, int64_t nv, int m, int prec,
                   int reorth, double* alpha, double* beta, int* m_eff);
+void householder_lanczos(Ctx* c, const cola_linop* op, const void* Q0, int64_t nv, int m,
+                         int prec, double* alpha, double* beta, int* m_eff);
 void bilinear_entry(Ctx* c, const cola_linop* op, const void* U, const void* X,
                     const double* weights, int64_t R, int prec, void* const* grads,
                     int accumulate, int depth);

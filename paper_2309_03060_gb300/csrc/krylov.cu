@@ -1249,6 +1249,8 @@ cola_status cola_lanczos(cola_ctx* ctx, const cola_linop* op, const void* Q0, in
     COLA_REQUIRE(nvec >= 1 && m >= 1, COLA_ERR_INVALID_ARG, "nvec/m");
     COLA_REQUIRE(prec >= COLA_PREC_F64 && prec <= COLA_PREC_MIXED, COLA_ERR_INVALID_ARG,
                  "precision");
+    COLA_REQUIRE(reorth >= 0 && reorth <= 2, COLA_ERR_INVALID_ARG, "reorth = %d (0, 1, 2)",
+                 reorth);
     StreamJoin j(ctx, stream);
     lanczos_impl(ctx, op, Q0, nvec, m, prec, reorth, alpha, beta, m_eff);
   });
@@ -1326,6 +1328,10 @@ static void lanczos_run(Ctx* c, cola_linop* op, const T* Q0, int64_t nv, int m, 
 void lanczos_impl(Ctx* c, const cola_linop* op, const void* Q0, int64_t nv, int m, int prec,
                   int reorth, double* alpha, double* beta, int* m_eff) {
   cola_linop* mo = const_cast<cola_linop*>(op);
+  if (reorth == 2) {  // Householder basis (Algorithm 2)
+    householder_lanczos(c, op, Q0, nv, m, prec, alpha, beta, m_eff);
+    return;
+  }
   if (prec == COLA_PREC_F64)
     lanczos_run<double>(c, mo, (const double*)Q0, nv, m, prec, reorth, alpha, beta, m_eff);
   else
@@ -1390,6 +1396,8 @@ extern "C" cola_status cola_slq_logdet(cola_ctx* ctx, const cola_linop* op, int3
     COLA_REQUIRE(nprobes >= 1 && m >= 1, COLA_ERR_INVALID_ARG, "nprobes/m");
     COLA_REQUIRE(prec >= COLA_PREC_F64 && prec <= COLA_PREC_MIXED, COLA_ERR_INVALID_ARG,
                  "precision");
+    COLA_REQUIRE(reorth >= 0 && reorth <= 2, COLA_ERR_INVALID_ARG, "reorth = %d (0, 1, 2)",
+                 reorth);
     cola::StreamJoin j(ctx, stream);
     cola::slq_impl(ctx, op, nprobes, m, seed, probes, prec, reorth, logdet, std_err, per_probe,
                    clamped);

@@ -317,6 +317,34 @@ def run_diag_estimate(cola, ctx, device, args, stream):
     return out
 
 
+def run_householder(cola, ctx, device, args, stream):
+    """SLQ log-det of the bench operator (K1 (x) K2 (x) K3 + 0.01 I, 128^3) with 8
+    Rademacher probes x 100 steps in MIXED precision, plain Lanczos against the
+    Householder basis (Algorithm 2): time, and error against the exact log-det
+    from the factor eigenvalues."""
+    import torch
+    w = wl.config2(nrhs=1)
+    op, _ = build_operator(cola, ctx, w, device)
+    exact_ld = cola.cola_kron_eig_logdet(ctx, op)
+    out = {"workload": "SLQ on kron3_rbf128 (N = 2^21), 8 probes x 100 steps, MIXED",
+           "logdet_exact": exact_ld}
+    for name, reorth in (("plain", 0), ("householder", 2)):
+        def call():
+            return cola.cola_slq_logdet(ctx, op, 8, 100, seed=3, precision=cola.PREC_MIXED,
+                                        reorth=reorth)
+        call()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ld, se, _, clamped = call()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        out[name] = {"seconds": round(e0.elapsed_time(e1) / 1e3, 4), "logdet": ld,
+                     "rel_error": abs(ld - exact_ld) / abs(exact_ld), "stderr": se,
+                     "clamped": clamped}
+    return out
+
+
 def time_queued(torch, ctx, fn, reps):
     """Device time of `reps` calls of fn, on the library's launch stream (the
     calls are issued on that stream, so no cross-stream join sits between
@@ -487,6 +515,8 @@ def run_ours(args):
         if (rank == 0 and args.bipoisson) else None
     dest = run_diag_estimate(cola, ctx, device, args, stream) \
         if (rank == 0 and args.diag_est) else None
+    hh = run_householder(cola, ctx, device, args, stream) \
+        if (rank == 0 and args.householder) else None
 
     plain = None
     if rank == 0 and args.plain:
@@ -526,6 +556,7 @@ def run_ours(args):
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
             "clocks": clk, "plain_fp32": plain, "kron_eig": eig, "batched": batched,
             "kron_precond": kprec, "bipoisson": bipo, "diag_estimate": dest,
+            "householder_slq": hh,
         }
         print(json.dumps(line))
     ctx.close()
@@ -626,6 +657,10 @@ def main():
                     help="also time the doubly stochastic diagonal estimator")
     ap.add_argument("--diag-est-only", action="store_true",
                     help="run only the doubly stochastic diagonal estimator")
+    ap.add_argument("--householder", action=argparse.BooleanOptionalAction, default=True,
+                    help="also time SLQ with the Householder Lanczos basis")
+    ap.add_argument("--householder-only", action="store_true",
+                    help="run only the Householder-basis SLQ comparison")
     ap.add_argument("--eig", action=argparse.BooleanOptionalAction, default=True,
                     help="also time the eigen-structured direct solve and exact log-det")
     ap.add_argument("--plain", action=argparse.BooleanOptionalAction, default=True,
@@ -644,6 +679,12 @@ def main():
         hbm, _, _ = peaks()
         print(json.dumps(run_batched_workload(cola, ctx, torch.device("cuda", 0), hbm,
                                               torch.cuda.current_stream())))
+    elif args.householder_only:
+        import torch
+        import paper_2309_03060_gb300 as cola
+        ctx = cola.Context(0)
+        print(json.dumps(run_householder(cola, ctx, torch.device("cuda", 0), args,
+                                         torch.cuda.current_stream())))
     elif args.diag_est_only:
         import torch
         import paper_2309_03060_gb300 as cola

@@ -333,7 +333,7 @@ def cola_lanczos(ctx: Context, op: LinOp, Q0: torch.Tensor, m: int, precision: i
 
 def cola_slq_logdet(ctx: Context, op: LinOp, nprobes: int, m: int, seed: int = 0,
                     probes: torch.Tensor | None = None, precision: int = PREC_F64,
-                    reorth: bool = False):
+                    reorth: int = 0):
     """Returns (logdet, std_err, per_probe tensor, clamped count)."""
     ld, se = C.c_double(), C.c_double()
     cl = C.c_int32()

@@ -15,11 +15,15 @@
 // ||tail|| (Golub & Van Loan 5.1.2): R_j nu_j then has -sign ||tail|| at j, so
 // H differs from Algorithm 2's by a +-1 diagonal similarity (same diagonal,
 // same eigenvalues, off-diagonal signs flipped).  Vectors and reflectors are
-// stored in the working precision; every dot product and the small W, H
-// arithmetic run in FP64.
+// stored in the working precision.  In FP64 every product runs in FP64; in
+// FP32 the long sums (the dot products with the stored reflectors and their
+// linear combinations) multiply in FP32 and accumulate runs of 16 products in
+// FP32 before adding them in FP64 (GB300's FP64 rate would otherwise bound
+// these passes), and the small W, H arithmetic stays FP64.
 #include <math.h>
 
 #include <algorithm>
+#include <type_traits>
 #include <vector>
 
 #include "internal.h"
@@ -121,7 +125,16 @@ __global__ void k_hh_multidot(int64_t N, const T* Y, int m, const T* X, int64_t 
   for (int i = warp; i < cnt; i += (int)(blockDim.x >> 5)) {
     const T* y = Y + (p * (m + 1) + i) * N;
     double s = 0.0;
-    for (int64_t k = k0 + lane; k < k1; k += 32) s += (double)y[k] * (double)x[k];
+    if constexpr (std::is_same<T, float>::value) {
+      int64_t k = k0 + lane;
+      while (k < k1) {
+        float f = 0.0f;
+        for (int t = 0; t < 16 && k < k1; ++t, k += 32) f = fmaf(y[k], x[k], f);
+        s += (double)f;
+      }
+    } else {
+      for (int64_t k = k0 + lane; k < k1; k += 32) s += (double)y[k] * (double)x[k];
+    }
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if (lane == 0) part[(p * (m + 1) + i) * nb + blockIdx.x] = s;
   }
@@ -181,13 +194,26 @@ __global__ void k_hh_lincomb(int64_t N, const T* base, int j, const T* Y, int m,
                              const double* c, T* out) {
   const int64_t p = blockIdx.y;
   __shared__ double cs[256];
+  __shared__ float cs32[256];
   const int M1 = m + 1;
-  for (int i = threadIdx.x; i < cnt; i += blockDim.x) cs[i] = c[p * M1 + i];
+  for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
+    cs[i] = c[p * M1 + i];
+    cs32[i] = (float)cs[i];
+  }
   __syncthreads();
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < N;
        k += (int64_t)gridDim.x * blockDim.x) {
     double acc = base ? (double)base[p * N + k] : (k == j ? 1.0 : 0.0);
-    for (int i = 0; i < cnt; ++i) acc += cs[i] * (double)Y[(p * M1 + i) * N + k];
+    if constexpr (std::is_same<T, float>::value) {
+      for (int i0 = 0; i0 < cnt; i0 += 16) {
+        float f = 0.0f;
+        const int i1 = min(cnt, i0 + 16);
+        for (int i = i0; i < i1; ++i) f = fmaf(cs32[i], Y[(p * M1 + i) * N + k], f);
+        acc += (double)f;
+      }
+    } else {
+      for (int i = 0; i < cnt; ++i) acc += cs[i] * (double)Y[(p * M1 + i) * N + k];
+    }
     out[p * N + k] = (T)acc;
   }
 }

@@ -159,12 +159,14 @@ __global__ void k_dot_partial(const T* a, const T* b, int64_t n, int nblk, doubl
   if (threadIdx.x == 0) part[r * nblk + blockIdx.x] = t;
 }
 
+// One block per vector: a strided serial sum per thread, then the block's
+// shuffle tree (fixed order, run-to-run deterministic).
 __global__ void k_dot_final(const double* part, int nblk, int64_t R, double* out) {
-  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= R) return;
+  const int64_t r = blockIdx.x;
   double s = 0.0;
-  for (int i = 0; i < nblk; ++i) s += part[r * nblk + i];
-  out[r] = s;
+  for (int i = threadIdx.x; i < nblk; i += blockDim.x) s += part[r * nblk + i];
+  const double t = block_sum(s);
+  if (threadIdx.x == 0) out[r] = t;
 }
 
 // ------------------------------------------------------------ elementwise
@@ -455,13 +457,13 @@ void dots(Ctx* c, const T* a, const T* b, int64_t n, int64_t R, double* partials
   const int nb = dot_blocks(n);
   k_dot_partial<T><<<dim3(nb, (unsigned)R), 256, 0, c->s>>>(a, b, n, nb, partials);
   c->count_launch();
-  k_dot_final<<<(unsigned)((R + 127) / 128), 128, 0, c->s>>>(partials, nb, R, out);
+  k_dot_final<<<(unsigned)R, 256, 0, c->s>>>(partials, nb, R, out);
   c->count_launch();
   COLA_CUDA(cudaGetLastError());
 }
 
 void dot_final(Ctx* c, const double* partials, int nblk, int64_t R, double* out) {
-  k_dot_final<<<(unsigned)((R + 127) / 128), 128, 0, c->s>>>(partials, nblk, R, out);
+  k_dot_final<<<(unsigned)R, 256, 0, c->s>>>(partials, nblk, R, out);
   c->count_launch();
   COLA_CUDA(cudaGetLastError());
 }

@@ -526,12 +526,15 @@ __global__ void k_lz_a(int64_t n, T* w, const T* qprev, const T* q, const LzStat
   if (threadIdx.x == 0) part[v * nblk + blockIdx.x] = t;
 }
 
+// One block per vector (fixed-order block reduction of the partials).
 __global__ void k_lz_alpha(LzState* st, const double* part, int nblk, int64_t nv, int j, int m,
                            double* alpha, double* a_cur) {
-  const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (v >= nv) return;
+  const int64_t v = blockIdx.x;
   double a = 0.0;
-  for (int b = 0; b < nblk; ++b) a += part[v * nblk + b];
+  for (int b = threadIdx.x; b < nblk; b += blockDim.x) a += part[v * nblk + b];
+  double unused;
+  a = block_sum2(a, &unused, 0.0);
+  if (threadIdx.x != 0) return;
   a_cur[v] = st[v].active ? a : 0.0;
   if (st[v].active) {
     alpha[v * m + j] = a;
@@ -1292,8 +1295,7 @@ static void lanczos_run(Ctx* c, cola_linop* op, const T* Q0, int64_t nv, int m, 
     apply<T>(c, op, q, w, nv, 1.0, 0.0, 1, false, prec);
     k_lz_a<T><<<rows_grid(N, nv, nblk), 256, 0, c->s>>>(N, w, qprev, q, st, nblk, part);
     c->count_launch();
-    k_lz_alpha<<<(unsigned)((nv + 127) / 128), 128, 0, c->s>>>(st, part, nblk, nv, j, m, alpha,
-                                                              a_cur);
+    k_lz_alpha<<<(unsigned)nv, 256, 0, c->s>>>(st, part, nblk, nv, j, m, alpha, a_cur);
     c->count_launch();
     k_lz_b<T><<<rows_grid(N, nv, nblk), 256, 0, c->s>>>(N, w, q, a_cur, nblk, part,
                                                          reorth ? 0 : 1);

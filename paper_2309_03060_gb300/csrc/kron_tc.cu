@@ -600,11 +600,13 @@ struct TcFsParams {
   int64_t rest, size_in, size_out, tiles_m, ntiles;
   int n_in, n_out, n_pad, kblocks, ksteps_last, xstages, nsrc;
   int img_rows;  // rows per (term, k block) of the split factor image
-  int e_mode;  // epilogue: 0 store; 1 fused shift term and p . Ap partials; 2 add beta Y
+  int e_mode;  // epilogue: 0 store; 1 fused shift term and p . Ap partials; 2 add beta Y;
+               // 3 as 1 with a per-element diagonal
+
   uint32_t x_src_bytes, e_bytes;  // e_bytes: rows staged per tile for e_mode 1 and 2
   const float* e_src;             // staged rows: p (e_mode 1) or the old Y (e_mode 2)
   float coeff, beta, e_coeff;     // e_coeff: coefficient of the shift term (e_mode 1)
-  const float* e_d;               // its diagonal value, d[0] (device)
+  const float* e_d;               // its diagonal: d[0] (e_mode 1) or d[N] (e_mode 3), device
   int* err;
   const double* pro_beta;
   float* pro_out;
@@ -691,18 +693,21 @@ __device__ __forceinline__ void fs_convert(const float* st, const float* stz, un
 
 // Stores this thread's 64 outputs (rows c < nrows of its column half, output
 // i): y = a (MODE 0), y = a + sc x with the partial sum of y x (MODE 1, x the
-// staged p), y = a + sc y_old (MODE 2, y_old staged).
+// staged p), y = a + sc y_old (MODE 2, y_old staged), y = a + sc d x with d
+// read per element from dp (MODE 3, otherwise as MODE 1).
 template <int MODE>
 __device__ __forceinline__ float fs_store(const float (&a)[64], float* yp, const float* es,
-                                          int64_t ld, int nrows, float sc) {
+                                          int64_t ld, int nrows, float sc,
+                                          const float* dp = nullptr) {
   float part = 0.0f;
 #pragma unroll
   for (int c = 0; c < 64; ++c) {
     if (c < nrows) {
       float v = a[c];
-      if (MODE == 1) {
+      if (MODE == 1 || MODE == 3) {
         const float xd = es[c * ld];
-        v = fmaf(sc, xd, v);
+        const float s = MODE == 3 ? sc * __ldg(dp + c * ld) : sc;
+        v = fmaf(s, xd, v);
         part = fmaf(v, xd, part);
       } else if (MODE == 2) {
         v = fmaf(sc, es[c * ld], v);
@@ -969,7 +974,7 @@ __global__ void __launch_bounds__(kThreadsFs, 1) k_kron_tc_fs(const __grid_const
     mbar_arrive(afac);
     pdl_wait();  // the factor copy above overlaps the previous kernel's tail
     const bool staged = p.e_mode != 0;
-    const float sc = p.e_mode == 1 ? p.e_coeff * p.e_d[0] : p.beta;
+    const float sc = p.e_mode == 1 ? p.e_coeff * p.e_d[0] : (p.e_mode == 3 ? p.e_coeff : p.beta);
     int64_t it = 0;
     for (int64_t t = blockIdx.x; t < p.ntiles; t += gridDim.x, ++it) {
       if (staged && !mbar_wait(efull, (uint32_t)(it & 1), abort_flag, p.err)) break;
@@ -1003,6 +1008,8 @@ __global__ void __launch_bounds__(kThreadsFs, 1) k_kron_tc_fs(const __grid_const
           fs_store<0>(a, yp, es, ld, nrows, 0.0f);
         else if (p.e_mode == 1)
           part = fs_store<1>(a, yp, es, ld, nrows, sc);
+        else if (p.e_mode == 3)
+          part = fs_store<3>(a, yp, es, ld, nrows, sc, p.e_d + mbase * ld + i);
         else
           fs_store<2>(a, yp, es, ld, nrows, sc);
       }
@@ -1260,11 +1267,10 @@ static size_t fs_smem(const TcFsParams& r, int tv) {
 static bool fs_plan(const TcParams& p, TcFsParams& r) {
   if (p.nchunks != 1 || p.n_pad > kTileM || p.kblocks > 2) return false;
   if (p.rest % 4 != 0 || p.size_in % 4 != 0) return false;
-  r.e_mode = p.epi_x ? 1 : (p.beta != 0.0f ? 2 : 0);
-  // a per-element diagonal in the fused shift term, or a fused shift with a
-  // nonzero beta, takes the streaming kernel
-  if (p.epi_x && (p.epi_dstride != 0 || p.beta != 0.0f)) return false;
-  r.e_src = r.e_mode == 1 ? p.epi_x : (r.e_mode == 2 ? p.Y : nullptr);
+  r.e_mode = p.epi_x ? (p.epi_dstride != 0 ? 3 : 1) : (p.beta != 0.0f ? 2 : 0);
+  // a fused shift with a nonzero beta takes the streaming kernel
+  if (p.epi_x && p.beta != 0.0f) return false;
+  r.e_src = (r.e_mode == 1 || r.e_mode == 3) ? p.epi_x : (r.e_mode == 2 ? p.Y : nullptr);
   if (r.e_src && (((uintptr_t)r.e_src & 15u) != 0 || p.size_out % 4 != 0)) return false;
   const int64_t xrows = p.batch * p.n_in;
   if (!tmap_rows(&r.tm_x, p.X, xrows, p.rest)) return false;

@@ -140,6 +140,54 @@ __global__ void k_hh_multidot(int64_t N, const T* Y, int m, const T* X, int64_t 
   }
 }
 
+// FP32 variant for N % 4 == 0: a block walks chunks of 2048 entries; every
+// thread keeps its 8 entries of x in registers and, for each stored reflector
+// i < cnt, multiplies them with 8 entries of Y[p][i] (two 16-byte loads per
+// thread, 512 coalesced bytes per warp), reduces across the warp in FP32 and
+// adds the warp's sum into an FP64 slot [i][warp] in shared memory.
+__global__ void k_hh_multidot4(int64_t N, const float* Y, int m, const float* X, int64_t xstride,
+                               int cnt, double* part) {
+  const int64_t p = blockIdx.y;
+  const int nb = gridDim.x;
+  __shared__ double wsum[256][8];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int i = lane; i < cnt; i += 32) wsum[i][warp] = 0.0;
+  __syncwarp();
+  const float* x = X + p * xstride;
+  const float* Yp = Y + p * (int64_t)(m + 1) * N;
+  const int64_t nchunks = (N + 2047) / 2048;
+  const float4 zero = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+  for (int64_t ch = blockIdx.x; ch < nchunks; ch += nb) {
+    const int64_t k = ch * 2048 + (int64_t)threadIdx.x * 8;
+    const bool in0 = k < N, in1 = k + 4 < N;
+    const float4 x0 = in0 ? *reinterpret_cast<const float4*>(x + k) : zero;
+    const float4 x1 = in1 ? *reinterpret_cast<const float4*>(x + k + 4) : zero;
+    for (int i = 0; i < cnt; ++i) {
+      const float* y = Yp + (int64_t)i * N;
+      const float4 y0 = in0 ? *reinterpret_cast<const float4*>(y + k) : zero;
+      const float4 y1 = in1 ? *reinterpret_cast<const float4*>(y + k + 4) : zero;
+      float f = x0.x * y0.x;
+      f = fmaf(x0.y, y0.y, f);
+      f = fmaf(x0.z, y0.z, f);
+      f = fmaf(x0.w, y0.w, f);
+      f = fmaf(x1.x, y1.x, f);
+      f = fmaf(x1.y, y1.y, f);
+      f = fmaf(x1.z, y1.z, f);
+      f = fmaf(x1.w, y1.w, f);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) f += __shfl_xor_sync(0xffffffffu, f, o);
+      if (lane == 0) wsum[i][warp] += (double)f;
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
+    double s = 0.0;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) s += wsum[i][w];
+    part[(p * (m + 1) + i) * nb + blockIdx.x] = s;
+  }
+}
+
 // out[p][i] = sum_b part[p][i][b] (fixed order), i < cnt.
 __global__ void k_hh_multidot_final(const double* part, int m, int nb, int cnt, double* out) {
   const int64_t p = blockIdx.x;
@@ -256,7 +304,11 @@ void hh_run(Ctx* c, const cola_linop* op, const T* Q0, int64_t nv, int m, int pr
   T* nu = (T*)ws.get("hh.nu", sizeof(T) * (size_t)nv * N);
   const int nb = (int)std::max<int64_t>(
       1, std::min<int64_t>((N + 4095) / 4096, std::max<int64_t>(1, 4 * c->num_sms / nv)));
-  double* part = (double*)ws.get("hh.part", 8 * (size_t)nv * M1 * nb);
+  // the FP32 multi-dot over 2048-entry chunks (N % 4 == 0; 16-byte rows)
+  const bool md4 = std::is_same<T, float>::value && N % 4 == 0;
+  const int nb4 = (int)std::max<int64_t>(
+      1, std::min<int64_t>((N + 2047) / 2048, std::max<int64_t>(1, 8 * c->num_sms / nv)));
+  double* part = (double*)ws.get("hh.part", 8 * (size_t)nv * M1 * std::max(nb, nb4));
   double* s = (double*)ws.get("hh.s", 8 * (size_t)nv * M1);
   double* cv = (double*)ws.get("hh.c", 8 * (size_t)nv * M1);
   double* W = (double*)ws.get("hh.W", 8 * (size_t)nv * M1 * M1);
@@ -270,7 +322,19 @@ void hh_run(Ctx* c, const cola_linop* op, const T* Q0, int64_t nv, int m, int pr
   c->count_launch();
   const double eps = (prec == COLA_PREC_F64) ? 1e-10 : 1e-6;
   const int gx = (int)std::max<int64_t>(1, std::min<int64_t>((N + 255) / 256, 2 * c->num_sms));
-  const dim3 g2(gx, (unsigned)nv), gnb(nb, (unsigned)nv);
+  const dim3 g2(gx, (unsigned)nv), gnb(nb, (unsigned)nv), gnb4(nb4, (unsigned)nv);
+  // s[p][0..cnt) = Y[p][0..cnt)^T x[p]
+  auto multidot = [&](const T* x, int64_t xstride, int cnt) {
+    if constexpr (std::is_same<T, float>::value) {
+      if (md4) {
+        k_hh_multidot4<<<gnb4, 256, 0, c->s>>>(N, Y, m, x, xstride, cnt, part);
+        k_hh_multidot_final<<<(unsigned)nv, 128, 0, c->s>>>(part, m, nb4, cnt, s);
+        return;
+      }
+    }
+    k_hh_multidot<T><<<gnb, 256, 0, c->s>>>(N, Y, m, x, xstride, cnt, part);
+    k_hh_multidot_final<<<(unsigned)nv, 128, 0, c->s>>>(part, m, nb, cnt, s);
+  };
   for (int j = 0; j <= m; ++j) {
     k_hh_tail<T><<<gnb, 256, 0, c->s>>>(N, nu, j, part);
     k_hh_reflector<T><<<pb, 128, 0, c->s>>>(N, (int)nv, nu, j, m, part, nb, eps, st, coef, H);
@@ -279,17 +343,14 @@ void hh_run(Ctx* c, const cola_linop* op, const T* Q0, int64_t nv, int m, int pr
     if (j == m) break;
     if (j >= 1) {
       // s = Y[0..j-1]^T u_j
-      k_hh_multidot<T><<<gnb, 256, 0, c->s>>>(N, Y, m, Y + (size_t)j * N, (int64_t)M1 * N, j,
-                                              part);
-      k_hh_multidot_final<<<(unsigned)nv, 128, 0, c->s>>>(part, m, nb, j, s);
+      multidot(Y + (size_t)j * N, (int64_t)M1 * N, j);
       for (int i = 0; i < 2; ++i) c->count_launch();
     }
     k_hh_w_and_c<T><<<(unsigned)nv, 128, 0, c->s>>>(N, Y, j, m, s, W, cv);
     k_hh_lincomb<T><<<g2, 256, 0, c->s>>>(N, nullptr, j, Y, m, j + 1, cv, q);
     for (int i = 0; i < 2; ++i) c->count_launch();
     apply<T>(c, op, q, w, nv, 1.0, 0.0, 1, false, prec);
-    k_hh_multidot<T><<<gnb, 256, 0, c->s>>>(N, Y, m, w, N, j + 1, part);
-    k_hh_multidot_final<<<(unsigned)nv, 128, 0, c->s>>>(part, m, nb, j + 1, s);
+    multidot(w, N, j + 1);
     k_hh_wt<<<(unsigned)nv, 128, 0, c->s>>>(W, m, j + 1, s, cv);
     k_hh_lincomb<T><<<g2, 256, 0, c->s>>>(N, w, j, Y, m, j + 1, cv, nu);
     for (int i = 0; i < 4; ++i) c->count_launch();

@@ -63,3 +63,31 @@ def test_null_arguments_are_rejected_without_a_device(lib):
     assert b"NULL" in lib.cola_last_error()
     assert lib.cola_linop_release(None) == 1
     assert lib.cola_destroy(None) == 1
+
+
+def test_new_entry_points_reject_null_without_a_device(lib):
+    """The structured, product, estimator and Householder calls check their
+    arguments before touching the device."""
+    from paper_2309_03060_gb300 import _abi
+    o = _abi.cola_cg_opts()
+    lib.cola_cg_opts_default(ctypes.byref(o))
+    assert lib.cola_product_solve(None, None, None, None, 1, ctypes.byref(o), 1, None, None) == 1
+    d = ctypes.c_double()
+    assert lib.cola_diag_estimate(None, None, 4, 0, 1, 0, None, ctypes.byref(d), None) == 1
+    assert lib.cola_arnoldi_householder(None, None, None, 1, 4, 0, None, None, None) == 1
+    assert lib.cola_kron_eig_solve(None, None, None, None, 1, 0, None) == 1
+    assert lib.cola_kron_eig_logdet(None, None, ctypes.byref(d), None) == 1
+
+
+def test_sym_eig_runs_on_the_host(lib):
+    """cola_sym_eig needs no GPU: A V = V diag(w) for a small symmetric matrix."""
+    import numpy as np
+    r = np.random.default_rng(3)
+    A = r.standard_normal((7, 7))
+    A = np.ascontiguousarray(A + A.T)
+    V = np.zeros((7, 7))
+    w = np.zeros(7)
+    st = lib.cola_sym_eig(7, A.ctypes.data, V.ctypes.data, w.ctypes.data)
+    assert st == 0
+    np.testing.assert_allclose(A @ V, V * w, atol=1e-12)
+    np.testing.assert_allclose(V.T @ V, np.eye(7), atol=1e-13)

@@ -163,11 +163,12 @@ typedef struct {
   int32_t graph_chunk;          /* iterations per CUDA-graph replay between host checks */
   int32_t jacobi;               /* 1 = Jacobi preconditioner M = Diag(A) from the Diag rules */
   int32_t x0_given;             /* 1 = X holds the initial guess, 0 = start from x = 0 */
-  int32_t kron_precond;         /* 1 = for A = c_k (K_1 (x) ... (x) K_d) + c_d Diag(d) with
-                                   symmetric dense K_k, precondition with
-                                   M = c_k (K_1 (x) ... (x) K_d) + c_d mean(d) I, applied
-                                   exactly from the factors' eigendecompositions (Table 3
-                                   Inverse / Eigs of Kron; Sec. 3.2 composition).  Needs M
+  int32_t kron_precond;         /* 1 = for A = c_k K + c_d Diag(d), K a Kronecker product
+                                   K_1 (x) ... (x) K_d or sum K_1 (+) ... (+) K_d of
+                                   symmetric dense factors, precondition with
+                                   M = c_k K + c_d mean(d) I, applied exactly from the
+                                   factors' eigendecompositions (Table 3 Inverse / Eigs of
+                                   Kron and KronSum; Sec. 3.2 composition).  Needs M
                                    positive definite; exclusive with jacobi; another operator
                                    shape is COLA_ERR_UNSUPPORTED.  Graph chunks are capped at
                                    8 iterations. */

@@ -398,6 +398,23 @@ __global__ void k_eig_inv(int64_t N, EigDims g, double ck, double shift, float* 
   }
 }
 
+// Per-block partial sums of x[0..n) (fixed order within a block).
+__global__ void k_partial_sum(int64_t n, const double* x, double* part) {
+  __shared__ double sh[32];
+  double s = 0.0;
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+       k += (int64_t)gridDim.x * blockDim.x)
+    s += x[k];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
+    part[blockIdx.x] = t;
+  }
+}
+
 // Y[r, i] *= inv[i]; grid.y runs over the right-hand sides.
 template <typename T>
 __global__ void k_scale_rows(T* Y, int64_t N, const T* inv) {
@@ -450,12 +467,18 @@ bool kron_precond_setup(Ctx* c, cola_linop* op, KronPrecond* P, int64_t R, int p
     if (f->kind != LK_DENSE || f->rows != f->cols) return false;
   const cola_linop* dg = op->kids[id];
   prepare_leaves(c, op, COLA_PREC_F64, 0);
+  // mean(d) on the device (block partials, summed here in a fixed order)
   const int64_t nd = dg->stride ? dg->rows : 1;
-  std::vector<double> d(nd);
-  COLA_CUDA(cudaMemcpyAsync(d.data(), leaf_ptr<double>(dg), 8 * nd, cudaMemcpyDeviceToHost, c->s));
+  const int nbs = (int)std::max<int64_t>(1, std::min<int64_t>((nd + 255) / 256, 1024));
+  double* dpart = (double*)c->ws.get("keig.dpart", 8 * 1024);
+  k_partial_sum<<<nbs, 256, 0, c->s>>>(nd, leaf_ptr<double>(dg), dpart);
+  c->count_launch();
+  COLA_CUDA(cudaGetLastError());
+  std::vector<double> hp(nbs);
+  COLA_CUDA(cudaMemcpyAsync(hp.data(), dpart, 8 * nbs, cudaMemcpyDeviceToHost, c->s));
   COLA_CUDA(cudaStreamSynchronize(c->s));
   double mean = 0.0;
-  for (double v : d) mean += v;
+  for (double v : hp) mean += v;
   mean /= (double)nd;
   const double shift = op->coeffs[id] * mean;
   KronShift m;

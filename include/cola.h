@@ -125,6 +125,18 @@ cola_status cola_linop_product(cola_ctx* ctx, int nterms, cola_linop* const* ter
  * adjoint solve require spd = 1 (they return COLA_ERR_INVALID_ARG otherwise). */
 cola_status cola_linop_set_spd(cola_linop* op, int spd);
 
+/* Reuse of prepared copies.  Every call converts the leaves it uses into the
+ * working precision (FP32 / FP64 copies, BF16 split images of Kronecker
+ * factors for MIXED), by default anew on each call, so that changes to the
+ * borrowed data are always seen.  cola_linop_cache_prepared(op, 1) lets the
+ * leaf op keep those copies across calls; the caller then reports a change
+ * of its data with cola_linop_touch (on the leaf, or on any node: every leaf
+ * below it counts as changed).  The Python binding sets the cache on the
+ * leaves it creates and touches a leaf whenever its tensor's version counter
+ * moved.  No counterpart in the paper. */
+cola_status cola_linop_cache_prepared(cola_linop* op, int32_t on);
+cola_status cola_linop_touch(cola_linop* op);
+
 cola_status cola_linop_shape(const cola_linop* op, int64_t* rows, int64_t* cols);
 
 /* Leaves in tree order (depth first, left to right; App. B.2 flatten).

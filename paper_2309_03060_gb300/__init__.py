@@ -92,13 +92,40 @@ def cola_create(device: int = 0) -> Context:
 
 
 class LinOp:
-    """A cola_linop handle; keeps the borrowed tensors and children alive."""
+    """A cola_linop handle; keeps the borrowed tensors and children alive.
+
+    Leaves keep their prepared copies (working-precision and split images)
+    across calls; reading ``handle`` first compares every borrowed tensor's
+    version counter with the one last seen and reports a change to the
+    library (cola_linop_touch), so in-place updates are picked up."""
 
     def __init__(self, ctx: Context, handle, keep=(), children=()):
         self.ctx = ctx
-        self.handle = handle
+        self._h = handle
         self._keep = list(keep)
+        self._seen = [t._version for t in self._keep]
         self._children = list(children)
+        if self._keep and handle:
+            check(_lib().cola_linop_cache_prepared(handle, 1))
+
+    def _sync(self):
+        for i, t in enumerate(self._keep):
+            if t._version != self._seen[i]:
+                check(_lib().cola_linop_touch(self._h))
+                self._seen = [u._version for u in self._keep]
+                break
+        for ch in self._children:
+            ch._sync()
+
+    @property
+    def handle(self):
+        if self._h:
+            self._sync()
+        return self._h
+
+    @handle.setter
+    def handle(self, h):
+        self._h = h
 
     @property
     def shape(self):
@@ -123,9 +150,9 @@ class LinOp:
         return self
 
     def release(self):
-        if self.handle:
-            check(_lib().cola_linop_release(self.handle))
-            self.handle = None
+        if self._h:
+            check(_lib().cola_linop_release(self._h))
+            self._h = None
 
     def __del__(self):
         try:

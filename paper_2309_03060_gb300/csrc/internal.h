@@ -134,8 +134,24 @@ struct cola_linop {
   std::vector<double> band_host;  // 3*n
   // converted copies of borrowed leaf data, owned here
   std::map<int, cola::Buf> derived;
+  // reuse of derived copies across calls (cola_linop_cache_prepared): a copy
+  // made while `version` was v is recorded as v + 1 and reused while the
+  // version is unchanged; cola_linop_touch bumps the version
+  bool cache_prepared = false;
+  uint64_t version = 0;
+  std::map<int, uint64_t> prep_version;
   ~cola_linop();
 };
+
+namespace cola {
+// True when derived copy `key` of leaf op may be reused as it is.
+inline bool prep_fresh(const cola_linop* op, int key) {
+  if (!op->cache_prepared || !op->derived.count(key)) return false;
+  auto it = op->prep_version.find(key);
+  return it != op->prep_version.end() && it->second == op->version + 1;
+}
+inline void prep_mark(cola_linop* op, int key) { op->prep_version[key] = op->version + 1; }
+}  // namespace cola
 
 namespace cola {
 

@@ -1184,6 +1184,7 @@ void kron_tc_prepare(Ctx* c, cola_linop* op, int split_terms) {
       const TcPlan q = make_plan(n_in, n_out, tf, 2);
       const size_t per_term = (size_t)q.kblocks * q.img_rows * kBlockK;
       const int key = 100 + tr * 10 + tf;
+      if (prep_fresh(f, key)) continue;
       auto it = f->derived.find(key);
       void* img;
       if (it == f->derived.end() || it->second.bytes < per_term * tf * 2) {
@@ -1207,6 +1208,7 @@ void kron_tc_prepare(Ctx* c, cola_linop* op, int split_terms) {
                                                       (uint16_t*)img);
       c->count_launch();
       COLA_CUDA(cudaGetLastError());
+      prep_mark(const_cast<cola_linop*>(f), key);
     }
   }
   op->derived[200] = Buf{nullptr, (size_t)tf};  // remembers the factor split terms

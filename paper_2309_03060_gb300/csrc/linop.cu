@@ -168,24 +168,32 @@ static void make_copy(Ctx* c, cola_linop* op, const void* src, int64_t rows, int
 
 void kron_tc_prepare(Ctx* c, cola_linop* op, int split_terms);  // kron_tc.cu
 
+// make_copy unless a reusable copy under `key` exists (prep_fresh).
+static void copy_once(Ctx* c, cola_linop* op, const void* src, int64_t rows, int64_t cols,
+                      int64_t ld, cola_dtype want, int key) {
+  if (prep_fresh(op, key)) return;
+  make_copy(c, op, src, rows, cols, ld, want, key);
+  prep_mark(op, key);
+}
+
 static void prepare_rec(Ctx* c, cola_linop* op, cola_dtype want, int prec, int split) {
   switch (op->kind) {
     case LK_DENSE:
       if (op->dtype != want || op->ld != op->cols)
-        make_copy(c, op, op->data, op->rows, op->cols, op->ld, want,
+        copy_once(c, op, op->data, op->rows, op->cols, op->ld, want,
                   want == COLA_F64 ? DK_F64 : DK_F32);
       break;
     case LK_DIAG:
       if (op->dtype != want)
-        make_copy(c, op, op->data, op->stride ? op->rows : 1, 1, 1, want,
+        copy_once(c, op, op->data, op->stride ? op->rows : 1, 1, 1, want,
                   want == COLA_F64 ? DK_F64 : DK_F32);
       break;
     case LK_LOWRANK:
       if (op->dtype != want) {
-        make_copy(c, op, op->data, op->rows, op->rank, op->rank, want,
+        copy_once(c, op, op->data, op->rows, op->rank, op->rank, want,
                   want == COLA_F64 ? DK_F64 : DK_F32);
         if (op->data2)
-          make_copy(c, op, op->data2, op->rows, op->rank, op->rank, want,
+          copy_once(c, op, op->data2, op->rows, op->rank, op->rank, want,
                     want == COLA_F64 ? DK_V_F64 : DK_V_F32);
       }
       break;
@@ -836,6 +844,25 @@ cola_status cola_linop_product(cola_ctx* ctx, int n, cola_linop* const* terms, c
     op->rows = terms[0]->rows;
     op->cols = terms[n - 1]->cols;
     *out = op;
+  });
+}
+
+cola_status cola_linop_cache_prepared(cola_linop* op, int32_t on) {
+  return guard([&] {
+    COLA_REQUIRE(op, COLA_ERR_INVALID_ARG, "op is NULL");
+    op->cache_prepared = on != 0;
+  });
+}
+
+static void touch_rec(cola_linop* op) {
+  ++op->version;
+  for (auto* k : op->kids) touch_rec(k);
+}
+
+cola_status cola_linop_touch(cola_linop* op) {
+  return guard([&] {
+    COLA_REQUIRE(op, COLA_ERR_INVALID_ARG, "op is NULL");
+    touch_rec(op);
   });
 }
 

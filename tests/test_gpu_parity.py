@@ -463,3 +463,27 @@ def test_poisson_lowrank_full_size(cola, ctx):
     res = krylov.true_relative_residual(oracle_tree(spec), w.B, X.double().cpu().numpy())
     assert np.all(res <= 2e-6), res
     assert max(i["iterations"] for i in info) < 200
+
+
+def test_prepared_copies_reused_and_refreshed_after_in_place_update(cola, ctx):
+    """A MIXED MVM reuses the leaves' FP32 copies and split images across calls
+    (only the 2 mode steps launch the second time), and an in-place update of
+    a factor tensor is picked up on the next call (version counter -> touch)."""
+    r = _rs(140)
+    K1 = torch.tensor(_spd(32, 141), device=DEV)
+    K2 = torch.tensor(_spd(48, 142), device=DEV)
+    op = cola.cola_linop_kron(ctx, cola.cola_linop_dense(ctx, K1), cola.cola_linop_dense(ctx, K2))
+    X = torch.tensor(r.standard_normal((2, 32 * 48)), dtype=torch.float32, device=DEV)
+    Y1 = cola.cola_matvec(ctx, op, X, cola.PREC_MIXED, split_terms=3)
+    torch.cuda.synchronize()
+    l0 = ctx.kernel_launches()
+    Y1b = cola.cola_matvec(ctx, op, X, cola.PREC_MIXED, split_terms=3)
+    torch.cuda.synchronize()
+    assert ctx.kernel_launches() - l0 == 2
+    assert torch.equal(Y1, Y1b)
+    K1.mul_(2.0)
+    Y2 = cola.cola_matvec(ctx, op, X, cola.PREC_MIXED, split_terms=3)
+    ref = oracle_tree(("kron", [("dense", K1.cpu().numpy()), ("dense", K2.cpu().numpy())]))
+    err = np.abs(Y2.double().cpu().numpy() - ref.mvm(X.double().cpu().numpy())).max()
+    assert err <= 1e-5 * np.abs(Y2.double().cpu().numpy()).max()
+    torch.testing.assert_close(Y2, 2.0 * Y1, rtol=1e-5, atol=1e-5)

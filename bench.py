@@ -339,10 +339,26 @@ def run_householder(cola, ctx, device, args, stream):
         ld, se, _, clamped = call()
         e1.record(stream)
         torch.cuda.synchronize()
-        out[name] = {"seconds": round(e0.elapsed_time(e1) / 1e3, 4), "logdet": ld,
+        t = e0.elapsed_time(e1) / 1e3
+        out[name] = {"seconds": round(t, 4), "logdet": ld,
                      "rel_error": abs(ld - exact_ld) / abs(exact_ld), "stderr": se,
                      "clamped": clamped}
+    # reflector reads per step j: Y^T u_j (j reflectors), q_j = e_j + Y c, Y^T A q_j and
+    # nu_{j+1} = A q_j + Y t (j + 1 each); 8 probes x N FP32 entries per reflector
+    refl = float(sum(j + 3 * (j + 1) for j in range(100))) * 8 * w.N * 4
+    out["householder"]["reflector_bytes"] = refl
+    out["householder"]["reflector_tbs"] = round(refl / out["householder"]["seconds"] / 1e12, 2)
     return out
+
+
+def optional_section(fn, enabled):
+    """Runs one secondary workload; None when disabled, {"error": ...} when it raised."""
+    if not enabled:
+        return None
+    try:
+        return fn()
+    except Exception as e:  # noqa: BLE001 - reported in the JSON line
+        return {"error": f"{type(e).__name__}: {e}"[:300]}
 
 
 def time_queued(torch, ctx, fn, reps):
@@ -506,17 +522,18 @@ def run_ours(args):
                "logdet_exact": ld_exact,
                "slq_rel_error": abs(ld - ld_exact) / abs(ld_exact)}
 
-    batched = run_batched_workload(cola, ctx, device, hbm, stream) if (rank == 0 and args.batched) \
-        else None
-
-    kprec = run_kron_precond(cola, ctx, device, args, stream) \
-        if (rank == 0 and args.kron_precond) else None
-    bipo = run_bipoisson(cola, ctx, device, args, stream) \
-        if (rank == 0 and args.bipoisson) else None
-    dest = run_diag_estimate(cola, ctx, device, args, stream) \
-        if (rank == 0 and args.diag_est) else None
-    hh = run_householder(cola, ctx, device, args, stream) \
-        if (rank == 0 and args.householder) else None
+    # the secondary workloads run after the timed region; a failure in one is
+    # reported in its field and does not cost the bench line
+    batched = optional_section(lambda: run_batched_workload(cola, ctx, device, hbm, stream),
+                               rank == 0 and args.batched)
+    kprec = optional_section(lambda: run_kron_precond(cola, ctx, device, args, stream),
+                             rank == 0 and args.kron_precond)
+    bipo = optional_section(lambda: run_bipoisson(cola, ctx, device, args, stream),
+                            rank == 0 and args.bipoisson)
+    dest = optional_section(lambda: run_diag_estimate(cola, ctx, device, args, stream),
+                            rank == 0 and args.diag_est)
+    hh = optional_section(lambda: run_householder(cola, ctx, device, args, stream),
+                          rank == 0 and args.householder)
 
     plain = None
     if rank == 0 and args.plain:

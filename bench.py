@@ -503,8 +503,7 @@ def run_ours(args):
     # the structured path: direct solve from the factor eigendecompositions
     # (Table 3 Inverse / Eigs rules) on the same right-hand sides, and the
     # exact log-det that the SLQ estimate is compared with
-    eig = None
-    if rank == 0 and args.eig:
+    def eig_section():
         Xe = cola.cola_kron_eig_solve(ctx, op, B, cola.PREC_F64)  # eigendecompositions here
         torch.cuda.synchronize()
         g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -517,10 +516,12 @@ def run_ours(args):
         Ae = cola.cola_matvec(ctx, op, Xe, cola.PREC_F64)
         rel_e = float(((B - Ae).norm(dim=1) / B.norm(dim=1)).max())
         ld_exact = cola.cola_kron_eig_logdet(ctx, op)
-        eig = {"solves_per_s": round(R / te, 2), "worst_rel_residual": rel_e,
-               "path": "FP64 mode products with the factor eigenvectors + eigenvalue scaling",
-               "logdet_exact": ld_exact,
-               "slq_rel_error": abs(ld - ld_exact) / abs(ld_exact)}
+        return {"solves_per_s": round(R / te, 2), "worst_rel_residual": rel_e,
+                "path": "FP64 mode products with the factor eigenvectors + eigenvalue scaling",
+                "logdet_exact": ld_exact,
+                "slq_rel_error": abs(ld - ld_exact) / abs(ld_exact)}
+
+    eig = optional_section(eig_section, rank == 0 and args.eig)
 
     # the secondary workloads run after the timed region; a failure in one is
     # reported in its field and does not cost the bench line
@@ -535,8 +536,7 @@ def run_ours(args):
     hh = optional_section(lambda: run_householder(cola, ctx, device, args, stream),
                           rank == 0 and args.householder)
 
-    plain = None
-    if rank == 0 and args.plain:
+    def plain_section():
         popts = cola.cola_cg_opts_default(precision=cola.PREC_F32, refine=1, tol=w.tol,
                                           maxiter=args.maxiter, graph_chunk=args.chunk,
                                           reliable_delta=args.delta)
@@ -545,10 +545,12 @@ def run_ours(args):
         Xp, pinfo, pst = cola.cola_cg_solve(ctx, op, B, popts)
         torch.cuda.synchronize()
         pt = time.perf_counter() - p0
-        plain = {"solves_per_s": R / pt, "iterations": max(i["iterations"] for i in pinfo),
-                 "status": pst, "worst_rel_residual": max(i["rel_residual"] for i in pinfo),
-                 "path": "FP32 SIMT mode products, same CG with FP64 replacements, 1 solve",
-                 "mixed_speedup": round(value / world / (R / pt), 3)}
+        return {"solves_per_s": R / pt, "iterations": max(i["iterations"] for i in pinfo),
+                "status": pst, "worst_rel_residual": max(i["rel_residual"] for i in pinfo),
+                "path": "FP32 SIMT mode products, same CG with FP64 replacements, 1 solve",
+                "mixed_speedup": round(value / world / (R / pt), 3)}
+
+    plain = optional_section(plain_section, rank == 0 and args.plain)
 
     if rank == 0:
         line = {

@@ -278,6 +278,21 @@ cola_status cola_product_solve(cola_ctx* ctx, const cola_linop* op, const void* 
                                int64_t nrhs, const cola_cg_opts* opts, int32_t use_structure,
                                cola_cg_info* info, cola_stream stream);
 
+/* The global tile table of one table-driven batched mode step, as
+ * cola_cg_solve_batched builds it (HOST arrays, no device work; the
+ * integer launch plan of the batched solve, no counterpart in the paper).
+ * Problem i has output width n_out[i], rest[i] rows per right-hand side and
+ * nrhs[i] right-hand sides; a tile is 128 consecutive rows of one right-hand
+ * side times one output chunk, the output width being padded to a multiple of
+ * 16 and split into the fewest equal chunks of at most chunk_cap (64 or 128)
+ * columns.  first[i] (nprob entries) receives the first global tile of
+ * problem i, tile_prob[t] (capacity entries) the problem of tile t, *total
+ * the number of tiles (written even when capacity is too small, which is
+ * COLA_ERR_INVALID_ARG). */
+cola_status cola_batch_tile_table(int32_t nprob, const int32_t* n_out, const int64_t* rest,
+                                  const int64_t* nrhs, int32_t chunk_cap, int64_t* first,
+                                  int32_t* tile_prob, int64_t capacity, int64_t* total);
+
 /* Symmetric eigendecomposition of an n x n matrix in HOST memory, the routine
  * the two calls above apply to each factor: A = V diag(w) V^T with V's
  * column j the unit eigenvector of w[j].  Householder tridiagonalisation and

@@ -1484,6 +1484,29 @@ static std::string tagged(const char* tag, const char* what) {
   return std::string(tag) + "." + what;
 }
 
+// Tiles of one problem of a batched mode step: 128-row tiles of each
+// right-hand side times the output chunks of the factor (host, integer).
+static int64_t batch_problem_tiles(int n_out, int64_t rest, int64_t R, int chunk_cap) {
+  int nchunks = 0;
+  chunk_layout(n_out, chunk_cap, &nchunks);
+  return (rest + kTileM - 1) / kTileM * R * nchunks;
+}
+
+// Global tile -> problem table of a batched launch (host, integer): problem i
+// owns tiles [first[i], first[i] + ntiles[i]) in problem order.
+static int64_t batch_tile_table(const std::vector<int64_t>& ntiles, std::vector<int64_t>& first,
+                                std::vector<int>& tile_prob) {
+  first.assign(ntiles.size(), 0);
+  tile_prob.clear();
+  int64_t tot = 0;
+  for (size_t i = 0; i < ntiles.size(); ++i) {
+    first[i] = tot;
+    tile_prob.insert(tile_prob.end(), (size_t)ntiles[i], (int)i);
+    tot += ntiles[i];
+  }
+  return tot;
+}
+
 std::vector<int64_t> kron_tc_batch_upload(Ctx* c, const std::vector<TcBatchProblem>& probs,
                                           int tf, int tv, const char* tag, int chunk_cap) {
   std::vector<TcParams> hp(probs.size());
@@ -1511,7 +1534,7 @@ std::vector<int64_t> kron_tc_batch_upload(Ctx* c, const std::vector<TcBatchProbl
     p.tiles_m = (b.rest + kTileM - 1) / kTileM;
     p.n_chunk = q.n_chunk;
     p.nchunks = q.nchunks;
-    p.ntiles = p.tiles_m * b.R * q.nchunks;
+    p.ntiles = batch_problem_tiles(n_out, b.rest, b.R, chunk_cap);
     p.n_in = n_in;
     p.n_out = n_out;
     p.n_pad = q.n_pad;
@@ -1529,11 +1552,9 @@ std::vector<int64_t> kron_tc_batch_upload(Ctx* c, const std::vector<TcBatchProbl
     p.epi_dstride = b.epi_dstride;
     p.epi_coeff = b.epi_coeff;
     p.epi_dot = b.epi_dot;
-    first[i] = tot;
     counts[i] = p.ntiles;
-    tile_prob.insert(tile_prob.end(), (size_t)p.ntiles, (int)i);
-    tot += p.ntiles;
   }
+  tot = batch_tile_table(counts, first, tile_prob);
   // fixed-capacity device tables so replays of a captured graph stay valid
   const size_t cap_p = std::max<size_t>(1, hp.size());
   void* dp = c->ws.get(tagged(tag, "probs"), sizeof(TcParams) * cap_p);
@@ -1595,3 +1616,34 @@ void kron_tc_batch_launch(Ctx* c, const char* tag, int tf, int tv, int max_n_chu
 }
 
 }  // namespace cola
+
+// ------------------------------------------------------------------ plans
+using namespace cola;
+
+extern "C" cola_status cola_batch_tile_table(int32_t nprob, const int32_t* n_out,
+                                             const int64_t* rest, const int64_t* nrhs,
+                                             int32_t chunk_cap, int64_t* first,
+                                             int32_t* tile_prob, int64_t capacity,
+                                             int64_t* total) {
+  return guard([&] {
+    COLA_REQUIRE(nprob >= 0 && (nprob == 0 || (n_out && rest && nrhs && first)) && total,
+                 COLA_ERR_INVALID_ARG, "NULL argument");
+    COLA_REQUIRE(chunk_cap == 64 || chunk_cap == 128, COLA_ERR_INVALID_ARG,
+                 "chunk_cap %d (64 or 128)", chunk_cap);
+    std::vector<int64_t> nt(nprob), f;
+    std::vector<int> tp;
+    for (int32_t i = 0; i < nprob; ++i) {
+      COLA_REQUIRE(n_out[i] >= 1 && n_out[i] <= 8192 && rest[i] >= 1 && nrhs[i] >= 1,
+                   COLA_ERR_INVALID_ARG, "problem %d: n_out %d rest %lld nrhs %lld", i,
+                   n_out[i], (long long)rest[i], (long long)nrhs[i]);
+      nt[i] = batch_problem_tiles(n_out[i], rest[i], nrhs[i], chunk_cap);
+    }
+    const int64_t tot = batch_tile_table(nt, f, tp);
+    *total = tot;
+    for (int32_t i = 0; i < nprob; ++i) first[i] = f[i];
+    COLA_REQUIRE(tot <= capacity && (tot == 0 || tile_prob), COLA_ERR_INVALID_ARG,
+                 "tile table of %lld entries, capacity %lld", (long long)tot,
+                 (long long)capacity);
+    for (int64_t t = 0; t < tot; ++t) tile_prob[t] = tp[(size_t)t];
+  });
+}

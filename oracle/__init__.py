@@ -29,6 +29,7 @@ What it computes, each by its plain definition in FP64 (numpy):
                 (App. B.2, rule 1) and the log-det gradient Tr(A^-1 dA/dtheta)
                 (rule 4), both by definition (brute force over leaf entries)
                 and in contracted form.
+* ``plan``    - the batched launch's integer tile table by its definition.
 * ``rng``     - the SplitMix64 counter generator and Rademacher probes that
                 seeded SLQ draws (its own implementation from the published
                 definition).
@@ -45,4 +46,4 @@ Arnoldi's orthogonality / Arnoldi relation / agreement with Lanczos, and the
 estimators' exactness over the full sign hypercube, variance by enumeration
 and sampled variances.  No function here is parity-unpinned.
 """
-from . import linop, krylov, exact, grad, rng, stochastic  # noqa: F401
+from . import linop, krylov, exact, grad, plan, rng, stochastic  # noqa: F401

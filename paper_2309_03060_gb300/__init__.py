@@ -22,6 +22,8 @@ __all__ = [
     "cola_linop_product", "cola_matvec", "cola_cg_solve", "cola_cg_solve_batched",
     "cola_lanczos", "cola_slq_logdet", "cola_bilinear_grad", "cola_solve_backward",
     "cola_logdet_backward", "cola_rademacher", "cola_cg_opts_default", "ColaError",
+    "cola_kron_eig_solve", "cola_kron_eig_logdet", "cola_sym_eig", "cola_product_solve",
+    "cola_diag_estimate", "cola_arnoldi_householder",
     "PREC_F64", "PREC_F32", "PREC_MIXED",
 ]
 

@@ -72,10 +72,10 @@ class _GPObjective(torch.autograd.Function):
         a = Sol[0]
         quad = 0.5 * torch.dot(y.detach().reshape(-1).to(a.dtype), a)
         prec = opts.precision
+        # the SLQ log-det and the Hutchinson gradient use the same probes Z
         ld, se, _, _ = cola_slq_logdet(cctx, op, m, slq_steps, seed=seed,
                                        probes=Z.to(torch.float64 if prec == PREC_F64 else
-                                                   torch.float32).contiguous()
-                                       if prec != PREC_F64 or Z.dtype == torch.float64 else None,
+                                                   torch.float32).contiguous(),
                                        precision=prec)
         fctx.cctx, fctx.op, fctx.opts = cctx, op, opts
         fctx.save_for_backward(Sol, Z)
@@ -105,6 +105,7 @@ class _GPObjective(torch.autograd.Function):
 def gp_objective(cctx, op, y, leaves, Z, opts=None, slq_steps=30, seed=0):
     """L = 1/2 y^T A^-1 y + 1/2 log det A with the adjoint backward above.
     ``Z`` holds the Rademacher probes (nprobes x N) shared by the trace
-    estimate of the gradient and the SLQ log-det."""
+    estimate of the gradient and the SLQ log-det (``seed`` is not used to draw
+    probes: both estimates always take Z)."""
     opts = opts or cola_cg_opts_default()
     return _GPObjective.apply(cctx, op, opts, Z, slq_steps, seed, y, *leaves)

@@ -40,20 +40,29 @@ extern "C" cola_status cola_kron_matvec_noalloc(int nfactors, const int64_t* row
     COLA_REQUIRE(rows && cols && factors && X && Y, COLA_ERR_INVALID_ARG, "NULL argument");
     COLA_REQUIRE(nrhs >= 1, COLA_ERR_INVALID_ARG, "nrhs = %lld", (long long)nrhs);
     COLA_REQUIRE(X != Y, COLA_ERR_INVALID_ARG, "X and Y must not alias");
+    // Every size below is checked before it is formed, so no product can wrap
+    // around and slip past the scratch bound.
+    constexpr int64_t kMax = INT64_MAX;
     int64_t cur = 1, maxsz = 0;
     for (int k = 0; k < nfactors; ++k) {
       COLA_REQUIRE(rows[k] >= 1 && cols[k] >= 1 && factors[k], COLA_ERR_INVALID_ARG,
                    "factor %d: bad shape or NULL data", k);
+      COLA_REQUIRE(cur <= kMax / cols[k], COLA_ERR_INVALID_ARG,
+                   "the product of the factor column counts overflows int64");
       cur *= cols[k];
     }
     // intermediate sizes of the cyclic steps (all but the last go to scratch)
     for (int k = 0; k + 1 < nfactors; ++k) {
-      cur = cur / cols[k] * rows[k];
+      const int64_t rest = cur / cols[k];
+      COLA_REQUIRE(rest <= kMax / rows[k], COLA_ERR_INVALID_ARG,
+                   "intermediate %d of the mode products overflows int64", k);
+      cur = rest * rows[k];
       maxsz = std::max(maxsz, cur);
     }
-    COLA_REQUIRE(maxsz * nrhs <= kScratchHalf, COLA_ERR_INVALID_ARG,
-                 "intermediate of %lld floats exceeds the fixed scratch of %lld floats per half",
-                 (long long)(maxsz * nrhs), (long long)kScratchHalf);
+    COLA_REQUIRE(maxsz == 0 || nrhs <= kScratchHalf / maxsz, COLA_ERR_INVALID_ARG,
+                 "nrhs = %lld times the largest intermediate (%lld floats) exceeds the fixed "
+                 "scratch of %lld floats per half",
+                 (long long)nrhs, (long long)maxsz, (long long)kScratchHalf);
 
     int dev = 0;
     COLA_CUDA(cudaGetDevice(&dev));

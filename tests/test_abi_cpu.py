@@ -91,3 +91,27 @@ def test_sym_eig_runs_on_the_host(lib):
     assert st == 0
     np.testing.assert_allclose(A @ V, V * w, atol=1e-12)
     np.testing.assert_allclose(V.T @ V, np.eye(7), atol=1e-13)
+
+
+def test_noalloc_rejects_oversize_and_overflow_without_a_device(lib):
+    """The allocation-free Kronecker MVM checks its scratch bound before it
+    looks at the device, with sizes that cannot wrap around: a huge nrhs, and
+    factor shapes whose product overflows int64, are refused with
+    COLA_ERR_INVALID_ARG and nothing is launched (the device pointers here are
+    placeholders that are never dereferenced)."""
+    fake = ctypes.c_void_p(256)
+    rows = (ctypes.c_int64 * 2)(64, 64)
+    cols = (ctypes.c_int64 * 2)(64, 64)
+    ptrs = (ctypes.c_void_p * 2)(256, 512)
+    huge = (1 << 62) // 64
+    st = lib.cola_kron_matvec_noalloc(2, rows, cols, ptrs, fake, ctypes.c_void_p(1024), huge,
+                                      None)
+    assert st == 1 and b"scratch" in lib.cola_last_error()
+    big = (ctypes.c_int64 * 3)(1 << 30, 1 << 30, 1 << 30)
+    ptrs3 = (ctypes.c_void_p * 3)(256, 512, 768)
+    st = lib.cola_kron_matvec_noalloc(3, big, big, ptrs3, fake, ctypes.c_void_p(1024), 1, None)
+    assert st == 1 and b"overflow" in lib.cola_last_error()
+    # nrhs = 2 with a 2048 x 2048 intermediate fits in 4 Mi floats only once
+    r2 = (ctypes.c_int64 * 2)(2048, 2048)
+    st = lib.cola_kron_matvec_noalloc(2, r2, r2, ptrs, fake, ctypes.c_void_p(1024), 2, None)
+    assert st == 1 and b"scratch" in lib.cola_last_error()

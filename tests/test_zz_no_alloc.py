@@ -1,12 +1,15 @@
 """The allocation-free Kronecker MVM entry point.
 
 cola_kron_matvec_noalloc is for callers that cannot let a library allocate
-device memory (a framework that owns all device memory through its own pool,
-code where an allocation would synchronise the device, callers without a
-context).  Its intermediate results live in a fixed file-scope device array;
-this test checks, through the C ABI, that two calls in a row give the same
-result as the regular cola_matvec (FP32) within the FP32 parity tolerance.
-The file sorts last so a failure here comes after every other test has run.
+device memory: a framework that owns all device memory through its own pool,
+code where an allocation would synchronise the device, and callers without a
+context.  Its intermediate results live in a fixed file-scope device array.
+This test calls it through the C ABI twice in a row and checks each result
+against the regular cola_matvec (FP32) on the same inputs, which runs the same
+SIMT mode products with the same shapes and strides, so the two must agree bit
+for bit; it also checks the result against the oracle's Kronecker MVM at the
+FP32 parity tolerance.  The file sorts last so a failure here comes after
+every other test has run.
 """
 import ctypes as C
 
@@ -14,6 +17,7 @@ import numpy as np
 import pytest
 
 import workloads as wl
+from oracle import linop as O
 
 pytestmark = pytest.mark.gpu
 
@@ -46,25 +50,37 @@ def _call(lib, factors, X, Y):
     assert st == 0, lib.cola_last_error().decode()
 
 
-def test_noalloc_matches_matvec_twice(lib_and_cola):
+def _factor_sets():
+    r = np.random.default_rng(11)
+    return {
+        "three_rect": [r.standard_normal((37, 29)), wl.rbf_factor(wl.uniform(5, (64,)), 0.2),
+                       r.standard_normal((5, 7))],
+        "one_factor": [r.standard_normal((50, 33))],
+    }
+
+
+@pytest.mark.parametrize("name", list(_factor_sets().keys()))
+def test_noalloc_matches_matvec_twice(lib_and_cola, name):
     lib, cola = lib_and_cola
     dev = torch.device("cuda", 0)
-    r = np.random.default_rng(11)
-    mats = [r.standard_normal((37, 29)), wl.rbf_factor(wl.uniform(5, (64,)), 0.2),
-            r.standard_normal((5, 7))]
+    r = np.random.default_rng(12)
+    mats = _factor_sets()[name]
     F32 = [torch.tensor(m, dtype=torch.float32, device=dev) for m in mats]
     ctx = cola.Context(0)
     op = cola.cola_linop_kron(ctx, *[cola.cola_linop_dense(ctx, f) for f in F32])
     rows, cols = op.shape
+    ref_op = O.Kron([O.Dense(f.double().cpu().numpy()) for f in F32])
     for call in range(2):
-        X = torch.tensor(r.standard_normal((3, cols)), dtype=torch.float32, device=dev)
+        Xh = r.standard_normal((3, cols))
+        X = torch.tensor(Xh, dtype=torch.float32, device=dev)
         Y = torch.full((3, rows), float("nan"), dtype=torch.float32, device=dev)
         _call(lib, F32, X, Y)
         ref = cola.cola_matvec(ctx, op, X, cola.PREC_F32)
         torch.cuda.synchronize()
-        y, yr = Y.double().cpu().numpy(), ref.double().cpu().numpy()
-        assert np.all(np.isfinite(y))
-        assert np.max(np.abs(y - yr)) <= 2e-6 * np.max(np.abs(yr)), call
+        assert torch.equal(Y, ref), (call, float((Y - ref).abs().max()))
+        y = Y.double().cpu().numpy()
+        exact = ref_op.mvm(X.double().cpu().numpy())
+        assert np.max(np.abs(y - exact)) <= 2e-6 * np.max(np.abs(exact)), call
 
 
 def test_noalloc_rejects_oversize(lib_and_cola):

@@ -313,7 +313,10 @@ cola_status cola_sym_eig(int64_t n, const double* A, double* V, double* w);
  * error).  reorth = 1 adds full reorthogonalisation (stores all q: nvec*m*N
  * elements of workspace); reorth = 2 builds the basis from Householder
  * reflectors instead (cola_arnoldi_householder; alpha_j = H_jj, beta_j =
- * |H_j+1,j|; nvec*(m+1)*N elements of workspace, m <= 255).  Asynchronous. */
+ * |H_j+1,j|; nvec*(m+1)*N elements of workspace, m <= 255).  With
+ * COLA_PREC_MIXED the Kronecker contractions use the BF16 split terms set by
+ * cola_set_split_terms (factor and vector terms), as cola_matvec does.
+ * Asynchronous. */
 cola_status cola_lanczos(cola_ctx* ctx, const cola_linop* op, const void* Q0, int64_t nvec,
                          int32_t m, int32_t precision, int32_t reorth, double* alpha,
                          double* beta, int32_t* m_eff, cola_stream stream);
@@ -358,12 +361,15 @@ cola_status cola_diag_estimate(cola_ctx* ctx, const cola_linop* op, int32_t npro
  * nprobes Rademacher probes z_v drawn on the device from `seed` (entry
  * (v, i) = sign of the top bit of SplitMix64 output v*N + i), or taken from
  * `probes` ([nprobes][N], same dtype as cola_lanczos's Q0) when it is not
- * NULL; m Lanczos steps each; per probe ||z||^2 sum_k S_0k^2 log(theta_k)
- * from the eigendecomposition of T_m computed on the device in FP64.
+ * NULL; m Lanczos steps each (cola_lanczos, MIXED with the context's split
+ * terms); per probe ||z||^2 sum_k S_0k^2 log(theta_k) from the
+ * eigendecomposition of T_m (implicit symmetric tridiagonal QR, FP64, on the
+ * host's cores: a few KB come back from the device).
  * logdet, std_err are HOST doubles (mean over probes, sample standard error);
  * per_probe (device FP64 [nprobes]) may be NULL.  A Ritz value <= 0 (low
  * precision) is clamped to the smallest positive one; the count of clamps is
- * written to *clamped (HOST, may be NULL).  Synchronous. */
+ * written to *clamped (HOST, may be NULL).  COLA_ERR_NOT_CONVERGED if the QR
+ * iteration of a tridiagonal matrix did not converge.  Synchronous. */
 cola_status cola_slq_logdet(cola_ctx* ctx, const cola_linop* op, int32_t nprobes, int32_t m,
                             uint64_t seed, const void* probes, int32_t precision,
                             int32_t reorth, double* logdet, double* std_err,
@@ -413,8 +419,9 @@ cola_status cola_rademacher(cola_ctx* ctx, uint64_t seed, int64_t offset, int64_
                             void* out, cola_dtype dtype, cola_stream stream);
 
 /* BF16 terms per Kronecker-factor entry and per vector entry (1..3) used by
- * cola_matvec with COLA_PREC_MIXED (the solvers take theirs from
- * cola_cg_opts).  Default 2 / 2. */
+ * cola_matvec, cola_lanczos, cola_slq_logdet, cola_diag_estimate and
+ * cola_arnoldi_householder with COLA_PREC_MIXED (the CG solvers take theirs
+ * from cola_cg_opts and leave this setting unchanged).  Default 2 / 2. */
 cola_status cola_set_split_terms(cola_ctx* ctx, int32_t factor_terms, int32_t vector_terms);
 
 /* Allocation-free Kronecker MVM (no counterpart in the paper; it exists for

@@ -349,9 +349,12 @@ def cola_arnoldi_householder(ctx: Context, op: LinOp, Q0: torch.Tensor, m: int,
 
 
 def cola_lanczos(ctx: Context, op: LinOp, Q0: torch.Tensor, m: int, precision: int = PREC_F64,
-                 reorth: int = 0):
-    """reorth: 0 none, 1 full reorthogonalisation, 2 Householder basis."""
+                 reorth: int = 0, split_terms=2):
+    """reorth: 0 none, 1 full reorthogonalisation, 2 Householder basis;
+    split_terms (MIXED) as in cola_matvec."""
     nv = Q0.shape[0]
+    ft, vt = (split_terms, split_terms) if isinstance(split_terms, int) else split_terms
+    check(_lib().cola_set_split_terms(ctx.handle, int(ft), int(vt)))
     alpha = torch.zeros((nv, m), dtype=torch.float64, device=Q0.device)
     beta = torch.zeros((nv, m), dtype=torch.float64, device=Q0.device)
     meff = torch.zeros(nv, dtype=torch.int32, device=Q0.device)
@@ -362,8 +365,11 @@ def cola_lanczos(ctx: Context, op: LinOp, Q0: torch.Tensor, m: int, precision: i
 
 def cola_slq_logdet(ctx: Context, op: LinOp, nprobes: int, m: int, seed: int = 0,
                     probes: torch.Tensor | None = None, precision: int = PREC_F64,
-                    reorth: int = 0):
-    """Returns (logdet, std_err, per_probe tensor, clamped count)."""
+                    reorth: int = 0, split_terms=2):
+    """Returns (logdet, std_err, per_probe tensor, clamped count); split_terms
+    (MIXED) as in cola_matvec."""
+    ft, vt = (split_terms, split_terms) if isinstance(split_terms, int) else split_terms
+    check(_lib().cola_set_split_terms(ctx.handle, int(ft), int(vt)))
     ld, se = C.c_double(), C.c_double()
     cl = C.c_int32()
     pp = torch.empty(nprobes, dtype=torch.float64, device=ctx.device)

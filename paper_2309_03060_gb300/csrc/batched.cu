@@ -391,7 +391,7 @@ cola_status batched_cg_fast(Ctx* c, int32_t nsys, const cola_linop* const* ops,
   }
   *handled = true;
   const int tf = o.split_factor_terms, tv = o.split_vector_terms;
-  c->split_vector_terms = tv;
+  VectorTermsScope vterms(c, tv);
   for (int s = 0; s < nsys; ++s) {
     cola_linop* m = const_cast<cola_linop*>(ops[s]);
     prepare_leaves(c, m, COLA_PREC_MIXED, tf);

@@ -93,6 +93,17 @@ struct Ctx {
   }
 };
 
+// Sets the context's BF16 vector split terms for the duration of one call
+// (a solve with its own option) and restores the caller's setting after it.
+struct VectorTermsScope {
+  Ctx* c;
+  int saved;
+  VectorTermsScope(Ctx* c_, int terms) : c(c_), saved(c_->split_vector_terms) {
+    c->split_vector_terms = terms;
+  }
+  ~VectorTermsScope() { c->split_vector_terms = saved; }
+};
+
 // Orders the internal stream after the caller's stream on entry and the
 // caller's stream after the internal one on exit.
 struct StreamJoin {

@@ -11,7 +11,7 @@
 //    with the breakdown test of the Arnoldi iteration (Algorithm 1).
 //  * stochastic Lanczos quadrature for log det A = Tr(log A) (App. A.2):
 //    per probe ||z||^2 sum_k S_0k^2 log(theta_k), T_m = S diag(theta) S^T,
-//    with an implicit-shift symmetric tridiagonal QR on the device.
+//    with an implicit-shift symmetric tridiagonal QR on the host (FP64).
 //  * the adjoint rules of App. B.2 (solve VJP, log-det gradient).
 #include <stdio.h>
 #include <stdlib.h>
@@ -21,6 +21,7 @@
 #include <cmath>
 #include <string>
 
+#include <thread>
 #include <type_traits>
 
 #include "internal.h"
@@ -603,27 +604,30 @@ __global__ void k_lz_meff(const LzState* st, int64_t nv, int* m_eff) {
 // --------------------------------------------------------------- quadrature
 // Implicit symmetric tridiagonal QR with Wilkinson shifts (Golub & Van Loan
 // Sec. 8.3), tracking the first row of the accumulated rotations: at
-// convergence a[k] are the Ritz values theta_k and w[k] = S_0k.
-__device__ void tridiag_eig_first_row(double* a, double* b, double* w, int n) {
+// convergence a[k] are the Ritz values theta_k and w[k] = S_0k.  Host FP64:
+// the bulge chase is a chain of dependent FP64 square roots and divisions,
+// which one GPU thread runs tens of times slower than a CPU core.  Returns
+// false when the QR sweeps did not converge within 60 n iterations.
+static bool tridiag_eig_first_row(double* a, double* b, double* w, int n) {
   for (int k = 0; k < n; ++k) w[k] = (k == 0) ? 1.0 : 0.0;
   if (n > 0) b[n - 1] = 0.0;
   const double eps = 2.220446049250313e-16;
   int q = n - 1, it = 0;
   while (q > 0 && it < 60 * n) {
-    if (fabs(b[q - 1]) <= eps * (fabs(a[q - 1]) + fabs(a[q]))) {
+    if (std::fabs(b[q - 1]) <= eps * (std::fabs(a[q - 1]) + std::fabs(a[q]))) {
       b[q - 1] = 0.0;
       --q;
       continue;
     }
     int p = q - 1;
-    while (p > 0 && fabs(b[p - 1]) > eps * (fabs(a[p - 1]) + fabs(a[p]))) --p;
+    while (p > 0 && std::fabs(b[p - 1]) > eps * (std::fabs(a[p - 1]) + std::fabs(a[p]))) --p;
     ++it;
     const double d = 0.5 * (a[q - 1] - a[q]), bb = b[q - 1];
     const double sg = d >= 0.0 ? 1.0 : -1.0;
-    const double mu = a[q] - bb * bb / (d + sg * hypot(d, bb));
+    const double mu = a[q] - bb * bb / (d + sg * std::hypot(d, bb));
     double x = a[p] - mu, z = b[p];
     for (int k = p; k < q; ++k) {
-      const double r = hypot(x, z);
+      const double r = std::hypot(x, z);
       const double c = x / r, s = z / r;
       if (k > p) b[k - 1] = r;
       const double ak = a[k], ak1 = a[k + 1], bk = b[k];
@@ -640,55 +644,37 @@ __device__ void tridiag_eig_first_row(double* a, double* b, double* w, int n) {
       }
     }
   }
+  return q <= 0;
 }
 
-constexpr int kMaxQuadM = 256;
+// Gauss quadrature of one probe: ||z||^2 sum_k S_0k^2 log(theta_k) from the
+// Lanczos coefficients (alpha_0..alpha_{n-1}, beta_0..beta_{n-2}); Ritz values
+// <= 0 are replaced by the smallest positive one and counted in *clamped.
+struct QuadResult {
+  double value = 0.0;
+  int clamped = 0;
+  bool converged = true;
+};
 
-__global__ void k_slq_quad(const double* alpha, const double* beta, const int* m_eff, int m,
-                           int nv, const double* znorm2, double* per_probe, double* summary,
-                           int* clamped) {
-  __shared__ double vals[1024];
-  __shared__ int nclamp;
-  if (threadIdx.x == 0) nclamp = 0;
-  __syncthreads();
-  for (int v = threadIdx.x; v < nv; v += blockDim.x) {
-    double a[kMaxQuadM], b[kMaxQuadM], w[kMaxQuadM];
-    const int n = m_eff[v];
-    for (int k = 0; k < n; ++k) {
-      a[k] = alpha[(int64_t)v * m + k];
-      b[k] = (k < n - 1) ? beta[(int64_t)v * m + k] : 0.0;
+static QuadResult slq_quadrature(const double* alpha, const double* beta, int n, double znorm2) {
+  std::vector<double> a(alpha, alpha + n), b(n, 0.0), w(n);
+  for (int k = 0; k + 1 < n; ++k) b[k] = beta[k];
+  QuadResult res;
+  res.converged = tridiag_eig_first_row(a.data(), b.data(), w.data(), n);
+  double tmin = 0.0;
+  for (int k = 0; k < n; ++k)
+    if (a[k] > 0.0 && (tmin == 0.0 || a[k] < tmin)) tmin = a[k];
+  double s = 0.0;
+  for (int k = 0; k < n; ++k) {
+    double th = a[k];
+    if (!(th > 0.0)) {
+      th = tmin;
+      ++res.clamped;
     }
-    tridiag_eig_first_row(a, b, w, n);
-    double tmin = 0.0;
-    for (int k = 0; k < n; ++k)
-      if (a[k] > 0.0 && (tmin == 0.0 || a[k] < tmin)) tmin = a[k];
-    double s = 0.0;
-    int cl = 0;
-    for (int k = 0; k < n; ++k) {
-      double th = a[k];
-      if (!(th > 0.0)) {
-        th = tmin;
-        ++cl;
-      }
-      s += w[k] * w[k] * log(th);
-    }
-    if (cl) atomicAdd(&nclamp, cl);
-    const double val = znorm2[v] * s;
-    per_probe[v] = val;
-    if (v < 1024) vals[v] = val;
+    s += w[k] * w[k] * std::log(th);
   }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    const int cnt = nv < 1024 ? nv : 1024;
-    double mean = 0.0;
-    for (int v = 0; v < cnt; ++v) mean += vals[v];
-    mean /= cnt;
-    double var = 0.0;
-    for (int v = 0; v < cnt; ++v) var += (vals[v] - mean) * (vals[v] - mean);
-    summary[0] = mean;
-    summary[1] = cnt > 1 ? sqrt(var / (cnt - 1) / cnt) : 0.0;
-    *clamped = nclamp;
-  }
+  res.value = znorm2 * s;
+  return res;
 }
 
 inline dim3 rows_grid(int64_t n, int64_t R, int nblk) { return dim3(nblk, (unsigned)R); }
@@ -892,7 +878,7 @@ static cola_status cg_run(Ctx* c, cola_linop* op, const void* Bin, void* Xout, i
   double* dp64 = (double*)ws.get("cg.dp64", 8 * dot_blocks(N) * R);
   const bool io64 = (prec == COLA_PREC_F64) || refine;
 
-  c->split_vector_terms = o.split_vector_terms;
+  VectorTermsScope vterms(c, o.split_vector_terms);
   prepare_leaves(c, op, prec, o.split_factor_terms);
   if (refine) prepare_leaves(c, op, COLA_PREC_F64, o.split_factor_terms);
 
@@ -1269,7 +1255,8 @@ static void lanczos_run(Ctx* c, cola_linop* op, const T* Q0, int64_t nv, int m, 
   const int64_t N = op->rows;
   const int nblk = dot_blocks(N);
   auto& ws = c->ws;
-  prepare_leaves(c, op, prec, 2);
+  // MIXED: the context's split terms (cola_set_split_terms), as cola_matvec
+  prepare_leaves(c, op, prec, c->split_factor_terms);
   T* bufs[3];
   bufs[0] = (T*)ws.get("lz.0", sizeof(T) * N * nv);
   bufs[1] = (T*)ws.get("lz.1", sizeof(T) * N * nv);
@@ -1348,8 +1335,6 @@ namespace cola {
 static void slq_impl(Ctx* c, const cola_linop* op, int nprobes, int m, uint64_t seed,
                      const void* probes, int prec, int reorth, double* logdet, double* std_err,
                      double* per_probe, int* clamped) {
-  COLA_REQUIRE(m <= kMaxQuadM, COLA_ERR_UNSUPPORTED, "SLQ: m = %d > %d", m, kMaxQuadM);
-  COLA_REQUIRE(nprobes <= 1024, COLA_ERR_UNSUPPORTED, "SLQ: nprobes = %d > 1024", nprobes);
   const int64_t N = op->rows;
   const bool f64 = prec == COLA_PREC_F64;
   const size_t es = f64 ? 8 : 4;
@@ -1363,26 +1348,57 @@ static void slq_impl(Ctx* c, const cola_linop* op, int nprobes, int m, uint64_t 
   double* beta = (double*)ws.get("slq.beta", 8 * (size_t)nprobes * m);
   int* meff = (int*)ws.get("slq.meff", 4 * nprobes);
   double* zn = (double*)ws.get("slq.zn", 8 * nprobes);
-  double* pp = per_probe ? per_probe : (double*)ws.get("slq.pp", 8 * nprobes);
-  double* summ = (double*)ws.get("slq.sum", 16);
-  int* ncl = (int*)ws.get("slq.ncl", 4);
   double* part = (double*)ws.get("slq.part", 8 * (size_t)dot_blocks(N) * nprobes);
   lanczos_impl(c, op, Z, nprobes, m, prec, reorth, alpha, beta, meff);
   if (f64)
     dots<double>(c, (const double*)Z, (const double*)Z, N, nprobes, part, zn);
   else
     dots<float>(c, (const float*)Z, (const float*)Z, N, nprobes, part, zn);
-  k_slq_quad<<<1, 128, 0, c->s>>>(alpha, beta, meff, m, nprobes, zn, pp, summ, ncl);
-  c->count_launch();
-  COLA_CUDA(cudaGetLastError());
-  double hs[2];
-  int hc = 0;
-  COLA_CUDA(cudaMemcpyAsync(hs, summ, 16, cudaMemcpyDeviceToHost, c->s));
-  COLA_CUDA(cudaMemcpyAsync(&hc, ncl, 4, cudaMemcpyDeviceToHost, c->s));
+  // the tridiagonal matrices T_m (a few KB) come back to the host, where the
+  // quadrature runs in FP64, probes spread over the host's cores
+  std::vector<double> ha((size_t)nprobes * m), hb((size_t)nprobes * m), hz(nprobes);
+  std::vector<int> hm(nprobes);
+  COLA_CUDA(cudaMemcpyAsync(ha.data(), alpha, 8 * ha.size(), cudaMemcpyDeviceToHost, c->s));
+  COLA_CUDA(cudaMemcpyAsync(hb.data(), beta, 8 * hb.size(), cudaMemcpyDeviceToHost, c->s));
+  COLA_CUDA(cudaMemcpyAsync(hz.data(), zn, 8 * hz.size(), cudaMemcpyDeviceToHost, c->s));
+  COLA_CUDA(cudaMemcpyAsync(hm.data(), meff, 4 * hm.size(), cudaMemcpyDeviceToHost, c->s));
   COLA_CUDA(cudaStreamSynchronize(c->s));
-  if (logdet) *logdet = hs[0];
-  if (std_err) *std_err = hs[1];
-  if (clamped) *clamped = hc;
+  std::vector<QuadResult> qr(nprobes);
+  const int nthreads = (int)std::max<int64_t>(
+      1, std::min<int64_t>(nprobes, std::max(1u, std::thread::hardware_concurrency())));
+  auto work = [&](int t0) {
+    for (int v = t0; v < nprobes; v += nthreads)
+      qr[v] = slq_quadrature(ha.data() + (size_t)v * m, hb.data() + (size_t)v * m, hm[v], hz[v]);
+  };
+  if (nthreads == 1) {
+    work(0);
+  } else {
+    std::vector<std::thread> pool;
+    for (int t = 0; t < nthreads; ++t) pool.emplace_back(work, t);
+    for (auto& th : pool) th.join();
+  }
+  std::vector<double> vals(nprobes);
+  int ncl = 0;
+  for (int v = 0; v < nprobes; ++v) {
+    COLA_REQUIRE(qr[v].converged, COLA_ERR_NOT_CONVERGED,
+                 "SLQ: the QR iteration of probe %d's tridiagonal matrix did not converge", v);
+    vals[v] = qr[v].value;
+    ncl += qr[v].clamped;
+  }
+  // mean and sample standard error over the probes, summed in probe order
+  double mean = 0.0;
+  for (int v = 0; v < nprobes; ++v) mean += vals[v];
+  mean /= nprobes;
+  double var = 0.0;
+  for (int v = 0; v < nprobes; ++v) var += (vals[v] - mean) * (vals[v] - mean);
+  if (per_probe) {
+    COLA_CUDA(cudaMemcpyAsync(per_probe, vals.data(), 8 * vals.size(), cudaMemcpyHostToDevice,
+                              c->s));
+    COLA_CUDA(cudaStreamSynchronize(c->s));
+  }
+  if (logdet) *logdet = mean;
+  if (std_err) *std_err = nprobes > 1 ? std::sqrt(var / (nprobes - 1) / nprobes) : 0.0;
+  if (clamped) *clamped = ncl;
 }
 
 }  // namespace cola

@@ -46,7 +46,8 @@ typedef enum {
   COLA_ERR_INVALID_ARG = 1,
   COLA_ERR_SHAPE = 2,
   COLA_ERR_DTYPE = 3,
-  COLA_ERR_BREAKDOWN = 4,      /* CG: p^T A p <= 0 or NaN (operator not SPD in working precision) */
+  COLA_ERR_BREAKDOWN = 4,      /* CG: p^T A p <= 0 or NaN (operator not SPD in working
+                                  precision), or a right-hand side with a NaN / Inf entry */
   COLA_ERR_NOT_CONVERGED = 5,  /* tolerance not reached in maxiter; results still written */
   COLA_ERR_TIMEOUT = 6,
   COLA_ERR_CUDA = 7,
@@ -445,6 +446,18 @@ cola_status cola_set_split_terms(cola_ctx* ctx, int32_t factor_terms, int32_t ve
 cola_status cola_kron_matvec_noalloc(int nfactors, const int64_t* rows, const int64_t* cols,
                                      const float* const* factors, const float* X, float* Y,
                                      int64_t nrhs, cola_stream stream);
+
+/* Test hook of the failure path (no counterpart in the paper).  The next
+ * tensor-core Kronecker MVM launch of this context that is not being captured
+ * into a CUDA graph has its MMA role first wait on a barrier that nothing
+ * completes, with a limit of wait_ns nanoseconds (1 .. 2e9; 0 disarms) in
+ * place of the usual 2 s.  When the limit runs out the launch takes the
+ * ordinary time-out path: every role of every CTA stops, each CTA waits for
+ * its own bulk copies and MMAs, frees its tensor memory and exits, and the
+ * device error flag reports COLA_ERR_TIMEOUT to the host (for cola_matvec on
+ * a later call of the context, as documented there).  Nothing faults or
+ * hangs; the context stays usable.  Used by the tests to exercise the path. */
+cola_status cola_test_stall_next_launch(cola_ctx* ctx, int64_t wait_ns);
 
 /* Number of kernels this library launched (or recorded into replayed graphs,
  * counted per replay) since the context was created. */

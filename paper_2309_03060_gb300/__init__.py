@@ -76,6 +76,10 @@ class Context:
         check(_lib().cola_kernel_launches(self.handle, C.byref(n)))
         return n.value
 
+    def test_stall_next_launch(self, wait_ns: int) -> None:
+        """Arms cola_test_stall_next_launch (time-out path test hook)."""
+        check(_lib().cola_test_stall_next_launch(self.handle, int(wait_ns)))
+
     def stream(self) -> "torch.cuda.ExternalStream":
         """The library's launch stream (for timing kernels with events)."""
         s = C.c_void_p()

@@ -81,6 +81,7 @@ SIGNATURES = {
     "cola_batch_tile_table": (I32, [I32, P, P, P, I32, P, P, I64, P]),
     "cola_sym_eig": (I32, [I64, P, P, P]),
     "cola_set_split_terms": (I32, [P, I32, I32]),
+    "cola_test_stall_next_launch": (I32, [P, I64]),
     "cola_kron_matvec_noalloc": (I32, [C.c_int, C.POINTER(I64), C.POINTER(I64), PP, P, P, I64, P]),
 }
 

@@ -84,6 +84,7 @@ struct Ctx {
   int* tc_err_host = nullptr;  // pinned copy of the tensor-core timeout flag
   cudaEvent_t tc_err_ev = nullptr;
   bool tc_err_pending = false;  // a copy of the flag is in flight
+  int64_t tc_stall_ns = 0;      // armed by cola_test_stall_next_launch, consumed once
   void* host_pinned(size_t bytes);
   void count_launch() {
     if (capturing)

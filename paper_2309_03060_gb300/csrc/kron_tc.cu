@@ -56,6 +56,8 @@ struct TcParams {
   uint32_t stage_bytes, a_term_bytes, b_term_bytes, tmem_cols;
   float coeff, beta;
   int* err;
+  uint64_t stall_ns;  // > 0: the MMA role first waits on a barrier that nothing
+                      // completes, with this limit (test of the time-out path)
   // optional prologue (first mode step of a CG iteration): the input is
   // p = z + beta_r * p_old, computed here and written back to X in place
   const float* pro_z;
@@ -118,16 +120,18 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   return ok != 0;
 }
 
-// Bounded wait: false when the phase did not complete within kWaitNs or
-// another role of the CTA already gave up.
+// Bounded wait: false when the phase did not complete within limit_ns (the
+// role then raises the CTA's abort flag and the device error flag) or another
+// role of the CTA already gave up.
 __device__ __noinline__ bool mbar_wait_slow(uint64_t* bar, uint32_t parity,
-                                            volatile int* abort_flag, int* err) {
+                                            volatile int* abort_flag, int* err,
+                                            uint64_t limit_ns) {
   const uint64_t t0 = now_ns();
   for (uint32_t i = 1;; ++i) {
     if (mbar_try_wait(bar, parity)) return true;
     if ((i & 63) == 0) {
       if (*abort_flag) return false;
-      if (now_ns() - t0 > kWaitNs) {
+      if (now_ns() - t0 > limit_ns) {
         *abort_flag = 1;
         atomicExch(err, COLA_ERR_TIMEOUT);
         return false;
@@ -139,7 +143,22 @@ __device__ __noinline__ bool mbar_wait_slow(uint64_t* bar, uint32_t parity,
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
                                           int* err) {
   if (mbar_try_wait(bar, parity)) return true;
-  return mbar_wait_slow(bar, parity, abort_flag, err);
+  return mbar_wait_slow(bar, parity, abort_flag, err, kWaitNs);
+}
+
+// Wait for this CTA's own bulk copies or MMAs to complete before it frees
+// tensor memory and exits: it does not give up when another role raised the
+// abort flag (the copies are in flight whatever the other roles do), only
+// after its own limit of kWaitNs.
+__device__ __noinline__ bool mbar_wait_own(uint64_t* bar, uint32_t parity, int* err) {
+  const uint64_t t0 = now_ns();
+  for (uint32_t i = 1;; ++i) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((i & 63) == 0 && now_ns() - t0 > kWaitNs) {
+      atomicExch(err, COLA_ERR_TIMEOUT);
+      return false;
+    }
+  }
 }
 
 __device__ __forceinline__ void fence_proxy_async() {
@@ -261,7 +280,9 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_kron_tc(Src src, TcParams K) 
   uint64_t* acc_full = bars + 2 * K.stages;
   uint64_t* acc_empty = acc_full + 2;
   uint64_t* drain = acc_empty + 2;
-  uint32_t* tmem_slot = (uint32_t*)(drain + 1);
+  uint64_t* cbar = drain + 1;        // [stages] factor copies of each stage
+  uint64_t* stall = cbar + K.stages;  // never completed (time-out test)
+  uint32_t* tmem_slot = (uint32_t*)(stall + 1);
   volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -269,12 +290,14 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_kron_tc(Src src, TcParams K) 
     for (int s = 0; s < K.stages; ++s) {
       mbar_init(&full[s], kProducerThreads);
       mbar_init(&empty[s], 1);
+      mbar_init(&cbar[s], 1);
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&acc_full[b], 1);
       mbar_init(&acc_empty[b], 128);
     }
     mbar_init(drain, 1);
+    mbar_init(stall, 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -294,8 +317,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_kron_tc(Src src, TcParams K) 
     // ------------------------------------------------------------ producers
     int s = 0;
     uint32_t ph = 0;
-    int last_s = -1;
-    uint32_t last_ph = 0;
+    uint32_t issued = 0, issued_ph = 0;  // bit s: a copy went to stage s / its parity
     bool ok = true;
     const int64_t ntiles = src.count();
     for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
@@ -318,14 +340,16 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_kron_tc(Src src, TcParams K) 
         }
         unsigned char* st = base + (size_t)s * K.stage_bytes;
         if (tid == 0) {
-          mbar_expect_tx(&full[s], p.b_term_bytes * K.tf);
+          // the factor block lands on its own barrier, so its completion can
+          // be awaited whatever the other producers do
+          mbar_arrive_expect_tx(&cbar[s], p.b_term_bytes * K.tf);
           for (int ti = 0; ti < K.tf; ++ti)
             bulk_g2s(st + K.tv * K.a_term_bytes + ti * p.b_term_bytes,
                      p.Bimg + (((size_t)ti * p.kblocks + kb) * (size_t)p.img_rows +
                                (size_t)nc * p.n_chunk) * kBlockK,
-                     p.b_term_bytes, &full[s]);
-          last_s = s;
-          last_ph = ph;
+                     p.b_term_bytes, &cbar[s]);
+          issued |= 1u << s;
+          issued_ph = (issued_ph & ~(1u << s)) | (ph << s);
         }
         const int k0 = kb * kBlockK;
         float v[kBlockK];
@@ -383,8 +407,12 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_kron_tc(Src src, TcParams K) 
         }
       }
     }
-    // make sure no bulk copy is still landing in this CTA's shared memory
-    if (tid == 0 && last_s >= 0) mbar_wait(&full[last_s], last_ph, abort_flag, K.err);
+    // no bulk copy may still be landing in this CTA's shared memory when it
+    // exits: earlier copies into a stage were consumed before the stage was
+    // refilled, so only the latest copy of each stage can be in flight
+    if (tid == 0)
+      for (int st = 0; st < K.stages; ++st)
+        if (issued & (1u << st)) mbar_wait_own(&cbar[st], (issued_ph >> st) & 1u, K.err);
   } else if (warp == 8) {
     // ----------------------------------------------------------------- MMA
     if (lane == 0) {
@@ -393,6 +421,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_kron_tc(Src src, TcParams K) 
       uint32_t ph = 0;
       int64_t it = 0;
       bool ok = true;
+      if (K.stall_ns) ok = mbar_wait_slow(stall, 0, abort_flag, K.err, K.stall_ns);
       const int64_t ntiles = src.count();
       for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++it) {
         int64_t lt;
@@ -411,7 +440,8 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_kron_tc(Src src, TcParams K) 
         const uint32_t d_small = d_big + (uint32_t)p.n_chunk;
         uint32_t acc_big = 0, acc_small = 0;
         for (int kb = 0; kb < p.kblocks; ++kb) {
-          if (!mbar_wait(&full[s], ph, abort_flag, K.err)) {
+          if (!mbar_wait(&full[s], ph, abort_flag, K.err) ||
+              !mbar_wait(&cbar[s], ph, abort_flag, K.err)) {
             ok = false;
             break;
           }
@@ -445,7 +475,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_kron_tc(Src src, TcParams K) 
       }
       // drain: all MMAs issued by this thread have completed
       mma_commit(drain);
-      mbar_wait(drain, 0, abort_flag, K.err);
+      mbar_wait_own(drain, 0, K.err);
     }
     __syncwarp();
   } else {
@@ -608,6 +638,7 @@ struct TcFsParams {
   float coeff, beta, e_coeff;     // e_coeff: coefficient of the shift term (e_mode 1)
   const float* e_d;               // its diagonal: d[0] (e_mode 1) or d[N] (e_mode 3), device
   int* err;
+  uint64_t stall_ns;              // > 0: time-out test (see TcParams)
   const double* pro_beta;
   float* pro_out;
   double* epi_dot;
@@ -739,7 +770,8 @@ __global__ void __launch_bounds__(kThreadsFs, 1) k_kron_tc_fs(const __grid_const
   uint64_t* drain = dempty + 1;
   uint64_t* efull = drain + 1;
   uint64_t* eempty = efull + 1;
-  uint32_t* tmem_slot = (uint32_t*)(eempty + 1);
+  uint64_t* stall = eempty + 1;  // never completed (time-out test)
+  uint32_t* tmem_slot = (uint32_t*)(stall + 1);
   volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -758,6 +790,7 @@ __global__ void __launch_bounds__(kThreadsFs, 1) k_kron_tc_fs(const __grid_const
     mbar_init(drain, 1);
     mbar_init(efull, 1);
     mbar_init(eempty, kFsEpiThreads);
+    mbar_init(stall, 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -779,38 +812,39 @@ __global__ void __launch_bounds__(kThreadsFs, 1) k_kron_tc_fs(const __grid_const
   if (warp == kFsLoaderWarp) {
     // ---------------------------------------------------------------- loader
     pdl_wait();
-    bool ok = true;
-    int s = 0;
-    uint32_t ph = 0;
-    int last_s = -1;
-    uint32_t last_ph = 0;
-    for (int64_t t = blockIdx.x; t < p.ntiles && ok; t += gridDim.x) {
-      const int64_t r = t / p.tiles_m, m0 = (t % p.tiles_m) * kTileM;
-      for (int kb = 0; kb < p.kblocks; ++kb) {
-        if (!mbar_wait(&xempty[s], ph ^ 1u, abort_flag, p.err)) {
-          ok = false;
-          break;
-        }
-        // rows past n_in or columns past rest arrive as zeros or as another
-        // right-hand side's rows; the converters mask both
-        if (lane == 0) {
+    if (lane == 0) {  // one thread waits, issues and tracks every copy
+      bool ok = true;
+      int s = 0;
+      uint32_t ph = 0;
+      uint32_t issued = 0, issued_ph = 0;  // bit s: a copy went to stage s / its parity
+      for (int64_t t = blockIdx.x; t < p.ntiles && ok; t += gridDim.x) {
+        const int64_t r = t / p.tiles_m, m0 = (t % p.tiles_m) * kTileM;
+        for (int kb = 0; kb < p.kblocks; ++kb) {
+          if (!mbar_wait(&xempty[s], ph ^ 1u, abort_flag, p.err)) {
+            ok = false;
+            break;
+          }
+          // rows past n_in or columns past rest arrive as zeros or as another
+          // right-hand side's rows; the converters mask both
           unsigned char* st = xsm + (size_t)s * p.nsrc * p.x_src_bytes;
           const int y = (int)(r * p.n_in) + kb * kBlockK;
           mbar_arrive_expect_tx(&xfull[s], p.x_src_bytes * (uint32_t)p.nsrc);
           tma_load_2d(st, &p.tm_x, (int)m0, y, &xfull[s]);
           if (p.nsrc > 1) tma_load_2d(st + p.x_src_bytes, &p.tm_z, (int)m0, y, &xfull[s]);
-        }
-        __syncwarp();
-        last_s = s;
-        last_ph = ph;
-        if (++s == p.xstages) {
-          s = 0;
-          ph ^= 1u;
+          issued |= 1u << s;
+          issued_ph = (issued_ph & ~(1u << s)) | (ph << s);
+          if (++s == p.xstages) {
+            s = 0;
+            ph ^= 1u;
+          }
         }
       }
+      // no bulk copy may still be landing when the CTA exits: earlier copies
+      // into a stage were consumed before the stage was refilled, so only the
+      // latest copy of each stage can be in flight
+      for (int st = 0; st < p.xstages; ++st)
+        if (issued & (1u << st)) mbar_wait_own(&xfull[st], (issued_ph >> st) & 1u, p.err);
     }
-    // no bulk copy may still be landing when the CTA exits
-    if (lane == 0 && last_s >= 0) mbar_wait(&xfull[last_s], last_ph, abort_flag, p.err);
     __syncwarp();
   } else if (warp == kFsEpiLoaderWarp) {
     // ------------------------------------------------ rows for the epilogue
@@ -825,8 +859,9 @@ __global__ void __launch_bounds__(kThreadsFs, 1) k_kron_tc_fs(const __grid_const
         mbar_arrive_expect_tx(efull, bytes);
         bulk_g2s(esm, p.e_src + r * p.size_out + m0 * p.n_out, bytes, efull);
       }
-      // the last copy has landed before the CTA exits
-      if (it > 0) mbar_wait(efull, (uint32_t)((it - 1) & 1), abort_flag, p.err);
+      // the last copy (the only one that can be in flight: each waited for
+      // the epilogue to free the buffer) has landed before the CTA exits
+      if (it > 0) mbar_wait_own(efull, (uint32_t)((it - 1) & 1), p.err);
     }
     __syncwarp();
   } else if (warp < kFsConvWarps) {
@@ -887,6 +922,7 @@ __global__ void __launch_bounds__(kThreadsFs, 1) k_kron_tc_fs(const __grid_const
     if (lane == 0) {
       constexpr uint32_t idesc = idesc_bf16(kTileM, kTileM);  // M = outputs, N = rows
       bool ok = mbar_wait(afac, 0, abort_flag, p.err);
+      if (ok && p.stall_ns) ok = mbar_wait_slow(stall, 0, abort_flag, p.err, p.stall_ns);
       tc_fence_after();
       const uint32_t bbase = smem_u32(bsm);
       int sb = 0;
@@ -932,7 +968,7 @@ __global__ void __launch_bounds__(kThreadsFs, 1) k_kron_tc_fs(const __grid_const
         mma_commit(dfull);
       }
       mma_commit(drain);
-      mbar_wait(drain, 0, abort_flag, p.err);
+      mbar_wait_own(drain, 0, p.err);
     }
     __syncwarp();
   } else {
@@ -1301,6 +1337,7 @@ static bool fs_plan(const TcParams& p, TcFsParams& r) {
   r.e_coeff = p.epi_coeff;
   r.e_d = p.epi_d;
   r.err = p.err;
+  r.stall_ns = p.stall_ns;
   r.pro_beta = p.pro_beta;
   r.pro_out = p.pro_out;
   r.epi_dot = p.epi_dot;
@@ -1386,6 +1423,10 @@ static int64_t kron_tc_run(Ctx* c, const cola_linop* op, const float* X, float* 
     p.coeff = (float)(last ? coeff : 1.0);
     p.beta = (float)(last ? beta : 0.0);
     p.err = err;
+    if (k == 0 && c->tc_stall_ns > 0 && !c->capturing) {
+      p.stall_ns = (uint64_t)c->tc_stall_ns;  // armed once by cola_test_stall_next_launch
+      c->tc_stall_ns = 0;
+    }
     if (k == 0) {
       p.pro_z = fu.pro_z;
       p.pro_beta = fu.pro_beta;

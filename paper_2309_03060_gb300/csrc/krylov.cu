@@ -412,6 +412,11 @@ __global__ void k_cg_restate(CgState* st, const double* part_rz, const double* p
     s.tol2 = tol * tol * bb[r];
     s.active = 1;
     s.alpha = s.beta = 0.0;
+    // a right-hand side with a NaN or Inf entry cannot be solved
+    if (!isfinite(bb[r])) {
+      s.status = COLA_ERR_BREAKDOWN;
+      s.active = 0;
+    }
   } else if (s.active) {
     s.updates += 1;
     if (s.paused || rr > kRestartGap2 * s.rr) {

@@ -933,6 +933,15 @@ cola_status cola_set_split_terms(cola_ctx* ctx, int32_t factor_terms, int32_t ve
   });
 }
 
+cola_status cola_test_stall_next_launch(cola_ctx* ctx, int64_t wait_ns) {
+  return guard([&] {
+    COLA_REQUIRE(ctx, COLA_ERR_INVALID_ARG, "ctx is NULL");
+    COLA_REQUIRE(wait_ns >= 0 && wait_ns <= 2000000000LL, COLA_ERR_INVALID_ARG,
+                 "wait_ns = %lld (0 .. 2e9)", (long long)wait_ns);
+    ctx->tc_stall_ns = wait_ns;
+  });
+}
+
 cola_status cola_kernel_launches(const cola_ctx* ctx, int64_t* count) {
   return guard([&] {
     COLA_REQUIRE(ctx && count, COLA_ERR_INVALID_ARG, "NULL argument");

@@ -256,6 +256,24 @@ cola_status cola_kron_eig_solve(cola_ctx* ctx, const cola_linop* op, const void*
 cola_status cola_kron_eig_logdet(cola_ctx* ctx, const cola_linop* op, double* logdet,
                                  cola_stream stream);
 
+/* Eigendecomposition of A = c_k (K_1 (x) ... (x) K_d) [+ c_d s I] (or of a
+ * Kronecker sum of the K_k) in Kronecker form, without forming A (Table 3
+ * Eigs rule; App. A.1.2): A = Q diag(lambda) Q^T with Q = V_1 (x) ... (x) V_d,
+ * K_k = V_k diag(w_k) V_k^T, and lambda at flat index (i_1..i_d) equal to
+ * c_k prod_k w_k[i_k] + c_d s (c_k sum_k w_k[i_k] + c_d s for a Kronecker sum),
+ * so column (i_1..i_d) of Q is the Kronecker product of the columns i_k of
+ * the V_k.  Same operator class and factor decompositions (cached, FP64) as
+ * cola_kron_eig_solve.  Outputs, each a DEVICE FP64 array or NULL (at least
+ * one given): factor_evals, the w_k concatenated (sum_k n_k entries);
+ * factor_evecs, the V_k concatenated (sum_k n_k^2 entries, each n_k x n_k
+ * row-major with column j the unit eigenvector of w_k[j]); evals, the N
+ * eigenvalues lambda of A in flat index order.  COLA_ERR_UNSUPPORTED for
+ * another operator shape, COLA_ERR_INVALID_ARG for a non-symmetric factor,
+ * COLA_ERR_NOT_CONVERGED if a factor's QR iteration did not converge.
+ * Synchronous on first use of a factor, asynchronous on stream afterwards. */
+cola_status cola_kron_eigs(cola_ctx* ctx, const cola_linop* op, double* factor_evals,
+                           double* factor_evecs, double* evals, cola_stream stream);
+
 /* Solve A X = B for A = A_1 A_2 ... A_m (cola_linop_product; nested products
  * are flattened) by splitting the product: X = A_m^-1 ( ... (A_1^-1 B)), one
  * factor at a time (Sec. 3.2: the inverse of a product is the product of the
@@ -299,7 +317,8 @@ cola_status cola_batch_tile_table(int32_t nprob, const int32_t* n_out, const int
  * column j the unit eigenvector of w[j].  Householder tridiagonalisation and
  * implicit symmetric QR with Wilkinson shifts, FP64 (Golub & Van Loan 8.3).
  * A (row-major, symmetric) is read only; V (n x n row-major) and w (n) are
- * written.  Needs no GPU. */
+ * written.  COLA_ERR_NOT_CONVERGED if the QR sweeps did not converge within
+ * 60 n iterations.  Needs no GPU. */
 cola_status cola_sym_eig(int64_t n, const double* A, double* V, double* w);
 
 /* --------------------------------------------------------- Lanczos / SLQ */

@@ -276,6 +276,28 @@ def cola_kron_eig_logdet(ctx: Context, op: LinOp) -> float:
     return v.value
 
 
+def cola_kron_eigs(ctx: Context, op: LinOp, want_evals: bool = True):
+    """Kronecker-form eigendecomposition: (factor eigenvalues [w_1, ..],
+    factor eigenvector matrices [V_1, ..] (columns = eigenvectors), and the N
+    eigenvalues of A in flat index order, or None when want_evals is False)."""
+    # the factors are the operator's dense leaves (a scalar shift is the other)
+    sizes = [r for k, r, _ in op.leaves() if k == 0]
+    dev = ctx.device
+    w = torch.empty(sum(sizes), dtype=torch.float64, device=dev)
+    V = torch.empty(sum(n * n for n in sizes), dtype=torch.float64, device=dev)
+    N = op.shape[0]
+    ev = torch.empty(N, dtype=torch.float64, device=dev) if want_evals else None
+    check(_lib().cola_kron_eigs(ctx.handle, op.handle, _ptr(w), _ptr(V),
+                                _ptr(ev) if ev is not None else None, _stream()))
+    ws, Vs, ow, ov = [], [], 0, 0
+    for n in sizes:
+        ws.append(w[ow:ow + n])
+        Vs.append(V[ov:ov + n * n].reshape(n, n))
+        ow += n
+        ov += n * n
+    return ws, Vs, ev
+
+
 def cola_sym_eig(A):
     """(w, V) with A = V diag(w) V^T for a symmetric matrix in host memory
     (a numpy array); the routine applied to every Kronecker factor."""

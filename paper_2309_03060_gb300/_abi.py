@@ -82,6 +82,7 @@ SIGNATURES = {
     "cola_sym_eig": (I32, [I64, P, P, P]),
     "cola_set_split_terms": (I32, [P, I32, I32]),
     "cola_test_stall_next_launch": (I32, [P, I64]),
+    "cola_kron_eigs": (I32, [P, P, P, P, P, P]),
     "cola_kron_matvec_noalloc": (I32, [C.c_int, C.POINTER(I64), C.POINTER(I64), PP, P, P, I64, P]),
 }
 

@@ -30,7 +30,8 @@ namespace {
 // deflation (Golub & Van Loan, Sec. 8.3), every reflection and rotation
 // applied to the accumulated orthogonal factor.  a: n x n row-major,
 // symmetric (destroyed).  Vt: n x n row-major, row j = the eigenvector of w[j].
-void sym_eig(int n, double* a, double* Vt, double* w) {
+// Returns false when the QR sweeps did not converge within 60 n iterations.
+bool sym_eig(int n, double* a, double* Vt, double* w) {
   for (int i = 0; i < n * n; ++i) Vt[i] = 0.0;
   for (int i = 0; i < n; ++i) Vt[(size_t)i * n + i] = 1.0;
   std::vector<double> v(n), p(n), q(n), u(n);
@@ -112,6 +113,7 @@ void sym_eig(int n, double* a, double* Vt, double* w) {
     }
   }
   for (int i = 0; i < n; ++i) w[i] = d[i];
+  return hi <= 0;
 }
 
 constexpr int kMaxFactors = 8;
@@ -145,6 +147,25 @@ __global__ void k_eig_scale(T* Y, int64_t N, int64_t R, EigDims g, double ck, co
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < tot;
        e += (int64_t)gridDim.x * blockDim.x)
     Y[e] = (T)((double)Y[e] / eig_at(g, e % N, ck, shift));
+}
+
+// out[i] = lambda_A(i) for every flat index (the eigenvalues of A in the
+// order of the Kronecker eigenvectors (x)_k V_k).
+__global__ void k_eig_values(int64_t N, EigDims g, double ck, const double* s, double cd,
+                             double* out) {
+  const double shift = s ? cd * s[0] : 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
+       i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = eig_at(g, i, ck, shift);
+}
+
+// V[i, j] = Vt[j, i] for an n x n row-major matrix.
+__global__ void k_transpose64(int64_t n, const double* Vt, double* V) {
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n * n;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = t / n, j = t % n;
+    V[t] = Vt[j * n + i];
+  }
 }
 
 // Per-block partial sums of log lambda_A(i); nonpos[b] counts lambda <= 0.
@@ -325,7 +346,9 @@ void prepare_eig(Ctx* c, const KronShift& m, bool want32) {
     COLA_REQUIRE(asym <= 1e-12 * amax, COLA_ERR_INVALID_ARG,
                  "Kronecker factor is not symmetric (max |K - K^T| = %g)", asym);
     std::vector<double> Vt((size_t)n * n), lam(n);
-    sym_eig((int)n, A.data(), Vt.data(), lam.data());
+    COLA_REQUIRE(sym_eig((int)n, A.data(), Vt.data(), lam.data()), COLA_ERR_NOT_CONVERGED,
+                 "symmetric QR of a %lld x %lld Kronecker factor did not converge",
+                 (long long)n, (long long)n);
     void* dv = eig_buf(f, kKeyVt64, (size_t)n * n * 8);
     void* dl = eig_buf(f, kKeyLam64, (size_t)n * 8);
     COLA_CUDA(cudaMemcpyAsync(dv, Vt.data(), (size_t)n * n * 8, cudaMemcpyHostToDevice, c->s));
@@ -569,7 +592,8 @@ cola_status cola_sym_eig(int64_t n, const double* A, double* V, double* w) {
     COLA_REQUIRE(A && V && w, COLA_ERR_INVALID_ARG, "NULL argument");
     COLA_REQUIRE(n >= 1 && n <= 8192, COLA_ERR_INVALID_ARG, "n = %lld", (long long)n);
     std::vector<double> a(A, A + n * n), Vt((size_t)(n * n));
-    sym_eig((int)n, a.data(), Vt.data(), w);
+    COLA_REQUIRE(sym_eig((int)n, a.data(), Vt.data(), w), COLA_ERR_NOT_CONVERGED,
+                 "symmetric QR did not converge within %lld iterations", (long long)(60 * n));
     for (int64_t i = 0; i < n; ++i)
       for (int64_t j = 0; j < n; ++j) V[i * n + j] = Vt[(size_t)(j * n + i)];
   });
@@ -593,6 +617,43 @@ cola_status cola_kron_eig_solve(cola_ctx* ctx, const cola_linop* op, const void*
       eig_solve<double>(ctx, m, s, m.cd, (const double*)B, (double*)X, nrhs);
     else
       eig_solve<float>(ctx, m, s, m.cd, (const float*)B, (float*)X, nrhs);
+  });
+}
+
+cola_status cola_kron_eigs(cola_ctx* ctx, const cola_linop* op, double* factor_evals,
+                           double* factor_evecs, double* evals, cola_stream stream) {
+  return guard([&] {
+    COLA_REQUIRE(ctx && op, COLA_ERR_INVALID_ARG, "NULL argument");
+    COLA_REQUIRE(factor_evals || factor_evecs || evals, COLA_ERR_INVALID_ARG,
+                 "no output requested");
+    StreamJoin j(ctx, stream);
+    const KronShift m = match(op);
+    prepare_leaves(ctx, const_cast<cola_linop*>(op), COLA_PREC_F64, 0);
+    prepare_eig(ctx, m, false);
+    int64_t off_w = 0, off_v = 0;
+    for (auto* f : m.kron->kids) {
+      const int64_t n = f->rows;
+      if (factor_evals)
+        COLA_CUDA(cudaMemcpyAsync(factor_evals + off_w, f->derived.at(kKeyLam64).p, 8 * n,
+                                  cudaMemcpyDeviceToDevice, ctx->s));
+      if (factor_evecs) {
+        const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((n * n + 255) / 256, 1024));
+        k_transpose64<<<grid, 256, 0, ctx->s>>>(n, (const double*)f->derived.at(kKeyVt64).p,
+                                                factor_evecs + off_v);
+        ctx->count_launch();
+      }
+      off_w += n;
+      off_v += n * n;
+    }
+    if (evals) {
+      const int64_t N = m.kron->rows;
+      const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((N + 255) / 256, 4096));
+      k_eig_values<<<grid, 256, 0, ctx->s>>>(N, dims_of(m), m.ck,
+                                             m.diag ? leaf_ptr<double>(m.diag) : nullptr, m.cd,
+                                             evals);
+      ctx->count_launch();
+    }
+    COLA_CUDA(cudaGetLastError());
   });
 }
 

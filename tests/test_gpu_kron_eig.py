@@ -122,3 +122,42 @@ def test_eig_path_rejects_what_it_cannot_diagonalise(cola, ctx):
     op2 = gpu_tree(cola, ctx, ("kron", [("dense", A), ("dense", K2)]), torch.float64, DEV)
     with pytest.raises(cola.ColaError, match="INVALID_ARG"):
         cola.cola_kron_eig_solve(ctx, op2, B, cola.PREC_F64)
+
+
+@pytest.mark.parametrize("kind", ["kron", "kronsum"])
+def test_kron_eigs_small_dense(cola, ctx, kind):
+    """cola_kron_eigs (Table 3 Eigs rule) on 2.5 * (K1 op K2) + 0.3 I with op
+    the Kronecker product or sum of a 7 x 7 and a 9 x 9 symmetric factor:
+    the N = 63 eigenvalues equal the dense matrix's (LAPACK eigvalsh, no
+    Kronecker structure used), each factor pair satisfies K V = V diag(w) with
+    orthonormal V, and column (i, j) of V1 (x) V2 is an eigenvector of A with
+    the eigenvalue at flat index i n2 + j."""
+    r = np.random.default_rng(31)
+    M1, M2 = r.standard_normal((7, 7)), r.standard_normal((9, 9))
+    K1, K2 = M1 @ M1.T / 7 + 0.2 * np.eye(7), M2 @ M2.T / 9 + 0.1 * np.eye(9)
+    spec = ("sum", [(kind, [("dense", K1), ("dense", K2)]), ("scalar", 0.3, 63)], [2.5, 1.0])
+    ref = oracle_tree(spec)
+    op = gpu_tree(cola, ctx, spec, torch.float64, DEV)
+    ws, Vs, ev = cola.cola_kron_eigs(ctx, op)
+    ev = ev.cpu().numpy()
+    np.testing.assert_allclose(np.sort(ev), np.linalg.eigvalsh(ref.dense()), rtol=1e-12,
+                               atol=1e-12)
+    for K, w, V in zip((K1, K2), ws, Vs):
+        w, V = w.cpu().numpy(), V.cpu().numpy()
+        np.testing.assert_allclose(K @ V, V * w, atol=1e-12)
+        np.testing.assert_allclose(V.T @ V, np.eye(len(w)), atol=1e-13)
+    V1, V2 = Vs[0].cpu().numpy(), Vs[1].cpu().numpy()
+    for i, j in [(0, 0), (3, 5), (6, 8)]:
+        q = np.kron(V1[:, i], V2[:, j])
+        np.testing.assert_allclose(ref @ q, ev[i * 9 + j] * q, atol=1e-11)
+
+
+def test_kron_eigs_full_size(cola, ctx):
+    """At the 128^3 workload the 2,097,152 eigenvalues equal the oracle's
+    (products of the factors' LAPACK eigenvalues plus the shift), as sets."""
+    w = wl.config2(nrhs=1)
+    op = gpu_tree(cola, ctx, _spec(w.factors, w.shift, w.N), torch.float64, DEV)
+    _, _, ev = cola.cola_kron_eigs(ctx, op)
+    ref = np.sort(exact.kron_eigenvalues(w.factors, w.shift))
+    got = np.sort(ev.cpu().numpy())
+    np.testing.assert_allclose(got, ref, rtol=1e-9, atol=1e-12 * ref.max())

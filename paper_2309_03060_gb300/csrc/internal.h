@@ -307,6 +307,11 @@ int64_t kron_tc_cg_mvm(Ctx* c, const cola_linop* op, const float* z, const doubl
                        const float* p_old, float* p_new, float* Ap, double* tile_dot, int64_t R,
                        int depth);
 int64_t kron_tc_tiles_per_rhs(const cola_linop* op);
+// Fused Lanczos MIXED MVM for Sum(Kron, scalar Diag); see kron_tc.cu.  0 = not applicable.
+int64_t kron_tc_lanczos_mvm(Ctx* c, const cola_linop* op, const float* w_in,
+                            const double* scale, float* q_out, const float* q_prev,
+                            const double* gamma, float* w_out, double* tile_dot, int64_t R,
+                            int depth);
 
 // One tensor-core mode-step problem of a batch (host mirror of the kernel's
 // per-problem parameters) and the launch over a device problem table.

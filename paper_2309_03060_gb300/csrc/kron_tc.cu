@@ -64,6 +64,12 @@ struct TcParams {
   const double* pro_beta;
   float* pro_out;  // where p is written (never the input X: tiles of several
                    // output chunks re-read the same X rows)
+  // pro_out without pro_z: the input is pro_beta[r] * X (a per-vector scale,
+  // the Lanczos normalisation q = w / beta), written to pro_out
+  // optional Lanczos term of the epilogue: Y -= epi_gamma[r] * epi_q2 (the
+  // previous basis vector), before the partial sums of epi_x . Y
+  const float* epi_q2;
+  const double* epi_gamma;
   // optional epilogue (last mode step, output in the input's layout):
   // Y += epi_coeff * d * epi_x (d = epi_d[0] when epi_dstride == 0), and the
   // per-(tile, epilogue warp) partial sums of epi_x . Y go to epi_dot[4 tile + warp]
@@ -332,6 +338,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_kron_tc(Src src, TcParams K) 
       const float* Zb = p.pro_z ? p.pro_z + r * p.size_in : nullptr;
       const float beta_r = p.pro_z ? (float)p.pro_beta[r] : 0.0f;
       const int64_t m = m0 + tid;
+      (void)r;
       const bool row_ok = m < p.rest;
       for (int kb = 0; kb < p.kblocks; ++kb) {
         if (!mbar_wait(&empty[s], ph ^ 1u, abort_flag, K.err)) {
@@ -371,6 +378,16 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_kron_tc(Src src, TcParams K) 
               v[g + k] = fmaf(beta_r, pp[k], zz[k]);
               if (row_ok && kk < p.n_in) Pw[(int64_t)kk * p.rest + m] = v[g + k];
             }
+          }
+        } else if (Pw) {
+          // scaled input, written back: q = beta_r x
+          const float sc = (float)p.pro_beta[r];
+#pragma unroll
+          for (int k = 0; k < kBlockK; ++k) {
+            const int kk = k0 + k;
+            const bool in = row_ok && kk < p.n_in;
+            v[k] = in ? sc * Pb[(int64_t)kk * p.rest + m] : 0.0f;
+            if (in) Pw[(int64_t)kk * p.rest + m] = v[k];
           }
         } else {
 #pragma unroll
@@ -502,6 +519,8 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_kron_tc(Src src, TcParams K) 
       const bool vec_ok = ((reinterpret_cast<uintptr_t>(yrow) & 15u) == 0);
       const float* xrow = p.epi_x ? p.epi_x + r * p.size_out + m * p.n_out + ncol0 : nullptr;
       const int64_t dbase = m * p.n_out + ncol0;
+      const float gam = p.epi_q2 ? (float)p.epi_gamma[r] : 0.0f;
+      const float* q2row = p.epi_q2 ? p.epi_q2 + r * p.size_out + m * p.n_out + ncol0 : nullptr;
       double dot = 0.0;
       const uint32_t taddr =
           tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * 2 * K.n_chunk);
@@ -530,6 +549,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_kron_tc(Src src, TcParams K) 
             const int i = c0 + e;
             const float dv = p.epi_dstride ? (i < ncols ? p.epi_d[dbase + i] : 0.0f) : p.epi_d[0];
             a[e] = fmaf(p.epi_coeff * dv, xd[e], a[e]);
+            if (gam != 0.0f && i < ncols) a[e] = fmaf(-gam, q2row[i], a[e]);
             if (p.beta == 0.0f && i < ncols) dot += (double)(a[e] * xd[e]);
           }
         }
@@ -642,6 +662,9 @@ struct TcFsParams {
   const double* pro_beta;
   float* pro_out;
   double* epi_dot;
+  int pro_scale;          // 1: the input is pro_beta[r] * X, written to pro_out
+  const float* e_q2;      // e_mode 4: previous Lanczos vector (output layout)
+  const double* e_gamma;  // e_mode 4: its coefficient per right-hand side
 };
 
 __device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t* r) {
@@ -687,6 +710,8 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, i
 // to chunk position c ^ (row & 7) of each term's B stage.  NSRC == 2 first
 // forms p = z + beta_r p and writes it to Pout (row m of p, k stride `rest`).
 // FULL: the row and the whole block are in range, nothing is masked.
+// NSRC == 0: the staged values times beta_r, written to Pout (the Lanczos
+// normalisation q = w / beta).
 template <int TV, int NSRC, bool FULL>
 __device__ __forceinline__ void fs_convert(const float* st, const float* stz, unsigned char* brow,
                                            int row, int khalf, int kbase, int n_in, bool row_ok,
@@ -702,6 +727,9 @@ __device__ __forceinline__ void fs_convert(const float* st, const float* stz, un
       float x = in ? st[kl * kTileM + row] : 0.0f;
       if (NSRC > 1 && in) {
         x = fmaf(beta_r, x, stz[kl * kTileM + row]);
+        Pout[(int64_t)(kbase + kl) * rest] = x;
+      } else if (NSRC == 0 && in) {
+        x = beta_r * x;
         Pout[(int64_t)(kbase + kl) * rest] = x;
       }
       v[e] = x;
@@ -726,19 +754,21 @@ __device__ __forceinline__ void fs_convert(const float* st, const float* stz, un
 // i): y = a (MODE 0), y = a + sc x with the partial sum of y x (MODE 1, x the
 // staged p), y = a + sc y_old (MODE 2, y_old staged), y = a + sc d x with d
 // read per element from dp (MODE 3, otherwise as MODE 1).
+// MODE 4: as MODE 1, then y -= gam q2 (q2 read per element from dp).
 template <int MODE>
 __device__ __forceinline__ float fs_store(const float (&a)[64], float* yp, const float* es,
                                           int64_t ld, int nrows, float sc,
-                                          const float* dp = nullptr) {
+                                          const float* dp = nullptr, float gam = 0.0f) {
   float part = 0.0f;
 #pragma unroll
   for (int c = 0; c < 64; ++c) {
     if (c < nrows) {
       float v = a[c];
-      if (MODE == 1 || MODE == 3) {
+      if (MODE == 1 || MODE == 3 || MODE == 4) {
         const float xd = es[c * ld];
         const float s = MODE == 3 ? sc * __ldg(dp + c * ld) : sc;
         v = fmaf(s, xd, v);
+        if (MODE == 4 && gam != 0.0f) v = fmaf(-gam, dp[c * ld], v);
         part = fmaf(v, xd, part);
       } else if (MODE == 2) {
         v = fmaf(sc, es[c * ld], v);
@@ -876,8 +906,9 @@ __global__ void __launch_bounds__(kThreadsFs, 1) k_kron_tc_fs(const __grid_const
       const int64_t r = t / p.tiles_m, m0 = (t % p.tiles_m) * kTileM;
       const int64_t m = m0 + row;
       const bool row_ok = m < p.rest;
-      const float beta_r = p.nsrc > 1 ? (float)p.pro_beta[r] : 0.0f;
-      float* Pout = p.nsrc > 1 ? p.pro_out + r * p.size_in + m : nullptr;
+      const bool pro = p.nsrc > 1 || p.pro_scale;
+      const float beta_r = pro ? (float)p.pro_beta[r] : 0.0f;
+      float* Pout = pro ? p.pro_out + r * p.size_in + m : nullptr;
       for (int kb = 0; kb < p.kblocks; ++kb) {
         if (!mbar_wait(&bempty[sb], phb ^ 1u, abort_flag, p.err) ||
             !mbar_wait(&xfull[s], ph, abort_flag, p.err)) {
@@ -895,6 +926,13 @@ __global__ void __launch_bounds__(kThreadsFs, 1) k_kron_tc_fs(const __grid_const
                                     Pout, p.rest);
           else
             fs_convert<TV, 2, false>(st, stz, brow, row, khalf, kbase, p.n_in, row_ok, beta_r,
+                                     Pout, p.rest);
+        } else if (p.pro_scale) {
+          if (full)
+            fs_convert<TV, 0, true>(st, stz, brow, row, khalf, kbase, p.n_in, row_ok, beta_r,
+                                    Pout, p.rest);
+          else
+            fs_convert<TV, 0, false>(st, stz, brow, row, khalf, kbase, p.n_in, row_ok, beta_r,
                                      Pout, p.rest);
         } else {
           if (full)
@@ -1010,7 +1048,8 @@ __global__ void __launch_bounds__(kThreadsFs, 1) k_kron_tc_fs(const __grid_const
     mbar_arrive(afac);
     pdl_wait();  // the factor copy above overlaps the previous kernel's tail
     const bool staged = p.e_mode != 0;
-    const float sc = p.e_mode == 1 ? p.e_coeff * p.e_d[0] : (p.e_mode == 3 ? p.e_coeff : p.beta);
+    const float sc = (p.e_mode == 1 || p.e_mode == 4) ? p.e_coeff * p.e_d[0]
+                                                      : (p.e_mode == 3 ? p.e_coeff : p.beta);
     int64_t it = 0;
     for (int64_t t = blockIdx.x; t < p.ntiles; t += gridDim.x, ++it) {
       if (staged && !mbar_wait(efull, (uint32_t)(it & 1), abort_flag, p.err)) break;
@@ -1046,6 +1085,9 @@ __global__ void __launch_bounds__(kThreadsFs, 1) k_kron_tc_fs(const __grid_const
           part = fs_store<1>(a, yp, es, ld, nrows, sc);
         else if (p.e_mode == 3)
           part = fs_store<3>(a, yp, es, ld, nrows, sc, p.e_d + mbase * ld + i);
+        else if (p.e_mode == 4)
+          part = fs_store<4>(a, yp, es, ld, nrows, sc, p.e_q2 + r * p.size_out + mbase * ld + i,
+                             (float)p.e_gamma[r]);
         else
           fs_store<2>(a, yp, es, ld, nrows, sc);
       }
@@ -1306,9 +1348,14 @@ static bool fs_plan(const TcParams& p, TcFsParams& r) {
   if (p.nchunks != 1 || p.n_pad > kTileM || p.kblocks > 2) return false;
   if (p.rest % 4 != 0 || p.size_in % 4 != 0) return false;
   r.e_mode = p.epi_x ? (p.epi_dstride != 0 ? 3 : 1) : (p.beta != 0.0f ? 2 : 0);
+  if (p.epi_q2) {
+    if (r.e_mode != 1) return false;  // the Lanczos term takes the scalar-shift epilogue
+    r.e_mode = 4;
+  }
   // a fused shift with a nonzero beta takes the streaming kernel
   if (p.epi_x && p.beta != 0.0f) return false;
-  r.e_src = (r.e_mode == 1 || r.e_mode == 3) ? p.epi_x : (r.e_mode == 2 ? p.Y : nullptr);
+  r.e_src = (r.e_mode == 1 || r.e_mode == 3 || r.e_mode == 4) ? p.epi_x
+                                                             : (r.e_mode == 2 ? p.Y : nullptr);
   if (r.e_src && (((uintptr_t)r.e_src & 15u) != 0 || p.size_out % 4 != 0)) return false;
   const int64_t xrows = p.batch * p.n_in;
   if (!tmap_rows(&r.tm_x, p.X, xrows, p.rest)) return false;
@@ -1341,6 +1388,9 @@ static bool fs_plan(const TcParams& p, TcFsParams& r) {
   r.pro_beta = p.pro_beta;
   r.pro_out = p.pro_out;
   r.epi_dot = p.epi_dot;
+  r.pro_scale = (p.pro_out && !p.pro_z) ? 1 : 0;
+  r.e_q2 = p.epi_q2;
+  r.e_gamma = p.epi_gamma;
   return true;
 }
 
@@ -1362,6 +1412,8 @@ struct TcFusion {
   int64_t epi_dstride = 0;
   float epi_coeff = 0.0f;
   double* epi_dot = nullptr;
+  const float* epi_q2 = nullptr;
+  const double* epi_gamma = nullptr;
 };
 
 // Runs the d mode steps of a Kronecker MVM on the tensor cores; returns the
@@ -1438,6 +1490,8 @@ static int64_t kron_tc_run(Ctx* c, const cola_linop* op, const float* X, float* 
       p.epi_dstride = fu.epi_dstride;
       p.epi_coeff = fu.epi_coeff;
       p.epi_dot = fu.epi_dot;
+      p.epi_q2 = fu.epi_q2;
+      p.epi_gamma = fu.epi_gamma;
       last_tiles = p.tiles_m * q.nchunks;
     }
     if (c->device < 64 && !attr_set[c->device]) {
@@ -1501,6 +1555,40 @@ int64_t kron_tc_cg_mvm(Ctx* c, const cola_linop* op, const float* z, const doubl
   fu.epi_coeff = (float)op->coeffs[id];
   fu.epi_dot = tile_dot;
   return kron_tc_run(c, kron, p_old, Ap, R, op->coeffs[ik], 0.0, depth, false, fu);
+}
+
+// One Lanczos MVM for A = c_k * Kron(...) + c_d * s I (s a device scalar): the
+// first mode step forms q = scale[r] * w_in and writes it to q_out, the last
+// writes w_out = A q - gamma[r] * q_prev and the per-(tile, warp) partials of
+// q . w_out.  w_in and w_out may be the same buffer (the first step has
+// finished reading before the last one writes).  Returns the last step's row
+// tiles per right-hand side, or 0 when the operator does not have this shape.
+int64_t kron_tc_lanczos_mvm(Ctx* c, const cola_linop* op, const float* w_in,
+                            const double* scale, float* q_out, const float* q_prev,
+                            const double* gamma, float* w_out, double* tile_dot, int64_t R,
+                            int depth) {
+  if (op->kind != LK_SUM || op->kids.size() != 2) return 0;
+  int ik = -1, id = -1;
+  for (int i = 0; i < 2; ++i) {
+    if (op->kids[i]->kind == LK_KRON) ik = i;
+    if (op->kids[i]->kind == LK_DIAG && op->kids[i]->stride == 0) id = i;
+  }
+  if (ik < 0 || id < 0) return 0;
+  const cola_linop* kron = op->kids[ik];
+  const cola_linop* dg = op->kids[id];
+  if (kron->kids.size() < 2 || !tc_supported(kron)) return 0;
+  if (kron->derived.find(200) == kron->derived.end()) return 0;
+  TcFusion fu;
+  fu.pro_beta = scale;
+  fu.pro_out = q_out;
+  fu.epi_x = q_out;
+  fu.epi_d = leaf_ptr<float>(dg);
+  fu.epi_dstride = 0;
+  fu.epi_coeff = (float)op->coeffs[id];
+  fu.epi_dot = tile_dot;
+  fu.epi_q2 = q_prev;
+  fu.epi_gamma = gamma;
+  return kron_tc_run(c, kron, w_in, w_out, R, op->coeffs[ik], 0.0, depth, false, fu);
 }
 
 int64_t kron_tc_tiles_per_rhs(const cola_linop* op) {

@@ -601,6 +601,14 @@ __global__ void k_lz_next(int64_t n, T* w, const double* b_cur) {
     w[v * n + i] *= s;
 }
 
+// dst[v] = 1 / sqrt(src[v]) (root = 1) or 1 / src[v] (root = 0); 0 when src[v] <= 0.
+__global__ void k_lz_recip(int64_t nv, const double* src, double* dst, int root) {
+  const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= nv) return;
+  const double x = src[v];
+  dst[v] = x > 0.0 ? 1.0 / (root ? sqrt(x) : x) : 0.0;
+}
+
 __global__ void k_lz_meff(const LzState* st, int64_t nv, int* m_eff) {
   const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (v < nv) m_eff[v] = st[v].m_eff;
@@ -1254,6 +1262,63 @@ cola_status cola_lanczos(cola_ctx* ctx, const cola_linop* op, const void* Q0, in
 
 namespace cola {
 
+// MIXED Lanczos for A = c_k Kron + c_d s I with the recurrence fused into the
+// tensor-core MVM: step j's first mode step forms q_j = w / beta_{j-1} (w =
+// Q0 and the scale 1 / ||z|| at j = 0), its last mode step writes
+// w = A q_j - beta_{j-1} q_{j-1} with the partials of alpha_j = q_j . w; one
+// vector pass then forms w -= alpha_j q_j and ||w||^2, the same recurrence
+// and breakdown test as the unfused loop.  false when the operator does not
+// have this shape.
+static bool lanczos_fused(Ctx* c, cola_linop* op, const float* Q0, int64_t nv, int m,
+                          double* alpha, double* beta, int* m_eff) {
+  const int64_t tiles = kron_tc_tiles_per_rhs(op);
+  if (tiles <= 0) return false;
+  const int64_t N = op->rows;
+  const int nblk = dot_blocks(N);
+  auto& ws = c->ws;
+  float* w = (float*)ws.get("lz.0", sizeof(float) * N * nv);
+  float* q[2] = {(float*)ws.get("lz.1", sizeof(float) * N * nv),
+                 (float*)ws.get("lz.2", sizeof(float) * N * nv)};
+  double* tdot = (double*)ws.get("lz.tdot", 8 * 8 * (size_t)tiles * nv);
+  double* part = (double*)ws.get("lz.part", 8 * nblk * nv);
+  double* nrm2 = (double*)ws.get("lz.nrm2", 8 * nv);
+  double* a_cur = (double*)ws.get("lz.a", 8 * nv);
+  double* b_cur = (double*)ws.get("lz.b", 8 * nv);
+  double* scale = (double*)ws.get("lz.scale", 8 * nv);
+  LzState* st = (LzState*)ws.get("lz.st", sizeof(LzState) * nv);
+  const unsigned vb = (unsigned)((nv + 127) / 128);
+  COLA_CUDA(cudaMemsetAsync(alpha, 0, 8 * nv * m, c->s));
+  COLA_CUDA(cudaMemsetAsync(beta, 0, 8 * nv * m, c->s));
+  COLA_CUDA(cudaMemsetAsync(b_cur, 0, 8 * nv, c->s));
+  dots<float>(c, Q0, Q0, N, nv, part, nrm2);
+  k_lz_init<<<vb, 128, 0, c->s>>>(st, nrm2, nv, m);
+  c->count_launch();
+  k_lz_recip<<<vb, 128, 0, c->s>>>(nv, nrm2, scale, 1);
+  c->count_launch();
+  const double eps = 1e-6;
+  for (int j = 0; j < m; ++j) {
+    float* qj = q[j & 1];
+    const float* qprev = q[(j + 1) & 1];
+    const int64_t t = kron_tc_lanczos_mvm(c, op, j == 0 ? Q0 : w, scale, qj, qprev, b_cur, w,
+                                          tdot, nv, 1);
+    COLA_REQUIRE(t == tiles, COLA_ERR_UNSUPPORTED, "internal: fused Lanczos tile count");
+    k_lz_alpha<<<(unsigned)nv, 256, 0, c->s>>>(st, tdot, (int)(8 * tiles), nv, j, m, alpha,
+                                               a_cur);
+    c->count_launch();
+    k_lz_b<float><<<rows_grid(N, nv, nblk), 256, 0, c->s>>>(N, w, qj, a_cur, nblk, part, 1);
+    c->count_launch();
+    dot_final(c, part, nblk, nv, nrm2);
+    k_lz_beta<<<vb, 128, 0, c->s>>>(st, nrm2, nv, j, m, eps, beta, b_cur);
+    c->count_launch();
+    k_lz_recip<<<vb, 128, 0, c->s>>>(nv, b_cur, scale, 0);
+    c->count_launch();
+  }
+  k_lz_meff<<<vb, 128, 0, c->s>>>(st, nv, m_eff);
+  c->count_launch();
+  COLA_CUDA(cudaGetLastError());
+  return true;
+}
+
 template <typename T>
 static void lanczos_run(Ctx* c, cola_linop* op, const T* Q0, int64_t nv, int m, int prec,
                         int reorth, double* alpha, double* beta, int* m_eff) {
@@ -1262,6 +1327,11 @@ static void lanczos_run(Ctx* c, cola_linop* op, const T* Q0, int64_t nv, int m, 
   auto& ws = c->ws;
   // MIXED: the context's split terms (cola_set_split_terms), as cola_matvec
   prepare_leaves(c, op, prec, c->split_factor_terms);
+  if constexpr (sizeof(T) == 4) {
+    if (prec == COLA_PREC_MIXED && !reorth &&
+        lanczos_fused(c, op, (const float*)Q0, nv, m, alpha, beta, m_eff))
+      return;
+  }
   T* bufs[3];
   bufs[0] = (T*)ws.get("lz.0", sizeof(T) * N * nv);
   bufs[1] = (T*)ws.get("lz.1", sizeof(T) * N * nv);

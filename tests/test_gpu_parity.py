@@ -487,3 +487,27 @@ def test_prepared_copies_reused_and_refreshed_after_in_place_update(cola, ctx):
     err = np.abs(Y2.double().cpu().numpy() - ref.mvm(X.double().cpu().numpy())).max()
     assert err <= 1e-5 * np.abs(Y2.double().cpu().numpy()).max()
     torch.testing.assert_close(Y2, 2.0 * Y1, rtol=1e-5, atol=1e-5)
+
+
+@pytest.mark.parametrize("sides", [(24, 20, 16), (160, 24)], ids=["factor_stationary", "streaming"])
+def test_lanczos_mixed_fused_matches_oracle(cola, ctx, sides):
+    """MIXED Lanczos on K (x) ... + 0.05 I runs the recurrence fused into the
+    tensor-core MVM (normalisation in the first mode step's prologue, shift,
+    three-term subtraction and alpha partials in the last one's epilogue).  Its
+    coefficients match the oracle's Lanczos on the same probes for the steps
+    before orthogonality is lost (3 x 3 split terms: FP32-level rounding)."""
+    F = [_spd(n, 500 + n) for n in sides]
+    N = int(np.prod(sides))
+    spec = ("sum", [("kron", [("dense", f) for f in F]), ("scalar", 0.05, N)], None)
+    ref = oracle_tree(spec)
+    op = gpu_tree(cola, ctx, spec, torch.float64, DEV).set_spd()
+    Z = rng.rademacher_probes(9, 3, N)
+    m, j0 = 12, 8
+    al, be, me = cola.cola_lanczos(ctx, op, torch.tensor(Z, dtype=torch.float32, device=DEV), m,
+                                   cola.PREC_MIXED, reorth=0, split_terms=3)
+    al, be, me = al.cpu().numpy(), be.cpu().numpy(), me.cpu().numpy()
+    for v in range(3):
+        a, b, _ = krylov.lanczos(ref, Z[v], m, reorth=False)
+        assert me[v] == m
+        np.testing.assert_allclose(al[v, :j0], a[:j0], rtol=1e-5)
+        np.testing.assert_allclose(be[v, :j0], b[:j0], rtol=1e-5)

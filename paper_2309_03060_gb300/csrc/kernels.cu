@@ -4,6 +4,7 @@
 // low-rank terms, deterministic per-vector reductions, leaf-gradient
 // contractions (App. B.2) and the SplitMix64 probe generator.
 #include <algorithm>
+#include <type_traits>
 
 #include "internal.h"
 
@@ -115,6 +116,118 @@ __global__ void __launch_bounds__(256) k_gemm(GemmP<T> g, int64_t batch0) {
   gemm_tile_body<T>(g, g.A + b * g.sA, g.B + b * g.sB, g.C + b * g.sC);
 }
 
+
+// FP32 mode product on the SIMT cores, for the layout of the Kronecker mode
+// steps: A m-fast (lam = 1, the input vector viewed as [k][m]), B k-fast
+// (lbk = 1, the row-major factor F[n][k]), C n-fast (lcn = 1).  128 x 128
+// output tile per block, k in tiles of 16, 256 threads with 8 x 8 outputs
+// each; float4 global loads of the next k tile are held in registers while
+// the current one is multiplied out of the other shared-memory buffer, so one
+// barrier per k tile separates the two.  Needs M, N, lak, lbn, lcm and sA,
+// sB, sC multiples of 4 and 16-byte aligned bases (checked on the host).
+constexpr int kMfBM = 128, kMfBN = 128, kMfBK = 16, kMfPadN = kMfBN + 4;
+
+__global__ void __launch_bounds__(256, 2) k_gemm_mode_f32(GemmP<float> g, int64_t batch0) {
+  __shared__ __align__(16) float As[2][kMfBK][kMfBM];
+  __shared__ __align__(16) float Bs[2][kMfBK][kMfPadN];
+  const int64_t b = batch0 + blockIdx.z;
+  const float* A = g.A + b * g.sA;
+  const float* B = g.B + b * g.sB;
+  float* C = g.C + b * g.sC;
+  const int64_t m0 = (int64_t)blockIdx.x * kMfBM, n0 = (int64_t)blockIdx.y * kMfBN;
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  // this thread's loads per k tile: A rows ka, ka + 8 at column ma (float4);
+  // B rows nb, nb + 64 at k offset kb (float4 along k)
+  const int ka = tid >> 5, ma = (tid & 31) * 4;
+  const int nb = tid >> 2, kb = (tid & 3) * 4;
+  const bool a_in = m0 + ma < g.M;
+  const bool b_in0 = n0 + nb < g.N, b_in1 = n0 + nb + 64 < g.N;
+  float4 ra[2], rb[2];
+  auto load = [&](int64_t k0) {
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int64_t k = k0 + ka + 8 * h;
+      ra[h] = (a_in && k < g.K)
+                  ? __ldg(reinterpret_cast<const float4*>(A + k * g.lak + m0 + ma))
+                  : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    const int64_t k = k0 + kb;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const bool in = (h ? b_in1 : b_in0);
+      const float* src = B + (n0 + nb + 64 * h) * g.lbn + k;
+      if (in && k + 4 <= g.K) {
+        rb[h] = __ldg(reinterpret_cast<const float4*>(src));
+      } else {
+        rb[h].x = (in && k < g.K) ? src[0] : 0.f;
+        rb[h].y = (in && k + 1 < g.K) ? src[1] : 0.f;
+        rb[h].z = (in && k + 2 < g.K) ? src[2] : 0.f;
+        rb[h].w = (in && k + 3 < g.K) ? src[3] : 0.f;
+      }
+    }
+  };
+  auto store = [&](int buf) {
+#pragma unroll
+    for (int h = 0; h < 2; ++h)
+      *reinterpret_cast<float4*>(&As[buf][ka + 8 * h][ma]) = ra[h];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int n = nb + 64 * h;
+      Bs[buf][kb + 0][n] = rb[h].x;
+      Bs[buf][kb + 1][n] = rb[h].y;
+      Bs[buf][kb + 2][n] = rb[h].z;
+      Bs[buf][kb + 3][n] = rb[h].w;
+    }
+  };
+  float acc[8][8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+  const int ntk = (int)((g.K + kMfBK - 1) / kMfBK);
+  load(0);
+  store(0);
+  __syncthreads();
+  for (int t = 0; t < ntk; ++t) {
+    const int cur = t & 1;
+    if (t + 1 < ntk) load((int64_t)(t + 1) * kMfBK);
+#pragma unroll
+    for (int kk = 0; kk < kMfBK; ++kk) {
+      float a[8], bb[8];
+      ld4(a, &As[cur][kk][ty * 4]);
+      ld4(a + 4, &As[cur][kk][64 + ty * 4]);
+      ld4(bb, &Bs[cur][kk][tx * 4]);
+      ld4(bb + 4, &Bs[cur][kk][64 + tx * 4]);
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(a[i], bb[j], acc[i][j]);
+    }
+    if (t + 1 < ntk) store(cur ^ 1);
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const int64_t m = m0 + (i < 4 ? ty * 4 + i : 64 + ty * 4 + (i - 4));
+    if (m >= g.M) continue;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int64_t n = n0 + h * 64 + tx * 4;
+      if (n >= g.N) continue;
+      float4* p = reinterpret_cast<float4*>(C + m * g.lcm + n);
+      float4 v = make_float4(g.alpha * acc[i][4 * h], g.alpha * acc[i][4 * h + 1],
+                             g.alpha * acc[i][4 * h + 2], g.alpha * acc[i][4 * h + 3]);
+      if (g.beta != 0.f) {
+        const float4 o = *p;
+        v.x += g.beta * o.x;
+        v.y += g.beta * o.y;
+        v.z += g.beta * o.z;
+        v.w += g.beta * o.w;
+      }
+      *p = v;
+    }
+  }
+}
 
 // Grouped variant: problem blockIdx.z of a device table, same tiling.
 template <typename T>
@@ -425,9 +538,21 @@ void gemm(Ctx* c, int64_t M, int64_t N, int64_t K, double alpha, const T* A, int
              (T)alpha, (T)beta};
   const int64_t gy = (N + 127) / 128;
   COLA_REQUIRE(gy <= 65535, COLA_ERR_UNSUPPORTED, "gemm: N=%lld too large", (long long)N);
+  auto a16 = [](const void* p) { return ((uintptr_t)p & 15u) == 0; };
+  const bool mode_f32 = std::is_same<T, float>::value && lda_m == 1 && ldb_k == 1 &&
+                        ldc_n == 1 && M % 4 == 0 && N % 4 == 0 && lda_k % 4 == 0 &&
+                        ldb_n % 4 == 0 && ldc_m % 4 == 0 && sA % 4 == 0 && sB % 4 == 0 &&
+                        sC % 4 == 0 && a16(A) && a16(B) && a16(C);
   for (int64_t b0 = 0; b0 < batch; b0 += 65535) {
     const int64_t nb = std::min<int64_t>(65535, batch - b0);
     dim3 grid((unsigned)((M + 127) / 128), (unsigned)gy, (unsigned)nb);
+    if constexpr (std::is_same<T, float>::value) {
+      if (mode_f32) {
+        k_gemm_mode_f32<<<grid, 256, 0, c->s>>>(g, b0);
+        c->count_launch();
+        continue;
+      }
+    }
     k_gemm<T><<<grid, 256, 0, c->s>>>(g, b0);
     c->count_launch();
   }

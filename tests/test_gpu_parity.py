@@ -511,3 +511,22 @@ def test_lanczos_mixed_fused_matches_oracle(cola, ctx, sides):
         assert me[v] == m
         np.testing.assert_allclose(al[v, :j0], a[:j0], rtol=1e-5)
         np.testing.assert_allclose(be[v, :j0], b[:j0], rtol=1e-5)
+
+
+@pytest.mark.parametrize("shapes", [[(132, 120), (40, 36)], [(128, 128), (128, 128), (128, 128)]],
+                         ids=["ragged", "cube128"])
+def test_matvec_f32_mode_kernel_parity(cola, ctx, shapes):
+    """The FP32 SIMT mode-product kernel (double-buffered 128 x 128 tiles)
+    on shapes with M, N and K tails (132 x 120 and 40 x 36 factors) and on
+    the 128^3 cube, against the oracle's mode products: within 2e-6 of
+    max |A x| (an n-term FP32 dot product per mode)."""
+    r = _rs(600)
+    F = [r.standard_normal(s) / np.sqrt(s[1]) for s in shapes]
+    spec = ("kron", [("dense", f) for f in F])
+    ref = oracle_tree(spec)
+    op = gpu_tree(cola, ctx, spec, torch.float64, DEV)
+    X = r.standard_normal((2, ref.cols))
+    Y = cola.cola_matvec(ctx, op, torch.tensor(X, dtype=torch.float32, device=DEV),
+                         cola.PREC_F32).double().cpu().numpy()
+    Y_ref = ref.mvm(X)
+    assert rel_max_err(Y, Y_ref) < 2e-6

@@ -54,6 +54,54 @@ def cg(op, b, tol=1e-10, maxiter=None, precond_diag=None, x0=None, precond=None)
     return x, it
 
 
+def cg_reorth_residuals(op, b, tol=1e-10, maxiter=None, dtype=np.float64):
+    """Conjugate gradients with re-orthogonalised residuals, the low-precision
+    CG variant of Maddox, Potapczynski & Wilson (UAI 2022) that Sec. 3.4 /
+    App. C.3 cite: every new residual r_{k+1} = r_k - alpha_k A p_k is made
+    orthogonal, by two passes of classical Gram-Schmidt, to all earlier
+    residuals r_0 .. r_k before it enters beta_k = r_{k+1}^T r_{k+1} / r_k^T r_k
+    and p_{k+1} = r_{k+1} + beta_k p_k.  In exact arithmetic CG's residuals are
+    already mutually orthogonal, so the iterates are those of ``cg``; in low
+    precision the projection restores that orthogonality.  Unpreconditioned.
+
+    ``dtype`` is the working precision of the vectors and the MVM (the
+    projections' dot products accumulate in FP64).  Returns (x, iterations,
+    R) with R the (iterations + 1, n) array of the residuals used.
+    """
+    b = np.asarray(b, dtype=np.float64)
+    n = b.shape[0]
+    maxiter = n if maxiter is None else maxiter
+    x = np.zeros(n, dtype=dtype)
+    r = b.astype(dtype)
+    p = r.copy()
+    rr = float(r.astype(np.float64) @ r.astype(np.float64))
+    bnorm = float(np.linalg.norm(b))
+    res = [r.copy()]
+    if bnorm == 0.0:
+        return x.astype(np.float64), 0, np.array(res)
+    it = 0
+    while np.sqrt(rr) > tol * bnorm and it < maxiter:
+        Ap = (op @ p.astype(np.float64)).astype(dtype)
+        pAp = float(p.astype(np.float64) @ Ap.astype(np.float64))
+        if not pAp > 0.0:
+            raise FloatingPointError("CG breakdown: p^T A p <= 0")
+        alpha = rr / pAp
+        x = (x + dtype(alpha) * p).astype(dtype)
+        r = (r - dtype(alpha) * Ap).astype(dtype)
+        for _ in range(2):
+            for q in res:
+                q64 = q.astype(np.float64)
+                c = float(q64 @ r.astype(np.float64)) / float(q64 @ q64)
+                r = (r - dtype(c) * q).astype(dtype)
+        rr_new = float(r.astype(np.float64) @ r.astype(np.float64))
+        beta = rr_new / rr
+        rr = rr_new
+        p = (r + dtype(beta) * p).astype(dtype)
+        res.append(r.copy())
+        it += 1
+    return x.astype(np.float64), it, np.array(res)
+
+
 def true_relative_residual(op, B, X):
     """||b - A x|| / ||b|| per right-hand side (rows of B, X)."""
     B = np.atleast_2d(B)

@@ -207,6 +207,53 @@ def test_cg_matches_dense_lu():
     assert it <= 40
 
 
+def test_cg_reorth_residuals_fp64_is_cg():
+    """In FP64 on a well-conditioned operator the re-orthogonalised CG takes
+    the textbook CG's iterations (exact-arithmetic CG residuals are already
+    orthogonal) and solves the system (dense LU)."""
+    mats = [_spd(4, 11), _spd(5, 12)]
+    op = Sum([Kron([Dense(m) for m in mats]), Diag(0.1, 20)])
+    b = _rs(13).standard_normal(20)
+    x_cg, it = krylov.cg(op, b, tol=1e-12, maxiter=200)
+    x_ro, it_ro, R = krylov.cg_reorth_residuals(op, b, tol=1e-12, maxiter=200)
+    # n = 20: exact-arithmetic CG ends within 20 steps; the textbook
+    # recursion may need one more to absorb rounding
+    assert it_ro <= 20 and abs(it_ro - it) <= 1 and R.shape == (it_ro + 1, 20)
+    np.testing.assert_allclose(x_ro, x_cg, rtol=1e-9)
+    np.testing.assert_allclose(x_ro, exact.dense_solve(op.dense(), b)[0], rtol=1e-9)
+
+
+def test_cg_reorth_residuals_keeps_them_orthogonal_in_fp32():
+    """The point of the variant: in FP32 the residuals it uses stay mutually
+    orthogonal to rounding level (|cos| <= 1e-5) on an ill-conditioned RBF
+    operator (kappa ~ 1e4, clustered small eigenvalues), so it takes within a
+    few iterations of the FP64 re-orthogonalised count (exact arithmetic up to
+    rounding), while even FP64 textbook CG, whose residuals lose
+    orthogonality, needs several times more; the FP32 solution meets the
+    tolerance against a dense LU solve."""
+    x = wl.uniform(5, (24,))
+    y = wl.uniform(6, (20,))
+    op = Sum([Kron([Dense(wl.rbf_factor(x, 0.2)), Dense(wl.rbf_factor(y, 0.2))]),
+              Diag(1e-3, 480)])
+    b = _rs(15).standard_normal(480)
+    _, it64 = krylov.cg(op, b, tol=1e-5, maxiter=2000)
+    _, it64_ro, _ = krylov.cg_reorth_residuals(op, b, tol=1e-5, maxiter=2000)
+    x32, it32, R = krylov.cg_reorth_residuals(op, b, tol=1e-5, maxiter=2000, dtype=np.float32)
+    Q = R.astype(np.float64)
+    Q /= np.linalg.norm(Q, axis=1, keepdims=True)
+    G = Q @ Q.T - np.eye(len(Q))
+    assert np.max(np.abs(G)) <= 1e-5
+    assert abs(it32 - it64_ro) <= 3
+    assert it64 >= 2 * it64_ro
+    # the true residual of an FP32 recursion stalls near u kappa (Higham,
+    # Accuracy and Stability, ch. 12), above the recursive 1e-5
+    lam = np.linalg.eigvalsh(op.dense())
+    kappa = lam.max() / lam.min()
+    u32 = 2.0 ** -24
+    res = np.linalg.norm(b - op @ x32) / np.linalg.norm(b)
+    assert res <= max(1e-5, 10 * u32 * kappa)
+
+
 def test_jacobi_pcg_matches_dense_lu():
     n = 6
     L = wl.dirichlet_laplacian(n)

@@ -883,10 +883,10 @@ def main():
     ap.add_argument("--maxiter", type=int, default=60000)
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--cpu-iters", type=int, default=2)
-    # DRAM bytes of one k_kron_tc_fs launch from its ncu capture (reads + writes)
-    # DRAM bytes of one launch from an ncu capture of the current kernel build; None
-    # (reported as null) since the kernel changed after the last capture
-    ap.add_argument("--traffic-bytes", type=float, default=None)
+    # DRAM bytes (reads + writes) of one k_kron_tc_fs launch of this workload, from
+    # the ncu capture of the current kernel build summarised in
+    # profiles/k_kron_tc_fs_kron3_rbf128_r16.md
+    ap.add_argument("--traffic-bytes", type=float, default=211.26e6)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--batched-only", action="store_true",
                     help="run only the 512-system batched workload (for profiler captures)")

@@ -185,6 +185,16 @@ typedef struct {
                                    positive definite; exclusive with jacobi; another operator
                                    shape is COLA_ERR_UNSUPPORTED.  Graph chunks are capped at
                                    8 iterations. */
+  int32_t reorth_residuals;     /* > 0: CG with re-orthogonalised residuals, the
+                                   low-precision CG variant Sec. 3.4 / App. C.3 cite
+                                   (Maddox, Potapczynski & Wilson 2022): every new residual
+                                   is made orthogonal, by two classical Gram-Schmidt passes,
+                                   to the residuals stored so far (up to this many per
+                                   right-hand side, 1 .. 4096; later ones are projected but
+                                   not stored) before it enters beta and the next direction.
+                                   Workspace reorth_residuals x nrhs x N vector elements.
+                                   Unpreconditioned, without FP64 refinement (refine = 0 for
+                                   F32 / MIXED); COLA_ERR_INVALID_ARG otherwise.  0 = off. */
 } cola_cg_opts;
 
 typedef struct {
@@ -200,7 +210,7 @@ typedef struct {
 /* Fill opts with defaults: tol 1e-8, maxiter 100000, MIXED, refine 1,
  * reliable_delta 0.1, max_updates 200, split terms 3 (factor) / 3 (vector),
  * graph_chunk 64,
- * jacobi 0, x0_given 0, kron_precond 0. */
+ * jacobi 0, x0_given 0, kron_precond 0, reorth_residuals 0. */
 void cola_cg_opts_default(cola_cg_opts* opts);
 
 /* Solve A X = B for nrhs right-hand sides by (preconditioned) conjugate

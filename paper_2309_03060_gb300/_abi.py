@@ -25,7 +25,7 @@ class cola_cg_opts(C.Structure):
                 ("max_updates", C.c_int32), ("split_factor_terms", C.c_int32),
                 ("split_vector_terms", C.c_int32), ("graph_chunk", C.c_int32),
                 ("jacobi", C.c_int32), ("x0_given", C.c_int32),
-                ("kron_precond", C.c_int32)]
+                ("kron_precond", C.c_int32), ("reorth_residuals", C.c_int32)]
 
 
 class cola_cg_info(C.Structure):

@@ -487,6 +487,87 @@ __global__ void k_invert(int64_t n, const double* d, float* out32, double* out64
   }
 }
 
+// ------------------------------------------- re-orthogonalised residuals
+// CG with re-orthogonalised residuals (the low-precision CG variant of
+// Maddox, Potapczynski & Wilson, UAI 2022, that Sec. 3.4 / App. C.3 cite):
+// the stored residuals Q[r][i] (i < k[r]) of each right-hand side; every new
+// residual is made orthogonal to them by classical Gram-Schmidt before it
+// enters beta and the next search direction.
+
+// c[r][i] = Q[r][i] . x_r / ||Q[r][i]||^2 for i < k[r] (0 beyond); one block
+// per (i, r), FP64 block reduction in a fixed order.
+template <typename T>
+__global__ void k_ro_dots(int64_t n, const T* Q, const T* x, const int* k, const double* n2,
+                          int cap, const CgState* st, double* coef) {
+  const int i = blockIdx.x;
+  const int64_t r = blockIdx.y;
+  if (!st[r].active || i >= k[r]) {
+    if (threadIdx.x == 0) coef[r * cap + i] = 0.0;
+    return;
+  }
+  const T* q = Q + ((int64_t)r * cap + i) * n;
+  const T* xr = x + r * n;
+  double acc = 0.0;
+  for (int64_t e = threadIdx.x; e < n; e += blockDim.x) acc += (double)q[e] * (double)xr[e];
+  double unused;
+  acc = block_sum2(acc, &unused, 0.0);
+  if (threadIdx.x == 0) coef[r * cap + i] = acc / n2[r * cap + i];
+}
+
+// x_r -= sum_{i < k[r]} c[r][i] Q[r][i] (the sum in FP64).
+template <typename T>
+__global__ void k_ro_sub(int64_t n, T* x, const T* Q, const int* k, const double* coef,
+                         int cap, const CgState* st) {
+  const int64_t r = blockIdx.y;
+  if (!st[r].active) return;
+  const int kr = k[r];
+  const T* Qr = Q + (int64_t)r * cap * n;
+  const double* cr = coef + (int64_t)r * cap;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    double acc = 0.0;
+    for (int i = 0; i < kr; ++i) acc += cr[i] * (double)Qr[(int64_t)i * n + e];
+    x[r * n + e] = (T)((double)x[r * n + e] - acc);
+  }
+}
+
+// Stores x_r as Q[r][k[r]] (while k[r] < cap) and writes the partials of
+// x_r . x_r as both r^T z and r^T r (unpreconditioned: z = r), in the layout
+// the residual kernels use.
+template <typename T>
+__global__ void k_ro_store(int64_t n, const T* x, T* Q, const int* k, int cap,
+                           const CgState* st, int nblk, double* part_rz, double* part_rr) {
+  const int64_t r = blockIdx.y;
+  if (!st[r].active) return;
+  const int kr = k[r];
+  T* dst = kr < cap ? Q + ((int64_t)r * cap + kr) * n : nullptr;
+  double acc = 0.0;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)nblk * blockDim.x) {
+    const T v = x[r * n + e];
+    if (dst) dst[e] = v;
+    acc += (double)v * (double)v;
+  }
+  double unused;
+  acc = block_sum2(acc, &unused, 0.0);
+  if (threadIdx.x == 0) {
+    part_rz[r * nblk + blockIdx.x] = acc;
+    part_rr[r * nblk + blockIdx.x] = acc;
+  }
+}
+
+// Records ||Q[r][k]||^2 = the r^T r the beta kernel (or the restate) just
+// summed and counts the stored residual; reset = 1 empties the store first.
+__global__ void k_ro_commit(int64_t R, const CgState* st, int* k, double* n2, int cap,
+                            int reset) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= R) return;
+  if (reset) k[r] = 0;
+  if (!st[r].active || k[r] >= cap) return;
+  n2[r * cap + k[r]] = st[r].rr;
+  k[r] += 1;
+}
+
 // ------------------------------------------------------------------ Lanczos
 struct LzState {
   double beta_prev, amax;
@@ -715,7 +796,44 @@ struct CgBufs {
   double* tile_dot;   // per-(tile, warp) partials of p^T A p (MIXED)
   int64_t fused_tiles;  // > 0: the fused tensor-core CG MVM applies
   CgState* st;
+  // re-orthogonalised residuals (ro_cap > 0): store [R][ro_cap][N], their
+  // squared norms and the Gram-Schmidt coefficients [R][ro_cap], counts [R]
+  int ro_cap;
+  T* roQ;
+  double *ro_n2, *ro_c;
+  int* ro_k;
 };
+
+// Re-orthogonalises the residual just formed (two classical Gram-Schmidt
+// passes against the stored residuals), stores it and rewrites the r^T z /
+// r^T r partials the beta kernel reads.
+template <typename T>
+static void ro_project(Ctx* c, CgBufs<T>& B, int64_t N, int64_t R, int nblk) {
+  for (int pass = 0; pass < 2; ++pass) {
+    k_ro_dots<T><<<dim3((unsigned)B.ro_cap, (unsigned)R), 256, 0, c->s>>>(
+        N, B.roQ, B.r, B.ro_k, B.ro_n2, B.ro_cap, B.st, B.ro_c);
+    c->count_launch();
+    k_ro_sub<T><<<dim3(ew_blocks(N), (unsigned)R), 256, 0, c->s>>>(N, B.r, B.roQ, B.ro_k,
+                                                                    B.ro_c, B.ro_cap, B.st);
+    c->count_launch();
+  }
+  k_ro_store<T><<<dim3((unsigned)nblk, (unsigned)R), 256, 0, c->s>>>(
+      N, B.r, B.roQ, B.ro_k, B.ro_cap, B.st, nblk, B.part_rz, B.part_rr);
+  c->count_launch();
+}
+
+// (Re)starts the store with the current residual, after a restate.
+template <typename T>
+static void ro_restart(Ctx* c, CgBufs<T>& B, int64_t N, int64_t R, int nblk) {
+  k_ro_commit<<<(unsigned)((R + 127) / 128), 128, 0, c->s>>>(R, B.st, B.ro_k, B.ro_n2, 0, 1);
+  c->count_launch();
+  k_ro_store<T><<<dim3((unsigned)nblk, (unsigned)R), 256, 0, c->s>>>(
+      N, B.r, B.roQ, B.ro_k, B.ro_cap, B.st, nblk, B.part_rz, B.part_rr);
+  c->count_launch();
+  k_ro_commit<<<(unsigned)((R + 127) / 128), 128, 0, c->s>>>(R, B.st, B.ro_k, B.ro_n2,
+                                                             B.ro_cap, 0);
+  c->count_launch();
+}
 
 static std::string key_of(const char* what, const cola_linop* op, int64_t R, int prec, int extra,
                           uint64_t gen) {
@@ -786,9 +904,15 @@ static void cg_iteration(Ctx* c, const cola_linop* op, CgBufs<T>& B, int64_t N, 
                                                          B.part_rz, B.part_rr);
   c->count_launch();
   precond_z<T>(c, B, N, R, nblk);
+  if (B.ro_cap > 0) ro_project<T>(c, B, N, R, nblk);
   k_cg_beta<<<(unsigned)R, 256, 0, c->s>>>(B.st, B.part_rz, B.part_rr, nblk, delta2, refine,
                                             B.beta_vec);
   c->count_launch();
+  if (B.ro_cap > 0) {
+    k_ro_commit<<<(unsigned)((R + 127) / 128), 128, 0, c->s>>>(R, B.st, B.ro_k, B.ro_n2,
+                                                               B.ro_cap, 0);
+    c->count_launch();
+  }
   if (B.fused_tiles <= 0) {
     k_cg_p<T><<<dim3(ew_blocks(N), (unsigned)R), 256, 0, c->s>>>(N, z_of(B), B.p,
                                                                   B.st);
@@ -885,6 +1009,13 @@ static cola_status cg_run(Ctx* c, cola_linop* op, const void* Bin, void* Xout, i
     B.defer_x = sizeof(T) == 4 && N % 4 == 0;
   }
   B.tile_dot = B.fused_tiles > 0 ? (double*)ws.get("cg.tdot", 8 * 8 * B.fused_tiles * R) : nullptr;
+  B.ro_cap = o.reorth_residuals;
+  if (B.ro_cap > 0) {
+    B.roQ = (T*)ws.get("cg.roQ", sizeof(T) * (size_t)N * R * B.ro_cap);
+    B.ro_n2 = (double*)ws.get("cg.ron2", 8 * (size_t)R * B.ro_cap);
+    B.ro_c = (double*)ws.get("cg.roc", 8 * (size_t)R * B.ro_cap);
+    B.ro_k = (int*)ws.get("cg.rok", 4 * R);
+  }
   COLA_CUDA(cudaMemsetAsync(B.beta_vec, 0, 8 * R, c->s));
   double* bb = (double*)ws.get("cg.bb", 8 * R);
   double* rr64 = (double*)ws.get("cg.rr64", 8 * R);
@@ -945,6 +1076,7 @@ static cola_status cg_run(Ctx* c, cola_linop* op, const void* Bin, void* Xout, i
   k_cg_restate<<<(unsigned)((R + 127) / 128), 128, 0, c->s>>>(
       B.st, B.part_rz, B.part_rr, nblk, R, refine ? rr64 : nullptr, bb, o.tol, 1, nullptr);
   c->count_launch();
+  if (B.ro_cap > 0) ro_restart<T>(c, B, N, R, nblk);
   k_copy_active<T><<<dim3(ew_blocks(N), (unsigned)R), 256, 0, c->s>>>(N, z_of(B), B.p,
                                                                       B.st);
   c->count_launch();
@@ -967,8 +1099,8 @@ static cola_status cg_run(Ctx* c, cola_linop* op, const void* Bin, void* Xout, i
   // everything a captured kernel bakes in is part of the graph key
   auto graph_key = [&] {
     char extra[128];
-    snprintf(extra, sizeof extra, ":%c:d%.17g:s%d%d:p%d", sizeof(T) == 8 ? 'd' : 'f', delta2,
-             o.split_factor_terms, o.split_vector_terms, B.cur);
+    snprintf(extra, sizeof extra, ":%c:d%.17g:s%d%d:p%d:o%d", sizeof(T) == 8 ? 'd' : 'f',
+             delta2, o.split_factor_terms, o.split_vector_terms, B.cur, B.ro_cap);
     return key_of("cg", op, R, prec, (refine ? 1 : 0) | (o.jacobi ? 2 : 0) | (o.kron_precond ? 4 : 0) | (chunk << 3),
                   0) +
            extra;
@@ -1057,6 +1189,8 @@ static cola_status cg_run(Ctx* c, cola_linop* op, const void* Bin, void* Xout, i
     any_active = false;
     for (int64_t r = 0; r < R; ++r) any_active |= hst[r].active != 0;
     if (!any_active) break;
+    // the true residual starts a new store of residuals
+    if (B.ro_cap > 0) ro_restart<T>(c, B, N, R, nblk);
     k_copy_active<T><<<dim3(ew_blocks(N), (unsigned)R), 256, 0, c->s>>>(N, z_of(B),
                                                                         B.p, B.st);
     c->count_launch();
@@ -1113,6 +1247,13 @@ void check_cg_args(const cola_linop* op, const cola_cg_opts* o, int64_t R) {
   COLA_REQUIRE(o->precision >= COLA_PREC_F64 && o->precision <= COLA_PREC_MIXED,
                COLA_ERR_INVALID_ARG, "precision %d", o->precision);
   COLA_REQUIRE(o->tol >= 0.0 && o->maxiter >= 0, COLA_ERR_INVALID_ARG, "tol/maxiter");
+  COLA_REQUIRE(o->reorth_residuals >= 0 && o->reorth_residuals <= 4096, COLA_ERR_INVALID_ARG,
+               "reorth_residuals = %d (0 .. 4096)", o->reorth_residuals);
+  COLA_REQUIRE(o->reorth_residuals == 0 ||
+                   (!o->jacobi && !o->kron_precond &&
+                    (o->precision == COLA_PREC_F64 || !o->refine)),
+               COLA_ERR_INVALID_ARG,
+               "reorth_residuals takes an unpreconditioned solve without FP64 refinement");
   COLA_REQUIRE(o->split_factor_terms >= 1 && o->split_factor_terms <= 3 &&
                    o->split_vector_terms >= 1 && o->split_vector_terms <= 3,
                COLA_ERR_INVALID_ARG, "split terms must be 1..3");
@@ -1205,6 +1346,7 @@ void cola_cg_opts_default(cola_cg_opts* o) {
   o->jacobi = 0;
   o->x0_given = 0;
   o->kron_precond = 0;
+  o->reorth_residuals = 0;
 }
 
 cola_status cola_cg_solve(cola_ctx* ctx, const cola_linop* op, const void* B, void* X,

@@ -53,6 +53,8 @@ def test_opts_defaults(lib):
     assert o.refine == 1 and o.split_factor_terms == 3 and o.split_vector_terms == 3
     assert o.graph_chunk == 64
     assert o.jacobi == 0 and o.x0_given == 0 and o.kron_precond == 0
+    assert o.reorth_residuals == 0
+    assert ctypes.sizeof(o) == 64  # sizeof(cola_cg_opts) in C (fields appended at the end)
 
 
 def test_null_arguments_are_rejected_without_a_device(lib):

@@ -377,11 +377,16 @@ def run_config1(cola, ctx, device, stream):
     (ld, se, _, clamped), t_slq = timed_call(torch, stream, slq)
     exact_ld = cola.cola_kron_eig_logdet(ctx, op)
     it = info[0]["iterations"]
+    steady = steady_iteration_time(
+        cola, ctx, torch, stream, op, B,
+        lambda n: cola.cola_cg_opts_default(precision=cola.PREC_F64, refine=0, tol=0.0,
+                                            maxiter=n, max_updates=0), 64, 192)
     return {"workload": f"{w.name}: K1(x)K2 + 0.1 I, 64-point RBF factors (l 0.2), N = {w.N}, "
                         "1 RHS, CG to 1e-10; SLQ 16 x 50, FP64",
             "bound": "latency (the FP64 working set, ~192 KB, fits on chip)",
             "cg": {"seconds": round(t_cg, 5), "iterations": it, "status": st,
                    "us_per_iteration": round(1e6 * t_cg / max(it, 1), 2),
+                   "us_per_iteration_steady": round(1e6 * steady, 2),
                    "rel_residual": info[0]["rel_residual"]},
             "slq": {"seconds": round(t_slq, 5), "logdets_per_s": round(1.0 / t_slq, 2),
                     "us_per_lanczos_step": round(1e6 * t_slq / w.slq_steps, 2),
@@ -412,11 +417,17 @@ def run_config3(cola, ctx, device, stream, hbm_peak):
     it = max(i["iterations"] for i in info)
     R, N = w.B.shape[0], w.N
     alg = 2.0 * N * 32 * 4 + 2.0 * N * 4 + 32.0 * N * R
-    per_it = t / max(it, 1)
+    per_it = steady_iteration_time(
+        cola, ctx, torch, stream, op, B,
+        lambda n: cola.cola_cg_opts_default(precision=cola.PREC_F32, refine=0, tol=0.0,
+                                            jacobi=1, maxiter=n, graph_chunk=8,
+                                            max_updates=0), 32, 96)
     return {"workload": f"{w.name}: L(+)L + D + U U^T, n 1024 (N = {N}), U 32 columns, "
                         f"{R} RHS, Jacobi PCG FP32 to {w.tol}",
             "seconds": round(t, 5), "iterations": it, "status": st,
-            "solves_per_s": round(R / t, 2), "us_per_iteration": round(1e6 * per_it, 2),
+            "solves_per_s": round(R / t, 2), "us_per_iteration_solve": round(1e6 * t / it, 2),
+            "us_per_iteration": round(1e6 * per_it, 2),
+            "per_iteration": "steady state: difference of 96- and 32-iteration solves",
             "worst_rel_residual": max(i["rel_residual"] for i in info),
             "roofline": {"bound": "hbm", "alg_bytes_per_iteration": alg,
                          "roofline_us": round(1e6 * alg / (hbm_peak * 1e9), 1),
@@ -451,6 +462,10 @@ def run_config5(cola, ctx, device, stream, hbm_peak, tflops):
     it = max(i["iterations"] for i in info)
     per_it = t / max(it, 1)
     N = w.N
+    Xf = torch.randn(R, N, dtype=torch.float32, device=device)
+    Yf = torch.empty_like(Xf)
+    (_, t_mvm) = timed_call(torch, stream, lambda: cola.cola_matvec(
+        ctx, op, Xf, cola.PREC_MIXED, out=Yf, split_terms=3))
     byts = 32.0 * N * R
     flop = 2.0 * N * (1024 + 1024) * R
     roof = max(byts / (hbm_peak * 1e9), flop / (tflops * 1e12))
@@ -462,11 +477,28 @@ def run_config5(cola, ctx, device, stream, hbm_peak, tflops):
                         "us_per_iteration": round(1e6 * per_it, 2),
                         "worst_rel_residual": max(i["rel_residual"] for i in info)},
             "backward_seconds": round(t_bw, 4),
+            "mvm": {"us": round(1e6 * t_mvm, 1),
+                    "tensor_tflops_split": round(6 * 2.0 * N * 2048 * R / t_mvm / 1e12, 1),
+                    "note": "one MIXED MVM of the 33-RHS block (2 mode steps, 6 split MMAs "
+                            "per product)"},
             "grad_s2": float(grads[2].double().sum()),
             "roofline": {"bound": "hbm (algorithmic); near the ridge",
                          "alg_bytes_per_iteration": byts, "alg_flop_per_iteration": flop,
                          "roofline_us": round(1e6 * roof, 1),
                          "frac": round(roof / per_it, 4)}}
+
+
+def steady_iteration_time(cola, ctx, torch, stream, op, B, make_opts, lo, hi):
+    """Seconds per CG iteration in steady state: the difference of two solves
+    that run exactly `hi` and `lo` iterations (tol 0, so they stop at maxiter),
+    which cancels the per-solve set-up (preparation, first restate, final true
+    residual)."""
+    def run(n):
+        return cola.cola_cg_solve(ctx, op, B, make_opts(n), raise_on_error=False)
+    (_, info_hi, _), t_hi = timed_call(torch, stream, lambda: run(hi))
+    (_, info_lo, _), t_lo = timed_call(torch, stream, lambda: run(lo))
+    d_it = max(i["iterations"] for i in info_hi) - max(i["iterations"] for i in info_lo)
+    return (t_hi - t_lo) / max(d_it, 1)
 
 
 def timed_call(torch, stream, fn, warm=True):
@@ -912,6 +944,11 @@ def main():
                     help="also time the N = 4096 FP64, PDE-style and GP-gradient workloads")
     ap.add_argument("--configs-only", action="store_true",
                     help="run only those three workload sections")
+    ap.add_argument("--config", type=int, choices=[1, 3, 5], default=None,
+                    help="run only one of those sections (profiler captures)")
+    ap.add_argument("--slq-only", action="store_true",
+                    help="run only --reps SLQ log-dets (32 probes x 100 steps, MIXED 3x3) "
+                         "of the bench operator (profiler captures)")
     ap.add_argument("--eig", action=argparse.BooleanOptionalAction, default=True,
                     help="also time the eigen-structured direct solve and exact log-det")
     ap.add_argument("--plain", action=argparse.BooleanOptionalAction, default=True,
@@ -923,6 +960,30 @@ def main():
     args = ap.parse_args()
     if args.mvm_only:
         run_mvm_only(args)
+    elif args.slq_only:
+        import torch
+        import paper_2309_03060_gb300 as cola
+        ctx = cola.Context(0)
+        w = wl.config2(nrhs=1)
+        op, _ = build_operator(cola, ctx, w, torch.device("cuda", 0))
+        st = torch.cuda.current_stream()
+        out = []
+        for _ in range(args.reps):
+            (ld, se, _, cl), t = timed_call(torch, st, lambda: cola.cola_slq_logdet(
+                ctx, op, w.slq_probes, w.slq_steps, seed=5, precision=cola.PREC_MIXED,
+                split_terms=(3, 3)), warm=False)
+            out.append(round(t, 4))
+        print(json.dumps({"mode": "slq-only", "seconds": out, "logdet": ld, "clamped": cl}))
+    elif args.config is not None:
+        import torch
+        import paper_2309_03060_gb300 as cola
+        ctx = cola.Context(0)
+        hbm, tflops, _ = peaks()
+        dev, st = torch.device("cuda", 0), torch.cuda.current_stream()
+        fn = {1: lambda: run_config1(cola, ctx, dev, st),
+              3: lambda: run_config3(cola, ctx, dev, st, hbm),
+              5: lambda: run_config5(cola, ctx, dev, st, hbm, tflops)}[args.config]
+        print(json.dumps(fn()))
     elif args.configs_only:
         import torch
         import paper_2309_03060_gb300 as cola

@@ -229,6 +229,35 @@ __global__ void __launch_bounds__(256, 2) k_gemm_mode_f32(GemmP<float> g, int64_
   }
 }
 
+// Small products (the whole C would fill only a few 128 x 128 tiles): one
+// thread per output element, so that the work spreads over many SMs instead
+// of sitting in one block; each thread runs its K-term dot product in order.
+template <typename T>
+__global__ void __launch_bounds__(256) k_gemm_small(GemmP<T> g, int64_t total) {
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t mn = g.M * g.N;
+    const int64_t b = t / mn, rem = t - b * mn;
+    // consecutive threads take consecutive m when A is m-fast, else consecutive n
+    int64_t m, n;
+    if (g.lam == 1) {
+      n = rem / g.M;
+      m = rem - n * g.M;
+    } else {
+      m = rem / g.N;
+      n = rem - m * g.N;
+    }
+    const T* a = g.A + b * g.sA + m * g.lam;
+    const T* bb = g.B + b * g.sB + n * g.lbn;
+    T acc = T(0);
+    for (int64_t k = 0; k < g.K; ++k) acc = fma(a[k * g.lak], bb[k * g.lbk], acc);
+    T* p = g.C + b * g.sC + m * g.lcm + n * g.lcn;
+    T v = g.alpha * acc;
+    if (g.beta != T(0)) v += g.beta * *p;
+    *p = v;
+  }
+}
+
 // Grouped variant: problem blockIdx.z of a device table, same tiling.
 template <typename T>
 __global__ void __launch_bounds__(256) k_gemm_grouped(const GemmDesc<T>* probs) {
@@ -543,6 +572,17 @@ void gemm(Ctx* c, int64_t M, int64_t N, int64_t K, double alpha, const T* A, int
                         ldc_n == 1 && M % 4 == 0 && N % 4 == 0 && lda_k % 4 == 0 &&
                         ldb_n % 4 == 0 && ldc_m % 4 == 0 && sA % 4 == 0 && sB % 4 == 0 &&
                         sC % 4 == 0 && a16(A) && a16(B) && a16(C);
+  // a product that fills fewer than a quarter of the SMs with 128 x 128 tiles
+  // runs one output per thread instead
+  const int64_t tiles = (M + 127) / 128 * gy * batch;
+  const int64_t total = M * N * batch;
+  if (tiles * 4 < c->num_sms && total <= ((int64_t)1 << 24)) {
+    const int grid = (int)std::min<int64_t>((total + 255) / 256, 65535);
+    k_gemm_small<T><<<grid, 256, 0, c->s>>>(g, total);
+    c->count_launch();
+    COLA_CUDA(cudaGetLastError());
+    return;
+  }
   for (int64_t b0 = 0; b0 < batch; b0 += 65535) {
     const int64_t nb = std::min<int64_t>(65535, batch - b0);
     dim3 grid((unsigned)((M + 127) / 128), (unsigned)gy, (unsigned)nb);

@@ -70,6 +70,7 @@ struct TcParams {
   // previous basis vector), before the partial sums of epi_x . Y
   const float* epi_q2;
   const double* epi_gamma;
+  int out_trans;  // 1: store Y[r][i][m] (output index major) instead of Y[r][m][i]
   // optional epilogue (last mode step, output in the input's layout):
   // Y += epi_coeff * d * epi_x (d = epi_d[0] when epi_dstride == 0), and the
   // per-(tile, epilogue warp) partial sums of epi_x . Y go to epi_dot[4 tile + warp]
@@ -549,7 +550,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1) k_kron_tc(Src src, TcParams K) 
             const int i = c0 + e;
             const float dv = p.epi_dstride ? (i < ncols ? p.epi_d[dbase + i] : 0.0f) : p.epi_d[0];
             a[e] = fmaf(p.epi_coeff * dv, xd[e], a[e]);
-            if (gam != 0.0f && i < ncols) a[e] = fmaf(-gam, q2row[i], a[e]);
+            if (gam != 0.0f && i < ncols) a[e] = fmaf(-gam, __ldg(q2row + i), a[e]);
             if (p.beta == 0.0f && i < ncols) dot += (double)(a[e] * xd[e]);
           }
         }
@@ -651,6 +652,7 @@ struct TcFsParams {
   int n_in, n_out, n_pad, kblocks, ksteps_last, xstages, nsrc;
   int img_rows;  // rows per (term, k block) of the split factor image
   int e_mode;  // epilogue: 0 store; 1 fused shift term and p . Ap partials; 2 add beta Y;
+               // 5 store transposed, Y[r][i][m] (output index major: slab-major layout)
                // 3 as 1 with a per-element diagonal
 
   uint32_t x_src_bytes, e_bytes;  // e_bytes: rows staged per tile for e_mode 1 and 2
@@ -768,7 +770,7 @@ __device__ __forceinline__ float fs_store(const float (&a)[64], float* yp, const
         const float xd = es[c * ld];
         const float s = MODE == 3 ? sc * __ldg(dp + c * ld) : sc;
         v = fmaf(s, xd, v);
-        if (MODE == 4 && gam != 0.0f) v = fmaf(-gam, dp[c * ld], v);
+        if (MODE == 4 && gam != 0.0f) v = fmaf(-gam, __ldg(dp + c * ld), v);
         part = fmaf(v, xd, part);
       } else if (MODE == 2) {
         v = fmaf(sc, es[c * ld], v);
@@ -1047,7 +1049,7 @@ __global__ void __launch_bounds__(kThreadsFs, 1) k_kron_tc_fs(const __grid_const
     tc_fence_before();
     mbar_arrive(afac);
     pdl_wait();  // the factor copy above overlaps the previous kernel's tail
-    const bool staged = p.e_mode != 0;
+    const bool staged = p.e_mode != 0 && p.e_mode != 5;
     const float sc = (p.e_mode == 1 || p.e_mode == 4) ? p.e_coeff * p.e_d[0]
                                                       : (p.e_mode == 3 ? p.e_coeff : p.beta);
     int64_t it = 0;
@@ -1075,7 +1077,21 @@ __global__ void __launch_bounds__(kThreadsFs, 1) k_kron_tc_fs(const __grid_const
       const int64_t mbase = m0 + chalf * 64;
       const int nrows = (int)((p.rest - mbase < 64) ? (p.rest - mbase) : 64);
       float part = 0.0f;  // this thread's <= 64 products of p . Ap
-      if (i < p.n_out && nrows > 0) {
+      if (p.e_mode == 5) {
+        // output index i major: this thread's rows m are contiguous
+        if (i < p.n_out && nrows > 0) {
+          float* yt = p.Y + r * p.size_out + (int64_t)i * p.rest + mbase;
+          if (nrows == 64) {
+#pragma unroll
+            for (int c = 0; c < 64; c += 4)
+              *reinterpret_cast<float4*>(yt + c) = make_float4(a[c], a[c + 1], a[c + 2], a[c + 3]);
+          } else {
+#pragma unroll
+            for (int c = 0; c < 64; ++c)
+              if (c < nrows) yt[c] = a[c];
+          }
+        }
+      } else if (i < p.n_out && nrows > 0) {
         const int64_t ld = p.n_out;
         float* yp = p.Y + r * p.size_out + mbase * ld + i;
         const float* es = reinterpret_cast<const float*>(esm) + chalf * 64 * ld + i;
@@ -1097,6 +1113,339 @@ __global__ void __launch_bounds__(kThreadsFs, 1) k_kron_tc_fs(const __grid_const
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) dsum += __shfl_xor_sync(0xffffffffu, dsum, o);
         if (lane == 0) p.epi_dot[t * kDotSlots + ew] = dsum;
+      }
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == kFsMmaWarp) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base),
+                 "r"(512)
+                 : "memory");
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Fused last two mode steps of a three-factor Kronecker MVM with 128 x 128
+// second and third factors (the slab kernel).  The first mode step writes its
+// output slab-major, T[r][i1][j2][j3] (e_mode 5), so every (right-hand side,
+// i1) slab S[j2][j3] is one contiguous 128 x 128 block; this kernel applies
+// K2 S K3^T to a slab with the intermediate kept on chip:
+//   GEMM 1  U^T[i2, j3] = sum_j2 K2[i2, j2] S[j2, j3]   (A = K2 in tensor memory,
+//           B = the split S tile in shared memory, accumulator lane i2)
+//   GEMM 2  Y^T[i3, i2] = sum_j3 K3[i3, j3] U[j3, i2]   (A = K3 in tensor memory,
+//           B = U re-split into BF16 terms by the epilogue, read from lane i2's
+//           accumulator row into a K-major shared-memory operand)
+// and writes Y[r][i1][i2][i3] = c_k Y + c_d s x (x the vector the MVM acts on,
+// in the output's layout) with the per-(slab, epilogue warp) partials of x . Y
+// (the CG step's p . Ap, or Lanczos' q . w after subtracting gamma q_prev).
+// Both factors' split images live in tensor memory (2 x 192 columns), the
+// accumulators are 32 columns wide (dominant and cross terms) and double
+// buffered (128 columns): each GEMM runs as four N = 32 quarter tiles, so the
+// epilogue drains one quarter while the tensor core computes the next.
+//   warps 0-7   converters: read S (global, coalesced), split into BF16 terms,
+//               store the GEMM 1 B operand (K-major, 128-byte swizzle)
+//   warps 8-15  epilogue: factor copies into tensor memory; GEMM 1 drains into
+//               the GEMM 2 B operand; GEMM 2 drains to Y
+//   warp 16     MMA issue, tensor-memory allocation
+constexpr int kSlabN = 128;                       // n2 = n3
+constexpr int kSlabThreads = 32 * (kFsEpiWarps + kFsConvWarps + 1);  // 544
+constexpr uint32_t kSlabF2Col = 0, kSlabF3Col = 192, kSlabAccCol = 384;
+
+struct TcSlabParams {
+  const float* S;        // [nslab][128][128] slab-major first-step output
+  const uint16_t* img2;  // split K2 image [tf][2][img_rows2][64]
+  const uint16_t* img3;  // split K3 image [tf][2][img_rows3][64]
+  int img_rows2, img_rows3;
+  float* Y;              // [nslab][128][128] output, natural layout
+  const float* x;        // vector the MVM acts on (shift term and dot), Y's layout
+  const float* q2;       // optional: Y -= gamma[r] q2 (Lanczos), Y's layout
+  const double* gamma;
+  const float* d;        // shift scalar (device), term c_d d[0] x
+  float coeff, dcoeff;
+  int64_t nslab, slabs_per_rhs;
+  double* dot;           // [nslab][8] partials of x . Y
+  int* err;
+  uint64_t stall_ns;
+};
+
+// Splits 16 FP32 values into TV BF16 terms and stores them as 16 consecutive
+// k positions (two 16-byte chunks, starting at chunk c0) of K-major row `row`
+// of a 128-row B operand with 128-byte swizzle.
+template <int TV>
+__device__ __forceinline__ void slab_put16(unsigned char* bst, int row, int c0, const float* v) {
+  uint32_t w[TV][8];
+#pragma unroll
+  for (int e = 0; e < 8; ++e) {
+    uint32_t o[3];
+    split2(v[2 * e], v[2 * e + 1], TV, o);
+#pragma unroll
+    for (int tv = 0; tv < TV; ++tv) w[tv][e] = o[tv];
+  }
+  unsigned char* rowp = bst + (size_t)row * 128;
+  const uint32_t swz = (uint32_t)(row & 7);
+#pragma unroll
+  for (int tv = 0; tv < TV; ++tv)
+#pragma unroll
+    for (int h = 0; h < 2; ++h)
+      *reinterpret_cast<uint4*>(rowp + (size_t)tv * kFsBTermBytes +
+                                (((uint32_t)(c0 + h) ^ swz) << 4)) =
+          make_uint4(w[tv][4 * h], w[tv][4 * h + 1], w[tv][4 * h + 2], w[tv][4 * h + 3]);
+}
+
+template <int TF, int TV>
+__global__ void __launch_bounds__(kSlabThreads, 1)
+    k_kron_tc_slab(const __grid_constant__ TcSlabParams p) {
+  constexpr int kMaxT = TF > TV ? TF : TV;
+  constexpr bool kSmall = TF > 1 || TV > 1;
+  constexpr uint32_t kKbBytes = (uint32_t)TV * kFsBTermBytes;  // one 64-wide k block, TV terms
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* base = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
+  unsigned char* b1 = base;                 // GEMM 1 B operand: 2 k blocks
+  unsigned char* b2 = base + 2 * kKbBytes;  // GEMM 2 B operand: 2 k blocks
+  uint64_t* bars = (uint64_t*)(base + 4 * kKbBytes);
+  uint64_t* bfull = bars;         // [2] S k block split (converters)
+  uint64_t* bempty = bfull + 2;   // [2] GEMM 1 done with it (MMA commit)
+  uint64_t* b2full = bempty + 2;  // U split (epilogue)
+  uint64_t* b2empty = b2full + 1; // GEMM 2 done with it (MMA commit)
+  uint64_t* afull = b2empty + 1;  // [2] accumulator buffer computed (MMA commit)
+  uint64_t* aempty = afull + 2;   // [2] accumulator buffer drained (epilogue)
+  uint64_t* afac = aempty + 2;    // factor images in tensor memory (epilogue)
+  uint64_t* drain = afac + 1;
+  uint64_t* stall = drain + 1;
+  uint32_t* tmem_slot = (uint32_t*)(stall + 1);
+  volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (tid == 0) {
+    for (int s = 0; s < 2; ++s) {
+      mbar_init(&bfull[s], kFsConvThreads);
+      mbar_init(&bempty[s], 1);
+      mbar_init(&afull[s], 1);
+      mbar_init(&aempty[s], kFsEpiThreads);
+    }
+    mbar_init(b2full, kFsEpiThreads);
+    mbar_init(b2empty, 1);
+    mbar_init(afac, kFsEpiThreads);
+    mbar_init(drain, 1);
+    mbar_init(stall, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == kFsMmaWarp) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(512)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+  pdl_trigger();
+
+  if (warp < kFsConvWarps) {
+    // ------------------------------------------------------------ converters
+    pdl_wait();
+    const int row = (warp & 3) * 32 + lane;  // j3: row of the B operand
+    const int khalf = warp >> 2;             // 32 of the 64 k (= j2) of a block
+    int64_t it = 0;
+    bool ok = true;
+    for (int64_t sl = blockIdx.x; sl < p.nslab && ok; sl += gridDim.x, ++it) {
+      const float* src = p.S + sl * (int64_t)(kSlabN * kSlabN) + row;
+      for (int kb = 0; kb < 2; ++kb) {
+        float v[32];
+        const int k0 = kb * 64 + khalf * 32;
+#pragma unroll
+        for (int e = 0; e < 32; ++e) v[e] = __ldg(src + (int64_t)(k0 + e) * kSlabN);
+        if (!mbar_wait(&bempty[kb], (uint32_t)(it & 1) ^ 1u, abort_flag, p.err)) {
+          ok = false;
+          break;
+        }
+        unsigned char* bst = b1 + (size_t)kb * kKbBytes;
+        slab_put16<TV>(bst, row, khalf * 4, v);
+        slab_put16<TV>(bst, row, khalf * 4 + 2, v + 16);
+        fence_proxy_async();
+        mbar_arrive(&bfull[kb]);
+      }
+    }
+  } else if (warp == kFsMmaWarp) {
+    // ------------------------------------------------------------------- MMA
+    if (lane == 0) {
+      constexpr uint32_t idesc = idesc_bf16(kTileM, 32);  // M = outputs, N = 32 columns
+      bool ok = mbar_wait(afac, 0, abort_flag, p.err);
+      if (ok && p.stall_ns) ok = mbar_wait_slow(stall, 0, abort_flag, p.err, p.stall_ns);
+      tc_fence_after();
+      const uint32_t b1a = smem_u32(b1), b2a = smem_u32(b2);
+      int64_t it = 0, g = 0;  // slab and quarter-tile counters
+      // one quarter tile: N = 32 rows q*32.. of the B operand at bbase, all of K
+      auto quarter = [&](uint32_t bbase, uint32_t acol, int q) -> bool {
+        const int b = (int)(g & 1);
+        const uint32_t u = (uint32_t)((g >> 1) & 1);
+        if (!mbar_wait(&aempty[b], u ^ 1u, abort_flag, p.err)) return false;
+        tc_fence_after();
+        const uint32_t d_dom = tmem_base + kSlabAccCol + (uint32_t)b * 64u;
+        const uint32_t d_small = d_dom + 32u;
+        uint32_t acc_small = 0;
+        for (int kb = 0; kb < 2; ++kb)
+          for (int kk = 0; kk < 4; ++kk) {
+#pragma unroll
+            for (int ti = 0; ti < TF; ++ti)
+#pragma unroll
+              for (int tv = 0; tv < TV; ++tv) {
+                if (ti + tv >= kMaxT) continue;
+                const uint32_t a = tmem_base + acol + (uint32_t)(ti * 64 + kb * 32 + kk * 8);
+                const uint64_t bd = sw128_desc(bbase + (uint32_t)kb * kKbBytes +
+                                               (uint32_t)tv * kFsBTermBytes +
+                                               (uint32_t)q * 4096u + (uint32_t)kk * 32u);
+                if (ti == 0 && tv == 0) {
+                  mma_bf16_ta(d_dom, a, bd, idesc, (kb | kk) ? 1u : 0u);
+                } else {
+                  mma_bf16_ta(d_small, a, bd, idesc, acc_small);
+                  acc_small = 1;
+                }
+              }
+          }
+        mma_commit(&afull[b]);
+        ++g;
+        return true;
+      };
+      for (int64_t sl = blockIdx.x; sl < p.nslab && ok; sl += gridDim.x, ++it) {
+        const uint32_t ph = (uint32_t)(it & 1);
+        if (!mbar_wait(&bfull[0], ph, abort_flag, p.err) ||
+            !mbar_wait(&bfull[1], ph, abort_flag, p.err)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        for (int q = 0; q < 4 && ok; ++q) ok = quarter(b1a, kSlabF2Col, q);
+        if (!ok) break;
+        mma_commit(&bempty[0]);
+        mma_commit(&bempty[1]);
+        if (!mbar_wait(b2full, ph, abort_flag, p.err)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        for (int q = 0; q < 4 && ok; ++q) ok = quarter(b2a, kSlabF3Col, q);
+        if (!ok) break;
+        mma_commit(b2empty);
+      }
+      mma_commit(drain);
+      mbar_wait_own(drain, 0, p.err);
+    }
+    __syncwarp();
+  } else {
+    // -------------------------------------------------------------- epilogue
+    const int ew = warp - kFsConvWarps;         // 0..7
+    const int quarter_l = warp & 3, chalf = ew >> 2;
+    const int i = quarter_l * 32 + lane;        // TMEM lane: i2 (GEMM 1) / i3 (GEMM 2)
+    const uint32_t lane_off = (uint32_t)(quarter_l * 32) << 16;
+    // factor images into tensor memory: k block `chalf` of every term, row i
+#pragma unroll
+    for (int f = 0; f < 2; ++f) {
+      const uint16_t* img = f == 0 ? p.img2 : p.img3;
+      const int rows = f == 0 ? p.img_rows2 : p.img_rows3;
+      const uint32_t col0 = f == 0 ? kSlabF2Col : kSlabF3Col;
+#pragma unroll
+      for (int ti = 0; ti < TF; ++ti) {
+#pragma unroll
+        for (int hh = 0; hh < 2; ++hh) {
+          uint32_t u[16];
+          const uint4* src = reinterpret_cast<const uint4*>(
+              img + ((size_t)(ti * 2 + chalf) * rows + i) * kBlockK);
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            const uint4 qv = __ldg(src + ((hh * 4 + c) ^ (i & 7)));
+            u[4 * c] = qv.x;
+            u[4 * c + 1] = qv.y;
+            u[4 * c + 2] = qv.z;
+            u[4 * c + 3] = qv.w;
+          }
+          tmem_st16(tmem_base + lane_off + col0 + (uint32_t)(ti * 64 + chalf * 32 + hh * 16),
+                    u);
+        }
+      }
+    }
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+    tc_fence_before();
+    mbar_arrive(afac);
+    pdl_wait();
+    const float sc = p.dcoeff * p.d[0];
+    int64_t it = 0, g = 0;
+    bool ok = true;
+    // drains the accumulator quarter of counter g: 16 columns (this thread's
+    // half) of the dominant and cross accumulators, summed
+    auto drain16 = [&](float* a) -> bool {
+      const int b = (int)(g & 1);
+      const uint32_t u = (uint32_t)((g >> 1) & 1);
+      if (!mbar_wait(&afull[b], u, abort_flag, p.err)) return false;
+      tc_fence_after();
+      const uint32_t taddr = tmem_base + lane_off + kSlabAccCol + (uint32_t)b * 64u +
+                             (uint32_t)chalf * 16u;
+      uint32_t v[16], w[16];
+      tmem_ld16(taddr, v);
+      if (kSmall) tmem_ld16(taddr + 32u, w);
+#pragma unroll
+      for (int e = 0; e < 16; ++e)
+        a[e] = __uint_as_float(v[e]) + (kSmall ? __uint_as_float(w[e]) : 0.0f);
+      tc_fence_before();
+      mbar_arrive(&aempty[b]);
+      ++g;
+      return true;
+    };
+    for (int64_t sl = blockIdx.x; sl < p.nslab && ok; sl += gridDim.x, ++it) {
+      const uint32_t ph = (uint32_t)(it & 1);
+      // GEMM 1 quarters -> U split into the GEMM 2 operand (row i2, k = j3)
+      if (!mbar_wait(b2empty, ph ^ 1u, abort_flag, p.err)) break;
+      for (int q = 0; q < 4 && ok; ++q) {
+        float a[16];
+        if (!drain16(a)) {
+          ok = false;
+          break;
+        }
+        // k = j3 = 32 q + 16 chalf .. +15: block q / 2, chunk 4 (q % 2) + 2 chalf
+        slab_put16<TV>(b2 + (size_t)(q >> 1) * kKbBytes, i, 4 * (q & 1) + 2 * chalf, a);
+      }
+      if (!ok) break;
+      fence_proxy_async();
+      mbar_arrive(b2full);
+      // GEMM 2 quarters -> Y rows i2 = 32 q + 16 chalf + c, column i3 = i
+      const int64_t r = sl / p.slabs_per_rhs;
+      const float gam = p.q2 ? (float)p.gamma[r] : 0.0f;
+      const int64_t sbase = sl * (int64_t)(kSlabN * kSlabN) + i;
+      float part = 0.0f;
+      for (int q = 0; q < 4 && ok; ++q) {
+        float a[16];
+        if (!drain16(a)) {
+          ok = false;
+          break;
+        }
+        // read-only loads gathered before the stores (x and q2 never alias Y)
+        const int64_t i0 = sbase + (int64_t)(q * 32 + chalf * 16) * kSlabN;
+        float xv[16], qv[16];
+#pragma unroll
+        for (int c = 0; c < 16; ++c) {
+          xv[c] = __ldg(p.x + i0 + (int64_t)c * kSlabN);
+          qv[c] = gam != 0.0f ? __ldg(p.q2 + i0 + (int64_t)c * kSlabN) : 0.0f;
+        }
+#pragma unroll
+        for (int c = 0; c < 16; ++c) {
+          float y = fmaf(sc, xv[c], p.coeff * a[c]);
+          if (gam != 0.0f) y = fmaf(-gam, qv[c], y);
+          part = fmaf(y, xv[c], part);
+          p.Y[i0 + (int64_t)c * kSlabN] = y;
+        }
+      }
+      if (!ok) break;
+      if (p.dot) {
+        double dsum = (double)part;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) dsum += __shfl_xor_sync(0xffffffffu, dsum, o);
+        if (lane == 0) p.dot[sl * kDotSlots + ew] = dsum;
       }
     }
   }
@@ -1352,6 +1701,10 @@ static bool fs_plan(const TcParams& p, TcFsParams& r) {
     if (r.e_mode != 1) return false;  // the Lanczos term takes the scalar-shift epilogue
     r.e_mode = 4;
   }
+  if (p.out_trans) {
+    if (r.e_mode != 0 || p.rest % 4 != 0) return false;
+    r.e_mode = 5;
+  }
   // a fused shift with a nonzero beta takes the streaming kernel
   if (p.epi_x && p.beta != 0.0f) return false;
   r.e_src = (r.e_mode == 1 || r.e_mode == 3 || r.e_mode == 4) ? p.epi_x
@@ -1375,7 +1728,9 @@ static bool fs_plan(const TcParams& p, TcFsParams& r) {
   r.ksteps_last = p.ksteps_last;
   r.nsrc = p.pro_z ? 2 : 1;
   r.x_src_bytes = (uint32_t)kBlockK * kTileM * 4u;
-  r.e_bytes = r.e_mode ? (((uint32_t)kTileM * (uint32_t)p.n_out * 4u + 1023u) & ~1023u) : 0u;
+  r.e_bytes = (r.e_mode && r.e_mode != 5)
+                  ? (((uint32_t)kTileM * (uint32_t)p.n_out * 4u + 1023u) & ~1023u)
+                  : 0u;
   const size_t avail = kSmemMax - 1024 - 256 - 2 * (size_t)p.tv * kFsBTermBytes - r.e_bytes;
   r.xstages = (int)std::min<size_t>(4, avail / ((size_t)r.nsrc * r.x_src_bytes));
   if (r.xstages < 2) return false;
@@ -1403,6 +1758,17 @@ static FsKernel fs_kernel(int tf, int tv) {
   return tab[tf - 1][tv - 1];
 }
 
+using SlabKernel = void (*)(TcSlabParams);
+static SlabKernel slab_kernel(int tf, int tv) {
+  static const SlabKernel tab[3][3] = {
+      {k_kron_tc_slab<1, 1>, k_kron_tc_slab<1, 2>, k_kron_tc_slab<1, 3>},
+      {k_kron_tc_slab<2, 1>, k_kron_tc_slab<2, 2>, k_kron_tc_slab<2, 3>},
+      {k_kron_tc_slab<3, 1>, k_kron_tc_slab<3, 2>, k_kron_tc_slab<3, 3>}};
+  return tab[tf - 1][tv - 1];
+}
+
+static size_t slab_smem(int tv) { return 1024 + 4 * (size_t)tv * kFsBTermBytes + 256; }
+
 struct TcFusion {
   const float* pro_z = nullptr;
   const double* pro_beta = nullptr;
@@ -1414,6 +1780,8 @@ struct TcFusion {
   double* epi_dot = nullptr;
   const float* epi_q2 = nullptr;
   const double* epi_gamma = nullptr;
+  int out_trans = 0;  // first mode step stores slab-major (the slab kernel's input)
+  int nsteps = -1;    // mode steps to run (-1: all)
 };
 
 // Runs the d mode steps of a Kronecker MVM on the tensor cores; returns the
@@ -1439,12 +1807,13 @@ static int64_t kron_tc_run(Ctx* c, const cola_linop* op, const float* X, float* 
   cur_size = tr ? op->rows : op->cols;
   const float* cur = X;
   int64_t last_tiles = 0;
-  for (int k = 0; k < d; ++k) {
+  const int nsteps = fu.nsteps < 0 ? d : fu.nsteps;
+  for (int k = 0; k < nsteps; ++k) {
     const cola_linop* f = op->kids[k];
     const int n_in = (int)(tr ? f->rows : f->cols), n_out = (int)(tr ? f->cols : f->rows);
     const TcPlan q = make_plan(n_in, n_out, tf, tv);
     const int64_t rest = cur_size / n_in, out_size = rest * n_out;
-    const bool last = (k == d - 1);
+    const bool last = (k == nsteps - 1);
     float* dst = last ? Y : (float*)c->ws.get(depth_name("kron", depth, k & 1), 4 * maxsz * R);
     TcParams p{};
     p.X = cur;
@@ -1483,8 +1852,9 @@ static int64_t kron_tc_run(Ctx* c, const cola_linop* op, const float* X, float* 
       p.pro_z = fu.pro_z;
       p.pro_beta = fu.pro_beta;
       p.pro_out = fu.pro_out;
+      p.out_trans = fu.out_trans;
     }
-    if (last) {
+    if (last && nsteps == d) {
       p.epi_x = fu.epi_x;
       p.epi_d = fu.epi_d;
       p.epi_dstride = fu.epi_dstride;
@@ -1500,9 +1870,12 @@ static int64_t kron_tc_run(Ctx* c, const cola_linop* op, const float* X, float* 
       COLA_CUDA(cudaFuncSetAttribute(k_kron_tc<ProbTable>,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
       for (int a = 1; a <= 3; ++a)
-        for (int b = 1; b <= 3; ++b)
+        for (int b = 1; b <= 3; ++b) {
           COLA_CUDA(cudaFuncSetAttribute(fs_kernel(a, b),
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemMax));
+          COLA_CUDA(cudaFuncSetAttribute(slab_kernel(a, b),
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemMax));
+        }
       attr_set[c->device] = true;
     }
     const int grid = (int)std::min<int64_t>(p.ntiles, c->num_sms);
@@ -1510,6 +1883,8 @@ static int64_t kron_tc_run(Ctx* c, const cola_linop* op, const float* X, float* 
     if (fs_plan(p, rp)) {
       launch_pdl(fs_kernel(tf, tv), dim3(grid), dim3(kThreadsFs), fs_smem(rp, tv), c->s, rp);
     } else {
+      COLA_REQUIRE(!p.out_trans, COLA_ERR_UNSUPPORTED,
+                   "internal: slab-major output needs the factor-stationary kernel");
       k_kron_tc<OneProb><<<grid, kThreadsTc, q.smem, c->s>>>(OneProb{p}, p);
     }
     c->count_launch();
@@ -1524,6 +1899,49 @@ template <>
 void kron_tc_apply<float>(Ctx* c, const cola_linop* op, const float* X, float* Y, int64_t R,
                           double coeff, double beta, int depth, bool tr) {
   kron_tc_run(c, op, X, Y, R, coeff, beta, depth, tr, TcFusion{});
+}
+
+// The slab kernel takes K_1 (x) K_2 (x) K_3 with K_2, K_3 square 128 x 128 and
+// K_1 square of side <= 128 (the first step on the factor-stationary kernel).
+static bool slab_ok(const cola_linop* kron) {
+  if (kron->kind != LK_KRON || kron->kids.size() != 3) return false;
+  const cola_linop* f1 = kron->kids[0];
+  for (int k = 1; k < 3; ++k)
+    if (kron->kids[k]->rows != kSlabN || kron->kids[k]->cols != kSlabN) return false;
+  return f1->rows == f1->cols && f1->rows <= kTileM;
+}
+
+// Steps 2 and 3 of the MVM of c_k Kron + c_d d[0] I from the slab-major first
+// step output T1: Y = c_k (K_2 (x) K_3 per slab) + c_d d[0] x [- gamma q2] and
+// the partials of x . Y.  Returns the slabs per right-hand side (K_1's side).
+static int64_t slab_launch(Ctx* c, const cola_linop* kron, const float* T1, float* Y,
+                           const float* x, const float* q2, const double* gamma, const float* d,
+                           float coeff, float dcoeff, double* dot, int64_t R) {
+  const int tf = (int)kron->derived.at(200).bytes;
+  const int tv = std::max(1, std::min(3, c->split_vector_terms));
+  TcSlabParams sp{};
+  sp.S = T1;
+  sp.img2 = (const uint16_t*)kron->kids[1]->derived.at(100 + tf).p;
+  sp.img3 = (const uint16_t*)kron->kids[2]->derived.at(100 + tf).p;
+  sp.img_rows2 = make_plan(kSlabN, kSlabN, tf, tv).img_rows;
+  sp.img_rows3 = sp.img_rows2;
+  sp.Y = Y;
+  sp.x = x;
+  sp.q2 = q2;
+  sp.gamma = gamma;
+  sp.d = d;
+  sp.coeff = coeff;
+  sp.dcoeff = dcoeff;
+  const int64_t n1 = kron->kids[0]->rows;
+  sp.nslab = R * n1;
+  sp.slabs_per_rhs = n1;
+  sp.dot = dot;
+  sp.err = tc_errflag(c);
+  const int grid = (int)std::min<int64_t>(sp.nslab, c->num_sms);
+  launch_pdl(slab_kernel(tf, tv), dim3(grid), dim3(kSlabThreads), slab_smem(tv), c->s, sp);
+  c->count_launch();
+  COLA_CUDA(cudaGetLastError());
+  return n1;
 }
 
 // One CG MVM for A = c_k * Kron(...) + c_d * Diag(d): the first mode step forms
@@ -1545,6 +1963,19 @@ int64_t kron_tc_cg_mvm(Ctx* c, const cola_linop* op, const float* z, const doubl
   const cola_linop* dg = op->kids[id];
   if (kron->kids.size() < 2 || !tc_supported(kron)) return 0;
   if (kron->derived.find(200) == kron->derived.end()) return 0;
+  if (slab_ok(kron) && dg->stride == 0) {
+    // first mode step (forming p) to a slab-major T1, then steps 2 and 3 fused
+    float* T1 = (float*)c->ws.get(depth_name("kslab", depth, 0), 4 * (size_t)kron->cols * R);
+    TcFusion f1;
+    f1.pro_z = z;
+    f1.pro_beta = beta_vec;
+    f1.pro_out = p_new;
+    f1.out_trans = 1;
+    f1.nsteps = 1;
+    kron_tc_run(c, kron, p_old, T1, R, 1.0, 0.0, depth, false, f1);
+    return slab_launch(c, kron, T1, Ap, p_new, nullptr, nullptr, leaf_ptr<float>(dg),
+                       (float)op->coeffs[ik], (float)op->coeffs[id], tile_dot, R);
+  }
   TcFusion fu;
   fu.pro_z = z;
   fu.pro_beta = beta_vec;
@@ -1578,6 +2009,17 @@ int64_t kron_tc_lanczos_mvm(Ctx* c, const cola_linop* op, const float* w_in,
   const cola_linop* dg = op->kids[id];
   if (kron->kids.size() < 2 || !tc_supported(kron)) return 0;
   if (kron->derived.find(200) == kron->derived.end()) return 0;
+  if (slab_ok(kron)) {
+    float* T1 = (float*)c->ws.get(depth_name("kslab", depth, 0), 4 * (size_t)kron->cols * R);
+    TcFusion f1;
+    f1.pro_beta = scale;
+    f1.pro_out = q_out;
+    f1.out_trans = 1;
+    f1.nsteps = 1;
+    kron_tc_run(c, kron, w_in, T1, R, 1.0, 0.0, depth, false, f1);
+    return slab_launch(c, kron, T1, w_out, q_out, q_prev, gamma, leaf_ptr<float>(dg),
+                       (float)op->coeffs[ik], (float)op->coeffs[id], tile_dot, R);
+  }
   TcFusion fu;
   fu.pro_beta = scale;
   fu.pro_out = q_out;

@@ -6,11 +6,14 @@ Workload: K1 (x) K2 + 1e-3 I with 64- and 48-point RBF factors (l = 0.2,
 N = 3072, kappa ~ 1e4, clustered small eigenvalues), 2 right-hand sides.
 * FP64: the solution matches the oracle's to 1e-9 and the iteration counts
   agree within 1 (the same recursion up to rounding order).
-* MIXED (3 x 3 split-BF16 tensor-core MVM, FP32 vectors), no refinement, to
-  1e-5: the re-orthogonalised solve takes within a few iterations of the
-  oracle's FP64 count (exact arithmetic up to rounding), far fewer than the
-  plain MIXED CG on the same system, and its true residual (oracle MVM) is
-  within the FP32 floor max(tol, 10 u kappa) (Higham ch. 12).
+* MIXED (3 x 3 split-BF16 tensor-core MVM, FP32 vectors), no refinement, the
+  recursion run until its residual meets 1e-5 (max_updates = 0: no
+  verify-and-continue on the true residual, which FP32 cannot bring below
+  about u kappa here): the re-orthogonalised solve takes within a few
+  iterations of the oracle's FP64 count (exact arithmetic up to rounding), at
+  most half the plain MIXED CG's count on the same system, and its true
+  residual (oracle MVM) is within the FP32 floor max(tol, 10 u kappa)
+  (Higham ch. 12).
 """
 import numpy as np
 import pytest
@@ -71,10 +74,11 @@ def test_reorth_cg_mixed_tracks_exact_arithmetic(cola, ctx, problem):
     op = gpu_tree(cola, ctx, spec, torch.float64, DEV).set_spd()
     B32 = torch.tensor(B, dtype=torch.float32, device=DEV)
     common = dict(precision=cola.PREC_MIXED, refine=0, tol=1e-5, maxiter=5000, graph_chunk=16,
-                  split_factor_terms=3, split_vector_terms=3)
+                  split_factor_terms=3, split_vector_terms=3, max_updates=0)
     X, info, st = cola.cola_cg_solve(ctx, op, B32,
-                                     cola.cola_cg_opts_default(reorth_residuals=600, **common))
-    assert st == 0
+                                     cola.cola_cg_opts_default(reorth_residuals=600, **common),
+                                     raise_on_error=False)
+    assert st in (0, 5)  # 5: the FP32 true residual sits above tol (checked below)
     Xp, info_p, st_p = cola.cola_cg_solve(ctx, op, B32, cola.cola_cg_opts_default(**common),
                                           raise_on_error=False)
     ref = oracle_tree(spec)

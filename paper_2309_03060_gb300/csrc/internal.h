@@ -245,6 +245,8 @@ void diag_apply(Ctx* c, const T* d, int64_t stride, const T* X, T* Y, int64_t n,
 template <typename T>
 void stencil_apply(Ctx* c, int nf, const int64_t* sizes, const T* bands, const T* X, T* Y,
                    int64_t R, double coeff, double beta);
+// Blocks of the low-rank V^T X reduction: partials hold kLowRankBlocks * k * R doubles.
+constexpr int kLowRankBlocks = 608;
 template <typename T>
 void lowrank_vtx(Ctx* c, const T* V, const T* X, int64_t n, int64_t k, int64_t R, T* W,
                  double* partials);  // W[k][R] = V^T X^T

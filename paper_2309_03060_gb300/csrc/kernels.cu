@@ -362,6 +362,58 @@ struct StencilP {
 };
 
 // Kronecker sum of tridiagonal factors: y = coeff * sum_k (A_k along mode k) x + beta y.
+// Two-factor Kronecker sum of tridiagonal factors (n1 x n2 grid, rows of n2
+// contiguous): four consecutive i2 of one row per thread, 32-bit indices within
+// a vector; the same terms in the same order as k_stencil.
+template <typename T>
+__global__ void k_stencil2(const T* bands, const T* X, T* Y, int n1, int n2, int64_t R, T coeff,
+                           T beta) {
+  const int q4 = n2 / 4;
+  const int64_t tot = (int64_t)n1 * q4 * R;
+  const T* lo0 = bands;
+  const T* di0 = bands + n1;
+  const T* up0 = bands + 2 * n1;
+  const T* lo1 = bands + 3 * n1;
+  const T* di1 = lo1 + n2;
+  const T* up1 = lo1 + 2 * n2;
+  const int64_t N = (int64_t)n1 * n2;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < tot;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = t / ((int64_t)n1 * q4);
+    const int rem = (int)(t - r * (int64_t)n1 * q4);
+    const int i1 = rem / q4, i2 = (rem - i1 * q4) * 4;
+    const T* x = X + r * N + (int64_t)i1 * n2;
+    T xc[4], xu[4], xd[4];
+    ld4(xc, x + i2);
+    if (i1 > 0) ld4(xu, x + i2 - n2);
+    if (i1 < n1 - 1) ld4(xd, x + i2 + n2);
+    const T xl = i2 > 0 ? x[i2 - 1] : T(0);
+    const T xr = i2 + 4 < n2 ? x[i2 + 4] : T(0);
+    T out[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const int j = i2 + e;
+      T v = T(0);
+      v = fma(di0[i1], xc[e], v);
+      if (i1 > 0) v = fma(lo0[i1], xu[e], v);
+      if (i1 < n1 - 1) v = fma(up0[i1], xd[e], v);
+      v = fma(di1[j], xc[e], v);
+      if (j > 0) v = fma(lo1[j], e > 0 ? xc[e - 1] : xl, v);
+      if (j < n2 - 1) v = fma(up1[j], e < 3 ? xc[e + 1] : xr, v);
+      out[e] = v * coeff;
+    }
+    T* y = Y + r * N + (int64_t)i1 * n2 + i2;
+    if (beta != T(0)) {
+      T yo[4];
+      ld4(yo, y);
+#pragma unroll
+      for (int e = 0; e < 4; ++e) out[e] += beta * yo[e];
+    }
+#pragma unroll
+    for (int e = 0; e < 4; ++e) y[e] = out[e];
+  }
+}
+
 template <typename T>
 __global__ void k_stencil(StencilP p, const T* bands, const T* X, T* Y, int64_t N, int64_t R,
                           T coeff, T beta) {
@@ -391,9 +443,13 @@ __global__ void k_stencil(StencilP p, const T* bands, const T* X, T* Y, int64_t 
 template <typename T>
 __global__ void k_lr_vtx(const T* V, const T* X, int64_t n, int64_t kdim, int64_t R,
                          int nblk, double* part) {
+  // lane = column k of V; a warp walks 32-row tiles, the x entries of the
+  // tile's rows travel by shuffle.  Full tiles load all 32 V rows before
+  // using them (32 independent loads in flight per lane).
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int64_t k0 = (int64_t)blockIdx.y * 32, r0 = (int64_t)blockIdx.z * 8;
   const int64_t col = k0 + lane;
+  const bool col_ok = col < kdim;
   T acc[8];
 #pragma unroll
   for (int q = 0; q < 8; ++q) acc[q] = T(0);
@@ -403,12 +459,22 @@ __global__ void k_lr_vtx(const T* V, const T* X, int64_t n, int64_t kdim, int64_
     T xr[8];
 #pragma unroll
     for (int q = 0; q < 8; ++q)
-      xr[q] = (r0 + q < R && i0 + lane < n) ? X[(r0 + q) * n + i0 + lane] : T(0);
-    const int jmax = (n - i0 < 32) ? (int)(n - i0) : 32;
-    for (int j = 0; j < jmax; ++j) {
-      const T v = (col < kdim) ? V[(i0 + j) * kdim + col] : T(0);
+      xr[q] = (r0 + q < R && i0 + lane < n) ? __ldg(X + (r0 + q) * n + i0 + lane) : T(0);
+    if (i0 + 32 <= n) {
+      T v[32];
 #pragma unroll
-      for (int q = 0; q < 8; ++q) acc[q] = fma(v, __shfl_sync(0xffffffffu, xr[q], j), acc[q]);
+      for (int j = 0; j < 32; ++j) v[j] = col_ok ? __ldg(V + (i0 + j) * kdim + col) : T(0);
+#pragma unroll
+      for (int j = 0; j < 32; ++j)
+#pragma unroll
+        for (int q = 0; q < 8; ++q) acc[q] = fma(v[j], __shfl_sync(0xffffffffu, xr[q], j), acc[q]);
+    } else {
+      const int jmax = (int)(n - i0);
+      for (int j = 0; j < jmax; ++j) {
+        const T v = col_ok ? V[(i0 + j) * kdim + col] : T(0);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) acc[q] = fma(v, __shfl_sync(0xffffffffu, xr[q], j), acc[q]);
+      }
     }
   }
   __shared__ double sh[8][8][32];
@@ -420,18 +486,67 @@ __global__ void k_lr_vtx(const T* V, const T* X, int64_t n, int64_t kdim, int64_
     for (int q = 0; q < 8; ++q) {
       double s = 0.0;
       for (int w = 0; w < nw; ++w) s += sh[w][q][lane];
-      if (col < kdim && r0 + q < R) part[((int64_t)blockIdx.x * kdim + col) * R + r0 + q] = s;
+      if (col_ok && r0 + q < R) part[((int64_t)blockIdx.x * kdim + col) * R + r0 + q] = s;
     }
   }
 }
 
 template <typename T>
 __global__ void k_lr_final(const double* part, int nblk, int64_t cnt, T* W) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  // one warp per output: lane l sums blocks l, l + 32, ...; then a fixed
+  // shuffle tree (run-to-run deterministic)
+  const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
   if (i >= cnt) return;
   double s = 0.0;
-  for (int b = 0; b < nblk; ++b) s += part[(int64_t)b * cnt + i];
-  W[i] = (T)s;
+  for (int b = lane; b < nblk; b += 32) s += part[(int64_t)b * cnt + i];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) W[i] = (T)s;
+}
+
+// k_lr_uw with the block's 256 rows of U staged in shared memory by
+// coalesced loads (row stride kdim + 1 against bank conflicts): thread t then
+// forms row t of Y from shared memory.
+template <typename T>
+__global__ void __launch_bounds__(256) k_lr_uw_staged(const T* U, const T* W, T* Y, int64_t n,
+                                                      int kdim, int64_t R, T coeff, T beta) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* Ws = reinterpret_cast<T*>(smem_raw);
+  T* Us = Ws + (size_t)kdim * R;
+  const int ld = kdim + 1;
+  for (int64_t e = threadIdx.x; e < kdim * R; e += blockDim.x) Ws[e] = W[e];
+  for (int64_t i0 = (int64_t)blockIdx.x * 256; i0 < n; i0 += (int64_t)gridDim.x * 256) {
+    const int rows = (int)((n - i0 < 256) ? (n - i0) : 256);
+    __syncthreads();
+    const T* src = U + i0 * kdim;
+    for (int e = threadIdx.x; e < rows * kdim; e += blockDim.x)
+      Us[(e / kdim) * ld + (e % kdim)] = __ldg(src + e);
+    __syncthreads();
+    const int t = threadIdx.x;
+    if (t < rows) {
+      const T* ur = Us + t * ld;
+      for (int64_t r0 = 0; r0 < R; r0 += 8) {
+        T acc[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) acc[q] = T(0);
+        for (int k = 0; k < kdim; ++k) {
+          const T u = ur[k];
+#pragma unroll
+          for (int q = 0; q < 8; ++q)
+            if (r0 + q < R) acc[q] = fma(u, Ws[k * R + r0 + q], acc[q]);
+        }
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          if (r0 + q >= R) break;
+          T* y = Y + (r0 + q) * n + i0 + t;
+          T v = coeff * acc[q];
+          if (beta != T(0)) v += beta * *y;
+          *y = v;
+        }
+      }
+    }
+  }
 }
 
 // Y[r, i] = coeff * sum_k U[i, k] W[k, r] + beta Y[r, i]; W staged in shared memory.
@@ -691,8 +806,17 @@ void stencil_apply(Ctx* c, int nf, const int64_t* sizes, const T* bands, const T
     p.boff[k] = off;
     off += 3 * sizes[k];
   }
-  k_stencil<T><<<grid_for(N * R, 4), kThreads, 0, c->s>>>(p, bands, X, Y, N, R, (T)coeff,
-                                                          (T)beta);
+  const uintptr_t al = (uintptr_t)X | (uintptr_t)Y;
+  if (nf == 2 && sizes[1] % 4 == 0 && sizes[0] < (1 << 30) && sizes[1] < (1 << 30) &&
+      (al & (4 * sizeof(T) - 1)) == 0) {
+    const int64_t tot = sizes[0] * (sizes[1] / 4) * R;
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((tot + 255) / 256, 152 * 32));
+    k_stencil2<T><<<grid, kThreads, 0, c->s>>>(bands, X, Y, (int)sizes[0], (int)sizes[1], R,
+                                               (T)coeff, (T)beta);
+  } else {
+    k_stencil<T><<<grid_for(N * R, 4), kThreads, 0, c->s>>>(p, bands, X, Y, N, R, (T)coeff,
+                                                            (T)beta);
+  }
   c->count_launch();
   COLA_CUDA(cudaGetLastError());
 }
@@ -701,12 +825,12 @@ template <typename T>
 void lowrank_vtx(Ctx* c, const T* V, const T* X, int64_t n, int64_t k, int64_t R, T* W,
                  double* partials) {
   const int64_t ntiles = (n + 31) / 32;
-  const int nblk = (int)std::max<int64_t>(1, std::min<int64_t>((ntiles + 7) / 8, 256));
+  const int nblk = (int)std::max<int64_t>(1, std::min<int64_t>((ntiles + 7) / 8, kLowRankBlocks));
   dim3 grid(nblk, (unsigned)((k + 31) / 32), (unsigned)((R + 7) / 8));
   k_lr_vtx<T><<<grid, 256, 0, c->s>>>(V, X, n, k, R, nblk, partials);
   c->count_launch();
   const int64_t cnt = k * R;
-  k_lr_final<T><<<(unsigned)((cnt + 255) / 256), 256, 0, c->s>>>(partials, nblk, cnt, W);
+  k_lr_final<T><<<(unsigned)((cnt * 32 + 255) / 256), 256, 0, c->s>>>(partials, nblk, cnt, W);
   c->count_launch();
   COLA_CUDA(cudaGetLastError());
 }
@@ -716,7 +840,13 @@ void lowrank_uw(Ctx* c, const T* U, const T* W, T* Y, int64_t n, int64_t k, int6
                 double coeff, double beta) {
   const size_t smem = sizeof(T) * k * R;
   COLA_REQUIRE(smem <= 48 * 1024, COLA_ERR_UNSUPPORTED, "low-rank: k*nrhs too large");
-  k_lr_uw<T><<<grid_for(n, 1), kThreads, smem, c->s>>>(U, W, Y, n, k, R, (T)coeff, (T)beta);
+  const size_t smem2 = smem + sizeof(T) * 256 * (k + 1);
+  if (smem2 <= 48 * 1024) {
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 152 * 8));
+    k_lr_uw_staged<T><<<grid, 256, smem2, c->s>>>(U, W, Y, n, (int)k, R, (T)coeff, (T)beta);
+  } else {
+    k_lr_uw<T><<<grid_for(n, 1), kThreads, smem, c->s>>>(U, W, Y, n, k, R, (T)coeff, (T)beta);
+  }
   c->count_launch();
   COLA_CUDA(cudaGetLastError());
 }

@@ -279,8 +279,7 @@ void apply(Ctx* c, const cola_linop* op, const T* X, T* Y, int64_t R, double coe
       const T* V = op->data2 ? leaf_ptr<T>(op, true) : U;
       if (tr) std::swap(U, V);
       T* W = tmp<T>(c, "lrW", depth, 0, op->rank * R);
-      const int64_t nblk = 256;
-      double* part = tmp<double>(c, "lrP", depth, 0, nblk * op->rank * R);
+      double* part = tmp<double>(c, "lrP", depth, 0, (int64_t)kLowRankBlocks * op->rank * R);
       lowrank_vtx<T>(c, V, X, op->rows, op->rank, R, W, part);
       lowrank_uw<T>(c, U, W, Y, op->rows, op->rank, R, coeff, beta);
       break;
@@ -488,7 +487,7 @@ static void bil_rec(Ctx* c, const cola_linop* op, const T* Uw, const T* X, int64
       const T* U = leaf_ptr<T>(op);
       const T* V = op->data2 ? leaf_ptr<T>(op, true) : U;
       T* W = tmp<T>(c, "blW", depth, 0, op->rank * R);
-      double* part = tmp<double>(c, "blP", depth, 0, 256 * op->rank * R);
+      double* part = tmp<double>(c, "blP", depth, 0, (int64_t)kLowRankBlocks * op->rank * R);
       lowrank_vtx<T>(c, V, X, op->rows, op->rank, R, W, part);  // W[k][r] = (V^T x_r)_k
       lowrank_grad<T>(c, Uw, W, G, op->rows, op->rank, R, scale);
       if (!op->data2) {

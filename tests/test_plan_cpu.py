@@ -89,3 +89,36 @@ def test_batch_tile_table_edge_cases(lib):
     # invalid chunk cap
     st, *_ = _call(lib, probs, 96)
     assert st == 1
+
+
+def test_oracle_plan_covers_every_output_once_with_fewest_tiles():
+    """Properties any valid table must have, found by search rather than by
+    the plan's own formula: problem i owns one contiguous run of tiles in
+    problem order; that run, spread evenly over its right-hand sides, is the
+    product of the fewest 128-row tiles covering `rest` rows and the fewest
+    chunks of at most `cap` columns (each a multiple of 16, the MMA's N step)
+    covering the n_out output columns, so every output element lies in
+    exactly one tile and no tile is empty."""
+    rng = np.random.default_rng(11)
+    probs = [(int(rng.integers(1, 520)), int(rng.integers(1, 900)), int(rng.integers(1, 9)))
+             for _ in range(60)] + [(16, 128, 1), (17, 129, 2), (128, 256, 1), (129, 1, 3)]
+
+    def fewest(total, width):
+        k = 1
+        while k * width < total:
+            k += 1
+        return k
+
+    for cap in (64, 128):
+        first, tp = plan.tile_table(probs, cap)
+        assert tp == sorted(tp)
+        for i, (n_out, rest, nrhs) in enumerate(probs):
+            count = tp.count(i)
+            assert first[i] == (tp.index(i) if count else len(tp))
+            assert count % nrhs == 0
+            n16 = next(w for w in range(n_out, n_out + 16) if w % 16 == 0)
+            # the fewest chunks whose width (a multiple of 16, <= cap) covers n16
+            chunks = next(k for k in range(1, n16 + 1)
+                          if -(-(-(-n16 // k)) // 16) * 16 <= cap)
+            assert count // nrhs == fewest(rest, 128) * chunks
+            assert chunks == fewest(n16, cap)

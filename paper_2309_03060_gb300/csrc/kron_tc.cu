@@ -1141,10 +1141,9 @@ __global__ void __launch_bounds__(kThreadsFs, 1) k_kron_tc_fs(const __grid_const
 // and writes Y[r][i1][i2][i3] = c_k Y + c_d s x (x the vector the MVM acts on,
 // in the output's layout) with the per-(slab, epilogue warp) partials of x . Y
 // (the CG step's p . Ap, or Lanczos' q . w after subtracting gamma q_prev).
-// Both factors' split images live in tensor memory (2 x 192 columns), the
-// accumulators are 32 columns wide (dominant and cross terms) and double
-// buffered (128 columns): each GEMM runs as four N = 32 quarter tiles, so the
-// epilogue drains one quarter while the tensor core computes the next.
+// Both factors' split images live in tensor memory (2 x 192 columns) and the
+// accumulator (dominant and cross terms, 64 columns each) takes the other 128:
+// each GEMM runs as two N = 64 half tiles, drained by the epilogue in turn.
 //   warps 0-7   converters: read S (global, coalesced), split into BF16 terms,
 //               store the GEMM 1 B operand (K-major, 128-byte swizzle)
 //   warps 8-15  epilogue: factor copies into tensor memory; GEMM 1 drains into
@@ -1275,20 +1274,18 @@ __global__ void __launch_bounds__(kSlabThreads, 1)
   } else if (warp == kFsMmaWarp) {
     // ------------------------------------------------------------------- MMA
     if (lane == 0) {
-      constexpr uint32_t idesc = idesc_bf16(kTileM, 32);  // M = outputs, N = 32 columns
+      constexpr uint32_t idesc = idesc_bf16(kTileM, 64);  // M = outputs, N = 64 columns
       bool ok = mbar_wait(afac, 0, abort_flag, p.err);
       if (ok && p.stall_ns) ok = mbar_wait_slow(stall, 0, abort_flag, p.err, p.stall_ns);
       tc_fence_after();
       const uint32_t b1a = smem_u32(b1), b2a = smem_u32(b2);
-      int64_t it = 0, g = 0;  // slab and quarter-tile counters
-      // one quarter tile: N = 32 rows q*32.. of the B operand at bbase, all of K
-      auto quarter = [&](uint32_t bbase, uint32_t acol, int q) -> bool {
-        const int b = (int)(g & 1);
-        const uint32_t u = (uint32_t)((g >> 1) & 1);
-        if (!mbar_wait(&aempty[b], u ^ 1u, abort_flag, p.err)) return false;
+      int64_t it = 0, g = 0;  // slab and half-tile counters
+      // one half tile: N = 64 rows h*64.. of the B operand at bbase, all of K
+      auto half = [&](uint32_t bbase, uint32_t acol, int h) -> bool {
+        if (!mbar_wait(&aempty[0], (uint32_t)(g & 1) ^ 1u, abort_flag, p.err)) return false;
         tc_fence_after();
-        const uint32_t d_dom = tmem_base + kSlabAccCol + (uint32_t)b * 64u;
-        const uint32_t d_small = d_dom + 32u;
+        const uint32_t d_dom = tmem_base + kSlabAccCol;
+        const uint32_t d_small = d_dom + 64u;
         uint32_t acc_small = 0;
         for (int kb = 0; kb < 2; ++kb)
           for (int kk = 0; kk < 4; ++kk) {
@@ -1300,7 +1297,7 @@ __global__ void __launch_bounds__(kSlabThreads, 1)
                 const uint32_t a = tmem_base + acol + (uint32_t)(ti * 64 + kb * 32 + kk * 8);
                 const uint64_t bd = sw128_desc(bbase + (uint32_t)kb * kKbBytes +
                                                (uint32_t)tv * kFsBTermBytes +
-                                               (uint32_t)q * 4096u + (uint32_t)kk * 32u);
+                                               (uint32_t)h * 8192u + (uint32_t)kk * 32u);
                 if (ti == 0 && tv == 0) {
                   mma_bf16_ta(d_dom, a, bd, idesc, (kb | kk) ? 1u : 0u);
                 } else {
@@ -1309,7 +1306,7 @@ __global__ void __launch_bounds__(kSlabThreads, 1)
                 }
               }
           }
-        mma_commit(&afull[b]);
+        mma_commit(&afull[0]);
         ++g;
         return true;
       };
@@ -1321,7 +1318,7 @@ __global__ void __launch_bounds__(kSlabThreads, 1)
           break;
         }
         tc_fence_after();
-        for (int q = 0; q < 4 && ok; ++q) ok = quarter(b1a, kSlabF2Col, q);
+        for (int h = 0; h < 2 && ok; ++h) ok = half(b1a, kSlabF2Col, h);
         if (!ok) break;
         mma_commit(&bempty[0]);
         mma_commit(&bempty[1]);
@@ -1330,7 +1327,7 @@ __global__ void __launch_bounds__(kSlabThreads, 1)
           break;
         }
         tc_fence_after();
-        for (int q = 0; q < 4 && ok; ++q) ok = quarter(b2a, kSlabF3Col, q);
+        for (int h = 0; h < 2 && ok; ++h) ok = half(b2a, kSlabF3Col, h);
         if (!ok) break;
         mma_commit(b2empty);
       }
@@ -1377,67 +1374,71 @@ __global__ void __launch_bounds__(kSlabThreads, 1)
     const float sc = p.dcoeff * p.d[0];
     int64_t it = 0, g = 0;
     bool ok = true;
-    // drains the accumulator quarter of counter g: 16 columns (this thread's
-    // half) of the dominant and cross accumulators, summed
-    auto drain16 = [&](float* a) -> bool {
-      const int b = (int)(g & 1);
-      const uint32_t u = (uint32_t)((g >> 1) & 1);
-      if (!mbar_wait(&afull[b], u, abort_flag, p.err)) return false;
+    // drains half tile g: 32 columns (this thread's half of the 64) of the
+    // dominant and cross accumulators, summed, then frees the accumulator
+    auto drain32 = [&](float* a) -> bool {
+      if (!mbar_wait(&afull[0], (uint32_t)(g & 1), abort_flag, p.err)) return false;
       tc_fence_after();
-      const uint32_t taddr = tmem_base + lane_off + kSlabAccCol + (uint32_t)b * 64u +
-                             (uint32_t)chalf * 16u;
-      uint32_t v[16], w[16];
-      tmem_ld16(taddr, v);
-      if (kSmall) tmem_ld16(taddr + 32u, w);
+      const uint32_t taddr = tmem_base + lane_off + kSlabAccCol + (uint32_t)chalf * 32u;
 #pragma unroll
-      for (int e = 0; e < 16; ++e)
-        a[e] = __uint_as_float(v[e]) + (kSmall ? __uint_as_float(w[e]) : 0.0f);
+      for (int hh = 0; hh < 2; ++hh) {
+        uint32_t v[16], w[16];
+        tmem_ld16(taddr + (uint32_t)hh * 16u, v);
+        if (kSmall) tmem_ld16(taddr + 64u + (uint32_t)hh * 16u, w);
+#pragma unroll
+        for (int e = 0; e < 16; ++e)
+          a[hh * 16 + e] = __uint_as_float(v[e]) + (kSmall ? __uint_as_float(w[e]) : 0.0f);
+      }
       tc_fence_before();
-      mbar_arrive(&aempty[b]);
+      mbar_arrive(&aempty[0]);
       ++g;
       return true;
     };
     for (int64_t sl = blockIdx.x; sl < p.nslab && ok; sl += gridDim.x, ++it) {
       const uint32_t ph = (uint32_t)(it & 1);
-      // GEMM 1 quarters -> U split into the GEMM 2 operand (row i2, k = j3)
+      // GEMM 1 halves -> U split into the GEMM 2 operand (row i2, k = j3)
       if (!mbar_wait(b2empty, ph ^ 1u, abort_flag, p.err)) break;
-      for (int q = 0; q < 4 && ok; ++q) {
-        float a[16];
-        if (!drain16(a)) {
+      for (int h = 0; h < 2 && ok; ++h) {
+        float a[32];
+        if (!drain32(a)) {
           ok = false;
           break;
         }
-        // k = j3 = 32 q + 16 chalf .. +15: block q / 2, chunk 4 (q % 2) + 2 chalf
-        slab_put16<TV>(b2 + (size_t)(q >> 1) * kKbBytes, i, 4 * (q & 1) + 2 * chalf, a);
+        // k = j3 = 64 h + 32 chalf .. +31: block h, chunks 4 chalf .. 4 chalf + 3
+        slab_put16<TV>(b2 + (size_t)h * kKbBytes, i, 4 * chalf, a);
+        slab_put16<TV>(b2 + (size_t)h * kKbBytes, i, 4 * chalf + 2, a + 16);
       }
       if (!ok) break;
       fence_proxy_async();
       mbar_arrive(b2full);
-      // GEMM 2 quarters -> Y rows i2 = 32 q + 16 chalf + c, column i3 = i
+      // GEMM 2 halves -> Y rows i2 = 64 h + 32 chalf + c, column i3 = i
       const int64_t r = sl / p.slabs_per_rhs;
       const float gam = p.q2 ? (float)p.gamma[r] : 0.0f;
       const int64_t sbase = sl * (int64_t)(kSlabN * kSlabN) + i;
       float part = 0.0f;
-      for (int q = 0; q < 4 && ok; ++q) {
-        float a[16];
-        if (!drain16(a)) {
+      for (int h = 0; h < 2 && ok; ++h) {
+        float a[32];
+        if (!drain32(a)) {
           ok = false;
           break;
         }
-        // read-only loads gathered before the stores (x and q2 never alias Y)
-        const int64_t i0 = sbase + (int64_t)(q * 32 + chalf * 16) * kSlabN;
-        float xv[16], qv[16];
 #pragma unroll
-        for (int c = 0; c < 16; ++c) {
-          xv[c] = __ldg(p.x + i0 + (int64_t)c * kSlabN);
-          qv[c] = gam != 0.0f ? __ldg(p.q2 + i0 + (int64_t)c * kSlabN) : 0.0f;
-        }
+        for (int hh = 0; hh < 2; ++hh) {
+          // read-only loads gathered before the stores (x and q2 never alias Y)
+          const int64_t i0 = sbase + (int64_t)(h * 64 + chalf * 32 + hh * 16) * kSlabN;
+          float xv[16], qv[16];
 #pragma unroll
-        for (int c = 0; c < 16; ++c) {
-          float y = fmaf(sc, xv[c], p.coeff * a[c]);
-          if (gam != 0.0f) y = fmaf(-gam, qv[c], y);
-          part = fmaf(y, xv[c], part);
-          p.Y[i0 + (int64_t)c * kSlabN] = y;
+          for (int c = 0; c < 16; ++c) {
+            xv[c] = __ldg(p.x + i0 + (int64_t)c * kSlabN);
+            qv[c] = gam != 0.0f ? __ldg(p.q2 + i0 + (int64_t)c * kSlabN) : 0.0f;
+          }
+#pragma unroll
+          for (int c = 0; c < 16; ++c) {
+            float y = fmaf(sc, xv[c], p.coeff * a[hh * 16 + c]);
+            if (gam != 0.0f) y = fmaf(-gam, qv[c], y);
+            part = fmaf(y, xv[c], part);
+            p.Y[i0 + (int64_t)c * kSlabN] = y;
+          }
         }
       }
       if (!ok) break;

@@ -1078,8 +1078,32 @@ __global__ void __launch_bounds__(kThreadsFs, 1) k_kron_tc_fs(const __grid_const
       const int nrows = (int)((p.rest - mbase < 64) ? (p.rest - mbase) : 64);
       float part = 0.0f;  // this thread's <= 64 products of p . Ap
       if (p.e_mode == 5) {
-        // output index i major: this thread's rows m are contiguous
-        if (i < p.n_out && nrows > 0) {
+        // output index i major: this thread's rows m are contiguous.  Lanes
+        // 2k and 2k + 1 (outputs i, i + 1) swap half of every 8-value group,
+        // so that each pair of 16-byte stores fills a whole 32-byte sector of
+        // one output row: the even lane stores the first halves, the odd lane
+        // the second halves, of row i and then of row i + 1.
+        const bool full = nrows == 64 && p.n_out % 2 == 0 && i < p.n_out;
+        if (__all_sync(0xffffffffu, full)) {
+          const bool odd = lane & 1;
+          float* y0 = p.Y + r * p.size_out + (int64_t)(i & ~1) * p.rest + mbase;
+#pragma unroll
+          for (int g = 0; g < 8; ++g) {
+            float recv[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e)
+              recv[e] = __shfl_xor_sync(0xffffffffu, odd ? a[8 * g + e] : a[8 * g + 4 + e], 1);
+            const int c0 = 8 * g + (odd ? 4 : 0);
+            const float4 lo = make_float4(a[8 * g], a[8 * g + 1], a[8 * g + 2], a[8 * g + 3]);
+            const float4 hi =
+                make_float4(a[8 * g + 4], a[8 * g + 5], a[8 * g + 6], a[8 * g + 7]);
+            const float4 rv = make_float4(recv[0], recv[1], recv[2], recv[3]);
+            const float4 first = odd ? rv : lo;
+            const float4 second = odd ? hi : rv;
+            *reinterpret_cast<float4*>(y0 + c0) = first;
+            *reinterpret_cast<float4*>(y0 + p.rest + c0) = second;
+          }
+        } else if (i < p.n_out && nrows > 0) {
           float* yt = p.Y + r * p.size_out + (int64_t)i * p.rest + mbase;
           if (nrows == 64) {
 #pragma unroll
@@ -1140,7 +1164,9 @@ __global__ void __launch_bounds__(kThreadsFs, 1) k_kron_tc_fs(const __grid_const
 //           accumulator row into a K-major shared-memory operand)
 // and writes Y[r][i1][i2][i3] = c_k Y + c_d s x (x the vector the MVM acts on,
 // in the output's layout) with the per-(slab, epilogue warp) partials of x . Y
-// (the CG step's p . Ap, or Lanczos' q . w after subtracting gamma q_prev).
+// (Lanczos' q . w after subtracting gamma q_prev; the Q2 = false variant, the
+// CG step's p . Ap, is kept in the code but the CG uses the three-step path,
+// which measured faster for it).
 // Both factors' split images live in tensor memory (2 x 192 columns) and the
 // accumulator (dominant and cross terms, 64 columns each) takes the other 128:
 // each GEMM runs as two N = 64 half tiles, drained by the epilogue in turn.
@@ -1194,7 +1220,7 @@ __device__ __forceinline__ void slab_put16(unsigned char* bst, int row, int c0, 
           make_uint4(w[tv][4 * h], w[tv][4 * h + 1], w[tv][4 * h + 2], w[tv][4 * h + 3]);
 }
 
-template <int TF, int TV>
+template <int TF, int TV, bool Q2>
 __global__ void __launch_bounds__(kSlabThreads, 1)
     k_kron_tc_slab(const __grid_constant__ TcSlabParams p) {
   constexpr int kMaxT = TF > TV ? TF : TV;
@@ -1413,10 +1439,22 @@ __global__ void __launch_bounds__(kSlabThreads, 1)
       mbar_arrive(b2full);
       // GEMM 2 halves -> Y rows i2 = 64 h + 32 chalf + c, column i3 = i
       const int64_t r = sl / p.slabs_per_rhs;
-      const float gam = p.q2 ? (float)p.gamma[r] : 0.0f;
+      const float gam = Q2 ? (float)p.gamma[r] : 0.0f;
       const int64_t sbase = sl * (int64_t)(kSlabN * kSlabN) + i;
       float part = 0.0f;
       for (int h = 0; h < 2 && ok; ++h) {
+        // x of this half's 32 rows: read-only loads issued before the wait for
+        // the half tile, so they overlap its MMAs
+        // (with the Lanczos term: x and q2 of the first 16 rows, the second
+        // 16 after the drain, to stay within the register budget)
+        const int64_t i0 = sbase + (int64_t)(h * 64 + chalf * 32) * kSlabN;
+        constexpr int kPre = Q2 ? 16 : 32;
+        float xv[32], qv[16];
+#pragma unroll
+        for (int c = 0; c < kPre; ++c) {
+          xv[c] = __ldg(p.x + i0 + (int64_t)c * kSlabN);
+          if (Q2) qv[c] = gam != 0.0f ? __ldg(p.q2 + i0 + (int64_t)c * kSlabN) : 0.0f;
+        }
         float a[32];
         if (!drain32(a)) {
           ok = false;
@@ -1424,20 +1462,20 @@ __global__ void __launch_bounds__(kSlabThreads, 1)
         }
 #pragma unroll
         for (int hh = 0; hh < 2; ++hh) {
-          // read-only loads gathered before the stores (x and q2 never alias Y)
-          const int64_t i0 = sbase + (int64_t)(h * 64 + chalf * 32 + hh * 16) * kSlabN;
-          float xv[16], qv[16];
+          if (Q2 && hh == 1) {
 #pragma unroll
-          for (int c = 0; c < 16; ++c) {
-            xv[c] = __ldg(p.x + i0 + (int64_t)c * kSlabN);
-            qv[c] = gam != 0.0f ? __ldg(p.q2 + i0 + (int64_t)c * kSlabN) : 0.0f;
+            for (int c = 0; c < 16; ++c) {
+              xv[16 + c] = __ldg(p.x + i0 + (int64_t)(16 + c) * kSlabN);
+              qv[c] = gam != 0.0f ? __ldg(p.q2 + i0 + (int64_t)(16 + c) * kSlabN) : 0.0f;
+            }
           }
 #pragma unroll
           for (int c = 0; c < 16; ++c) {
-            float y = fmaf(sc, xv[c], p.coeff * a[hh * 16 + c]);
-            if (gam != 0.0f) y = fmaf(-gam, qv[c], y);
-            part = fmaf(y, xv[c], part);
-            p.Y[i0 + (int64_t)c * kSlabN] = y;
+            const int cc = hh * 16 + c;
+            float y = fmaf(sc, xv[cc], p.coeff * a[cc]);
+            if (Q2) y = fmaf(-gam, qv[c], y);
+            part = fmaf(y, xv[cc], part);
+            p.Y[i0 + (int64_t)cc * kSlabN] = y;
           }
         }
       }
@@ -1762,9 +1800,9 @@ static FsKernel fs_kernel(int tf, int tv) {
 using SlabKernel = void (*)(TcSlabParams);
 static SlabKernel slab_kernel(int tf, int tv) {
   static const SlabKernel tab[3][3] = {
-      {k_kron_tc_slab<1, 1>, k_kron_tc_slab<1, 2>, k_kron_tc_slab<1, 3>},
-      {k_kron_tc_slab<2, 1>, k_kron_tc_slab<2, 2>, k_kron_tc_slab<2, 3>},
-      {k_kron_tc_slab<3, 1>, k_kron_tc_slab<3, 2>, k_kron_tc_slab<3, 3>}};
+      {k_kron_tc_slab<1, 1, true>, k_kron_tc_slab<1, 2, true>, k_kron_tc_slab<1, 3, true>},
+      {k_kron_tc_slab<2, 1, true>, k_kron_tc_slab<2, 2, true>, k_kron_tc_slab<2, 3, true>},
+      {k_kron_tc_slab<3, 1, true>, k_kron_tc_slab<3, 2, true>, k_kron_tc_slab<3, 3, true>}};
   return tab[tf - 1][tv - 1];
 }
 
@@ -1939,6 +1977,8 @@ static int64_t slab_launch(Ctx* c, const cola_linop* kron, const float* T1, floa
   sp.dot = dot;
   sp.err = tc_errflag(c);
   const int grid = (int)std::min<int64_t>(sp.nslab, c->num_sms);
+  COLA_REQUIRE(q2 != nullptr, COLA_ERR_INVALID_ARG, "internal: the slab kernel takes the "
+               "Lanczos term");
   launch_pdl(slab_kernel(tf, tv), dim3(grid), dim3(kSlabThreads), slab_smem(tv), c->s, sp);
   c->count_launch();
   COLA_CUDA(cudaGetLastError());
@@ -1964,19 +2004,8 @@ int64_t kron_tc_cg_mvm(Ctx* c, const cola_linop* op, const float* z, const doubl
   const cola_linop* dg = op->kids[id];
   if (kron->kids.size() < 2 || !tc_supported(kron)) return 0;
   if (kron->derived.find(200) == kron->derived.end()) return 0;
-  if (slab_ok(kron) && dg->stride == 0) {
-    // first mode step (forming p) to a slab-major T1, then steps 2 and 3 fused
-    float* T1 = (float*)c->ws.get(depth_name("kslab", depth, 0), 4 * (size_t)kron->cols * R);
-    TcFusion f1;
-    f1.pro_z = z;
-    f1.pro_beta = beta_vec;
-    f1.pro_out = p_new;
-    f1.out_trans = 1;
-    f1.nsteps = 1;
-    kron_tc_run(c, kron, p_old, T1, R, 1.0, 0.0, depth, false, f1);
-    return slab_launch(c, kron, T1, Ap, p_new, nullptr, nullptr, leaf_ptr<float>(dg),
-                       (float)op->coeffs[ik], (float)op->coeffs[id], tile_dot, R);
-  }
+  // (the slab kernel is not used here: for the CG step, whose first mode step
+  // also forms p from two input streams, the three-step path measured faster)
   TcFusion fu;
   fu.pro_z = z;
   fu.pro_beta = beta_vec;

@@ -533,13 +533,13 @@ def test_matvec_f32_mode_kernel_parity(cola, ctx, shapes):
 
 
 def test_cg_and_lanczos_mixed_slab_path(cola, ctx):
-    """K1 (x) K2 (x) K3 + 0.02 I with 128 x 128 second and third factors runs
-    its fused CG and Lanczos MVMs through the slab kernel (steps 2 and 3 of the
-    Kronecker product on chip per (right-hand side, i1) slab): a MIXED 3 x 3 CG
-    with FP64 refinement reaches 1e-8 (oracle FP64 true residual) and matches
-    the exact eigen-structured solve within the forward-error bound, and the
-    Lanczos coefficients match the oracle's on the same probes for the steps
-    before orthogonality is lost."""
+    """K1 (x) K2 (x) K3 + 0.02 I with 128 x 128 second and third factors: the
+    fused Lanczos MVM runs through the slab kernel (steps 2 and 3 of the
+    Kronecker product on chip per (right-hand side, i1) slab) and its
+    coefficients match the oracle's on the same probes for the steps before
+    orthogonality is lost; the fused three-step CG on the same operator (MIXED
+    3 x 3 with FP64 refinement) reaches 1e-8 (oracle FP64 true residual) and
+    matches the exact eigen-structured solve within the forward-error bound."""
     sides = (24, 128, 128)
     F = [wl.rbf_factor(wl.uniform(wl.substream(610, k), (n,)), 0.15) for k, n in enumerate(sides)]
     N = int(np.prod(sides))

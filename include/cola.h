@@ -440,6 +440,35 @@ cola_status cola_logdet_backward(cola_ctx* ctx, const cola_linop* op, const void
                                  void* const* grads, int32_t accumulate,
                                  const cola_cg_opts* opts, cola_stream stream);
 
+/* GP training objective (Sec. 4 GP application; App. D GP training):
+ *   L = 1/2 y^T A^-1 y + 1/2 log det A.
+ * Solves the block [y, z_1 .. z_m] (1 + nprobes right-hand sides) with opts
+ * in one CG call (the probes share the solve, App. D), takes y^T A^-1 y from
+ * the first solution (FP64 reduction) and log det A by SLQ (App. A.2) on the
+ * same probes Z with slq_steps Lanczos steps, and returns L in *value.
+ * y [N], Z [nprobes][N] and Sol [1 + nprobes][N] (written: A^-1 [y, Z]) follow
+ * the dtype rule of cola_cg_solve (FP64 when precision is F64 or refine = 1,
+ * FP32 else).  value, logdet, logdet_se: HOST doubles (the last two may be
+ * NULL); info: HOST, 1 + nprobes entries, may be NULL.  Returns the solve's
+ * status (COLA_ERR_NOT_CONVERGED with everything still written).  Synchronous. */
+cola_status cola_gp_objective(cola_ctx* ctx, const cola_linop* op, const void* y, const void* Z,
+                              int64_t nprobes, int32_t slq_steps, const cola_cg_opts* opts,
+                              void* Sol, double* value, double* logdet, double* logdet_se,
+                              cola_cg_info* info, cola_stream stream);
+
+/* Backward of cola_gp_objective scaled by g = dLoss/dL (App. B.2 rules 1 and
+ * 4 with the Hutchinson trace of App. B.1): for every leaf theta,
+ *   grads[l] = g (-1/2 a^T (dA/dtheta) a + 1/2 (1/m) sum_k u_k^T (dA/dtheta) z_k),
+ * a = Sol[0], u_k = Sol[k] (m = nprobes), in the leaf's shape and dtype, and
+ * grad_y = g a.  Sol and Z are FP64 for precision F64 and FP32 for F32 (the
+ * contraction precision; FP64 keeps the cancelling lengthscale terms exact).
+ * grads: HOST array of num_leaves device pointers (NULL entries, or grads
+ * NULL, skip leaves); grad_y: device [N] or NULL.  Asynchronous. */
+cola_status cola_gp_objective_backward(cola_ctx* ctx, const cola_linop* op, const void* Sol,
+                                       const void* Z, int64_t nprobes, double g,
+                                       int32_t precision, void* const* grads, void* grad_y,
+                                       cola_stream stream);
+
 /* ------------------------------------------------------------- utilities */
 
 /* Fill out [count] (device, FP64 or FP32 by dtype) with Rademacher signs of

@@ -442,6 +442,40 @@ def cola_bilinear_grad(ctx: Context, op: LinOp, U: torch.Tensor, X: torch.Tensor
     return grads
 
 
+def cola_gp_objective(ctx: Context, op: LinOp, y: torch.Tensor, Z: torch.Tensor,
+                      slq_steps: int, opts: cola_cg_opts | None = None):
+    """L = 1/2 y^T A^-1 y + 1/2 log det A.  Returns (L, Sol = A^-1 [y, Z],
+    logdet, logdet standard error, info list, status)."""
+    opts = opts or cola_cg_opts_default()
+    want = _vec_dtype(opts.precision, bool(opts.refine))
+    if y.dtype != want or Z.dtype != want:
+        raise TypeError(f"this precision/refine setting needs {want} vectors")
+    m = Z.shape[0]
+    N = y.numel()
+    Sol = torch.empty((1 + m, N), dtype=want, device=y.device)
+    info = (cola_cg_info * (1 + m))()
+    v, ld, se = C.c_double(), C.c_double(), C.c_double()
+    st = _lib().cola_gp_objective(ctx.handle, op.handle, _ptr(y.contiguous()), _ptr(Z.contiguous()),
+                                  m, int(slq_steps), C.byref(opts), _ptr(Sol), C.byref(v),
+                                  C.byref(ld), C.byref(se), info, _stream())
+    if st not in (0, 5):
+        check(st)
+    return v.value, Sol, ld.value, se.value, _info_list(info, 1 + m), st
+
+
+def cola_gp_objective_backward(ctx: Context, op: LinOp, Sol: torch.Tensor, Z: torch.Tensor,
+                               g: float, precision: int = PREC_F64, leaf_dtypes=None):
+    """(leaf gradients, grad_y) of g * L from the forward solution block."""
+    m = Z.shape[0]
+    nl = len(op.leaves())
+    grads = _leaf_grad_buffers(op, leaf_dtypes or [Sol.dtype] * nl, Sol.device)
+    gy = torch.empty(Sol.shape[1], dtype=Sol.dtype, device=Sol.device)
+    check(_lib().cola_gp_objective_backward(
+        ctx.handle, op.handle, _ptr(Sol), _ptr(Z), m, float(g), precision,
+        (C.c_void_p * nl)(*[t.data_ptr() for t in grads]), _ptr(gy), _stream()))
+    return grads, gy
+
+
 def cola_solve_backward(ctx: Context, op: LinOp, X: torch.Tensor, gradX: torch.Tensor,
                         opts: cola_cg_opts | None = None, leaf_dtypes=None):
     """Returns (gradB, leaf grads, info, status)."""

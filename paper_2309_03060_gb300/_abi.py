@@ -83,6 +83,10 @@ SIGNATURES = {
     "cola_set_split_terms": (I32, [P, I32, I32]),
     "cola_test_stall_next_launch": (I32, [P, I64]),
     "cola_kron_eigs": (I32, [P, P, P, P, P, P]),
+    "cola_gp_objective": (I32, [P, P, P, P, I64, I32, C.POINTER(cola_cg_opts), P,
+                                C.POINTER(D), C.POINTER(D), C.POINTER(D),
+                                C.POINTER(cola_cg_info), P]),
+    "cola_gp_objective_backward": (I32, [P, P, P, P, I64, D, I32, PP, P, P]),
     "cola_kron_matvec_noalloc": (I32, [C.c_int, C.POINTER(I64), C.POINTER(I64), PP, P, P, I64, P]),
 }
 

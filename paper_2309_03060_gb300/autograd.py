@@ -4,10 +4,10 @@
   the same kernels) and, for every leaf theta of A,
   dL/dtheta = -(A^-T gradX)^T (dA/dtheta) X  (rule 1).  Only X is saved; no
   Krylov iterate is stored.
-* ``gp_objective``: L = 1/2 y^T A^-1 y + 1/2 log det A.  The forward solves
-  [y, z_1 .. z_m] as one block (the probes reuse the solve, App. D GP
-  training) and estimates log det A by SLQ; the backward is one weighted
-  bilinear-gradient call:
+* ``gp_objective``: L = 1/2 y^T A^-1 y + 1/2 log det A (cola_gp_objective).
+  The forward solves [y, z_1 .. z_m] as one block (the probes reuse the
+  solve, App. D GP training) and estimates log det A by SLQ; the backward
+  (cola_gp_objective_backward) is one weighted bilinear-gradient call:
       dL/dtheta = -1/2 a^T (dA/dtheta) a + 1/2 (1/m) sum_k u_k^T (dA/dtheta) z_k,
   a = A^-1 y, u_k = A^-1 z_k (rules 1 and 4 with the Hutchinson trace of App. B.1),
   and dL/dy = a.
@@ -20,8 +20,8 @@ from __future__ import annotations
 
 import torch
 
-from . import (PREC_F64, ColaError, cola_bilinear_grad, cola_cg_opts_default, cola_cg_solve,
-               cola_slq_logdet, cola_solve_backward)
+from . import (PREC_F64, ColaError, cola_cg_opts_default, cola_cg_solve, cola_gp_objective,
+               cola_gp_objective_backward, cola_solve_backward)
 
 
 def _require_converged(st, info):
@@ -64,48 +64,38 @@ def solve(cctx, op, B, leaves, opts=None):
 
 class _GPObjective(torch.autograd.Function):
     @staticmethod
-    def forward(fctx, cctx, op, opts, Z, slq_steps, seed, y, *leaves):
-        m = Z.shape[0]
-        block = torch.cat([y.detach().reshape(1, -1), Z], dim=0).contiguous()
-        Sol, info, st = cola_cg_solve(cctx, op, block, opts)
+    def forward(fctx, cctx, op, opts, Z, slq_steps, y, *leaves):
+        want = torch.float64 if (opts.precision == PREC_F64 or opts.refine) else torch.float32
+        Zs = Z.to(want).contiguous()
+        val, Sol, ld, se, info, st = cola_gp_objective(
+            cctx, op, y.detach().reshape(-1).to(want).contiguous(), Zs, slq_steps, opts)
         _require_converged(st, info)
-        a = Sol[0]
-        quad = 0.5 * torch.dot(y.detach().reshape(-1).to(a.dtype), a)
-        prec = opts.precision
-        # the SLQ log-det and the Hutchinson gradient use the same probes Z
-        ld, se, _, _ = cola_slq_logdet(cctx, op, m, slq_steps, seed=seed,
-                                       probes=Z.to(torch.float64 if prec == PREC_F64 else
-                                                   torch.float32).contiguous(),
-                                       precision=prec)
-        fctx.cctx, fctx.op, fctx.opts = cctx, op, opts
-        fctx.save_for_backward(Sol, Z)
+        fctx.cctx, fctx.op = cctx, op
+        fctx.save_for_backward(Sol, Zs)
         fctx.leaf_meta = [(l.shape, l.dtype) for l in leaves]
+        fctx.y_meta = (y.shape, y.dtype)
         fctx.logdet, fctx.logdet_se, fctx.info = ld, se, info
-        return quad + 0.5 * torch.tensor(ld, dtype=quad.dtype, device=quad.device)
+        return torch.tensor(val, dtype=y.dtype, device=y.device)
 
     @staticmethod
     def backward(fctx, g):
-        Sol, Z = fctx.saved_tensors
-        m = Z.shape[0]
-        U = Sol                                     # [a, u_1 .. u_m]
-        Xr = torch.cat([Sol[:1], Z.to(Sol.dtype)], dim=0).contiguous()
-        w = [-0.5] + [0.5 / m] * m
+        Sol, Zs = fctx.saved_tensors
         # FP64 contractions whenever the solve returned FP64 vectors: the
         # lengthscale gradients are differences of O(1e7) terms
         prec = PREC_F64 if Sol.dtype == torch.float64 else 1
-        Uw = U if prec == PREC_F64 else U.float().contiguous()
-        Xw = Xr if prec == PREC_F64 else Xr.float().contiguous()
-        grads = cola_bilinear_grad(fctx.cctx, fctx.op, Uw.contiguous(), Xw, w, prec,
-                                   leaf_dtypes=[d for _, d in fctx.leaf_meta])
-        gs = float(g)
-        lg = [gs * gr.reshape(s) for gr, (s, _) in zip(grads, fctx.leaf_meta)]
-        return (None, None, None, None, None, None, gs * Sol[0], *lg)
+        grads, gy = cola_gp_objective_backward(
+            fctx.cctx, fctx.op, Sol, Zs, float(g), prec,
+            leaf_dtypes=[d for _, d in fctx.leaf_meta])
+        lg = [gr.reshape(s) for gr, (s, _) in zip(grads, fctx.leaf_meta)]
+        ys, yd = fctx.y_meta
+        return (None, None, None, None, None, gy.reshape(ys).to(yd), *lg)
 
 
 def gp_objective(cctx, op, y, leaves, Z, opts=None, slq_steps=30, seed=0):
-    """L = 1/2 y^T A^-1 y + 1/2 log det A with the adjoint backward above.
+    """L = 1/2 y^T A^-1 y + 1/2 log det A with the adjoint backward above (both
+    computed by the library: cola_gp_objective / cola_gp_objective_backward).
     ``Z`` holds the Rademacher probes (nprobes x N) shared by the trace
-    estimate of the gradient and the SLQ log-det (``seed`` is not used to draw
-    probes: both estimates always take Z)."""
+    estimate of the gradient and the SLQ log-det; ``seed`` is accepted for
+    compatibility and not used (both estimates always take Z)."""
     opts = opts or cola_cg_opts_default()
-    return _GPObjective.apply(cctx, op, opts, Z, slq_steps, seed, y, *leaves)
+    return _GPObjective.apply(cctx, op, opts, Z, slq_steps, y, *leaves)

@@ -9,6 +9,7 @@
 //  * many independent systems (one CG per system, driven in turn).
 #include <string.h>
 
+#include <algorithm>
 #include <vector>
 
 #include "internal.h"
@@ -53,11 +54,100 @@ cola_status batched_cg_impl(Ctx* c, int32_t nsys, const cola_linop* const* ops,
   return worst;
 }
 
+template <typename T>
+__global__ void k_scaled_copy(int64_t n, const T* src, double g, T* dst) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    dst[i] = (T)(g * (double)src[i]);
+}
+
 }  // namespace cola
 
 using namespace cola;
 
 extern "C" {
+
+cola_status cola_gp_objective(cola_ctx* ctx, const cola_linop* op, const void* y, const void* Z,
+                              int64_t nprobes, int32_t slq_steps, const cola_cg_opts* opts,
+                              void* Sol, double* value, double* logdet, double* logdet_se,
+                              cola_cg_info* info, cola_stream stream) {
+  cola_status result = COLA_OK;
+  cola_status st = guard([&] {
+    COLA_REQUIRE(ctx && op && y && Z && opts && Sol && value, COLA_ERR_INVALID_ARG,
+                 "NULL argument");
+    COLA_REQUIRE(nprobes >= 1 && slq_steps >= 1, COLA_ERR_INVALID_ARG, "nprobes / slq_steps");
+    check_cg_args(op, opts, 1 + nprobes);
+    StreamJoin j(ctx, stream);
+    const int64_t N = op->rows, R = 1 + nprobes;
+    const bool io64 = (opts->precision == COLA_PREC_F64) || opts->refine;
+    const size_t es = io64 ? 8 : 4;
+    // the block [y, z_1 .. z_m]: one solve for the data term and the probes
+    char* block = (char*)ctx->ws.get("gp.block", es * N * R);
+    COLA_CUDA(cudaMemcpyAsync(block, y, es * N, cudaMemcpyDeviceToDevice, ctx->s));
+    COLA_CUDA(cudaMemcpyAsync(block + es * N, Z, es * N * nprobes, cudaMemcpyDeviceToDevice,
+                              ctx->s));
+    cola_cg_opts o = *opts;
+    o.x0_given = 0;
+    result = cg_solve_impl(ctx, op, block, Sol, R, o, info);
+    // y^T A^-1 y (deterministic FP64 reduction of the working-precision products)
+    double* part = (double*)ctx->ws.get("gp.part", 8 * (size_t)dot_blocks(N));
+    double* quad_d = (double*)ctx->ws.get("gp.quad", 8);
+    if (io64)
+      dots<double>(ctx, (const double*)y, (const double*)Sol, N, 1, part, quad_d);
+    else
+      dots<float>(ctx, (const float*)y, (const float*)Sol, N, 1, part, quad_d);
+    double quad = 0.0;
+    COLA_CUDA(cudaMemcpyAsync(&quad, quad_d, 8, cudaMemcpyDeviceToHost, ctx->s));
+    COLA_CUDA(cudaStreamSynchronize(ctx->s));
+    // log det A by SLQ on the same probes (FP32 probes for F32 / MIXED)
+    const bool f64 = opts->precision == COLA_PREC_F64;
+    const void* probes = as_working(ctx, Z, N * nprobes, io64, f64, "gp.Z");
+    double ld = 0.0, se = 0.0;
+    int clamped = 0;
+    slq_impl(ctx, op, (int)nprobes, slq_steps, 0, probes, opts->precision, 0, &ld, &se, nullptr,
+             &clamped);
+    *value = 0.5 * quad + 0.5 * ld;
+    if (logdet) *logdet = ld;
+    if (logdet_se) *logdet_se = se;
+  });
+  return st != COLA_OK ? st : result;
+}
+
+cola_status cola_gp_objective_backward(cola_ctx* ctx, const cola_linop* op, const void* Sol,
+                                       const void* Z, int64_t nprobes, double g,
+                                       int32_t precision, void* const* grads, void* grad_y,
+                                       cola_stream stream) {
+  return guard([&] {
+    COLA_REQUIRE(ctx && op && Sol && Z, COLA_ERR_INVALID_ARG, "NULL argument");
+    COLA_REQUIRE(nprobes >= 1, COLA_ERR_INVALID_ARG, "nprobes = %lld", (long long)nprobes);
+    COLA_REQUIRE(precision == COLA_PREC_F64 || precision == COLA_PREC_F32,
+                 COLA_ERR_INVALID_ARG, "precision must be F64 or F32");
+    StreamJoin j(ctx, stream);
+    const int64_t N = op->rows, R = 1 + nprobes;
+    const bool f64 = precision == COLA_PREC_F64;
+    const size_t es = f64 ? 8 : 4;
+    // X = [a, z_1 .. z_m] next to U = Sol = [a, u_1 .. u_m]
+    char* X = (char*)ctx->ws.get("gpb.X", es * N * R);
+    COLA_CUDA(cudaMemcpyAsync(X, Sol, es * N, cudaMemcpyDeviceToDevice, ctx->s));
+    COLA_CUDA(cudaMemcpyAsync(X + es * N, Z, es * N * nprobes, cudaMemcpyDeviceToDevice,
+                              ctx->s));
+    if (grads) {
+      std::vector<double> w(R, 0.5 * g / (double)nprobes);
+      w[0] = -0.5 * g;
+      bilinear_entry(ctx, op, Sol, X, w.data(), R, precision, grads, 0, 0);
+    }
+    if (grad_y) {
+      const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((N + 255) / 256, 4096));
+      if (f64)
+        k_scaled_copy<double><<<grid, 256, 0, ctx->s>>>(N, (const double*)Sol, g,
+                                                        (double*)grad_y);
+      else
+        k_scaled_copy<float><<<grid, 256, 0, ctx->s>>>(N, (const float*)Sol, g, (float*)grad_y);
+      ctx->count_launch();
+      COLA_CUDA(cudaGetLastError());
+    }
+  });
+}
 
 cola_status cola_solve_backward(cola_ctx* ctx, const cola_linop* op, const void* X,
                                 const void* gradX, void* gradB, int64_t nrhs,

@@ -296,6 +296,10 @@ void lanczos_impl(Ctx* c, const cola_linop* op, const void* Q0, int64_t nv, int 
                   int reorth, double* alpha, double* beta, int* m_eff);
 void householder_lanczos(Ctx* c, const cola_linop* op, const void* Q0, int64_t nv, int m,
                          int prec, double* alpha, double* beta, int* m_eff);
+// SLQ log-det estimate (cola_slq_logdet without the argument checks); synchronous.
+void slq_impl(Ctx* c, const cola_linop* op, int nprobes, int m, uint64_t seed,
+              const void* probes, int prec, int reorth, double* logdet, double* std_err,
+              double* per_probe, int* clamped);
 void bilinear_entry(Ctx* c, const cola_linop* op, const void* U, const void* X,
                     const double* weights, int64_t R, int prec, void* const* grads,
                     int accumulate, int depth);

@@ -1549,9 +1549,9 @@ void lanczos_impl(Ctx* c, const cola_linop* op, const void* Q0, int64_t nv, int 
 // ===================================================================== SLQ
 namespace cola {
 
-static void slq_impl(Ctx* c, const cola_linop* op, int nprobes, int m, uint64_t seed,
-                     const void* probes, int prec, int reorth, double* logdet, double* std_err,
-                     double* per_probe, int* clamped) {
+void slq_impl(Ctx* c, const cola_linop* op, int nprobes, int m, uint64_t seed,
+              const void* probes, int prec, int reorth, double* logdet, double* std_err,
+              double* per_probe, int* clamped) {
   const int64_t N = op->rows;
   const bool f64 = prec == COLA_PREC_F64;
   const size_t es = f64 ? 8 : 4;

@@ -946,6 +946,9 @@ def main():
                     help="run only those three workload sections")
     ap.add_argument("--config", type=int, choices=[1, 3, 5], default=None,
                     help="run only one of those sections (profiler captures)")
+    ap.add_argument("--mvm-gp", action="store_true",
+                    help="only run --reps MIXED MVMs of the GP workload's 33-RHS block "
+                         "(1024-point factors; profiler captures of the streaming kernel)")
     ap.add_argument("--slq-only", action="store_true",
                     help="run only --reps SLQ log-dets (32 probes x 100 steps, MIXED 3x3) "
                          "of the bench operator (profiler captures)")
@@ -960,6 +963,24 @@ def main():
     args = ap.parse_args()
     if args.mvm_only:
         run_mvm_only(args)
+    elif args.mvm_gp:
+        import torch
+        import paper_2309_03060_gb300 as cola
+        ctx = cola.Context(0)
+        dev, st = torch.device("cuda", 0), torch.cuda.current_stream()
+        w = wl.config5()
+        K = [torch.tensor(wl.rbf_factor(p_, l), device=dev) for p_, l in zip(w.points, w.ells)]
+        s2 = torch.tensor([w.sigma2], dtype=torch.float64, device=dev)
+        kron = cola.cola_linop_kron(ctx, *[cola.cola_linop_dense(ctx, k) for k in K])
+        op = cola.cola_linop_sum(ctx, [kron, cola.cola_linop_diag(ctx, s2, n=w.N)])
+        X = torch.randn(33, w.N, dtype=torch.float32, device=dev)
+        Y = torch.empty_like(X)
+        ts = []
+        for _ in range(args.reps):
+            _, t = timed_call(torch, st, lambda: cola.cola_matvec(
+                ctx, op, X, cola.PREC_MIXED, out=Y, split_terms=3), warm=False)
+            ts.append(round(t * 1e6, 1))
+        print(json.dumps({"mode": "mvm-gp", "us": ts}))
     elif args.slq_only:
         import torch
         import paper_2309_03060_gb300 as cola

@@ -169,7 +169,9 @@ namespace cola {
 
 enum DerivedKey {
   DK_F64 = 0, DK_F32 = 1, DK_BAND64 = 2, DK_BAND32 = 3,
-  DK_V_F64 = 4, DK_V_F32 = 5, DK_SPLIT_BF16 = 6
+  DK_V_F64 = 4, DK_V_F32 = 5, DK_SPLIT_BF16 = 6,
+  // transposed (k x n) low-rank factors in the working type: U, V for FP64 / FP32
+  DK_UT_F64 = 20, DK_UT_F32 = 21, DK_VT_F64 = 22, DK_VT_F32 = 23
 };
 
 // dtype used for vectors at a precision
@@ -252,7 +254,11 @@ void lowrank_vtx(Ctx* c, const T* V, const T* X, int64_t n, int64_t k, int64_t R
                  double* partials);  // W[k][R] = V^T X^T
 template <typename T>
 void lowrank_uw(Ctx* c, const T* U, const T* W, T* Y, int64_t n, int64_t k, int64_t R,
-                double coeff, double beta);  // Y[r,i] = coeff sum_k U[i,k] W[k,r] + beta Y
+                double coeff, double beta,
+                const T* Ut = nullptr);  // Y[r,i] = coeff sum_k U[i,k] W[k,r] + beta Y
+                                          // (Ut: U transposed, k x n, when prepared)
+template <typename T>
+void transpose_nk(Ctx* c, const T* src, T* dst, int64_t n, int64_t k);  // n x k -> k x n
 template <typename T>
 void lowrank_grad(Ctx* c, const T* A, const T* W, T* G, int64_t n, int64_t k, int64_t R,
                   double scale);  // G[i,k] += scale sum_r A[r,i] W[k,r]

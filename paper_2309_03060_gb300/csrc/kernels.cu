@@ -505,6 +505,58 @@ __global__ void k_lr_final(const double* part, int nblk, int64_t cnt, T* W) {
   if (lane == 0) W[i] = (T)s;
 }
 
+// Y[r, i] = coeff sum_k Ut[k, i] W[k, r] + beta Y[r, i] from the transposed
+// low-rank factor (k x n): thread i reads column i of Ut, so every load of a
+// warp is one coalesced row segment; W in shared memory.
+template <typename T>
+__global__ void __launch_bounds__(256) k_lr_uw_t(const T* Ut, const T* W, T* Y, int64_t n,
+                                                 int kdim, int64_t R, T coeff, T beta) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* Ws = reinterpret_cast<T*>(smem_raw);
+  for (int64_t e = threadIdx.x; e < kdim * R; e += blockDim.x) Ws[e] = W[e];
+  __syncthreads();
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t r0 = 0; r0 < R; r0 += 8) {
+      T acc[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) acc[q] = T(0);
+#pragma unroll 8
+      for (int k = 0; k < kdim; ++k) {
+        const T u = __ldg(Ut + (int64_t)k * n + i);
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+          if (r0 + q < R) acc[q] = fma(u, Ws[k * R + r0 + q], acc[q]);
+      }
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        if (r0 + q >= R) break;
+        T* y = Y + (r0 + q) * n + i;
+        T v = coeff * acc[q];
+        if (beta != T(0)) v += beta * *y;
+        *y = v;
+      }
+    }
+  }
+}
+
+// Transpose of an n x k row-major matrix into k x n (32 x 32 shared tiles).
+template <typename T>
+__global__ void k_transpose_nk(const T* src, T* dst, int64_t n, int64_t k) {
+  __shared__ T tile[32][33];
+  const int64_t i0 = (int64_t)blockIdx.x * 32, k0 = (int64_t)blockIdx.y * 32;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8 threads
+  for (int r = ty; r < 32; r += 8) {
+    const int64_t i = i0 + r, kk = k0 + tx;
+    tile[r][tx] = (i < n && kk < k) ? src[i * k + kk] : T(0);
+  }
+  __syncthreads();
+  for (int r = ty; r < 32; r += 8) {
+    const int64_t kk = k0 + r, i = i0 + tx;
+    if (kk < k && i < n) dst[kk * n + i] = tile[tx][r];
+  }
+}
+
 // k_lr_uw with the block's 256 rows of U staged in shared memory by
 // coalesced loads (row stride kdim + 1 against bank conflicts): thread t then
 // forms row t of Y from shared memory.
@@ -836,10 +888,25 @@ void lowrank_vtx(Ctx* c, const T* V, const T* X, int64_t n, int64_t k, int64_t R
 }
 
 template <typename T>
+void transpose_nk(Ctx* c, const T* src, T* dst, int64_t n, int64_t k) {
+  dim3 grid((unsigned)((n + 31) / 32), (unsigned)((k + 31) / 32));
+  k_transpose_nk<T><<<grid, 256, 0, c->s>>>(src, dst, n, k);
+  c->count_launch();
+  COLA_CUDA(cudaGetLastError());
+}
+
+template <typename T>
 void lowrank_uw(Ctx* c, const T* U, const T* W, T* Y, int64_t n, int64_t k, int64_t R,
-                double coeff, double beta) {
+                double coeff, double beta, const T* Ut) {
   const size_t smem = sizeof(T) * k * R;
   COLA_REQUIRE(smem <= 48 * 1024, COLA_ERR_UNSUPPORTED, "low-rank: k*nrhs too large");
+  if (Ut) {
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 152 * 16));
+    k_lr_uw_t<T><<<grid, 256, smem, c->s>>>(Ut, W, Y, n, (int)k, R, (T)coeff, (T)beta);
+    c->count_launch();
+    COLA_CUDA(cudaGetLastError());
+    return;
+  }
   const size_t smem2 = smem + sizeof(T) * 256 * (k + 1);
   if (smem2 <= 48 * 1024) {
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 152 * 8));
@@ -943,7 +1010,8 @@ void add_partials(Ctx* c, const T* P, T* G, int64_t count, int64_t nparts, doubl
   template void lowrank_vtx<T>(Ctx*, const T*, const T*, int64_t, int64_t, int64_t, T*,     \
                                double*);                                                    \
   template void lowrank_uw<T>(Ctx*, const T*, const T*, T*, int64_t, int64_t, int64_t,      \
-                              double, double);                                              \
+                              double, double, const T*);                                    \
+  template void transpose_nk<T>(Ctx*, const T*, T*, int64_t, int64_t);                      \
   template void lowrank_grad<T>(Ctx*, const T*, const T*, T*, int64_t, int64_t, int64_t,    \
                                 double);                                                    \
   template void rowsum_products<T>(Ctx*, const T*, const T*, T*, int64_t, int64_t, double,  \

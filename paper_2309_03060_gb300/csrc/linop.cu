@@ -196,6 +196,18 @@ static void prepare_rec(Ctx* c, cola_linop* op, cola_dtype want, int prec, int s
           copy_once(c, op, op->data2, op->rows, op->rank, op->rank, want,
                     want == COLA_F64 ? DK_V_F64 : DK_V_F32);
       }
+      // k x n transposes of U (and V) for the coalesced U W product
+      for (int second = 0; second < (op->data2 ? 2 : 1); ++second) {
+        const int key = want == COLA_F64 ? (second ? DK_VT_F64 : DK_UT_F64)
+                                         : (second ? DK_VT_F32 : DK_UT_F32);
+        if (prep_fresh(op, key)) continue;
+        void* dst = derived_buf(op, key, op->rows * op->rank * dtype_size(want));
+        if (want == COLA_F64)
+          transpose_nk<double>(c, leaf_ptr<double>(op, second), (double*)dst, op->rows, op->rank);
+        else
+          transpose_nk<float>(c, leaf_ptr<float>(op, second), (float*)dst, op->rows, op->rank);
+        prep_mark(op, key);
+      }
       break;
     default:
       for (auto* k : op->kids) prepare_rec(c, k, want, prec, split);
@@ -281,7 +293,13 @@ void apply(Ctx* c, const cola_linop* op, const T* X, T* Y, int64_t R, double coe
       T* W = tmp<T>(c, "lrW", depth, 0, op->rank * R);
       double* part = tmp<double>(c, "lrP", depth, 0, (int64_t)kLowRankBlocks * op->rank * R);
       lowrank_vtx<T>(c, V, X, op->rows, op->rank, R, W, part);
-      lowrank_uw<T>(c, U, W, Y, op->rows, op->rank, R, coeff, beta);
+      // the transposed copy of whichever factor multiplies W
+      const bool f64 = dtype_of<T>() == COLA_F64;
+      const bool use_v = tr && op->data2;
+      const int tkey = f64 ? (use_v ? DK_VT_F64 : DK_UT_F64) : (use_v ? DK_VT_F32 : DK_UT_F32);
+      auto it = op->derived.find(tkey);
+      const T* Ut = it != op->derived.end() ? (const T*)it->second.p : nullptr;
+      lowrank_uw<T>(c, U, W, Y, op->rows, op->rank, R, coeff, beta, Ut);
       break;
     }
     case LK_SUM:

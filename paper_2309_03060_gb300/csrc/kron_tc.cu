@@ -1281,18 +1281,22 @@ __global__ void __launch_bounds__(kSlabThreads, 1)
     bool ok = true;
     for (int64_t sl = blockIdx.x; sl < p.nslab && ok; sl += gridDim.x, ++it) {
       const float* src = p.S + sl * (int64_t)(kSlabN * kSlabN) + row;
-      for (int kb = 0; kb < 2; ++kb) {
-        float v[32];
-        const int k0 = kb * 64 + khalf * 32;
+      // both k blocks' values in flight together (one load latency per slab)
+      float v[2][32];
 #pragma unroll
-        for (int e = 0; e < 32; ++e) v[e] = __ldg(src + (int64_t)(k0 + e) * kSlabN);
+      for (int kb = 0; kb < 2; ++kb)
+#pragma unroll
+        for (int e = 0; e < 32; ++e)
+          v[kb][e] = __ldg(src + (int64_t)(kb * 64 + khalf * 32 + e) * kSlabN);
+#pragma unroll
+      for (int kb = 0; kb < 2; ++kb) {
         if (!mbar_wait(&bempty[kb], (uint32_t)(it & 1) ^ 1u, abort_flag, p.err)) {
           ok = false;
           break;
         }
         unsigned char* bst = b1 + (size_t)kb * kKbBytes;
-        slab_put16<TV>(bst, row, khalf * 4, v);
-        slab_put16<TV>(bst, row, khalf * 4 + 2, v + 16);
+        slab_put16<TV>(bst, row, khalf * 4, v[kb]);
+        slab_put16<TV>(bst, row, khalf * 4 + 2, v[kb] + 16);
         fence_proxy_async();
         mbar_arrive(&bfull[kb]);
       }

@@ -506,8 +506,9 @@ cola_status cola_kron_matvec_noalloc(int nfactors, const int64_t* rows, const in
                                      int64_t nrhs, cola_stream stream);
 
 /* Test hook of the failure path (no counterpart in the paper).  The next
- * tensor-core Kronecker MVM launch of this context that is not being captured
- * into a CUDA graph has its MMA role first wait on a barrier that nothing
+ * tensor-core Kronecker launch of this context (a mode step of an MVM or of
+ * a batched solve) that is not being captured into a CUDA graph has its MMA
+ * role first wait on a barrier that nothing
  * completes, with a limit of wait_ns nanoseconds (1 .. 2e9; 0 disarms) in
  * place of the usual 2 s.  When the limit runs out the launch takes the
  * ordinary time-out path: every role of every CTA stops, each CTA waits for

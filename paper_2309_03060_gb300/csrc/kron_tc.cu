@@ -1152,6 +1152,324 @@ __global__ void __launch_bounds__(kThreadsFs, 1) k_kron_tc_fs(const __grid_const
 }
 
 // ---------------------------------------------------------------------------
+// Split GEMM mode step for factors with a side above 128 (no factor in tensor
+// memory).  A pre-split pass writes the mode step's input as K-major BF16
+// term images (and forms the fused first-step input p = z + beta p or
+// beta x on the way); the GEMM then moves both operands with copy engines
+// only:
+//   D[i, m] = sum_k K[i, k] X[m, k]   A = factor block (128 outputs x 64 k per
+//   term, pre-split image, one cp.async.bulk each), B = X image block (128
+//   rows x 64 k per term, 2-D TMA with the 128-byte swizzle); accumulator
+//   lane i holds output i of the tile's rows, so the 32 lanes of an epilogue
+//   warp store 32 consecutive outputs of one row.  With the whole of tensor
+//   memory free for accumulators, the dominant / cross-term pair is
+//   double-buffered (2 x 256 columns): the epilogue drains one tile while the
+//   MMAs of the next run.
+//   warp 0      loader (one lane)
+//   warp 1      MMA (one lane), tensor-memory allocation
+//   warps 2-9   epilogue: warp w drains TMEM lanes 32 (w mod 4) .. + 31 of
+//               column half (w - 2) / 4 (rows 0-63 or 64-127 of the tile)
+// Tiles (right-hand side r, 128-row tile of rest, 128-output chunk nc) run
+// with the chunk fastest, so CTAs working at the same time share X blocks in
+// L2.
+constexpr int kGemmThreads = 320;
+constexpr uint32_t kGemmTermBytes = (uint32_t)kTileM * 128u;  // 128 rows x 64 BF16
+
+struct TcGemmParams {
+  CUtensorMap tm_x;      // X image [TV * xrows][kpad] BF16, box 64 x 128, 128-byte swizzle
+  const uint16_t* Bimg;  // factor image [tf][kblocks][img_rows][64] BF16, swizzled rows
+  float* Y;
+  int64_t rest, size_out, tiles_m, ntiles, xrows;  // xrows = R * rest
+  int n_out, nchunks, kblocks, img_rows, stages;
+  float coeff, beta;
+  const float* epi_x;  // epilogue terms as in TcParams
+  const float* epi_d;
+  int64_t epi_dstride;
+  float epi_coeff;
+  double* epi_dot;
+  const float* epi_q2;
+  const double* epi_gamma;
+  int* err;
+  uint64_t stall_ns;
+};
+
+// Pre-split pass: X [R][n_in][rest] FP32 (mode 0), or beta_r X + z (mode 2)
+// or beta_r X (mode 1), both also written to pro_out, into TV K-major BF16
+// term images img[t][r rest + m][kpad] (zero for k >= n_in).  A block moves a
+// 64 (k) x 64 (m) tile through shared memory: reads along m, writes 128-byte
+// rows along k.
+template <int TV>
+__global__ void __launch_bounds__(256) k_presplit(const float* X, int n_in, int64_t rest,
+                                                  int kpad, int64_t xrows, int mode,
+                                                  const float* pro_z, const double* pro_beta,
+                                                  float* pro_out, uint16_t* img) {
+  __shared__ float tile[64][65];
+  const int64_t m0 = (int64_t)blockIdx.x * 64, r = blockIdx.z;
+  const int k0 = blockIdx.y * 64;
+  const int64_t off = r * (int64_t)n_in * rest;
+  const float beta_r = mode != 0 ? (float)pro_beta[r] : 0.0f;
+  pdl_wait();
+  for (int e = threadIdx.x; e < 64 * 64; e += 256) {
+    const int kl = e >> 6, ml = e & 63;
+    const int k = k0 + kl;
+    const int64_t m = m0 + ml;
+    float v = 0.0f;
+    if (k < n_in && m < rest) {
+      const int64_t idx = off + (int64_t)k * rest + m;
+      v = X[idx];
+      if (mode == 2) {
+        v = fmaf(beta_r, v, pro_z[idx]);
+        pro_out[idx] = v;
+      } else if (mode == 1) {
+        v = beta_r * v;
+        pro_out[idx] = v;
+      }
+    }
+    tile[kl][ml] = v;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < 64 * 8; e += 256) {
+    const int ml = e >> 3, ch = e & 7;
+    const int64_t m = m0 + ml;
+    if (m >= rest) continue;
+    uint32_t w[3][4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      uint32_t o[3];
+      split2(tile[ch * 8 + 2 * j][ml], tile[ch * 8 + 2 * j + 1][ml], TV, o);
+      w[0][j] = o[0];
+      w[1][j] = o[1];
+      w[2][j] = o[2];
+    }
+#pragma unroll
+    for (int t = 0; t < TV; ++t)
+      *reinterpret_cast<uint4*>(img + ((size_t)t * xrows + r * rest + m) * kpad + k0 + ch * 8) =
+          make_uint4(w[t][0], w[t][1], w[t][2], w[t][3]);
+  }
+}
+
+template <int TF, int TV>
+__global__ void __launch_bounds__(kGemmThreads, 1)
+    k_kron_tc_gemm(const __grid_constant__ TcGemmParams p) {
+  constexpr int kMaxT = TF > TV ? TF : TV;
+  constexpr bool kSmall = TF > 1 || TV > 1;
+  constexpr uint32_t kStageBytes = (uint32_t)(TF + TV) * kGemmTermBytes;
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* base = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
+  uint64_t* full = (uint64_t*)(base + (size_t)p.stages * kStageBytes);  // [stages]
+  uint64_t* empty = full + p.stages;                                   // [stages]
+  uint64_t* afull = empty + p.stages;                                  // [2]
+  uint64_t* aempty = afull + 2;                                        // [2]
+  uint64_t* drain = aempty + 2;
+  uint64_t* stall = drain + 1;  // never completed (time-out test)
+  uint32_t* tmem_slot = (uint32_t*)(stall + 1);
+  volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (tid == 0) {
+    for (int s = 0; s < p.stages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&afull[b], 1);
+      mbar_init(&aempty[b], kGemmThreads - 64);
+    }
+    mbar_init(drain, 1);
+    mbar_init(stall, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(512)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+  pdl_trigger();
+
+  if (warp == 0) {
+    // ---------------------------------------------------------------- loader
+    pdl_wait();
+    if (lane == 0) {
+      bool ok = true;
+      int s = 0;
+      uint32_t ph = 0;
+      uint32_t issued = 0, issued_ph = 0;  // bit s: a copy went to stage s / its parity
+      for (int64_t t = blockIdx.x; t < p.ntiles && ok; t += gridDim.x) {
+        const int nc = (int)(t % p.nchunks);
+        const int64_t tm = t / p.nchunks;
+        const int64_t r = tm / p.tiles_m, m0 = (tm % p.tiles_m) * kTileM;
+        // rows past rest arrive as the next right-hand side's rows (or zeros
+        // past the image); the epilogue masks them
+        const int y0 = (int)(r * p.rest + m0);
+        for (int kb = 0; kb < p.kblocks; ++kb) {
+          if (!mbar_wait(&empty[s], ph ^ 1u, abort_flag, p.err)) {
+            ok = false;
+            break;
+          }
+          unsigned char* st = base + (size_t)s * kStageBytes;
+          mbar_arrive_expect_tx(&full[s], kStageBytes);
+#pragma unroll
+          for (int tv = 0; tv < TV; ++tv)
+            tma_load_2d(st + tv * kGemmTermBytes, &p.tm_x, kb * kBlockK,
+                        (int)(tv * p.xrows) + y0, &full[s]);
+#pragma unroll
+          for (int ti = 0; ti < TF; ++ti)
+            bulk_g2s(st + (TV + ti) * kGemmTermBytes,
+                     p.Bimg + (((size_t)ti * p.kblocks + kb) * (size_t)p.img_rows +
+                               (size_t)nc * kTileM) * kBlockK,
+                     kGemmTermBytes, &full[s]);
+          issued |= 1u << s;
+          issued_ph = (issued_ph & ~(1u << s)) | (ph << s);
+          if (++s == p.stages) {
+            s = 0;
+            ph ^= 1u;
+          }
+        }
+      }
+      // only the latest copy of each stage can still be in flight
+      for (int st = 0; st < p.stages; ++st)
+        if (issued & (1u << st)) mbar_wait_own(&full[st], (issued_ph >> st) & 1u, p.err);
+    }
+    __syncwarp();
+  } else if (warp == 1) {
+    // ------------------------------------------------------------------- MMA
+    if (lane == 0) {
+      constexpr uint32_t idesc = idesc_bf16(kTileM, kTileM);  // M = outputs, N = rows
+      bool ok = true;
+      if (p.stall_ns) ok = mbar_wait_slow(stall, 0, abort_flag, p.err, p.stall_ns);
+      int s = 0;
+      uint32_t ph = 0;
+      int64_t it = 0;
+      for (int64_t t = blockIdx.x; t < p.ntiles && ok; t += gridDim.x, ++it) {
+        const int b = (int)(it & 1);
+        if (!mbar_wait(&aempty[b], (uint32_t)((it >> 1) & 1) ^ 1u, abort_flag, p.err)) break;
+        tc_fence_after();
+        const uint32_t d_big = tmem_base + (uint32_t)b * 256u, d_small = d_big + 128u;
+        uint32_t acc_big = 0, acc_small = 0;
+        for (int kb = 0; kb < p.kblocks; ++kb) {
+          if (!mbar_wait(&full[s], ph, abort_flag, p.err)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t st = smem_u32(base + (size_t)s * kStageBytes);
+#pragma unroll
+          for (int kk = 0; kk < 4; ++kk) {
+#pragma unroll
+            for (int ti = 0; ti < TF; ++ti)
+#pragma unroll
+              for (int tv = 0; tv < TV; ++tv) {
+                if (ti + tv >= kMaxT) continue;
+                const uint64_t ad =
+                    sw128_desc(st + (uint32_t)(TV + ti) * kGemmTermBytes + (uint32_t)kk * 32u);
+                const uint64_t bd =
+                    sw128_desc(st + (uint32_t)tv * kGemmTermBytes + (uint32_t)kk * 32u);
+                if (ti == 0 && tv == 0) {
+                  mma_bf16(d_big, ad, bd, idesc, acc_big);
+                  acc_big = 1;
+                } else {
+                  mma_bf16(d_small, ad, bd, idesc, acc_small);
+                  acc_small = 1;
+                }
+              }
+          }
+          mma_commit(&empty[s]);
+          if (++s == p.stages) {
+            s = 0;
+            ph ^= 1u;
+          }
+        }
+        if (!ok) break;
+        mma_commit(&afull[b]);
+      }
+      mma_commit(drain);
+      mbar_wait_own(drain, 0, p.err);
+    }
+    __syncwarp();
+  } else {
+    // -------------------------------------------------------------- epilogue
+    pdl_wait();
+    const int ew = warp - 2;
+    const int quarter = warp & 3, chalf = ew >> 2;
+    const int il = quarter * 32 + lane;  // output within the chunk = TMEM lane
+    const uint32_t lane_off = (uint32_t)(quarter * 32) << 16;
+    const float d0 = (p.epi_x && p.epi_dstride == 0) ? p.epi_d[0] : 0.0f;
+    int64_t it = 0;
+    for (int64_t t = blockIdx.x; t < p.ntiles; t += gridDim.x, ++it) {
+      const int b = (int)(it & 1);
+      if (!mbar_wait(&afull[b], (uint32_t)((it >> 1) & 1), abort_flag, p.err)) break;
+      tc_fence_after();
+      const int nc = (int)(t % p.nchunks);
+      const int64_t tm = t / p.nchunks;
+      const int64_t r = tm / p.tiles_m, m0 = (tm % p.tiles_m) * kTileM;
+      const uint32_t taddr = tmem_base + lane_off + (uint32_t)b * 256u + (uint32_t)chalf * 64u;
+      float a[64];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        uint32_t v[8], w[8];
+        tmem_ld8(taddr + (uint32_t)(q * 8), v);
+        if (kSmall) tmem_ld8(taddr + 128u + (uint32_t)(q * 8), w);
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+        for (int e = 0; e < 8; ++e)
+          a[q * 8 + e] =
+              p.coeff * (__uint_as_float(v[e]) + (kSmall ? __uint_as_float(w[e]) : 0.0f));
+      }
+      tc_fence_before();
+      mbar_arrive(&aempty[b]);
+      const int i = nc * kTileM + il;
+      const int64_t mbase = m0 + chalf * 64;
+      const int nrows = (int)((p.rest - mbase < 64) ? (p.rest - mbase) : 64);
+      float part = 0.0f;  // this thread's <= 64 products of x . y
+      if (i < p.n_out && nrows > 0) {
+        const int64_t ld = p.n_out;
+        float* yp = p.Y + r * p.size_out + mbase * ld + i;
+        const float* ex = p.epi_x ? p.epi_x + r * p.size_out + mbase * ld + i : nullptr;
+        const float* ed = (p.epi_x && p.epi_dstride) ? p.epi_d + mbase * ld + i : nullptr;
+        const float* eq = p.epi_q2 ? p.epi_q2 + r * p.size_out + mbase * ld + i : nullptr;
+        const float gam = p.epi_q2 ? (float)p.epi_gamma[r] : 0.0f;
+#pragma unroll
+        for (int c = 0; c < 64; ++c) {
+          if (c < nrows) {
+            float v = a[c];
+            if (ex) {
+              const float xd = __ldg(ex + c * ld);
+              const float dv = ed ? __ldg(ed + c * ld) : d0;
+              v = fmaf(p.epi_coeff * dv, xd, v);
+              if (eq) v = fmaf(-gam, __ldg(eq + c * ld), v);
+              part = fmaf(v, xd, part);
+            }
+            if (p.beta != 0.0f) v = fmaf(p.beta, yp[c * ld], v);
+            yp[c * ld] = v;
+          }
+        }
+      }
+      if (p.epi_dot) {
+        double dsum = (double)part;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) dsum += __shfl_xor_sync(0xffffffffu, dsum, o);
+        if (lane == 0) p.epi_dot[t * kDotSlots + ew] = dsum;
+      }
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 1) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base),
+                 "r"(512)
+                 : "memory");
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Fused last two mode steps of a three-factor Kronecker MVM with 128 x 128
 // second and third factors (the slab kernel).  The first mode step writes its
 // output slab-major, T[r][i1][j2][j3] (e_mode 5), so every (right-hand side,
@@ -1792,6 +2110,124 @@ static bool fs_plan(const TcParams& p, TcFsParams& r) {
   return true;
 }
 
+// BF16 image [rows][cols] of the GEMM path's X image, box 64 columns x 128
+// rows, 128-byte swizzle (the UMMA K-major layout); reads past the rows
+// return zeros.
+static bool tmap_image(CUtensorMap* m, const uint16_t* base, int64_t rows, int64_t cols) {
+  EncodeTiledFn enc = encode_tiled();
+  if (!enc) return false;
+  const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)cols * 2};
+  const cuuint32_t box[2] = {(cuuint32_t)kBlockK, (cuuint32_t)kTileM};
+  const cuuint32_t estr[2] = {1, 1};
+  return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<uint16_t*>(base), dims, strides,
+             box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+using GemmKernel = void (*)(TcGemmParams);
+static GemmKernel gemm_kernel(int tf, int tv) {
+  static const GemmKernel tab[3][3] = {
+      {k_kron_tc_gemm<1, 1>, k_kron_tc_gemm<1, 2>, k_kron_tc_gemm<1, 3>},
+      {k_kron_tc_gemm<2, 1>, k_kron_tc_gemm<2, 2>, k_kron_tc_gemm<2, 3>},
+      {k_kron_tc_gemm<3, 1>, k_kron_tc_gemm<3, 2>, k_kron_tc_gemm<3, 3>}};
+  return tab[tf - 1][tv - 1];
+}
+using PresplitKernel = void (*)(const float*, int, int64_t, int, int64_t, int, const float*,
+                                const double*, float*, uint16_t*);
+static PresplitKernel presplit_kernel(int tv) {
+  static const PresplitKernel tab[3] = {k_presplit<1>, k_presplit<2>, k_presplit<3>};
+  return tab[tv - 1];
+}
+constexpr int kGemmStages = 2;
+static size_t gemm_smem(int tf, int tv) {
+  return 1024 + (size_t)kGemmStages * (tf + tv) * kGemmTermBytes + 256;
+}
+
+// The split GEMM mode step (factor sides above 128): pre-split pass, then the
+// GEMM.  The factor's GEMM image (128-row output chunks) is made on first use
+// outside graph capture; false (the caller takes the streaming kernel) while
+// it does not exist yet, or when the step has a form the GEMM does not take.
+static bool gemm_launch(Ctx* c, const cola_linop* f, bool tr, const TcParams& p, int depth,
+                        int k) {
+  if (p.n_in <= kTileM && p.n_out <= kTileM) return false;  // the factor-stationary kernel's
+  if (p.out_trans || p.tf < 1 || p.tf > 3 || p.tv < 1 || p.tv > 3) return false;
+  const int kblocks = (p.n_in + kBlockK - 1) / kBlockK, kpad = kblocks * kBlockK;
+  const int nch = (p.n_out + kTileM - 1) / kTileM, img_rows = nch * kTileM;
+  const int64_t xrows = p.batch * p.rest;
+  if ((int64_t)p.tv * xrows > INT32_MAX || p.rest > INT32_MAX) return false;
+  cola_linop* fm = const_cast<cola_linop*>(f);
+  const int key = 120 + (tr ? 10 : 0) + p.tf;
+  if (!prep_fresh(f, key)) {
+    if (c->capturing) return false;
+    const size_t per_term = (size_t)kblocks * img_rows * kBlockK;
+    auto it = fm->derived.find(key);
+    if (it != fm->derived.end() && it->second.bytes < per_term * p.tf * 2) {
+      cudaFree(it->second.p);
+      fm->derived.erase(it);
+      it = fm->derived.end();
+    }
+    void* img = nullptr;
+    if (it == fm->derived.end()) {
+      COLA_CUDA(cudaMalloc(&img, per_term * p.tf * 2));
+      fm->derived[key] = Buf{img, per_term * (size_t)p.tf * 2};
+    } else {
+      img = it->second.p;
+    }
+    const int grid = (int)std::min<size_t>(1024, (per_term + 255) / 256);
+    if (f->dtype == COLA_F64)
+      k_split_factor<double><<<grid, 256, 0, c->s>>>((const double*)f->data, f->ld, tr ? 1 : 0,
+                                                      p.n_out, p.n_in, img_rows, kblocks, p.tf,
+                                                      (uint16_t*)img);
+    else
+      k_split_factor<float><<<grid, 256, 0, c->s>>>((const float*)f->data, f->ld, tr ? 1 : 0,
+                                                    p.n_out, p.n_in, img_rows, kblocks, p.tf,
+                                                    (uint16_t*)img);
+    c->count_launch();
+    COLA_CUDA(cudaGetLastError());
+    prep_mark(fm, key);
+  }
+  uint16_t* ximg = (uint16_t*)c->ws.get(depth_name("kgemm", depth, k & 1),
+                                        (size_t)p.tv * xrows * kpad * 2);
+  TcGemmParams g{};
+  if (!tmap_image(&g.tm_x, ximg, (int64_t)p.tv * xrows, kpad)) return false;
+  const int mode = p.pro_z ? 2 : (p.pro_out ? 1 : 0);
+  const dim3 pgrid((unsigned)((p.rest + 63) / 64), (unsigned)(kpad / 64), (unsigned)p.batch);
+  presplit_kernel(p.tv)<<<pgrid, 256, 0, c->s>>>(p.X, p.n_in, p.rest, kpad, xrows, mode, p.pro_z,
+                                                  p.pro_beta, p.pro_out, ximg);
+  c->count_launch();
+  COLA_CUDA(cudaGetLastError());
+  g.Bimg = (const uint16_t*)f->derived.at(key).p;
+  g.Y = p.Y;
+  g.rest = p.rest;
+  g.size_out = p.size_out;
+  g.tiles_m = p.tiles_m;
+  g.nchunks = nch;
+  g.ntiles = p.tiles_m * p.batch * nch;
+  g.xrows = xrows;
+  g.n_out = p.n_out;
+  g.kblocks = kblocks;
+  g.img_rows = img_rows;
+  g.stages = kGemmStages;
+  g.coeff = p.coeff;
+  g.beta = p.beta;
+  g.epi_x = p.epi_x;
+  g.epi_d = p.epi_d;
+  g.epi_dstride = p.epi_dstride;
+  g.epi_coeff = p.epi_coeff;
+  g.epi_dot = p.epi_dot;
+  g.epi_q2 = p.epi_q2;
+  g.epi_gamma = p.epi_gamma;
+  g.err = p.err;
+  g.stall_ns = p.stall_ns;
+  const int grid = (int)std::min<int64_t>(g.ntiles, c->num_sms);
+  launch_pdl(gemm_kernel(p.tf, p.tv), dim3(grid), dim3(kGemmThreads), gemm_smem(p.tf, p.tv), c->s,
+             g);
+  c->count_launch();
+  COLA_CUDA(cudaGetLastError());
+  return true;
+}
+
 using FsKernel = void (*)(TcFsParams);
 static FsKernel fs_kernel(int tf, int tv) {
   static const FsKernel tab[3][3] = {
@@ -1918,6 +2354,9 @@ static int64_t kron_tc_run(Ctx* c, const cola_linop* op, const float* X, float* 
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemMax));
           COLA_CUDA(cudaFuncSetAttribute(slab_kernel(a, b),
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemMax));
+          COLA_CUDA(cudaFuncSetAttribute(gemm_kernel(a, b),
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)gemm_smem(a, b)));
         }
       attr_set[c->device] = true;
     }
@@ -1925,13 +2364,15 @@ static int64_t kron_tc_run(Ctx* c, const cola_linop* op, const float* X, float* 
     TcFsParams rp{};
     if (fs_plan(p, rp)) {
       launch_pdl(fs_kernel(tf, tv), dim3(grid), dim3(kThreadsFs), fs_smem(rp, tv), c->s, rp);
-    } else {
+      c->count_launch();
+      COLA_CUDA(cudaGetLastError());
+    } else if (!gemm_launch(c, f, tr, p, depth, k)) {
       COLA_REQUIRE(!p.out_trans, COLA_ERR_UNSUPPORTED,
                    "internal: slab-major output needs the factor-stationary kernel");
       k_kron_tc<OneProb><<<grid, kThreadsTc, q.smem, c->s>>>(OneProb{p}, p);
+      c->count_launch();
+      COLA_CUDA(cudaGetLastError());
     }
-    c->count_launch();
-    COLA_CUDA(cudaGetLastError());
     cur = dst;
     cur_size = out_size;
   }
@@ -2207,6 +2648,10 @@ void kron_tc_batch_launch(Ctx* c, const char* tag, int tf, int tv, int max_n_chu
   while (cols < (uint32_t)(2 * K.nbuf * max_n_chunk)) cols <<= 1;
   K.tmem_cols = cols;
   K.err = tc_errflag(c);
+  if (c->tc_stall_ns > 0 && !c->capturing) {
+    K.stall_ns = (uint64_t)c->tc_stall_ns;  // armed once by cola_test_stall_next_launch
+    c->tc_stall_ns = 0;
+  }
   const size_t smem = (size_t)K.stages * K.stage_bytes + 1024 + 256;
   ProbTable src;
   src.probs = (const TcParams*)c->ws.bufs.at(tagged(tag, "probs")).p;

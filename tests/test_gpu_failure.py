@@ -6,7 +6,10 @@
   stops, each CTA waits for its own copies and MMAs, frees tensor memory and
   exits); the host sees COLA_ERR_TIMEOUT on the context's next call, and the
   call after that is bit-identical to one made before the stall and matches
-  the oracle.  Both kernels: factor-stationary (sides <= 128) and streaming.
+  the oracle.  Both kernels of a single MVM: factor-stationary (sides <= 128)
+  and the split GEMM (a side above 128); and the table-driven kernel of a
+  batched solve, which then ends with COLA_ERR_TIMEOUT and succeeds when run
+  again.
 * Breakdown, injected on the host: a right-hand side with a NaN or an Inf
   entry, and an operator annotated spd that is not (p^T A p < 0 in the first
   iteration), end with COLA_ERR_BREAKDOWN in that right-hand side's info while
@@ -49,7 +52,7 @@ def _rbf(n, seed):
 
 
 @pytest.mark.parametrize("sides", [(64, 48, 32), (160, 24, 16)],
-                         ids=["factor_stationary", "streaming"])
+                         ids=["factor_stationary", "split_gemm"])
 def test_tensor_core_timeout_reported_and_context_recovers(cola, ctx, sides):
     F = [_rbf(n, 70 + k) for k, n in enumerate(sides)]
     op = cola.cola_linop_kron(ctx, *[cola.cola_linop_dense(ctx, torch.tensor(f, device=DEV))
@@ -73,6 +76,34 @@ def test_tensor_core_timeout_reported_and_context_recovers(cola, ctx, sides):
     Xh = X.double().cpu().numpy()
     bound = O.Kron([O.Dense(np.abs(f)) for f in F]).mvm(np.abs(Xh))
     assert np.max(np.abs(after.double().cpu().numpy() - ref.mvm(Xh)) / bound) < 1e-5
+
+
+def test_batched_timeout_reported_and_context_recovers(cola, ctx):
+    """The table-driven kernel of batched solves (every factor size) takes the
+    same time-out path: a batched solve whose first tensor-core launch is made
+    to stall ends with COLA_ERR_TIMEOUT, and the same solve run again reaches
+    1e-8 by the oracle's FP64 true residual."""
+    probs = []
+    for k, (n1, n2, R) in enumerate([(40, 48, 2), (150, 24, 1)]):
+        F = [_rbf(n1, 90 + k), _rbf(n2, 95 + k)]
+        spec = ("sum", [("kron", [("dense", f) for f in F]), ("scalar", 0.05, n1 * n2)], None)
+        B = np.random.default_rng(20 + k).standard_normal((R, n1 * n2))
+        probs.append((spec, B))
+    ops = [gpu_tree(cola, ctx, sp, torch.float64, DEV).set_spd() for sp, _ in probs]
+    Bs = [torch.tensor(B, device=DEV) for _, B in probs]
+    opts = cola.cola_cg_opts_default(precision=cola.PREC_MIXED, refine=1, tol=1e-8,
+                                     maxiter=3000, graph_chunk=16)
+    torch.cuda.synchronize()
+    ctx.test_stall_next_launch(20_000_000)
+    with pytest.raises(cola.ColaError) as e:
+        cola.cola_cg_solve_batched(ctx, ops, Bs, opts)
+    assert e.value.status == TIMEOUT
+    torch.cuda.synchronize()
+    Xs, info, st = cola.cola_cg_solve_batched(ctx, ops, Bs, opts)
+    assert st == 0, info
+    for (spec, B), X in zip(probs, Xs):
+        res = krylov.true_relative_residual(oracle_tree(spec), B, X.cpu().numpy())
+        assert np.all(res <= 1e-8), res
 
 
 def _kron_shift(n1, n2, shift, seed):

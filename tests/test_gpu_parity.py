@@ -489,7 +489,7 @@ def test_prepared_copies_reused_and_refreshed_after_in_place_update(cola, ctx):
     torch.testing.assert_close(Y2, 2.0 * Y1, rtol=1e-5, atol=1e-5)
 
 
-@pytest.mark.parametrize("sides", [(24, 20, 16), (160, 24)], ids=["factor_stationary", "streaming"])
+@pytest.mark.parametrize("sides", [(24, 20, 16), (160, 24)], ids=["factor_stationary", "split_gemm"])
 def test_lanczos_mixed_fused_matches_oracle(cola, ctx, sides):
     """MIXED Lanczos on K (x) ... + 0.05 I runs the recurrence fused into the
     tensor-core MVM (normalisation in the first mode step's prologue, shift,
@@ -566,3 +566,64 @@ def test_cg_and_lanczos_mixed_slab_path(cola, ctx):
         a, b, _ = krylov.lanczos(ref, Z[v], 12, reorth=False)
         np.testing.assert_allclose(al[v, :8], a[:8], rtol=1e-5)
         np.testing.assert_allclose(be[v, :8], b[:8], rtol=1e-5)
+
+
+@pytest.mark.parametrize("terms", [1, 2, 3])
+def test_matvec_mixed_split_gemm_parity(cola, ctx, terms):
+    """Factors with a side above 128 take the split GEMM mode step (the mode
+    step's input pre-split into K-major BF16 images, both operands moved by
+    copy engines, double-buffered accumulators): a three-factor product that
+    mixes it with the factor-stationary kernel (257 x 131, 24 x 16 and
+    150 x 200 factors: ragged row tiles, k blocks and 128-output chunks), 3
+    right-hand sides, per entry within three mode steps' split error of
+    sum |K||x|."""
+    r = _rs(700)
+    F = [r.standard_normal((257, 131)) / np.sqrt(131), r.standard_normal((24, 16)) / 4.0,
+         r.standard_normal((150, 200)) / np.sqrt(200)]
+    spec = ("kron", [("dense", f) for f in F])
+    ref = oracle_tree(spec)
+    op = gpu_tree(cola, ctx, spec, torch.float64, DEV)
+    X = r.standard_normal((3, ref.cols)).astype(np.float32).astype(np.float64)
+    Y = cola.cola_matvec(ctx, op, torch.tensor(X, dtype=torch.float32, device=DEV),
+                         cola.PREC_MIXED, split_terms=terms).double().cpu().numpy()
+    bound = oracle_tree(_abs_spec(spec)).mvm(np.abs(X))
+    assert np.max(np.abs(Y - ref.mvm(X)) / bound) < 3 * MIXED_TOL[terms]
+
+
+def test_cg_and_lanczos_mixed_split_gemm(cola, ctx):
+    """K1 (x) K2 + 0.05 I with 200- and 150-point RBF factors, both mode
+    steps on the split GEMM path.  CG (p = r + beta p formed in the pre-split
+    pass, the shift term and the p . Ap partials in the GEMM epilogue; MIXED
+    3 x 3 with FP64 refinement) reaches 1e-8 by the oracle's FP64 true
+    residual and matches the exact eigen-structured solve within the
+    forward-error bound; Lanczos (q = w / beta in the pre-split pass, the
+    three-term subtraction and alpha partials in the epilogue) matches the
+    oracle's coefficients on the same probes before orthogonality is lost."""
+    sides = (200, 150)
+    F = [wl.rbf_factor(wl.uniform(wl.substream(710, k), (n,)), 0.2) for k, n in enumerate(sides)]
+    N = int(np.prod(sides))
+    spec = ("sum", [("kron", [("dense", f) for f in F]), ("scalar", 0.05, N)], None)
+    ref = oracle_tree(spec)
+    op = gpu_tree(cola, ctx, spec, torch.float64, DEV).set_spd()
+    B = wl.normal(wl.substream(710, 9), (3, N))
+    opts = cola.cola_cg_opts_default(precision=cola.PREC_MIXED, refine=1, tol=1e-8,
+                                     maxiter=40000, split_factor_terms=3, split_vector_terms=3)
+    X, info, st = cola.cola_cg_solve(ctx, op, torch.tensor(B, device=DEV), opts)
+    assert st == 0, info
+    Xh = X.cpu().numpy()
+    res = krylov.true_relative_residual(ref, B, Xh)
+    assert np.all(res <= 1e-8), res
+    lam = exact.kron_eigenvalues(F, 0.05)
+    x_ref = exact.kron_shift_solve(F, 0.05, B)
+    fe = np.linalg.norm(Xh - x_ref, axis=1) / np.linalg.norm(x_ref, axis=1)
+    assert np.all(fe <= lam.max() / lam.min() * 1e-8), fe
+    Z = rng.rademacher_probes(11, 3, N)
+    m, j0 = 12, 8
+    al, be, me = cola.cola_lanczos(ctx, op, torch.tensor(Z, dtype=torch.float32, device=DEV), m,
+                                   cola.PREC_MIXED, reorth=0, split_terms=3)
+    al, be, me = al.cpu().numpy(), be.cpu().numpy(), me.cpu().numpy()
+    for v in range(3):
+        a, b, _ = krylov.lanczos(ref, Z[v], m, reorth=False)
+        assert me[v] == m
+        np.testing.assert_allclose(al[v, :j0], a[:j0], rtol=1e-5)
+        np.testing.assert_allclose(be[v, :j0], b[:j0], rtol=1e-5)

@@ -18,6 +18,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <string>
 
@@ -66,6 +67,9 @@ __device__ __forceinline__ double block_sum2(T v, double* out_other, T v2) {
 // by 1e6 since the last replacement; restart its search direction when a
 // replacement finds the true residual norm more than 10x the recursive one.
 constexpr double kPauseDrop2 = 1e-12;
+// A replacement costing more than this many iterations waits for half of the
+// right-hand sides (see cg_run).
+constexpr double kDeferRatio = 100.0;
 constexpr double kRestartGap2 = 100.0;
 
 // alpha = r^T z / p^T A p, with p^T A p the ordered sum of nparts partials.
@@ -1107,6 +1111,8 @@ static cola_status cg_run(Ctx* c, cola_linop* op, const void* Bin, void* Xout, i
   };
   int64_t iters = 0;
   int updates = 0;
+  bool defer = false;   // replacements wait for half of the right-hand sides
+  double iter_s = 0.0;  // host time per iteration of the fastest chunk so far
   // COLA_TRACE=1 prints the worst relative residual of the active right-hand
   // sides after every chunk and every FP64 replacement (stderr).
   const char* tr_env = getenv("COLA_TRACE");
@@ -1137,17 +1143,37 @@ static cola_status cg_run(Ctx* c, cola_linop* op, const void* Bin, void* Xout, i
   for (int verify = 0;; ++verify) {
   while (any_active) {
     if (iters >= o.maxiter) break;
+    const auto tc0 = std::chrono::steady_clock::now();
     cg_chunk<T>(c, op, B, N, R, nblk, prec, delta2, refine ? 1 : 0, chunk, graph_key());
     iters += chunk;
     read_state();
-    trace_line("chunk");
-    bool flag = false;
-    any_active = false;
-    for (int64_t r = 0; r < R; ++r) {
-      any_active |= hst[r].active != 0;
-      flag |= hst[r].active && hst[r].flag;
+    {
+      const double t = std::chrono::duration<double>(std::chrono::steady_clock::now() - tc0)
+                           .count() / chunk;
+      iter_s = iter_s > 0.0 ? std::min(iter_s, t) : t;
     }
+    trace_line("chunk");
+    // A replacement refreshes every right-hand side with one FP64 MVM of the
+    // whole block.  Where that costs more than kDeferRatio iterations (large
+    // factors: FP64 runs at a small fraction of the tensor rate on this GPU)
+    // it waits until at least half of the active right-hand sides ask for
+    // one, the others iterating meanwhile (a right-hand side whose recursion
+    // ran 1e6-fold ahead pauses, and a pause triggers it); otherwise the first
+    // request triggers it, which keeps the recursions closest to the true
+    // residuals (fewest iterations).  Decided once per solve from the host
+    // time of the first replacement and of the fastest chunk.
+    int nact = 0, nflag = 0;
+    bool paused = false;
+    for (int64_t r = 0; r < R; ++r) {
+      if (!hst[r].active) continue;
+      ++nact;
+      nflag += hst[r].flag ? 1 : 0;
+      paused |= hst[r].paused != 0;
+    }
+    any_active = nact > 0;
+    const bool flag = paused || (defer ? (nflag > 0 && 2 * nflag >= nact) : nflag > 0);
     if (refine && (flag || !any_active) && updates < o.max_updates) {
+      const auto tr0 = std::chrono::steady_clock::now();
       // FP64 residual replacement: x64 += x; r64 = b - A x64; r = (T) r64.
       k_accum_x<T><<<ew_blocks(N * R), 256, 0, c->s>>>(N * R, B.x64, B.x);
       c->count_launch();
@@ -1166,6 +1192,11 @@ static cola_status cg_run(Ctx* c, cola_linop* op, const void* Bin, void* Xout, i
       c->count_launch();
       ++updates;
       read_state();
+      if (updates == 1 && iter_s > 0.0) {
+        const double t_repl =
+            std::chrono::duration<double>(std::chrono::steady_clock::now() - tr0).count();
+        defer = t_repl > kDeferRatio * iter_s;
+      }
       trace_line("update");
       any_active = false;
       for (int64_t r = 0; r < R; ++r) any_active |= hst[r].active != 0;

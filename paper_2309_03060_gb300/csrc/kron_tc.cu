@@ -1409,47 +1409,80 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
       const int64_t tm = t / p.nchunks;
       const int64_t r = tm / p.tiles_m, m0 = (tm % p.tiles_m) * kTileM;
       const uint32_t taddr = tmem_base + lane_off + (uint32_t)b * 256u + (uint32_t)chalf * 64u;
-      float a[64];
-#pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        uint32_t v[8], w[8];
-        tmem_ld8(taddr + (uint32_t)(q * 8), v);
-        if (kSmall) tmem_ld8(taddr + 128u + (uint32_t)(q * 8), w);
-        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-        for (int e = 0; e < 8; ++e)
-          a[q * 8 + e] =
-              p.coeff * (__uint_as_float(v[e]) + (kSmall ? __uint_as_float(w[e]) : 0.0f));
-      }
-      tc_fence_before();
-      mbar_arrive(&aempty[b]);
       const int i = nc * kTileM + il;
       const int64_t mbase = m0 + chalf * 64;
       const int nrows = (int)((p.rest - mbase < 64) ? (p.rest - mbase) : 64);
+      const bool live = i < p.n_out && nrows > 0;
+      const int64_t ld = p.n_out;
+      float* yp = p.Y + r * p.size_out + mbase * ld + i;
+      const float* ex = p.epi_x ? p.epi_x + r * p.size_out + mbase * ld + i : nullptr;
+      const float* ed = (p.epi_x && p.epi_dstride) ? p.epi_d + mbase * ld + i : nullptr;
+      const float* eq = p.epi_q2 ? p.epi_q2 + r * p.size_out + mbase * ld + i : nullptr;
+      const float gam = p.epi_q2 ? (float)p.epi_gamma[r] : 0.0f;
+      const float sc = p.epi_coeff * d0;
       float part = 0.0f;  // this thread's <= 64 products of x . y
-      if (i < p.n_out && nrows > 0) {
-        const int64_t ld = p.n_out;
-        float* yp = p.Y + r * p.size_out + mbase * ld + i;
-        const float* ex = p.epi_x ? p.epi_x + r * p.size_out + mbase * ld + i : nullptr;
-        const float* ed = (p.epi_x && p.epi_dstride) ? p.epi_d + mbase * ld + i : nullptr;
-        const float* eq = p.epi_q2 ? p.epi_q2 + r * p.size_out + mbase * ld + i : nullptr;
-        const float gam = p.epi_q2 ? (float)p.epi_gamma[r] : 0.0f;
+      if (!ex && p.beta == 0.0f) {
+        // plain step: the whole accumulator into registers, released, stored
+        float a[64];
 #pragma unroll
-        for (int c = 0; c < 64; ++c) {
-          if (c < nrows) {
-            float v = a[c];
-            if (ex) {
-              const float xd = __ldg(ex + c * ld);
-              const float dv = ed ? __ldg(ed + c * ld) : d0;
-              v = fmaf(p.epi_coeff * dv, xd, v);
-              if (eq) v = fmaf(-gam, __ldg(eq + c * ld), v);
-              part = fmaf(v, xd, part);
-            }
-            if (p.beta != 0.0f) v = fmaf(p.beta, yp[c * ld], v);
-            yp[c * ld] = v;
+        for (int q = 0; q < 8; ++q) {
+          uint32_t v[8], w[8];
+          tmem_ld8(taddr + (uint32_t)(q * 8), v);
+          if (kSmall) tmem_ld8(taddr + 128u + (uint32_t)(q * 8), w);
+          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+          for (int e = 0; e < 8; ++e)
+            a[q * 8 + e] =
+                p.coeff * (__uint_as_float(v[e]) + (kSmall ? __uint_as_float(w[e]) : 0.0f));
+        }
+        tc_fence_before();
+        mbar_arrive(&aempty[b]);
+        if (live) {
+#pragma unroll
+          for (int c = 0; c < 64; ++c)
+            if (c < nrows) yp[c * ld] = a[c];
+        }
+        continue;
+      }
+      // 16 rows at a time: accumulator columns, then every load of the group,
+      // then its stores (the stores may alias the loaded arrays as far as the
+      // compiler knows, so loads interleaved with them would cost one global
+      // latency per row); the accumulator is released after the last group
+      // (the MMAs meanwhile fill the other buffer)
+#pragma unroll 1
+      for (int h = 0; h < 4; ++h) {
+        uint32_t v[16], w[16];
+        tmem_ld8(taddr + (uint32_t)(h * 16), v);
+        tmem_ld8(taddr + (uint32_t)(h * 16 + 8), v + 8);
+        if (kSmall) {
+          tmem_ld8(taddr + 128u + (uint32_t)(h * 16), w);
+          tmem_ld8(taddr + 128u + (uint32_t)(h * 16 + 8), w + 8);
+        }
+        float xd[16], dd[16], qd[16], yo[16];
+#pragma unroll
+        for (int e = 0; e < 16; ++e) {
+          const bool in = live && h * 16 + e < nrows;
+          xd[e] = (ex && in) ? __ldg(ex + (h * 16 + e) * ld) : 0.0f;
+          dd[e] = (ed && in) ? __ldg(ed + (h * 16 + e) * ld) : 0.0f;
+          qd[e] = (eq && in) ? __ldg(eq + (h * 16 + e) * ld) : 0.0f;
+          yo[e] = (p.beta != 0.0f && in) ? yp[(h * 16 + e) * ld] : 0.0f;
+        }
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+        for (int e = 0; e < 16; ++e) {
+          float y = p.coeff * (__uint_as_float(v[e]) + (kSmall ? __uint_as_float(w[e]) : 0.0f));
+          const bool in = live && h * 16 + e < nrows;
+          if (ex) {
+            y = fmaf(ed ? p.epi_coeff * dd[e] : sc, xd[e], y);
+            if (eq) y = fmaf(-gam, qd[e], y);
+            if (in) part = fmaf(y, xd[e], part);
           }
+          y = fmaf(p.beta, yo[e], y);
+          if (in) yp[(h * 16 + e) * ld] = y;
         }
       }
+      tc_fence_before();
+      mbar_arrive(&aempty[b]);
       if (p.epi_dot) {
         double dsum = (double)part;
 #pragma unroll

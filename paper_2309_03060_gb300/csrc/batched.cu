@@ -466,7 +466,9 @@ cola_status batched_cg_fast(Ctx* c, int32_t nsys, const cola_linop* const* ops,
                               c->s));
     COLA_CUDA(cudaStreamSynchronize(c->s));
   };
+  constexpr int kChunkGemm = 128;  // output chunk of the split GEMM form
   int tile_cap = kBatchChunkCap, tile_stages = 0;  // set by the tuner below
+  bool use_gemm = false;  // split GEMM form of the mode steps (tuner's choice)
   tdot_layout(tile_cap);
   upload_slot_tables();
 
@@ -484,6 +486,8 @@ cola_status batched_cg_fast(Ctx* c, int32_t nsys, const cola_linop* const* ops,
   // (re-reads of the same X rows by several output chunks stay idempotent).
   static const char* kTc1[2] = {"bcg.tc1a", "bcg.tc1b"};
   static const char* kTc2[2] = {"bcg.tc2a", "bcg.tc2b"};
+  static const char* kGm1[2] = {"bcg.gm1a", "bcg.gm1b"};
+  static const char* kGm2[2] = {"bcg.gm2a", "bcg.gm2b"};
   auto tc_tables = [&](const std::vector<char>& lv) {
     tdot_layout(tile_cap);
     for (int q = 0; q < 2; ++q) {
@@ -520,8 +524,14 @@ cola_status batched_cg_fast(Ctx* c, int32_t nsys, const cola_linop* const* ops,
         q2.epi_dot = tdot + tdot_off[s];
         s2.push_back(q2);
       }
-      kron_tc_batch_upload(c, s1, tf, tv, kTc1[q], tile_cap);
-      kron_tc_batch_upload(c, s2, tf, tv, kTc2[q], tile_cap);
+      if (use_gemm) {
+        // step 1's and step 2's pre-split images never live at the same time
+        kron_tc_gemm_batch_upload(c, s1, tf, tv, kGm1[q], "bcg.gimg1");
+        kron_tc_gemm_batch_upload(c, s2, tf, tv, kGm2[q], "bcg.gimg2");
+      } else {
+        kron_tc_batch_upload(c, s1, tf, tv, kTc1[q], tile_cap);
+        kron_tc_batch_upload(c, s2, tf, tv, kTc2[q], tile_cap);
+      }
     }
   };
 
@@ -589,11 +599,12 @@ cola_status batched_cg_fast(Ctx* c, int32_t nsys, const cola_linop* const* ops,
     c->count_launch();
     COLA_CUDA(cudaGetLastError());
   }
-  // Tile-shape autotuner: the output-chunk width (N tile, 64 or 128 columns)
-  // and the pipeline depth of the batched tensor-core launch are timed on
-  // this batch's own mode steps (two launches per MVM, CUDA events, parity-0
-  // tables; outputs go to scratch buffers the first iteration rewrites), and
-  // the fastest is cached per (terms, histogram of factor sizes and RHS counts).
+  // Autotuner: the output-chunk width (N tile, 64 or 128 columns) and the
+  // pipeline depth of the streaming table kernel, and the split GEMM form
+  // (pre-split pass + table-driven GEMM, 128-output chunks), are timed on this
+  // batch's own mode steps (CUDA events, parity-0 tables; outputs go to
+  // scratch buffers the first iteration rewrites), and the fastest is cached
+  // per (terms, histogram of factor sizes and RHS counts).
   {
     std::map<std::tuple<int, int, int64_t>, int> hist;
     for (auto& s : sys)
@@ -607,6 +618,7 @@ cola_status batched_cg_fast(Ctx* c, int32_t nsys, const cola_linop* const* ops,
     if (hit != c->tuned.end()) {
       tile_cap = hit->second.first;
       tile_stages = hit->second.second;
+      use_gemm = tile_stages < 0;
     } else {
       cudaEvent_t e0, e1;
       COLA_CUDA(cudaEventCreate(&e0));
@@ -637,16 +649,43 @@ cola_status batched_cg_fast(Ctx* c, int32_t nsys, const cola_linop* const* ops,
           }
         }
       }
+      {
+        use_gemm = true;
+        tile_cap = kChunkGemm;
+        tc_tables(live);
+        kron_tc_gemm_batch_launch(c, kGm1[0], tf, tv);  // warm-up
+        kron_tc_gemm_batch_launch(c, kGm2[0], tf, tv);
+        COLA_CUDA(cudaEventRecord(e0, c->s));
+        for (int rep = 0; rep < 2; ++rep) {
+          kron_tc_gemm_batch_launch(c, kGm1[0], tf, tv);
+          kron_tc_gemm_batch_launch(c, kGm2[0], tf, tv);
+        }
+        COLA_CUDA(cudaEventRecord(e1, c->s));
+        COLA_CUDA(cudaEventSynchronize(e1));
+        float ms = 0.0f;
+        COLA_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+        if (ms < best) {
+          best = ms;
+          best_cap = kChunkGemm;
+          best_st = -1;  // the split GEMM form
+        }
+      }
       cudaEventDestroy(e0);
       cudaEventDestroy(e1);
       tc_check_error(c);
       tile_cap = best_cap;
       tile_stages = best_st;
+      use_gemm = tile_stages < 0;
       c->tuned[tkey] = std::make_pair(tile_cap, tile_stages);
     }
     const char* tr = getenv("COLA_TRACE");
-    if (tr && tr[0] == '1')
-      fprintf(stderr, "[cola batched] N tile <= %d columns, %d stages\n", tile_cap, tile_stages);
+    if (tr && tr[0] == '1') {
+      if (use_gemm)
+        fprintf(stderr, "[cola batched] split GEMM form\n");
+      else
+        fprintf(stderr, "[cola batched] N tile <= %d columns, %d stages\n", tile_cap,
+                tile_stages);
+    }
   }
   tc_tables(live);
   upload_slot_tables();
@@ -654,8 +693,13 @@ cola_status batched_cg_fast(Ctx* c, int32_t nsys, const cola_linop* const* ops,
   const int max_chunk = max_chunk_for(tile_cap);
   int cur = 0;  // parity: the current search direction is pbuf[cur]
   auto iteration = [&] {
-    kron_tc_batch_launch(c, kTc1[cur], tf, tv, max_chunk, tile_stages);
-    kron_tc_batch_launch(c, kTc2[cur], tf, tv, max_chunk, tile_stages);
+    if (use_gemm) {
+      kron_tc_gemm_batch_launch(c, kGm1[cur], tf, tv);
+      kron_tc_gemm_batch_launch(c, kGm2[cur], tf, tv);
+    } else {
+      kron_tc_batch_launch(c, kTc1[cur], tf, tv, max_chunk, tile_stages);
+      kron_tc_batch_launch(c, kTc2[cur], tf, tv, max_chunk, tile_stages);
+    }
     float* p_new = pbuf[cur ^ 1];
     cur ^= 1;
     k_seg_alpha<<<small_grid(G), 128, 0, c->s>>>(st, live_seg.seg_list, live_seg.nseg, seg_p0,

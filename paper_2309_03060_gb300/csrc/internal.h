@@ -352,6 +352,17 @@ std::vector<int64_t> kron_tc_batch_upload(Ctx* c, const std::vector<TcBatchProbl
 // `stages` pipeline stages (0: as many as fit, at most 4).
 void kron_tc_batch_launch(Ctx* c, const char* tag, int tf, int tv, int max_n_chunk, int stages);
 int kron_tc_batch_max_stages(int tf, int tv, int max_n_chunk);
+// Split GEMM form of a batched mode step (kron_tc.cu): uploads its tables under
+// `tag`, the pre-split images in the workspace buffer `image` (one buffer may
+// serve the table sets of steps that never run at the same time), and returns
+// the tiles per problem (128-row tiles x 128-output chunks, chunk fastest:
+// the p . Ap slots follow this tile order).
+std::vector<int64_t> kron_tc_gemm_batch_upload(Ctx* c, const std::vector<TcBatchProblem>& probs,
+                                               int tf, int tv, const char* tag,
+                                               const char* image);
+// Launches the pre-split pass and the persistent split GEMM over the tables
+// uploaded under `tag`.
+void kron_tc_gemm_batch_launch(Ctx* c, const char* tag, int tf, int tv);
 // Chunk width (and count) of n_out output columns under a chunk cap.
 int kron_tc_chunk_width(int n_out, int chunk_cap, int* nchunks);
 

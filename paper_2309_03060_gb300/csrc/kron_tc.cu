@@ -1175,12 +1175,17 @@ __global__ void __launch_bounds__(kThreadsFs, 1) k_kron_tc_fs(const __grid_const
 constexpr int kGemmThreads = 320;
 constexpr uint32_t kGemmTermBytes = (uint32_t)kTileM * 128u;  // 128 rows x 64 BF16
 
+// One problem of the split GEMM (a mode step of one operator, all its
+// right-hand sides).
 struct TcGemmParams {
-  CUtensorMap tm_x;      // X image [TV * xrows][kpad] BF16, box 64 x 128, 128-byte swizzle
+  CUtensorMap tm_x;      // one problem: X image [TV * xrows][kpad] BF16, box 64 x 128,
+                         // 128-byte swizzle (TMA)
+  const uint16_t* ximg;  // batched: X image [TV][kblocks][rows_pad][64] BF16, rows pre-swizzled
+                         // (bulk copies); rows_pad = R tiles_m 128 (128-row aligned per RHS)
   const uint16_t* Bimg;  // factor image [tf][kblocks][img_rows][64] BF16, swizzled rows
   float* Y;
-  int64_t rest, size_out, tiles_m, ntiles, xrows;  // xrows = R * rest
-  int n_out, nchunks, kblocks, img_rows, stages;
+  int64_t rest, size_out, tiles_m, ntiles, xrows, rows_pad;  // xrows = R * rest
+  int n_out, nchunks, kblocks, img_rows;
   float coeff, beta;
   const float* epi_x;  // epilogue terms as in TcParams
   const float* epi_d;
@@ -1189,27 +1194,66 @@ struct TcGemmParams {
   double* epi_dot;
   const float* epi_q2;
   const double* epi_gamma;
-  int* err;
-  uint64_t stall_ns;
+  // batched pre-split pass: the step's input and its fused first-step terms
+  const float* X;
+  const float* pro_z;
+  const double* pro_beta;
+  float* pro_out;
+  int n_in, kpad, mode;  // mode as k_presplit's
+  int64_t R;
 };
 
-// Pre-split pass: X [R][n_in][rest] FP32 (mode 0), or beta_r X + z (mode 2)
-// or beta_r X (mode 1), both also written to pro_out, into TV K-major BF16
-// term images img[t][r rest + m][kpad] (zero for k >= n_in).  A block moves a
-// 64 (k) x 64 (m) tile through shared memory: reads along m, writes 128-byte
-// rows along k.
-template <int TV>
-__global__ void __launch_bounds__(256) k_presplit(const float* X, int n_in, int64_t rest,
-                                                  int kpad, int64_t xrows, int mode,
-                                                  const float* pro_z, const double* pro_beta,
-                                                  float* pro_out, uint16_t* img) {
-  __shared__ float tile[64][65];
-  const int64_t m0 = (int64_t)blockIdx.x * 64, r = blockIdx.z;
-  const int k0 = blockIdx.y * 64;
+// Launch-wide settings of the split GEMM.
+struct TcGemmLaunch {
+  int stages;
+  int* err;
+  uint64_t stall_ns;  // > 0: time-out test (see TcParams)
+};
+
+// Tile sources of the split GEMM: one problem by value (X by TMA), or a
+// device table of problems (X by bulk copies of pre-swizzled images).
+struct GemmOne {
+  static constexpr bool kTma = true;
+  TcGemmParams p;
+  __device__ __forceinline__ int64_t count() const { return p.ntiles; }
+  __device__ __forceinline__ const TcGemmParams& get(int64_t t, int64_t& lt) const {
+    lt = t;
+    return p;
+  }
+};
+struct GemmTab {
+  static constexpr bool kTma = false;
+  const TcGemmParams* probs;
+  const int* tile_prob;      // problem of every global tile
+  const int64_t* first;      // first global tile of every problem
+  const int64_t* count_dev;  // number of live tiles (read at kernel start)
+  __device__ __forceinline__ int64_t count() const { return *count_dev; }
+  __device__ __forceinline__ const TcGemmParams& get(int64_t t, int64_t& lt) const {
+    const int i = tile_prob[t];
+    lt = t - first[i];
+    return probs[i];
+  }
+};
+
+// One 64 (k) x 64 (m) tile of the pre-split pass: X [R][n_in][rest] FP32
+// (mode 0), or beta_r X + z (mode 2) or beta_r X (mode 1), both also written
+// to pro_out, into TV K-major BF16 terms (zero for k >= n_in), through shared
+// memory: reads along m, writes 16-byte runs of 8 k along each row.  SWZ
+// false: img[t][xrows][kpad], rows r rest + m (the TMA-loaded layout); SWZ
+// true: img[t][kblocks][rows_pad][64], rows r rest128 + m with rest128 =
+// rest rounded up to 128 (every 128-row tile starts on an 8-row boundary, and
+// a tile's rows past rest are zero padding), the 16-byte runs of row j at
+// position c ^ (j mod 8) (the bulk-copied layout of a 128-byte swizzled
+// K-major operand).
+template <int TV, bool SWZ>
+__device__ __forceinline__ void presplit_tile(float (*tile)[65], const float* X, int n_in,
+                                              int64_t rest, int kpad, int64_t xrows,
+                                              int64_t rows_pad, int mode, const float* pro_z,
+                                              const double* pro_beta, float* pro_out,
+                                              uint16_t* img, int64_t r, int64_t m0, int k0) {
   const int64_t off = r * (int64_t)n_in * rest;
   const float beta_r = mode != 0 ? (float)pro_beta[r] : 0.0f;
-  pdl_wait();
-  for (int e = threadIdx.x; e < 64 * 64; e += 256) {
+  for (int e = threadIdx.x; e < 64 * 64; e += blockDim.x) {
     const int kl = e >> 6, ml = e & 63;
     const int k = k0 + kl;
     const int64_t m = m0 + ml;
@@ -1228,7 +1272,7 @@ __global__ void __launch_bounds__(256) k_presplit(const float* X, int n_in, int6
     tile[kl][ml] = v;
   }
   __syncthreads();
-  for (int e = threadIdx.x; e < 64 * 8; e += 256) {
+  for (int e = threadIdx.x; e < 64 * 8; e += blockDim.x) {
     const int ml = e >> 3, ch = e & 7;
     const int64_t m = m0 + ml;
     if (m >= rest) continue;
@@ -1241,24 +1285,70 @@ __global__ void __launch_bounds__(256) k_presplit(const float* X, int n_in, int6
       w[1][j] = o[1];
       w[2][j] = o[2];
     }
+    const int64_t row = SWZ ? r * ((rest + kTileM - 1) / kTileM * kTileM) + m : r * rest + m;
 #pragma unroll
-    for (int t = 0; t < TV; ++t)
-      *reinterpret_cast<uint4*>(img + ((size_t)t * xrows + r * rest + m) * kpad + k0 + ch * 8) =
-          make_uint4(w[t][0], w[t][1], w[t][2], w[t][3]);
+    for (int t = 0; t < TV; ++t) {
+      size_t pos;
+      if (SWZ) {
+        const int kblocks = kpad / kBlockK;
+        pos = (((size_t)t * kblocks + k0 / kBlockK) * rows_pad + row) * kBlockK +
+              (size_t)((ch ^ (int)(row & 7)) * 8);
+      } else {
+        pos = ((size_t)t * xrows + row) * kpad + k0 + ch * 8;
+      }
+      *reinterpret_cast<uint4*>(img + pos) = make_uint4(w[t][0], w[t][1], w[t][2], w[t][3]);
+    }
+  }
+  __syncthreads();  // the tile is reused by the block's next tile
+}
+
+// Pre-split pass of one mode step: block (m tile, k tile, right-hand side).
+template <int TV>
+__global__ void __launch_bounds__(256) k_presplit(const float* X, int n_in, int64_t rest,
+                                                  int kpad, int64_t xrows, int mode,
+                                                  const float* pro_z, const double* pro_beta,
+                                                  float* pro_out, uint16_t* img) {
+  __shared__ float tile[64][65];
+  pdl_wait();
+  presplit_tile<TV, false>(tile, X, n_in, rest, kpad, xrows, 0, mode, pro_z, pro_beta, pro_out,
+                           img, blockIdx.z, (int64_t)blockIdx.x * 64, blockIdx.y * 64);
+}
+
+// Pre-split pass of a batched mode step: persistent blocks over a table of
+// tiles (tile -> problem; a problem's tiles run over right-hand side, m tile,
+// k tile with the k tile fastest).
+template <int TV>
+__global__ void __launch_bounds__(256) k_presplit_tab(const TcGemmParams* probs,
+                                                      const int* tile_prob, const int64_t* first,
+                                                      const int64_t* count_dev) {
+  __shared__ float tile[64][65];
+  pdl_wait();
+  const int64_t n = *count_dev;
+  for (int64_t t = blockIdx.x; t < n; t += gridDim.x) {
+    const int i = tile_prob[t];
+    const TcGemmParams& q = probs[i];
+    const int64_t lt = t - first[i];
+    const int nk = q.kpad / 64;
+    const int64_t nm = (q.rest + 63) / 64;
+    const int kt = (int)(lt % nk);
+    const int64_t mt = (lt / nk) % nm, r = lt / nk / nm;
+    presplit_tile<TV, true>(tile, q.X, q.n_in, q.rest, q.kpad, q.xrows, q.rows_pad, q.mode,
+                            q.pro_z, q.pro_beta, q.pro_out, const_cast<uint16_t*>(q.ximg), r,
+                            mt * 64, kt * 64);
   }
 }
 
-template <int TF, int TV>
+template <int TF, int TV, class Src>
 __global__ void __launch_bounds__(kGemmThreads, 1)
-    k_kron_tc_gemm(const __grid_constant__ TcGemmParams p) {
+    k_kron_tc_gemm(const __grid_constant__ Src src, const TcGemmLaunch L) {
   constexpr int kMaxT = TF > TV ? TF : TV;
   constexpr bool kSmall = TF > 1 || TV > 1;
   constexpr uint32_t kStageBytes = (uint32_t)(TF + TV) * kGemmTermBytes;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* base = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
-  uint64_t* full = (uint64_t*)(base + (size_t)p.stages * kStageBytes);  // [stages]
-  uint64_t* empty = full + p.stages;                                   // [stages]
-  uint64_t* afull = empty + p.stages;                                  // [2]
+  uint64_t* full = (uint64_t*)(base + (size_t)L.stages * kStageBytes);  // [stages]
+  uint64_t* empty = full + L.stages;                                   // [stages]
+  uint64_t* afull = empty + L.stages;                                  // [2]
   uint64_t* aempty = afull + 2;                                        // [2]
   uint64_t* drain = aempty + 2;
   uint64_t* stall = drain + 1;  // never completed (time-out test)
@@ -1266,7 +1356,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
   volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if (tid == 0) {
-    for (int s = 0; s < p.stages; ++s) {
+    for (int s = 0; s < L.stages; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
@@ -1300,41 +1390,53 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
       int s = 0;
       uint32_t ph = 0;
       uint32_t issued = 0, issued_ph = 0;  // bit s: a copy went to stage s / its parity
-      for (int64_t t = blockIdx.x; t < p.ntiles && ok; t += gridDim.x) {
-        const int nc = (int)(t % p.nchunks);
-        const int64_t tm = t / p.nchunks;
+      const int64_t ntiles = src.count();
+      for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+        int64_t lt;
+        const TcGemmParams& p = src.get(t, lt);
+        const int nc = (int)(lt % p.nchunks);
+        const int64_t tm = lt / p.nchunks;
         const int64_t r = tm / p.tiles_m, m0 = (tm % p.tiles_m) * kTileM;
+        const int kblocks = p.kblocks, img_rows = p.img_rows;
+        const uint16_t* bimg = p.Bimg;
         // rows past rest arrive as the next right-hand side's rows (or zeros
         // past the image); the epilogue masks them
         const int y0 = (int)(r * p.rest + m0);
-        for (int kb = 0; kb < p.kblocks; ++kb) {
-          if (!mbar_wait(&empty[s], ph ^ 1u, abort_flag, p.err)) {
+        for (int kb = 0; kb < kblocks; ++kb) {
+          if (!mbar_wait(&empty[s], ph ^ 1u, abort_flag, L.err)) {
             ok = false;
             break;
           }
           unsigned char* st = base + (size_t)s * kStageBytes;
           mbar_arrive_expect_tx(&full[s], kStageBytes);
 #pragma unroll
-          for (int tv = 0; tv < TV; ++tv)
-            tma_load_2d(st + tv * kGemmTermBytes, &p.tm_x, kb * kBlockK,
-                        (int)(tv * p.xrows) + y0, &full[s]);
+          for (int tv = 0; tv < TV; ++tv) {
+            if constexpr (Src::kTma)
+              tma_load_2d(st + tv * kGemmTermBytes, &p.tm_x, kb * kBlockK,
+                          (int)(tv * p.xrows) + y0, &full[s]);
+            else
+              bulk_g2s(st + tv * kGemmTermBytes,
+                       p.ximg + (((size_t)tv * kblocks + kb) * (size_t)p.rows_pad +
+                                 (size_t)((r * p.tiles_m) * kTileM + m0)) * kBlockK,
+                       kGemmTermBytes, &full[s]);
+          }
 #pragma unroll
           for (int ti = 0; ti < TF; ++ti)
             bulk_g2s(st + (TV + ti) * kGemmTermBytes,
-                     p.Bimg + (((size_t)ti * p.kblocks + kb) * (size_t)p.img_rows +
+                     bimg + (((size_t)ti * kblocks + kb) * (size_t)img_rows +
                                (size_t)nc * kTileM) * kBlockK,
                      kGemmTermBytes, &full[s]);
           issued |= 1u << s;
           issued_ph = (issued_ph & ~(1u << s)) | (ph << s);
-          if (++s == p.stages) {
+          if (++s == L.stages) {
             s = 0;
             ph ^= 1u;
           }
         }
       }
       // only the latest copy of each stage can still be in flight
-      for (int st = 0; st < p.stages; ++st)
-        if (issued & (1u << st)) mbar_wait_own(&full[st], (issued_ph >> st) & 1u, p.err);
+      for (int st = 0; st < L.stages; ++st)
+        if (issued & (1u << st)) mbar_wait_own(&full[st], (issued_ph >> st) & 1u, L.err);
     }
     __syncwarp();
   } else if (warp == 1) {
@@ -1342,18 +1444,21 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
     if (lane == 0) {
       constexpr uint32_t idesc = idesc_bf16(kTileM, kTileM);  // M = outputs, N = rows
       bool ok = true;
-      if (p.stall_ns) ok = mbar_wait_slow(stall, 0, abort_flag, p.err, p.stall_ns);
+      if (L.stall_ns) ok = mbar_wait_slow(stall, 0, abort_flag, L.err, L.stall_ns);
       int s = 0;
       uint32_t ph = 0;
       int64_t it = 0;
-      for (int64_t t = blockIdx.x; t < p.ntiles && ok; t += gridDim.x, ++it) {
+      const int64_t ntiles = src.count();
+      for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++it) {
+        int64_t lt;
+        const int kblocks = src.get(t, lt).kblocks;
         const int b = (int)(it & 1);
-        if (!mbar_wait(&aempty[b], (uint32_t)((it >> 1) & 1) ^ 1u, abort_flag, p.err)) break;
+        if (!mbar_wait(&aempty[b], (uint32_t)((it >> 1) & 1) ^ 1u, abort_flag, L.err)) break;
         tc_fence_after();
         const uint32_t d_big = tmem_base + (uint32_t)b * 256u, d_small = d_big + 128u;
         uint32_t acc_big = 0, acc_small = 0;
-        for (int kb = 0; kb < p.kblocks; ++kb) {
-          if (!mbar_wait(&full[s], ph, abort_flag, p.err)) {
+        for (int kb = 0; kb < kblocks; ++kb) {
+          if (!mbar_wait(&full[s], ph, abort_flag, L.err)) {
             ok = false;
             break;
           }
@@ -1380,7 +1485,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
               }
           }
           mma_commit(&empty[s]);
-          if (++s == p.stages) {
+          if (++s == L.stages) {
             s = 0;
             ph ^= 1u;
           }
@@ -1389,7 +1494,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
         mma_commit(&afull[b]);
       }
       mma_commit(drain);
-      mbar_wait_own(drain, 0, p.err);
+      mbar_wait_own(drain, 0, L.err);
     }
     __syncwarp();
   } else {
@@ -1399,14 +1504,17 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
     const int quarter = warp & 3, chalf = ew >> 2;
     const int il = quarter * 32 + lane;  // output within the chunk = TMEM lane
     const uint32_t lane_off = (uint32_t)(quarter * 32) << 16;
-    const float d0 = (p.epi_x && p.epi_dstride == 0) ? p.epi_d[0] : 0.0f;
     int64_t it = 0;
-    for (int64_t t = blockIdx.x; t < p.ntiles; t += gridDim.x, ++it) {
+    const int64_t ntiles = src.count();
+    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
       const int b = (int)(it & 1);
-      if (!mbar_wait(&afull[b], (uint32_t)((it >> 1) & 1), abort_flag, p.err)) break;
+      if (!mbar_wait(&afull[b], (uint32_t)((it >> 1) & 1), abort_flag, L.err)) break;
       tc_fence_after();
-      const int nc = (int)(t % p.nchunks);
-      const int64_t tm = t / p.nchunks;
+      int64_t lt;
+      const TcGemmParams& p = src.get(t, lt);
+      const float d0 = (p.epi_x && p.epi_dstride == 0) ? p.epi_d[0] : 0.0f;
+      const int nc = (int)(lt % p.nchunks);
+      const int64_t tm = lt / p.nchunks;
       const int64_t r = tm / p.tiles_m, m0 = (tm % p.tiles_m) * kTileM;
       const uint32_t taddr = tmem_base + lane_off + (uint32_t)b * 256u + (uint32_t)chalf * 64u;
       const int i = nc * kTileM + il;
@@ -1487,7 +1595,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
         double dsum = (double)part;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) dsum += __shfl_xor_sync(0xffffffffu, dsum, o);
-        if (lane == 0) p.epi_dot[t * kDotSlots + ew] = dsum;
+        if (lane == 0) p.epi_dot[lt * kDotSlots + ew] = dsum;
       }
     }
   }
@@ -2158,12 +2266,14 @@ static bool tmap_image(CUtensorMap* m, const uint16_t* base, int64_t rows, int64
              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-using GemmKernel = void (*)(TcGemmParams);
-static GemmKernel gemm_kernel(int tf, int tv) {
-  static const GemmKernel tab[3][3] = {
-      {k_kron_tc_gemm<1, 1>, k_kron_tc_gemm<1, 2>, k_kron_tc_gemm<1, 3>},
-      {k_kron_tc_gemm<2, 1>, k_kron_tc_gemm<2, 2>, k_kron_tc_gemm<2, 3>},
-      {k_kron_tc_gemm<3, 1>, k_kron_tc_gemm<3, 2>, k_kron_tc_gemm<3, 3>}};
+template <class Src>
+using GemmKernel = void (*)(Src, TcGemmLaunch);
+template <class Src>
+static GemmKernel<Src> gemm_kernel(int tf, int tv) {
+  static const GemmKernel<Src> tab[3][3] = {
+      {k_kron_tc_gemm<1, 1, Src>, k_kron_tc_gemm<1, 2, Src>, k_kron_tc_gemm<1, 3, Src>},
+      {k_kron_tc_gemm<2, 1, Src>, k_kron_tc_gemm<2, 2, Src>, k_kron_tc_gemm<2, 3, Src>},
+      {k_kron_tc_gemm<3, 1, Src>, k_kron_tc_gemm<3, 2, Src>, k_kron_tc_gemm<3, 3, Src>}};
   return tab[tf - 1][tv - 1];
 }
 using PresplitKernel = void (*)(const float*, int, int64_t, int, int64_t, int, const float*,
@@ -2181,6 +2291,47 @@ static size_t gemm_smem(int tf, int tv) {
 // GEMM.  The factor's GEMM image (128-row output chunks) is made on first use
 // outside graph capture; false (the caller takes the streaming kernel) while
 // it does not exist yet, or when the step has a form the GEMM does not take.
+// The split GEMM's image of a factor: [tf][kblocks][nch * 128][64] BF16 with
+// swizzled rows (128-row output chunks, zero past the factor), made on first
+// use; nullptr while it does not exist and the stream is being captured.
+static const uint16_t* gemm_factor_image(Ctx* c, const cola_linop* f, bool tr, int tf) {
+  const int n_out = (int)(tr ? f->cols : f->rows), n_in = (int)(tr ? f->rows : f->cols);
+  const int kblocks = (n_in + kBlockK - 1) / kBlockK;
+  const int img_rows = (n_out + kTileM - 1) / kTileM * kTileM;
+  cola_linop* fm = const_cast<cola_linop*>(f);
+  const int key = 120 + (tr ? 10 : 0) + tf;
+  if (!prep_fresh(f, key)) {
+    if (c->capturing) return nullptr;
+    const size_t per_term = (size_t)kblocks * img_rows * kBlockK;
+    auto it = fm->derived.find(key);
+    if (it != fm->derived.end() && it->second.bytes < per_term * tf * 2) {
+      cudaFree(it->second.p);
+      fm->derived.erase(it);
+      it = fm->derived.end();
+    }
+    void* img = nullptr;
+    if (it == fm->derived.end()) {
+      COLA_CUDA(cudaMalloc(&img, per_term * tf * 2));
+      fm->derived[key] = Buf{img, per_term * (size_t)tf * 2};
+    } else {
+      img = it->second.p;
+    }
+    const int grid = (int)std::min<size_t>(1024, (per_term + 255) / 256);
+    if (f->dtype == COLA_F64)
+      k_split_factor<double><<<grid, 256, 0, c->s>>>((const double*)f->data, f->ld, tr ? 1 : 0,
+                                                      n_out, n_in, img_rows, kblocks, tf,
+                                                      (uint16_t*)img);
+    else
+      k_split_factor<float><<<grid, 256, 0, c->s>>>((const float*)f->data, f->ld, tr ? 1 : 0,
+                                                    n_out, n_in, img_rows, kblocks, tf,
+                                                    (uint16_t*)img);
+    c->count_launch();
+    COLA_CUDA(cudaGetLastError());
+    prep_mark(fm, key);
+  }
+  return (const uint16_t*)f->derived.at(key).p;
+}
+
 static bool gemm_launch(Ctx* c, const cola_linop* f, bool tr, const TcParams& p, int depth,
                         int k) {
   if (p.n_in <= kTileM && p.n_out <= kTileM) return false;  // the factor-stationary kernel's
@@ -2189,37 +2340,8 @@ static bool gemm_launch(Ctx* c, const cola_linop* f, bool tr, const TcParams& p,
   const int nch = (p.n_out + kTileM - 1) / kTileM, img_rows = nch * kTileM;
   const int64_t xrows = p.batch * p.rest;
   if ((int64_t)p.tv * xrows > INT32_MAX || p.rest > INT32_MAX) return false;
-  cola_linop* fm = const_cast<cola_linop*>(f);
-  const int key = 120 + (tr ? 10 : 0) + p.tf;
-  if (!prep_fresh(f, key)) {
-    if (c->capturing) return false;
-    const size_t per_term = (size_t)kblocks * img_rows * kBlockK;
-    auto it = fm->derived.find(key);
-    if (it != fm->derived.end() && it->second.bytes < per_term * p.tf * 2) {
-      cudaFree(it->second.p);
-      fm->derived.erase(it);
-      it = fm->derived.end();
-    }
-    void* img = nullptr;
-    if (it == fm->derived.end()) {
-      COLA_CUDA(cudaMalloc(&img, per_term * p.tf * 2));
-      fm->derived[key] = Buf{img, per_term * (size_t)p.tf * 2};
-    } else {
-      img = it->second.p;
-    }
-    const int grid = (int)std::min<size_t>(1024, (per_term + 255) / 256);
-    if (f->dtype == COLA_F64)
-      k_split_factor<double><<<grid, 256, 0, c->s>>>((const double*)f->data, f->ld, tr ? 1 : 0,
-                                                      p.n_out, p.n_in, img_rows, kblocks, p.tf,
-                                                      (uint16_t*)img);
-    else
-      k_split_factor<float><<<grid, 256, 0, c->s>>>((const float*)f->data, f->ld, tr ? 1 : 0,
-                                                    p.n_out, p.n_in, img_rows, kblocks, p.tf,
-                                                    (uint16_t*)img);
-    c->count_launch();
-    COLA_CUDA(cudaGetLastError());
-    prep_mark(fm, key);
-  }
+  const uint16_t* fimg = gemm_factor_image(c, f, tr, p.tf);
+  if (!fimg) return false;
   uint16_t* ximg = (uint16_t*)c->ws.get(depth_name("kgemm", depth, k & 1),
                                         (size_t)p.tv * xrows * kpad * 2);
   TcGemmParams g{};
@@ -2230,7 +2352,7 @@ static bool gemm_launch(Ctx* c, const cola_linop* f, bool tr, const TcParams& p,
                                                   p.pro_beta, p.pro_out, ximg);
   c->count_launch();
   COLA_CUDA(cudaGetLastError());
-  g.Bimg = (const uint16_t*)f->derived.at(key).p;
+  g.Bimg = fimg;
   g.Y = p.Y;
   g.rest = p.rest;
   g.size_out = p.size_out;
@@ -2241,7 +2363,6 @@ static bool gemm_launch(Ctx* c, const cola_linop* f, bool tr, const TcParams& p,
   g.n_out = p.n_out;
   g.kblocks = kblocks;
   g.img_rows = img_rows;
-  g.stages = kGemmStages;
   g.coeff = p.coeff;
   g.beta = p.beta;
   g.epi_x = p.epi_x;
@@ -2251,11 +2372,10 @@ static bool gemm_launch(Ctx* c, const cola_linop* f, bool tr, const TcParams& p,
   g.epi_dot = p.epi_dot;
   g.epi_q2 = p.epi_q2;
   g.epi_gamma = p.epi_gamma;
-  g.err = p.err;
-  g.stall_ns = p.stall_ns;
+  TcGemmLaunch L{kGemmStages, p.err, p.stall_ns};
   const int grid = (int)std::min<int64_t>(g.ntiles, c->num_sms);
-  launch_pdl(gemm_kernel(p.tf, p.tv), dim3(grid), dim3(kGemmThreads), gemm_smem(p.tf, p.tv), c->s,
-             g);
+  launch_pdl(gemm_kernel<GemmOne>(p.tf, p.tv), dim3(grid), dim3(kGemmThreads),
+             gemm_smem(p.tf, p.tv), c->s, GemmOne{g}, L);
   c->count_launch();
   COLA_CUDA(cudaGetLastError());
   return true;
@@ -2387,7 +2507,10 @@ static int64_t kron_tc_run(Ctx* c, const cola_linop* op, const float* X, float* 
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemMax));
           COLA_CUDA(cudaFuncSetAttribute(slab_kernel(a, b),
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemMax));
-          COLA_CUDA(cudaFuncSetAttribute(gemm_kernel(a, b),
+          COLA_CUDA(cudaFuncSetAttribute(gemm_kernel<GemmOne>(a, b),
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)gemm_smem(a, b)));
+          COLA_CUDA(cudaFuncSetAttribute(gemm_kernel<GemmTab>(a, b),
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)gemm_smem(a, b)));
         }
@@ -2654,6 +2777,123 @@ std::vector<int64_t> kron_tc_batch_upload(Ctx* c, const std::vector<TcBatchProbl
   // the host vectors' lifetime irrelevant by waiting here (tables are small)
   COLA_CUDA(cudaStreamSynchronize(c->s));
   return counts;
+}
+
+// Split GEMM form of a batched mode step: per problem the pre-split image of
+// its input (inside the shared buffer `image`, zeroed here), its factor's
+// GEMM image, and tile tables for the pre-split pass (64 x 64 tiles) and the
+// GEMM (128-row tiles x 128-output chunks, chunk fastest), under `tag`.
+std::vector<int64_t> kron_tc_gemm_batch_upload(Ctx* c, const std::vector<TcBatchProblem>& probs,
+                                               int tf, int tv, const char* tag,
+                                               const char* image) {
+  const size_t n = probs.size();
+  std::vector<TcGemmParams> hp(n);
+  std::vector<int64_t> counts(n), pcounts(n), first, pfirst;
+  std::vector<int> tile_prob, ptile_prob;
+  size_t img_elems = 0;
+  std::vector<size_t> img_off(n);
+  for (size_t i = 0; i < n; ++i) {
+    const TcBatchProblem& b = probs[i];
+    const cola_linop* f = b.factor;
+    const int n_in = (int)(b.transpose ? f->rows : f->cols);
+    const int n_out = (int)(b.transpose ? f->cols : f->rows);
+    const int kblocks = (n_in + kBlockK - 1) / kBlockK;
+    TcGemmParams& g = hp[i];
+    g = TcGemmParams{};
+    g.Bimg = gemm_factor_image(c, f, b.transpose, tf);
+    COLA_REQUIRE(g.Bimg, COLA_ERR_INVALID_ARG, "internal: batch factor image during capture");
+    g.Y = b.Y;
+    g.rest = b.rest;
+    g.size_out = b.size_out;
+    g.tiles_m = (b.rest + kTileM - 1) / kTileM;
+    g.nchunks = (n_out + kTileM - 1) / kTileM;
+    g.ntiles = b.R * g.tiles_m * g.nchunks;
+    g.xrows = b.R * b.rest;
+    g.rows_pad = b.R * g.tiles_m * kTileM;  // each RHS's rows start on a tile boundary
+    g.n_out = n_out;
+    g.kblocks = kblocks;
+    g.img_rows = (int)(g.nchunks * kTileM);
+    g.coeff = b.coeff;
+    g.beta = b.beta;
+    g.epi_x = b.epi_x;
+    g.epi_d = b.epi_d;
+    g.epi_dstride = b.epi_dstride;
+    g.epi_coeff = b.epi_coeff;
+    g.epi_dot = b.epi_dot;
+    g.X = b.X;
+    g.pro_z = b.pro_z;
+    g.pro_beta = b.pro_beta;
+    g.pro_out = b.pro_out;
+    g.n_in = n_in;
+    g.kpad = kblocks * kBlockK;
+    g.mode = b.pro_z ? 2 : (b.pro_out ? 1 : 0);
+    g.R = b.R;
+    img_off[i] = img_elems;
+    img_elems += (size_t)tv * kblocks * (size_t)g.rows_pad * kBlockK;
+    counts[i] = g.ntiles;
+    pcounts[i] = b.R * ((b.rest + 63) / 64) * (g.kpad / 64);
+  }
+  uint16_t* img = (uint16_t*)c->ws.get(image, std::max<size_t>(1, img_elems) * 2);
+  COLA_CUDA(cudaMemsetAsync(img, 0, img_elems * 2, c->s));
+  for (size_t i = 0; i < n; ++i) hp[i].ximg = img + img_off[i];
+  const int64_t tot = batch_tile_table(counts, first, tile_prob);
+  const int64_t ptot = batch_tile_table(pcounts, pfirst, ptile_prob);
+  // fixed-capacity device tables so replays of a captured graph stay valid
+  const size_t cap_p = std::max<size_t>(1, n);
+  void* dp = c->ws.get(tagged(tag, "gprobs"), sizeof(TcGemmParams) * cap_p);
+  void* dt = c->ws.get(tagged(tag, "gtile"), sizeof(int) * std::max<size_t>(1, tile_prob.size()));
+  void* df = c->ws.get(tagged(tag, "gfirst"), sizeof(int64_t) * cap_p);
+  void* dc = c->ws.get(tagged(tag, "gcount"), 2 * sizeof(int64_t));
+  void* pt = c->ws.get(tagged(tag, "ptile"), sizeof(int) * std::max<size_t>(1, ptile_prob.size()));
+  void* pf = c->ws.get(tagged(tag, "pfirst"), sizeof(int64_t) * cap_p);
+  if (n) {
+    COLA_CUDA(cudaMemcpyAsync(dp, hp.data(), sizeof(TcGemmParams) * n, cudaMemcpyHostToDevice,
+                              c->s));
+    COLA_CUDA(cudaMemcpyAsync(df, first.data(), sizeof(int64_t) * n, cudaMemcpyHostToDevice,
+                              c->s));
+    COLA_CUDA(cudaMemcpyAsync(pf, pfirst.data(), sizeof(int64_t) * n, cudaMemcpyHostToDevice,
+                              c->s));
+  }
+  if (!tile_prob.empty())
+    COLA_CUDA(cudaMemcpyAsync(dt, tile_prob.data(), sizeof(int) * tile_prob.size(),
+                              cudaMemcpyHostToDevice, c->s));
+  if (!ptile_prob.empty())
+    COLA_CUDA(cudaMemcpyAsync(pt, ptile_prob.data(), sizeof(int) * ptile_prob.size(),
+                              cudaMemcpyHostToDevice, c->s));
+  const int64_t cnt[2] = {tot, ptot};
+  COLA_CUDA(cudaMemcpyAsync(dc, cnt, 2 * sizeof(int64_t), cudaMemcpyHostToDevice, c->s));
+  COLA_CUDA(cudaStreamSynchronize(c->s));  // host vectors go out of scope
+  return counts;
+}
+
+void kron_tc_gemm_batch_launch(Ctx* c, const char* tag, int tf, int tv) {
+  const TcGemmParams* probs = (const TcGemmParams*)c->ws.bufs.at(tagged(tag, "gprobs")).p;
+  const int64_t* cnt = (const int64_t*)c->ws.bufs.at(tagged(tag, "gcount")).p;
+  const int* pt = (const int*)c->ws.bufs.at(tagged(tag, "ptile")).p;
+  const int64_t* pf = (const int64_t*)c->ws.bufs.at(tagged(tag, "pfirst")).p;
+  const dim3 pgrid((unsigned)(4 * c->num_sms));
+  if (tv == 1)
+    k_presplit_tab<1><<<pgrid, 256, 0, c->s>>>(probs, pt, pf, cnt + 1);
+  else if (tv == 2)
+    k_presplit_tab<2><<<pgrid, 256, 0, c->s>>>(probs, pt, pf, cnt + 1);
+  else
+    k_presplit_tab<3><<<pgrid, 256, 0, c->s>>>(probs, pt, pf, cnt + 1);
+  c->count_launch();
+  COLA_CUDA(cudaGetLastError());
+  TcGemmLaunch L{kGemmStages, tc_errflag(c), 0};
+  if (c->tc_stall_ns > 0 && !c->capturing) {
+    L.stall_ns = (uint64_t)c->tc_stall_ns;  // armed once by cola_test_stall_next_launch
+    c->tc_stall_ns = 0;
+  }
+  GemmTab src{probs, (const int*)c->ws.bufs.at(tagged(tag, "gtile")).p,
+              (const int64_t*)c->ws.bufs.at(tagged(tag, "gfirst")).p, cnt};
+  COLA_CUDA(cudaFuncSetAttribute(gemm_kernel<GemmTab>(tf, tv),
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)gemm_smem(tf, tv)));
+  launch_pdl(gemm_kernel<GemmTab>(tf, tv), dim3(c->num_sms), dim3(kGemmThreads),
+             gemm_smem(tf, tv), c->s, src, L);
+  c->count_launch();
+  COLA_CUDA(cudaGetLastError());
 }
 
 int kron_tc_batch_max_stages(int tf, int tv, int max_n_chunk) {

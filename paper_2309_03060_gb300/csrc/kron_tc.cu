@@ -1245,6 +1245,8 @@ struct GemmTab {
 // a tile's rows past rest are zero padding), the 16-byte runs of row j at
 // position c ^ (j mod 8) (the bulk-copied layout of a 128-byte swizzled
 // K-major operand).
+constexpr int kPresplitThreads = 256;  // block size of the pre-split passes
+
 template <int TV, bool SWZ>
 __device__ __forceinline__ void presplit_tile(float (*tile)[65], const float* X, int n_in,
                                               int64_t rest, int kpad, int64_t xrows,
@@ -1253,26 +1255,35 @@ __device__ __forceinline__ void presplit_tile(float (*tile)[65], const float* X,
                                               uint16_t* img, int64_t r, int64_t m0, int k0) {
   const int64_t off = r * (int64_t)n_in * rest;
   const float beta_r = mode != 0 ? (float)pro_beta[r] : 0.0f;
-  for (int e = threadIdx.x; e < 64 * 64; e += blockDim.x) {
-    const int kl = e >> 6, ml = e & 63;
+  // this thread's 16 entries: every load issued before the first store (a
+  // store to pro_out, which the compiler cannot prove distinct from X and z,
+  // would otherwise hold back the next load)
+  constexpr int kPer = 64 * 64 / kPresplitThreads;
+  const int ml = threadIdx.x & 63, kl0 = threadIdx.x >> 6;
+  const int64_t m = m0 + ml;
+  float v[kPer], zv[kPer];
+#pragma unroll
+  for (int j = 0; j < kPer; ++j) {
+    const int k = k0 + kl0 + j * (kPresplitThreads / 64);
+    const bool in = k < n_in && m < rest;
+    const int64_t idx = off + (int64_t)k * rest + m;
+    v[j] = in ? X[idx] : 0.0f;
+    zv[j] = (in && mode == 2) ? pro_z[idx] : 0.0f;
+  }
+#pragma unroll
+  for (int j = 0; j < kPer; ++j) {
+    const int kl = kl0 + j * (kPresplitThreads / 64);
     const int k = k0 + kl;
-    const int64_t m = m0 + ml;
-    float v = 0.0f;
-    if (k < n_in && m < rest) {
-      const int64_t idx = off + (int64_t)k * rest + m;
-      v = X[idx];
-      if (mode == 2) {
-        v = fmaf(beta_r, v, pro_z[idx]);
-        pro_out[idx] = v;
-      } else if (mode == 1) {
-        v = beta_r * v;
-        pro_out[idx] = v;
-      }
-    }
-    tile[kl][ml] = v;
+    float x = v[j];
+    if (mode == 2)
+      x = fmaf(beta_r, x, zv[j]);
+    else if (mode == 1)
+      x = beta_r * x;
+    if (mode != 0 && k < n_in && m < rest) pro_out[off + (int64_t)k * rest + m] = x;
+    tile[kl][ml] = x;
   }
   __syncthreads();
-  for (int e = threadIdx.x; e < 64 * 8; e += blockDim.x) {
+  for (int e = threadIdx.x; e < 64 * 8; e += kPresplitThreads) {
     const int ml = e >> 3, ch = e & 7;
     const int64_t m = m0 + ml;
     if (m >= rest) continue;
@@ -1304,7 +1315,7 @@ __device__ __forceinline__ void presplit_tile(float (*tile)[65], const float* X,
 
 // Pre-split pass of one mode step: block (m tile, k tile, right-hand side).
 template <int TV>
-__global__ void __launch_bounds__(256) k_presplit(const float* X, int n_in, int64_t rest,
+__global__ void __launch_bounds__(kPresplitThreads) k_presplit(const float* X, int n_in, int64_t rest,
                                                   int kpad, int64_t xrows, int mode,
                                                   const float* pro_z, const double* pro_beta,
                                                   float* pro_out, uint16_t* img) {
@@ -1318,7 +1329,7 @@ __global__ void __launch_bounds__(256) k_presplit(const float* X, int n_in, int6
 // tiles (tile -> problem; a problem's tiles run over right-hand side, m tile,
 // k tile with the k tile fastest).
 template <int TV>
-__global__ void __launch_bounds__(256) k_presplit_tab(const TcGemmParams* probs,
+__global__ void __launch_bounds__(kPresplitThreads) k_presplit_tab(const TcGemmParams* probs,
                                                       const int* tile_prob, const int64_t* first,
                                                       const int64_t* count_dev) {
   __shared__ float tile[64][65];
@@ -1552,41 +1563,69 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
         }
         continue;
       }
-      // 16 rows at a time: accumulator columns, then every load of the group,
-      // then its stores (the stores may alias the loaded arrays as far as the
-      // compiler knows, so loads interleaved with them would cost one global
-      // latency per row); the accumulator is released after the last group
-      // (the MMAs meanwhile fill the other buffer)
-#pragma unroll 1
-      for (int h = 0; h < 4; ++h) {
-        uint32_t v[16], w[16];
-        tmem_ld8(taddr + (uint32_t)(h * 16), v);
-        tmem_ld8(taddr + (uint32_t)(h * 16 + 8), v + 8);
-        if (kSmall) {
-          tmem_ld8(taddr + 128u + (uint32_t)(h * 16), w);
-          tmem_ld8(taddr + 128u + (uint32_t)(h * 16 + 8), w + 8);
-        }
-        float xd[16], dd[16], qd[16], yo[16];
+      if (ex && !ed && !eq && p.beta == 0.0f) {
+        // the CG step: x for all 64 rows first (one global latency; loads
+        // issued after a store to a buffer the compiler cannot prove distinct
+        // would wait for it), then 16 rows at a time from the accumulator
+        float xa[64];
 #pragma unroll
-        for (int e = 0; e < 16; ++e) {
-          const bool in = live && h * 16 + e < nrows;
-          xd[e] = (ex && in) ? __ldg(ex + (h * 16 + e) * ld) : 0.0f;
-          dd[e] = (ed && in) ? __ldg(ed + (h * 16 + e) * ld) : 0.0f;
-          qd[e] = (eq && in) ? __ldg(eq + (h * 16 + e) * ld) : 0.0f;
-          yo[e] = (p.beta != 0.0f && in) ? yp[(h * 16 + e) * ld] : 0.0f;
-        }
-        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        for (int c = 0; c < 64; ++c) xa[c] = (live && c < nrows) ? __ldg(ex + c * ld) : 0.0f;
 #pragma unroll
-        for (int e = 0; e < 16; ++e) {
-          float y = p.coeff * (__uint_as_float(v[e]) + (kSmall ? __uint_as_float(w[e]) : 0.0f));
-          const bool in = live && h * 16 + e < nrows;
-          if (ex) {
-            y = fmaf(ed ? p.epi_coeff * dd[e] : sc, xd[e], y);
-            if (eq) y = fmaf(-gam, qd[e], y);
-            if (in) part = fmaf(y, xd[e], part);
+        for (int h = 0; h < 4; ++h) {
+          uint32_t v[16], w[16];
+          tmem_ld8(taddr + (uint32_t)(h * 16), v);
+          tmem_ld8(taddr + (uint32_t)(h * 16 + 8), v + 8);
+          if (kSmall) {
+            tmem_ld8(taddr + 128u + (uint32_t)(h * 16), w);
+            tmem_ld8(taddr + 128u + (uint32_t)(h * 16 + 8), w + 8);
           }
-          y = fmaf(p.beta, yo[e], y);
-          if (in) yp[(h * 16 + e) * ld] = y;
+          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+          for (int e = 0; e < 16; ++e) {
+            const int c = h * 16 + e;
+            float y = p.coeff * (__uint_as_float(v[e]) + (kSmall ? __uint_as_float(w[e]) : 0.0f));
+            y = fmaf(sc, xa[c], y);
+            if (live && c < nrows) {
+              part = fmaf(y, xa[c], part);
+              yp[c * ld] = y;
+            }
+          }
+        }
+      } else {
+        // 16 rows at a time: accumulator columns, every load of the group, then
+        // its stores (loads interleaved with the stores would wait for them)
+#pragma unroll 1
+        for (int h = 0; h < 4; ++h) {
+          uint32_t v[16], w[16];
+          tmem_ld8(taddr + (uint32_t)(h * 16), v);
+          tmem_ld8(taddr + (uint32_t)(h * 16 + 8), v + 8);
+          if (kSmall) {
+            tmem_ld8(taddr + 128u + (uint32_t)(h * 16), w);
+            tmem_ld8(taddr + 128u + (uint32_t)(h * 16 + 8), w + 8);
+          }
+          float xd[16], dd[16], qd[16], yo[16];
+#pragma unroll
+          for (int e = 0; e < 16; ++e) {
+            const bool in = live && h * 16 + e < nrows;
+            xd[e] = (ex && in) ? __ldg(ex + (h * 16 + e) * ld) : 0.0f;
+            dd[e] = (ed && in) ? __ldg(ed + (h * 16 + e) * ld) : 0.0f;
+            qd[e] = (eq && in) ? __ldg(eq + (h * 16 + e) * ld) : 0.0f;
+            yo[e] = (p.beta != 0.0f && in) ? yp[(h * 16 + e) * ld] : 0.0f;
+          }
+          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+          for (int e = 0; e < 16; ++e) {
+            float y =
+                p.coeff * (__uint_as_float(v[e]) + (kSmall ? __uint_as_float(w[e]) : 0.0f));
+            const bool in = live && h * 16 + e < nrows;
+            if (ex) {
+              y = fmaf(ed ? p.epi_coeff * dd[e] : sc, xd[e], y);
+              if (eq) y = fmaf(-gam, qd[e], y);
+              if (in) part = fmaf(y, xd[e], part);
+            }
+            y = fmaf(p.beta, yo[e], y);
+            if (in) yp[(h * 16 + e) * ld] = y;
+          }
         }
       }
       tc_fence_before();
@@ -2348,7 +2387,7 @@ static bool gemm_launch(Ctx* c, const cola_linop* f, bool tr, const TcParams& p,
   if (!tmap_image(&g.tm_x, ximg, (int64_t)p.tv * xrows, kpad)) return false;
   const int mode = p.pro_z ? 2 : (p.pro_out ? 1 : 0);
   const dim3 pgrid((unsigned)((p.rest + 63) / 64), (unsigned)(kpad / 64), (unsigned)p.batch);
-  presplit_kernel(p.tv)<<<pgrid, 256, 0, c->s>>>(p.X, p.n_in, p.rest, kpad, xrows, mode, p.pro_z,
+  presplit_kernel(p.tv)<<<pgrid, kPresplitThreads, 0, c->s>>>(p.X, p.n_in, p.rest, kpad, xrows, mode, p.pro_z,
                                                   p.pro_beta, p.pro_out, ximg);
   c->count_launch();
   COLA_CUDA(cudaGetLastError());
@@ -2871,13 +2910,15 @@ void kron_tc_gemm_batch_launch(Ctx* c, const char* tag, int tf, int tv) {
   const int64_t* cnt = (const int64_t*)c->ws.bufs.at(tagged(tag, "gcount")).p;
   const int* pt = (const int*)c->ws.bufs.at(tagged(tag, "ptile")).p;
   const int64_t* pf = (const int64_t*)c->ws.bufs.at(tagged(tag, "pfirst")).p;
-  const dim3 pgrid((unsigned)(4 * c->num_sms));
+  // persistent: as many blocks as are resident at once (3 x 256 threads x 80
+  // registers per SM), so that no block starts its share of tiles late
+  const dim3 pgrid((unsigned)(3 * c->num_sms));
   if (tv == 1)
-    k_presplit_tab<1><<<pgrid, 256, 0, c->s>>>(probs, pt, pf, cnt + 1);
+    k_presplit_tab<1><<<pgrid, kPresplitThreads, 0, c->s>>>(probs, pt, pf, cnt + 1);
   else if (tv == 2)
-    k_presplit_tab<2><<<pgrid, 256, 0, c->s>>>(probs, pt, pf, cnt + 1);
+    k_presplit_tab<2><<<pgrid, kPresplitThreads, 0, c->s>>>(probs, pt, pf, cnt + 1);
   else
-    k_presplit_tab<3><<<pgrid, 256, 0, c->s>>>(probs, pt, pf, cnt + 1);
+    k_presplit_tab<3><<<pgrid, kPresplitThreads, 0, c->s>>>(probs, pt, pf, cnt + 1);
   c->count_launch();
   COLA_CUDA(cudaGetLastError());
   TcGemmLaunch L{kGemmStages, tc_errflag(c), 0};

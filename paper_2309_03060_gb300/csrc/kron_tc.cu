@@ -1408,8 +1408,12 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
         const int nc = (int)(lt % p.nchunks);
         const int64_t tm = lt / p.nchunks;
         const int64_t r = tm / p.tiles_m, m0 = (tm % p.tiles_m) * kTileM;
+        // the tile's fields in registers (a problem table in global memory
+        // would be re-read after every asm statement of the loop below)
         const int kblocks = p.kblocks, img_rows = p.img_rows;
         const uint16_t* bimg = p.Bimg;
+        const uint16_t* ximg = p.ximg;
+        const int64_t rows_pad = p.rows_pad, xrows = p.xrows, xrow0 = r * p.tiles_m * kTileM + m0;
         // rows past rest arrive as the next right-hand side's rows (or zeros
         // past the image); the epilogue masks them
         const int y0 = (int)(r * p.rest + m0);
@@ -1424,11 +1428,11 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
           for (int tv = 0; tv < TV; ++tv) {
             if constexpr (Src::kTma)
               tma_load_2d(st + tv * kGemmTermBytes, &p.tm_x, kb * kBlockK,
-                          (int)(tv * p.xrows) + y0, &full[s]);
+                          (int)(tv * xrows) + y0, &full[s]);
             else
               bulk_g2s(st + tv * kGemmTermBytes,
-                       p.ximg + (((size_t)tv * kblocks + kb) * (size_t)p.rows_pad +
-                                 (size_t)((r * p.tiles_m) * kTileM + m0)) * kBlockK,
+                       ximg + (((size_t)tv * kblocks + kb) * (size_t)rows_pad + (size_t)xrow0) *
+                                  kBlockK,
                        kGemmTermBytes, &full[s]);
           }
 #pragma unroll
@@ -1539,8 +1543,12 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
       const float* eq = p.epi_q2 ? p.epi_q2 + r * p.size_out + mbase * ld + i : nullptr;
       const float gam = p.epi_q2 ? (float)p.epi_gamma[r] : 0.0f;
       const float sc = p.epi_coeff * d0;
+      // the tile's scalars in registers: with a problem table in global memory
+      // the compiler would reload them after every store of the loops below
+      const float coeff = p.coeff, beta = p.beta, ecoef = p.epi_coeff;
+      double* const edot = p.epi_dot;
       float part = 0.0f;  // this thread's <= 64 products of x . y
-      if (!ex && p.beta == 0.0f) {
+      if (!ex && beta == 0.0f) {
         // plain step: the whole accumulator into registers, released, stored
         float a[64];
 #pragma unroll
@@ -1552,7 +1560,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
 #pragma unroll
           for (int e = 0; e < 8; ++e)
             a[q * 8 + e] =
-                p.coeff * (__uint_as_float(v[e]) + (kSmall ? __uint_as_float(w[e]) : 0.0f));
+                coeff * (__uint_as_float(v[e]) + (kSmall ? __uint_as_float(w[e]) : 0.0f));
         }
         tc_fence_before();
         mbar_arrive(&aempty[b]);
@@ -1563,7 +1571,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
         }
         continue;
       }
-      if (ex && !ed && !eq && p.beta == 0.0f) {
+      if (ex && !ed && !eq && beta == 0.0f) {
         // the CG step: x for all 64 rows first (one global latency; loads
         // issued after a store to a buffer the compiler cannot prove distinct
         // would wait for it), then 16 rows at a time from the accumulator
@@ -1583,7 +1591,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
 #pragma unroll
           for (int e = 0; e < 16; ++e) {
             const int c = h * 16 + e;
-            float y = p.coeff * (__uint_as_float(v[e]) + (kSmall ? __uint_as_float(w[e]) : 0.0f));
+            float y = coeff * (__uint_as_float(v[e]) + (kSmall ? __uint_as_float(w[e]) : 0.0f));
             y = fmaf(sc, xa[c], y);
             if (live && c < nrows) {
               part = fmaf(y, xa[c], part);
@@ -1610,31 +1618,31 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
             xd[e] = (ex && in) ? __ldg(ex + (h * 16 + e) * ld) : 0.0f;
             dd[e] = (ed && in) ? __ldg(ed + (h * 16 + e) * ld) : 0.0f;
             qd[e] = (eq && in) ? __ldg(eq + (h * 16 + e) * ld) : 0.0f;
-            yo[e] = (p.beta != 0.0f && in) ? yp[(h * 16 + e) * ld] : 0.0f;
+            yo[e] = (beta != 0.0f && in) ? yp[(h * 16 + e) * ld] : 0.0f;
           }
           asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
           for (int e = 0; e < 16; ++e) {
             float y =
-                p.coeff * (__uint_as_float(v[e]) + (kSmall ? __uint_as_float(w[e]) : 0.0f));
+                coeff * (__uint_as_float(v[e]) + (kSmall ? __uint_as_float(w[e]) : 0.0f));
             const bool in = live && h * 16 + e < nrows;
             if (ex) {
-              y = fmaf(ed ? p.epi_coeff * dd[e] : sc, xd[e], y);
+              y = fmaf(ed ? ecoef * dd[e] : sc, xd[e], y);
               if (eq) y = fmaf(-gam, qd[e], y);
               if (in) part = fmaf(y, xd[e], part);
             }
-            y = fmaf(p.beta, yo[e], y);
+            y = fmaf(beta, yo[e], y);
             if (in) yp[(h * 16 + e) * ld] = y;
           }
         }
       }
       tc_fence_before();
       mbar_arrive(&aempty[b]);
-      if (p.epi_dot) {
+      if (edot) {
         double dsum = (double)part;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) dsum += __shfl_xor_sync(0xffffffffu, dsum, o);
-        if (lane == 0) p.epi_dot[lt * kDotSlots + ew] = dsum;
+        if (lane == 0) edot[lt * kDotSlots + ew] = dsum;
       }
     }
   }

@@ -525,9 +525,9 @@ cola_status batched_cg_fast(Ctx* c, int32_t nsys, const cola_linop* const* ops,
         s2.push_back(q2);
       }
       if (use_gemm) {
-        // step 1's and step 2's pre-split images never live at the same time
-        kron_tc_gemm_batch_upload(c, s1, tf, tv, kGm1[q], "bcg.gimg1");
-        kron_tc_gemm_batch_upload(c, s2, tf, tv, kGm2[q], "bcg.gimg2");
+        // step 1's epilogue writes step 2's image (two-factor systems)
+        kron_tc_gemm_batch_upload_pair(c, s1, s2, tf, tv, kGm1[q], kGm2[q], "bcg.gimg1",
+                                       "bcg.gimg2");
       } else {
         kron_tc_batch_upload(c, s1, tf, tv, kTc1[q], tile_cap);
         kron_tc_batch_upload(c, s2, tf, tv, kTc2[q], tile_cap);
@@ -654,11 +654,11 @@ cola_status batched_cg_fast(Ctx* c, int32_t nsys, const cola_linop* const* ops,
         tile_cap = kChunkGemm;
         tc_tables(live);
         kron_tc_gemm_batch_launch(c, kGm1[0], tf, tv);  // warm-up
-        kron_tc_gemm_batch_launch(c, kGm2[0], tf, tv);
+        kron_tc_gemm_batch_launch(c, kGm2[0], tf, tv, false);
         COLA_CUDA(cudaEventRecord(e0, c->s));
         for (int rep = 0; rep < 2; ++rep) {
           kron_tc_gemm_batch_launch(c, kGm1[0], tf, tv);
-          kron_tc_gemm_batch_launch(c, kGm2[0], tf, tv);
+          kron_tc_gemm_batch_launch(c, kGm2[0], tf, tv, false);
         }
         COLA_CUDA(cudaEventRecord(e1, c->s));
         COLA_CUDA(cudaEventSynchronize(e1));
@@ -695,7 +695,7 @@ cola_status batched_cg_fast(Ctx* c, int32_t nsys, const cola_linop* const* ops,
   auto iteration = [&] {
     if (use_gemm) {
       kron_tc_gemm_batch_launch(c, kGm1[cur], tf, tv);
-      kron_tc_gemm_batch_launch(c, kGm2[cur], tf, tv);
+      kron_tc_gemm_batch_launch(c, kGm2[cur], tf, tv, false);
     } else {
       kron_tc_batch_launch(c, kTc1[cur], tf, tv, max_chunk, tile_stages);
       kron_tc_batch_launch(c, kTc2[cur], tf, tv, max_chunk, tile_stages);

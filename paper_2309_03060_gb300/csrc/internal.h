@@ -360,9 +360,17 @@ int kron_tc_batch_max_stages(int tf, int tv, int max_n_chunk);
 std::vector<int64_t> kron_tc_gemm_batch_upload(Ctx* c, const std::vector<TcBatchProblem>& probs,
                                                int tf, int tv, const char* tag,
                                                const char* image);
-// Launches the pre-split pass and the persistent split GEMM over the tables
+// Both steps of two-factor problems (s2[i] is the second mode step of
+// s1[i]'s operator): step 1's epilogue writes step 2's pre-split image, so
+// step 2 runs without a pre-split pass.
+void kron_tc_gemm_batch_upload_pair(Ctx* c, const std::vector<TcBatchProblem>& s1,
+                                    const std::vector<TcBatchProblem>& s2, int tf, int tv,
+                                    const char* tag1, const char* tag2, const char* image1,
+                                    const char* image2);
+// Launches the pre-split pass (unless `presplit` is false: the image was
+// written by the previous step) and the persistent split GEMM over the tables
 // uploaded under `tag`.
-void kron_tc_gemm_batch_launch(Ctx* c, const char* tag, int tf, int tv);
+void kron_tc_gemm_batch_launch(Ctx* c, const char* tag, int tf, int tv, bool presplit = true);
 // Chunk width (and count) of n_out output columns under a chunk cap.
 int kron_tc_chunk_width(int n_out, int chunk_cap, int* nchunks);
 

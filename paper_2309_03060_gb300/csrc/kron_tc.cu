@@ -1201,6 +1201,13 @@ struct TcGemmParams {
   float* pro_out;
   int n_in, kpad, mode;  // mode as k_presplit's
   int64_t R;
+  // image output (a two-factor product's first step): instead of Y the
+  // epilogue writes the second step's pre-split image, whose contraction
+  // index is this step's row index and whose rows are this step's outputs
+  uint16_t* oimg;
+  int64_t o_rstride;  // image rows per right-hand side
+  int64_t o_rows;     // rows per term (TMA layout) or per (term, k block) (swizzled)
+  int o_kpad, o_swz;  // the second step's padded k; 1: pre-swizzled layout
 };
 
 // Launch-wide settings of the split GEMM.
@@ -1547,6 +1554,9 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
       // the compiler would reload them after every store of the loops below
       const float coeff = p.coeff, beta = p.beta, ecoef = p.epi_coeff;
       double* const edot = p.epi_dot;
+      uint16_t* const oimg = p.oimg;
+      const int64_t o_rstride = p.o_rstride, o_rows = p.o_rows;
+      const int o_kpad = p.o_kpad, o_swz = p.o_swz;
       float part = 0.0f;  // this thread's <= 64 products of x . y
       if (!ex && beta == 0.0f) {
         // plain step: the whole accumulator into registers, released, stored
@@ -1564,7 +1574,33 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
         }
         tc_fence_before();
         mbar_arrive(&aempty[b]);
-        if (live) {
+        if (live && oimg) {
+          // row i (this step's output) of the next step's image, its 64 k
+          // (this step's rows mbase ..) in TV split terms, zero past rest
+          const int64_t row = r * o_rstride + i;
+          const int kb = (int)(mbase / kBlockK);
+#pragma unroll
+          for (int ch = 0; ch < 8; ++ch) {
+            uint32_t w[3][4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+              const int c = ch * 8 + 2 * j;
+              uint32_t o[3];
+              split2(c < nrows ? a[c] : 0.0f, c + 1 < nrows ? a[c + 1] : 0.0f, TV, o);
+              w[0][j] = o[0];
+              w[1][j] = o[1];
+              w[2][j] = o[2];
+            }
+#pragma unroll
+            for (int tv = 0; tv < TV; ++tv) {
+              const size_t pos =
+                  o_swz ? (((size_t)tv * (o_kpad / kBlockK) + kb) * (size_t)o_rows + row) * kBlockK +
+                              (size_t)((ch ^ (int)(row & 7)) * 8)
+                        : ((size_t)tv * o_rows + row) * o_kpad + mbase + ch * 8;
+              *reinterpret_cast<uint4*>(oimg + pos) = make_uint4(w[tv][0], w[tv][1], w[tv][2], w[tv][3]);
+            }
+          }
+        } else if (live) {
 #pragma unroll
           for (int c = 0; c < 64; ++c)
             if (c < nrows) yp[c * ld] = a[c];
@@ -2379,26 +2415,51 @@ static const uint16_t* gemm_factor_image(Ctx* c, const cola_linop* f, bool tr, i
   return (const uint16_t*)f->derived.at(key).p;
 }
 
-static bool gemm_launch(Ctx* c, const cola_linop* f, bool tr, const TcParams& p, int depth,
-                        int k) {
+// True when a mode step with these sizes takes the split GEMM (the factor's
+// GEMM image is made here when missing, outside graph capture).
+static bool gemm_ok(Ctx* c, const TcParams& p, const cola_linop* f, bool tr) {
   if (p.n_in <= kTileM && p.n_out <= kTileM) return false;  // the factor-stationary kernel's
   if (p.out_trans || p.tf < 1 || p.tf > 3 || p.tv < 1 || p.tv > 3) return false;
+  const int64_t xrows = p.batch * p.rest;
+  if ((int64_t)p.tv * xrows > INT32_MAX || p.rest > INT32_MAX) return false;
+  return gemm_factor_image(c, f, tr, p.tf) != nullptr;
+}
+
+// The X image of a split GEMM step: TMA layout [tv][R rest][kpad].
+static uint16_t* gemm_ximage(Ctx* c, const TcParams& p, int depth, int k) {
+  const int kpad = (p.n_in + kBlockK - 1) / kBlockK * kBlockK;
+  return (uint16_t*)c->ws.get(depth_name("kgemm", depth, k & 1),
+                              (size_t)p.tv * p.batch * p.rest * kpad * 2);
+}
+
+// One split GEMM mode step.  `next` (a two-factor product's first step): the
+// epilogue writes the second step's X image instead of Y.  `have_img`: this
+// step's X image was written by the previous step's epilogue (no pre-split).
+static bool gemm_launch(Ctx* c, const cola_linop* f, bool tr, const TcParams& p, int depth,
+                        int k, const TcParams* next = nullptr, bool have_img = false) {
+  if (!gemm_ok(c, p, f, tr)) return false;
   const int kblocks = (p.n_in + kBlockK - 1) / kBlockK, kpad = kblocks * kBlockK;
   const int nch = (p.n_out + kTileM - 1) / kTileM, img_rows = nch * kTileM;
   const int64_t xrows = p.batch * p.rest;
-  if ((int64_t)p.tv * xrows > INT32_MAX || p.rest > INT32_MAX) return false;
   const uint16_t* fimg = gemm_factor_image(c, f, tr, p.tf);
-  if (!fimg) return false;
-  uint16_t* ximg = (uint16_t*)c->ws.get(depth_name("kgemm", depth, k & 1),
-                                        (size_t)p.tv * xrows * kpad * 2);
+  uint16_t* ximg = gemm_ximage(c, p, depth, k);
   TcGemmParams g{};
   if (!tmap_image(&g.tm_x, ximg, (int64_t)p.tv * xrows, kpad)) return false;
-  const int mode = p.pro_z ? 2 : (p.pro_out ? 1 : 0);
-  const dim3 pgrid((unsigned)((p.rest + 63) / 64), (unsigned)(kpad / 64), (unsigned)p.batch);
-  presplit_kernel(p.tv)<<<pgrid, kPresplitThreads, 0, c->s>>>(p.X, p.n_in, p.rest, kpad, xrows, mode, p.pro_z,
-                                                  p.pro_beta, p.pro_out, ximg);
-  c->count_launch();
-  COLA_CUDA(cudaGetLastError());
+  if (!have_img) {
+    const int mode = p.pro_z ? 2 : (p.pro_out ? 1 : 0);
+    const dim3 pgrid((unsigned)((p.rest + 63) / 64), (unsigned)(kpad / 64), (unsigned)p.batch);
+    presplit_kernel(p.tv)<<<pgrid, kPresplitThreads, 0, c->s>>>(
+        p.X, p.n_in, p.rest, kpad, xrows, mode, p.pro_z, p.pro_beta, p.pro_out, ximg);
+    c->count_launch();
+    COLA_CUDA(cudaGetLastError());
+  }
+  if (next) {
+    g.oimg = gemm_ximage(c, *next, depth, k + 1);
+    g.o_rstride = next->rest;  // = this step's n_out
+    g.o_rows = next->batch * next->rest;
+    g.o_kpad = (next->n_in + kBlockK - 1) / kBlockK * kBlockK;
+    g.o_swz = 0;
+  }
   g.Bimg = fimg;
   g.Y = p.Y;
   g.rest = p.rest;
@@ -2487,6 +2548,29 @@ static int64_t kron_tc_run(Ctx* c, const cola_linop* op, const float* X, float* 
   const float* cur = X;
   int64_t last_tiles = 0;
   const int nsteps = fu.nsteps < 0 ? d : fu.nsteps;
+  // A two-factor product whose both steps take the split GEMM: the first
+  // step's epilogue writes the second step's X image (no FP32 intermediate,
+  // no second pre-split pass)
+  bool chain = false;
+  TcParams p1{};
+  if (d == 2 && nsteps == 2 && !fu.out_trans) {
+    const cola_linop* f0 = op->kids[0];
+    const cola_linop* f1 = op->kids[1];
+    TcParams p0{};
+    p0.n_in = (int)(tr ? f0->rows : f0->cols);
+    p0.n_out = (int)(tr ? f0->cols : f0->rows);
+    p0.rest = cur_size / p0.n_in;
+    p0.batch = R;
+    p0.tf = tf;
+    p0.tv = tv;
+    p1.n_in = (int)(tr ? f1->rows : f1->cols);
+    p1.n_out = (int)(tr ? f1->cols : f1->rows);
+    p1.rest = p0.rest * p0.n_out / p1.n_in;
+    p1.batch = R;
+    p1.tf = tf;
+    p1.tv = tv;
+    chain = gemm_ok(c, p0, f0, tr) && gemm_ok(c, p1, f1, tr);
+  }
   for (int k = 0; k < nsteps; ++k) {
     const cola_linop* f = op->kids[k];
     const int n_in = (int)(tr ? f->rows : f->cols), n_out = (int)(tr ? f->cols : f->rows);
@@ -2569,7 +2653,9 @@ static int64_t kron_tc_run(Ctx* c, const cola_linop* op, const float* X, float* 
       launch_pdl(fs_kernel(tf, tv), dim3(grid), dim3(kThreadsFs), fs_smem(rp, tv), c->s, rp);
       c->count_launch();
       COLA_CUDA(cudaGetLastError());
-    } else if (!gemm_launch(c, f, tr, p, depth, k)) {
+    } else if (!gemm_launch(c, f, tr, p, depth, k, chain && k == 0 ? &p1 : nullptr,
+                            chain && k == 1)) {
+      COLA_REQUIRE(!chain, COLA_ERR_CUDA, "internal: chained split GEMM step not launched");
       COLA_REQUIRE(!p.out_trans, COLA_ERR_UNSUPPORTED,
                    "internal: slab-major output needs the factor-stationary kernel");
       k_kron_tc<OneProb><<<grid, kThreadsTc, q.smem, c->s>>>(OneProb{p}, p);
@@ -2826,17 +2912,23 @@ std::vector<int64_t> kron_tc_batch_upload(Ctx* c, const std::vector<TcBatchProbl
   return counts;
 }
 
+// Host tables of a batched split GEMM step.
+struct GemmBatchTables {
+  std::vector<TcGemmParams> hp;
+  std::vector<int64_t> counts, pcounts;
+};
+
 // Split GEMM form of a batched mode step: per problem the pre-split image of
 // its input (inside the shared buffer `image`, zeroed here), its factor's
-// GEMM image, and tile tables for the pre-split pass (64 x 64 tiles) and the
-// GEMM (128-row tiles x 128-output chunks, chunk fastest), under `tag`.
-std::vector<int64_t> kron_tc_gemm_batch_upload(Ctx* c, const std::vector<TcBatchProblem>& probs,
-                                               int tf, int tv, const char* tag,
-                                               const char* image) {
+// GEMM image, and the tile counts of the pre-split pass (64 x 64 tiles) and
+// the GEMM (128-row tiles x 128-output chunks, chunk fastest).
+static GemmBatchTables gemm_batch_build(Ctx* c, const std::vector<TcBatchProblem>& probs, int tf,
+                                        int tv, const char* image) {
   const size_t n = probs.size();
-  std::vector<TcGemmParams> hp(n);
-  std::vector<int64_t> counts(n), pcounts(n), first, pfirst;
-  std::vector<int> tile_prob, ptile_prob;
+  GemmBatchTables T;
+  T.hp.resize(n);
+  T.counts.resize(n);
+  T.pcounts.resize(n);
   size_t img_elems = 0;
   std::vector<size_t> img_off(n);
   for (size_t i = 0; i < n; ++i) {
@@ -2845,7 +2937,7 @@ std::vector<int64_t> kron_tc_gemm_batch_upload(Ctx* c, const std::vector<TcBatch
     const int n_in = (int)(b.transpose ? f->rows : f->cols);
     const int n_out = (int)(b.transpose ? f->cols : f->rows);
     const int kblocks = (n_in + kBlockK - 1) / kBlockK;
-    TcGemmParams& g = hp[i];
+    TcGemmParams& g = T.hp[i];
     g = TcGemmParams{};
     g.Bimg = gemm_factor_image(c, f, b.transpose, tf);
     COLA_REQUIRE(g.Bimg, COLA_ERR_INVALID_ARG, "internal: batch factor image during capture");
@@ -2877,15 +2969,23 @@ std::vector<int64_t> kron_tc_gemm_batch_upload(Ctx* c, const std::vector<TcBatch
     g.R = b.R;
     img_off[i] = img_elems;
     img_elems += (size_t)tv * kblocks * (size_t)g.rows_pad * kBlockK;
-    counts[i] = g.ntiles;
-    pcounts[i] = b.R * ((b.rest + 63) / 64) * (g.kpad / 64);
+    T.counts[i] = g.ntiles;
+    T.pcounts[i] = b.R * ((b.rest + 63) / 64) * (g.kpad / 64);
   }
   uint16_t* img = (uint16_t*)c->ws.get(image, std::max<size_t>(1, img_elems) * 2);
   COLA_CUDA(cudaMemsetAsync(img, 0, img_elems * 2, c->s));
-  for (size_t i = 0; i < n; ++i) hp[i].ximg = img + img_off[i];
-  const int64_t tot = batch_tile_table(counts, first, tile_prob);
-  const int64_t ptot = batch_tile_table(pcounts, pfirst, ptile_prob);
-  // fixed-capacity device tables so replays of a captured graph stay valid
+  for (size_t i = 0; i < n; ++i) T.hp[i].ximg = img + img_off[i];
+  return T;
+}
+
+// Uploads the tables under `tag` (fixed-capacity device buffers, so replays of
+// a captured graph stay valid).
+static void gemm_batch_put(Ctx* c, const GemmBatchTables& T, const char* tag) {
+  const size_t n = T.hp.size();
+  std::vector<int64_t> first, pfirst;
+  std::vector<int> tile_prob, ptile_prob;
+  const int64_t tot = batch_tile_table(T.counts, first, tile_prob);
+  const int64_t ptot = batch_tile_table(T.pcounts, pfirst, ptile_prob);
   const size_t cap_p = std::max<size_t>(1, n);
   void* dp = c->ws.get(tagged(tag, "gprobs"), sizeof(TcGemmParams) * cap_p);
   void* dt = c->ws.get(tagged(tag, "gtile"), sizeof(int) * std::max<size_t>(1, tile_prob.size()));
@@ -2894,7 +2994,7 @@ std::vector<int64_t> kron_tc_gemm_batch_upload(Ctx* c, const std::vector<TcBatch
   void* pt = c->ws.get(tagged(tag, "ptile"), sizeof(int) * std::max<size_t>(1, ptile_prob.size()));
   void* pf = c->ws.get(tagged(tag, "pfirst"), sizeof(int64_t) * cap_p);
   if (n) {
-    COLA_CUDA(cudaMemcpyAsync(dp, hp.data(), sizeof(TcGemmParams) * n, cudaMemcpyHostToDevice,
+    COLA_CUDA(cudaMemcpyAsync(dp, T.hp.data(), sizeof(TcGemmParams) * n, cudaMemcpyHostToDevice,
                               c->s));
     COLA_CUDA(cudaMemcpyAsync(df, first.data(), sizeof(int64_t) * n, cudaMemcpyHostToDevice,
                               c->s));
@@ -2910,10 +3010,40 @@ std::vector<int64_t> kron_tc_gemm_batch_upload(Ctx* c, const std::vector<TcBatch
   const int64_t cnt[2] = {tot, ptot};
   COLA_CUDA(cudaMemcpyAsync(dc, cnt, 2 * sizeof(int64_t), cudaMemcpyHostToDevice, c->s));
   COLA_CUDA(cudaStreamSynchronize(c->s));  // host vectors go out of scope
-  return counts;
 }
 
-void kron_tc_gemm_batch_launch(Ctx* c, const char* tag, int tf, int tv) {
+std::vector<int64_t> kron_tc_gemm_batch_upload(Ctx* c, const std::vector<TcBatchProblem>& probs,
+                                               int tf, int tv, const char* tag,
+                                               const char* image) {
+  const GemmBatchTables T = gemm_batch_build(c, probs, tf, tv, image);
+  gemm_batch_put(c, T, tag);
+  return T.counts;
+}
+
+void kron_tc_gemm_batch_upload_pair(Ctx* c, const std::vector<TcBatchProblem>& s1,
+                                    const std::vector<TcBatchProblem>& s2, int tf, int tv,
+                                    const char* tag1, const char* tag2, const char* image1,
+                                    const char* image2) {
+  COLA_REQUIRE(s1.size() == s2.size(), COLA_ERR_INVALID_ARG, "internal: unpaired batch steps");
+  GemmBatchTables T1 = gemm_batch_build(c, s1, tf, tv, image1);
+  GemmBatchTables T2 = gemm_batch_build(c, s2, tf, tv, image2);
+  for (size_t i = 0; i < s1.size(); ++i) {
+    TcGemmParams& a = T1.hp[i];
+    const TcGemmParams& b = T2.hp[i];
+    COLA_REQUIRE(b.n_in == a.rest && b.rest == a.n_out && b.R == a.R, COLA_ERR_INVALID_ARG,
+                 "internal: batch steps do not chain");
+    a.oimg = const_cast<uint16_t*>(b.ximg);
+    a.o_rstride = b.tiles_m * kTileM;
+    a.o_rows = b.rows_pad;
+    a.o_kpad = b.kpad;
+    a.o_swz = 1;
+    T2.pcounts[i] = 0;  // step 2's image comes from step 1's epilogue
+  }
+  gemm_batch_put(c, T1, tag1);
+  gemm_batch_put(c, T2, tag2);
+}
+
+void kron_tc_gemm_batch_launch(Ctx* c, const char* tag, int tf, int tv, bool presplit) {
   const TcGemmParams* probs = (const TcGemmParams*)c->ws.bufs.at(tagged(tag, "gprobs")).p;
   const int64_t* cnt = (const int64_t*)c->ws.bufs.at(tagged(tag, "gcount")).p;
   const int* pt = (const int*)c->ws.bufs.at(tagged(tag, "ptile")).p;
@@ -2921,14 +3051,16 @@ void kron_tc_gemm_batch_launch(Ctx* c, const char* tag, int tf, int tv) {
   // persistent: as many blocks as are resident at once (3 x 256 threads x 80
   // registers per SM), so that no block starts its share of tiles late
   const dim3 pgrid((unsigned)(3 * c->num_sms));
-  if (tv == 1)
-    k_presplit_tab<1><<<pgrid, kPresplitThreads, 0, c->s>>>(probs, pt, pf, cnt + 1);
-  else if (tv == 2)
-    k_presplit_tab<2><<<pgrid, kPresplitThreads, 0, c->s>>>(probs, pt, pf, cnt + 1);
-  else
-    k_presplit_tab<3><<<pgrid, kPresplitThreads, 0, c->s>>>(probs, pt, pf, cnt + 1);
-  c->count_launch();
-  COLA_CUDA(cudaGetLastError());
+  if (presplit) {
+    if (tv == 1)
+      k_presplit_tab<1><<<pgrid, kPresplitThreads, 0, c->s>>>(probs, pt, pf, cnt + 1);
+    else if (tv == 2)
+      k_presplit_tab<2><<<pgrid, kPresplitThreads, 0, c->s>>>(probs, pt, pf, cnt + 1);
+    else
+      k_presplit_tab<3><<<pgrid, kPresplitThreads, 0, c->s>>>(probs, pt, pf, cnt + 1);
+    c->count_launch();
+    COLA_CUDA(cudaGetLastError());
+  }
   TcGemmLaunch L{kGemmStages, tc_errflag(c), 0};
   if (c->tc_stall_ns > 0 && !c->capturing) {
     L.stall_ns = (uint64_t)c->tc_stall_ns;  // armed once by cola_test_stall_next_launch

@@ -569,17 +569,19 @@ def test_cg_and_lanczos_mixed_slab_path(cola, ctx):
 
 
 @pytest.mark.parametrize("terms", [1, 2, 3])
-def test_matvec_mixed_split_gemm_parity(cola, ctx, terms):
+@pytest.mark.parametrize("shapes", [[(257, 131), (24, 16), (150, 200)], [(257, 131), (150, 200)]],
+                         ids=["three_factor", "two_factor_chained"])
+def test_matvec_mixed_split_gemm_parity(cola, ctx, terms, shapes):
     """Factors with a side above 128 take the split GEMM mode step (the mode
     step's input pre-split into K-major BF16 images, both operands moved by
     copy engines, double-buffered accumulators): a three-factor product that
     mixes it with the factor-stationary kernel (257 x 131, 24 x 16 and
-    150 x 200 factors: ragged row tiles, k blocks and 128-output chunks), 3
-    right-hand sides, per entry within three mode steps' split error of
-    sum |K||x|."""
+    150 x 200 factors: ragged row tiles, k blocks and 128-output chunks), and
+    a two-factor product whose first step's epilogue writes the second step's
+    split image; 3 right-hand sides, per entry within the mode steps' split
+    error of sum |K||x|."""
     r = _rs(700)
-    F = [r.standard_normal((257, 131)) / np.sqrt(131), r.standard_normal((24, 16)) / 4.0,
-         r.standard_normal((150, 200)) / np.sqrt(200)]
+    F = [r.standard_normal(sh) / np.sqrt(sh[1]) for sh in shapes]
     spec = ("kron", [("dense", f) for f in F])
     ref = oracle_tree(spec)
     op = gpu_tree(cola, ctx, spec, torch.float64, DEV)

@@ -324,6 +324,21 @@ int64_t kron_tc_lanczos_mvm(Ctx* c, const cola_linop* op, const float* w_in,
                             const double* scale, float* q_out, const float* q_prev,
                             const double* gamma, float* w_out, double* tile_dot, int64_t R,
                             int depth);
+// Lanczos with unnormalised basis vectors v_j (q_j = s_j v_j, s_j = 1 / beta_j)
+// for Sum(c_k K_1 (x) K_2 (x) K_3, c_d s I) with 128 x 128 K_2, K_3 (kron_tc.cu):
+//   step 1: v_out = w + coef[r] v_prev (coef = -alpha_{j-1} s_{j-1}), written,
+//           its K_1 mode product slab-major, per (tile, warp) partials of
+//           ||v_out||^2 in nrm (8 per tile; returns the tiles per right-hand
+//           side); w == nullptr: v_prev itself, nothing written
+//   slab:   w_out = s (c_k K v + c_d s v) - gamma v_prev and the per-(slab,
+//           warp) partials of (s v) . w_out (returns the slabs per RHS)
+bool kron_tc_lanczos_unnormalised(const cola_linop* op);
+int64_t kron_tc_lanczos_step1(Ctx* c, const cola_linop* op, const float* v_prev, const float* w,
+                              const double* coef, float* v_out, double* nrm, int64_t R,
+                              int depth);
+int64_t kron_tc_lanczos_slab(Ctx* c, const cola_linop* op, const float* v, const float* v_prev,
+                             const double* gamma, const double* scale, float* w_out,
+                             double* tile_dot, int64_t R, int depth);
 
 // One tensor-core mode-step problem of a batch (host mirror of the kernel's
 // per-problem parameters) and the launch over a device problem table.

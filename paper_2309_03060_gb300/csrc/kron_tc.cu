@@ -71,6 +71,8 @@ struct TcParams {
   const float* epi_q2;
   const double* epi_gamma;
   int out_trans;  // 1: store Y[r][i][m] (output index major) instead of Y[r][m][i]
+  double* pro_nrm;  // with pro_z: per (tile, warp) partials of the formed input's ||p||^2
+                    // (factor-stationary kernel)
   // optional epilogue (last mode step, output in the input's layout):
   // Y += epi_coeff * d * epi_x (d = epi_d[0] when epi_dstride == 0), and the
   // per-(tile, epilogue warp) partial sums of epi_x . Y go to epi_dot[4 tile + warp]
@@ -667,6 +669,7 @@ struct TcFsParams {
   int pro_scale;          // 1: the input is pro_beta[r] * X, written to pro_out
   const float* e_q2;      // e_mode 4: previous Lanczos vector (output layout)
   const double* e_gamma;  // e_mode 4: its coefficient per right-hand side
+  double* pro_nrm;        // two-source input: per (tile, converter warp) partials of ||p||^2
 };
 
 __device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t* r) {
@@ -712,12 +715,13 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, i
 // to chunk position c ^ (row & 7) of each term's B stage.  NSRC == 2 first
 // forms p = z + beta_r p and writes it to Pout (row m of p, k stride `rest`).
 // FULL: the row and the whole block are in range, nothing is masked.
+// NSRC == 2 also adds the squares of the formed values to nrm.
 // NSRC == 0: the staged values times beta_r, written to Pout (the Lanczos
 // normalisation q = w / beta).
 template <int TV, int NSRC, bool FULL>
 __device__ __forceinline__ void fs_convert(const float* st, const float* stz, unsigned char* brow,
                                            int row, int khalf, int kbase, int n_in, bool row_ok,
-                                           float beta_r, float* Pout, int64_t rest) {
+                                           float beta_r, float* Pout, int64_t rest, float& nrm) {
   const uint32_t swz = (uint32_t)(row & 7);
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
@@ -730,6 +734,7 @@ __device__ __forceinline__ void fs_convert(const float* st, const float* stz, un
       if (NSRC > 1 && in) {
         x = fmaf(beta_r, x, stz[kl * kTileM + row]);
         Pout[(int64_t)(kbase + kl) * rest] = x;
+        nrm = fmaf(x, x, nrm);
       } else if (NSRC == 0 && in) {
         x = beta_r * x;
         Pout[(int64_t)(kbase + kl) * rest] = x;
@@ -911,6 +916,7 @@ __global__ void __launch_bounds__(kThreadsFs, 1) k_kron_tc_fs(const __grid_const
       const bool pro = p.nsrc > 1 || p.pro_scale;
       const float beta_r = pro ? (float)p.pro_beta[r] : 0.0f;
       float* Pout = pro ? p.pro_out + r * p.size_in + m : nullptr;
+      float nrm = 0.0f;  // squares of the formed values (two-source mode)
       for (int kb = 0; kb < p.kblocks; ++kb) {
         if (!mbar_wait(&bempty[sb], phb ^ 1u, abort_flag, p.err) ||
             !mbar_wait(&xfull[s], ph, abort_flag, p.err)) {
@@ -925,24 +931,24 @@ __global__ void __launch_bounds__(kThreadsFs, 1) k_kron_tc_fs(const __grid_const
         if (p.nsrc > 1) {
           if (full)
             fs_convert<TV, 2, true>(st, stz, brow, row, khalf, kbase, p.n_in, row_ok, beta_r,
-                                    Pout, p.rest);
+                                    Pout, p.rest, nrm);
           else
             fs_convert<TV, 2, false>(st, stz, brow, row, khalf, kbase, p.n_in, row_ok, beta_r,
-                                     Pout, p.rest);
+                                     Pout, p.rest, nrm);
         } else if (p.pro_scale) {
           if (full)
             fs_convert<TV, 0, true>(st, stz, brow, row, khalf, kbase, p.n_in, row_ok, beta_r,
-                                    Pout, p.rest);
+                                    Pout, p.rest, nrm);
           else
             fs_convert<TV, 0, false>(st, stz, brow, row, khalf, kbase, p.n_in, row_ok, beta_r,
-                                     Pout, p.rest);
+                                     Pout, p.rest, nrm);
         } else {
           if (full)
             fs_convert<TV, 1, true>(st, stz, brow, row, khalf, kbase, p.n_in, row_ok, beta_r,
-                                    Pout, p.rest);
+                                    Pout, p.rest, nrm);
           else
             fs_convert<TV, 1, false>(st, stz, brow, row, khalf, kbase, p.n_in, row_ok, beta_r,
-                                     Pout, p.rest);
+                                     Pout, p.rest, nrm);
         }
         fence_proxy_async();
         mbar_arrive(&xempty[s]);
@@ -955,6 +961,13 @@ __global__ void __launch_bounds__(kThreadsFs, 1) k_kron_tc_fs(const __grid_const
           sb = 0;
           phb ^= 1u;
         }
+      }
+      if (p.pro_nrm && ok) {
+        // per (tile, converter warp) partial of the formed input's squared norm
+        double dn = (double)nrm;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) dn += __shfl_xor_sync(0xffffffffu, dn, o);
+        if (lane == 0) p.pro_nrm[t * kDotSlots + warp] = dn;
       }
     }
   } else if (warp == kFsMmaWarp) {
@@ -1730,6 +1743,8 @@ struct TcSlabParams {
   const float* x;        // vector the MVM acts on (shift term and dot), Y's layout
   const float* q2;       // optional: Y -= gamma[r] q2 (Lanczos), Y's layout
   const double* gamma;
+  const double* scale;   // optional per right-hand side: Y = scale[r] (c_k K x + c_d d[0] x)
+                         // - gamma q2, partials of scale[r] x . Y (x unnormalised)
   const float* d;        // shift scalar (device), term c_d d[0] x
   float coeff, dcoeff;
   int64_t nslab, slabs_per_rhs;
@@ -1986,6 +2001,7 @@ __global__ void __launch_bounds__(kSlabThreads, 1)
       // GEMM 2 halves -> Y rows i2 = 64 h + 32 chalf + c, column i3 = i
       const int64_t r = sl / p.slabs_per_rhs;
       const float gam = Q2 ? (float)p.gamma[r] : 0.0f;
+      const float srr = p.scale ? (float)p.scale[r] : 1.0f;
       const int64_t sbase = sl * (int64_t)(kSlabN * kSlabN) + i;
       float part = 0.0f;
       for (int h = 0; h < 2 && ok; ++h) {
@@ -2018,7 +2034,7 @@ __global__ void __launch_bounds__(kSlabThreads, 1)
 #pragma unroll
           for (int c = 0; c < 16; ++c) {
             const int cc = hh * 16 + c;
-            float y = fmaf(sc, xv[cc], p.coeff * a[cc]);
+            float y = srr * fmaf(sc, xv[cc], p.coeff * a[cc]);
             if (Q2) y = fmaf(-gam, qv[c], y);
             part = fmaf(y, xv[cc], part);
             p.Y[i0 + (int64_t)cc * kSlabN] = y;
@@ -2030,7 +2046,7 @@ __global__ void __launch_bounds__(kSlabThreads, 1)
         double dsum = (double)part;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) dsum += __shfl_xor_sync(0xffffffffu, dsum, o);
-        if (lane == 0) p.dot[sl * kDotSlots + ew] = dsum;
+        if (lane == 0) p.dot[sl * kDotSlots + ew] = dsum * (double)srr;
       }
     }
   }
@@ -2331,6 +2347,7 @@ static bool fs_plan(const TcParams& p, TcFsParams& r) {
   r.pro_scale = (p.pro_out && !p.pro_z) ? 1 : 0;
   r.e_q2 = p.epi_q2;
   r.e_gamma = p.epi_gamma;
+  r.pro_nrm = p.pro_nrm;
   return true;
 }
 
@@ -2522,6 +2539,7 @@ struct TcFusion {
   const double* epi_gamma = nullptr;
   int out_trans = 0;  // first mode step stores slab-major (the slab kernel's input)
   int nsteps = -1;    // mode steps to run (-1: all)
+  double* pro_nrm = nullptr;
 };
 
 // Runs the d mode steps of a Kronecker MVM on the tensor cores; returns the
@@ -2616,6 +2634,7 @@ static int64_t kron_tc_run(Ctx* c, const cola_linop* op, const float* X, float* 
       p.pro_beta = fu.pro_beta;
       p.pro_out = fu.pro_out;
       p.out_trans = fu.out_trans;
+      p.pro_nrm = fu.pro_nrm;
     }
     if (last && nsteps == d) {
       p.epi_x = fu.epi_x;
@@ -2689,7 +2708,8 @@ static bool slab_ok(const cola_linop* kron) {
 // the partials of x . Y.  Returns the slabs per right-hand side (K_1's side).
 static int64_t slab_launch(Ctx* c, const cola_linop* kron, const float* T1, float* Y,
                            const float* x, const float* q2, const double* gamma, const float* d,
-                           float coeff, float dcoeff, double* dot, int64_t R) {
+                           float coeff, float dcoeff, double* dot, int64_t R,
+                           const double* scale = nullptr) {
   const int tf = (int)kron->derived.at(200).bytes;
   const int tv = std::max(1, std::min(3, c->split_vector_terms));
   TcSlabParams sp{};
@@ -2702,6 +2722,7 @@ static int64_t slab_launch(Ctx* c, const cola_linop* kron, const float* T1, floa
   sp.x = x;
   sp.q2 = q2;
   sp.gamma = gamma;
+  sp.scale = scale;
   sp.d = d;
   sp.coeff = coeff;
   sp.dcoeff = dcoeff;
@@ -2795,6 +2816,63 @@ int64_t kron_tc_lanczos_mvm(Ctx* c, const cola_linop* op, const float* w_in,
   fu.epi_q2 = q_prev;
   fu.epi_gamma = gamma;
   return kron_tc_run(c, kron, w_in, w_out, R, op->coeffs[ik], 0.0, depth, false, fu);
+}
+
+// Lanczos with unnormalised vectors on a slab-shaped operator (see
+// kron_tc_lanczos_unnormalised): the kron node and diagonal of Sum(Kron, Diag).
+static bool lanczos_parts(const cola_linop* op, const cola_linop** kron, const cola_linop** dg,
+                          int* ik, int* id) {
+  if (op->kind != LK_SUM || op->kids.size() != 2) return false;
+  *ik = -1;
+  *id = -1;
+  for (int i = 0; i < 2; ++i) {
+    if (op->kids[i]->kind == LK_KRON) *ik = i;
+    if (op->kids[i]->kind == LK_DIAG && op->kids[i]->stride == 0) *id = i;
+  }
+  if (*ik < 0 || *id < 0) return false;
+  *kron = op->kids[*ik];
+  *dg = op->kids[*id];
+  return (*kron)->derived.count(200) && slab_ok(*kron);
+}
+
+bool kron_tc_lanczos_unnormalised(const cola_linop* op) {
+  const cola_linop *kron, *dg;
+  int ik, id;
+  return lanczos_parts(op, &kron, &dg, &ik, &id);
+}
+
+int64_t kron_tc_lanczos_step1(Ctx* c, const cola_linop* op, const float* v_prev, const float* w,
+                              const double* coef, float* v_out, double* nrm, int64_t R,
+                              int depth) {
+  const cola_linop *kron, *dg;
+  int ik, id;
+  COLA_REQUIRE(lanczos_parts(op, &kron, &dg, &ik, &id), COLA_ERR_UNSUPPORTED,
+               "internal: unnormalised Lanczos needs a slab-shaped operator");
+  float* T1 = (float*)c->ws.get(depth_name("kslab", depth, 0), 4 * (size_t)kron->cols * R);
+  TcFusion f1;
+  f1.out_trans = 1;
+  f1.nsteps = 1;
+  if (w) {
+    f1.pro_z = w;
+    f1.pro_beta = coef;
+    f1.pro_out = v_out;
+    f1.pro_nrm = nrm;
+  }
+  kron_tc_run(c, kron, v_prev, T1, R, 1.0, 0.0, depth, false, f1);
+  return (kron->cols / kron->kids[0]->cols + kTileM - 1) / kTileM;
+}
+
+int64_t kron_tc_lanczos_slab(Ctx* c, const cola_linop* op, const float* v, const float* v_prev,
+                             const double* gamma, const double* scale, float* w_out,
+                             double* tile_dot, int64_t R, int depth) {
+  const cola_linop *kron, *dg;
+  int ik, id;
+  COLA_REQUIRE(lanczos_parts(op, &kron, &dg, &ik, &id), COLA_ERR_UNSUPPORTED,
+               "internal: unnormalised Lanczos needs a slab-shaped operator");
+  const float* T1 = (const float*)c->ws.get(depth_name("kslab", depth, 0),
+                                            4 * (size_t)kron->cols * R);
+  return slab_launch(c, kron, T1, w_out, v, v_prev, gamma, leaf_ptr<float>(dg),
+                     (float)op->coeffs[ik], (float)op->coeffs[id], tile_dot, R, scale);
 }
 
 int64_t kron_tc_tiles_per_rhs(const cola_linop* op) {

@@ -694,6 +694,24 @@ __global__ void k_lz_recip(int64_t nv, const double* src, double* dst, int root)
   dst[v] = x > 0.0 ? 1.0 / (root ? sqrt(x) : x) : 0.0;
 }
 
+// Unnormalised Lanczos (v_j = beta_j q_j): coef = -alpha_{j-1} s_{j-1}, the
+// coefficient of v_{j-1} in v_j = w + coef v_{j-1}.
+__global__ void k_lz_coef(int64_t nv, const double* a_cur, const double* s_prev, double* coef) {
+  const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (v < nv) coef[v] = -a_cur[v] * s_prev[v];
+}
+
+// s_j = 1 / beta_j (0 after a breakdown, beta_j = 0) and gamma = beta_j s_{j-1},
+// the coefficient of v_{j-1} in w = A q_j - beta_j q_{j-1}.
+__global__ void k_lz_scales(int64_t nv, const double* b_cur, const double* s_prev, double* s_new,
+                            double* gamma) {
+  const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= nv) return;
+  const double b = b_cur[v];
+  s_new[v] = b > 0.0 ? 1.0 / b : 0.0;
+  gamma[v] = b * s_prev[v];
+}
+
 __global__ void k_lz_meff(const LzState* st, int64_t nv, int* m_eff) {
   const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (v < nv) m_eff[v] = st[v].m_eff;
@@ -1442,10 +1460,90 @@ namespace cola {
 // vector pass then forms w -= alpha_j q_j and ||w||^2, the same recurrence
 // and breakdown test as the unfused loop.  false when the operator does not
 // have this shape.
+// The fused Lanczos step with unnormalised basis vectors v_j = beta_j q_j
+// (slab-shaped operators): the first mode step forms v_j = w - alpha_{j-1}
+// s_{j-1} v_{j-1} from the two streams and the partials of ||v_j||^2, so no
+// separate pass subtracts alpha q and normalises; the slab kernel's epilogue
+// applies s_j = 1 / beta_j.  The same recurrence as Algorithm 1 (Table 5)
+// with the division by beta_j moved after the Kronecker product.
+static void lanczos_unnormalised(Ctx* c, cola_linop* op, const float* Q0, int64_t nv, int m,
+                                 double* alpha, double* beta, int* m_eff) {
+  const int64_t N = op->rows;
+  const int nblk = dot_blocks(N);
+  auto& ws = c->ws;
+  const int64_t tiles = kron_tc_tiles_per_rhs(op);  // slabs per right-hand side
+  float* w = (float*)ws.get("lz.0", sizeof(float) * N * nv);
+  float* vb[2] = {(float*)ws.get("lz.1", sizeof(float) * N * nv),
+                  (float*)ws.get("lz.2", sizeof(float) * N * nv)};
+  double* tdot = (double*)ws.get("lz.tdot", 8 * 8 * (size_t)tiles * nv);
+  double* part = (double*)ws.get("lz.part", 8 * nblk * nv);
+  double* nrm2 = (double*)ws.get("lz.nrm2", 8 * nv);
+  double* a_cur = (double*)ws.get("lz.a", 8 * nv);
+  double* b_cur = (double*)ws.get("lz.b", 8 * nv);
+  double* coef = (double*)ws.get("lz.coef", 8 * nv);
+  double* gam = (double*)ws.get("lz.gam", 8 * nv);
+  double* sc[2] = {(double*)ws.get("lz.s0", 8 * nv), (double*)ws.get("lz.s1", 8 * nv)};
+  LzState* st = (LzState*)ws.get("lz.st", sizeof(LzState) * nv);
+  const unsigned vb_ = (unsigned)((nv + 127) / 128);
+  COLA_CUDA(cudaMemsetAsync(alpha, 0, 8 * nv * m, c->s));
+  COLA_CUDA(cudaMemsetAsync(beta, 0, 8 * nv * m, c->s));
+  COLA_CUDA(cudaMemsetAsync(b_cur, 0, 8 * nv, c->s));
+  COLA_CUDA(cudaMemsetAsync(gam, 0, 8 * nv, c->s));
+  dots<float>(c, Q0, Q0, N, nv, part, nrm2);
+  k_lz_init<<<vb_, 128, 0, c->s>>>(st, nrm2, nv, m);
+  c->count_launch();
+  k_lz_recip<<<vb_, 128, 0, c->s>>>(nv, nrm2, sc[0], 1);  // s_0 = 1 / ||z||
+  c->count_launch();
+  const double eps = 1e-6;
+  // step 0: v_0 = z
+  kron_tc_lanczos_step1(c, op, Q0, nullptr, nullptr, nullptr, nullptr, nv, 1);
+  double* npart = nullptr;
+  int64_t tiles1 = 0;
+  int64_t t = kron_tc_lanczos_slab(c, op, Q0, Q0, gam, sc[0], w, tdot, nv, 1);
+  COLA_REQUIRE(t == tiles, COLA_ERR_UNSUPPORTED, "internal: fused Lanczos tile count");
+  k_lz_alpha<<<(unsigned)nv, 256, 0, c->s>>>(st, tdot, (int)(8 * tiles), nv, 0, m, alpha, a_cur);
+  c->count_launch();
+  for (int j = 1; j < m; ++j) {
+    const float* vprev = (j == 1) ? Q0 : vb[(j - 1) & 1];
+    float* vj = vb[j & 1];
+    double* s_prev = sc[(j - 1) & 1];
+    double* s_new = sc[j & 1];
+    k_lz_coef<<<vb_, 128, 0, c->s>>>(nv, a_cur, s_prev, coef);
+    c->count_launch();
+    if (!npart) {
+      const cola_linop* kr = op->kids[0]->kind == LK_KRON ? op->kids[0] : op->kids[1];
+      tiles1 = (kr->cols / kr->kids[0]->cols + 127) / 128;
+      npart = (double*)ws.get("lz.npart", 8 * 8 * (size_t)tiles1 * nv);
+    }
+    const int64_t t1 = kron_tc_lanczos_step1(c, op, vprev, w, coef, vj, npart, nv, 1);
+    COLA_REQUIRE(t1 == tiles1, COLA_ERR_UNSUPPORTED, "internal: fused Lanczos step-1 tiles");
+    dot_final(c, npart, (int)(8 * tiles1), nv, nrm2);
+    k_lz_beta<<<vb_, 128, 0, c->s>>>(st, nrm2, nv, j - 1, m, eps, beta, b_cur);
+    c->count_launch();
+    k_lz_scales<<<vb_, 128, 0, c->s>>>(nv, b_cur, s_prev, s_new, gam);
+    c->count_launch();
+    t = kron_tc_lanczos_slab(c, op, vj, vprev, gam, s_new, w, tdot, nv, 1);
+    COLA_REQUIRE(t == tiles, COLA_ERR_UNSUPPORTED, "internal: fused Lanczos tile count");
+    k_lz_alpha<<<(unsigned)nv, 256, 0, c->s>>>(st, tdot, (int)(8 * tiles), nv, j, m, alpha,
+                                               a_cur);
+    c->count_launch();
+  }
+  // the last step: every right-hand side still running took all m steps
+  k_lz_beta<<<vb_, 128, 0, c->s>>>(st, nrm2, nv, m - 1, m, eps, beta, b_cur);
+  c->count_launch();
+  k_lz_meff<<<vb_, 128, 0, c->s>>>(st, nv, m_eff);
+  c->count_launch();
+  COLA_CUDA(cudaGetLastError());
+}
+
 static bool lanczos_fused(Ctx* c, cola_linop* op, const float* Q0, int64_t nv, int m,
                           double* alpha, double* beta, int* m_eff) {
   const int64_t tiles = kron_tc_tiles_per_rhs(op);
   if (tiles <= 0) return false;
+  if (kron_tc_lanczos_unnormalised(op)) {
+    lanczos_unnormalised(c, op, Q0, nv, m, alpha, beta, m_eff);
+    return true;
+  }
   const int64_t N = op->rows;
   const int nblk = dot_blocks(N);
   auto& ws = c->ws;

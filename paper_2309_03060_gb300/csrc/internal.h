@@ -244,9 +244,13 @@ void rademacher(Ctx* c, uint64_t seed, int64_t offset, int64_t count, void* out,
 template <typename T>
 void diag_apply(Ctx* c, const T* d, int64_t stride, const T* X, T* Y, int64_t n, int64_t R,
                 double coeff, double beta);
+// Kronecker sum of tridiagonal factors; with dg, also the diagonal term
+// dcoeff Diag(d) X in the same pass where the two-factor kernel runs (returns
+// true then; false: the caller applies the diagonal itself).
 template <typename T>
-void stencil_apply(Ctx* c, int nf, const int64_t* sizes, const T* bands, const T* X, T* Y,
-                   int64_t R, double coeff, double beta);
+bool stencil_apply(Ctx* c, int nf, const int64_t* sizes, const T* bands, const T* X, T* Y,
+                   int64_t R, double coeff, double beta, const T* dg = nullptr,
+                   int64_t dstride = 0, double dcoeff = 0.0);
 // Blocks of the low-rank V^T X reduction: partials hold kLowRankBlocks * k * R doubles.
 constexpr int kLowRankBlocks = 608;
 template <typename T>

@@ -364,10 +364,12 @@ struct StencilP {
 // Kronecker sum of tridiagonal factors: y = coeff * sum_k (A_k along mode k) x + beta y.
 // Two-factor Kronecker sum of tridiagonal factors (n1 x n2 grid, rows of n2
 // contiguous): four consecutive i2 of one row per thread, 32-bit indices within
-// a vector; the same terms in the same order as k_stencil.
+// a vector; the same terms in the same order as k_stencil.  Optionally a
+// diagonal term in the same pass: y += dcoeff d (.) x (d per element when
+// dstride != 0, else d[0]).
 template <typename T>
 __global__ void k_stencil2(const T* bands, const T* X, T* Y, int n1, int n2, int64_t R, T coeff,
-                           T beta) {
+                           T beta, const T* dg, int64_t dstride, T dcoeff) {
   const int q4 = n2 / 4;
   const int64_t tot = (int64_t)n1 * q4 * R;
   const T* lo0 = bands;
@@ -401,6 +403,15 @@ __global__ void k_stencil2(const T* bands, const T* X, T* Y, int n1, int n2, int
       if (j > 0) v = fma(lo1[j], e > 0 ? xc[e - 1] : xl, v);
       if (j < n2 - 1) v = fma(up1[j], e < 3 ? xc[e + 1] : xr, v);
       out[e] = v * coeff;
+    }
+    if (dg) {
+      T dd[4];
+      if (dstride)
+        ld4(dd, dg + (int64_t)i1 * n2 + i2);
+      else
+        dd[0] = dd[1] = dd[2] = dd[3] = dg[0];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) out[e] = fma(dcoeff * dd[e], xc[e], out[e]);
     }
     T* y = Y + r * N + (int64_t)i1 * n2 + i2;
     if (beta != T(0)) {
@@ -528,13 +539,63 @@ __global__ void __launch_bounds__(256) k_lr_uw_t(const T* Ut, const T* W, T* Y, 
         for (int q = 0; q < 8; ++q)
           if (r0 + q < R) acc[q] = fma(u, Ws[k * R + r0 + q], acc[q]);
       }
+      // every load of the group's old y before its stores
+      T yo[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q)
+        yo[q] = (beta != T(0) && r0 + q < R) ? Y[(r0 + q) * n + i] : T(0);
+#pragma unroll
+      for (int q = 0; q < 8; ++q)
+        if (r0 + q < R) Y[(r0 + q) * n + i] = coeff * acc[q] + beta * yo[q];
+    }
+  }
+}
+
+// FP32 form of k_lr_uw_t with four consecutive outputs per thread: 16-byte
+// loads of the rows of Ut and of Y.
+__global__ void __launch_bounds__(256) k_lr_uw_t4(const float* Ut, const float* W, float* Y,
+                                                  int64_t n, int kdim, int64_t R, float coeff,
+                                                  float beta) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float* Ws = reinterpret_cast<float*>(smem_raw);
+  for (int64_t e = threadIdx.x; e < kdim * R; e += blockDim.x) Ws[e] = W[e];
+  __syncthreads();
+  const int64_t n4 = n / 4;
+  for (int64_t i4 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i4 < n4;
+       i4 += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = 4 * i4;
+    for (int64_t r0 = 0; r0 < R; r0 += 8) {
+      float4 acc[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) acc[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll 4
+      for (int k = 0; k < kdim; ++k) {
+        const float4 u = __ldg(reinterpret_cast<const float4*>(Ut + (int64_t)k * n + i));
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          if (r0 + q >= R) break;
+          const float w = Ws[k * R + r0 + q];
+          acc[q].x = fmaf(u.x, w, acc[q].x);
+          acc[q].y = fmaf(u.y, w, acc[q].y);
+          acc[q].z = fmaf(u.z, w, acc[q].z);
+          acc[q].w = fmaf(u.w, w, acc[q].w);
+        }
+      }
+      float4 yo[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q)
+        yo[q] = (beta != 0.0f && r0 + q < R)
+                    ? *reinterpret_cast<const float4*>(Y + (r0 + q) * n + i)
+                    : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
       for (int q = 0; q < 8; ++q) {
         if (r0 + q >= R) break;
-        T* y = Y + (r0 + q) * n + i;
-        T v = coeff * acc[q];
-        if (beta != T(0)) v += beta * *y;
-        *y = v;
+        float4 v;
+        v.x = fmaf(coeff, acc[q].x, beta * yo[q].x);
+        v.y = fmaf(coeff, acc[q].y, beta * yo[q].y);
+        v.z = fmaf(coeff, acc[q].z, beta * yo[q].z);
+        v.w = fmaf(coeff, acc[q].w, beta * yo[q].w);
+        *reinterpret_cast<float4*>(Y + (r0 + q) * n + i) = v;
       }
     }
   }
@@ -843,8 +904,10 @@ void diag_apply(Ctx* c, const T* d, int64_t stride, const T* X, T* Y, int64_t n,
 }
 
 template <typename T>
-void stencil_apply(Ctx* c, int nf, const int64_t* sizes, const T* bands, const T* X, T* Y,
-                   int64_t R, double coeff, double beta) {
+bool stencil_apply(Ctx* c, int nf, const int64_t* sizes, const T* bands, const T* X, T* Y,
+                   int64_t R, double coeff, double beta, const T* dg, int64_t dstride,
+                   double dcoeff) {
+  bool fused = false;
   COLA_REQUIRE(nf >= 1 && nf <= 8, COLA_ERR_UNSUPPORTED, "stencil: %d factors", nf);
   StencilP p{};
   p.nf = nf;
@@ -858,19 +921,21 @@ void stencil_apply(Ctx* c, int nf, const int64_t* sizes, const T* bands, const T
     p.boff[k] = off;
     off += 3 * sizes[k];
   }
-  const uintptr_t al = (uintptr_t)X | (uintptr_t)Y;
+  const uintptr_t al = (uintptr_t)X | (uintptr_t)Y | (dg && dstride ? (uintptr_t)dg : 0);
   if (nf == 2 && sizes[1] % 4 == 0 && sizes[0] < (1 << 30) && sizes[1] < (1 << 30) &&
       (al & (4 * sizeof(T) - 1)) == 0) {
     const int64_t tot = sizes[0] * (sizes[1] / 4) * R;
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((tot + 255) / 256, 152 * 32));
+    fused = dg != nullptr;
     k_stencil2<T><<<grid, kThreads, 0, c->s>>>(bands, X, Y, (int)sizes[0], (int)sizes[1], R,
-                                               (T)coeff, (T)beta);
+                                               (T)coeff, (T)beta, dg, dstride, (T)dcoeff);
   } else {
     k_stencil<T><<<grid_for(N * R, 4), kThreads, 0, c->s>>>(p, bands, X, Y, N, R, (T)coeff,
                                                             (T)beta);
   }
   c->count_launch();
   COLA_CUDA(cudaGetLastError());
+  return fused;
 }
 
 template <typename T>
@@ -900,6 +965,15 @@ void lowrank_uw(Ctx* c, const T* U, const T* W, T* Y, int64_t n, int64_t k, int6
                 double coeff, double beta, const T* Ut) {
   const size_t smem = sizeof(T) * k * R;
   COLA_REQUIRE(smem <= 48 * 1024, COLA_ERR_UNSUPPORTED, "low-rank: k*nrhs too large");
+  const uintptr_t al = (uintptr_t)Ut | (uintptr_t)Y;
+  if (Ut && sizeof(T) == 4 && n % 4 == 0 && (al & 15) == 0) {
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((n / 4 + 255) / 256, 152 * 8));
+    k_lr_uw_t4<<<grid, 256, smem, c->s>>>((const float*)Ut, (const float*)W, (float*)Y, n,
+                                          (int)k, R, (float)coeff, (float)beta);
+    c->count_launch();
+    COLA_CUDA(cudaGetLastError());
+    return;
+  }
   if (Ut) {
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 152 * 16));
     k_lr_uw_t<T><<<grid, 256, smem, c->s>>>(Ut, W, Y, n, (int)k, R, (T)coeff, (T)beta);
@@ -1005,8 +1079,8 @@ void add_partials(Ctx* c, const T* P, T* G, int64_t count, int64_t nparts, doubl
   template void scale_rows<T>(Ctx*, T*, int64_t, int64_t, const double*);                   \
   template void diag_apply<T>(Ctx*, const T*, int64_t, const T*, T*, int64_t, int64_t,      \
                               double, double);                                              \
-  template void stencil_apply<T>(Ctx*, int, const int64_t*, const T*, const T*, T*, int64_t, \
-                                 double, double);                                           \
+  template bool stencil_apply<T>(Ctx*, int, const int64_t*, const T*, const T*, T*, int64_t, \
+                                 double, double, const T*, int64_t, double);                \
   template void lowrank_vtx<T>(Ctx*, const T*, const T*, int64_t, int64_t, int64_t, T*,     \
                                double*);                                                    \
   template void lowrank_uw<T>(Ctx*, const T*, const T*, T*, int64_t, int64_t, int64_t,      \

@@ -302,11 +302,26 @@ void apply(Ctx* c, const cola_linop* op, const T* X, T* Y, int64_t R, double coe
       lowrank_uw<T>(c, U, W, Y, op->rows, op->rank, R, coeff, beta, Ut);
       break;
     }
-    case LK_SUM:
-      for (size_t i = 0; i < op->kids.size(); ++i)
+    case LK_SUM: {
+      size_t i0 = 0;
+      // a tridiagonal Kronecker sum followed by a diagonal term: one pass
+      const cola_linop* k0 = op->kids[0];
+      if (op->kids.size() >= 2 && k0->kind == LK_KRONSUM && k0->tridiag &&
+          op->kids[1]->kind == LK_DIAG) {
+        std::vector<int64_t> dims;
+        for (auto* f : k0->kids) dims.push_back(f->rows);
+        const cola_linop* dg = op->kids[1];
+        i0 = stencil_apply<T>(c, (int)dims.size(), dims.data(), band_ptr<T>(k0, tr), X, Y, R,
+                              coeff * op->coeffs[0], beta, leaf_ptr<T>(dg), dg->stride,
+                              coeff * op->coeffs[1])
+                 ? 2
+                 : 1;
+      }
+      for (size_t i = i0; i < op->kids.size(); ++i)
         apply<T>(c, op->kids[i], X, Y, R, coeff * op->coeffs[i], i == 0 ? beta : 1.0, depth + 1,
                  tr, prec);
       break;
+    }
     case LK_PRODUCT: {
       const int m = (int)op->kids.size();
       const T* cur = X;

@@ -502,6 +502,118 @@ __global__ void k_lr_vtx(const T* V, const T* X, int64_t n, int64_t kdim, int64_
   }
 }
 
+// 16-byte asynchronous global -> shared copy; src_bytes = 0 fills zeros and
+// reads nothing.
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, int src_bytes) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(src), "r"(src_bytes)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// FP32 W partials through a ring of shared-memory stages.  A block owns the
+// contiguous rows [rb0, rb1) (a multiple of 128 apart), one 32-column group
+// of V and one group of 8 right-hand sides; stage = 128 rows: V tile
+// [128][32] and X tile [8][128], copied 16 bytes at a time with cp.async
+// (kVtxStages - 1 stages in flight while one is consumed).  Lane (c, g) of
+// warp w, c = lane & 7, g = lane >> 3, multiplies the V block of rows
+// 16 w + 4 g .. + 3 and columns 4 c .. + 3 with those rows' x entries of the
+// 8 right-hand sides.  Needs n % 4 == 0, kdim % 4 == 0, 16-byte aligned V, X.
+constexpr int kVtxStages = 4;
+constexpr int kVtxStage = 128 * 32 + 8 * 128;  // floats per stage
+constexpr size_t kVtxSmem = sizeof(float) * kVtxStages * kVtxStage;
+
+__global__ void __launch_bounds__(256, 2) k_lr_vtx_cp(const float* V, const float* X, int64_t n,
+                                                     int64_t kdim, int64_t R, int64_t rpb,
+                                                     double* part) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float* sm = reinterpret_cast<float*>(smem_raw);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int c = lane & 7, g = lane >> 3;
+  const int64_t k0 = (int64_t)blockIdx.y * 32, r0 = (int64_t)blockIdx.z * 8;
+  const int kw = (int)(kdim - k0 < 32 ? kdim - k0 : 32);
+  const int64_t rb0 = (int64_t)blockIdx.x * rpb;
+  const int64_t rb1 = rb0 + rpb < n ? rb0 + rpb : n;
+  const int nst = rb0 < rb1 ? (int)((rb1 - rb0 + 127) / 128) : 0;
+  auto issue = [&](int st) {
+    float* vs = sm + (st % kVtxStages) * kVtxStage;
+    float* xs = vs + 128 * 32;
+    const int64_t i0 = rb0 + (int64_t)st * 128;
+    const int rows = (int)(rb1 - i0 < 128 ? rb1 - i0 : 128);
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {  // 1024 chunks of V: row e >> 3, columns 4 (e & 7) ..
+      const int e = tid + 256 * m, row = e >> 3, j = e & 7;
+      const bool ok = row < rows && 4 * j < kw;
+      cp_async16(vs + row * 32 + 4 * j, ok ? V + (i0 + row) * kdim + k0 + 4 * j : V, ok ? 16 : 0);
+    }
+    {  // 256 chunks of X: right-hand side tid >> 5, rows 4 (tid & 31) ..
+      const int q = tid >> 5, j = tid & 31;
+      const bool ok = 4 * j < rows && r0 + q < R;
+      cp_async16(xs + q * 128 + 4 * j, ok ? X + (r0 + q) * n + i0 + 4 * j : X, ok ? 16 : 0);
+    }
+  };
+  float acc[4][8];
+#pragma unroll
+  for (int e = 0; e < 4; ++e)
+#pragma unroll
+    for (int q = 0; q < 8; ++q) acc[e][q] = 0.f;
+#pragma unroll
+  for (int st = 0; st < kVtxStages - 1; ++st) {
+    if (st < nst) issue(st);
+    cp_async_commit();
+  }
+  const int rr = warp * 16 + 4 * g;
+  for (int st = 0; st < nst; ++st) {
+    cp_async_wait<kVtxStages - 2>();
+    __syncthreads();  // stage st landed for every thread; stage st - 1's slot is free
+    if (st + kVtxStages - 1 < nst) issue(st + kVtxStages - 1);
+    cp_async_commit();
+    const float* vs = sm + (st % kVtxStages) * kVtxStage;
+    const float* xs = vs + 128 * 32;
+    float4 v[4], x[8];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) v[u] = *reinterpret_cast<const float4*>(vs + (rr + u) * 32 + 4 * c);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) x[q] = *reinterpret_cast<const float4*>(xs + q * 128 + rr);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const float xq[4] = {x[q].x, x[q].y, x[q].z, x[q].w};
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        acc[0][q] = fmaf(v[u].x, xq[u], acc[0][q]);
+        acc[1][q] = fmaf(v[u].y, xq[u], acc[1][q]);
+        acc[2][q] = fmaf(v[u].z, xq[u], acc[2][q]);
+        acc[3][q] = fmaf(v[u].w, xq[u], acc[3][q]);
+      }
+    }
+  }
+  cp_async_wait<0>();
+  __syncthreads();
+  // the 4 row quads of a warp (shuffles), then the 8 warps in a fixed order
+  double* sh = reinterpret_cast<double*>(smem_raw);  // [8 warps][32 columns][8]
+#pragma unroll
+  for (int e = 0; e < 4; ++e)
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      double a = (double)acc[e][q];
+      a += __shfl_xor_sync(0xffffffffu, a, 8);
+      a += __shfl_xor_sync(0xffffffffu, a, 16);
+      if (g == 0) sh[(warp * 32 + 4 * c + e) * 8 + q] = a;
+    }
+  __syncthreads();
+  {
+    const int kc = tid >> 3, q = tid & 7;
+    double sum = 0.0;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) sum += sh[(w * 32 + kc) * 8 + q];
+    if (k0 + kc < kdim && r0 + q < R) part[((int64_t)blockIdx.x * kdim + k0 + kc) * R + r0 + q] = sum;
+  }
+}
+
 template <typename T>
 __global__ void k_lr_final(const double* part, int nblk, int64_t cnt, T* W) {
   // one warp per output: lane l sums blocks l, l + 32, ...; then a fixed
@@ -552,41 +664,55 @@ __global__ void __launch_bounds__(256) k_lr_uw_t(const T* Ut, const T* W, T* Y, 
 }
 
 // FP32 form of k_lr_uw_t with four consecutive outputs per thread: 16-byte
-// loads of the rows of Ut and of Y.
-__global__ void __launch_bounds__(256) k_lr_uw_t4(const float* Ut, const float* W, float* Y,
-                                                  int64_t n, int kdim, int64_t R, float coeff,
-                                                  float beta) {
+// loads of the rows of Ut and of Y, 16 rows of Ut in flight per thread, W in
+// shared memory as
+// [group of 8 right-hand sides][k][8] (zero-padded) for 16-byte broadcasts.
+__global__ void __launch_bounds__(256, 2) k_lr_uw_t4(const float* Ut, const float* W, float* Y,
+                                                    int64_t n, int kdim, int64_t R, float coeff,
+                                                    float beta) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float* Ws = reinterpret_cast<float*>(smem_raw);
-  for (int64_t e = threadIdx.x; e < kdim * R; e += blockDim.x) Ws[e] = W[e];
+  const int64_t ngr = (R + 7) / 8;
+  for (int64_t e = threadIdx.x; e < ngr * kdim * 8; e += blockDim.x) {
+    const int64_t q = e & 7, k = (e >> 3) % kdim, rg = (e >> 3) / kdim;
+    Ws[e] = rg * 8 + q < R ? W[k * R + rg * 8 + q] : 0.f;
+  }
   __syncthreads();
   const int64_t n4 = n / 4;
   for (int64_t i4 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i4 < n4;
        i4 += (int64_t)gridDim.x * blockDim.x) {
     const int64_t i = 4 * i4;
-    for (int64_t r0 = 0; r0 < R; r0 += 8) {
-      float4 acc[8];
+    for (int64_t rg = 0; rg < ngr; ++rg) {
+      const int64_t r0 = rg * 8;
+      const float* wg = Ws + rg * kdim * 8;
+      float4 acc[8], yo[8];
 #pragma unroll
       for (int q = 0; q < 8; ++q) acc[q] = make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll 4
-      for (int k = 0; k < kdim; ++k) {
-        const float4 u = __ldg(reinterpret_cast<const float4*>(Ut + (int64_t)k * n + i));
+      for (int kb = 0; kb < kdim; kb += 16) {
+        float4 u[16];
 #pragma unroll
-        for (int q = 0; q < 8; ++q) {
-          if (r0 + q >= R) break;
-          const float w = Ws[k * R + r0 + q];
-          acc[q].x = fmaf(u.x, w, acc[q].x);
-          acc[q].y = fmaf(u.y, w, acc[q].y);
-          acc[q].z = fmaf(u.z, w, acc[q].z);
-          acc[q].w = fmaf(u.w, w, acc[q].w);
+        for (int j = 0; j < 16; ++j)
+          u[j] = kb + j < kdim ? __ldg(reinterpret_cast<const float4*>(Ut + (int64_t)(kb + j) * n + i))
+                               : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          if (kb + j >= kdim) break;
+          const float4 wa = *reinterpret_cast<const float4*>(wg + (kb + j) * 8);
+          const float4 wb = *reinterpret_cast<const float4*>(wg + (kb + j) * 8 + 4);
+          const float w[8] = {wa.x, wa.y, wa.z, wa.w, wb.x, wb.y, wb.z, wb.w};
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            acc[q].x = fmaf(u[j].x, w[q], acc[q].x);
+            acc[q].y = fmaf(u[j].y, w[q], acc[q].y);
+            acc[q].z = fmaf(u[j].z, w[q], acc[q].z);
+            acc[q].w = fmaf(u[j].w, w[q], acc[q].w);
+          }
         }
       }
-      float4 yo[8];
 #pragma unroll
       for (int q = 0; q < 8; ++q)
-        yo[q] = (beta != 0.0f && r0 + q < R)
-                    ? *reinterpret_cast<const float4*>(Y + (r0 + q) * n + i)
-                    : make_float4(0.f, 0.f, 0.f, 0.f);
+        yo[q] = (beta != 0.0f && r0 + q < R) ? *reinterpret_cast<const float4*>(Y + (r0 + q) * n + i)
+                                             : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
       for (int q = 0; q < 8; ++q) {
         if (r0 + q >= R) break;
@@ -941,10 +1067,28 @@ bool stencil_apply(Ctx* c, int nf, const int64_t* sizes, const T* bands, const T
 template <typename T>
 void lowrank_vtx(Ctx* c, const T* V, const T* X, int64_t n, int64_t k, int64_t R, T* W,
                  double* partials) {
-  const int64_t ntiles = (n + 31) / 32;
-  const int nblk = (int)std::max<int64_t>(1, std::min<int64_t>((ntiles + 7) / 8, kLowRankBlocks));
-  dim3 grid(nblk, (unsigned)((k + 31) / 32), (unsigned)((R + 7) / 8));
-  k_lr_vtx<T><<<grid, 256, 0, c->s>>>(V, X, n, k, R, nblk, partials);
+  const uintptr_t al = (uintptr_t)V | (uintptr_t)X;
+  int nblk;
+  if (sizeof(T) == 4 && n % 4 == 0 && k % 4 == 0 && (al & 15) == 0) {
+    // one resident wave (2 blocks per SM), contiguous 128-row stages per block
+    static bool attr = false;
+    if (!attr) {
+      COLA_CUDA(cudaFuncSetAttribute(k_lr_vtx_cp, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)kVtxSmem));
+      attr = true;
+    }
+    const int64_t nstages = (n + 127) / 128;
+    nblk = (int)std::max<int64_t>(1, std::min<int64_t>(nstages, 2 * 152));
+    const int64_t rpb = (nstages + nblk - 1) / nblk * 128;
+    dim3 grid(nblk, (unsigned)((k + 31) / 32), (unsigned)((R + 7) / 8));
+    k_lr_vtx_cp<<<grid, 256, kVtxSmem, c->s>>>((const float*)V, (const float*)X, n, k, R, rpb,
+                                              partials);
+  } else {
+    const int64_t ntiles = (n + 31) / 32;
+    nblk = (int)std::max<int64_t>(1, std::min<int64_t>((ntiles + 7) / 8, kLowRankBlocks));
+    dim3 grid(nblk, (unsigned)((k + 31) / 32), (unsigned)((R + 7) / 8));
+    k_lr_vtx<T><<<grid, 256, 0, c->s>>>(V, X, n, k, R, nblk, partials);
+  }
   c->count_launch();
   const int64_t cnt = k * R;
   k_lr_final<T><<<(unsigned)((cnt * 32 + 255) / 256), 256, 0, c->s>>>(partials, nblk, cnt, W);
@@ -966,9 +1110,10 @@ void lowrank_uw(Ctx* c, const T* U, const T* W, T* Y, int64_t n, int64_t k, int6
   const size_t smem = sizeof(T) * k * R;
   COLA_REQUIRE(smem <= 48 * 1024, COLA_ERR_UNSUPPORTED, "low-rank: k*nrhs too large");
   const uintptr_t al = (uintptr_t)Ut | (uintptr_t)Y;
-  if (Ut && sizeof(T) == 4 && n % 4 == 0 && (al & 15) == 0) {
+  const size_t smem4 = sizeof(float) * ((R + 7) / 8) * 8 * k;
+  if (Ut && sizeof(T) == 4 && n % 4 == 0 && (al & 15) == 0 && smem4 <= 48 * 1024) {
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((n / 4 + 255) / 256, 152 * 8));
-    k_lr_uw_t4<<<grid, 256, smem, c->s>>>((const float*)Ut, (const float*)W, (float*)Y, n,
+    k_lr_uw_t4<<<grid, 256, smem4, c->s>>>((const float*)Ut, (const float*)W, (float*)Y, n,
                                           (int)k, R, (float)coeff, (float)beta);
     c->count_launch();
     COLA_CUDA(cudaGetLastError());

@@ -446,6 +446,25 @@ def test_batched_mixed_uneven_one_launch_per_step(cola, ctx):
     assert all(i["rel_residual"] <= 1e-8 for i in info)
 
 
+@pytest.mark.parametrize("n,k,nrhs", [(40004, 36, 11), (4096, 4, 8), (1048576, 32, 8)])
+def test_lowrank_vectorised_parity(cola, ctx, n, k, nrhs):
+    """The FP32 low-rank product on its 16-byte paths (n and k multiples of 4),
+    added to a diagonal term's output: a ragged last 128-row stage, a partial
+    second 32-column group, a partial second group of 8 right-hand sides, and
+    the 2^20 x 32 PDE-workload shape."""
+    r = _rs(150)
+    U = r.standard_normal((n, k)) / np.sqrt(n)
+    V = r.standard_normal((n, k)) / np.sqrt(n)
+    spec = ("sum", [("diag", 0.5 + r.random(n)), ("lowrank", U, V)], [1.0, 1.5])
+    ref = oracle_tree(spec)
+    op = gpu_tree(cola, ctx, spec, torch.float64, DEV)
+    X = r.standard_normal((nrhs, n))
+    Y = cola.cola_matvec(ctx, op, torch.tensor(X, dtype=torch.float32, device=DEV),
+                         cola.PREC_F32)
+    err = rel_max_err(Y.double().cpu().numpy(), ref.mvm(X))
+    assert err < 2e-6, err
+
+
 def test_poisson_lowrank_full_size(cola, ctx):
     """A = (L (+) L) + D + U U^T with the 1024-point Dirichlet Laplacian
     (N = 1,048,576), U 32 columns, 8 right-hand sides: Jacobi PCG in FP32 to

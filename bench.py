@@ -566,6 +566,29 @@ def run_mvm_only(args):
     ctx.close()
 
 
+def run_cg_short(args):
+    """A CG solve of the bench operator capped at --maxiter iterations (the
+    solve's kernels in their launch configuration, for profiler captures)."""
+    import torch
+    import paper_2309_03060_gb300 as cola
+    device = torch.device("cuda", 0)
+    ctx = cola.Context(0)
+    w = wl.config2(nrhs=args.nrhs)
+    op, _ = build_operator(cola, ctx, w, device)
+    B = torch.tensor(w.B, device=device)
+    opts = cola.cola_cg_opts_default(precision=cola.PREC_MIXED, refine=1, tol=w.tol,
+                                     maxiter=args.maxiter, split_factor_terms=args.fterms,
+                                     split_vector_terms=args.vterms, graph_chunk=args.chunk)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    _, info, st = cola.cola_cg_solve(ctx, op, B, opts)
+    torch.cuda.synchronize()
+    print(json.dumps({"mode": "cg-short", "nrhs": args.nrhs, "status": st,
+                      "iterations": max(i["iterations"] for i in info),
+                      "seconds": time.perf_counter() - t0, "launches": ctx.kernel_launches()}))
+    ctx.close()
+
+
 def bench_config(args, world):
     """The `config` object of the JSON line, shared by both arms."""
     return {"workload": WORKLOAD, "nrhs_per_gpu": args.nrhs, "N": 128 ** 3,
@@ -664,29 +687,35 @@ def run_ours(args):
             "h2d_bytes_per_step": B_host.numel() * 8, "d2h_bytes_per_step": Xh.numel() * 8 + 16}
            if args.e2e_steps > 0 else None)
 
-    # dominant kernel: the tensor-core Kronecker mode step, timed alone on the
-    # same operator and launch configuration as inside the solve (3 launches / MVM).
-    # Algorithmic bytes of an MVM (8 R N: X read once, Y written once, FP32;
-    # intermediates between mode steps excluded), a third of them per launch.
+    # dominant work: one MIXED Kronecker MVM of the bench operator, timed alone
+    # in the launch configuration the solve uses: the first mode step
+    # (k_kron_tc_fs, slab-major output) and the slab kernel (k_kron_tc_slab,
+    # steps 2 and 3 on chip), two launches.  Algorithmic bytes of an MVM:
+    # 8 R N (X read once, Y written once, FP32; the intermediate excluded).
     hbm, tflops, peak_src = peaks()
     Xf = torch.randn(R, w.N, dtype=torch.float32, device=device)
     Yf = torch.empty_like(Xf)
     for _ in range(3):
         cola.cola_matvec(ctx, kron, Xf, cola.PREC_MIXED, out=Yf, split_terms=terms)
+    l_mvm = ctx.kernel_launches()
+    cola.cola_matvec(ctx, kron, Xf, cola.PREC_MIXED, out=Yf, split_terms=terms)
+    launches_per_mvm = ctx.kernel_launches() - l_mvm
     reps = 20
     per_mvm = time_queued(torch, ctx, lambda: cola.cola_matvec(
         ctx, kron, Xf, cola.PREC_MIXED, out=Yf, split_terms=terms), reps)
-    per_launch = per_mvm / 3
     alg_mvm = 8.0 * R * w.N
-    achieved = alg_mvm / 3 / per_launch / 1e9
-    roofline = {"kernel": "k_kron_tc_fs (split-BF16 tcgen05 mode step)", "bound": "hbm",
+    achieved = alg_mvm / per_mvm / 1e9
+    roofline = {"kernel": "one MIXED Kronecker MVM: k_kron_tc_fs (mode 1, slab-major output) + "
+                          "k_kron_tc_slab (modes 2 and 3 on chip)",
+                "bound": "hbm",
                 "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
                 "frac": round(achieved / hbm, 4), "peak_source": peak_src,
-                "traffic": args.traffic_bytes, "launch_us": round(per_launch * 1e6, 2),
-                "alg_bytes_per_launch": alg_mvm / 3,
-                "accounting": "8 R N bytes per MVM (X read, Y written; intermediates excluded) "
-                              "/ 3 launches",
-                "moved_gbs_per_launch": round(alg_mvm / per_launch / 1e9, 1)}
+                "traffic": args.traffic_bytes, "mvm_us": round(per_mvm * 1e6, 2),
+                "launches_per_mvm": launches_per_mvm,
+                "alg_bytes_per_mvm": alg_mvm,
+                "accounting": "8 R N bytes per MVM (X read, Y written; the slab-major "
+                              "intermediate excluded) / event-timed MVM",
+                "moved_gbs": round(2 * alg_mvm / per_mvm / 1e9, 1)}
     # CG iteration roofline: 32 N R algorithmic bytes per iteration of the block
     cg_iters = sum(iters)
     it_time = t_cg / max(cg_iters, 1)
@@ -915,10 +944,10 @@ def main():
     ap.add_argument("--maxiter", type=int, default=60000)
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--cpu-iters", type=int, default=2)
-    # DRAM bytes (reads + writes) of one k_kron_tc_fs launch of this workload, from
-    # the ncu capture of the current kernel build summarised in
-    # profiles/k_kron_tc_fs_kron3_rbf128_r16.md
-    ap.add_argument("--traffic-bytes", type=float, default=211.26e6)
+    # DRAM bytes (reads + writes) of one MIXED MVM of this workload (both
+    # launches), from the ncu capture of the current kernel build summarised in
+    # profiles/ (None until one is taken)
+    ap.add_argument("--traffic-bytes", type=float, default=None)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--batched-only", action="store_true",
                     help="run only the 512-system batched workload (for profiler captures)")
@@ -959,8 +988,14 @@ def main():
     ap.add_argument("--mvm-only", action="store_true",
                     help="only run --reps MIXED MVMs of the bench operator (profiler captures)")
     ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--cg-short", action="store_true",
+                    help="one CG solve of the bench operator capped at --maxiter iterations "
+                         "(for profiler captures)")
     ap.add_argument("--with-shift", action="store_true")
     args = ap.parse_args()
+    if args.cg_short:
+        run_cg_short(args)
+        return
     if args.mvm_only:
         run_mvm_only(args)
     elif args.mvm_gp:

@@ -1732,7 +1732,6 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
 //   warp 16     MMA issue, tensor-memory allocation
 constexpr int kSlabN = 128;                       // n2 = n3
 constexpr int kSlabThreads = 32 * (kFsEpiWarps + kFsConvWarps + 1);  // 544
-constexpr uint32_t kSlabF2Col = 0, kSlabF3Col = 192, kSlabAccCol = 384;
 
 struct TcSlabParams {
   const float* S;        // [nslab][128][128] slab-major first-step output
@@ -1740,7 +1739,8 @@ struct TcSlabParams {
   const uint16_t* img3;  // split K3 image [tf][2][img_rows3][64]
   int img_rows2, img_rows3;
   float* Y;              // [nslab][128][128] output, natural layout
-  const float* x;        // vector the MVM acts on (shift term and dot), Y's layout
+  const float* x;        // vector the MVM acts on (shift term and dot), Y's layout;
+                         // nullptr: Y = c_k K S only (no shift term, no partials)
   const float* q2;       // optional: Y -= gamma[r] q2 (Lanczos), Y's layout
   const double* gamma;
   const double* scale;   // optional per right-hand side: Y = scale[r] (c_k K x + c_d d[0] x)
@@ -1777,25 +1777,119 @@ __device__ __forceinline__ void slab_put16(unsigned char* bst, int row, int c0, 
           make_uint4(w[tv][4 * h], w[tv][4 * h + 1], w[tv][4 * h + 2], w[tv][4 * h + 3]);
 }
 
-template <int TF, int TV, bool Q2>
+// Slab kernel, full-width form.  Both GEMMs of a slab run as N = 128 tiles
+// (48 MMAs each at 3 x 3 split terms) into one dominant / cross accumulator
+// pair (256 tensor-memory columns):
+//   GEMM 1  U^T = K2 S     A = K2's split image in tensor memory (192 columns)
+//   GEMM 2  Y^T = K3 U^T   A = K3's split image in shared memory (one bulk
+//                          copy per term and k block at the start)
+// One B operand buffer holds the slab's split (GEMM 1) and then the re-split
+// intermediate U (GEMM 2), tracked per 64-wide k block: GEMM 2 starts on a k
+// block of U as soon as the epilogue warps of that column half have written
+// it, and the converters write a k block of the next slab's split as soon as
+// GEMM 2 has finished reading it.  The two accumulator uses are drained by
+// different warps, so that the re-split feeding GEMM 2 never waits behind the
+// global loads and stores of the output:
+//   warps 0-7   converters: thread (row j3, k half) loads its 64 values of the
+//               next slab's S (j2 = its k half of both k blocks) and splits
+//               them into B; then drains GEMM 2 of the previous slab (lane i3,
+//               columns i2 of its half) into Y with the shift term, the
+//               Lanczos term and the partials of x . Y
+//   warp 16     MMA (one lane), tensor-memory allocation, K3 image copies
+//   warps 8-15  epilogue: K2 image into tensor memory; per slab drains GEMM 1
+//               (lane i2, columns j3 of its half) into the U split
+constexpr uint32_t kSlabAccCol = 256;  // dominant accumulator; cross term at +128
+
+// Issues the loads of 16 columns of the dominant and of the cross accumulator
+// (no wait).
+template <bool kSmall>
+__device__ __forceinline__ void slab_ld16(uint32_t taddr, uint32_t* v, uint32_t* w) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+        "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+        "=r"(v[14]), "=r"(v[15])
+      : "r"(taddr));
+  if (kSmall)
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+        : "=r"(w[0]), "=r"(w[1]), "=r"(w[2]), "=r"(w[3]), "=r"(w[4]), "=r"(w[5]), "=r"(w[6]),
+          "=r"(w[7]), "=r"(w[8]), "=r"(w[9]), "=r"(w[10]), "=r"(w[11]), "=r"(w[12]),
+          "=r"(w[13]), "=r"(w[14]), "=r"(w[15])
+        : "r"(taddr + 128u));
+}
+
+// Waits for the tensor-memory loads in flight; v (and w) are tied to the wait
+// so that no use of them moves above it.
+template <bool kSmall>
+__device__ __forceinline__ void slab_ld_wait(uint32_t* v, uint32_t* w) {
+  asm volatile("tcgen05.wait::ld.sync.aligned;"
+               : "+r"(v[0]), "+r"(v[1]), "+r"(v[2]), "+r"(v[3]), "+r"(v[4]), "+r"(v[5]),
+                 "+r"(v[6]), "+r"(v[7]), "+r"(v[8]), "+r"(v[9]), "+r"(v[10]), "+r"(v[11]),
+                 "+r"(v[12]), "+r"(v[13]), "+r"(v[14]), "+r"(v[15])
+               :
+               : "memory");
+  if (kSmall)
+    asm volatile(""
+                 : "+r"(w[0]), "+r"(w[1]), "+r"(w[2]), "+r"(w[3]), "+r"(w[4]), "+r"(w[5]),
+                   "+r"(w[6]), "+r"(w[7]), "+r"(w[8]), "+r"(w[9]), "+r"(w[10]), "+r"(w[11]),
+                   "+r"(w[12]), "+r"(w[13]), "+r"(w[14]), "+r"(w[15])
+                 :
+                 : "memory");
+}
+
+// Loads 16 columns of the dominant and of the cross accumulator (one wait)
+// and returns their sums.
+template <bool kSmall>
+__device__ __forceinline__ void slab_drain16(uint32_t taddr, float* a) {
+  uint32_t v[16], w[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+        "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+        "=r"(v[14]), "=r"(v[15])
+      : "r"(taddr));
+  if (kSmall)
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+        : "=r"(w[0]), "=r"(w[1]), "=r"(w[2]), "=r"(w[3]), "=r"(w[4]), "=r"(w[5]), "=r"(w[6]),
+          "=r"(w[7]), "=r"(w[8]), "=r"(w[9]), "=r"(w[10]), "=r"(w[11]), "=r"(w[12]),
+          "=r"(w[13]), "=r"(w[14]), "=r"(w[15])
+        : "r"(taddr + 128u));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int e = 0; e < 16; ++e)
+    a[e] = __uint_as_float(v[e]) + (kSmall ? __uint_as_float(w[e]) : 0.0f);
+}
+
+// EM: 0 Y = c_k K S; 1 adds the shift term c_d d[0] x and writes the partials
+// of x . Y; 2 as 1 with the Lanczos term (- gamma q2) and the scale.
+template <int TF, int TV, int EM>
 __global__ void __launch_bounds__(kSlabThreads, 1)
     k_kron_tc_slab(const __grid_constant__ TcSlabParams p) {
+  constexpr bool Q2 = EM == 2, HX = EM >= 1;
   constexpr int kMaxT = TF > TV ? TF : TV;
   constexpr bool kSmall = TF > 1 || TV > 1;
   constexpr uint32_t kKbBytes = (uint32_t)TV * kFsBTermBytes;  // one 64-wide k block, TV terms
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* base = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
-  unsigned char* b1 = base;                 // GEMM 1 B operand: 2 k blocks
-  unsigned char* b2 = base + 2 * kKbBytes;  // GEMM 2 B operand: 2 k blocks
-  uint64_t* bars = (uint64_t*)(base + 4 * kKbBytes);
-  uint64_t* bfull = bars;         // [2] S k block split (converters)
-  uint64_t* bempty = bfull + 2;   // [2] GEMM 1 done with it (MMA commit)
-  uint64_t* b2full = bempty + 2;  // U split (epilogue)
-  uint64_t* b2empty = b2full + 1; // GEMM 2 done with it (MMA commit)
-  uint64_t* afull = b2empty + 1;  // [2] accumulator buffer computed (MMA commit)
-  uint64_t* aempty = afull + 2;   // [2] accumulator buffer drained (epilogue)
-  uint64_t* afac = aempty + 2;    // factor images in tensor memory (epilogue)
-  uint64_t* drain = afac + 1;
+  unsigned char* bbuf = base;                  // B operand: 2 k blocks x TV terms
+  unsigned char* a3 = base + 2 * kKbBytes;     // K3 image: TF terms x 2 k blocks
+  uint64_t* bars = (uint64_t*)(a3 + (size_t)TF * 2 * kFsBTermBytes);
+  uint64_t* bfull = bars;           // [2] S k block split (converters)
+  uint64_t* bfree = bfull + 2;      // [2] GEMM 2 done reading a k block (MMA commit)
+  uint64_t* ufull = bfree + 2;      // [2] U k block split (epilogue column half)
+  uint64_t* a1full = ufull + 2;     // GEMM 1 accumulated (MMA commit)
+  uint64_t* a1empty = a1full + 1;   // GEMM 1 drained (epilogue)
+  uint64_t* a2full = a1empty + 1;   // GEMM 2 accumulated (MMA commit)
+  uint64_t* a2empty = a2full + 1;   // GEMM 2 drained (converters)
+  uint64_t* afac = a2empty + 1;     // K2 image in tensor memory (epilogue)
+  uint64_t* a3full = afac + 1;      // K3 image in shared memory (bulk copies)
+  uint64_t* drain = a3full + 1;
   uint64_t* stall = drain + 1;
   uint32_t* tmem_slot = (uint32_t*)(stall + 1);
   volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
@@ -1804,13 +1898,15 @@ __global__ void __launch_bounds__(kSlabThreads, 1)
   if (tid == 0) {
     for (int s = 0; s < 2; ++s) {
       mbar_init(&bfull[s], kFsConvThreads);
-      mbar_init(&bempty[s], 1);
-      mbar_init(&afull[s], 1);
-      mbar_init(&aempty[s], kFsEpiThreads);
+      mbar_init(&bfree[s], 1);
+      mbar_init(&ufull[s], kFsEpiThreads / 2);
     }
-    mbar_init(b2full, kFsEpiThreads);
-    mbar_init(b2empty, 1);
+    mbar_init(a1full, 1);
+    mbar_init(a1empty, kFsEpiThreads);
+    mbar_init(a2full, 1);
+    mbar_init(a2empty, kFsConvThreads);
     mbar_init(afac, kFsEpiThreads);
+    mbar_init(a3full, 1);
     mbar_init(drain, 1);
     mbar_init(stall, 1);
     *abort_flag = 0;
@@ -1830,61 +1926,132 @@ __global__ void __launch_bounds__(kSlabThreads, 1)
   pdl_trigger();
 
   if (warp < kFsConvWarps) {
-    // ------------------------------------------------------------ converters
+    // ---------------------------------------- converters and GEMM 2 drains
     pdl_wait();
-    const int row = (warp & 3) * 32 + lane;  // j3: row of the B operand
-    const int khalf = warp >> 2;             // 32 of the 64 k (= j2) of a block
-    int64_t it = 0;
-    bool ok = true;
-    for (int64_t sl = blockIdx.x; sl < p.nslab && ok; sl += gridDim.x, ++it) {
+    const int row = (warp & 3) * 32 + lane;  // j3: row of the B operand; i3: TMEM lane
+    const int khalf = warp >> 2;             // 32 of the 64 k (= j2) of a block; i2 half
+    const uint32_t taddr =
+        tmem_base + ((uint32_t)((warp & 3) * 32) << 16) + kSlabAccCol + (uint32_t)khalf * 64u;
+    const float sc = HX ? p.dcoeff * p.d[0] : 0.0f;
+    float v[2][32];
+    auto load_s = [&](int64_t sl) {
       const float* src = p.S + sl * (int64_t)(kSlabN * kSlabN) + row;
-      // both k blocks' values in flight together (one load latency per slab)
-      float v[2][32];
 #pragma unroll
       for (int kb = 0; kb < 2; ++kb)
 #pragma unroll
         for (int e = 0; e < 32; ++e)
           v[kb][e] = __ldg(src + (int64_t)(kb * 64 + khalf * 32 + e) * kSlabN);
+    };
+    // GEMM 2 of slab sl (its it-th): Y[i2][i3], i3 = row, i2 = 64 khalf + c
+    auto drain_y = [&](int64_t sl, int64_t it) -> bool {
+      if (!mbar_wait(a2full, (uint32_t)(it & 1), abort_flag, p.err)) return false;
+      tc_fence_after();
+      float a[64];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) slab_drain16<kSmall>(taddr + (uint32_t)q * 16u, a + 16 * q);
+      tc_fence_before();
+      mbar_arrive(a2empty);
+      const int64_t r = sl / p.slabs_per_rhs;
+      const float gam = Q2 ? (float)p.gamma[r] : 0.0f;
+      const float srr = (HX && p.scale) ? (float)p.scale[r] : 1.0f;
+      const int64_t i0 = sl * (int64_t)(kSlabN * kSlabN) + (int64_t)(khalf * 64) * kSlabN + row;
+      constexpr int kBlk = 16;
+      float part = 0.0f;
+#pragma unroll
+      for (int blk = 0; blk < 64 / kBlk; ++blk) {
+        float xv[kBlk], qv[Q2 ? kBlk : 1];
+#pragma unroll
+        for (int c = 0; c < kBlk; ++c) {
+          const int64_t o = i0 + (int64_t)(blk * kBlk + c) * kSlabN;
+          xv[c] = HX ? __ldg(p.x + o) : 0.0f;
+          if (Q2) qv[c] = gam != 0.0f ? __ldg(p.q2 + o) : 0.0f;
+        }
+#pragma unroll
+        for (int c = 0; c < kBlk; ++c) {
+          const int cc = blk * kBlk + c;
+          float y = HX ? srr * fmaf(sc, xv[c], p.coeff * a[cc]) : p.coeff * a[cc];
+          if (Q2) y = fmaf(-gam, qv[c], y);
+          if (HX) part = fmaf(y, xv[c], part);
+          p.Y[i0 + (int64_t)cc * kSlabN] = y;
+        }
+      }
+      if (HX && p.dot) {
+        double dsum = (double)part;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) dsum += __shfl_xor_sync(0xffffffffu, dsum, o);
+        if (lane == 0) p.dot[sl * kDotSlots + warp] = dsum * (double)srr;
+      }
+      return true;
+    };
+    // Iteration `it` loads slab sl's values (issued right after the previous
+    // iteration's output stores, they land while the GEMMs of the previous
+    // slab run), writes its split into each k block of B once GEMM 2 of the
+    // previous slab has finished reading it, then stores the previous slab's
+    // output.
+    int64_t it = 0;
+    bool ok = true;
+    for (int64_t sl = blockIdx.x; sl < p.nslab; sl += gridDim.x, ++it) {
+      load_s(sl);
 #pragma unroll
       for (int kb = 0; kb < 2; ++kb) {
-        if (!mbar_wait(&bempty[kb], (uint32_t)(it & 1) ^ 1u, abort_flag, p.err)) {
+        if (!mbar_wait(&bfree[kb], (uint32_t)(it & 1) ^ 1u, abort_flag, p.err)) {
           ok = false;
           break;
         }
-        unsigned char* bst = b1 + (size_t)kb * kKbBytes;
+        unsigned char* bst = bbuf + (size_t)kb * kKbBytes;
         slab_put16<TV>(bst, row, khalf * 4, v[kb]);
         slab_put16<TV>(bst, row, khalf * 4 + 2, v[kb] + 16);
         fence_proxy_async();
         mbar_arrive(&bfull[kb]);
       }
+      if (!ok) break;
+      if (it > 0 && !drain_y(sl - gridDim.x, it - 1)) {
+        ok = false;
+        break;
+      }
     }
+    if (ok && it > 0) drain_y(blockIdx.x + (it - 1) * (int64_t)gridDim.x, it - 1);
   } else if (warp == kFsMmaWarp) {
     // ------------------------------------------------------------------- MMA
     if (lane == 0) {
-      constexpr uint32_t idesc = idesc_bf16(kTileM, 64);  // M = outputs, N = 64 columns
-      bool ok = mbar_wait(afac, 0, abort_flag, p.err);
+      constexpr uint32_t idesc = idesc_bf16(kTileM, kSlabN);  // M = outputs, N = 128 rows
+      // K3's split image: TF terms x 2 k blocks of 128 swizzled rows
+      mbar_arrive_expect_tx(a3full, (uint32_t)(TF * 2) * kFsBTermBytes);
+#pragma unroll
+      for (int b = 0; b < TF * 2; ++b)
+        bulk_g2s(a3 + (size_t)b * kFsBTermBytes, p.img3 + (size_t)b * p.img_rows3 * kBlockK,
+                 kFsBTermBytes, a3full);
+      bool ok = mbar_wait_own(a3full, 0, p.err) && mbar_wait(afac, 0, abort_flag, p.err);
       if (ok && p.stall_ns) ok = mbar_wait_slow(stall, 0, abort_flag, p.err, p.stall_ns);
       tc_fence_after();
-      const uint32_t b1a = smem_u32(b1), b2a = smem_u32(b2);
-      int64_t it = 0, g = 0;  // slab and half-tile counters
-      // one half tile: N = 64 rows h*64.. of the B operand at bbase, all of K
-      auto half = [&](uint32_t bbase, uint32_t acol, int h) -> bool {
-        if (!mbar_wait(&aempty[0], (uint32_t)(g & 1) ^ 1u, abort_flag, p.err)) return false;
-        tc_fence_after();
-        const uint32_t d_dom = tmem_base + kSlabAccCol;
-        const uint32_t d_small = d_dom + 64u;
+      // operand descriptors: base descriptor plus (offset >> 4), the 14-bit
+      // address field holding any shared-memory address below 256 KB
+      const uint64_t bdesc0 = sw128_desc(smem_u32(bbuf)), adesc0 = sw128_desc(smem_u32(a3));
+      const uint32_t d_dom = tmem_base + kSlabAccCol, d_small = d_dom + 128u;
+      int64_t it = 0;
+      for (int64_t sl = blockIdx.x; sl < p.nslab && ok; sl += gridDim.x, ++it) {
+        const uint32_t ph = (uint32_t)(it & 1);
+        // GEMM 1: A = K2 (tensor memory), B = S split; the accumulator is free
+        // once the converters drained GEMM 2 of the previous slab
+        if (!mbar_wait(a2empty, ph ^ 1u, abort_flag, p.err)) break;
         uint32_t acc_small = 0;
-        for (int kb = 0; kb < 2; ++kb)
-          for (int kk = 0; kk < 4; ++kk) {
+        for (int kb = 0; kb < 2 && ok; ++kb) {
+          if (!mbar_wait(&bfull[kb], ph, abort_flag, p.err)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+#pragma unroll
+          for (int kk = 0; kk < 4; ++kk)
 #pragma unroll
             for (int ti = 0; ti < TF; ++ti)
 #pragma unroll
               for (int tv = 0; tv < TV; ++tv) {
                 if (ti + tv >= kMaxT) continue;
-                const uint32_t a = tmem_base + acol + (uint32_t)(ti * 64 + kb * 32 + kk * 8);
-                const uint64_t bd = sw128_desc(bbase + (uint32_t)kb * kKbBytes +
-                                               (uint32_t)tv * kFsBTermBytes +
-                                               (uint32_t)h * 8192u + (uint32_t)kk * 32u);
+                const uint32_t a = tmem_base + (uint32_t)(ti * 64 + kb * 32 + kk * 8);
+                const uint64_t bd =
+                    bdesc0 + (((uint32_t)kb * kKbBytes + (uint32_t)tv * kFsBTermBytes +
+                               (uint32_t)kk * 32u) >> 4);
                 if (ti == 0 && tv == 0) {
                   mma_bf16_ta(d_dom, a, bd, idesc, (kb | kk) ? 1u : 0u);
                 } else {
@@ -1892,31 +2059,41 @@ __global__ void __launch_bounds__(kSlabThreads, 1)
                   acc_small = 1;
                 }
               }
+        }
+        if (!ok) break;
+        mma_commit(a1full);
+        // GEMM 2: A = K3 (shared memory), B = U split, one k block at a time
+        if (!mbar_wait(a1empty, ph, abort_flag, p.err)) break;
+        acc_small = 0;
+        for (int kb = 0; kb < 2 && ok; ++kb) {
+          if (!mbar_wait(&ufull[kb], ph, abort_flag, p.err)) {
+            ok = false;
+            break;
           }
-        mma_commit(&afull[0]);
-        ++g;
-        return true;
-      };
-      for (int64_t sl = blockIdx.x; sl < p.nslab && ok; sl += gridDim.x, ++it) {
-        const uint32_t ph = (uint32_t)(it & 1);
-        if (!mbar_wait(&bfull[0], ph, abort_flag, p.err) ||
-            !mbar_wait(&bfull[1], ph, abort_flag, p.err)) {
-          ok = false;
-          break;
+          tc_fence_after();
+#pragma unroll
+          for (int kk = 0; kk < 4; ++kk)
+#pragma unroll
+            for (int ti = 0; ti < TF; ++ti)
+#pragma unroll
+              for (int tv = 0; tv < TV; ++tv) {
+                if (ti + tv >= kMaxT) continue;
+                const uint64_t ad =
+                    adesc0 + (((uint32_t)(ti * 2 + kb) * kFsBTermBytes + (uint32_t)kk * 32u) >> 4);
+                const uint64_t bd =
+                    bdesc0 + (((uint32_t)kb * kKbBytes + (uint32_t)tv * kFsBTermBytes +
+                               (uint32_t)kk * 32u) >> 4);
+                if (ti == 0 && tv == 0) {
+                  mma_bf16(d_dom, ad, bd, idesc, (kb | kk) ? 1u : 0u);
+                } else {
+                  mma_bf16(d_small, ad, bd, idesc, acc_small);
+                  acc_small = 1;
+                }
+              }
+          mma_commit(&bfree[kb]);
         }
-        tc_fence_after();
-        for (int h = 0; h < 2 && ok; ++h) ok = half(b1a, kSlabF2Col, h);
         if (!ok) break;
-        mma_commit(&bempty[0]);
-        mma_commit(&bempty[1]);
-        if (!mbar_wait(b2full, ph, abort_flag, p.err)) {
-          ok = false;
-          break;
-        }
-        tc_fence_after();
-        for (int h = 0; h < 2 && ok; ++h) ok = half(b2a, kSlabF3Col, h);
-        if (!ok) break;
-        mma_commit(b2empty);
+        mma_commit(a2full);
       }
       mma_commit(drain);
       mbar_wait_own(drain, 0, p.err);
@@ -1924,130 +2101,56 @@ __global__ void __launch_bounds__(kSlabThreads, 1)
     __syncwarp();
   } else {
     // -------------------------------------------------------------- epilogue
-    const int ew = warp - kFsConvWarps;         // 0..7
+    const int ew = warp - kFsConvWarps;  // 0..7
     const int quarter_l = warp & 3, chalf = ew >> 2;
-    const int i = quarter_l * 32 + lane;        // TMEM lane: i2 (GEMM 1) / i3 (GEMM 2)
+    const int i = quarter_l * 32 + lane;  // TMEM lane: i2
     const uint32_t lane_off = (uint32_t)(quarter_l * 32) << 16;
-    // factor images into tensor memory: k block `chalf` of every term, row i
+    // K2's split image into tensor memory: k block `chalf` of every term, row i
 #pragma unroll
-    for (int f = 0; f < 2; ++f) {
-      const uint16_t* img = f == 0 ? p.img2 : p.img3;
-      const int rows = f == 0 ? p.img_rows2 : p.img_rows3;
-      const uint32_t col0 = f == 0 ? kSlabF2Col : kSlabF3Col;
+    for (int ti = 0; ti < TF; ++ti) {
 #pragma unroll
-      for (int ti = 0; ti < TF; ++ti) {
+      for (int hh = 0; hh < 2; ++hh) {
+        uint32_t u[16];
+        const uint4* src = reinterpret_cast<const uint4*>(
+            p.img2 + ((size_t)(ti * 2 + chalf) * p.img_rows2 + i) * kBlockK);
 #pragma unroll
-        for (int hh = 0; hh < 2; ++hh) {
-          uint32_t u[16];
-          const uint4* src = reinterpret_cast<const uint4*>(
-              img + ((size_t)(ti * 2 + chalf) * rows + i) * kBlockK);
-#pragma unroll
-          for (int c = 0; c < 4; ++c) {
-            const uint4 qv = __ldg(src + ((hh * 4 + c) ^ (i & 7)));
-            u[4 * c] = qv.x;
-            u[4 * c + 1] = qv.y;
-            u[4 * c + 2] = qv.z;
-            u[4 * c + 3] = qv.w;
-          }
-          tmem_st16(tmem_base + lane_off + col0 + (uint32_t)(ti * 64 + chalf * 32 + hh * 16),
-                    u);
+        for (int c = 0; c < 4; ++c) {
+          const uint4 qv = __ldg(src + ((hh * 4 + c) ^ (i & 7)));
+          u[4 * c] = qv.x;
+          u[4 * c + 1] = qv.y;
+          u[4 * c + 2] = qv.z;
+          u[4 * c + 3] = qv.w;
         }
+        tmem_st16(tmem_base + lane_off + (uint32_t)(ti * 64 + chalf * 32 + hh * 16), u);
       }
     }
     asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
     tc_fence_before();
     mbar_arrive(afac);
-    pdl_wait();
-    const float sc = p.dcoeff * p.d[0];
-    int64_t it = 0, g = 0;
-    bool ok = true;
-    // drains half tile g: 32 columns (this thread's half of the 64) of the
-    // dominant and cross accumulators, summed, then frees the accumulator
-    auto drain32 = [&](float* a) -> bool {
-      if (!mbar_wait(&afull[0], (uint32_t)(g & 1), abort_flag, p.err)) return false;
+    const uint32_t taddr = tmem_base + lane_off + kSlabAccCol + (uint32_t)chalf * 64u;
+    int64_t it = 0;
+    for (int64_t sl = blockIdx.x; sl < p.nslab; sl += gridDim.x, ++it) {
+      // GEMM 1 -> U split: row i2 = i of the B operand, k = j3 = 64 chalf + c
+      if (!mbar_wait(a1full, (uint32_t)(it & 1), abort_flag, p.err)) break;
       tc_fence_after();
-      const uint32_t taddr = tmem_base + lane_off + kSlabAccCol + (uint32_t)chalf * 32u;
+      // the loads of the next 16 columns are in flight while this thread
+      // splits and stores the current ones
+      uint32_t v[2][16], w[2][16];
+      slab_ld16<kSmall>(taddr, v[0], w[0]);
 #pragma unroll
-      for (int hh = 0; hh < 2; ++hh) {
-        uint32_t v[16], w[16];
-        tmem_ld16(taddr + (uint32_t)hh * 16u, v);
-        if (kSmall) tmem_ld16(taddr + 64u + (uint32_t)hh * 16u, w);
+      for (int q = 0; q < 4; ++q) {
+        slab_ld_wait<kSmall>(v[q & 1], w[q & 1]);
+        if (q < 3) slab_ld16<kSmall>(taddr + (uint32_t)(q + 1) * 16u, v[(q + 1) & 1], w[(q + 1) & 1]);
+        float a[16];
 #pragma unroll
         for (int e = 0; e < 16; ++e)
-          a[hh * 16 + e] = __uint_as_float(v[e]) + (kSmall ? __uint_as_float(w[e]) : 0.0f);
+          a[e] = __uint_as_float(v[q & 1][e]) + (kSmall ? __uint_as_float(w[q & 1][e]) : 0.0f);
+        slab_put16<TV>(bbuf + (size_t)chalf * kKbBytes, i, 2 * q, a);
       }
       tc_fence_before();
-      mbar_arrive(&aempty[0]);
-      ++g;
-      return true;
-    };
-    for (int64_t sl = blockIdx.x; sl < p.nslab && ok; sl += gridDim.x, ++it) {
-      const uint32_t ph = (uint32_t)(it & 1);
-      // GEMM 1 halves -> U split into the GEMM 2 operand (row i2, k = j3)
-      if (!mbar_wait(b2empty, ph ^ 1u, abort_flag, p.err)) break;
-      for (int h = 0; h < 2 && ok; ++h) {
-        float a[32];
-        if (!drain32(a)) {
-          ok = false;
-          break;
-        }
-        // k = j3 = 64 h + 32 chalf .. +31: block h, chunks 4 chalf .. 4 chalf + 3
-        slab_put16<TV>(b2 + (size_t)h * kKbBytes, i, 4 * chalf, a);
-        slab_put16<TV>(b2 + (size_t)h * kKbBytes, i, 4 * chalf + 2, a + 16);
-      }
-      if (!ok) break;
+      mbar_arrive(a1empty);
       fence_proxy_async();
-      mbar_arrive(b2full);
-      // GEMM 2 halves -> Y rows i2 = 64 h + 32 chalf + c, column i3 = i
-      const int64_t r = sl / p.slabs_per_rhs;
-      const float gam = Q2 ? (float)p.gamma[r] : 0.0f;
-      const float srr = p.scale ? (float)p.scale[r] : 1.0f;
-      const int64_t sbase = sl * (int64_t)(kSlabN * kSlabN) + i;
-      float part = 0.0f;
-      for (int h = 0; h < 2 && ok; ++h) {
-        // x of this half's 32 rows: read-only loads issued before the wait for
-        // the half tile, so they overlap its MMAs
-        // (with the Lanczos term: x and q2 of the first 16 rows, the second
-        // 16 after the drain, to stay within the register budget)
-        const int64_t i0 = sbase + (int64_t)(h * 64 + chalf * 32) * kSlabN;
-        constexpr int kPre = Q2 ? 16 : 32;
-        float xv[32], qv[16];
-#pragma unroll
-        for (int c = 0; c < kPre; ++c) {
-          xv[c] = __ldg(p.x + i0 + (int64_t)c * kSlabN);
-          if (Q2) qv[c] = gam != 0.0f ? __ldg(p.q2 + i0 + (int64_t)c * kSlabN) : 0.0f;
-        }
-        float a[32];
-        if (!drain32(a)) {
-          ok = false;
-          break;
-        }
-#pragma unroll
-        for (int hh = 0; hh < 2; ++hh) {
-          if (Q2 && hh == 1) {
-#pragma unroll
-            for (int c = 0; c < 16; ++c) {
-              xv[16 + c] = __ldg(p.x + i0 + (int64_t)(16 + c) * kSlabN);
-              qv[c] = gam != 0.0f ? __ldg(p.q2 + i0 + (int64_t)(16 + c) * kSlabN) : 0.0f;
-            }
-          }
-#pragma unroll
-          for (int c = 0; c < 16; ++c) {
-            const int cc = hh * 16 + c;
-            float y = srr * fmaf(sc, xv[cc], p.coeff * a[cc]);
-            if (Q2) y = fmaf(-gam, qv[c], y);
-            part = fmaf(y, xv[cc], part);
-            p.Y[i0 + (int64_t)cc * kSlabN] = y;
-          }
-        }
-      }
-      if (!ok) break;
-      if (p.dot) {
-        double dsum = (double)part;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) dsum += __shfl_xor_sync(0xffffffffu, dsum, o);
-        if (lane == 0) p.dot[sl * kDotSlots + ew] = dsum * (double)srr;
-      }
+      mbar_arrive(&ufull[chalf]);
     }
   }
 
@@ -2516,15 +2619,19 @@ static FsKernel fs_kernel(int tf, int tv) {
 }
 
 using SlabKernel = void (*)(TcSlabParams);
-static SlabKernel slab_kernel(int tf, int tv) {
-  static const SlabKernel tab[3][3] = {
-      {k_kron_tc_slab<1, 1, true>, k_kron_tc_slab<1, 2, true>, k_kron_tc_slab<1, 3, true>},
-      {k_kron_tc_slab<2, 1, true>, k_kron_tc_slab<2, 2, true>, k_kron_tc_slab<2, 3, true>},
-      {k_kron_tc_slab<3, 1, true>, k_kron_tc_slab<3, 2, true>, k_kron_tc_slab<3, 3, true>}};
-  return tab[tf - 1][tv - 1];
+static SlabKernel slab_kernel(int tf, int tv, int em) {
+#define COLA_SLAB_ROW(a, e) \
+  {k_kron_tc_slab<a, 1, e>, k_kron_tc_slab<a, 2, e>, k_kron_tc_slab<a, 3, e>}
+#define COLA_SLAB_EM(e) {COLA_SLAB_ROW(1, e), COLA_SLAB_ROW(2, e), COLA_SLAB_ROW(3, e)}
+  static const SlabKernel tab[3][3][3] = {COLA_SLAB_EM(0), COLA_SLAB_EM(1), COLA_SLAB_EM(2)};
+#undef COLA_SLAB_EM
+#undef COLA_SLAB_ROW
+  return tab[em][tf - 1][tv - 1];
 }
 
-static size_t slab_smem(int tv) { return 1024 + 4 * (size_t)tv * kFsBTermBytes + 256; }
+static size_t slab_smem(int tf, int tv) {
+  return 1024 + 2 * (size_t)(tf + tv) * kFsBTermBytes + 256;
+}
 
 struct TcFusion {
   const float* pro_z = nullptr;
@@ -2655,8 +2762,10 @@ static int64_t kron_tc_run(Ctx* c, const cola_linop* op, const float* X, float* 
         for (int b = 1; b <= 3; ++b) {
           COLA_CUDA(cudaFuncSetAttribute(fs_kernel(a, b),
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemMax));
-          COLA_CUDA(cudaFuncSetAttribute(slab_kernel(a, b),
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemMax));
+          for (int em = 0; em < 3; ++em)
+            COLA_CUDA(cudaFuncSetAttribute(slab_kernel(a, b, em),
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)slab_smem(a, b)));
           COLA_CUDA(cudaFuncSetAttribute(gemm_kernel<GemmOne>(a, b),
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)gemm_smem(a, b)));
@@ -2687,11 +2796,6 @@ static int64_t kron_tc_run(Ctx* c, const cola_linop* op, const float* X, float* 
   return last_tiles;
 }
 
-template <>
-void kron_tc_apply<float>(Ctx* c, const cola_linop* op, const float* X, float* Y, int64_t R,
-                          double coeff, double beta, int depth, bool tr) {
-  kron_tc_run(c, op, X, Y, R, coeff, beta, depth, tr, TcFusion{});
-}
 
 // The slab kernel takes K_1 (x) K_2 (x) K_3 with K_2, K_3 square 128 x 128 and
 // K_1 square of side <= 128 (the first step on the factor-stationary kernel).
@@ -2732,12 +2836,32 @@ static int64_t slab_launch(Ctx* c, const cola_linop* kron, const float* T1, floa
   sp.dot = dot;
   sp.err = tc_errflag(c);
   const int grid = (int)std::min<int64_t>(sp.nslab, c->num_sms);
-  COLA_REQUIRE(q2 != nullptr, COLA_ERR_INVALID_ARG, "internal: the slab kernel takes the "
-               "Lanczos term");
-  launch_pdl(slab_kernel(tf, tv), dim3(grid), dim3(kSlabThreads), slab_smem(tv), c->s, sp);
+  const int em = q2 ? 2 : (x ? 1 : 0);
+  launch_pdl(slab_kernel(tf, tv, em), dim3(grid), dim3(kSlabThreads),
+             slab_smem(tf, tv), c->s, sp);
   c->count_launch();
   COLA_CUDA(cudaGetLastError());
   return n1;
+}
+
+// A Kronecker product of the slab shape (see slab_ok) runs as the first mode
+// step (slab-major output) and the slab kernel (steps 2 and 3 on chip); other
+// shapes, Y = coeff K X + beta Y with beta != 0 and transposes take the d mode
+// steps.
+template <>
+void kron_tc_apply<float>(Ctx* c, const cola_linop* op, const float* X, float* Y, int64_t R,
+                          double coeff, double beta, int depth, bool tr) {
+  if (!tr && beta == 0.0 && slab_ok(op) && op->derived.count(200)) {
+    float* T1 = (float*)c->ws.get(depth_name("kslab", depth, 0), 4 * (size_t)op->cols * R);
+    TcFusion f1;
+    f1.out_trans = 1;
+    f1.nsteps = 1;
+    kron_tc_run(c, op, X, T1, R, 1.0, 0.0, depth, false, f1);
+    slab_launch(c, op, T1, Y, nullptr, nullptr, nullptr, nullptr, (float)coeff, 0.0f, nullptr,
+                R);
+    return;
+  }
+  kron_tc_run(c, op, X, Y, R, coeff, beta, depth, tr, TcFusion{});
 }
 
 // One CG MVM for A = c_k * Kron(...) + c_d * Diag(d): the first mode step forms
@@ -2759,8 +2883,20 @@ int64_t kron_tc_cg_mvm(Ctx* c, const cola_linop* op, const float* z, const doubl
   const cola_linop* dg = op->kids[id];
   if (kron->kids.size() < 2 || !tc_supported(kron)) return 0;
   if (kron->derived.find(200) == kron->derived.end()) return 0;
-  // (the slab kernel is not used here: for the CG step, whose first mode step
-  // also forms p from two input streams, the three-step path measured faster)
+  if (slab_ok(kron) && dg->stride == 0) {
+    // first mode step: p = z + beta p, written, and the slab-major T1; then
+    // steps 2 and 3 on chip with the shift term and the p . Ap partials
+    float* T1 = (float*)c->ws.get(depth_name("kslab", depth, 0), 4 * (size_t)kron->cols * R);
+    TcFusion f1;
+    f1.pro_z = z;
+    f1.pro_beta = beta_vec;
+    f1.pro_out = p_new;
+    f1.out_trans = 1;
+    f1.nsteps = 1;
+    kron_tc_run(c, kron, p_old, T1, R, 1.0, 0.0, depth, false, f1);
+    return slab_launch(c, kron, T1, Ap, p_new, nullptr, nullptr, leaf_ptr<float>(dg),
+                       (float)op->coeffs[ik], (float)op->coeffs[id], tile_dot, R);
+  }
   TcFusion fu;
   fu.pro_z = z;
   fu.pro_beta = beta_vec;

@@ -83,14 +83,29 @@ __global__ void k_seg_xr(const SegBlock* blk, const int* nblk, float* x, float* 
     const SegBlock B = blk[b];
     const float a = (float)st[B.seg].alpha;
     float s = 0.0f;
-    for (int64_t i = B.start + threadIdx.x; i < B.start + B.len; i += blockDim.x) {
-      float ri = r[i];
-      if (a != 0.0f) {
-        x[i] = fmaf(a, p[i], x[i]);
-        ri = fmaf(-a, Ap[i], ri);
-        r[i] = ri;
+    const int64_t end = B.start + B.len;
+    // four elements per thread per pass, every load issued before the stores
+    for (int64_t i0 = B.start + threadIdx.x; i0 < end; i0 += 4 * (int64_t)blockDim.x) {
+      float ri[4], xi[4], pi[4], ai[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int64_t i = i0 + (int64_t)u * blockDim.x;
+        const bool in = i < end;
+        ri[u] = in ? r[i] : 0.0f;
+        xi[u] = (in && a != 0.0f) ? x[i] : 0.0f;
+        pi[u] = (in && a != 0.0f) ? p[i] : 0.0f;
+        ai[u] = (in && a != 0.0f) ? Ap[i] : 0.0f;
       }
-      s = fmaf(ri, ri, s);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int64_t i = i0 + (int64_t)u * blockDim.x;
+        if (i < end && a != 0.0f) {
+          x[i] = fmaf(a, pi[u], xi[u]);
+          ri[u] = fmaf(-a, ai[u], ri[u]);
+          r[i] = ri[u];
+        }
+        s = fmaf(ri[u], ri[u], s);
+      }
     }
     double t = s, u = 0.0;
     block_sum_pair(t, u);

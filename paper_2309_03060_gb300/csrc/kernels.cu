@@ -268,6 +268,56 @@ __global__ void __launch_bounds__(256) k_gemm_grouped(const GemmDesc<T>* probs) 
   gemm_tile_body<T>(g, g.A, g.B, g.C);
 }
 
+// Grouped FP64 products in 32 x 32 output tiles (k in steps of 8, 256 threads
+// with 4 outputs each).  At this GPU's FP64 rate every multiply-add counts and
+// memory does not: the small tiles keep the zero padding of problems with
+// sides of 16 to 256 low (a 128 x 128 tile of a 40 x 60 problem is 85 %
+// padding).
+template <typename T>
+__global__ void __launch_bounds__(256) k_gemm_grouped32(const GemmDesc<T>* probs) {
+  constexpr int BM = 32, BN = 32, BK = 8;
+  const GemmDesc<T>& q = probs[blockIdx.z];
+  const int64_t m0 = (int64_t)blockIdx.x * BM, n0 = (int64_t)blockIdx.y * BN;
+  if (m0 >= q.M || n0 >= q.N) return;
+  __shared__ T As[BK][BM];
+  __shared__ T Bs[BK][BN];
+  const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;  // n = tx, m = 4 ty + i
+  const bool a_m_fast = (q.lam == 1), b_n_fast = (q.lbn == 1);
+  T acc[4] = {T(0), T(0), T(0), T(0)};
+  for (int64_t k0 = 0; k0 < q.K; k0 += BK) {
+    {
+      const int e = tid;  // BM * BK = 256 elements of A, 256 of B
+      int mm, kk;
+      if (a_m_fast) { mm = e % BM; kk = e / BM; } else { kk = e % BK; mm = e / BK; }
+      const int64_t m = m0 + mm, k = k0 + kk;
+      As[kk][mm] = (m < q.M && k < q.K) ? q.A[m * q.lam + k * q.lak] : T(0);
+      int nn;
+      if (b_n_fast) { nn = e % BN; kk = e / BN; } else { kk = e % BK; nn = e / BK; }
+      const int64_t n = n0 + nn, kb = k0 + kk;
+      Bs[kk][nn] = (n < q.N && kb < q.K) ? q.B[kb * q.lbk + n * q.lbn] : T(0);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      const T b = Bs[kk][tx];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) acc[i] = fma(As[kk][4 * ty + i], b, acc[i]);
+    }
+    __syncthreads();
+  }
+  const int64_t n = n0 + tx;
+  if (n >= q.N) return;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int64_t m = m0 + 4 * ty + i;
+    if (m >= q.M) continue;
+    T* p = q.C + m * q.lcm + n * q.lcn;
+    T v = q.alpha * acc[i];
+    if (q.beta != T(0)) v += q.beta * *p;
+    *p = v;
+  }
+}
+
 // ------------------------------------------------------------- reductions
 template <typename T>
 __device__ __forceinline__ double block_sum(T v) {
@@ -958,8 +1008,14 @@ void gemm_grouped(Ctx* c, const GemmDesc<T>* dev_probs, int nprob, int64_t max_m
                   int64_t max_n) {
   if (nprob <= 0) return;
   COLA_REQUIRE(nprob <= 65535, COLA_ERR_UNSUPPORTED, "grouped gemm: %d problems", nprob);
-  dim3 grid((unsigned)((max_m + 127) / 128), (unsigned)((max_n + 127) / 128), (unsigned)nprob);
-  k_gemm_grouped<T><<<grid, 256, 0, c->s>>>(dev_probs);
+  if (std::is_same<T, double>::value) {
+    dim3 grid((unsigned)((max_m + 31) / 32), (unsigned)((max_n + 31) / 32), (unsigned)nprob);
+    k_gemm_grouped32<T><<<grid, 256, 0, c->s>>>(dev_probs);
+  } else {
+    dim3 grid((unsigned)((max_m + 127) / 128), (unsigned)((max_n + 127) / 128),
+              (unsigned)nprob);
+    k_gemm_grouped<T><<<grid, 256, 0, c->s>>>(dev_probs);
+  }
   c->count_launch();
   COLA_CUDA(cudaGetLastError());
 }

@@ -390,6 +390,28 @@ def test_matvec_mixed_kron3_full_size_sampled(cola, ctx):
             assert abs(Yh[r, I] - ref) <= MIXED_TOL[3] * 3 * bound
 
 
+@pytest.mark.parametrize("n1", [1, 24, 128])
+@pytest.mark.parametrize("terms", [2, 3])
+def test_matvec_mixed_slab_path_parity(cola, ctx, n1, terms):
+    """A three-factor Kronecker product with 128 x 128 second and third
+    factors runs as the first mode step (slab-major output) and the slab
+    kernel (modes 2 and 3 on chip): every entry matches the oracle's mode
+    products within the split-term bound, for a first factor of side 1 (one
+    slab per right-hand side), a ragged 24 and the full 128, with a
+    coefficient on the product."""
+    F = [wl.rbf_factor(wl.uniform(wl.substream(640 + n1, k), (n,)), 0.15)
+         for k, n in enumerate((n1, 128, 128))]
+    spec = ("sum", [("kron", [("dense", f) for f in F])], [2.5])
+    ref = oracle_tree(spec)
+    op = gpu_tree(cola, ctx, spec, torch.float64, DEV)
+    X = _rs(641).standard_normal((3, ref.cols))
+    Y = cola.cola_matvec(ctx, op, torch.tensor(X, dtype=torch.float32, device=DEV),
+                         cola.PREC_MIXED, split_terms=terms).double().cpu().numpy()
+    bound = oracle_tree(_abs_spec(spec)).mvm(np.abs(X))
+    err = np.abs(Y - ref.mvm(X))
+    assert np.all(err <= 3 * MIXED_TOL[terms] * bound + 1e-30), float(np.max(err / bound))
+
+
 def test_matvec_on_library_stream_matches_joined_call(cola, ctx):
     """A caller working on the context's own stream (no cross-stream join)
     gets bit-identical results to a call from another stream, also for calls

@@ -494,6 +494,114 @@ __global__ void k_stencil2(const T* bands, const T* X, T* Y, int n1, int n2, int
   }
 }
 
+// k_stencil2 by strips: a thread walks S (<= kStencilStrip) rows of one column quad,
+// keeping the rows above, at and below in registers (each row of x is loaded
+// once per strip, plus one halo row at each end), and takes the left and right
+// neighbours of its quad from the adjacent lanes.  The same terms in the same
+// order as k_stencil2 (bit-identical results).  Work item t = (r, strip, quad),
+// the quad fastest; a warp runs its items together (lanes past the end only
+// take part in the exchanges).
+constexpr int kStencilStrip = 16;
+template <typename T>
+__global__ void k_stencil2s(const T* bands, const T* X, T* Y, int n1, int n2, int64_t R, T coeff,
+                            T beta, const T* dg, int64_t dstride, T dcoeff, int S) {
+  const int q4 = n2 / 4;
+  const int ns = (n1 + S - 1) / S;
+  const int64_t tot = (int64_t)R * ns * q4;
+  const T* lo0 = bands;
+  const T* di0 = bands + n1;
+  const T* up0 = bands + 2 * n1;
+  const T* lo1 = bands + 3 * n1;
+  const T* di1 = lo1 + n2;
+  const T* up1 = lo1 + 2 * n2;
+  const int64_t N = (int64_t)n1 * n2;
+  const int lane = threadIdx.x & 31;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t t0 = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); t0 < tot;
+       t0 += stride) {
+    const int64_t t = t0 + lane;
+    const bool on = t < tot;
+    const int64_t tt = on ? t : tot - 1;
+    const int cq = (int)(tt % q4);
+    const int64_t rs = tt / q4;
+    const int sidx = (int)(rs % ns);
+    const int64_t r = rs / ns;
+    const int i2 = cq * 4;
+    const int i1a = sidx * S;  // < n1
+    const int i1b = min(i1a + S, n1);
+    const T* x = X + r * N + i2;
+    T* y = Y + r * N + i2;
+    // the left neighbour comes from lane - 1 when that lane holds quad cq - 1 of
+    // the same rows, the right one from lane + 1 likewise
+    const bool l_sh = lane > 0 && cq > 0;
+    const bool r_sh = lane < 31 && cq < q4 - 1 && t + 1 < tot;
+    T b_lo1[4], b_di1[4], b_up1[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      b_lo1[e] = lo1[i2 + e];
+      b_di1[e] = di1[i2 + e];
+      b_up1[e] = up1[i2 + e];
+    }
+    T xu[4], xc[4], xd[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) xu[e] = xd[e] = T(0);
+    if (i1a > 0) ld4(xu, x + (int64_t)(i1a - 1) * n2);
+    ld4(xc, x + (int64_t)i1a * n2);
+    // every lane takes S steps (the exchanges need the whole warp); a step
+    // past the lane's strip computes and stores nothing
+    for (int k = 0; k < S; ++k) {
+      const int i1 = i1a + k;
+      const bool act = i1 < i1b;
+      const T* xrow = x + (int64_t)(act ? i1 : i1a) * n2;
+      if (act && i1 + 1 < n1) ld4(xd, xrow + n2);
+      T xl = __shfl_up_sync(0xffffffffu, xc[3], 1);
+      T xr = __shfl_down_sync(0xffffffffu, xc[0], 1);
+      if (!act) continue;
+      if (!l_sh) xl = cq > 0 ? xrow[-1] : T(0);
+      if (!r_sh) xr = cq < q4 - 1 ? xrow[4] : T(0);
+      const T a0 = di0[i1], l0 = lo0[i1], u0 = up0[i1];
+      T out[4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int j = i2 + e;
+        T v = T(0);
+        v = fma(a0, xc[e], v);
+        if (i1 > 0) v = fma(l0, xu[e], v);
+        if (i1 < n1 - 1) v = fma(u0, xd[e], v);
+        v = fma(b_di1[e], xc[e], v);
+        if (j > 0) v = fma(b_lo1[e], e > 0 ? xc[e - 1] : xl, v);
+        if (j < n2 - 1) v = fma(b_up1[e], e < 3 ? xc[e + 1] : xr, v);
+        out[e] = v * coeff;
+      }
+      if (dg) {
+        T dd[4];
+        if (dstride)
+          ld4(dd, dg + (int64_t)i1 * n2 + i2);
+        else
+          dd[0] = dd[1] = dd[2] = dd[3] = dg[0];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) out[e] = fma(dcoeff * dd[e], xc[e], out[e]);
+      }
+      T* yrow = y + (int64_t)i1 * n2;
+      if (on) {
+        if (beta != T(0)) {
+          T yo[4];
+          ld4(yo, yrow);
+#pragma unroll
+          for (int e = 0; e < 4; ++e) out[e] += beta * yo[e];
+        }
+#pragma unroll
+        for (int e = 0; e < 4; ++e) yrow[e] = out[e];
+      }
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        xu[e] = xc[e];
+        xc[e] = xd[e];
+      }
+    }
+  }
+}
+
 template <typename T>
 __global__ void k_stencil(StencilP p, const T* bands, const T* X, T* Y, int64_t N, int64_t R,
                           T coeff, T beta) {
@@ -1138,8 +1246,23 @@ bool stencil_apply(Ctx* c, int nf, const int64_t* sizes, const T* bands, const T
     const int64_t tot = sizes[0] * (sizes[1] / 4) * R;
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((tot + 255) / 256, 152 * 32));
     fused = dg != nullptr;
-    k_stencil2<T><<<grid, kThreads, 0, c->s>>>(bands, X, Y, (int)sizes[0], (int)sizes[1], R,
-                                               (T)coeff, (T)beta, dg, dstride, (T)dcoeff);
+    // strips of up to 16 rows while they leave at least 512 threads per SM;
+    // shorter strips than 8 rows do not pay for the halo rows and the lane
+    // exchanges (a single right-hand side on a 1000^2 grid, 250 k row quads,
+    // measured slower than one quad per thread)
+    const int64_t quads = R * sizes[0] * (sizes[1] / 4);
+    const int S = (int)std::min<int64_t>(kStencilStrip, quads / ((int64_t)c->num_sms * 512));
+    if (S >= 8) {
+      const int64_t items = R * ((sizes[0] + S - 1) / S) * (sizes[1] / 4);
+      const int sgrid =
+          (int)std::max<int64_t>(1, std::min<int64_t>((items + 255) / 256, 152 * 16));
+      k_stencil2s<T><<<sgrid, kThreads, 0, c->s>>>(bands, X, Y, (int)sizes[0], (int)sizes[1],
+                                                   R, (T)coeff, (T)beta, dg, dstride, (T)dcoeff,
+                                                   S);
+    } else {
+      k_stencil2<T><<<grid, kThreads, 0, c->s>>>(bands, X, Y, (int)sizes[0], (int)sizes[1], R,
+                                                 (T)coeff, (T)beta, dg, dstride, (T)dcoeff);
+    }
   } else {
     k_stencil<T><<<grid_for(N * R, 4), kThreads, 0, c->s>>>(p, bands, X, Y, N, R, (T)coeff,
                                                             (T)beta);

@@ -412,6 +412,53 @@ def test_matvec_mixed_slab_path_parity(cola, ctx, n1, terms):
     assert np.all(err <= 3 * MIXED_TOL[terms] * bound + 1e-30), float(np.max(err / bound))
 
 
+def _tridiag(n, seed):
+    r = _rs(seed)
+    T = np.diag(2.0 + r.random(n))
+    if n > 1:
+        T += np.diag(-0.5 - r.random(n - 1), 1) + np.diag(-0.5 - r.random(n - 1), -1)
+    return T
+
+
+@pytest.mark.parametrize("sides", [(1, 4), (5, 44), (37, 44), (130, 128)],
+                         ids=lambda s: f"{s[0]}x{s[1]}")
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("diag", ["per_element", "scalar"])
+def test_matvec_tridiag_kronsum_stencil_parity(cola, ctx, sides, prec, diag):
+    """A Kronecker sum of two (non-symmetric) tridiagonal factors with a
+    diagonal term runs as the two-factor stencil (one row quad per thread at
+    these sizes): every entry matches the oracle, for one row, and column-quad
+    counts that are not multiples of a warp."""
+    _stencil_case(cola, ctx, sides, prec, diag, 3)
+
+
+def _stencil_case(cola, ctx, sides, prec, diag, nrhs):
+    n1, n2 = sides
+    T1, T2 = _tridiag(n1, 650 + n1), _tridiag(n2, 651 + n2)
+    N = n1 * n2
+    dterm = ("diag", 0.5 + _rs(652).random(N)) if diag == "per_element" else ("scalar", 0.3, N)
+    spec = ("sum", [("kronsum", [("dense", T1), ("dense", T2)]), dterm], [1.5, 0.5])
+    ref = oracle_tree(spec)
+    op = gpu_tree(cola, ctx, spec, torch.float64, DEV)
+    X = _rs(653).standard_normal((nrhs, N))
+    P = cola.PREC_F64 if prec == "f64" else cola.PREC_F32
+    dt = torch.float64 if prec == "f64" else torch.float32
+    Y = cola.cola_matvec(ctx, op, torch.tensor(X, dtype=dt, device=DEV), P).double().cpu().numpy()
+    Yr = ref.mvm(X)
+    tol = 1e-13 if prec == "f64" else 1e-6
+    bound = oracle_tree(_abs_spec(spec)).mvm(np.abs(X))
+    assert np.all(np.abs(Y - Yr) <= tol * bound + 1e-300), float(np.max(np.abs(Y - Yr) / bound))
+
+
+@pytest.mark.parametrize("prec,diag", [("f32", "per_element"), ("f64", "scalar")])
+def test_matvec_tridiag_kronsum_strips_parity(cola, ctx, prec, diag):
+    """Enough rows for the stencil's strip form (a thread walks 16 rows of one
+    column quad): 1037 rows (a ragged last strip of 13), 1028 columns (257
+    quads per row, so warps straddle rows and strips), 8 right-hand sides;
+    every entry against the oracle."""
+    _stencil_case(cola, ctx, (1037, 1028), prec, diag, 8)
+
+
 def test_matvec_on_library_stream_matches_joined_call(cola, ctx):
     """A caller working on the context's own stream (no cross-stream join)
     gets bit-identical results to a call from another stream, also for calls

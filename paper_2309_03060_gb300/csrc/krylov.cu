@@ -196,7 +196,10 @@ __global__ void k_cg_r4(int64_t n4, float4* r, const float4* Ap, const float4* i
                         const CgState* st, int nblk, double* part_rz, double* part_rr) {
   pdl_trigger();
   pdl_wait();
-  const int64_t v = blockIdx.y;
+  // Right-hand sides and elements in reverse order: the MVM that wrote Ap ends
+  // with the last right-hand side's slabs, still in L2, and the next MVM starts
+  // with the first right-hand side's leading rows, left in L2 by this pass.
+  const int64_t v = gridDim.y - 1 - blockIdx.y;
   const float a = (float)st[v].alpha;
   float4* rv = r + v * n4;
   const float4* Av = Ap + v * n4;
@@ -205,9 +208,10 @@ __global__ void k_cg_r4(int64_t n4, float4* r, const float4* Ap, const float4* i
   const int64_t stride = (int64_t)nblk * blockDim.x;
   // two elements per step, both loaded before either is stored: twice the
   // bytes in flight of a one-element loop
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += 2 * stride) {
-    const int64_t j = i + stride;
-    const bool two = j < n4;
+  for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i0 < n4; i0 += 2 * stride) {
+    const int64_t j0 = i0 + stride;
+    const bool two = j0 < n4;
+    const int64_t i = n4 - 1 - i0, j = n4 - 1 - j0;
     float4 ri[2], ai[2];
     ri[0] = rv[i];
     ai[0] = a != 0.0f ? Av[i] : make_float4(0.f, 0.f, 0.f, 0.f);

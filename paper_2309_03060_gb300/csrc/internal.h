@@ -319,9 +319,11 @@ void tc_check_error(Ctx* c);        // synchronises the stream
 void tc_check_error_async(Ctx* c);  // reports an earlier call's timeout, queues a check
 // Fused MIXED CG MVM for Sum(Kron, Diag); see kron_tc.cu.  0 = not applicable.
 // p_new = z + beta p_old is formed in the first mode step (p_new != p_old).
+// rev: the first mode step walks its tiles in reverse order (and the slab
+// kernel, where used, the other way); results do not depend on it.
 int64_t kron_tc_cg_mvm(Ctx* c, const cola_linop* op, const float* z, const double* beta_vec,
                        const float* p_old, float* p_new, float* Ap, double* tile_dot, int64_t R,
-                       int depth);
+                       int depth, int rev = 0);
 int64_t kron_tc_tiles_per_rhs(const cola_linop* op);
 // Fused Lanczos MIXED MVM for Sum(Kron, scalar Diag); see kron_tc.cu.  0 = not applicable.
 int64_t kron_tc_lanczos_mvm(Ctx* c, const cola_linop* op, const float* w_in,

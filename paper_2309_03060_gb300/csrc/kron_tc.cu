@@ -72,6 +72,7 @@ struct TcParams {
   const double* epi_gamma;
   int out_trans;  // 1: store Y[r][i][m] (output index major) instead of Y[r][m][i]
   double* pro_nrm;  // with pro_z: per (tile, warp) partials of the formed input's ||p||^2
+  int rev;          // factor-stationary kernel: tiles in reverse order (same results)
                     // (factor-stationary kernel)
   // optional epilogue (last mode step, output in the input's layout):
   // Y += epi_coeff * d * epi_x (d = epi_d[0] when epi_dstride == 0), and the
@@ -670,6 +671,7 @@ struct TcFsParams {
   const float* e_q2;      // e_mode 4: previous Lanczos vector (output layout)
   const double* e_gamma;  // e_mode 4: its coefficient per right-hand side
   double* pro_nrm;        // two-source input: per (tile, converter warp) partials of ||p||^2
+  int rev;                // tiles in reverse order (same results; L2 reuse between kernels)
 };
 
 __device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t* r) {
@@ -854,7 +856,8 @@ __global__ void __launch_bounds__(kThreadsFs, 1) k_kron_tc_fs(const __grid_const
       int s = 0;
       uint32_t ph = 0;
       uint32_t issued = 0, issued_ph = 0;  // bit s: a copy went to stage s / its parity
-      for (int64_t t = blockIdx.x; t < p.ntiles && ok; t += gridDim.x) {
+      for (int64_t t0 = blockIdx.x; t0 < p.ntiles && ok; t0 += gridDim.x) {
+        const int64_t t = p.rev ? p.ntiles - 1 - t0 : t0;  // tile (order of rev)
         const int64_t r = t / p.tiles_m, m0 = (t % p.tiles_m) * kTileM;
         for (int kb = 0; kb < p.kblocks; ++kb) {
           if (!mbar_wait(&xempty[s], ph ^ 1u, abort_flag, p.err)) {
@@ -888,7 +891,8 @@ __global__ void __launch_bounds__(kThreadsFs, 1) k_kron_tc_fs(const __grid_const
     pdl_wait();
     if (lane == 0 && p.e_bytes) {
       int64_t it = 0;
-      for (int64_t t = blockIdx.x; t < p.ntiles; t += gridDim.x, ++it) {
+      for (int64_t t0 = blockIdx.x; t0 < p.ntiles; t0 += gridDim.x, ++it) {
+        const int64_t t = p.rev ? p.ntiles - 1 - t0 : t0;  // tile (order of rev)
         if (!mbar_wait(eempty, (uint32_t)(it & 1) ^ 1u, abort_flag, p.err)) break;
         const int64_t r = t / p.tiles_m, m0 = (t % p.tiles_m) * kTileM;
         const int64_t rows = (p.rest - m0 < kTileM) ? (p.rest - m0) : kTileM;
@@ -909,7 +913,8 @@ __global__ void __launch_bounds__(kThreadsFs, 1) k_kron_tc_fs(const __grid_const
     uint32_t ph = 0, phb = 0;
     const int quarter = warp & 3, khalf = warp >> 2;
     const int row = quarter * 32 + lane;
-    for (int64_t t = blockIdx.x; t < p.ntiles && ok; t += gridDim.x) {
+    for (int64_t t0 = blockIdx.x; t0 < p.ntiles && ok; t0 += gridDim.x) {
+        const int64_t t = p.rev ? p.ntiles - 1 - t0 : t0;  // tile (order of rev)
       const int64_t r = t / p.tiles_m, m0 = (t % p.tiles_m) * kTileM;
       const int64_t m = m0 + row;
       const bool row_ok = m < p.rest;
@@ -981,7 +986,7 @@ __global__ void __launch_bounds__(kThreadsFs, 1) k_kron_tc_fs(const __grid_const
       int sb = 0;
       uint32_t phb = 0;
       int64_t it = 0;
-      for (int64_t t = blockIdx.x; t < p.ntiles && ok; t += gridDim.x, ++it) {
+      for (int64_t t0 = blockIdx.x; t0 < p.ntiles && ok; t0 += gridDim.x, ++it) {
         if (!mbar_wait(dempty, (uint32_t)(it & 1) ^ 1u, abort_flag, p.err)) break;
         tc_fence_after();
         uint32_t acc_small = 0;
@@ -1066,7 +1071,8 @@ __global__ void __launch_bounds__(kThreadsFs, 1) k_kron_tc_fs(const __grid_const
     const float sc = (p.e_mode == 1 || p.e_mode == 4) ? p.e_coeff * p.e_d[0]
                                                       : (p.e_mode == 3 ? p.e_coeff : p.beta);
     int64_t it = 0;
-    for (int64_t t = blockIdx.x; t < p.ntiles; t += gridDim.x, ++it) {
+    for (int64_t t0 = blockIdx.x; t0 < p.ntiles; t0 += gridDim.x, ++it) {
+        const int64_t t = p.rev ? p.ntiles - 1 - t0 : t0;  // tile (order of rev)
       if (staged && !mbar_wait(efull, (uint32_t)(it & 1), abort_flag, p.err)) break;
       if (!mbar_wait(dfull, (uint32_t)(it & 1), abort_flag, p.err)) break;
       tc_fence_after();
@@ -1751,6 +1757,7 @@ struct TcSlabParams {
   double* dot;           // [nslab][8] partials of x . Y
   int* err;
   uint64_t stall_ns;
+  int rev;  // slabs in reverse order (same results; L2 reuse between kernels)
 };
 
 // Splits 16 FP32 values into TV BF16 terms and stores them as 16 consecutive
@@ -1990,8 +1997,9 @@ __global__ void __launch_bounds__(kSlabThreads, 1)
     // output.
     int64_t it = 0;
     bool ok = true;
+    auto slab_at = [&](int64_t k) { return p.rev ? p.nslab - 1 - k : k; };
     for (int64_t sl = blockIdx.x; sl < p.nslab; sl += gridDim.x, ++it) {
-      load_s(sl);
+      load_s(slab_at(sl));
 #pragma unroll
       for (int kb = 0; kb < 2; ++kb) {
         if (!mbar_wait(&bfree[kb], (uint32_t)(it & 1) ^ 1u, abort_flag, p.err)) {
@@ -2005,12 +2013,12 @@ __global__ void __launch_bounds__(kSlabThreads, 1)
         mbar_arrive(&bfull[kb]);
       }
       if (!ok) break;
-      if (it > 0 && !drain_y(sl - gridDim.x, it - 1)) {
+      if (it > 0 && !drain_y(slab_at(sl - gridDim.x), it - 1)) {
         ok = false;
         break;
       }
     }
-    if (ok && it > 0) drain_y(blockIdx.x + (it - 1) * (int64_t)gridDim.x, it - 1);
+    if (ok && it > 0) drain_y(slab_at(blockIdx.x + (it - 1) * (int64_t)gridDim.x), it - 1);
   } else if (warp == kFsMmaWarp) {
     // ------------------------------------------------------------------- MMA
     if (lane == 0) {
@@ -2431,6 +2439,7 @@ static bool fs_plan(const TcParams& p, TcFsParams& r) {
   r.kblocks = p.kblocks;
   r.ksteps_last = p.ksteps_last;
   r.nsrc = p.pro_z ? 2 : 1;
+  r.rev = p.rev;
   r.x_src_bytes = (uint32_t)kBlockK * kTileM * 4u;
   r.e_bytes = (r.e_mode && r.e_mode != 5)
                   ? (((uint32_t)kTileM * (uint32_t)p.n_out * 4u + 1023u) & ~1023u)
@@ -2647,6 +2656,7 @@ struct TcFusion {
   int out_trans = 0;  // first mode step stores slab-major (the slab kernel's input)
   int nsteps = -1;    // mode steps to run (-1: all)
   double* pro_nrm = nullptr;
+  int rev = 0;        // first mode step: tiles in reverse order
 };
 
 // Runs the d mode steps of a Kronecker MVM on the tensor cores; returns the
@@ -2742,6 +2752,7 @@ static int64_t kron_tc_run(Ctx* c, const cola_linop* op, const float* X, float* 
       p.pro_out = fu.pro_out;
       p.out_trans = fu.out_trans;
       p.pro_nrm = fu.pro_nrm;
+      p.rev = fu.rev;
     }
     if (last && nsteps == d) {
       p.epi_x = fu.epi_x;
@@ -2813,10 +2824,11 @@ static bool slab_ok(const cola_linop* kron) {
 static int64_t slab_launch(Ctx* c, const cola_linop* kron, const float* T1, float* Y,
                            const float* x, const float* q2, const double* gamma, const float* d,
                            float coeff, float dcoeff, double* dot, int64_t R,
-                           const double* scale = nullptr) {
+                           const double* scale = nullptr, int rev = 0) {
   const int tf = (int)kron->derived.at(200).bytes;
   const int tv = std::max(1, std::min(3, c->split_vector_terms));
   TcSlabParams sp{};
+  sp.rev = rev;
   sp.S = T1;
   sp.img2 = (const uint16_t*)kron->kids[1]->derived.at(100 + tf).p;
   sp.img3 = (const uint16_t*)kron->kids[2]->derived.at(100 + tf).p;
@@ -2871,7 +2883,7 @@ void kron_tc_apply<float>(Ctx* c, const cola_linop* op, const float* X, float* Y
 // not have this shape (the caller then takes the generic path).
 int64_t kron_tc_cg_mvm(Ctx* c, const cola_linop* op, const float* z, const double* beta_vec,
                        const float* p_old, float* p_new, float* Ap, double* tile_dot, int64_t R,
-                       int depth) {
+                       int depth, int rev) {
   if (op->kind != LK_SUM || op->kids.size() != 2) return 0;
   int ik = -1, id = -1;
   for (int i = 0; i < 2; ++i) {
@@ -2893,9 +2905,13 @@ int64_t kron_tc_cg_mvm(Ctx* c, const cola_linop* op, const float* z, const doubl
     f1.pro_out = p_new;
     f1.out_trans = 1;
     f1.nsteps = 1;
+    // the two launches run in opposite orders, so that the slab kernel starts
+    // on the part of T1 and p the first step wrote last (still in L2)
+    f1.rev = rev;
     kron_tc_run(c, kron, p_old, T1, R, 1.0, 0.0, depth, false, f1);
     return slab_launch(c, kron, T1, Ap, p_new, nullptr, nullptr, leaf_ptr<float>(dg),
-                       (float)op->coeffs[ik], (float)op->coeffs[id], tile_dot, R);
+                       (float)op->coeffs[ik], (float)op->coeffs[id], tile_dot, R, nullptr,
+                       !rev);
   }
   TcFusion fu;
   fu.pro_z = z;

@@ -192,14 +192,15 @@ __global__ void k_cg_xr4(int64_t n4, float4* x, float4* r, const float4* p, cons
 
 // k_cg_xr4 without the solution update: r -= alpha Ap, z = M^-1 r and the
 // partial dots.  x is brought up to date every kPRing iterations by k_cg_xbatch.
+// rev: right-hand sides and elements in reverse order.  The CG's kernels
+// alternate their directions so that each starts on the part of its input the
+// kernel before it wrote last (still in L2).
 __global__ void k_cg_r4(int64_t n4, float4* r, const float4* Ap, const float4* invd, float4* z,
-                        const CgState* st, int nblk, double* part_rz, double* part_rr) {
+                        const CgState* st, int nblk, double* part_rz, double* part_rr,
+                        int rev) {
   pdl_trigger();
   pdl_wait();
-  // Right-hand sides and elements in reverse order: the MVM that wrote Ap ends
-  // with the last right-hand side's slabs, still in L2, and the next MVM starts
-  // with the first right-hand side's leading rows, left in L2 by this pass.
-  const int64_t v = gridDim.y - 1 - blockIdx.y;
+  const int64_t v = rev ? gridDim.y - 1 - blockIdx.y : blockIdx.y;
   const float a = (float)st[v].alpha;
   float4* rv = r + v * n4;
   const float4* Av = Ap + v * n4;
@@ -211,7 +212,7 @@ __global__ void k_cg_r4(int64_t n4, float4* r, const float4* Ap, const float4* i
   for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i0 < n4; i0 += 2 * stride) {
     const int64_t j0 = i0 + stride;
     const bool two = j0 < n4;
-    const int64_t i = n4 - 1 - i0, j = n4 - 1 - j0;
+    const int64_t i = rev ? n4 - 1 - i0 : i0, j = rev ? n4 - 1 - j0 : j0;
     float4 ri[2], ai[2];
     ri[0] = rv[i];
     ai[0] = a != 0.0f ? Av[i] : make_float4(0.f, 0.f, 0.f, 0.f);
@@ -894,8 +895,11 @@ static void cg_iteration(Ctx* c, const cola_linop* op, CgBufs<T>& B, int64_t N, 
     const int nxt = (B.cur + 1) % kPRing;
     T* p_old = B.pp[B.cur];
     T* p_new = B.pp[nxt];
+    // odd ring positions: the first mode step runs its tiles backwards, the
+    // slab kernel forwards, the residual update backwards; even ones the
+    // other way round (each kernel starts where the one before it ended)
     kron_tc_cg_mvm(c, op, (const float*)z_of(B), B.beta_vec, (const float*)p_old,
-                   (float*)p_new, (float*)B.Ap, B.tile_dot, R, 1);
+                   (float*)p_new, (float*)B.Ap, B.tile_dot, R, 1, B.cur & 1);
     B.cur = nxt;
     B.p = p_new;
     // the small CG kernels launch normally (an early launch measured slower);
@@ -917,7 +921,8 @@ static void cg_iteration(Ctx* c, const cola_linop* op, CgBufs<T>& B, int64_t N, 
     if (vec4 && defer)
       k_cg_r4<<<rows_grid(N, R, nblk), 256, 0, c->s>>>(
           N / 4, (float4*)B.r, (const float4*)B.Ap, (const float4*)B.invd,
-          B.invd ? (float4*)B.z : nullptr, B.st, nblk, B.part_rz, B.part_rr);
+          B.invd ? (float4*)B.z : nullptr, B.st, nblk, B.part_rz, B.part_rr,
+          (B.cur & 1) ? 0 : 1);
     else if (vec4)
       k_cg_xr4<<<rows_grid(N, R, nblk), 256, 0, c->s>>>(
           N / 4, (float4*)B.x, (float4*)B.r, (const float4*)B.p, (const float4*)B.Ap,

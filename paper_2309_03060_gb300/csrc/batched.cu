@@ -76,10 +76,14 @@ __device__ __forceinline__ void block_sum_pair(double& x, double& y) {
 }
 
 // x += alpha p; r -= alpha Ap; partials of r^T r (twice: rz = rr without a preconditioner)
+// Segment blocks in reverse order: the MVM before ends with the last systems'
+// Ap (still in L2) and the pre-split pass after starts with the first systems'
+// r (left in L2 by this pass).  Each block's result is the same in any order.
 __global__ void k_seg_xr(const SegBlock* blk, const int* nblk, float* x, float* r, const float* p,
                          const float* Ap, const CgState* st, double* part_rz, double* part_rr) {
   const int nb = *nblk;
-  for (int b = blockIdx.x; b < nb; b += gridDim.x) {
+  for (int bb = blockIdx.x; bb < nb; bb += gridDim.x) {
+    const int b = nb - 1 - bb;
     const SegBlock B = blk[b];
     const float a = (float)st[B.seg].alpha;
     float s = 0.0f;

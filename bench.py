@@ -947,7 +947,7 @@ def main():
     # DRAM bytes (reads + writes) of one MIXED MVM of this workload (both
     # launches), from the ncu capture of the current kernel build summarised in
     # profiles/mvm_kron_tc_fs_slab_kron3_rbf128_r16.md
-    ap.add_argument("--traffic-bytes", type=float, default=434.5e6)
+    ap.add_argument("--traffic-bytes", type=float, default=431.2e6)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--batched-only", action="store_true",
                     help="run only the 512-system batched workload (for profiler captures)")

@@ -1234,6 +1234,7 @@ struct TcGemmLaunch {
   int stages;
   int* err;
   uint64_t stall_ns;  // > 0: time-out test (see TcParams)
+  int rev = 0;        // tiles in reverse order (same results; L2 reuse between kernels)
 };
 
 // Tile sources of the split GEMM: one problem by value (X by TMA), or a
@@ -1428,7 +1429,8 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
       uint32_t ph = 0;
       uint32_t issued = 0, issued_ph = 0;  // bit s: a copy went to stage s / its parity
       const int64_t ntiles = src.count();
-      for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+      for (int64_t t0 = blockIdx.x; t0 < ntiles && ok; t0 += gridDim.x) {
+        const int64_t t = L.rev ? ntiles - 1 - t0 : t0;
         int64_t lt;
         const TcGemmParams& p = src.get(t, lt);
         const int nc = (int)(lt % p.nchunks);
@@ -1490,7 +1492,8 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
       uint32_t ph = 0;
       int64_t it = 0;
       const int64_t ntiles = src.count();
-      for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++it) {
+      for (int64_t t0 = blockIdx.x; t0 < ntiles && ok; t0 += gridDim.x, ++it) {
+        const int64_t t = L.rev ? ntiles - 1 - t0 : t0;
         int64_t lt;
         const int kblocks = src.get(t, lt).kblocks;
         const int b = (int)(it & 1);
@@ -1547,7 +1550,8 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
     const uint32_t lane_off = (uint32_t)(quarter * 32) << 16;
     int64_t it = 0;
     const int64_t ntiles = src.count();
-    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
+    for (int64_t t0 = blockIdx.x; t0 < ntiles; t0 += gridDim.x, ++it) {
+      const int64_t t = L.rev ? ntiles - 1 - t0 : t0;
       const int b = (int)(it & 1);
       if (!mbar_wait(&afull[b], (uint32_t)((it >> 1) & 1), abort_flag, L.err)) break;
       tc_fence_after();
@@ -3296,6 +3300,10 @@ void kron_tc_gemm_batch_launch(Ctx* c, const char* tag, int tf, int tv, bool pre
     L.stall_ns = (uint64_t)c->tc_stall_ns;  // armed once by cola_test_stall_next_launch
     c->tc_stall_ns = 0;
   }
+  // the first step of a CG iteration runs its tiles backwards: it starts on
+  // the images the pre-split pass wrote last, and leaves the first problems'
+  // output in L2 for the second step, which runs forwards
+  L.rev = presplit ? 1 : 0;
   GemmTab src{probs, (const int*)c->ws.bufs.at(tagged(tag, "gtile")).p,
               (const int64_t*)c->ws.bufs.at(tagged(tag, "gfirst")).p, cnt};
   COLA_CUDA(cudaFuncSetAttribute(gemm_kernel<GemmTab>(tf, tv),

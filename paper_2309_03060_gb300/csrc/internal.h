@@ -339,12 +339,13 @@ int64_t kron_tc_lanczos_mvm(Ctx* c, const cola_linop* op, const float* w_in,
 //   slab:   w_out = s (c_k K v + c_d s v) - gamma v_prev and the per-(slab,
 //           warp) partials of (s v) . w_out (returns the slabs per RHS)
 bool kron_tc_lanczos_unnormalised(const cola_linop* op);
+// rev: tiles (slabs) in reverse order; results do not depend on it.
 int64_t kron_tc_lanczos_step1(Ctx* c, const cola_linop* op, const float* v_prev, const float* w,
                               const double* coef, float* v_out, double* nrm, int64_t R,
-                              int depth);
+                              int depth, int rev = 0);
 int64_t kron_tc_lanczos_slab(Ctx* c, const cola_linop* op, const float* v, const float* v_prev,
                              const double* gamma, const double* scale, float* w_out,
-                             double* tile_dot, int64_t R, int depth);
+                             double* tile_dot, int64_t R, int depth, int rev = 0);
 
 // One tensor-core mode-step problem of a batch (host mirror of the kernel's
 // per-problem parameters) and the launch over a device problem table.

@@ -2999,7 +2999,7 @@ bool kron_tc_lanczos_unnormalised(const cola_linop* op) {
 
 int64_t kron_tc_lanczos_step1(Ctx* c, const cola_linop* op, const float* v_prev, const float* w,
                               const double* coef, float* v_out, double* nrm, int64_t R,
-                              int depth) {
+                              int depth, int rev) {
   const cola_linop *kron, *dg;
   int ik, id;
   COLA_REQUIRE(lanczos_parts(op, &kron, &dg, &ik, &id), COLA_ERR_UNSUPPORTED,
@@ -3008,6 +3008,7 @@ int64_t kron_tc_lanczos_step1(Ctx* c, const cola_linop* op, const float* v_prev,
   TcFusion f1;
   f1.out_trans = 1;
   f1.nsteps = 1;
+  f1.rev = rev;
   if (w) {
     f1.pro_z = w;
     f1.pro_beta = coef;
@@ -3020,7 +3021,7 @@ int64_t kron_tc_lanczos_step1(Ctx* c, const cola_linop* op, const float* v_prev,
 
 int64_t kron_tc_lanczos_slab(Ctx* c, const cola_linop* op, const float* v, const float* v_prev,
                              const double* gamma, const double* scale, float* w_out,
-                             double* tile_dot, int64_t R, int depth) {
+                             double* tile_dot, int64_t R, int depth, int rev) {
   const cola_linop *kron, *dg;
   int ik, id;
   COLA_REQUIRE(lanczos_parts(op, &kron, &dg, &ik, &id), COLA_ERR_UNSUPPORTED,
@@ -3028,7 +3029,7 @@ int64_t kron_tc_lanczos_slab(Ctx* c, const cola_linop* op, const float* v, const
   const float* T1 = (const float*)c->ws.get(depth_name("kslab", depth, 0),
                                             4 * (size_t)kron->cols * R);
   return slab_launch(c, kron, T1, w_out, v, v_prev, gamma, leaf_ptr<float>(dg),
-                     (float)op->coeffs[ik], (float)op->coeffs[id], tile_dot, R, scale);
+                     (float)op->coeffs[ik], (float)op->coeffs[id], tile_dot, R, scale, rev);
 }
 
 int64_t kron_tc_tiles_per_rhs(const cola_linop* op) {

@@ -1508,7 +1508,7 @@ static void lanczos_unnormalised(Ctx* c, cola_linop* op, const float* Q0, int64_
   kron_tc_lanczos_step1(c, op, Q0, nullptr, nullptr, nullptr, nullptr, nv, 1);
   double* npart = nullptr;
   int64_t tiles1 = 0;
-  int64_t t = kron_tc_lanczos_slab(c, op, Q0, Q0, gam, sc[0], w, tdot, nv, 1);
+  int64_t t = kron_tc_lanczos_slab(c, op, Q0, Q0, gam, sc[0], w, tdot, nv, 1, 1);
   COLA_REQUIRE(t == tiles, COLA_ERR_UNSUPPORTED, "internal: fused Lanczos tile count");
   k_lz_alpha<<<(unsigned)nv, 256, 0, c->s>>>(st, tdot, (int)(8 * tiles), nv, 0, m, alpha, a_cur);
   c->count_launch();
@@ -1531,7 +1531,9 @@ static void lanczos_unnormalised(Ctx* c, cola_linop* op, const float* Q0, int64_
     c->count_launch();
     k_lz_scales<<<vb_, 128, 0, c->s>>>(nv, b_cur, s_prev, s_new, gam);
     c->count_launch();
-    t = kron_tc_lanczos_slab(c, op, vj, vprev, gam, s_new, w, tdot, nv, 1);
+    // the slab kernel walks its slabs backwards and the first mode step its
+    // tiles forwards, so each starts on what the launch before it wrote last
+    t = kron_tc_lanczos_slab(c, op, vj, vprev, gam, s_new, w, tdot, nv, 1, 1);
     COLA_REQUIRE(t == tiles, COLA_ERR_UNSUPPORTED, "internal: fused Lanczos tile count");
     k_lz_alpha<<<(unsigned)nv, 256, 0, c->s>>>(st, tdot, (int)(8 * tiles), nv, j, m, alpha,
                                                a_cur);
